@@ -1,0 +1,172 @@
+/*
+ * qaoa.h -- C ABI of the B300 LR-QAOA state-vector library (libqaoa.so).
+ *
+ * The library simulates depth-p linear-ramp QAOA (LR-QAOA) on weighted MaxCut
+ * as defined in arxiv 2604.26423, Sec. II-B:
+ *   H_C = sum_{(i,j) in E} w_ij Z_i Z_j                       (Eq. H_C)
+ *   U_C(gamma_k) = exp(-i gamma_k s H_C)                      (Eq. UC)
+ *   U_B(beta_k)  = exp(+i beta_k sum_q X_q)                   (Eq. UB)
+ *   |psi_p> = U_B(beta_{p-1}) U_C(gamma_{p-1}) ... U_B(beta_0) U_C(gamma_0) |+>^n
+ *   beta_k = (1 - k/p) dbeta, gamma_k = (k+1)/p dgamma, k = 0..p-1
+ *   C(x) = sum_{k<l} w_kl (x_k + x_l - 2 x_k x_l)             (Eq. for C(x))
+ *   r = (<C> - C_min) / (C_max - C_min)                       (Eq. r, exact mean)
+ * The integer weights w_ij enter the phases multiplied by s = weight_scale.
+ * Bit q of every amplitude or sample index is qubit q.
+ *
+ * Conventions for every call:
+ *   - Return value: QAOA_OK or one of the QAOA_E* codes below; the message of
+ *     the last failure on a context is available from qaoa_last_error().
+ *   - Host pointers are read or written before the call returns. Device
+ *     pointers must stay valid while the context uses them.
+ *   - All GPU work is ordered on the CUDA stream given to qaoa_init_graph.
+ *     Calls that return host results synchronise that stream.
+ *   - The library never frees memory it did not allocate.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef QAOA_H
+#define QAOA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define QAOA_OK 0
+#define QAOA_EINVAL 1   /* invalid argument (sizes, graph, angles, shots) */
+#define QAOA_ENOMEM 2   /* allocation failed or a caller buffer is too small */
+#define QAOA_ECUDA 3    /* a CUDA runtime call failed; see qaoa_last_error */
+#define QAOA_ETIMEOUT 4 /* a bounded device-side wait gave up (batched queue) */
+#define QAOA_ESTATE 5   /* call order violated (e.g. qaoa_expect before qaoa_run) */
+
+/* state precision: complex64 (2 x fp32 per amplitude) or complex128 */
+#define QAOA_C64 0
+#define QAOA_C128 1
+
+/* how the cost phase obtains C(x): choose automatically, recompute it from the
+ * weight matrix inside each tile, or stream a precomputed int32 diagonal */
+#define QAOA_COST_AUTO 0
+#define QAOA_COST_RECOMPUTE 1
+#define QAOA_COST_STREAM 2
+
+/* largest qubit counts accepted (state of 64 GiB each) */
+#define QAOA_MAX_QUBITS_C64 34
+#define QAOA_MAX_QUBITS_C128 33
+
+typedef struct qaoa_ctx qaoa_ctx;
+
+/* Bytes of one state vector: 2^n * 8 (C64) or 2^n * 16 (C128); 0 if invalid. */
+size_t qaoa_state_bytes(int n, int precision);
+
+/*
+ * Bytes of the optional auxiliary device buffer: the adjoint vector lambda
+ * (one state's worth, needed by qaoa_grad) followed by the int32 cost diagonal
+ * (2^n * 4 bytes, needed by QAOA_COST_STREAM). with_grad selects the first part,
+ * cost_mode the second.
+ */
+size_t qaoa_aux_bytes(int n, int precision, int cost_mode, int with_grad);
+
+/*
+ * Creates a context for one graph (Sec. II-B: weighted MaxCut instance).
+ *   n            qubits = vertices, 1 <= n <= QAOA_MAX_QUBITS_*.
+ *   n_edges      number of edges m >= 0; u[e] != v[e], both in [0, n), no
+ *                repeated pair, w[e] != 0, sum |w| < 2^31. Host arrays of
+ *                length m, copied; the caller keeps ownership.
+ *   weight_scale s > 0 in the phases exp(-i gamma s h(x)); <C>, C_min and C_max
+ *                are reported in integer weight units.
+ *   precision    QAOA_C64 or QAOA_C128.
+ *   cost_mode    QAOA_COST_*; AUTO picks recompute unless the autotuner cache
+ *                says streaming is faster for (n, precision).
+ *   state_dev    device buffer of exactly qaoa_state_bytes(n, precision)
+ *                bytes, 256-byte aligned, or NULL (the library allocates).
+ *   aux_dev      device buffer of aux_bytes >= qaoa_aux_bytes(...) or NULL
+ *                (the library allocates lazily when first needed).
+ *   cuda_stream  cudaStream_t to order all work on (NULL = legacy stream).
+ * Computes the exhaustive C_min / C_max (with smallest argmin / argmax) on the
+ * GPU before returning. Errors: EINVAL (bad graph or sizes), ENOMEM (buffer too
+ * small or allocation failure), ECUDA. On failure *ctx is NULL.
+ */
+int qaoa_init_graph(qaoa_ctx **ctx, int n, int n_edges, const int32_t *u, const int32_t *v,
+                    const int32_t *w, double weight_scale, int precision, int cost_mode,
+                    void *state_dev, size_t state_bytes, void *aux_dev, size_t aux_bytes,
+                    void *cuda_stream);
+
+/*
+ * Prepares |psi_p> with the linear-ramp schedule (Sec. II-B) and computes <C>
+ * and the norm on the GPU. p >= 0 (p = 0 leaves |+>^n). Asynchronous: results
+ * are read by qaoa_expect. Errors: EINVAL, ECUDA.
+ */
+int qaoa_run(qaoa_ctx *ctx, int p, double dgamma, double dbeta);
+
+/* As qaoa_run with explicit angles gamma[0..p-1], beta[0..p-1] (host arrays). */
+int qaoa_run_angles(qaoa_ctx *ctx, int p, const double *gamma, const double *beta);
+
+/*
+ * Results of the last run (any output pointer may be NULL): <C> and the norm
+ * (FP64 reductions), r = (<C> - C_min)/(C_max - C_min) (Eq. r with the exact
+ * mean; 1 when C_max == C_min), and the exhaustive extremes with their smallest
+ * indices. Synchronises the stream. Errors: ESTATE (no run yet), ECUDA.
+ */
+int qaoa_expect(qaoa_ctx *ctx, double *exp_c, double *r, double *norm, int64_t *c_min,
+                int64_t *c_max, uint64_t *argmin, uint64_t *argmax);
+
+/*
+ * Draws `shots` measurement samples from the last prepared state (Sec. II-B:
+ * repeated preparation and measurement). Shot i is the smallest index x with
+ * F(x) > u_i * total, where F is the cumulative |psi|^2 in index order and
+ * total = F(2^n - 1), both accumulated in FP64. u_i = uniforms[i] if uniforms
+ * is non-NULL (host array of `shots` values in [0, 1)), else u_i is draw i of
+ * SplitMix64 stream `seed`: (mix(seed + (i+1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53.
+ * out: host array of `shots` indices. Errors: EINVAL, ESTATE, ECUDA.
+ */
+int qaoa_sample(qaoa_ctx *ctx, int shots, const double *uniforms, uint64_t seed, uint64_t *out);
+
+/*
+ * Adjoint gradient of <C> for the linear-ramp schedule: runs the forward
+ * circuit, sets lambda = C psi_p and walks the layers backwards, uncomputing
+ * psi and lambda with the inverse gates while accumulating
+ *   g_beta[k]  = 2 Re <lambda| i H_B |psi>        (at layer k's mixer)
+ *   g_gamma[k] = 2 Re <lambda| -i s H_C |psi>     (at layer k's cost phase)
+ * and the chain rule d<C>/d dgamma = sum_k (k+1)/p g_gamma[k],
+ * d<C>/d dbeta = sum_k (1 - k/p) g_beta[k]. Holds two state vectors (psi in
+ * state_dev, lambda in the aux buffer). Any output may be NULL; g_gamma and
+ * g_beta hold p doubles. Leaves the context without a prepared state (the
+ * walk back ends near |+>), so call qaoa_run again before qaoa_sample.
+ * Errors: EINVAL (p < 1), ENOMEM, ECUDA.
+ */
+int qaoa_grad(qaoa_ctx *ctx, int p, double dgamma, double dbeta, double *g_gamma,
+              double *g_beta, double *d_dgamma, double *d_dbeta, double *exp_c);
+
+/* As qaoa_grad with explicit angles; returns the per-layer gradients only. */
+int qaoa_grad_angles(qaoa_ctx *ctx, int p, const double *gamma, const double *beta,
+                     double *g_gamma, double *g_beta, double *exp_c);
+
+/*
+ * Writes C(x) for all x (int32, 2^n entries) into the device buffer out_dev,
+ * using the same GPU evaluation as the cost phase. Errors: EINVAL, ECUDA.
+ */
+int qaoa_cost_diag(qaoa_ctx *ctx, int32_t *out_dev);
+
+/* Device pointer of the context's state vector (interleaved re, im). */
+void *qaoa_state_ptr(qaoa_ctx *ctx);
+
+/*
+ * Fills `out` (host, cap bytes) with a text description of the pass plan the
+ * context would use for depth p (one line per pass and round). Host-only; for
+ * inspection and tests. Returns the number of bytes needed (excluding NUL).
+ */
+int qaoa_describe_plan(int n, int precision, int p, int adjoint, char *out, int cap);
+
+/* Message of the last failure on ctx (or of the last failed qaoa_init_graph
+ * when ctx is NULL). Never NULL. */
+const char *qaoa_last_error(const qaoa_ctx *ctx);
+
+/* Releases the context and every buffer the library allocated for it. */
+void qaoa_free(qaoa_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QAOA_H */

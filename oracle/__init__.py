@@ -1,0 +1,251 @@
+"""Oracle for the LR-QAOA state-vector hot path: plain, slow, obviously correct.
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package. The product path
+never calls it and shares no code with it.
+
+The C part (``oracle.c``) applies gates one at a time in complex128; this file
+builds the per-gate angles from the paper's schedule and wraps the results.
+Every function names the passage of the paper it follows:
+
+* ``lr_schedule``      -- Sec. II-B, linear schedules for beta_i and gamma_i.
+* ``cut_values``       -- Sec. II-B, Eq. for C(x) (literal double sum).
+* ``extremes``         -- Sec. II-B, C(x*) = max cut; here by exhaustive search.
+* ``simulate``         -- Sec. II-B Eqs. H_C, UC, UB; gates as in Sec. II-E.
+* ``expectation``      -- <C> = sum |psi_x|^2 C(x); r as in Eq. r with the
+                          exact mean in place of the sample mean.
+* ``sample``           -- Sec. II-B, repeated preparation and measurement.
+* ``grad_fd``          -- central finite differences of <C> (h = 1e-5).
+* ``grad_param_shift`` -- exact two-term shift rule per gate (each gate is
+                          exp(-i theta/2 P) with a Pauli product P).
+* ``gate_counts``      -- Sec. II-B, N_2q = p N(N-1)/2 and N_1q = (p+1) N.
+
+Pins that tie this oracle to the paper and to mathematics (dense matrix
+exponentials, the uniform-state identity, the closed-form single-layer
+expectation, norm, conjugation symmetry, brute force on tiny graphs and the
+paper's printed gate counts) live in ``tests/test_oracle.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles ``oracle.c`` with gcc -O2 -fopenmp into ``liboracle.so``."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11",
+                               "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P = ctypes.POINTER
+        i32p, i64p, u64p, f64p = P(ctypes.c_int32), P(ctypes.c_int64), P(ctypes.c_uint64), P(ctypes.c_double)
+        lib.oracle_cut_values.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, i64p]
+        lib.oracle_extremes.argtypes = [ctypes.c_int, i64p, i64p, i64p, u64p, u64p]
+        lib.oracle_circuit.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, ctypes.c_int,
+                                       f64p, f64p, f64p, i64p]
+        lib.oracle_expectation.argtypes = [ctypes.c_int, f64p, i64p, f64p]
+        lib.oracle_expectation.restype = ctypes.c_double
+        lib.oracle_sample.argtypes = [ctypes.c_int, f64p, ctypes.c_int, f64p, u64p]
+        lib.oracle_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def lr_schedule(p: int, dgamma: float, dbeta: float):
+    """beta_i = (1 - i/p) dbeta and gamma_i = (i + 1)/p dgamma, i = 0..p-1 (Sec. II-B)."""
+    i = np.arange(p, dtype=np.float64)
+    beta = (1.0 - i / p) * dbeta
+    gamma = (i + 1.0) / p * dgamma
+    return gamma, beta
+
+
+def gate_counts(n: int, p: int):
+    """N_2q = p n(n-1)/2 and N_1q = (p + 1) n for a fully connected graph (Sec. II-B)."""
+    return p * n * (n - 1) // 2, (p + 1) * n
+
+
+def _edges(u, v, w):
+    u = np.ascontiguousarray(u, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    return u, v, w
+
+
+def cut_values(n: int, u, v, w) -> np.ndarray:
+    """C(x) = sum_{k<l} w_kl (x_k + x_l - 2 x_k x_l) for all 2^n bitstrings, int64."""
+    u, v, w = _edges(u, v, w)
+    out = np.empty(1 << n, dtype=np.int64)
+    rc = _load().oracle_cut_values(n, len(u), _ptr(u, ctypes.c_int32), _ptr(v, ctypes.c_int32),
+                                   _ptr(w, ctypes.c_int32), _ptr(out, ctypes.c_int64))
+    if rc:
+        raise ValueError("oracle_cut_values rejected its arguments")
+    return out
+
+
+def extremes(n: int, cut: np.ndarray):
+    """(C_min, C_max, argmin, argmax) by exhaustive search; ties -> smallest index."""
+    cmin, cmax = ctypes.c_int64(), ctypes.c_int64()
+    amin, amax = ctypes.c_uint64(), ctypes.c_uint64()
+    cut = np.ascontiguousarray(cut, dtype=np.int64)
+    _load().oracle_extremes(n, _ptr(cut, ctypes.c_int64), ctypes.byref(cmin), ctypes.byref(cmax),
+                            ctypes.byref(amin), ctypes.byref(amax))
+    return cmin.value, cmax.value, amin.value, amax.value
+
+
+def gate_angles(n: int, w, scale: float, gamma, beta):
+    """Per-gate angles: RZZ(2 gamma_k s w_e) per edge and RX(-2 beta_k) per qubit."""
+    w = np.asarray(w, dtype=np.float64)
+    gamma = np.asarray(gamma, dtype=np.float64)
+    beta = np.asarray(beta, dtype=np.float64)
+    zz = 2.0 * gamma[:, None] * scale * w[None, :]
+    xx = np.repeat((-2.0 * beta)[:, None], n, axis=1)
+    return np.ascontiguousarray(zz), np.ascontiguousarray(xx)
+
+
+def circuit(n: int, u, v, zz_theta, x_phi, return_count: bool = False):
+    """Applies the gate list with explicit per-gate angles; returns complex128 psi."""
+    u, v, _ = _edges(u, v, np.zeros(len(u)))
+    zz_theta = np.ascontiguousarray(zz_theta, dtype=np.float64)
+    x_phi = np.ascontiguousarray(x_phi, dtype=np.float64)
+    p = zz_theta.shape[0] if zz_theta.ndim == 2 else 0
+    if p == 0:
+        p = x_phi.shape[0] if x_phi.ndim == 2 else 0
+    psi = np.empty(1 << n, dtype=np.complex128)
+    cnt = ctypes.c_int64()
+    rc = _load().oracle_circuit(n, len(u), _ptr(u, ctypes.c_int32), _ptr(v, ctypes.c_int32), p,
+                                _ptr(zz_theta, ctypes.c_double), _ptr(x_phi, ctypes.c_double),
+                                psi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(cnt))
+    if rc:
+        raise ValueError("oracle_circuit rejected its arguments")
+    return (psi, cnt.value) if return_count else psi
+
+
+def simulate(n: int, u, v, w, scale: float, gamma, beta) -> np.ndarray:
+    """prod_k exp(+i beta_k H_B) exp(-i gamma_k s H_C) |+>^n, gate by gate, complex128."""
+    gamma = np.atleast_1d(np.asarray(gamma, dtype=np.float64))
+    beta = np.atleast_1d(np.asarray(beta, dtype=np.float64))
+    zz, xx = gate_angles(n, w, scale, gamma, beta)
+    return circuit(n, u, v, zz, xx)
+
+
+def expectation(psi: np.ndarray, cut: np.ndarray):
+    """(<C>, norm) with <C> = sum_x |psi_x|^2 C(x), accumulated in index order."""
+    n = int(round(math.log2(len(psi))))
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    cut = np.ascontiguousarray(cut, dtype=np.int64)
+    norm = ctypes.c_double()
+    e = _load().oracle_expectation(n, psi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   _ptr(cut, ctypes.c_int64), ctypes.byref(norm))
+    return float(e), norm.value
+
+
+def approximation_ratio(exp_c: float, cmin: int, cmax: int) -> float:
+    """r = (<C> - C_min) / (C_max - C_min); equals <C>/C(x*) when C_min = 0 (Eq. r)."""
+    return (exp_c - cmin) / (cmax - cmin) if cmax != cmin else 1.0
+
+
+def sample(psi: np.ndarray, uni) -> np.ndarray:
+    """Shot i = smallest x with F(x) > u_i * total, F the sequential CDF of |psi|^2."""
+    n = int(round(math.log2(len(psi))))
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    uni = np.ascontiguousarray(uni, dtype=np.float64)
+    out = np.empty(len(uni), dtype=np.uint64)
+    rc = _load().oracle_sample(n, psi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(uni),
+                               _ptr(uni, ctypes.c_double), _ptr(out, ctypes.c_uint64))
+    if rc:
+        raise MemoryError("oracle_sample could not allocate the CDF")
+    return out
+
+
+def run(n: int, u, v, w, scale: float, gamma, beta):
+    """Full forward result: dict with psi, <C>, norm, C_min, C_max, argmin, argmax, r."""
+    cut = cut_values(n, u, v, w)
+    psi = simulate(n, u, v, w, scale, gamma, beta)
+    e, nrm = expectation(psi, cut)
+    cmin, cmax, amin, amax = extremes(n, cut)
+    return dict(psi=psi, cut=cut, exp_c=e, norm=nrm, c_min=cmin, c_max=cmax, argmin=amin,
+                argmax=amax, r=approximation_ratio(e, cmin, cmax))
+
+
+def _expect_angles(n, u, v, cut, zz, xx):
+    return expectation(circuit(n, u, v, zz, xx), cut)[0]
+
+
+def grad_fd(n: int, u, v, w, scale: float, gamma, beta, h: float = 1e-5):
+    """Central differences of <C> in each gamma_k and beta_k (complex128)."""
+    gamma = np.asarray(gamma, dtype=np.float64)
+    beta = np.asarray(beta, dtype=np.float64)
+    cut = cut_values(n, u, v, w)
+
+    def f(g, b):
+        return expectation(simulate(n, u, v, w, scale, g, b), cut)[0]
+
+    gg = np.zeros(len(gamma))
+    gb = np.zeros(len(beta))
+    for k in range(len(gamma)):
+        e = np.zeros(len(gamma)); e[k] = h
+        gg[k] = (f(gamma + e, beta) - f(gamma - e, beta)) / (2 * h)
+        gb[k] = (f(gamma, beta + e) - f(gamma, beta - e)) / (2 * h)
+    return gg, gb
+
+
+def grad_param_shift(n: int, u, v, w, scale: float, gamma, beta):
+    """Exact gradient by shifting one gate angle at a time by +-pi/2.
+
+    Every gate is exp(-i theta/2 P) with P a Pauli product, so
+    d<C>/d theta = (f(theta + pi/2) - f(theta - pi/2)) / 2. RZZ on edge e in
+    layer k has theta = 2 gamma_k s w_e, so it contributes 2 s w_e times its
+    shift difference to d/d gamma_k; RX on qubit q in layer k has
+    phi = -2 beta_k and contributes -2 times its shift difference to d/d beta_k.
+    """
+    gamma = np.asarray(gamma, dtype=np.float64)
+    beta = np.asarray(beta, dtype=np.float64)
+    cut = cut_values(n, u, v, w)
+    zz, xx = gate_angles(n, w, scale, gamma, beta)
+    wf = np.asarray(w, dtype=np.float64)
+    gg = np.zeros(len(gamma))
+    gb = np.zeros(len(beta))
+    s2 = math.pi / 2
+    for k in range(len(gamma)):
+        for e in range(len(wf)):
+            zp = zz.copy(); zp[k, e] += s2
+            zm = zz.copy(); zm[k, e] -= s2
+            d = 0.5 * (_expect_angles(n, u, v, cut, zp, xx) - _expect_angles(n, u, v, cut, zm, xx))
+            gg[k] += 2.0 * scale * wf[e] * d
+        for q in range(n):
+            xp = xx.copy(); xp[k, q] += s2
+            xm = xx.copy(); xm[k, q] -= s2
+            d = 0.5 * (_expect_angles(n, u, v, cut, zz, xp) - _expect_angles(n, u, v, cut, zz, xm))
+            gb[k] += -2.0 * d
+    return gg, gb
+
+
+def lr_chain(g_gamma, g_beta):
+    """d<C>/d dgamma = sum_k (k+1)/p g_gamma[k]; d<C>/d dbeta = sum_k (1 - k/p) g_beta[k]."""
+    p = len(g_gamma)
+    k = np.arange(p, dtype=np.float64)
+    return float(np.sum((k + 1) / p * np.asarray(g_gamma))), float(np.sum((1 - k / p) * np.asarray(g_beta)))
