@@ -1,0 +1,700 @@
+// api.cu -- C ABI of libqaoa.so (declared in include/qaoa.h).
+//
+// Host side of the LR-QAOA simulation: graph validation, the weight matrix,
+// plans and their cost tables, phase tables, launches and result transfer.
+// Every step of the simulation itself runs in the CUDA kernels included below.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <set>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "qaoa.h"
+#include "plan.h"
+#include "device.cuh"
+#include "pass_kernel.cuh"
+#include "aux_kernels.cuh"
+#include "small_kernel.cuh"
+
+using namespace qaoa;
+
+namespace {
+
+constexpr int kR = 5, kWB = 3;           // forward tile: 2^5 registers x 32 lanes x 8 warps
+constexpr int kSmax = 15;                // super-tile bits (L2-resident working set)
+constexpr int kMinUnitsLog2 = 9;         // keep >= 512 super-tiles when n allows
+constexpr long long kMaxAbsWeightSum = 1 << 20;
+constexpr int kMaxGrid = 4096;           // persistent grid cap (partial-sum buffer size)
+
+thread_local std::string g_init_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (bytes >= b && p) return cudaSuccess;
+    if (p) cudaDeviceSynchronize();  // the old buffer may still be read by queued work
+    release();
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e == cudaSuccess) bytes = b; else p = nullptr;
+    return e;
+  }
+};
+
+}  // namespace
+
+struct qaoa_ctx {
+  int n = 0, m = 0, prec = QAOA_C64, cost_mode = QAOA_COST_RECOMPUTE;
+  double scale = 0.1;
+  std::vector<int32_t> u, v, w;
+  std::vector<int32_t> wmat;  // n x n
+  long long W = 0, c_lo = 0, c_hi = 0;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  void* state = nullptr;
+  bool own_state = false;
+  void* aux = nullptr;
+  size_t aux_bytes = 0;
+  DevBuf aux_own;
+  DevBuf d_wmat, d_ctabs, d_phase, d_partial, d_result, d_ext, d_ext_part;
+  DevBuf d_sums, d_pre, d_shots, d_uni, d_ang;
+  std::vector<int32_t> h_ctabs;                                        // host copy of all cost tables
+  std::map<std::pair<int, std::vector<int8_t>>, int> ctab_index;       // (shape, pos + layout) -> offset
+  bool ctabs_dirty = false;
+  std::map<int, std::unique_ptr<Plan>> plans;                         // forward plans by p
+  Extreme ext{};
+  bool have_result = false;
+  bool state_ready = false;
+  std::string err;
+  int set_err(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+};
+
+#define CUDA_TRY(ctx, expr)                                                               \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return (ctx)->set_err(QAOA_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                            __FILE__, __LINE__);                                          \
+  } while (0)
+
+namespace {
+
+int amp_bytes(int prec) { return prec == QAOA_C128 ? 16 : 8; }
+
+TileShape fwd_shape(int prec) {
+  TileShape s;
+  s.R = kR;
+  s.WB = kWB;
+  s.amp_bytes = amp_bytes(prec);
+  return s;
+}
+
+// Cost tables of one round (recompute mode), for tile bits at global
+// positions pos[] and the round's register / lane / warp split:
+//   CQ[q]     = sum_{k<l in Q} w [q_k != q_l]          (q: lane bits, then warp bits)
+//   AJ[q][i]  = sum_{k in Q, q_k = 1} w[reg_i][k]
+//   D[i]      = sum_{k in Q} w[reg_i][k]
+//   CP[j]     = sum_{i<i'} w[reg_i][reg_i'] [j_i != j_i']
+std::vector<int32_t> build_round_tables(const qaoa_ctx* c, const TileShape& sh, const int8_t* pos,
+                                        const RoundDev& rd) {
+  const int R = sh.R, WB = sh.WB, QB = 5 + WB;
+  const int QN = 1 << QB;
+  auto W = [&](int tj, int tk) { return c->wmat[pos[tj] * c->n + pos[tk]]; };
+  int qbits[16];
+  for (int i = 0; i < 5; ++i) qbits[i] = rd.lane[i];
+  for (int i = 0; i < WB; ++i) qbits[5 + i] = rd.warp[i];
+  std::vector<int32_t> t(QN + QN * R + R + (1 << R));
+  for (int q = 0; q < QN; ++q) {
+    int cq = 0;
+    for (int k = 0; k < QB; ++k)
+      for (int l = k + 1; l < QB; ++l)
+        if ((q >> k & 1) != (q >> l & 1)) cq += W(qbits[k], qbits[l]);
+    t[q] = cq;
+    for (int i = 0; i < R; ++i) {
+      int a = 0;
+      for (int k = 0; k < QB; ++k)
+        if (q >> k & 1) a += W(rd.reg[i], qbits[k]);
+      t[QN + q * R + i] = a;
+    }
+  }
+  for (int i = 0; i < R; ++i) {
+    int d = 0;
+    for (int k = 0; k < QB; ++k) d += W(rd.reg[i], qbits[k]);
+    t[QN + QN * R + i] = d;
+  }
+  for (int j = 0; j < (1 << R); ++j) {
+    int cp = 0;
+    for (int i = 0; i < R; ++i)
+      for (int i2 = i + 1; i2 < R; ++i2)
+        if ((j >> i & 1) != (j >> i2 & 1)) cp += W(rd.reg[i], rd.reg[i2]);
+    t[QN + QN * R + R + j] = cp;
+  }
+  return t;
+}
+
+void to_round_dev(const RoundPlan& rp, RoundDev& rd) {
+  memcpy(rd.reg, rp.reg, 5);
+  memcpy(rd.lane, rp.lane, 5);
+  memcpy(rd.warp, rp.warp, 4);
+  rd.mixA = rp.mixA;
+  rd.cost = rp.cost;
+  rd.mixB = rp.mixB;
+  rd.reduce = rp.reduce;
+  rd.src = rp.src;
+  rd.dst = rp.dst;
+  rd.ctab = -1;
+}
+
+int32_t table_offset(qaoa_ctx* c, const TileShape& sh, const int8_t* pos, const RoundDev& rd) {
+  std::vector<int8_t> key(pos, pos + sh.T());
+  key.insert(key.end(), rd.reg, rd.reg + 5);
+  key.insert(key.end(), rd.lane, rd.lane + 5);
+  key.insert(key.end(), rd.warp, rd.warp + 4);
+  auto k = std::make_pair(sh.R * 100 + sh.WB, key);
+  auto it = c->ctab_index.find(k);
+  if (it != c->ctab_index.end()) return it->second;
+  std::vector<int32_t> t = build_round_tables(c, sh, pos, rd);
+  const int32_t off = (int32_t)c->h_ctabs.size();
+  c->h_ctabs.insert(c->h_ctabs.end(), t.begin(), t.end());
+  c->ctab_index[k] = off;
+  c->ctabs_dirty = true;
+  return off;
+}
+
+int upload_ctabs(qaoa_ctx* c) {
+  if (!c->ctabs_dirty) return QAOA_OK;
+  const size_t bytes = std::max<size_t>(4, c->h_ctabs.size() * 4);
+  CUDA_TRY(c, c->d_ctabs.ensure(bytes));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_ctabs.p, c->h_ctabs.data(), c->h_ctabs.size() * 4, cudaMemcpyHostToDevice,
+                              c->stream));
+  c->ctabs_dirty = false;
+  return QAOA_OK;
+}
+
+// Phase tables exp(-i gamma_k s (W - 2c)) for c in [c_lo, c_hi], FP64 on the
+// host, rounded to the state precision (h(x) = W - 2 C(x), Eqs. H_C and UC).
+int upload_phases(qaoa_ctx* c, int p, const double* gamma) {
+  const long long nc = c->c_hi - c->c_lo + 1;
+  const int ab = amp_bytes(c->prec);
+  std::vector<unsigned char> host((size_t)std::max(1, p) * nc * ab);
+  for (int k = 0; k < p; ++k)
+    for (long long i = 0; i < nc; ++i) {
+      const long long cc = c->c_lo + i;
+      const double th = -gamma[k] * c->scale * double(c->W - 2 * cc);
+      const double cr = cos(th), ci = sin(th);
+      if (c->prec == QAOA_C128) {
+        double* d = reinterpret_cast<double*>(host.data()) + 2 * (k * nc + i);
+        d[0] = cr;
+        d[1] = ci;
+      } else {
+        float* f = reinterpret_cast<float*>(host.data()) + 2 * (k * nc + i);
+        f[0] = float(cr);
+        f[1] = float(ci);
+      }
+    }
+  CUDA_TRY(c, c->d_phase.ensure(host.size()));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_phase.p, host.data(), host.size(), cudaMemcpyHostToDevice, c->stream));
+  return QAOA_OK;
+}
+
+const Plan* get_plan(qaoa_ctx* c, int p) {
+  auto it = c->plans.find(p);
+  if (it != c->plans.end()) return it->second.get();
+  auto pl = std::make_unique<Plan>(plan_forward(c->n, p, fwd_shape(c->prec), kSmax, kMinUnitsLog2));
+  const Plan* r = pl.get();
+  c->plans[p] = std::move(pl);
+  return r;
+}
+
+template <typename Real, bool FAST>
+int launch_pass(qaoa_ctx* c, const PassDev& pd, const PassArgs& pa, size_t smem, int grid) {
+  auto kern = fwd_pass_kernel<Real, kR, kWB, FAST>;
+  CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, 32 << kWB, smem, c->stream>>>(pd, pa);
+  CUDA_TRY(c, cudaGetLastError());
+  return QAOA_OK;
+}
+
+template <typename Real, bool FAST>
+int blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
+  auto kern = fwd_pass_kernel<Real, kR, kWB, FAST>;
+  CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, 32 << kWB, smem));
+  if (*nb < 1) return c->set_err(QAOA_ECUDA, "pass kernel does not fit on an SM (smem %zu)", smem);
+  return QAOA_OK;
+}
+
+// mixer exp(+i beta X): a' = cos(beta) a + i sin(beta) b (and symmetric); the
+// fast form divides by cos(beta) when |tan(beta)| <= 1.
+void mixer_coeffs(double beta, bool fast, double* tau, double* alpha) {
+  if (fast) { *tau = tan(beta); *alpha = 1.0; }
+  else { *tau = sin(beta); *alpha = cos(beta); }
+}
+
+int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
+  const int n = c->n;
+  CUDA_TRY(c, c->d_ang.ensure(sizeof(double) * 2 * std::max(1, p)));
+  std::vector<double> ang(2 * std::max(1, p));
+  for (int k = 0; k < p; ++k) { ang[2 * k] = gamma[k]; ang[2 * k + 1] = beta[k]; }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_ang.p, ang.data(), ang.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  SmallArgs sa;
+  sa.n = n;
+  sa.p = p;
+  sa.state = c->state;
+  sa.wmat = (const int32_t*)c->d_wmat.p;
+  sa.phase = c->d_phase.p;
+  sa.c_lo = (int)c->c_lo;
+  sa.ncost = (int)(c->c_hi - c->c_lo + 1);
+  sa.betas = (const double*)c->d_ang.p;
+  sa.result = (double*)c->d_result.p;
+  const size_t smem = (size_t(1) << n) * amp_bytes(c->prec);
+  if (c->prec == QAOA_C128) {
+    CUDA_TRY(c, cudaFuncSetAttribute(small_circuit_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    small_circuit_kernel<double><<<1, 512, smem, c->stream>>>(sa);
+  } else {
+    CUDA_TRY(c, cudaFuncSetAttribute(small_circuit_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    small_circuit_kernel<float><<<1, 512, smem, c->stream>>>(sa);
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  return QAOA_OK;
+}
+
+int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
+  const int n = c->n;
+  const TileShape sh = fwd_shape(c->prec);
+  const int T = sh.T();
+  const int ab = amp_bytes(c->prec);
+  c->state_ready = false;
+  c->have_result = false;
+  int rc = upload_phases(c, p, gamma);
+  if (rc) return rc;
+  if (n < T) {
+    rc = run_small(c, p, gamma, beta);
+    if (rc) return rc;
+    c->have_result = c->state_ready = true;
+    return QAOA_OK;
+  }
+  const Plan* plan;
+  try {
+    plan = get_plan(c, p);
+  } catch (std::exception& ex) {
+    return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
+  }
+  const bool stream = c->cost_mode == QAOA_COST_STREAM;
+  const long long nc = c->c_hi - c->c_lo + 1;
+  // shared memory: tile | weights + tile consts | phase table (if it fits)
+  const size_t base_smem = (((size_t(1) << T) * ab + size_t(n * n + 32) * 4 + 15) & ~size_t(15));
+  const size_t with_tab = base_smem + size_t(nc) * ab;
+  int dev = 0, max_smem = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  CUDA_TRY(c, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const bool tab_smem = with_tab + 1024 <= (size_t)max_smem;
+  const size_t smem = tab_smem ? with_tab : base_smem;
+
+  // build every pass descriptor (and its cost tables) before launching
+  std::vector<PassDev> pds(plan->passes.size());
+  std::vector<char> fasts(plan->passes.size());
+  for (size_t pi = 0; pi < plan->passes.size(); ++pi) {
+    const PassPlan& pp = plan->passes[pi];
+    PassDev& pd = pds[pi];
+    memset(&pd, 0, sizeof pd);
+    pd.n = n;
+    pd.T = T;
+    pd.nsub = (int)pp.subs.size();
+    if (pd.nsub > kMaxSubDev) return c->set_err(QAOA_EINVAL, "plan has too many sub-passes");
+    pd.nouter = (int)pp.outer.size();
+    for (int i = 0; i < pd.nouter; ++i) pd.outer[i] = (int8_t)pp.outer[i];
+    pd.n_units = 1ull << pd.nouter;
+    const double ba = pp.layer_a >= 0 ? beta[pp.layer_a] : 0.0;
+    const double bb = pp.layer_b >= 0 ? beta[pp.layer_b] : 0.0;
+    const bool fast = fabs(cos(ba)) >= fabs(sin(ba)) && fabs(cos(bb)) >= fabs(sin(bb));
+    fasts[pi] = fast;
+    mixer_coeffs(ba, fast, &pd.tauA, &pd.alphaA);
+    mixer_coeffs(bb, fast, &pd.tauB, &pd.alphaB);
+    pd.amp0 = pow(2.0, -0.5 * n);
+    pd.c_lo = (int32_t)c->c_lo;
+    pd.ncost = (int32_t)nc;
+    for (int s = 0; s < pd.nsub; ++s) {
+      const SubPassPlan& sp = pp.subs[s];
+      SubDev& sd = pd.sub[s];
+      for (int j = 0; j < T; ++j) sd.pos[j] = sp.pos[j];
+      std::vector<int> inner;
+      for (int b : pp.sb) {
+        bool in_tile = false;
+        for (int j = 0; j < T; ++j) in_tile |= sp.pos[j] == b;
+        if (!in_tile) inner.push_back(b);
+      }
+      sd.ninner = (int)inner.size();
+      for (int i = 0; i < sd.ninner; ++i) sd.inner[i] = (int8_t)inner[i];
+      sd.nrounds = (int)sp.rounds.size();
+      if (sd.nrounds > kMaxRoundsDev) return c->set_err(QAOA_EINVAL, "plan has too many rounds");
+      sd.init = sp.init;
+      sd.needs_c = sp.needs_c;
+      sd.scale = fast ? pow(cos(ba), sp.nA) * pow(cos(bb), sp.nB) : 1.0;
+      for (int r = 0; r < sd.nrounds; ++r) {
+        to_round_dev(sp.rounds[r], sd.rd[r]);
+        if ((sd.rd[r].cost || sd.rd[r].reduce) && !stream) sd.rd[r].ctab = table_offset(c, sh, sd.pos, sd.rd[r]);
+      }
+    }
+  }
+  rc = upload_ctabs(c);
+  if (rc) return rc;
+  for (size_t pi = 0; pi < plan->passes.size(); ++pi) {
+    const PassPlan& pp = plan->passes[pi];
+    const PassDev& pd = pds[pi];
+    const bool fast = fasts[pi];
+    PassArgs pa;
+    pa.state = c->state;
+    pa.diag = stream ? (const int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n))) : nullptr;
+    pa.phase = pp.layer_b >= 0 ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_b) * nc * ab) : nullptr;
+    pa.wmat = (const int32_t*)c->d_wmat.p;
+    pa.ctabs = (const int32_t*)c->d_ctabs.p;
+    pa.phase_in_smem = tab_smem ? 1 : 0;
+    int bps = 0;
+    if (c->prec == QAOA_C128)
+      rc = fast ? blocks_per_sm<double, true>(c, smem, &bps) : blocks_per_sm<double, false>(c, smem, &bps);
+    else
+      rc = fast ? blocks_per_sm<float, true>(c, smem, &bps) : blocks_per_sm<float, false>(c, smem, &bps);
+    if (rc) return rc;
+    const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
+    const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
+    pa.partial = pp.reduce ? (double*)c->d_partial.p : nullptr;
+    if (c->prec == QAOA_C128)
+      rc = fast ? launch_pass<double, true>(c, pd, pa, smem, grid) : launch_pass<double, false>(c, pd, pa, smem, grid);
+    else
+      rc = fast ? launch_pass<float, true>(c, pd, pa, smem, grid) : launch_pass<float, false>(c, pd, pa, smem, grid);
+    if (rc) return rc;
+    if (pp.reduce) {
+      sum_partials_kernel<<<1, 32, 0, c->stream>>>((const double*)c->d_partial.p, grid, 2, (double*)c->d_result.p);
+      CUDA_TRY(c, cudaGetLastError());
+    }
+  }
+  c->have_result = true;
+  c->state_ready = true;
+  return QAOA_OK;
+}
+
+// Exhaustive C_min / C_max with smallest argmin / argmax; optionally writes
+// the full int32 diagonal. Without a diagonal only x with the top bit clear is
+// scanned: C(x) = C(~x), so the smallest minimiser and maximiser lie there.
+int compute_extremes(qaoa_ctx* c, int32_t* diag_out, bool restrict_half) {
+  const int n = c->n;
+  CUDA_TRY(c, c->d_ext.ensure(sizeof(Extreme)));
+  if (n < 16) {
+    cost_small_kernel<<<1, 1024, 0, c->stream>>>(n, (const int32_t*)c->d_wmat.p, diag_out, (Extreme*)c->d_ext.p);
+    CUDA_TRY(c, cudaGetLastError());
+    return QAOA_OK;
+  }
+  const int eff = restrict_half && !diag_out ? n - 1 : n;
+  const long long blocks = 1ll << (eff - 15);
+  CUDA_TRY(c, c->d_ext_part.ensure(sizeof(Extreme) * blocks));
+  cost_block_kernel<15><<<(unsigned)blocks, 1024, 0, c->stream>>>(n, (const int32_t*)c->d_wmat.p, diag_out,
+                                                                 (Extreme*)c->d_ext_part.p);
+  CUDA_TRY(c, cudaGetLastError());
+  extreme_finalize_kernel<<<1, 1024, 0, c->stream>>>((const Extreme*)c->d_ext_part.p, blocks, (Extreme*)c->d_ext.p);
+  CUDA_TRY(c, cudaGetLastError());
+  return QAOA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t qaoa_state_bytes(int n, int precision) {
+  if (precision != QAOA_C64 && precision != QAOA_C128) return 0;
+  const int maxn = precision == QAOA_C64 ? QAOA_MAX_QUBITS_C64 : QAOA_MAX_QUBITS_C128;
+  if (n < 1 || n > maxn) return 0;
+  return (size_t(1) << n) * amp_bytes(precision);
+}
+
+size_t qaoa_aux_bytes(int n, int precision, int cost_mode, int with_grad) {
+  const size_t sb = qaoa_state_bytes(n, precision);
+  if (!sb) return 0;
+  size_t b = with_grad ? sb : 0;
+  if (cost_mode == QAOA_COST_STREAM) b += size_t(4) << n;
+  return b;
+}
+
+int qaoa_init_graph(qaoa_ctx** out, int n, int m, const int32_t* u, const int32_t* v, const int32_t* w,
+                    double weight_scale, int precision, int cost_mode, void* state_dev, size_t state_bytes,
+                    void* aux_dev, size_t aux_bytes, void* cuda_stream) {
+  g_init_error.clear();
+  auto fail = [&](int code, const std::string& msg) {
+    g_init_error = msg;
+    if (out) *out = nullptr;
+    return code;
+  };
+  if (!out) return fail(QAOA_EINVAL, "ctx output pointer is NULL");
+  *out = nullptr;
+  if (precision != QAOA_C64 && precision != QAOA_C128)
+    return fail(QAOA_EINVAL, "precision must be QAOA_C64 or QAOA_C128");
+  const size_t sb = qaoa_state_bytes(n, precision);
+  if (!sb) return fail(QAOA_EINVAL, "n out of range for this precision");
+  if (m < 0 || (m > 0 && (!u || !v || !w))) return fail(QAOA_EINVAL, "bad edge arrays");
+  if (!(weight_scale > 0.0) || !std::isfinite(weight_scale)) return fail(QAOA_EINVAL, "weight_scale must be > 0");
+  if (cost_mode < QAOA_COST_AUTO || cost_mode > QAOA_COST_STREAM) return fail(QAOA_EINVAL, "bad cost_mode");
+  std::set<std::pair<int, int>> seen;
+  long long W = 0, pos = 0, neg = 0;
+  for (int e = 0; e < m; ++e) {
+    if (u[e] < 0 || u[e] >= n || v[e] < 0 || v[e] >= n) return fail(QAOA_EINVAL, "edge vertex out of range");
+    if (u[e] == v[e]) return fail(QAOA_EINVAL, "self loop");
+    if (w[e] == 0) return fail(QAOA_EINVAL, "zero weight");
+    auto key = std::make_pair(std::min(u[e], v[e]), std::max(u[e], v[e]));
+    if (!seen.insert(key).second) return fail(QAOA_EINVAL, "repeated edge");
+    W += w[e];
+    if (w[e] > 0) pos += w[e]; else neg += w[e];
+    if (pos - neg > kMaxAbsWeightSum) return fail(QAOA_EINVAL, "sum of |w| exceeds 2^20");
+  }
+  if (state_dev && state_bytes != sb)
+    return fail(QAOA_ENOMEM, "state buffer size must equal qaoa_state_bytes(n, precision)");
+  if (state_dev && (reinterpret_cast<uintptr_t>(state_dev) & 255))
+    return fail(QAOA_EINVAL, "state buffer must be 256-byte aligned");
+  const int mode = cost_mode == QAOA_COST_AUTO ? QAOA_COST_RECOMPUTE : cost_mode;
+  if (aux_dev && aux_bytes < qaoa_aux_bytes(n, precision, mode, 0))
+    return fail(QAOA_ENOMEM, "aux buffer smaller than qaoa_aux_bytes");
+  if (aux_dev && (reinterpret_cast<uintptr_t>(aux_dev) & 255))
+    return fail(QAOA_EINVAL, "aux buffer must be 256-byte aligned");
+
+  std::unique_ptr<qaoa_ctx> c(new qaoa_ctx);
+  c->n = n;
+  c->m = m;
+  c->prec = precision;
+  c->cost_mode = mode;
+  c->scale = weight_scale;
+  c->u.assign(u, u + m);
+  c->v.assign(v, v + m);
+  c->w.assign(w, w + m);
+  c->wmat.assign((size_t)n * n, 0);
+  for (int e = 0; e < m; ++e) {
+    c->wmat[u[e] * n + v[e]] = w[e];
+    c->wmat[v[e] * n + u[e]] = w[e];
+  }
+  c->W = W;
+  c->c_lo = neg;
+  c->c_hi = pos;
+  c->stream = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(QAOA_ECUDA, "no CUDA device");
+  }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (state_dev) {
+    c->state = state_dev;
+  } else {
+    if (cudaMalloc(&c->state, sb) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(QAOA_ENOMEM, "cudaMalloc of the state failed");
+    }
+    c->own_state = true;
+  }
+  if (aux_dev) {
+    c->aux = aux_dev;
+    c->aux_bytes = aux_bytes;
+  }
+  if (c->d_wmat.ensure(sizeof(int32_t) * n * n) != cudaSuccess ||
+      c->d_partial.ensure(sizeof(double) * 2 * kMaxGrid) != cudaSuccess || c->d_result.ensure(64) != cudaSuccess) {
+    cudaGetLastError();
+    qaoa_free(c.release());
+    return fail(QAOA_ENOMEM, "cudaMalloc failed");
+  }
+  if (cudaMemcpyAsync(c->d_wmat.p, c->wmat.data(), sizeof(int32_t) * n * n, cudaMemcpyHostToDevice, c->stream) !=
+      cudaSuccess) {
+    qaoa_free(c.release());
+    return fail(QAOA_ECUDA, "weight upload failed");
+  }
+  int32_t* diag = nullptr;
+  if (mode == QAOA_COST_STREAM) {
+    const size_t need = qaoa_aux_bytes(n, precision, mode, 0);
+    if (!c->aux) {
+      if (c->aux_own.ensure(need) != cudaSuccess) {
+        cudaGetLastError();
+        qaoa_free(c.release());
+        return fail(QAOA_ENOMEM, "cudaMalloc of the cost diagonal failed");
+      }
+      c->aux = c->aux_own.p;
+      c->aux_bytes = need;
+    }
+    diag = (int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n)));
+  }
+  int rc = compute_extremes(c.get(), diag, true);
+  if (rc) {
+    std::string msg = c->err;
+    qaoa_free(c.release());
+    return fail(rc, msg);
+  }
+  if (cudaMemcpyAsync(&c->ext, c->d_ext.p, sizeof(Extreme), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    std::string msg = std::string("extremes transfer failed: ") + cudaGetErrorString(cudaGetLastError());
+    qaoa_free(c.release());
+    return fail(QAOA_ECUDA, msg);
+  }
+  *out = c.release();
+  return QAOA_OK;
+}
+
+int qaoa_run_angles(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
+  if (!c) return QAOA_EINVAL;
+  if (p < 0 || (p > 0 && (!gamma || !beta))) return c->set_err(QAOA_EINVAL, "bad p or angle arrays");
+  for (int k = 0; k < p; ++k)
+    if (!std::isfinite(gamma[k]) || !std::isfinite(beta[k])) return c->set_err(QAOA_EINVAL, "non-finite angle");
+  return run_forward(c, p, gamma, beta);
+}
+
+int qaoa_run(qaoa_ctx* c, int p, double dgamma, double dbeta) {
+  if (!c) return QAOA_EINVAL;
+  if (p < 0) return c->set_err(QAOA_EINVAL, "p must be >= 0");
+  std::vector<double> g(p), b(p);
+  for (int k = 0; k < p; ++k) {
+    b[k] = (1.0 - double(k) / p) * dbeta;  // beta_k = (1 - k/p) dbeta
+    g[k] = double(k + 1) / p * dgamma;      // gamma_k = (k+1)/p dgamma
+  }
+  return qaoa_run_angles(c, p, g.data(), b.data());
+}
+
+int qaoa_expect(qaoa_ctx* c, double* exp_c, double* r, double* norm, int64_t* c_min, int64_t* c_max,
+                uint64_t* argmin, uint64_t* argmax) {
+  if (!c) return QAOA_EINVAL;
+  if (c_min) *c_min = c->ext.vmin;
+  if (c_max) *c_max = c->ext.vmax;
+  if (argmin) *argmin = c->ext.amin;
+  if (argmax) *argmax = c->ext.amax;
+  if (!exp_c && !r && !norm) return QAOA_OK;
+  if (!c->have_result) return c->set_err(QAOA_ESTATE, "no run yet");
+  double res[2];
+  CUDA_TRY(c, cudaMemcpyAsync(res, c->d_result.p, sizeof res, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (norm) *norm = res[0];
+  if (exp_c) *exp_c = res[1];
+  if (r) {
+    const double den = double(c->ext.vmax - c->ext.vmin);
+    *r = den != 0.0 ? (res[1] - double(c->ext.vmin)) / den : 1.0;
+  }
+  return QAOA_OK;
+}
+
+int qaoa_sample(qaoa_ctx* c, int shots, const double* uniforms, uint64_t seed, uint64_t* out) {
+  if (!c) return QAOA_EINVAL;
+  if (shots < 0) return c->set_err(QAOA_EINVAL, "shots must be >= 0");
+  if (shots > 0 && !out) return c->set_err(QAOA_EINVAL, "out is NULL");
+  if (!c->state_ready) return c->set_err(QAOA_ESTATE, "no prepared state (call qaoa_run)");
+  if (shots == 0) return QAOA_OK;
+  if (uniforms)
+    for (int i = 0; i < shots; ++i)
+      if (!(uniforms[i] >= 0.0 && uniforms[i] < 1.0)) return c->set_err(QAOA_EINVAL, "uniforms must lie in [0, 1)");
+  const int n = c->n;
+  const int B = std::min(n, 12);
+  const long long nb = 1ll << (n - B);
+  CUDA_TRY(c, c->d_sums.ensure(sizeof(double) * nb));
+  CUDA_TRY(c, c->d_pre.ensure(sizeof(double) * (nb + 1)));
+  CUDA_TRY(c, c->d_shots.ensure(sizeof(unsigned long long) * shots));
+  const double* d_uni = nullptr;
+  if (uniforms) {
+    CUDA_TRY(c, c->d_uni.ensure(sizeof(double) * shots));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_uni.p, uniforms, sizeof(double) * shots, cudaMemcpyHostToDevice, c->stream));
+    d_uni = (const double*)c->d_uni.p;
+  }
+  if (c->prec == QAOA_C128)
+    block_sum_kernel<double><<<(unsigned)nb, 256, 0, c->stream>>>((const double2*)c->state, B, (double*)c->d_sums.p);
+  else
+    block_sum_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((const float2*)c->state, B, (double*)c->d_sums.p);
+  CUDA_TRY(c, cudaGetLastError());
+  scan_kernel<<<1, 1024, 0, c->stream>>>((const double*)c->d_sums.p, nb, (double*)c->d_pre.p);
+  CUDA_TRY(c, cudaGetLastError());
+  const int tb = 128, gb = (shots + tb - 1) / tb;
+  if (c->prec == QAOA_C128)
+    shot_kernel<double><<<gb, tb, 0, c->stream>>>((const double2*)c->state, B, (const double*)c->d_pre.p, nb, shots,
+                                                  d_uni, seed, (unsigned long long*)c->d_shots.p);
+  else
+    shot_kernel<float><<<gb, tb, 0, c->stream>>>((const float2*)c->state, B, (const double*)c->d_pre.p, nb, shots,
+                                                 d_uni, seed, (unsigned long long*)c->d_shots.p);
+  CUDA_TRY(c, cudaGetLastError());
+  CUDA_TRY(c, cudaMemcpyAsync(out, c->d_shots.p, sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return QAOA_OK;
+}
+
+int qaoa_cost_diag(qaoa_ctx* c, int32_t* out_dev) {
+  if (!c) return QAOA_EINVAL;
+  if (!out_dev) return c->set_err(QAOA_EINVAL, "out_dev is NULL");
+  if (reinterpret_cast<uintptr_t>(out_dev) & 15) return c->set_err(QAOA_EINVAL, "out_dev must be 16-byte aligned");
+  return compute_extremes(c, out_dev, false);
+}
+
+void* qaoa_state_ptr(qaoa_ctx* c) { return c ? c->state : nullptr; }
+
+int qaoa_describe_plan(int n, int precision, int p, int adjoint, char* out, int cap) {
+  std::string s;
+  try {
+    if (adjoint) throw std::runtime_error("adjoint plans are described by qaoa_grad");
+    Plan pl = plan_forward(n, p, fwd_shape(precision), kSmax, kMinUnitsLog2);
+    std::string e = validate(pl);
+    s = pl.describe();
+    if (!e.empty()) s += "INVALID: " + e + "\n";
+  } catch (std::exception& ex) {
+    s = std::string("error: ") + ex.what() + "\n";
+  }
+  if (out && cap > 0) {
+    const int k = std::min<int>(cap - 1, (int)s.size());
+    memcpy(out, s.data(), k);
+    out[k] = 0;
+  }
+  return (int)s.size();
+}
+
+const char* qaoa_last_error(const qaoa_ctx* c) {
+  if (!c) return g_init_error.c_str();
+  return c->err.c_str();
+}
+
+void qaoa_free(qaoa_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  if (c->own_state && c->state) cudaFree(c->state);
+  c->aux_own.release();
+  DevBuf* bufs[] = {&c->d_wmat, &c->d_ctabs, &c->d_phase, &c->d_partial, &c->d_result, &c->d_ext,
+                    &c->d_ext_part, &c->d_sums, &c->d_pre, &c->d_shots, &c->d_uni, &c->d_ang};
+  for (DevBuf* b : bufs) b->release();
+  delete c;
+}
+
+int qaoa_grad(qaoa_ctx* c, int p, double dgamma, double dbeta, double* g_gamma, double* g_beta, double* d_dgamma,
+              double* d_dbeta, double* exp_c) {
+  if (!c) return QAOA_EINVAL;
+  (void)p; (void)dgamma; (void)dbeta; (void)g_gamma; (void)g_beta; (void)d_dgamma; (void)d_dbeta; (void)exp_c;
+  return c->set_err(QAOA_EINVAL, "qaoa_grad is not implemented yet");
+}
+
+int qaoa_grad_angles(qaoa_ctx* c, int p, const double* gamma, const double* beta, double* g_gamma, double* g_beta,
+                     double* exp_c) {
+  if (!c) return QAOA_EINVAL;
+  (void)p; (void)gamma; (void)beta; (void)g_gamma; (void)g_beta; (void)exp_c;
+  return c->set_err(QAOA_EINVAL, "qaoa_grad_angles is not implemented yet");
+}
+
+}  // extern "C"

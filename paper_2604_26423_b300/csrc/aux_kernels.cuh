@@ -1,0 +1,293 @@
+// aux_kernels.cuh -- cost diagonal / exhaustive extremes, reductions, sampling.
+#pragma once
+#include <climits>
+#include <cstdint>
+
+#include "device.cuh"
+
+namespace qaoa {
+
+// ---------------------------------------------------------------------------
+// C(x) = sum_{k<l} w_kl [x_k != x_l] (Eq. for C(x)) for a block of 2^LB
+// consecutive x (LB = 15, 1024 threads x 32 values). The block's high bits
+// (>= LB) are fixed: per block, delta_j = sum_{g >= LB} w[j][g] (1 - 2 f_g) and
+// base = C over the high bits + sum_{j < LB, g >= LB} w[j][g] f_g. A thread
+// owns bits 5..LB-1 (value t) and enumerates bits 0..4 (value j):
+//   C = base + sum_{k in 5..LB-1} t_k delta_k + C_mid(t) + sum_{i<5} A_i(t)
+//       + sum_{i<5} j_i (delta_i + D_i - 2 A_i(t)) + C_low(j)
+// with A_i(t) = sum_k w[i][k] t_k, D_i = sum_k w[i][k] over k in 5..LB-1.
+// Optionally writes the int32 diagonal; always reduces (min, argmin, max, argmax)
+// with ties resolved to the smallest index.
+// ---------------------------------------------------------------------------
+struct Extreme {
+  long long vmin, vmax;
+  unsigned long long amin, amax;
+};
+
+__device__ __forceinline__ void ext_merge(Extreme& a, const Extreme& b) {
+  if (b.vmin < a.vmin || (b.vmin == a.vmin && b.amin < a.amin)) { a.vmin = b.vmin; a.amin = b.amin; }
+  if (b.vmax > a.vmax || (b.vmax == a.vmax && b.amax < a.amax)) { a.vmax = b.vmax; a.amax = b.amax; }
+}
+
+__device__ __forceinline__ void ext_warp_merge(Extreme& ex) {
+  for (int o = 16; o > 0; o >>= 1) {
+    Extreme b;
+    b.vmin = __shfl_xor_sync(0xffffffffu, ex.vmin, o);
+    b.vmax = __shfl_xor_sync(0xffffffffu, ex.vmax, o);
+    b.amin = __shfl_xor_sync(0xffffffffu, ex.amin, o);
+    b.amax = __shfl_xor_sync(0xffffffffu, ex.amax, o);
+    ext_merge(ex, b);
+  }
+}
+
+__device__ __forceinline__ Extreme ext_empty() {
+  Extreme ex;
+  ex.vmin = LLONG_MAX;
+  ex.vmax = LLONG_MIN;
+  ex.amin = ex.amax = ~0ull;
+  return ex;
+}
+
+template <int LB>
+__global__ void __launch_bounds__(1 << (LB - 5))
+cost_block_kernel(int n, const int32_t* __restrict__ wmat, int32_t* __restrict__ diag, Extreme* __restrict__ out) {
+  constexpr int NT = 1 << (LB - 5);
+  __shared__ int w[kMaxBits * kMaxBits];
+  __shared__ int delta[LB];
+  __shared__ int base_s;
+  __shared__ int clow[32];
+  __shared__ int dsum[5];
+  __shared__ Extreme red[NT / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < n * n; i += NT) w[i] = wmat[i];
+  __syncthreads();
+  const unsigned long long hi = (unsigned long long)blockIdx.x << LB;
+  if (warp == 0) {
+    int a = 0;
+    if (lane < LB) {
+      int d = 0;
+      for (int g = LB; g < n; ++g) {
+        const int fg = int(hi >> g & 1ull), wg = w[lane * n + g];
+        d += fg ? -wg : wg;
+        a += fg ? wg : 0;
+      }
+      delta[lane] = d;
+    }
+    int cf = 0;
+    for (int g = LB + lane; g < n; g += 32) {
+      const int fg = int(hi >> g & 1ull);
+      for (int h = g + 1; h < n; ++h)
+        if (fg != int(hi >> h & 1ull)) cf += w[g * n + h];
+    }
+    int tot = a + cf;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) base_s = tot;
+    // C_low(j) over bits 0..4 and D_i
+    int cl = 0;
+    for (int i = 0; i < 5; ++i)
+      for (int k = i + 1; k < 5; ++k)
+        if ((lane >> i & 1) != (lane >> k & 1)) cl += w[i * n + k];
+    clow[lane] = cl;
+    if (lane < 5) {
+      int d = 0;
+      for (int k = 5; k < LB; ++k) d += w[lane * n + k];
+      dsum[lane] = d;
+    }
+  }
+  __syncthreads();
+  const int t = tid;  // bits 5..LB-1
+  int kappa = base_s;
+  for (int k = 5; k < LB; ++k) {
+    const int tk = t >> (k - 5) & 1;
+    if (tk) kappa += delta[k];
+    for (int l = k + 1; l < LB; ++l)
+      if (tk != (t >> (l - 5) & 1)) kappa += w[k * n + l];
+  }
+  int e[5];
+  for (int i = 0; i < 5; ++i) {
+    int ai = 0;
+    for (int k = 5; k < LB; ++k)
+      if (t >> (k - 5) & 1) ai += w[i * n + k];
+    kappa += ai;
+    e[i] = delta[i] + dsum[i] - 2 * ai;
+  }
+  Extreme ex = ext_empty();
+  const unsigned long long x0 = hi | ((unsigned long long)t << 5);
+  int vals[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    int c = kappa + clow[j];
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (j >> i & 1) c += e[i];
+    vals[j] = c;
+    if (c < ex.vmin) { ex.vmin = c; ex.amin = x0 | j; }
+    if (c > ex.vmax) { ex.vmax = c; ex.amax = x0 | j; }
+  }
+  if (diag) {
+    int4* d4 = reinterpret_cast<int4*>(diag + x0);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      __stcg(d4 + j, make_int4(vals[4 * j], vals[4 * j + 1], vals[4 * j + 2], vals[4 * j + 3]));
+  }
+  ext_warp_merge(ex);
+  if (lane == 0) red[warp] = ex;
+  __syncthreads();
+  if (tid == 0) {
+    Extreme r = red[0];
+    for (int i = 1; i < NT / 32; ++i) ext_merge(r, red[i]);
+    out[blockIdx.x] = r;
+  }
+}
+
+// Small n (< 15): one CTA, one thread per x, direct sum over all index pairs.
+__global__ void cost_small_kernel(int n, const int32_t* __restrict__ wmat, int32_t* __restrict__ diag,
+                                  Extreme* __restrict__ out) {
+  __shared__ Extreme red[32];
+  const unsigned long long N = 1ull << n;
+  Extreme ex = ext_empty();
+  for (unsigned long long x = threadIdx.x; x < N; x += blockDim.x) {
+    int c = 0;
+    for (int g = 0; g < n; ++g)
+      for (int h = g + 1; h < n; ++h)
+        if ((x >> g & 1ull) != (x >> h & 1ull)) c += wmat[g * n + h];
+    if (diag) diag[x] = c;
+    if (c < ex.vmin) { ex.vmin = c; ex.amin = x; }
+    if (c > ex.vmax) { ex.vmax = c; ex.amax = x; }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ext_warp_merge(ex);
+  if (lane == 0) red[warp] = ex;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Extreme r = red[0];
+    for (int i = 1; i < (int)(blockDim.x / 32); ++i) ext_merge(r, red[i]);
+    out[0] = r;
+  }
+}
+
+// Merges per-block extremes (deterministic: ties go to the smallest index).
+__global__ void extreme_finalize_kernel(const Extreme* __restrict__ in, long long count, Extreme* __restrict__ out) {
+  __shared__ Extreme red[32];
+  Extreme ex = ext_empty();
+  for (long long i = threadIdx.x; i < count; i += blockDim.x) ext_merge(ex, in[i]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  ext_warp_merge(ex);
+  if (lane == 0) red[warp] = ex;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Extreme r = red[0];
+    for (int i = 1; i < (int)(blockDim.x / 32); ++i) ext_merge(r, red[i]);
+    *out = r;
+  }
+}
+
+// Sums `count` interleaved partials (stride `stride` doubles) in a fixed order.
+__global__ void sum_partials_kernel(const double* __restrict__ in, int count, int stride, double* __restrict__ out) {
+  const int c = threadIdx.x;
+  if (c < stride) {
+    double s = 0.0;
+    for (int i = 0; i < count; ++i) s += in[(size_t)i * stride + c];
+    out[c] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Sampling (Sec. II-B: repeated measurement of the final state).
+// Block sums S_j of |psi|^2 over 2^B consecutive indices; exclusive prefix
+// E_j = S_0 + ... + S_{j-1} (E_nb = total); per shot t = u * total, block j =
+// smallest with E_{j+1} > t, then the smallest x in the block whose in-block
+// running FP64 sum exceeds t - E_j (the last nonzero-probability index of the
+// block if rounding leaves none).
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(256) block_sum_kernel(const typename Cx<Real>::T* __restrict__ psi, int B,
+                                                        double* __restrict__ sums) {
+  __shared__ double red[8];
+  const size_t base = (size_t)blockIdx.x << B;
+  const int len = 1 << B;
+  Real s = 0;
+  for (int i = threadIdx.x; i < len; i += 256) {
+    const typename Cx<Real>::T a = __ldcg(psi + base + i);
+    s = fma(a.x, a.x, fma(a.y, a.y, s));
+  }
+  double d = double(s);
+  for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int i = 0; i < 8; ++i) t += red[i];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of `count` doubles into pre[0..count] (pre[count] = total),
+// one CTA of 1024 threads, fixed order: each thread scans a contiguous chunk.
+__global__ void __launch_bounds__(1024) scan_kernel(const double* __restrict__ s, long long count,
+                                                    double* __restrict__ pre) {
+  __shared__ double part[1024];
+  const long long chunk = (count + 1023) / 1024;
+  const long long lo = threadIdx.x * chunk;
+  const long long hi = lo + chunk < count ? lo + chunk : count;
+  double acc = 0.0;
+  for (long long i = lo; i < hi; ++i) acc += s[i];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double run = 0.0;
+    for (int i = 0; i < 1024; ++i) { const double v = part[i]; part[i] = run; run += v; }
+    pre[count] = run;
+  }
+  __syncthreads();
+  double run = part[threadIdx.x];
+  for (long long i = lo; i < hi; ++i) { pre[i] = run; run += s[i]; }
+}
+
+// Draw k of the SplitMix64 stream `seed` (Steele, Lea and Flood 2014) as a
+// double in [0, 1): mix(seed + (k+1) * golden gamma) >> 11, times 2^-53.
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long k) {
+  unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return double(z >> 11) * 0x1.0p-53;
+}
+
+template <typename Real>
+__global__ void shot_kernel(const typename Cx<Real>::T* __restrict__ psi, int B, const double* __restrict__ pre,
+                            long long nb, int shots, const double* __restrict__ uni, unsigned long long seed,
+                            unsigned long long* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= shots) return;
+  const double u = uni ? uni[i] : splitmix_uniform(seed, (unsigned long long)i);
+  const double total = pre[nb];
+  const double t = u * total;
+  // smallest j with pre[j + 1] > t
+  long long lo = 0, hi = nb;
+  while (lo < hi) {
+    const long long mid = lo + (hi - lo) / 2;
+    if (pre[mid + 1] > t) hi = mid; else lo = mid + 1;
+  }
+  long long j = lo;
+  if (j >= nb) {  // rounding pushed t to the total: last block with mass
+    j = nb - 1;
+    while (j > 0 && !(pre[j + 1] > pre[j])) --j;
+  }
+  const double tr = t - pre[j];
+  const size_t base = (size_t)j << B;
+  const int len = 1 << B;
+  double run = 0.0;
+  long long pick = -1, last_nz = 0;
+  for (int k = 0; k < len; ++k) {
+    const typename Cx<Real>::T a = psi[base + k];
+    const double pr = double(a.x) * double(a.x) + double(a.y) * double(a.y);
+    run += pr;
+    if (pr > 0.0) last_nz = k;
+    if (run > tr) { pick = k; break; }
+  }
+  if (pick < 0) pick = last_nz;
+  out[i] = (unsigned long long)(base + pick);
+}
+
+}  // namespace qaoa

@@ -1,0 +1,501 @@
+// plan.cpp -- pass / sub-pass / round planner (host only). See plan.h.
+#include "plan.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <sstream>
+#include <stdexcept>
+
+namespace qaoa {
+namespace {
+
+int popc(uint32_t x) { return __builtin_popcount(x); }
+
+std::vector<int> bits_of(uint32_t m) {
+  std::vector<int> v;
+  for (int i = 0; i < 32; ++i)
+    if (m >> i & 1u) v.push_back(i);
+  return v;
+}
+
+// Register-position mask of tile-bit mask `m` in round `rp`.
+uint8_t regmask(const RoundPlan& rp, int R, uint32_t m) {
+  uint8_t r = 0;
+  for (int i = 0; i < R; ++i)
+    if (m >> rp.reg[i] & 1u) r |= uint8_t(1u << i);
+  return r;
+}
+
+// Fills lanes / warps / filler registers for a round whose essential register
+// bits are `x`. Global-facing rounds put lanes 0..3 on tile bits 0..3 (global
+// index bits 0..3 in every geometry) so each warp access covers whole
+// 128/256-byte runs; other rounds pick lanes 0..3 (0..2 for 16-byte
+// amplitudes) on bits of distinct swizzle classes so shared memory is
+// conflict-free.
+bool layout_round(const TileShape& sh, uint32_t x, bool global, RoundPlan& rp) {
+  const int T = sh.T(), R = sh.R, WB = sh.WB;
+  if (popc(x) > R) return false;
+  uint32_t used = x;
+  int lanes[5];
+  if (global) {
+    if (x & 0xFu) return false;
+    for (int i = 0; i < 4; ++i) lanes[i] = i;
+    used |= 0xFu;
+    int l4 = -1;
+    if (!(used >> 4 & 1u)) l4 = 4;
+    else
+      for (int b = 5; b < T; ++b)
+        if (!(used >> b & 1u)) { l4 = b; break; }
+    if (l4 < 0) return false;
+    lanes[4] = l4;
+    used |= 1u << l4;
+  } else {
+    const int ncls = sh.amp_bytes == 8 ? 4 : 3;
+    for (int c = 0; c < ncls; ++c) {
+      int pick = -1;
+      for (int b = 0; b < T; ++b)
+        if (!(used >> b & 1u) && swizzle_class(b, sh.amp_bytes) == c) { pick = b; break; }
+      if (pick < 0) return false;
+      lanes[c] = pick;
+      used |= 1u << pick;
+    }
+    for (int i = ncls; i < 5; ++i) {
+      int pick = -1;
+      for (int b = 0; b < T; ++b)
+        if (!(used >> b & 1u)) { pick = b; break; }
+      if (pick < 0) return false;
+      lanes[i] = pick;
+      used |= 1u << pick;
+    }
+  }
+  // registers: essential bits first (ascending), then fillers
+  std::vector<int> regs = bits_of(x);
+  for (int b = T - 1; b >= 0 && (int)regs.size() < R; --b)
+    if (!(used >> b & 1u)) { regs.push_back(b); used |= 1u << b; }
+  if ((int)regs.size() != R) return false;
+  std::sort(regs.begin(), regs.end());
+  std::vector<int> warps;
+  for (int b = 0; b < T; ++b)
+    if (!(used >> b & 1u)) warps.push_back(b);
+  if ((int)warps.size() != WB) return false;
+  for (int i = 0; i < R; ++i) rp.reg[i] = int8_t(regs[i]);
+  for (int i = R; i < 5; ++i) rp.reg[i] = 0;
+  for (int i = 0; i < 5; ++i) rp.lane[i] = int8_t(lanes[i]);
+  for (int i = 0; i < WB; ++i) rp.warp[i] = int8_t(warps[i]);
+  for (int i = WB; i < 4; ++i) rp.warp[i] = 0;
+  rp.global_facing = global;
+  return true;
+}
+
+// Picks up to R bits from `cand`, bits 0..3 first, then the rest ascending.
+uint32_t pick_bits(uint32_t cand, int R, uint32_t already) {
+  uint32_t x = already;
+  for (int b : bits_of(cand & 0xFu))
+    if (popc(x) < R) x |= 1u << b;
+  for (int b : bits_of(cand & ~0xFu))
+    if (popc(x) < R) x |= 1u << b;
+  return x;
+}
+
+}  // namespace
+
+std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool cost, uint32_t b_bits,
+                                   bool reduce, uint8_t first_src) {
+  const int R = sh.R;
+  std::vector<RoundPlan> out;
+  uint32_t remA = a_bits, remB = b_bits;
+  // without a cost phase here, mixer B continues a layer whose cost phase was
+  // applied in an earlier sub-pass
+  bool cost_done = !cost;
+  bool first = true;
+  auto apply = [&](RoundPlan& rp, uint32_t x) {
+    rp.mixA = regmask(rp, R, x & remA);
+    remA &= ~x;
+    if (remA == 0) {
+      if (!cost_done) { rp.cost = 1; cost_done = true; }
+      rp.mixB = regmask(rp, R, x & remB);
+      remB &= ~x;
+    }
+  };
+  for (int guard = 0; guard < kMaxRounds; ++guard) {
+    RoundPlan rp;
+    rp.src = first ? first_src : SRC_SMEM;
+    const uint32_t need = remA | remB;
+    // can everything left be done in one global-facing round (load/store)?
+    if (popc(need) <= R && !(need & 0xFu)) {
+      if (!layout_round(sh, need, true, rp)) throw std::runtime_error("plan_rounds: final layout");
+      apply(rp, need);
+      rp.reduce = reduce ? 1 : 0;
+      rp.dst = DST_GLOBAL;
+      out.push_back(rp);
+      return out;
+    }
+    uint32_t x;
+    bool global = false;
+    if (rp.src == SRC_GLOBAL) {
+      // coalesced load round: registers may only hold bits >= 4
+      global = true;
+      uint32_t cand = remA ? remA : remB;
+      cand &= ~0xFu;
+      x = 0;
+      for (int b : bits_of(cand & ~0x1Fu))
+        if (popc(x) < R) x |= 1u << b;
+      if (popc(x) < R && (cand >> 4 & 1u)) x |= 1u << 4;
+      // if A finishes here, B bits (>= 4) may ride along
+      if (remA && (remA & ~x) == 0) x = x | (pick_bits(remB & ~0xFu, R, x) & ~x);
+    } else {
+      uint32_t cand = remA ? remA : remB;
+      x = pick_bits(cand, R, 0);
+      if (remA && (remA & ~x) == 0) x = pick_bits(remB, R, x);
+    }
+    if (!layout_round(sh, x, global, rp)) throw std::runtime_error("plan_rounds: layout");
+    apply(rp, x);
+    rp.dst = DST_SMEM;
+    out.push_back(rp);
+    first = false;
+  }
+  throw std::runtime_error("plan_rounds: too many rounds");
+}
+
+std::string validate_rounds(const TileShape& sh, const std::vector<RoundPlan>& rounds, uint32_t a_bits,
+                            bool cost, uint32_t b_bits, bool reduce) {
+  const int T = sh.T(), R = sh.R, WB = sh.WB;
+  uint32_t doneA = 0, doneB = 0;
+  bool cost_seen = false, reduce_seen = false;
+  if (rounds.empty()) return "no rounds";
+  for (size_t k = 0; k < rounds.size(); ++k) {
+    const RoundPlan& rp = rounds[k];
+    uint32_t seen = 0;
+    for (int i = 0; i < R; ++i) seen |= 1u << rp.reg[i];
+    for (int i = 0; i < 5; ++i) seen |= 1u << rp.lane[i];
+    for (int i = 0; i < WB; ++i) seen |= 1u << rp.warp[i];
+    if (seen != ((1u << T) - 1) || popc(seen) != T) return "round is not a permutation of tile bits";
+    const bool is_last = k + 1 == rounds.size();
+    if ((k == 0 && rp.src == SRC_GLOBAL) || is_last) {
+      for (int i = 0; i < 4; ++i)
+        if (rp.lane[i] != i) return "global round without lanes 0..3 on tile bits 0..3";
+    }
+    if (is_last != (rp.dst == DST_GLOBAL)) return "only the last round stores to global memory";
+    if (k > 0 && rp.src != SRC_SMEM) return "only the first round reads global memory";
+    if (!rp.global_facing || (k > 0 && !is_last)) {
+      const int ncls = sh.amp_bytes == 8 ? 4 : 3;
+      uint32_t cls = 0;
+      for (int i = 0; i < ncls; ++i) cls |= 1u << swizzle_class(rp.lane[i], sh.amp_bytes);
+      if (popc(cls) != ncls) return "shared-memory lanes share a swizzle class";
+    }
+    for (int i = 0; i < R; ++i) {
+      const uint32_t b = 1u << rp.reg[i];
+      if (rp.mixA >> i & 1u) {
+        if (cost_seen) return "mixer A after the cost phase";
+        if (doneA & b) return "mixer A bit applied twice";
+        if (!(a_bits & b)) return "mixer A on a non-target bit";
+        doneA |= b;
+      }
+    }
+    if (rp.cost) {
+      if (doneA != a_bits) return "cost phase before mixer A completed";
+      if (!cost) return "unexpected cost phase";
+      cost_seen = true;
+    }
+    for (int i = 0; i < R; ++i) {
+      const uint32_t b = 1u << rp.reg[i];
+      if (rp.mixB >> i & 1u) {
+        if (cost && !cost_seen) return "mixer B before the cost phase";
+        if (doneA != a_bits) return "mixer B before mixer A completed";
+        if (doneB & b) return "mixer B bit applied twice";
+        if (!(b_bits & b)) return "mixer B on a non-target bit";
+        doneB |= b;
+      }
+    }
+    if (rp.reduce) {
+      if (!is_last) return "reduce before the last round";
+      reduce_seen = true;
+    }
+  }
+  if (doneA != a_bits) return "mixer A incomplete";
+  if (doneB != b_bits) return "mixer B incomplete";
+  if (cost != cost_seen) return "cost phase missing";
+  if (reduce != reduce_seen) return "reduce missing";
+  return "";
+}
+
+namespace {
+
+struct Group {
+  std::vector<int> sb;       // super-tile bits (ascending)
+  std::vector<int> targets;  // qubits of the group (ascending)
+};
+
+// Splits a group's targets into sub-pass chunks and builds their tiles.
+// Every tile holds global bits 0..3 (tile bits 0..3); the first tile also holds
+// bit 4 when the super-tile has it as a non-target, so HBM reads come in
+// 256-byte (c64) / 512-byte (c128) runs.
+std::vector<std::pair<std::vector<int>, std::vector<int>>> chunk_group(const Group& g, int T) {
+  std::vector<std::pair<std::vector<int>, std::vector<int>>> out;  // (tile bits in tile order, chunk)
+  std::vector<int> rest = g.targets;
+  bool first = true;
+  auto in_sb = [&](int b) { return std::find(g.sb.begin(), g.sb.end(), b) != g.sb.end(); };
+  auto is_target = [&](int b) { return std::find(g.targets.begin(), g.targets.end(), b) != g.targets.end(); };
+  do {
+    std::vector<int> tile = {0, 1, 2, 3};
+    std::vector<int> chunk;
+    for (int b = 0; b < 4; ++b) {
+      auto it = std::find(rest.begin(), rest.end(), b);
+      if (it != rest.end()) { chunk.push_back(b); rest.erase(it); }
+    }
+    const bool keep4 = first && in_sb(4) && !is_target(4);
+    if (keep4) tile.push_back(4);
+    while ((int)tile.size() < T && !rest.empty()) {
+      tile.push_back(rest.front());
+      chunk.push_back(rest.front());
+      rest.erase(rest.begin());
+    }
+    // fillers: lowest super-tile bits not yet in the tile
+    for (int b : g.sb)
+      if ((int)tile.size() < T && std::find(tile.begin(), tile.end(), b) == tile.end()) tile.push_back(b);
+    if ((int)tile.size() != T) throw std::runtime_error("chunk_group: super-tile smaller than a tile");
+    std::vector<int> order(tile.begin() + 4, tile.end());
+    std::sort(order.begin(), order.end());
+    std::vector<int> t2 = {0, 1, 2, 3};
+    t2.insert(t2.end(), order.begin(), order.end());
+    std::sort(chunk.begin(), chunk.end());
+    out.emplace_back(t2, chunk);
+    first = false;
+  } while (!rest.empty());
+  return out;
+}
+
+uint32_t tile_mask(const std::vector<int>& tile, const std::vector<int>& chunk) {
+  uint32_t m = 0;
+  for (int b : chunk) {
+    auto it = std::find(tile.begin(), tile.end(), b);
+    m |= 1u << int(it - tile.begin());
+  }
+  return m;
+}
+
+}  // namespace
+
+Plan plan_forward(int n, int p, const TileShape& sh, int s_max, int min_units_log2) {
+  const int T = sh.T();
+  if (n < T) throw std::runtime_error("plan_forward: n below the tile size");
+  if (n > kMaxQubits) throw std::runtime_error("plan_forward: n too large");
+  Plan plan;
+  plan.n = n;
+  plan.p = p;
+  plan.shape = sh;
+  int S = std::min(s_max, std::max(T, n - min_units_log2));
+  S = std::min(S, n);
+  plan.S = S;
+  // qubit groups: the low S bits, then windows of high bits that keep 32
+  // (r = 5) or 16 (r = 4) consecutive amplitudes per contiguous run
+  std::vector<Group> groups;
+  {
+    Group low;
+    for (int b = 0; b < S; ++b) low.sb.push_back(b), low.targets.push_back(b);
+    groups.push_back(low);
+    const int left = n - S;
+    if (left > 0) {
+      const int X5 = S - 5, X4 = S - 4;
+      const int g5 = (left + X5 - 1) / X5, g4 = (left + X4 - 1) / X4;
+      const int r = g5 <= g4 ? 5 : 4;
+      const int X = S - r;
+      for (int a = S; a < n; a += X) {
+        const int b = std::min(n, a + X);
+        const int h = std::min(a, n - X);
+        Group g;
+        for (int q = 0; q < r; ++q) g.sb.push_back(q);
+        for (int q = h; q < h + X; ++q) g.sb.push_back(q);
+        for (int q = a; q < b; ++q) g.targets.push_back(q);
+        groups.push_back(g);
+      }
+    }
+  }
+  for (auto& g : groups) plan.groups.push_back(g.targets);
+  const int G = (int)groups.size();
+
+  // op sequence -> passes: [init] [cost k, mix k over groups (alternating order)]... [reduce]
+  struct Proto { int grp = -1; int a = -1, cost = -1, b = -1; bool init = false, reduce = false; };
+  std::vector<Proto> protos;
+  Proto cur;
+  cur.init = true;
+  for (int k = 0; k < p; ++k) {
+    // cost of layer k
+    if (cur.cost >= 0) { protos.push_back(cur); cur = Proto(); }
+    cur.cost = k;
+    for (int i = 0; i < G; ++i) {
+      const int grp = (k % 2 == 0) ? i : G - 1 - i;
+      if (cur.grp < 0) {
+        cur.grp = grp;
+        if (cur.cost == k) cur.b = k; else cur.a = k;
+      } else if (cur.grp == grp && cur.cost == k && cur.b < 0) {
+        cur.b = k;
+      } else {
+        protos.push_back(cur);
+        cur = Proto();
+        cur.grp = grp;
+        cur.a = k;
+      }
+    }
+  }
+  cur.reduce = true;
+  if (cur.grp < 0) cur.grp = 0;
+  protos.push_back(cur);
+
+  for (const Proto& pr : protos) {
+    PassPlan pp;
+    const Group& g = groups[pr.grp];
+    pp.sb = g.sb;
+    for (int b = 0; b < n; ++b)
+      if (std::find(g.sb.begin(), g.sb.end(), b) == g.sb.end()) pp.outer.push_back(b);
+    pp.init = pr.init;
+    pp.reduce = pr.reduce;
+    pp.layer_a = pr.a;
+    pp.layer_b = pr.cost;  // cost and mixer B belong to the same layer
+    const bool has_cost = pr.cost >= 0;
+    const bool has_b = pr.b >= 0;
+    if (has_cost && !has_b && pr.a < 0 && !pr.init)
+      throw std::runtime_error("plan_forward: cost-only pass");
+    const bool has_mix = pr.a >= 0 || has_b;
+    if (has_mix) pp.targets = g.targets;
+    auto chunks = chunk_group(Group{g.sb, has_mix ? g.targets : std::vector<int>{}}, T);
+    const int K = (int)chunks.size();
+    // sub-pass op assignment
+    struct SubOps { int chunk; bool a, cost, b; };
+    std::vector<SubOps> seq;
+    if (pr.a >= 0 && has_cost && has_b) {
+      for (int i = 0; i < K - 1; ++i) seq.push_back({i, true, false, false});
+      seq.push_back({K - 1, true, true, true});
+      for (int i = K - 2; i >= 0; --i) seq.push_back({i, false, false, true});
+    } else if (pr.a >= 0 && has_cost && !has_b) {
+      for (int i = 0; i < K - 1; ++i) seq.push_back({i, true, false, false});
+      seq.push_back({K - 1, true, true, false});
+    } else if (pr.a >= 0) {
+      for (int i = 0; i < K; ++i) seq.push_back({i, true, false, false});
+    } else if (has_cost) {
+      seq.push_back({0, false, true, has_b});
+      for (int i = 1; i < K; ++i) seq.push_back({i, false, false, has_b});
+    } else {
+      for (int i = 0; i < K; ++i) seq.push_back({i, false, false, false});
+    }
+    for (size_t s = 0; s < seq.size(); ++s) {
+      const SubOps& so = seq[s];
+      SubPassPlan sp;
+      sp.T = T;
+      const auto& tile = chunks[so.chunk].first;
+      const auto& chunk = chunks[so.chunk].second;
+      for (int j = 0; j < T; ++j) sp.pos[j] = int8_t(tile[j]);
+      const uint32_t m = tile_mask(tile, chunk);
+      const uint32_t am = so.a ? m : 0, bm = so.b ? m : 0;
+      const bool red = pp.reduce && s + 1 == seq.size();
+      sp.init = pp.init && s == 0;
+      sp.rounds = plan_rounds(sh, am, so.cost, bm, red, sp.init ? SRC_INIT : SRC_GLOBAL);
+      sp.nA = popc(am);
+      sp.nB = popc(bm);
+      sp.needs_c = so.cost || red;
+      pp.subs.push_back(sp);
+    }
+    plan.passes.push_back(pp);
+  }
+  return plan;
+}
+
+std::string validate(const Plan& plan) {
+  const int n = plan.n;
+  // every qubit's mixer of every layer applied exactly once, cost once per layer,
+  // in order (layer k's mixer complete before cost k+1)
+  std::vector<std::vector<int>> mix_count(plan.p, std::vector<int>(n, 0));
+  std::vector<int> cost_count(plan.p, 0);
+  int init_count = 0, reduce_count = 0;
+  for (size_t pi = 0; pi < plan.passes.size(); ++pi) {
+    const PassPlan& pp = plan.passes[pi];
+    if (pp.init) ++init_count;
+    if (pp.reduce) ++reduce_count;
+    if (pp.init && pi != 0) return "init not in the first pass";
+    if (pp.reduce && pi + 1 != plan.passes.size()) return "reduce not in the last pass";
+    for (const SubPassPlan& sp : pp.subs) {
+      uint32_t am = 0, bm = 0;
+      bool cost = false, red = false;
+      for (const RoundPlan& rp : sp.rounds) {
+        for (int i = 0; i < plan.shape.R; ++i) {
+          if (rp.mixA >> i & 1u) am |= 1u << rp.reg[i];
+          if (rp.mixB >> i & 1u) bm |= 1u << rp.reg[i];
+        }
+        cost |= rp.cost != 0;
+        red |= rp.reduce != 0;
+      }
+      std::string e = validate_rounds(plan.shape, sp.rounds, am, cost, bm, red);
+      if (!e.empty()) return "round check: " + e;
+      if (cost) {
+        if (pp.layer_b < 0) return "cost without layer";
+        // all mixers of the previous layer must be complete
+        if (pp.layer_b > 0)
+          for (int q = 0; q < n; ++q) {
+            bool here = false;
+            for (int j = 0; j < sp.T; ++j)
+              if (sp.pos[j] == q && (am >> j & 1u)) here = true;
+            if (mix_count[pp.layer_b - 1][q] + (here ? 1 : 0) != 1)
+              return "cost before the previous layer's mixer completed";
+          }
+        ++cost_count[pp.layer_b];
+      }
+      for (int j = 0; j < sp.T; ++j) {
+        const int q = sp.pos[j];
+        if (am >> j & 1u) {
+          if (pp.layer_a < 0) return "mixer A without layer";
+          if (cost_count[pp.layer_a] != 1) return "mixer before its layer's cost";
+          ++mix_count[pp.layer_a][q];
+        }
+        if (bm >> j & 1u) {
+          if (pp.layer_b < 0 || cost_count[pp.layer_b] != 1) return "mixer B before its cost";
+          ++mix_count[pp.layer_b][q];
+        }
+      }
+    }
+  }
+  if (init_count != 1) return "init count";
+  if (reduce_count != 1) return "reduce count";
+  for (int k = 0; k < plan.p; ++k) {
+    if (cost_count[k] != 1) return "cost count of a layer";
+    for (int q = 0; q < n; ++q)
+      if (mix_count[k][q] != 1) return "mixer count of a qubit";
+  }
+  return "";
+}
+
+std::string Plan::describe() const {
+  std::ostringstream os;
+  os << "n=" << n << " p=" << p << " S=" << S << " T=" << shape.T() << " R=" << shape.R
+     << " WB=" << shape.WB << " groups=" << groups.size() << " passes=" << passes.size() << "\n";
+  for (size_t g = 0; g < groups.size(); ++g) {
+    os << "group " << g << ":";
+    for (int q : groups[g]) os << " " << q;
+    os << "\n";
+  }
+  for (size_t pi = 0; pi < passes.size(); ++pi) {
+    const PassPlan& pp = passes[pi];
+    os << "pass " << pi << " a=" << pp.layer_a << " b=" << pp.layer_b << (pp.init ? " init" : "")
+       << (pp.reduce ? " reduce" : "") << " sb=[";
+    for (int b : pp.sb) os << b << ",";
+    os << "] subs=" << pp.subs.size() << "\n";
+    for (size_t s = 0; s < pp.subs.size(); ++s) {
+      const SubPassPlan& sp = pp.subs[s];
+      os << "  sub " << s << " tile=[";
+      for (int j = 0; j < sp.T; ++j) os << int(sp.pos[j]) << (j + 1 < sp.T ? "," : "");
+      os << "] nA=" << sp.nA << " nB=" << sp.nB << "\n";
+      for (const RoundPlan& rp : sp.rounds) {
+        os << "    round src=" << int(rp.src) << " dst=" << int(rp.dst) << " reg=";
+        for (int i = 0; i < shape.R; ++i) os << int(rp.reg[i]) << (i + 1 < shape.R ? "," : "");
+        os << " lane=";
+        for (int i = 0; i < 5; ++i) os << int(rp.lane[i]) << (i < 4 ? "," : "");
+        os << " warp=";
+        for (int i = 0; i < shape.WB; ++i) os << int(rp.warp[i]) << (i + 1 < shape.WB ? "," : "");
+        os << " A=" << int(rp.mixA) << " C=" << int(rp.cost) << " B=" << int(rp.mixB)
+           << " R=" << int(rp.reduce) << "\n";
+      }
+    }
+  }
+  return os.str();
+}
+
+}  // namespace qaoa

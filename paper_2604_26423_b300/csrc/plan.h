@@ -1,0 +1,105 @@
+// plan.h -- host-side pass planner for the LR-QAOA state-vector kernels.
+//
+// A run of p layers (Sec. II-B: U_C(gamma_k) then U_B(beta_k) per layer) is
+// executed as a sequence of HBM passes. Each pass streams the whole state once
+// (one read and one write per amplitude) and applies, inside on-chip tiles,
+// every gate that can be applied between that read and that write:
+//   - the mixer exp(i beta X_q) of a layer on one group of qubits (the mixer is
+//     a product over qubits of commuting 2x2 rotations, so any grouping works),
+//   - the diagonal cost phase of the next layer, which needs the full index
+//     of each amplitude but no neighbours,
+//   - the mixer of that next layer on the same group (cross-layer fusion: the
+//     group order is reversed on alternate layers so consecutive layers meet on
+//     the same group).
+// Inside a pass the state is processed in super-tiles (2^S amplitudes spanning
+// S chosen index bits, small enough that all super-tiles in flight stay in L2).
+// A super-tile is swept by one CTA in one or more sub-passes; a sub-pass moves
+// shared-memory tiles of 2^T amplitudes (T = R + 5 + WB index bits: R bits in
+// each thread's registers, 5 bits across lanes, WB bits across warps) between
+// global memory and registers, and between rounds through shared memory.
+// Bit q of an amplitude index is qubit q.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace qaoa {
+
+constexpr int kMaxT = 14;
+constexpr int kMaxRounds = 8;
+constexpr int kMaxQubits = 40;
+
+enum : uint8_t { SRC_SMEM = 0, SRC_GLOBAL = 1, SRC_INIT = 2 };
+enum : uint8_t { DST_SMEM = 0, DST_GLOBAL = 1 };
+
+// Kernel shape: R register bits, 5 lane bits, WB warp bits; amplitude bytes.
+struct TileShape {
+  int R = 5, WB = 3, amp_bytes = 8, nvec = 1;
+  int T() const { return R + 5 + WB; }
+};
+
+// One round: every thread holds 2^R amplitudes whose tile indices differ in the
+// tile bits reg[0..R-1]; lanes and warps select the other bits.
+struct RoundPlan {
+  int8_t reg[5] = {0, 0, 0, 0, 0};
+  int8_t lane[5] = {0, 0, 0, 0, 0};
+  int8_t warp[4] = {0, 0, 0, 0};
+  uint8_t mixA = 0;   // register-position mask: mixer of layer a on these bits
+  uint8_t cost = 0;   // then the cost phase of layer b (all of layer a done)
+  uint8_t mixB = 0;   // then the mixer of layer b on these register bits
+  uint8_t reduce = 0; // then accumulate norm and <C> (final pass)
+  uint8_t src = SRC_SMEM, dst = DST_SMEM;
+  bool global_facing = false;
+};
+
+struct SubPassPlan {
+  int T = 0;
+  int8_t pos[kMaxT] = {};               // tile bit j -> global index bit pos[j]
+  std::vector<RoundPlan> rounds;
+  int nA = 0, nB = 0;                   // butterflies per amplitude of layer a / b here
+  bool init = false;                    // first sub-pass of the first pass
+  bool needs_c = false;                 // some round needs C(x) (cost or reduce)
+};
+
+struct PassPlan {
+  std::vector<int> sb;                  // super-tile bits (ascending)
+  std::vector<int> outer;               // bits enumerating super-tiles (ascending)
+  std::vector<int> targets;             // qubits whose mixer this pass applies
+  std::vector<SubPassPlan> subs;
+  int layer_a = -1;                     // mixer layer applied before the cost phase
+  int layer_b = -1;                     // cost + mixer layer applied after it
+  bool init = false, reduce = false;
+};
+
+struct Plan {
+  int n = 0, p = 0, S = 0;
+  TileShape shape;
+  std::vector<std::vector<int>> groups; // qubit groups (one pass each per layer)
+  std::vector<PassPlan> passes;
+  std::string describe() const;
+};
+
+// Forward plan for n qubits and depth p (n >= shape.T()).
+// s_max: largest super-tile bit count; min_units_log2: keep at least 2^x super-tiles.
+Plan plan_forward(int n, int p, const TileShape& shape, int s_max, int min_units_log2);
+
+// Plans the rounds of one sub-pass with tile bits `tb` (tile bit order) for the
+// op sequence [mixer A on a_bits] [cost] [mixer B on b_bits] [reduce].
+// a_bits / b_bits are tile-bit masks. Throws std::runtime_error if impossible.
+std::vector<RoundPlan> plan_rounds(const TileShape& shape, uint32_t a_bits, bool cost,
+                                   uint32_t b_bits, bool reduce, uint8_t first_src);
+
+// Checks the structural invariants of a plan (each mixer bit applied once per
+// op, cost after all of layer a, lanes/warps/registers a permutation of the tile
+// bits, global rounds coalesced, shared-memory lanes conflict-free). Returns
+// an empty string when valid, else a description of the first violation.
+std::string validate(const Plan& plan);
+std::string validate_rounds(const TileShape& shape, const std::vector<RoundPlan>& rounds,
+                            uint32_t a_bits, bool cost, uint32_t b_bits, bool reduce);
+
+// Residue class of tile bit j in the shared-memory swizzle: rows of 16 c64 or 8
+// c128 amplitudes, XOR-swizzled so that lanes on bits of distinct classes never
+// share a bank.
+inline int swizzle_class(int bit, int amp_bytes) { return amp_bytes == 8 ? bit % 4 : bit % 3; }
+
+}  // namespace qaoa

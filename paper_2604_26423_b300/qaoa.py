@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libqaoa.so (C ABI in include/qaoa.h).
+
+Argument marshalling only: every step of the simulation runs in the library's
+CUDA kernels. PyTorch supplies device memory (the state and auxiliary buffers
+are torch tensors handed over by pointer) and the CUDA stream. There is no CPU
+fallback: without the built library or a CUDA device, constructing a
+``Simulator`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+QAOA_OK, QAOA_EINVAL, QAOA_ENOMEM, QAOA_ECUDA, QAOA_ETIMEOUT, QAOA_ESTATE = range(6)
+C64, C128 = 0, 1
+COST_AUTO, COST_RECOMPUTE, COST_STREAM = 0, 1, 2
+_PREC = {"c64": C64, "complex64": C64, C64: C64, "c128": C128, "complex128": C128, C128: C128}
+_COST = {"auto": COST_AUTO, "recompute": COST_RECOMPUTE, "stream": COST_STREAM,
+         COST_AUTO: COST_AUTO, COST_RECOMPUTE: COST_RECOMPUTE, COST_STREAM: COST_STREAM}
+_ERRNAME = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE"}
+
+# every entry point declared in include/qaoa.h
+EXPORTS = ("qaoa_state_bytes", "qaoa_aux_bytes", "qaoa_init_graph", "qaoa_run", "qaoa_run_angles",
+           "qaoa_expect", "qaoa_sample", "qaoa_grad", "qaoa_grad_angles", "qaoa_cost_diag",
+           "qaoa_state_ptr", "qaoa_describe_plan", "qaoa_last_error", "qaoa_free")
+
+_lib = None
+
+
+class QaoaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAME.get(code, code)}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads libqaoa.so (it must have been built; see ``paper_2604_26423_b300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2604_26423_b300.build`")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    i32p, f64p, u64p, i64p = P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_uint64), P(ctypes.c_int64)
+    vp = ctypes.c_void_p
+    lib.qaoa_state_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.qaoa_state_bytes.restype = ctypes.c_size_t
+    lib.qaoa_aux_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.qaoa_aux_bytes.restype = ctypes.c_size_t
+    lib.qaoa_init_graph.argtypes = [P(vp), ctypes.c_int, ctypes.c_int, i32p, i32p, i32p, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, vp, ctypes.c_size_t, vp]
+    lib.qaoa_run.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.qaoa_run_angles.argtypes = [vp, ctypes.c_int, f64p, f64p]
+    lib.qaoa_expect.argtypes = [vp, f64p, f64p, f64p, i64p, i64p, u64p, u64p]
+    lib.qaoa_sample.argtypes = [vp, ctypes.c_int, f64p, ctypes.c_uint64, u64p]
+    lib.qaoa_grad.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, f64p, f64p, f64p, f64p, f64p]
+    lib.qaoa_grad_angles.argtypes = [vp, ctypes.c_int, f64p, f64p, f64p, f64p, f64p]
+    lib.qaoa_cost_diag.argtypes = [vp, vp]
+    lib.qaoa_state_ptr.argtypes = [vp]
+    lib.qaoa_state_ptr.restype = vp
+    lib.qaoa_describe_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
+                                       ctypes.c_int]
+    lib.qaoa_last_error.argtypes = [vp]
+    lib.qaoa_last_error.restype = ctypes.c_char_p
+    lib.qaoa_free.argtypes = [vp]
+    lib.qaoa_free.restype = None
+    _lib = lib
+    return lib
+
+
+def _f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def state_bytes(n: int, precision="c64") -> int:
+    return int(load().qaoa_state_bytes(n, _PREC[precision]))
+
+
+def aux_bytes(n: int, precision="c64", cost_mode="recompute", with_grad=False) -> int:
+    return int(load().qaoa_aux_bytes(n, _PREC[precision], _COST[cost_mode], int(bool(with_grad))))
+
+
+def describe_plan(n: int, p: int, precision="c64", adjoint=False) -> str:
+    lib = load()
+    need = lib.qaoa_describe_plan(n, _PREC[precision], p, int(adjoint), None, 0)
+    buf = ctypes.create_string_buffer(need + 1)
+    lib.qaoa_describe_plan(n, _PREC[precision], p, int(adjoint), buf, need + 1)
+    return buf.value.decode()
+
+
+def lr_angles(p: int, dgamma: float, dbeta: float):
+    """Linear-ramp angles gamma_k = (k+1)/p dgamma, beta_k = (1 - k/p) dbeta (Sec. II-B)."""
+    k = np.arange(p, dtype=np.float64)
+    return (k + 1) / p * dgamma, (1 - k / p) * dbeta
+
+
+class Simulator:
+    """One weighted MaxCut instance on one GPU (``qaoa_init_graph``).
+
+    ``state`` / ``aux``: optional caller-owned torch CUDA tensors of exactly
+    ``state_bytes(n, precision)`` / at least ``aux_bytes(...)`` bytes; by
+    default they are allocated here with torch.
+    """
+
+    def __init__(self, n, u, v, w, scale=0.1, precision="c64", cost_mode="recompute", with_grad=False,
+                 state=None, aux=None, stream=None):
+        import torch
+        lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqaoa needs a CUDA device")
+        self.n = int(n)
+        self.precision = _PREC[precision]
+        self.cost_mode = _COST[cost_mode]
+        self.with_grad = bool(with_grad)
+        u = np.ascontiguousarray(u, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.int32)
+        self.m = len(u)
+        sb = state_bytes(self.n, self.precision)
+        if sb == 0:
+            raise QaoaError(QAOA_EINVAL, "n out of range")
+        cdt = torch.complex128 if self.precision == C128 else torch.complex64
+        if state is None:
+            state = torch.empty(1 << self.n, dtype=cdt, device="cuda")
+        ab = aux_bytes(self.n, self.precision, self.cost_mode, self.with_grad)
+        if aux is None and ab > 0:
+            aux = torch.empty(ab, dtype=torch.uint8, device="cuda")
+        self._state_t = state
+        self._aux_t = aux
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ctx = ctypes.c_void_p()
+        rc = lib.qaoa_init_graph(ctypes.byref(ctx), self.n, self.m,
+                                 u.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 w.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 float(scale), self.precision, self.cost_mode,
+                                 ctypes.c_void_p(state.data_ptr()), state.numel() * state.element_size(),
+                                 ctypes.c_void_p(aux.data_ptr() if aux is not None else None),
+                                 (aux.numel() * aux.element_size()) if aux is not None else 0,
+                                 ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != QAOA_OK:
+            raise QaoaError(rc, lib.qaoa_last_error(None).decode())
+        self._ctx = ctx
+        self._lib = lib
+
+    # -- helpers
+    def _check(self, rc):
+        if rc != QAOA_OK:
+            raise QaoaError(rc, self._lib.qaoa_last_error(self._ctx).decode())
+
+    @property
+    def handle(self):
+        """The qaoa_ctx pointer, for direct calls into the C ABI."""
+        return self._ctx
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.qaoa_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- API
+    def run(self, p: int, dgamma: float, dbeta: float):
+        self._check(self._lib.qaoa_run(self._ctx, int(p), float(dgamma), float(dbeta)))
+
+    def run_angles(self, gamma, beta):
+        g, gp = _f64(gamma)
+        b, bp = _f64(beta)
+        if len(g) != len(b):
+            raise ValueError("gamma and beta need the same length")
+        self._check(self._lib.qaoa_run_angles(self._ctx, len(g), gp, bp))
+
+    def expect(self) -> dict:
+        e, r, nrm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        cmin, cmax = ctypes.c_int64(), ctypes.c_int64()
+        amin, amax = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self._lib.qaoa_expect(self._ctx, ctypes.byref(e), ctypes.byref(r), ctypes.byref(nrm),
+                                          ctypes.byref(cmin), ctypes.byref(cmax), ctypes.byref(amin),
+                                          ctypes.byref(amax)))
+        return dict(exp_c=e.value, r=r.value, norm=nrm.value, c_min=cmin.value, c_max=cmax.value,
+                    argmin=amin.value, argmax=amax.value)
+
+    def extremes(self) -> dict:
+        cmin, cmax = ctypes.c_int64(), ctypes.c_int64()
+        amin, amax = ctypes.c_uint64(), ctypes.c_uint64()
+        self._check(self._lib.qaoa_expect(self._ctx, None, None, None, ctypes.byref(cmin), ctypes.byref(cmax),
+                                          ctypes.byref(amin), ctypes.byref(amax)))
+        return dict(c_min=cmin.value, c_max=cmax.value, argmin=amin.value, argmax=amax.value)
+
+    def sample(self, shots: int, uniforms=None, seed: int = 0) -> np.ndarray:
+        out = np.empty(int(shots), dtype=np.uint64)
+        up = None
+        if uniforms is not None:
+            uarr, up = _f64(uniforms)
+            if len(uarr) != shots:
+                raise ValueError("uniforms must have `shots` entries")
+        self._check(self._lib.qaoa_sample(self._ctx, int(shots), up, ctypes.c_uint64(seed),
+                                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return out
+
+    def grad(self, p: int, dgamma: float, dbeta: float) -> dict:
+        gg = np.zeros(p)
+        gb = np.zeros(p)
+        ddg, ddb, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.qaoa_grad(self._ctx, int(p), float(dgamma), float(dbeta),
+                                        gg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        gb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.byref(ddg), ctypes.byref(ddb), ctypes.byref(e)))
+        return dict(g_gamma=gg, g_beta=gb, d_dgamma=ddg.value, d_dbeta=ddb.value, exp_c=e.value)
+
+    def grad_angles(self, gamma, beta) -> dict:
+        g, gp = _f64(gamma)
+        b, bp = _f64(beta)
+        gg = np.zeros(len(g))
+        gb = np.zeros(len(g))
+        e = ctypes.c_double()
+        self._check(self._lib.qaoa_grad_angles(self._ctx, len(g), gp, bp,
+                                               gg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               gb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                               ctypes.byref(e)))
+        return dict(g_gamma=gg, g_beta=gb, exp_c=e.value)
+
+    def cost_diag(self):
+        import torch
+        out = torch.empty(1 << self.n, dtype=torch.int32, device="cuda")
+        self._check(self._lib.qaoa_cost_diag(self._ctx, ctypes.c_void_p(out.data_ptr())))
+        self.stream.synchronize()
+        return out
+
+    def state(self):
+        """The state vector (torch complex tensor on the GPU, shares memory)."""
+        self.stream.synchronize()
+        return self._state_t

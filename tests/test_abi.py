@@ -1,0 +1,103 @@
+"""CPU tests of the C ABI library: it loads, exports every declared symbol,
+rejects invalid arguments before touching a GPU, and plans validly."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2604_26423_b300 import build, qaoa
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_library()
+    return qaoa.load()
+
+
+def declared_symbols():
+    syms = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            syms |= set(re.findall(r"\b(qaoa_\w+)\s*\(", text))
+    return syms
+
+
+def test_exports_every_declared_symbol(lib):
+    syms = declared_symbols()
+    assert "qaoa_init_graph" in syms and "qaoa_run" in syms
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(qaoa.EXPORTS) <= syms
+
+
+def test_sizes(lib):
+    assert qaoa.state_bytes(33, "c64") == 64 << 30          # 2^(N+3) bytes in FP32 (Sec. II-E)
+    assert qaoa.state_bytes(32, "c128") == 64 << 30
+    assert qaoa.state_bytes(35, "c64") == 0
+    assert qaoa.state_bytes(0, "c64") == 0
+    assert qaoa.aux_bytes(20, "c64", "stream", False) == 4 << 20
+    assert qaoa.aux_bytes(20, "c64", "recompute", True) == 8 << 20
+
+
+def _init(lib, n, u, v, w, scale=0.1, prec=0, mode=1):
+    ctx = ctypes.c_void_p()
+    u = np.ascontiguousarray(u, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    P = ctypes.POINTER(ctypes.c_int32)
+    rc = lib.qaoa_init_graph(ctypes.byref(ctx), n, len(u), u.ctypes.data_as(P), v.ctypes.data_as(P),
+                             w.ctypes.data_as(P), scale, prec, mode, None, 0, None, 0, None)
+    return rc, ctx, lib.qaoa_last_error(None).decode()
+
+
+@pytest.mark.parametrize("n,u,v,w,scale,prec,mode,word", [
+    (5, [0], [0], [1], 0.1, 0, 1, "self loop"),
+    (5, [0], [5], [1], 0.1, 0, 1, "out of range"),
+    (5, [0, 1], [1, 0], [1, 2], 0.1, 0, 1, "repeated"),
+    (5, [0], [1], [0], 0.1, 0, 1, "zero weight"),
+    (5, [0], [1], [1], -1.0, 0, 1, "weight_scale"),
+    (0, [], [], [], 0.1, 0, 1, "n out of range"),
+    (35, [], [], [], 0.1, 0, 1, "n out of range"),
+    (34, [], [], [], 0.1, 1, 1, "n out of range"),
+    (5, [0], [1], [1], 0.1, 7, 1, "precision"),
+    (5, [0], [1], [1], 0.1, 0, 9, "cost_mode"),
+    (5, [0, 1], [1, 2], [1 << 20, 1], 0.1, 0, 1, "exceeds"),
+])
+def test_invalid_graphs_rejected(lib, n, u, v, w, scale, prec, mode, word):
+    rc, ctx, msg = _init(lib, n, u, v, w, scale, prec, mode)
+    assert rc == qaoa.QAOA_EINVAL
+    assert not ctx.value
+    assert word in msg
+
+
+def test_null_context_calls(lib):
+    assert lib.qaoa_run(None, 1, 0.1, 0.1) == qaoa.QAOA_EINVAL
+    lib.qaoa_free(None)
+
+
+@pytest.mark.parametrize("n", [13, 16, 24, 28, 30, 33, 34])
+@pytest.mark.parametrize("p", [0, 1, 3, 10])
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_plans_valid(lib, n, p, prec):
+    text = qaoa.describe_plan(n, p, prec)
+    assert "INVALID" not in text and not text.startswith("error"), text[:500]
+    passes = int(re.search(r"passes=(\d+)", text).group(1))
+    groups = int(re.search(r"groups=(\d+)", text).group(1))
+    if p == 0:
+        assert passes == 1
+    elif groups > 1:
+        assert passes == 1 + p * (groups - 1)   # cross-layer fusion
+    else:
+        assert passes == p
+
+
+def test_n33_three_groups(lib):
+    # 33 qubits: one group of 15 low qubits, two of high qubits -> 7 HBM passes at p = 3
+    text = qaoa.describe_plan(33, 3, "c64")
+    assert "groups=3 passes=7" in text

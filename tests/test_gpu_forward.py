@@ -1,0 +1,205 @@
+"""GPU forward path vs the oracle: cost diagonal, extremes, state, <C>, r, shots.
+
+Tolerances (from the arithmetic):
+* integer work (C(x) diagonal, C_min / C_max, argmin / argmax): bit-exact;
+* complex128 state: L2 distance <= 1e-12 (unit-norm state);
+* complex64 state: L2 distance <= 1e-4 (FP32 rounding of ~n butterflies and a
+  phase per amplitude per layer, ~1e-7 each);
+* <C> relative: 1e-11 (c128), 2e-5 (c64); |r - r_oracle| is held to 1e-9
+  (c128) and 1e-5 (c64);
+* shots (c128, shared uniforms): identical except where u * total falls within
+  1e-9 (relative) of a CDF step, where both answers are valid.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_26423_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+S = 0.1
+
+
+def sim(*a, **k):
+    from paper_2604_26423_b300.qaoa import Simulator
+    return Simulator(*a, **k)
+
+
+def graph(kind, n, seed):
+    if kind == "complete":
+        return inputs.complete_graph(n, seed)
+    if kind == "chain":
+        return inputs.chain_graph(n, seed)
+    if kind == "sparse":
+        u, v, w = inputs.complete_graph(n, seed)
+        keep = inputs.uniforms(seed + 5, len(u)) < 0.3
+        keep[0] = True
+        return u[keep], v[keep], w[keep]
+    if kind == "signed":
+        u, v, w = inputs.complete_graph(n, seed)
+        sign = np.where(inputs.uniforms(seed + 9, len(u)) < 0.4, -1, 1).astype(np.int32)
+        return u, v, w * sign
+    raise ValueError(kind)
+
+
+def state_np(s):
+    return s.state().cpu().numpy().astype(np.complex128)
+
+
+@pytest.mark.parametrize("n,kind", [(3, "complete"), (9, "sparse"), (14, "complete"), (15, "signed"),
+                                    (16, "complete"), (17, "complete"), (19, "chain"), (21, "complete")])
+def test_cost_diag_and_extremes_exact(n, kind):
+    u, v, w = graph(kind, n, 100 + n)
+    ref = oracle.cut_values(n, u, v, w)
+    with sim(n, u, v, w, S, "c64") as s:
+        got = s.cost_diag().cpu().numpy().astype(np.int64)
+        ext = s.extremes()
+    assert np.array_equal(got, ref)
+    cmin, cmax, amin, amax = oracle.extremes(n, ref)
+    assert (ext["c_min"], ext["c_max"], ext["argmin"], ext["argmax"]) == (cmin, cmax, amin, amax)
+
+
+CASES = [
+    # n, p, kind, precision
+    (2, 1, "complete", "c128"), (5, 3, "sparse", "c128"), (12, 2, "complete", "c128"),
+    (13, 2, "complete", "c128"), (13, 1, "complete", "c64"), (14, 3, "signed", "c128"),
+    (16, 3, "complete", "c128"), (16, 3, "complete", "c64"), (17, 2, "chain", "c64"),
+    (18, 1, "sparse", "c128"), (19, 4, "complete", "c128"), (20, 3, "complete", "c64"),
+    (21, 2, "signed", "c64"), (16, 0, "complete", "c128"), (15, 5, "complete", "c64"),
+]
+
+
+@pytest.mark.parametrize("n,p,kind,prec", CASES)
+@pytest.mark.parametrize("cost_mode", ["recompute", "stream"])
+def test_forward_vs_oracle(n, p, kind, prec, cost_mode):
+    u, v, w = graph(kind, n, 200 + n + p)
+    g, b = oracle.lr_schedule(p, 0.6, 0.3) if p else (np.zeros(0), np.zeros(0))
+    ref = oracle.run(n, u, v, w, S, g, b)
+    with sim(n, u, v, w, S, prec, cost_mode=cost_mode) as s:
+        s.run(p, 0.6, 0.3)
+        res = s.expect()
+        psi = state_np(s)
+    l2 = np.linalg.norm(psi - ref["psi"])
+    tol_l2, tol_e, tol_r = (1e-12, 1e-11, 1e-9) if prec == "c128" else (1e-4, 2e-5, 1e-5)
+    assert l2 <= tol_l2, f"L2 {l2:.3e}"
+    assert abs(res["exp_c"] - ref["exp_c"]) <= tol_e * max(1.0, abs(ref["exp_c"]))
+    assert abs(res["norm"] - 1.0) <= (1e-12 if prec == "c128" else 1e-5)
+    assert abs(res["r"] - ref["r"]) <= tol_r, f"|r - r_oracle| = {abs(res['r'] - ref['r']):.3e}"
+    assert (res["c_min"], res["c_max"], res["argmin"], res["argmax"]) == \
+        (ref["c_min"], ref["c_max"], ref["argmin"], ref["argmax"])
+
+
+@pytest.mark.parametrize("n,prec", [(9, "c128"), (14, "c128"), (17, "c64")])
+def test_explicit_angles_wide_range(n, prec):
+    # angles beyond the ramp: |beta| > pi/4 uses the plain butterfly form,
+    # negative gamma and beta exercise both rotation signs
+    u, v, w = graph("complete", n, 300 + n)
+    gamma = np.array([0.7, -1.1, 2.0])
+    beta = np.array([1.2, -0.4, 2.6])
+    ref = oracle.simulate(n, u, v, w, S, gamma, beta)
+    with sim(n, u, v, w, S, prec) as s:
+        s.run_angles(gamma, beta)
+        psi = state_np(s)
+    assert np.linalg.norm(psi - ref) <= (1e-12 if prec == "c128" else 1e-4)
+
+
+@pytest.mark.parametrize("n", [14, 18])
+def test_stream_equals_recompute_bitwise(n):
+    u, v, w = graph("complete", n, 400 + n)
+    outs = []
+    for mode in ("recompute", "stream"):
+        with sim(n, u, v, w, S, "c64", cost_mode=mode) as s:
+            s.run(3, 0.6, 0.3)
+            outs.append(s.state().cpu().numpy().copy())
+    assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
+
+
+def _boundary(psi, uni, tol=1e-9):
+    """Shots whose u * total lies within tol (relative) of a CDF step."""
+    pr = np.abs(psi) ** 2
+    F = np.cumsum(pr)
+    t = uni * F[-1]
+    idx = np.searchsorted(F, t, side="right")
+    near = np.zeros(len(uni), dtype=bool)
+    for k, (i, tt) in enumerate(zip(idx, t)):
+        for j in (i - 1, i):
+            if 0 <= j < len(F) and abs(F[j] - tt) <= tol * F[-1]:
+                near[k] = True
+    return near
+
+
+@pytest.mark.parametrize("n,p", [(6, 2), (12, 3), (16, 3)])
+def test_shots_match_oracle_c128(n, p):
+    u, v, w = graph("complete", n, 500 + n)
+    g, b = oracle.lr_schedule(p, 0.6, 0.3)
+    psi_ref = oracle.simulate(n, u, v, w, S, g, b)
+    uni = inputs.uniforms(77 + n, 1024)
+    ref = oracle.sample(psi_ref, uni)
+    with sim(n, u, v, w, S, "c128") as s:
+        s.run(p, 0.6, 0.3)
+        got = s.sample(1024, uniforms=uni)
+        got_seed = s.sample(1024, seed=77 + n)
+    ok = (got == ref) | _boundary(psi_ref, uni)
+    assert ok.all(), f"{(~ok).sum()} shot mismatches"
+    # the device SplitMix64 stream equals the host generator's
+    assert np.array_equal(got_seed, got)
+
+
+def test_shots_rule_on_gpu_state_c64():
+    # the sampling kernel applies the oracle's rule to the GPU's own c64 state
+    n, p = 15, 3
+    u, v, w = graph("complete", n, 600)
+    uni = inputs.uniforms(601, 4096)
+    with sim(n, u, v, w, S, "c64") as s:
+        s.run(p, 0.6, 0.3)
+        psi = state_np(s)
+        got = s.sample(4096, uniforms=uni)
+    ref = oracle.sample(psi, uni)
+    ok = (got == ref) | _boundary(psi, uni, 1e-6)
+    assert ok.all(), f"{(~ok).sum()} shot mismatches"
+
+
+def test_config_n16_full():
+    # n=16, K_16 (120 edges), w in {1..10}, s = 1/10, p = 3, dgamma 0.6, dbeta 0.3,
+    # complex128, <C>, r from exhaustive C_min / C_max, 1024 shots
+    n, p = 16, 3
+    u, v, w = inputs.complete_graph(n, 16)
+    assert len(u) == 120
+    g, b = oracle.lr_schedule(p, 0.6, 0.3)
+    ref = oracle.run(n, u, v, w, S, g, b)
+    uni = inputs.uniforms(1601, 1024)
+    shots_ref = oracle.sample(ref["psi"], uni)
+    with sim(n, u, v, w, S, "c128") as s:
+        s.run(p, 0.6, 0.3)
+        res = s.expect()
+        shots = s.sample(1024, uniforms=uni)
+        psi = state_np(s)
+    assert np.linalg.norm(psi - ref["psi"]) <= 1e-12
+    assert abs(res["r"] - ref["r"]) <= 1e-9
+    assert (res["c_min"], res["c_max"]) == (ref["c_min"], ref["c_max"])
+    assert ((shots == shots_ref) | _boundary(ref["psi"], uni)).all()
+
+
+def test_repeated_runs_reuse_context():
+    n = 17
+    u, v, w = graph("complete", n, 700)
+    with sim(n, u, v, w, S, "c64") as s:
+        vals = []
+        for p in (1, 3, 1, 3):
+            s.run(p, 0.6, 0.3)
+            vals.append(s.expect()["exp_c"])
+    assert vals[0] == vals[2] and vals[1] == vals[3]
+
+
+def test_errors_reported():
+    from paper_2604_26423_b300.qaoa import QaoaError
+    u, v, w = graph("complete", 14, 800)
+    with sim(14, u, v, w, S, "c64") as s:
+        with pytest.raises(QaoaError):
+            s.sample(10)                      # no prepared state yet
+        with pytest.raises(QaoaError):
+            s.run(-1, 0.6, 0.3)
+        s.run(1, 0.6, 0.3)
+        with pytest.raises(QaoaError):
+            s.sample(10, uniforms=np.array([0.1] * 9 + [1.5]))
