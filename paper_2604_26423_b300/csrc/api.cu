@@ -31,6 +31,8 @@ namespace {
 
 constexpr int kR = 5, kWB = 3;           // forward tile: 2^5 registers x 32 lanes x 8 warps
 constexpr int kSmax = 15;                // super-tile bits (L2-resident working set)
+constexpr int kRAdj = 4, kWBAdj = 3;     // adjoint tile: psi and lambda, 2^4 registers each
+constexpr int kSmaxAdj = 14;             // adjoint super-tile (two vectors in L2)
 constexpr int kMinUnitsLog2 = 9;         // keep >= 512 super-tiles when n allows
 constexpr long long kMaxAbsWeightSum = 1 << 20;
 constexpr int kMaxGrid = 4096;           // persistent grid cap (partial-sum buffer size)
@@ -108,6 +110,15 @@ TileShape fwd_shape(int prec) {
   s.R = kR;
   s.WB = kWB;
   s.amp_bytes = amp_bytes(prec);
+  return s;
+}
+
+TileShape adj_shape(int prec) {
+  TileShape s;
+  s.R = kRAdj;
+  s.WB = kWBAdj;
+  s.amp_bytes = amp_bytes(prec);
+  s.nvec = 2;
   return s;
 }
 
@@ -330,7 +341,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     for (int i = 0; i < pd.nouter; ++i) pd.outer[i] = (int8_t)pp.outer[i];
     pd.n_units = 1ull << pd.nouter;
     const double ba = pp.layer_a >= 0 ? beta[pp.layer_a] : 0.0;
-    const double bb = pp.layer_b >= 0 ? beta[pp.layer_b] : 0.0;
+    const double bb = pp.layer_b >= 0 ? beta[pp.layer_b] : 0.0;  // forward: mixer B shares the cost's layer
     const bool fast = fabs(cos(ba)) >= fabs(sin(ba)) && fabs(cos(bb)) >= fabs(sin(bb));
     fasts[pi] = fast;
     mixer_coeffs(ba, fast, &pd.tauA, &pd.alphaA);
@@ -370,7 +381,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     PassArgs pa;
     pa.state = c->state;
     pa.diag = stream ? (const int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n))) : nullptr;
-    pa.phase = pp.layer_b >= 0 ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_b) * nc * ab) : nullptr;
+    pa.phase = pp.layer_c >= 0 ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_c) * nc * ab) : nullptr;
     pa.wmat = (const int32_t*)c->d_wmat.p;
     pa.ctabs = (const int32_t*)c->d_ctabs.p;
     pa.phase_in_smem = tab_smem ? 1 : 0;
@@ -650,8 +661,8 @@ void* qaoa_state_ptr(qaoa_ctx* c) { return c ? c->state : nullptr; }
 int qaoa_describe_plan(int n, int precision, int p, int adjoint, char* out, int cap) {
   std::string s;
   try {
-    if (adjoint) throw std::runtime_error("adjoint plans are described by qaoa_grad");
-    Plan pl = plan_forward(n, p, fwd_shape(precision), kSmax, kMinUnitsLog2);
+    Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), kSmaxAdj, kMinUnitsLog2)
+                      : plan_forward(n, p, fwd_shape(precision), kSmax, kMinUnitsLog2);
     std::string e = validate(pl);
     s = pl.describe();
     if (!e.empty()) s += "INVALID: " + e + "\n";

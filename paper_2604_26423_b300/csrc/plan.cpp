@@ -100,7 +100,7 @@ uint32_t pick_bits(uint32_t cand, int R, uint32_t already) {
 }  // namespace
 
 std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool cost, uint32_t b_bits,
-                                   bool reduce, uint8_t first_src) {
+                                   bool reduce, uint8_t first_src, bool lam) {
   const int R = sh.R;
   std::vector<RoundPlan> out;
   uint32_t remA = a_bits, remB = b_bits;
@@ -126,6 +126,7 @@ std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool co
       if (!layout_round(sh, need, true, rp)) throw std::runtime_error("plan_rounds: final layout");
       apply(rp, need);
       rp.reduce = reduce ? 1 : 0;
+      rp.lam = (lam && out.empty()) ? 1 : 0;
       rp.dst = DST_GLOBAL;
       out.push_back(rp);
       return out;
@@ -150,6 +151,7 @@ std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool co
     }
     if (!layout_round(sh, x, global, rp)) throw std::runtime_error("plan_rounds: layout");
     apply(rp, x);
+    rp.lam = (lam && out.empty()) ? 1 : 0;
     rp.dst = DST_SMEM;
     out.push_back(rp);
     first = false;
@@ -276,98 +278,102 @@ uint32_t tile_mask(const std::vector<int>& tile, const std::vector<int>& chunk) 
 
 }  // namespace
 
-Plan plan_forward(int n, int p, const TileShape& sh, int s_max, int min_units_log2) {
-  const int T = sh.T();
-  if (n < T) throw std::runtime_error("plan_forward: n below the tile size");
-  if (n > kMaxQubits) throw std::runtime_error("plan_forward: n too large");
-  Plan plan;
-  plan.n = n;
-  plan.p = p;
-  plan.shape = sh;
-  int S = std::min(s_max, std::max(T, n - min_units_log2));
-  S = std::min(S, n);
-  plan.S = S;
-  // qubit groups: the low S bits, then windows of high bits that keep 32
-  // (r = 5) or 16 (r = 4) consecutive amplitudes per contiguous run
+namespace {
+
+std::vector<Group> make_groups(int n, int S) {
+  // the low S bits, then windows of high bits that keep 32 (r = 5) or 16
+  // (r = 4) consecutive amplitudes per contiguous run
   std::vector<Group> groups;
-  {
-    Group low;
-    for (int b = 0; b < S; ++b) low.sb.push_back(b), low.targets.push_back(b);
-    groups.push_back(low);
-    const int left = n - S;
-    if (left > 0) {
-      const int X5 = S - 5, X4 = S - 4;
-      const int g5 = (left + X5 - 1) / X5, g4 = (left + X4 - 1) / X4;
-      const int r = g5 <= g4 ? 5 : 4;
-      const int X = S - r;
-      for (int a = S; a < n; a += X) {
-        const int b = std::min(n, a + X);
-        const int h = std::min(a, n - X);
-        Group g;
-        for (int q = 0; q < r; ++q) g.sb.push_back(q);
-        for (int q = h; q < h + X; ++q) g.sb.push_back(q);
-        for (int q = a; q < b; ++q) g.targets.push_back(q);
-        groups.push_back(g);
-      }
+  Group low;
+  for (int b = 0; b < S; ++b) low.sb.push_back(b), low.targets.push_back(b);
+  groups.push_back(low);
+  const int left = n - S;
+  if (left > 0) {
+    const int X5 = S - 5, X4 = S - 4;
+    const int g5 = (left + X5 - 1) / X5, g4 = (left + X4 - 1) / X4;
+    const int r = g5 <= g4 ? 5 : 4;
+    const int X = S - r;
+    for (int a = S; a < n; a += X) {
+      const int b = std::min(n, a + X);
+      const int h = std::min(a, n - X);
+      Group g;
+      for (int q = 0; q < r; ++q) g.sb.push_back(q);
+      for (int q = h; q < h + X; ++q) g.sb.push_back(q);
+      for (int q = a; q < b; ++q) g.targets.push_back(q);
+      groups.push_back(g);
     }
   }
-  for (auto& g : groups) plan.groups.push_back(g.targets);
-  const int G = (int)groups.size();
+  return groups;
+}
 
-  // op sequence -> passes: [init] [cost k, mix k over groups (alternating order)]... [reduce]
-  struct Proto { int grp = -1; int a = -1, cost = -1, b = -1; bool init = false, reduce = false; };
-  std::vector<Proto> protos;
+enum OpKind { OP_MIX, OP_COST };
+struct Op { OpKind kind; int layer, grp; };
+struct Proto { int grp = -1; int a = -1, cost = -1, b = -1; };
+
+// Packs an op sequence into passes of the form [mixer A][cost][mixer B], all
+// mixers of a pass on one group, at most one cost phase per pass.
+std::vector<Proto> pack_ops(const std::vector<Op>& ops) {
+  std::vector<Proto> out;
   Proto cur;
-  cur.init = true;
-  for (int k = 0; k < p; ++k) {
-    // cost of layer k
-    if (cur.cost >= 0) { protos.push_back(cur); cur = Proto(); }
-    cur.cost = k;
-    for (int i = 0; i < G; ++i) {
-      const int grp = (k % 2 == 0) ? i : G - 1 - i;
-      if (cur.grp < 0) {
-        cur.grp = grp;
-        if (cur.cost == k) cur.b = k; else cur.a = k;
-      } else if (cur.grp == grp && cur.cost == k && cur.b < 0) {
-        cur.b = k;
+  for (const Op& op : ops) {
+    if (op.kind == OP_MIX) {
+      if (cur.grp < 0 && cur.a < 0 && cur.b < 0) {
+        cur.grp = op.grp;
+        if (cur.cost >= 0) cur.b = op.layer; else cur.a = op.layer;
+      } else if (cur.cost >= 0 && cur.b < 0 && (cur.grp < 0 || cur.grp == op.grp)) {
+        cur.grp = op.grp;
+        cur.b = op.layer;
       } else {
-        protos.push_back(cur);
+        out.push_back(cur);
         cur = Proto();
-        cur.grp = grp;
-        cur.a = k;
+        cur.grp = op.grp;
+        cur.a = op.layer;
+      }
+    } else {
+      if (cur.cost < 0 && cur.b < 0) {
+        cur.cost = op.layer;
+      } else {
+        out.push_back(cur);
+        cur = Proto();
+        cur.cost = op.layer;
       }
     }
   }
-  cur.reduce = true;
   if (cur.grp < 0) cur.grp = 0;
-  protos.push_back(cur);
+  out.push_back(cur);
+  return out;
+}
 
-  for (const Proto& pr : protos) {
+void build_passes(Plan& plan, const std::vector<Group>& groups, const std::vector<Proto>& protos, bool backward) {
+  const int n = plan.n, T = plan.shape.T();
+  for (size_t pi = 0; pi < protos.size(); ++pi) {
+    const Proto& pr = protos[pi];
     PassPlan pp;
     const Group& g = groups[pr.grp];
     pp.sb = g.sb;
     for (int b = 0; b < n; ++b)
       if (std::find(g.sb.begin(), g.sb.end(), b) == g.sb.end()) pp.outer.push_back(b);
-    pp.init = pr.init;
-    pp.reduce = pr.reduce;
+    const bool first = pi == 0, last = pi + 1 == protos.size();
+    pp.init = !backward && first;
+    pp.linit = backward && first;
+    pp.reduce = !backward && last;
+    pp.store = !(backward && last);
     pp.layer_a = pr.a;
-    pp.layer_b = pr.cost;  // cost and mixer B belong to the same layer
+    pp.layer_c = pr.cost;
+    pp.layer_b = pr.b;
     const bool has_cost = pr.cost >= 0;
     const bool has_b = pr.b >= 0;
-    if (has_cost && !has_b && pr.a < 0 && !pr.init)
-      throw std::runtime_error("plan_forward: cost-only pass");
     const bool has_mix = pr.a >= 0 || has_b;
     if (has_mix) pp.targets = g.targets;
     auto chunks = chunk_group(Group{g.sb, has_mix ? g.targets : std::vector<int>{}}, T);
     const int K = (int)chunks.size();
-    // sub-pass op assignment
     struct SubOps { int chunk; bool a, cost, b; };
     std::vector<SubOps> seq;
     if (pr.a >= 0 && has_cost && has_b) {
       for (int i = 0; i < K - 1; ++i) seq.push_back({i, true, false, false});
       seq.push_back({K - 1, true, true, true});
       for (int i = K - 2; i >= 0; --i) seq.push_back({i, false, false, true});
-    } else if (pr.a >= 0 && has_cost && !has_b) {
+    } else if (pr.a >= 0 && has_cost) {
       for (int i = 0; i < K - 1; ++i) seq.push_back({i, true, false, false});
       seq.push_back({K - 1, true, true, false});
     } else if (pr.a >= 0) {
@@ -387,75 +393,127 @@ Plan plan_forward(int n, int p, const TileShape& sh, int s_max, int min_units_lo
       for (int j = 0; j < T; ++j) sp.pos[j] = int8_t(tile[j]);
       const uint32_t m = tile_mask(tile, chunk);
       const uint32_t am = so.a ? m : 0, bm = so.b ? m : 0;
-      const bool red = pp.reduce && s + 1 == seq.size();
+      const bool lastsub = s + 1 == seq.size();
+      const bool red = pp.reduce && lastsub;
       sp.init = pp.init && s == 0;
-      sp.rounds = plan_rounds(sh, am, so.cost, bm, red, sp.init ? SRC_INIT : SRC_GLOBAL);
+      sp.linit = pp.linit && s == 0;
+      sp.store = pp.store || !lastsub;
+      sp.rounds = plan_rounds(plan.shape, am, so.cost, bm, red, sp.init ? SRC_INIT : SRC_GLOBAL, sp.linit);
       sp.nA = popc(am);
       sp.nB = popc(bm);
-      sp.needs_c = so.cost || red;
+      sp.needs_c = so.cost || red || sp.linit;
       pp.subs.push_back(sp);
     }
     plan.passes.push_back(pp);
   }
+}
+
+Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2, bool backward) {
+  const int T = sh.T();
+  if (n < T) throw std::runtime_error("planner: n below the tile size");
+  if (n > kMaxQubits) throw std::runtime_error("planner: n too large");
+  if (backward && p < 1) throw std::runtime_error("planner: the adjoint needs p >= 1");
+  Plan plan;
+  plan.n = n;
+  plan.p = p;
+  plan.shape = sh;
+  plan.backward = backward;
+  int S = std::min(s_max, std::max(T, n - min_units_log2));
+  S = std::min(S, n);
+  plan.S = S;
+  const std::vector<Group> groups = make_groups(n, S);
+  for (auto& g : groups) plan.groups.push_back(g.targets);
+  const int G = (int)groups.size();
+  std::vector<Op> ops;
+  if (!backward) {
+    // [init] then per layer k: cost k, mixer k over the groups (alternating order)
+    for (int k = 0; k < p; ++k) {
+      ops.push_back({OP_COST, k, -1});
+      for (int i = 0; i < G; ++i) ops.push_back({OP_MIX, k, (k % 2 == 0) ? i : G - 1 - i});
+    }
+  } else {
+    // [lambda] then per layer k = p-1..0: inverse mixer k over the groups, inverse cost k
+    for (int j = 0; j < p; ++j) {
+      const int k = p - 1 - j;
+      for (int i = 0; i < G; ++i) ops.push_back({OP_MIX, k, (j % 2 == 0) ? G - 1 - i : i});
+      ops.push_back({OP_COST, k, -1});
+    }
+  }
+  build_passes(plan, groups, pack_ops(ops), backward);
   return plan;
 }
 
+}  // namespace
+
+Plan plan_forward(int n, int p, const TileShape& sh, int s_max, int min_units_log2) {
+  return make_plan(n, p, sh, s_max, min_units_log2, false);
+}
+
+Plan plan_backward(int n, int p, const TileShape& sh, int s_max, int min_units_log2) {
+  return make_plan(n, p, sh, s_max, min_units_log2, true);
+}
+
 std::string validate(const Plan& plan) {
-  const int n = plan.n;
-  // every qubit's mixer of every layer applied exactly once, cost once per layer,
-  // in order (layer k's mixer complete before cost k+1)
-  std::vector<std::vector<int>> mix_count(plan.p, std::vector<int>(n, 0));
-  std::vector<int> cost_count(plan.p, 0);
-  int init_count = 0, reduce_count = 0;
+  const int n = plan.n, P = plan.p;
+  const bool bwd = plan.backward;
+  // Dependencies. Forward: mixer of layer k after cost k; cost k after every
+  // qubit's mixer of layer k-1. Adjoint (layers walked backwards): inverse
+  // mixer of layer k after the inverse cost of layer k+1; inverse cost of
+  // layer k after every qubit's inverse mixer of layer k. Each op once.
+  std::vector<std::vector<int>> mix_count(P, std::vector<int>(n, 0));
+  std::vector<int> cost_count(P, 0);
+  auto mix = [&](int L, int q) -> std::string {
+    if (L < 0 || L >= P) return "mixer without layer";
+    if (!bwd && cost_count[L] != 1) return "mixer before its layer's cost";
+    if (bwd && L + 1 < P && cost_count[L + 1] != 1) return "inverse mixer before the later layer's inverse cost";
+    if (mix_count[L][q]++ != 0) return "mixer applied twice";
+    return "";
+  };
+  auto cost = [&](int L) -> std::string {
+    if (L < 0 || L >= P) return "cost without layer";
+    const int need = bwd ? L : L - 1;
+    if (need >= 0)
+      for (int q = 0; q < n; ++q)
+        if (mix_count[need][q] != 1) return "cost phase before the mixer it depends on completed";
+    if (cost_count[L]++ != 0) return "cost applied twice";
+    return "";
+  };
+  int init_count = 0, reduce_count = 0, linit_count = 0;
   for (size_t pi = 0; pi < plan.passes.size(); ++pi) {
     const PassPlan& pp = plan.passes[pi];
-    if (pp.init) ++init_count;
-    if (pp.reduce) ++reduce_count;
-    if (pp.init && pi != 0) return "init not in the first pass";
-    if (pp.reduce && pi + 1 != plan.passes.size()) return "reduce not in the last pass";
-    for (const SubPassPlan& sp : pp.subs) {
+    const bool first = pi == 0, last = pi + 1 == plan.passes.size();
+    init_count += pp.init;
+    reduce_count += pp.reduce;
+    linit_count += pp.linit;
+    if ((pp.init || pp.linit) && !first) return "initialisation not in the first pass";
+    if (pp.reduce && !last) return "reduce not in the last pass";
+    if (!pp.store && !last) return "only the last pass may skip its store";
+    for (size_t si = 0; si < pp.subs.size(); ++si) {
+      const SubPassPlan& sp = pp.subs[si];
+      if (!sp.store && !(last && si + 1 == pp.subs.size())) return "a sub-pass other than the very last skips its store";
       uint32_t am = 0, bm = 0;
-      bool cost = false, red = false;
+      bool c = false, red = false;
       for (const RoundPlan& rp : sp.rounds) {
         for (int i = 0; i < plan.shape.R; ++i) {
           if (rp.mixA >> i & 1u) am |= 1u << rp.reg[i];
           if (rp.mixB >> i & 1u) bm |= 1u << rp.reg[i];
         }
-        cost |= rp.cost != 0;
+        c |= rp.cost != 0;
         red |= rp.reduce != 0;
       }
-      std::string e = validate_rounds(plan.shape, sp.rounds, am, cost, bm, red);
+      if (sp.linit && !sp.rounds.empty() && !sp.rounds[0].lam) return "lambda creation not in the first round";
+      std::string e = validate_rounds(plan.shape, sp.rounds, am, c, bm, red);
       if (!e.empty()) return "round check: " + e;
-      if (cost) {
-        if (pp.layer_b < 0) return "cost without layer";
-        // all mixers of the previous layer must be complete
-        if (pp.layer_b > 0)
-          for (int q = 0; q < n; ++q) {
-            bool here = false;
-            for (int j = 0; j < sp.T; ++j)
-              if (sp.pos[j] == q && (am >> j & 1u)) here = true;
-            if (mix_count[pp.layer_b - 1][q] + (here ? 1 : 0) != 1)
-              return "cost before the previous layer's mixer completed";
-          }
-        ++cost_count[pp.layer_b];
-      }
-      for (int j = 0; j < sp.T; ++j) {
-        const int q = sp.pos[j];
-        if (am >> j & 1u) {
-          if (pp.layer_a < 0) return "mixer A without layer";
-          if (cost_count[pp.layer_a] != 1) return "mixer before its layer's cost";
-          ++mix_count[pp.layer_a][q];
-        }
-        if (bm >> j & 1u) {
-          if (pp.layer_b < 0 || cost_count[pp.layer_b] != 1) return "mixer B before its cost";
-          ++mix_count[pp.layer_b][q];
-        }
-      }
+      for (int j = 0; j < sp.T; ++j)
+        if (am >> j & 1u) { e = mix(pp.layer_a, sp.pos[j]); if (!e.empty()) return e; }
+      if (c) { e = cost(pp.layer_c); if (!e.empty()) return e; }
+      for (int j = 0; j < sp.T; ++j)
+        if (bm >> j & 1u) { e = mix(pp.layer_b, sp.pos[j]); if (!e.empty()) return e; }
     }
   }
-  if (init_count != 1) return "init count";
-  if (reduce_count != 1) return "reduce count";
-  for (int k = 0; k < plan.p; ++k) {
+  if (bwd ? (linit_count != 1 || init_count || reduce_count) : (init_count != 1 || reduce_count != 1 || linit_count))
+    return "initialisation / reduction count";
+  for (int k = 0; k < P; ++k) {
     if (cost_count[k] != 1) return "cost count of a layer";
     for (int q = 0; q < n; ++q)
       if (mix_count[k][q] != 1) return "mixer count of a qubit";
@@ -474,8 +532,9 @@ std::string Plan::describe() const {
   }
   for (size_t pi = 0; pi < passes.size(); ++pi) {
     const PassPlan& pp = passes[pi];
-    os << "pass " << pi << " a=" << pp.layer_a << " b=" << pp.layer_b << (pp.init ? " init" : "")
-       << (pp.reduce ? " reduce" : "") << " sb=[";
+    os << "pass " << pi << " a=" << pp.layer_a << " c=" << pp.layer_c << " b=" << pp.layer_b
+       << (pp.init ? " init" : "") << (pp.linit ? " lambda" : "") << (pp.reduce ? " reduce" : "")
+       << (pp.store ? "" : " nostore") << " sb=[";
     for (int b : pp.sb) os << b << ",";
     os << "] subs=" << pp.subs.size() << "\n";
     for (size_t s = 0; s < pp.subs.size(); ++s) {
@@ -491,7 +550,7 @@ std::string Plan::describe() const {
         os << " warp=";
         for (int i = 0; i < shape.WB; ++i) os << int(rp.warp[i]) << (i + 1 < shape.WB ? "," : "");
         os << " A=" << int(rp.mixA) << " C=" << int(rp.cost) << " B=" << int(rp.mixB)
-           << " R=" << int(rp.reduce) << "\n";
+           << " R=" << int(rp.reduce) << (rp.lam ? " L=1" : "") << "\n";
       }
     }
   }

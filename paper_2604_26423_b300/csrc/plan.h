@@ -48,6 +48,7 @@ struct RoundPlan {
   uint8_t cost = 0;   // then the cost phase of layer b (all of layer a done)
   uint8_t mixB = 0;   // then the mixer of layer b on these register bits
   uint8_t reduce = 0; // then accumulate norm and <C> (final pass)
+  uint8_t lam = 0;    // adjoint: load psi only and set lambda = C(x) psi first
   uint8_t src = SRC_SMEM, dst = DST_SMEM;
   bool global_facing = false;
 };
@@ -58,7 +59,9 @@ struct SubPassPlan {
   std::vector<RoundPlan> rounds;
   int nA = 0, nB = 0;                   // butterflies per amplitude of layer a / b here
   bool init = false;                    // first sub-pass of the first pass
-  bool needs_c = false;                 // some round needs C(x) (cost or reduce)
+  bool linit = false;                   // adjoint: first sub-pass creates lambda = C psi
+  bool store = true;                    // the last round writes its tile back
+  bool needs_c = false;                 // some round needs C(x) (cost, reduce, lambda)
 };
 
 struct PassPlan {
@@ -67,12 +70,16 @@ struct PassPlan {
   std::vector<int> targets;             // qubits whose mixer this pass applies
   std::vector<SubPassPlan> subs;
   int layer_a = -1;                     // mixer layer applied before the cost phase
-  int layer_b = -1;                     // cost + mixer layer applied after it
+  int layer_c = -1;                     // layer of the cost phase
+  int layer_b = -1;                     // mixer layer applied after it
   bool init = false, reduce = false;
+  bool linit = false;                   // adjoint: creates lambda = C psi
+  bool store = true;                    // false only for the adjoint's final pass
 };
 
 struct Plan {
   int n = 0, p = 0, S = 0;
+  bool backward = false;
   TileShape shape;
   std::vector<std::vector<int>> groups; // qubit groups (one pass each per layer)
   std::vector<PassPlan> passes;
@@ -83,11 +90,17 @@ struct Plan {
 // s_max: largest super-tile bit count; min_units_log2: keep at least 2^x super-tiles.
 Plan plan_forward(int n, int p, const TileShape& shape, int s_max, int min_units_log2);
 
+// Adjoint plan: lambda = C psi, then for k = p-1..0 the inverse mixer of layer
+// k on every group followed by the inverse cost phase of layer k, packed into
+// passes like the forward plan (cross-layer fusion through alternating group
+// order). Nothing is stored after the last inverse cost phase.
+Plan plan_backward(int n, int p, const TileShape& shape, int s_max, int min_units_log2);
+
 // Plans the rounds of one sub-pass with tile bits `tb` (tile bit order) for the
 // op sequence [mixer A on a_bits] [cost] [mixer B on b_bits] [reduce].
 // a_bits / b_bits are tile-bit masks. Throws std::runtime_error if impossible.
 std::vector<RoundPlan> plan_rounds(const TileShape& shape, uint32_t a_bits, bool cost,
-                                   uint32_t b_bits, bool reduce, uint8_t first_src);
+                                   uint32_t b_bits, bool reduce, uint8_t first_src, bool lam = false);
 
 // Checks the structural invariants of a plan (each mixer bit applied once per
 // op, cost after all of layer a, lanes/warps/registers a permutation of the tile

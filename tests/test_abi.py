@@ -101,3 +101,24 @@ def test_n33_three_groups(lib):
     # 33 qubits: one group of 15 low qubits, two of high qubits -> 7 HBM passes at p = 3
     text = qaoa.describe_plan(33, 3, "c64")
     assert "groups=3 passes=7" in text
+
+
+@pytest.mark.parametrize("n", [12, 16, 24, 28, 33])
+@pytest.mark.parametrize("p", [1, 3, 5, 20])
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_adjoint_plans_valid(lib, n, p, prec):
+    text = qaoa.describe_plan(n, p, prec, adjoint=True)
+    assert "INVALID" not in text and not text.startswith("error"), text[:800]
+    assert " lambda" in text.splitlines()[2 + text.count("group ")] or "lambda" in text
+    assert "nostore" in text.splitlines()[-1] or "nostore" in text
+    passes = int(re.search(r"passes=(\d+)", text).group(1))
+    groups = int(re.search(r"groups=(\d+)", text).group(1))
+    assert passes == (1 + p * (groups - 1) if groups > 1 else p)
+
+
+def test_adjoint_matches_forward_group_count_at_config_sizes(lib):
+    # the adjoint keeps as many qubit groups as the forward at 24, 28 and 33 qubits
+    for n in (24, 28, 33):
+        f = int(re.search(r"groups=(\d+)", qaoa.describe_plan(n, 5, "c64")).group(1))
+        b = int(re.search(r"groups=(\d+)", qaoa.describe_plan(n, 5, "c64", adjoint=True)).group(1))
+        assert b == f, (n, f, b)
