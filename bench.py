@@ -1,0 +1,329 @@
+"""Benchmark: LR-QAOA layers/s at n = 33 qubits (complex64 state, 64 GiB) on one B300.
+
+Workload (the n = 33 single-GPU configuration): fully connected weighted MaxCut
+K_33 (528 edges), integer weights uniform in {1..10} (SplitMix64 seed 33),
+phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
+
+* step (``value``): one preparation of |psi_3> (all fused HBM passes), the FP64
+  <C> / norm reduction and r, and 4096 measurement shots, on a context whose
+  per-graph preprocessing (weight matrix, exhaustive C_min / C_max) is done
+  before the timed region. The state (64 GiB) is far larger than L2, so no
+  flush is needed between steps.
+* ``e2e``: the same job through the public C ABI from host arrays: per step
+  qaoa_init_graph (edge arrays from pinned host memory, exhaustive extremes),
+  qaoa_run, qaoa_expect and qaoa_sample back to host memory, qaoa_free.
+* ``roofline``: the fused pass kernel's algorithmic bytes (one read and one
+  write of the state per pass; no read in the |+> pass) over its event-timed
+  duration, against the measured HBM copy bandwidth.
+* ``cpu_baseline`` / ``--impl reference``: the gate-by-gate complex128 oracle on
+  the host cores, timed on one LR-QAOA layer of K_nc (nc chosen so the sample
+  takes seconds), scaled to one layer of K_33 by amplitude count times gate
+  count.
+
+Multi-GPU (torchrun, N > 1): independent replicas (the method's one-GPU path
+does not shard); each rank runs the same workload on its own GPU, timing is the
+max over ranks, and ``value`` counts the layers of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_QUBITS, P, DGAMMA, DBETA, SCALE, SEED, SHOTS = 33, 3, 0.6, 0.3, 0.1, 33, 4096
+METRIC = "LR-QAOA layers/s at n=33 (complex64, K_33, p=3)"
+PROFILE_JSON = os.path.join(ROOT, "profiles", "fwd_pass_kernel_traffic.json")
+KERNEL_SOURCES = ["paper_2604_26423_b300/csrc/pass_kernel.cuh", "paper_2604_26423_b300/csrc/device.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int):
+    """Max over ranks (identity for one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def oracle_layer_time(budget_s: float = 12.0):
+    """Times one LR-QAOA layer of the oracle on K_nc; returns (seconds, nc, threads)."""
+    import oracle
+    from paper_2604_26423_b300 import inputs
+    nc = 20
+    t = 0.0
+    while True:
+        u, v, w = inputs.complete_graph(nc, SEED)
+        g, b = oracle.lr_schedule(P, DGAMMA, DBETA)
+        zz, xx = oracle.gate_angles(nc, w, SCALE, g[:1], b[:1])
+        t0 = time.perf_counter()
+        oracle.circuit(nc, u, v, zz, xx)
+        t = time.perf_counter() - t0
+        # grow the sample while it stays inside the budget (state doubles, gates grow)
+        grow = 2.0 * ((nc + 1) * nc / 2 + nc + 1) / (nc * (nc - 1) / 2 + nc)
+        if t * grow > budget_s or nc >= 26:
+            return t, nc, oracle.num_threads()
+        nc += 1
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    t, nc, thr = oracle_layer_time(budget_s)
+    gates_c = nc * (nc - 1) / 2 + nc
+    gates_33 = N_QUBITS * (N_QUBITS - 1) / 2 + N_QUBITS
+    t33 = t * 2 ** (N_QUBITS - nc) * gates_33 / gates_c
+    return {"value": 1.0 / t33, "unit": "layers/s", "cores": thr, "kind": "oracle",
+            "sample": f"one LR-QAOA layer of K_{nc} ({nc*(nc-1)//2} RZZ + {nc} RX gates, complex128, "
+                      f"{(16 << nc) >> 20} MiB state) in {t:.2f} s, scaled to K_{N_QUBITS} by 2^{N_QUBITS-nc} "
+                      f"amplitudes x {gates_33:.0f}/{gates_c:.0f} gates"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2604_26423_b300 import inputs
+    from paper_2604_26423_b300.qaoa import Simulator
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    u, v, w = inputs.complete_graph(N_QUBITS, SEED)
+    stream = torch.cuda.current_stream()
+    sim = Simulator(N_QUBITS, u, v, w, SCALE, "c64", cost_mode=args.cost_mode)
+    state_buf = sim._state_t
+
+    def step():
+        sim.run(P, DGAMMA, DBETA)
+        res = sim.expect()
+        shots = sim.sample(SHOTS, seed=SEED + 1)
+        return res, shots
+
+    for _ in range(args.warmup):
+        res, shots = step()
+    sim.profile(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            res, shots = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms_local = e0.elapsed_time(e1)
+    prof = sim.profile_read("pass")
+    launches = sum(sim.profile_read(k)["launches"] for k in ("pass", "adjoint", "cost", "sample", "small"))
+    launches_all = sim.profile_read(5)["launches"]
+    sim.profile(False)
+    ms = reduce_max(ms_local, world)
+
+    # end to end through the C ABI from host arrays (per step: init, run, expect, sample, free)
+    uh = torch.from_numpy(u).pin_memory().numpy()
+    vh = torch.from_numpy(v).pin_memory().numpy()
+    wh = torch.from_numpy(w).pin_memory().numpy()
+    sim.close()
+
+    def e2e_step():
+        s2 = Simulator(N_QUBITS, uh, vh, wh, SCALE, "c64", cost_mode=args.cost_mode, state=state_buf)
+        s2.run(P, DGAMMA, DBETA)
+        r2 = s2.expect()
+        sh = s2.sample(SHOTS, seed=SEED + 1)
+        s2.close()
+        return r2, sh
+
+    e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world)
+    barrier(world)
+
+    peak, peak_kind = measured_peak()
+    achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else 0.0
+    traffic = None
+    try:
+        with open(PROFILE_JSON) as f:
+            pj = json.load(f)
+        if pj.get("kernel_hash") == kernel_hash():
+            traffic = pj.get("dram_bytes_per_launch_n33")
+    except Exception:
+        pass
+    layers = P * args.steps * world
+    out = {
+        "metric": METRIC, "value": layers / (ms * 1e-3), "unit": "layers/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 pairs), fp64 reductions",
+        "data": "synthetic: SplitMix64 K_33 weights in {1..10}",
+        "config": {"workload": "LR-QAOA K_33 weighted MaxCut, complex64 (64 GiB state), p=3, dgamma=0.6, "
+                               "dbeta=0.3, <C>, r and 4096 shots per step",
+                   "n": N_QUBITS, "p": P, "precision": "complex64", "cost_mode": args.cost_mode,
+                   "state_bytes": 8 << N_QUBITS, "l2": "state 64 GiB >> 126 MB L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": P * args.e2e_steps * world / e2e_s, "unit": "layers/s",
+                "h2d_bytes_per_step": int(u.nbytes + v.nbytes + w.nbytes + 16),
+                "d2h_bytes_per_step": int(SHOTS * 8 + 7 * 8)},
+        "gpu_launches": int(launches_all) if launches_all else int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "fwd_pass_kernel", "launches": prof["launches"],
+                     "bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
+                     "ms_per_launch": prof["ms"] / max(1, prof["launches"])},
+        "result": {"exp_c": res["exp_c"], "r": res["r"], "norm": res["norm"], "c_max": res["c_max"]},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ reference arm (the oracle)
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_layer_time(min(args.cpu_budget, 4.0))
+    t0 = time.perf_counter()
+    samples = []
+    for _ in range(args.steps):
+        samples.append(cpu_baseline(min(args.cpu_budget, 4.0)))
+    wall = time.perf_counter() - t0
+    v = statistics.median(s["value"] for s in samples)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "layers/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (oracle)",
+           "data": "synthetic: SplitMix64 K_n weights in {1..10}",
+           "config": {"workload": "LR-QAOA K_33 weighted MaxCut, p=3 (bounded oracle sample, scaled)",
+                      "n": N_QUBITS, "p": P},
+           "cpu_baseline": {"value": v, "unit": "layers/s", "cores": samples[-1]["cores"], "kind": "oracle",
+                            "sample": samples[-1]["sample"]},
+           "e2e": {"value": v, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cost-mode", default="recompute", choices=["recompute", "stream"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

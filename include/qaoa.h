@@ -159,6 +159,21 @@ void *qaoa_state_ptr(qaoa_ctx *ctx);
  */
 int qaoa_describe_plan(int n, int precision, int p, int adjoint, char *out, int cap);
 
+/*
+ * Per-kernel timing (CUDA events recorded on the context's stream around every
+ * launch of the library's kernels while enabled). kind: 0 forward pass
+ * kernel, 1 adjoint pass kernel, 2 cost diagonal / extremes, 3 sampling,
+ * 4 small-n whole-circuit kernels; kind 5 returns only the count of every
+ * kernel launch (all kinds, including reduction and scan helpers) since
+ * enabling. qaoa_profile_enable(ctx, 1) clears the
+ * counters and starts recording; 0 stops. qaoa_profile_read synchronises the
+ * stream and returns, for `kind`, the number of launches, their summed device
+ * time in ms and the algorithmic bytes they moved (state reads and writes, plus
+ * the int32 diagonal in stream mode). Errors: EINVAL (bad kind), ECUDA.
+ */
+int qaoa_profile_enable(qaoa_ctx *ctx, int enable);
+int qaoa_profile_read(qaoa_ctx *ctx, int kind, int64_t *launches, double *ms, double *bytes);
+
 /* Message of the last failure on ctx (or of the last failed qaoa_init_graph
  * when ctx is NULL). Never NULL. */
 const char *qaoa_last_error(const qaoa_ctx *ctx);

@@ -78,6 +78,14 @@ struct qaoa_ctx {
   std::map<std::pair<int, std::vector<int8_t>>, int> ctab_index;       // (shape, pos + layout) -> offset
   bool ctabs_dirty = false;
   std::map<int, std::unique_ptr<Plan>> plans;                         // forward plans by p
+  // per-kernel CUDA-event timing (qaoa_profile_enable / qaoa_profile_read)
+  struct ProfRec { int kind; cudaEvent_t a, b; double bytes; };
+  bool prof_on = false;
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[5] = {0, 0, 0, 0, 0}, prof_bytes[5] = {0, 0, 0, 0, 0};
+  long long prof_n[5] = {0, 0, 0, 0, 0};
+  long long nlaunch = 0;  // every kernel launch while profiling is enabled
   Extreme ext{};
   bool have_result = false;
   bool state_ready = false;
@@ -104,6 +112,38 @@ struct qaoa_ctx {
 namespace {
 
 int amp_bytes(int prec) { return prec == QAOA_C128 ? 16 : 8; }
+
+cudaEvent_t prof_event(qaoa_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel launch with events on the context's stream (when enabled).
+struct ProfScope {
+  qaoa_ctx* c;
+  int kind;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(qaoa_ctx* c_, int kind_, double bytes_) : c(c_), kind(kind_), bytes(bytes_) {
+    if (c->prof_on) {
+      a = prof_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = prof_event(c);
+      cudaEventRecord(b, c->stream);
+      c->prof_pending.push_back({kind, a, b, bytes});
+    }
+  }
+};
 
 TileShape fwd_shape(int prec) {
   TileShape s;
@@ -244,6 +284,7 @@ int launch_pass(qaoa_ctx* c, const PassDev& pd, const PassArgs& pa, size_t smem,
   auto kern = fwd_pass_kernel<Real, kR, kWB, FAST>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, 32 << kWB, smem, c->stream>>>(pd, pa);
+  if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   return QAOA_OK;
 }
@@ -281,14 +322,17 @@ int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   sa.betas = (const double*)c->d_ang.p;
   sa.result = (double*)c->d_result.p;
   const size_t smem = (size_t(1) << n) * amp_bytes(c->prec);
+  ProfScope ps(c, 4, double(smem));
   if (c->prec == QAOA_C128) {
     CUDA_TRY(c, cudaFuncSetAttribute(small_circuit_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     small_circuit_kernel<double><<<1, 512, smem, c->stream>>>(sa);
+    if (c->prof_on) ++c->nlaunch;
   } else {
     CUDA_TRY(c, cudaFuncSetAttribute(small_circuit_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     small_circuit_kernel<float><<<1, 512, smem, c->stream>>>(sa);
+    if (c->prof_on) ++c->nlaunch;
   }
   CUDA_TRY(c, cudaGetLastError());
   return QAOA_OK;
@@ -394,13 +438,23 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
     pa.partial = pp.reduce ? (double*)c->d_partial.p : nullptr;
-    if (c->prec == QAOA_C128)
-      rc = fast ? launch_pass<double, true>(c, pd, pa, smem, grid) : launch_pass<double, false>(c, pd, pa, smem, grid);
-    else
-      rc = fast ? launch_pass<float, true>(c, pd, pa, smem, grid) : launch_pass<float, false>(c, pd, pa, smem, grid);
+    {
+      // algorithmic HBM bytes: one read (none for the |+> pass) and one write of
+      // the state, plus one int32 diagonal read per sub-pass needing C(x)
+      const double N = double(1ull << n);
+      double bytes = (pp.init ? 0.0 : N * ab) + N * ab;
+      if (stream)
+        for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
+      ProfScope ps(c, 0, bytes);
+      if (c->prec == QAOA_C128)
+        rc = fast ? launch_pass<double, true>(c, pd, pa, smem, grid) : launch_pass<double, false>(c, pd, pa, smem, grid);
+      else
+        rc = fast ? launch_pass<float, true>(c, pd, pa, smem, grid) : launch_pass<float, false>(c, pd, pa, smem, grid);
+    }
     if (rc) return rc;
     if (pp.reduce) {
       sum_partials_kernel<<<1, 32, 0, c->stream>>>((const double*)c->d_partial.p, grid, 2, (double*)c->d_result.p);
+      if (c->prof_on) ++c->nlaunch;
       CUDA_TRY(c, cudaGetLastError());
     }
   }
@@ -415,8 +469,10 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
 int compute_extremes(qaoa_ctx* c, int32_t* diag_out, bool restrict_half) {
   const int n = c->n;
   CUDA_TRY(c, c->d_ext.ensure(sizeof(Extreme)));
+  ProfScope ps(c, 2, diag_out ? 4.0 * double(1ull << n) : 0.0);
   if (n < 16) {
     cost_small_kernel<<<1, 1024, 0, c->stream>>>(n, (const int32_t*)c->d_wmat.p, diag_out, (Extreme*)c->d_ext.p);
+    if (c->prof_on) ++c->nlaunch;
     CUDA_TRY(c, cudaGetLastError());
     return QAOA_OK;
   }
@@ -425,8 +481,10 @@ int compute_extremes(qaoa_ctx* c, int32_t* diag_out, bool restrict_half) {
   CUDA_TRY(c, c->d_ext_part.ensure(sizeof(Extreme) * blocks));
   cost_block_kernel<15><<<(unsigned)blocks, 1024, 0, c->stream>>>(n, (const int32_t*)c->d_wmat.p, diag_out,
                                                                  (Extreme*)c->d_ext_part.p);
+  if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   extreme_finalize_kernel<<<1, 1024, 0, c->stream>>>((const Extreme*)c->d_ext_part.p, blocks, (Extreme*)c->d_ext.p);
+  if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   return QAOA_OK;
 }
@@ -629,12 +687,15 @@ int qaoa_sample(qaoa_ctx* c, int shots, const double* uniforms, uint64_t seed, u
     CUDA_TRY(c, cudaMemcpyAsync(c->d_uni.p, uniforms, sizeof(double) * shots, cudaMemcpyHostToDevice, c->stream));
     d_uni = (const double*)c->d_uni.p;
   }
+  ProfScope ps(c, 3, double(1ull << n) * amp_bytes(c->prec));
   if (c->prec == QAOA_C128)
     block_sum_kernel<double><<<(unsigned)nb, 256, 0, c->stream>>>((const double2*)c->state, B, (double*)c->d_sums.p);
   else
     block_sum_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((const float2*)c->state, B, (double*)c->d_sums.p);
+  if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   scan_kernel<<<1, 1024, 0, c->stream>>>((const double*)c->d_sums.p, nb, (double*)c->d_pre.p);
+  if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   const int tb = 128, gb = (shots + tb - 1) / tb;
   if (c->prec == QAOA_C128)
@@ -643,6 +704,7 @@ int qaoa_sample(qaoa_ctx* c, int shots, const double* uniforms, uint64_t seed, u
   else
     shot_kernel<float><<<gb, tb, 0, c->stream>>>((const float2*)c->state, B, (const double*)c->d_pre.p, nb, shots,
                                                  d_uni, seed, (unsigned long long*)c->d_shots.p);
+  if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaMemcpyAsync(out, c->d_shots.p, sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -677,6 +739,45 @@ int qaoa_describe_plan(int n, int precision, int p, int adjoint, char* out, int 
   return (int)s.size();
 }
 
+int qaoa_profile_enable(qaoa_ctx* c, int enable) {
+  if (!c) return QAOA_EINVAL;
+  if (enable) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (auto& r : c->prof_pending) { c->ev_pool.push_back(r.a); c->ev_pool.push_back(r.b); }
+    c->prof_pending.clear();
+    for (int k = 0; k < 5; ++k) { c->prof_ms[k] = 0; c->prof_bytes[k] = 0; c->prof_n[k] = 0; }
+    c->nlaunch = 0;
+  }
+  c->prof_on = enable != 0;
+  return QAOA_OK;
+}
+
+int qaoa_profile_read(qaoa_ctx* c, int kind, int64_t* launches, double* ms, double* bytes) {
+  if (!c) return QAOA_EINVAL;
+  if (kind < 0 || kind > 5) return c->set_err(QAOA_EINVAL, "profile kind must be 0..5");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (auto& r : c->prof_pending) {
+    float t = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&t, r.a, r.b));
+    c->prof_ms[r.kind] += t;
+    c->prof_bytes[r.kind] += r.bytes;
+    c->prof_n[r.kind] += 1;
+    c->ev_pool.push_back(r.a);
+    c->ev_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+  if (kind == 5) {
+    if (launches) *launches = c->nlaunch;
+    if (ms) *ms = 0.0;
+    if (bytes) *bytes = 0.0;
+    return QAOA_OK;
+  }
+  if (launches) *launches = c->prof_n[kind];
+  if (ms) *ms = c->prof_ms[kind];
+  if (bytes) *bytes = c->prof_bytes[kind];
+  return QAOA_OK;
+}
+
 const char* qaoa_last_error(const qaoa_ctx* c) {
   if (!c) return g_init_error.c_str();
   return c->err.c_str();
@@ -691,6 +792,8 @@ void qaoa_free(qaoa_ctx* c) {
   DevBuf* bufs[] = {&c->d_wmat, &c->d_ctabs, &c->d_phase, &c->d_partial, &c->d_result, &c->d_ext,
                     &c->d_ext_part, &c->d_sums, &c->d_pre, &c->d_shots, &c->d_uni, &c->d_ang};
   for (DevBuf* b : bufs) b->release();
+  for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
 

@@ -432,10 +432,11 @@ Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2,
       for (int i = 0; i < G; ++i) ops.push_back({OP_MIX, k, (k % 2 == 0) ? i : G - 1 - i});
     }
   } else {
-    // [lambda] then per layer k = p-1..0: inverse mixer k over the groups, inverse cost k
+    // [lambda] then per layer k = p-1..0: inverse mixer k over the groups in the
+    // reverse of the forward order of layer k, then inverse cost k
     for (int j = 0; j < p; ++j) {
       const int k = p - 1 - j;
-      for (int i = 0; i < G; ++i) ops.push_back({OP_MIX, k, (j % 2 == 0) ? G - 1 - i : i});
+      for (int i = 0; i < G; ++i) ops.push_back({OP_MIX, k, (k % 2 == 0) ? G - 1 - i : i});
       ops.push_back({OP_COST, k, -1});
     }
   }

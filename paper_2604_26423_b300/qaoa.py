@@ -26,7 +26,9 @@ _ERRNAME = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE"}
 # every entry point declared in include/qaoa.h
 EXPORTS = ("qaoa_state_bytes", "qaoa_aux_bytes", "qaoa_init_graph", "qaoa_run", "qaoa_run_angles",
            "qaoa_expect", "qaoa_sample", "qaoa_grad", "qaoa_grad_angles", "qaoa_cost_diag",
-           "qaoa_state_ptr", "qaoa_describe_plan", "qaoa_last_error", "qaoa_free")
+           "qaoa_state_ptr", "qaoa_describe_plan", "qaoa_profile_enable", "qaoa_profile_read",
+           "qaoa_last_error", "qaoa_free")
+PROFILE_KINDS = {"pass": 0, "adjoint": 1, "cost": 2, "sample": 3, "small": 4}
 
 _lib = None
 
@@ -70,6 +72,8 @@ def load():
     lib.qaoa_state_ptr.restype = vp
     lib.qaoa_describe_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_char_p,
                                        ctypes.c_int]
+    lib.qaoa_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.qaoa_profile_read.argtypes = [vp, ctypes.c_int, i64p, f64p, f64p]
     lib.qaoa_last_error.argtypes = [vp]
     lib.qaoa_last_error.restype = ctypes.c_char_p
     lib.qaoa_free.argtypes = [vp]
@@ -241,6 +245,18 @@ class Simulator:
                                                gb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                ctypes.byref(e)))
         return dict(g_gamma=gg, g_beta=gb, exp_c=e.value)
+
+    def profile(self, enable: bool = True):
+        """Starts (clearing the counters) or stops per-kernel event timing."""
+        self._check(self._lib.qaoa_profile_enable(self._ctx, int(bool(enable))))
+
+    def profile_read(self, kind="pass") -> dict:
+        """Launch count, summed device ms and algorithmic bytes of one kernel kind."""
+        k = PROFILE_KINDS.get(kind, kind)
+        n, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.qaoa_profile_read(self._ctx, int(k), ctypes.byref(n), ctypes.byref(ms),
+                                                ctypes.byref(by)))
+        return dict(launches=n.value, ms=ms.value, bytes=by.value)
 
     def cost_diag(self):
         import torch
