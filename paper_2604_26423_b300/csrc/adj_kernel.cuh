@@ -1,0 +1,241 @@
+// adj_kernel.cuh -- adjoint (reverse-mode) pass kernel for d<C>/d(gamma_k, beta_k).
+//
+// After the forward pass leaves psi_p = U_{p-1} ... U_0 |+>, the adjoint walks
+// the layers backwards with two vectors, psi and lambda = U_{>k}^dag C psi_p,
+// uncomputing both with the inverse gates (Sec. II-B: U_B(beta) = exp(+i beta
+// H_B), U_C(gamma) = exp(-i gamma s H_C)), and accumulates
+//   dbeta_k:  2 Re <lambda| i H_B |psi> = -2 sum_q Im <lambda| X_q |psi>
+//   dgamma_k: 2 Re <lambda| -i s H_C |psi> = 2 s Im sum_x conj(lambda_x) psi_x h(x)
+// with h(x) = W - 2 C(x). X_q commutes with every factor exp(+i beta X_q') of
+// the mixer, so <lambda| X_q |psi> may be taken at any point of the mixer's
+// uncomputation; a round evaluates the terms of all its bits first and then
+// applies their inverse butterflies. Each round rescales by cos(beta)^k after
+// its k fast-form butterflies so the next round's terms see normalised vectors.
+// Passes, sub-passes and rounds come from the adjoint plan (plan.h); one launch
+// is one HBM pass reading and writing both vectors.
+#pragma once
+#include "device.cuh"
+
+namespace qaoa {
+
+struct AdjArgs {
+  void* psi;              // 2^n amplitudes (state)
+  void* lam;              // 2^n amplitudes (adjoint vector)
+  const int32_t* diag;    // int32 C(x) (stream mode) or nullptr
+  const void* phase;      // phase table of the cost layer (ncost entries)
+  const int32_t* wmat;    // n x n weights
+  const int32_t* ctabs;   // per-round cost tables
+  double* partial;        // per-CTA [dA, dC, dB] partial sums
+  int phase_in_smem;
+};
+
+// Sum over the round's register pairs along bit i of Im(conj(l_a) v_b + conj(l_b) v_a).
+template <int R, typename V, typename Real>
+__device__ __forceinline__ Real pair_term(const V* v, const V* l, int i) {
+  Real s = 0;
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) {
+    if (j >> i & 1) continue;
+    const int k = j | (1 << i);
+    s = fma(l[j].x, v[k].y, s);
+    s = fma(-l[j].y, v[k].x, s);
+    s = fma(l[k].x, v[j].y, s);
+    s = fma(-l[k].y, v[j].x, s);
+  }
+  return s;
+}
+
+// inverse mixer exp(-i beta X) on both vectors for the bits in `mask`; the
+// gradient terms of those bits are added to `acc` first
+template <int R, typename V, typename Real>
+__device__ __forceinline__ void inverse_mixer(V* v, V* l, uint8_t mask, Real tau, Real alpha, bool fast, Real scale,
+                                              Real& acc) {
+  if (!mask) return;
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+    if (mask >> i & 1) acc += pair_term<R, V, Real>(v, l, i);
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    if (mask >> i & 1) {
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j)
+        if (!(j >> i & 1)) {
+          bfly<Real>(v[j], v[j | (1 << i)], -tau, alpha, fast);
+          bfly<Real>(l[j], l[j | (1 << i)], -tau, alpha, fast);
+        }
+    }
+  }
+  if (fast) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+      v[j].x *= scale; v[j].y *= scale;
+      l[j].x *= scale; l[j].y *= scale;
+    }
+  }
+}
+
+template <typename Real>
+__device__ __forceinline__ Real pow_bits(Real c, uint8_t mask) {
+  Real r = 1;
+  for (int i = 0; i < 8; ++i)
+    if (mask >> i & 1) r *= c;
+  return r;
+}
+
+// Shared memory: psi tile[2^T] | lambda tile[2^T] | wmat[n*n] | tile consts | phase table
+template <typename Real, int R, int WB, bool FAST>
+__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
+adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
+  using C2 = typename Cx<Real>::T;
+  constexpr int T = R + 5 + WB;
+  constexpr int NT = 32 << WB;
+  constexpr int NA = 1 << R;
+  constexpr int AB = sizeof(C2);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2* tv = reinterpret_cast<C2*>(smem_raw);
+  C2* tl = tv + (1 << T);
+  int* wsm = reinterpret_cast<int*>(tl + (1 << T));
+  int* tconst = wsm + P.n * P.n;
+  C2* ptab = reinterpret_cast<C2*>(smem_raw +
+                                   (((size_t(2) << T) * AB + size_t(P.n * P.n + 32) * 4 + 15) & ~size_t(15)));
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = P.n;
+  for (int i = tid; i < n * n; i += NT) wsm[i] = A.wmat[i];
+  const C2* phase = reinterpret_cast<const C2*>(A.phase);
+  if (A.phase_in_smem && A.phase) {
+    for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
+    phase = ptab;
+  }
+  C2* gpsi = reinterpret_cast<C2*>(A.psi);
+  C2* glam = reinterpret_cast<C2*>(A.lam);
+  const bool stream = A.diag != nullptr;
+  const Real tauA = Real(P.tauA), alphaA = Real(P.alphaA), tauB = Real(P.tauB), alphaB = Real(P.alphaB);
+  double gA = 0.0, gC = 0.0, gB = 0.0;
+
+  for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
+    const uint64_t ubase = scatter_bits(unit, P.outer, P.nouter);
+    for (int s = 0; s < P.nsub; ++s) {
+      const SubDev& sp = P.sub[s];
+      const uint64_t ntiles = 1ull << sp.ninner;
+      for (uint64_t ti = 0; ti < ntiles; ++ti) {
+        const uint64_t gbase = ubase | scatter_bits(ti, sp.inner, sp.ninner);
+        __syncthreads();
+        if (sp.needs_c && !stream && warp == 0) tile_consts<T>(sp.pos, gbase, wsm, n, tconst, lane);
+        if (sp.needs_c && !stream) __syncthreads();
+        for (int r = 0; r < sp.nrounds; ++r) {
+          const RoundDev& rd = sp.rd[r];
+          if (rd.src == SRC_SMEM_D) __syncthreads();
+          uint32_t tb = 0;
+          uint64_t gb = gbase;
+#pragma unroll
+          for (int i = 0; i < 5; ++i)
+            if (lane >> i & 1) { tb |= 1u << rd.lane[i]; gb |= 1ull << sp.pos[rd.lane[i]]; }
+#pragma unroll
+          for (int i = 0; i < WB; ++i)
+            if (warp >> i & 1) { tb |= 1u << rd.warp[i]; gb |= 1ull << sp.pos[rd.warp[i]]; }
+          uint32_t sstr[R];
+          uint64_t gstr[R];
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            sstr[i] = swz<AB>(1u << rd.reg[i]);
+            gstr[i] = 1ull << sp.pos[rd.reg[i]];
+          }
+          const uint32_t sb0 = swz<AB>(tb);
+          auto soff = [&](int j) {
+            uint32_t o = sb0;
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+              if (j >> i & 1) o ^= sstr[i];
+            return o;
+          };
+          auto goff = [&](int j) {
+            uint64_t o = gb;
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+              if (j >> i & 1) o |= gstr[i];
+            return o;
+          };
+          const bool need_c = rd.cost || rd.lam;
+          RoundCost<R, WB> rcost;
+          if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
+          auto cv = [&](int j) { return stream ? __ldcg(A.diag + goff(j)) : rcost(j); };
+
+          C2 v[NA], l[NA];
+          if (rd.src == SRC_GLOBAL_D) {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) v[j] = __ldcg(gpsi + goff(j));
+            if (rd.lam) {
+              // lambda = C(x) psi (the operator whose expectation is differentiated)
+#pragma unroll
+              for (int j = 0; j < NA; ++j) {
+                const Real c = Real(cv(j));
+                l[j].x = c * v[j].x;
+                l[j].y = c * v[j].y;
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < NA; ++j) l[j] = __ldcg(glam + goff(j));
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) { v[j] = tv[soff(j)]; l[j] = tl[soff(j)]; }
+          }
+
+          Real ga = 0, gc = 0, gbv = 0;
+          inverse_mixer<R>(v, l, rd.mixA, tauA, alphaA, FAST, pow_bits(Real(P.cA), rd.mixA), ga);
+          if (rd.cost) {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+              const int c = cv(j);
+              const Real h = Real(P.wsum - 2 * c);
+              gc = fma(fma(l[j].x, v[j].y, -l[j].y * v[j].x), h, gc);
+              const C2 ph = phase[min(max(c - P.c_lo, 0), P.ncost - 1)];
+              // multiply both vectors by the conjugate phase (inverse cost unitary)
+              const Real vr = v[j].x, vi = v[j].y, lr = l[j].x, li = l[j].y;
+              v[j].x = vr * ph.x + vi * ph.y;
+              v[j].y = vi * ph.x - vr * ph.y;
+              l[j].x = lr * ph.x + li * ph.y;
+              l[j].y = li * ph.x - lr * ph.y;
+            }
+          }
+          inverse_mixer<R>(v, l, rd.mixB, tauB, alphaB, FAST, pow_bits(Real(P.cB), rd.mixB), gbv);
+          gA += double(ga);
+          gC += double(gc);
+          gB += double(gbv);
+
+          if (rd.dst == DST_GLOBAL_D) {
+            if (sp.store) {
+#pragma unroll
+              for (int j = 0; j < NA; ++j) {
+                __stcg(gpsi + goff(j), v[j]);
+                __stcg(glam + goff(j), l[j]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < NA; ++j) { tv[soff(j)] = v[j]; tl[soff(j)] = l[j]; }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  __shared__ double red[3][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    gA += __shfl_xor_sync(0xffffffffu, gA, o);
+    gC += __shfl_xor_sync(0xffffffffu, gC, o);
+    gB += __shfl_xor_sync(0xffffffffu, gB, o);
+  }
+  if (lane == 0) { red[0][warp] = gA; red[1][warp] = gC; red[2][warp] = gB; }
+  __syncthreads();
+  if (tid == 0) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int w = 0; w < NT / 32; ++w) { s0 += red[0][w]; s1 += red[1][w]; s2 += red[2][w]; }
+    A.partial[3 * blockIdx.x] = s0;
+    A.partial[3 * blockIdx.x + 1] = s1;
+    A.partial[3 * blockIdx.x + 2] = s2;
+  }
+}
+
+}  // namespace qaoa

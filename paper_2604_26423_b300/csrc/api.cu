@@ -24,6 +24,7 @@
 #include "pass_kernel.cuh"
 #include "aux_kernels.cuh"
 #include "small_kernel.cuh"
+#include "adj_kernel.cuh"
 
 using namespace qaoa;
 
@@ -74,10 +75,12 @@ struct qaoa_ctx {
   DevBuf aux_own;
   DevBuf d_wmat, d_ctabs, d_phase, d_partial, d_result, d_ext, d_ext_part;
   DevBuf d_sums, d_pre, d_shots, d_uni, d_ang;
+  DevBuf d_lambda, d_gacc;                                            // adjoint vector (if no aux), per-pass sums
   std::vector<int32_t> h_ctabs;                                        // host copy of all cost tables
   std::map<std::pair<int, std::vector<int8_t>>, int> ctab_index;       // (shape, pos + layout) -> offset
   bool ctabs_dirty = false;
   std::map<int, std::unique_ptr<Plan>> plans;                         // forward plans by p
+  std::map<int, std::unique_ptr<Plan>> bplans;                        // adjoint plans by p
   // per-kernel CUDA-event timing (qaoa_profile_enable / qaoa_profile_read)
   struct ProfRec { int kind; cudaEvent_t a, b; double bytes; };
   bool prof_on = false;
@@ -215,6 +218,8 @@ void to_round_dev(const RoundPlan& rp, RoundDev& rd) {
   rd.reduce = rp.reduce;
   rd.src = rp.src;
   rd.dst = rp.dst;
+  rd.lam = rp.lam;
+  rd.pad = 0;
   rd.ctab = -1;
 }
 
@@ -393,6 +398,9 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     pd.amp0 = pow(2.0, -0.5 * n);
     pd.c_lo = (int32_t)c->c_lo;
     pd.ncost = (int32_t)nc;
+    pd.wsum = (int32_t)c->W;
+    pd.cA = cos(ba);
+    pd.cB = cos(bb);
     for (int s = 0; s < pd.nsub; ++s) {
       const SubPassPlan& sp = pp.subs[s];
       SubDev& sd = pd.sub[s];
@@ -409,6 +417,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
       if (sd.nrounds > kMaxRoundsDev) return c->set_err(QAOA_EINVAL, "plan has too many rounds");
       sd.init = sp.init;
       sd.needs_c = sp.needs_c;
+      sd.store = sp.store;
       sd.scale = fast ? pow(cos(ba), sp.nA) * pow(cos(bb), sp.nB) : 1.0;
       for (int r = 0; r < sd.nrounds; ++r) {
         to_round_dev(sp.rounds[r], sd.rd[r]);
@@ -460,6 +469,224 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   }
   c->have_result = true;
   c->state_ready = true;
+  return QAOA_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+const Plan* get_bplan(qaoa_ctx* c, int p) {
+  auto it = c->bplans.find(p);
+  if (it != c->bplans.end()) return it->second.get();
+  auto pl = std::make_unique<Plan>(plan_backward(c->n, p, adj_shape(c->prec), kSmaxAdj, kMinUnitsLog2));
+  const Plan* r = pl.get();
+  c->bplans[p] = std::move(pl);
+  return r;
+}
+
+template <typename Real, bool FAST>
+int adj_blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
+  auto kern = adj_pass_kernel<Real, kRAdj, kWBAdj, FAST>;
+  CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, 32 << kWBAdj, smem));
+  if (*nb < 1) return c->set_err(QAOA_ECUDA, "adjoint kernel does not fit on an SM (smem %zu)", smem);
+  return QAOA_OK;
+}
+
+template <typename Real, bool FAST>
+int launch_adj(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid) {
+  auto kern = adj_pass_kernel<Real, kRAdj, kWBAdj, FAST>;
+  CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, 32 << kWBAdj, smem, c->stream>>>(pd, aa);
+  if (c->prof_on) ++c->nlaunch;
+  CUDA_TRY(c, cudaGetLastError());
+  return QAOA_OK;
+}
+
+void* lambda_ptr(qaoa_ctx* c) {
+  const size_t sb = qaoa_state_bytes(c->n, c->prec);
+  const size_t need = qaoa_aux_bytes(c->n, c->prec, c->cost_mode, 1);
+  if (c->aux && c->aux_bytes >= need) return c->aux;  // lambda is the first part of the aux buffer
+  if (c->d_lambda.ensure(sb) != cudaSuccess) return nullptr;
+  return c->d_lambda.p;
+}
+
+int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, double* g_gamma, double* g_beta,
+                 double* exp_c) {
+  const int n = c->n;
+  const int ab = amp_bytes(c->prec);
+  const TileShape sh = adj_shape(c->prec);
+  const int T = sh.T();
+  std::vector<double> gg(p, 0.0), gbt(p, 0.0);
+  if (n < T) {
+    int rc = upload_phases(c, p, gamma);
+    if (rc) return rc;
+    CUDA_TRY(c, c->d_ang.ensure(sizeof(double) * 2 * p));
+    std::vector<double> ang(2 * p);
+    for (int k = 0; k < p; ++k) { ang[2 * k] = gamma[k]; ang[2 * k + 1] = beta[k]; }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_ang.p, ang.data(), ang.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, c->d_gacc.ensure(sizeof(double) * (2 * p + 2)));
+    SmallGradArgs ga;
+    ga.base.n = n;
+    ga.base.p = p;
+    ga.base.state = c->state;
+    ga.base.wmat = (const int32_t*)c->d_wmat.p;
+    ga.base.phase = c->d_phase.p;
+    ga.base.c_lo = (int)c->c_lo;
+    ga.base.ncost = (int)(c->c_hi - c->c_lo + 1);
+    ga.base.betas = (const double*)c->d_ang.p;
+    ga.base.result = nullptr;
+    ga.scale_s = c->scale;
+    ga.wsum = (int)c->W;
+    ga.grads = (double*)c->d_gacc.p;
+    const size_t smem = (size_t(2) << n) * ab;
+    {
+      ProfScope ps(c, 4, 0.0);
+      if (c->prec == QAOA_C128) {
+        CUDA_TRY(c, cudaFuncSetAttribute(small_grad_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        small_grad_kernel<double><<<1, 512, smem, c->stream>>>(ga);
+      } else {
+        CUDA_TRY(c, cudaFuncSetAttribute(small_grad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        small_grad_kernel<float><<<1, 512, smem, c->stream>>>(ga);
+      }
+      if (c->prof_on) ++c->nlaunch;
+    }
+    CUDA_TRY(c, cudaGetLastError());
+    std::vector<double> h(2 * p + 2);
+    CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->d_gacc.p, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < p; ++k) { gg[k] = h[k]; gbt[k] = h[p + k]; }
+    if (g_gamma) memcpy(g_gamma, gg.data(), sizeof(double) * p);
+    if (g_beta) memcpy(g_beta, gbt.data(), sizeof(double) * p);
+    if (exp_c) *exp_c = h[2 * p];
+    c->state_ready = false;
+    c->have_result = false;
+    return QAOA_OK;
+  }
+  // forward: psi_p and <C>
+  int rc = run_forward(c, p, gamma, beta);
+  if (rc) return rc;
+  void* lam = lambda_ptr(c);
+  if (!lam) return c->set_err(QAOA_ENOMEM, "allocation of the adjoint vector failed");
+  const Plan* plan;
+  try {
+    plan = get_bplan(c, p);
+  } catch (std::exception& ex) {
+    return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
+  }
+  const bool stream = c->cost_mode == QAOA_COST_STREAM;
+  const long long nc = c->c_hi - c->c_lo + 1;
+  const size_t base_smem = (((size_t(2) << T) * ab + size_t(n * n + 32) * 4 + 15) & ~size_t(15));
+  const size_t with_tab = base_smem + size_t(nc) * ab;
+  int dev = 0, max_smem = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  CUDA_TRY(c, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const bool tab_smem = with_tab + 1024 <= (size_t)max_smem;
+  const size_t smem = tab_smem ? with_tab : base_smem;
+  const size_t npass = plan->passes.size();
+  std::vector<PassDev> pds(npass);
+  std::vector<char> fasts(npass);
+  for (size_t pi = 0; pi < npass; ++pi) {
+    const PassPlan& pp = plan->passes[pi];
+    PassDev& pd = pds[pi];
+    memset(&pd, 0, sizeof pd);
+    pd.n = n;
+    pd.T = T;
+    pd.nsub = (int)pp.subs.size();
+    if (pd.nsub > kMaxSubDev) return c->set_err(QAOA_EINVAL, "adjoint plan has too many sub-passes");
+    pd.nouter = (int)pp.outer.size();
+    for (int i = 0; i < pd.nouter; ++i) pd.outer[i] = (int8_t)pp.outer[i];
+    pd.n_units = 1ull << pd.nouter;
+    const double ba = pp.layer_a >= 0 ? beta[pp.layer_a] : 0.0;
+    const double bb = pp.layer_b >= 0 ? beta[pp.layer_b] : 0.0;
+    const bool fast = fabs(cos(ba)) >= fabs(sin(ba)) && fabs(cos(bb)) >= fabs(sin(bb));
+    fasts[pi] = fast;
+    mixer_coeffs(ba, fast, &pd.tauA, &pd.alphaA);
+    mixer_coeffs(bb, fast, &pd.tauB, &pd.alphaB);
+    pd.c_lo = (int32_t)c->c_lo;
+    pd.ncost = (int32_t)nc;
+    pd.wsum = (int32_t)c->W;
+    pd.cA = cos(ba);
+    pd.cB = cos(bb);
+    for (int s = 0; s < pd.nsub; ++s) {
+      const SubPassPlan& sp = pp.subs[s];
+      SubDev& sd = pd.sub[s];
+      for (int j = 0; j < T; ++j) sd.pos[j] = sp.pos[j];
+      std::vector<int> inner;
+      for (int b : pp.sb) {
+        bool in_tile = false;
+        for (int j = 0; j < T; ++j) in_tile |= sp.pos[j] == b;
+        if (!in_tile) inner.push_back(b);
+      }
+      sd.ninner = (int)inner.size();
+      for (int i = 0; i < sd.ninner; ++i) sd.inner[i] = (int8_t)inner[i];
+      sd.nrounds = (int)sp.rounds.size();
+      if (sd.nrounds > kMaxRoundsDev) return c->set_err(QAOA_EINVAL, "adjoint plan has too many rounds");
+      sd.needs_c = sp.needs_c;
+      sd.store = sp.store;
+      sd.scale = 1.0;
+      for (int r = 0; r < sd.nrounds; ++r) {
+        to_round_dev(sp.rounds[r], sd.rd[r]);
+        if ((sd.rd[r].cost || sd.rd[r].lam) && !stream) sd.rd[r].ctab = table_offset(c, sh, sd.pos, sd.rd[r]);
+      }
+    }
+  }
+  rc = upload_ctabs(c);
+  if (rc) return rc;
+  CUDA_TRY(c, c->d_gacc.ensure(sizeof(double) * 3 * npass));
+  for (size_t pi = 0; pi < npass; ++pi) {
+    const PassPlan& pp = plan->passes[pi];
+    const PassDev& pd = pds[pi];
+    const bool fast = fasts[pi];
+    AdjArgs aa;
+    aa.psi = c->state;
+    aa.lam = lam;
+    aa.diag = stream ? (const int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n))) : nullptr;
+    aa.phase = pp.layer_c >= 0 ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_c) * nc * ab) : nullptr;
+    aa.wmat = (const int32_t*)c->d_wmat.p;
+    aa.ctabs = (const int32_t*)c->d_ctabs.p;
+    aa.partial = (double*)c->d_partial.p;
+    aa.phase_in_smem = tab_smem ? 1 : 0;
+    int bps = 0;
+    if (c->prec == QAOA_C128)
+      rc = fast ? adj_blocks_per_sm<double, true>(c, smem, &bps) : adj_blocks_per_sm<double, false>(c, smem, &bps);
+    else
+      rc = fast ? adj_blocks_per_sm<float, true>(c, smem, &bps) : adj_blocks_per_sm<float, false>(c, smem, &bps);
+    if (rc) return rc;
+    const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
+    const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
+    {
+      // algorithmic bytes: both vectors read (psi only when lambda is created)
+      // and both written (nothing in the final pass)
+      const double N = double(1ull << n);
+      double bytes = (pp.linit ? 1.0 : 2.0) * N * ab + (pp.store ? 2.0 * N * ab : 0.0);
+      if (stream)
+        for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
+      ProfScope ps(c, 1, bytes);
+      if (c->prec == QAOA_C128)
+        rc = fast ? launch_adj<double, true>(c, pd, aa, smem, grid) : launch_adj<double, false>(c, pd, aa, smem, grid);
+      else
+        rc = fast ? launch_adj<float, true>(c, pd, aa, smem, grid) : launch_adj<float, false>(c, pd, aa, smem, grid);
+    }
+    if (rc) return rc;
+    sum_partials_kernel<<<1, 32, 0, c->stream>>>((const double*)c->d_partial.p, grid, 3,
+                                                 (double*)c->d_gacc.p + 3 * pi);
+    if (c->prof_on) ++c->nlaunch;
+    CUDA_TRY(c, cudaGetLastError());
+  }
+  std::vector<double> h(3 * npass);
+  double res[2];
+  CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->d_gacc.p, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(res, c->d_result.p, sizeof res, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (size_t pi = 0; pi < npass; ++pi) {
+    const PassPlan& pp = plan->passes[pi];
+    if (pp.layer_a >= 0) gbt[pp.layer_a] += -2.0 * h[3 * pi];
+    if (pp.layer_c >= 0) gg[pp.layer_c] += 2.0 * c->scale * h[3 * pi + 1];
+    if (pp.layer_b >= 0) gbt[pp.layer_b] += -2.0 * h[3 * pi + 2];
+  }
+  if (g_gamma) memcpy(g_gamma, gg.data(), sizeof(double) * p);
+  if (g_beta) memcpy(g_beta, gbt.data(), sizeof(double) * p);
+  if (exp_c) *exp_c = res[1];
+  c->state_ready = false;  // psi has been walked back towards |+>
   return QAOA_OK;
 }
 
@@ -586,7 +813,7 @@ int qaoa_init_graph(qaoa_ctx** out, int n, int m, const int32_t* u, const int32_
     c->aux_bytes = aux_bytes;
   }
   if (c->d_wmat.ensure(sizeof(int32_t) * n * n) != cudaSuccess ||
-      c->d_partial.ensure(sizeof(double) * 2 * kMaxGrid) != cudaSuccess || c->d_result.ensure(64) != cudaSuccess) {
+      c->d_partial.ensure(sizeof(double) * 4 * kMaxGrid) != cudaSuccess || c->d_result.ensure(64) != cudaSuccess) {
     cudaGetLastError();
     qaoa_free(c.release());
     return fail(QAOA_ENOMEM, "cudaMalloc failed");
@@ -790,25 +1017,45 @@ void qaoa_free(qaoa_ctx* c) {
   if (c->own_state && c->state) cudaFree(c->state);
   c->aux_own.release();
   DevBuf* bufs[] = {&c->d_wmat, &c->d_ctabs, &c->d_phase, &c->d_partial, &c->d_result, &c->d_ext,
-                    &c->d_ext_part, &c->d_sums, &c->d_pre, &c->d_shots, &c->d_uni, &c->d_ang};
+                    &c->d_ext_part, &c->d_sums, &c->d_pre, &c->d_shots, &c->d_uni, &c->d_ang,
+                    &c->d_lambda, &c->d_gacc};
   for (DevBuf* b : bufs) b->release();
   for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
 
-int qaoa_grad(qaoa_ctx* c, int p, double dgamma, double dbeta, double* g_gamma, double* g_beta, double* d_dgamma,
-              double* d_dbeta, double* exp_c) {
-  if (!c) return QAOA_EINVAL;
-  (void)p; (void)dgamma; (void)dbeta; (void)g_gamma; (void)g_beta; (void)d_dgamma; (void)d_dbeta; (void)exp_c;
-  return c->set_err(QAOA_EINVAL, "qaoa_grad is not implemented yet");
-}
-
 int qaoa_grad_angles(qaoa_ctx* c, int p, const double* gamma, const double* beta, double* g_gamma, double* g_beta,
                      double* exp_c) {
   if (!c) return QAOA_EINVAL;
-  (void)p; (void)gamma; (void)beta; (void)g_gamma; (void)g_beta; (void)exp_c;
-  return c->set_err(QAOA_EINVAL, "qaoa_grad_angles is not implemented yet");
+  if (p < 1 || !gamma || !beta) return c->set_err(QAOA_EINVAL, "the gradient needs p >= 1 and angle arrays");
+  for (int k = 0; k < p; ++k)
+    if (!std::isfinite(gamma[k]) || !std::isfinite(beta[k])) return c->set_err(QAOA_EINVAL, "non-finite angle");
+  return run_gradient(c, p, gamma, beta, g_gamma, g_beta, exp_c);
+}
+
+int qaoa_grad(qaoa_ctx* c, int p, double dgamma, double dbeta, double* g_gamma, double* g_beta, double* d_dgamma,
+              double* d_dbeta, double* exp_c) {
+  if (!c) return QAOA_EINVAL;
+  if (p < 1) return c->set_err(QAOA_EINVAL, "the gradient needs p >= 1");
+  std::vector<double> g(p), b(p), gg(p), gb(p);
+  for (int k = 0; k < p; ++k) {
+    b[k] = (1.0 - double(k) / p) * dbeta;
+    g[k] = double(k + 1) / p * dgamma;
+  }
+  const int rc = qaoa_grad_angles(c, p, g.data(), b.data(), gg.data(), gb.data(), exp_c);
+  if (rc) return rc;
+  // chain rule through gamma_k = (k+1)/p dgamma and beta_k = (1 - k/p) dbeta
+  double sg = 0.0, sb = 0.0;
+  for (int k = 0; k < p; ++k) {
+    sg += double(k + 1) / p * gg[k];
+    sb += (1.0 - double(k) / p) * gb[k];
+  }
+  if (g_gamma) memcpy(g_gamma, gg.data(), sizeof(double) * p);
+  if (g_beta) memcpy(g_beta, gb.data(), sizeof(double) * p);
+  if (d_dgamma) *d_dgamma = sg;
+  if (d_dbeta) *d_dbeta = sb;
+  return QAOA_OK;
 }
 
 }  // extern "C"

@@ -97,39 +97,7 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
       for (uint64_t ti = 0; ti < ntiles; ++ti) {
         const uint64_t gbase = ubase | scatter_bits(ti, sp.inner, sp.ninner);
         __syncthreads();  // previous tile finished with shared memory
-        if (sp.needs_c && !stream && warp == 0) {
-          // per-tile constants over the fixed (non-tile) bits F:
-          //   delta_j = sum_{g in F} w[pos_j][g] (1 - 2 f_g)
-          //   base    = C restricted to F + sum_j sum_{g in F} w[pos_j][g] f_g
-          uint64_t tbits = 0;
-          for (int j = 0; j < T; ++j) tbits |= 1ull << sp.pos[j];
-          int a = 0;
-          if (lane < T) {
-            const int pj = sp.pos[lane];
-            int d = 0;
-            for (int g = 0; g < n; ++g) {
-              if (tbits >> g & 1ull) continue;
-              const int wg = wsm[pj * n + g];
-              const int fg = int(gbase >> g & 1ull);
-              d += fg ? -wg : wg;
-              a += fg ? wg : 0;
-            }
-            tconst[lane] = d;
-          }
-          int cf = 0;
-          for (int g = lane; g < n; g += 32) {
-            if (tbits >> g & 1ull) continue;
-            const int fg = int(gbase >> g & 1ull);
-            for (int h = g + 1; h < n; ++h) {
-              if (tbits >> h & 1ull) continue;
-              if (fg != int(gbase >> h & 1ull)) cf += wsm[g * n + h];
-            }
-          }
-          int tot = a + cf;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-          if (lane == 0) tconst[16] = tot;
-        }
+        if (sp.needs_c && !stream && warp == 0) tile_consts<T>(sp.pos, gbase, wsm, n, tconst, lane);
         if (sp.needs_c && !stream) __syncthreads();
 
         for (int r = 0; r < sp.nrounds; ++r) {
@@ -185,36 +153,9 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
           if (rd.cost | rd.reduce) {
             // C(x) of register amplitude j: streamed from the diagonal, or
             // kappa + CP[j] + sum_{i: j_i = 1} e_i from the round's tables
-            int kappa = 0;
-            int e[R];
-            const int* cp = nullptr;
-            if (!stream) {
-              const int* tab = A.ctabs + rd.ctab;
-              const int QN = 1 << (T - R);
-              const int q = lane | (warp << 5);
-              kappa = tconst[16] + __ldg(tab + q);
-#pragma unroll
-              for (int i = 0; i < 5; ++i)
-                if (lane >> i & 1) kappa += tconst[rd.lane[i]];
-#pragma unroll
-              for (int i = 0; i < WB; ++i)
-                if (warp >> i & 1) kappa += tconst[rd.warp[i]];
-#pragma unroll
-              for (int i = 0; i < R; ++i) {
-                const int aj = __ldg(tab + QN + q * R + i);
-                kappa += aj;
-                e[i] = tconst[rd.reg[i]] + __ldg(tab + QN + QN * R + i) - 2 * aj;
-              }
-              cp = tab + QN + QN * R + R;
-            }
-            auto cv = [&](int j) {
-              if (stream) return __ldcg(A.diag + goff(j));
-              int c = kappa + __ldg(cp + j);
-#pragma unroll
-              for (int i = 0; i < R; ++i)
-                if (j >> i & 1) c += e[i];
-              return c;
-            };
+            RoundCost<R, WB> rc;
+            if (!stream) rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
+            auto cv = [&](int j) { return stream ? __ldcg(A.diag + goff(j)) : rc(j); };
             if (rd.cost) {
 #pragma unroll
               for (int j = 0; j < NA; ++j) {
