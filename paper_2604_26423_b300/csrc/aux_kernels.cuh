@@ -141,7 +141,7 @@ cost_block_kernel(int n, const int32_t* __restrict__ wmat, int32_t* __restrict__
 }
 
 // Small n (< 15): one CTA, one thread per x, direct sum over all index pairs.
-__global__ void cost_small_kernel(int n, const int32_t* __restrict__ wmat, int32_t* __restrict__ diag,
+static __global__ void cost_small_kernel(int n, const int32_t* __restrict__ wmat, int32_t* __restrict__ diag,
                                   Extreme* __restrict__ out) {
   __shared__ Extreme red[32];
   const unsigned long long N = 1ull << n;
@@ -167,7 +167,7 @@ __global__ void cost_small_kernel(int n, const int32_t* __restrict__ wmat, int32
 }
 
 // Merges per-block extremes (deterministic: ties go to the smallest index).
-__global__ void extreme_finalize_kernel(const Extreme* __restrict__ in, long long count, Extreme* __restrict__ out) {
+static __global__ void extreme_finalize_kernel(const Extreme* __restrict__ in, long long count, Extreme* __restrict__ out) {
   __shared__ Extreme red[32];
   Extreme ex = ext_empty();
   for (long long i = threadIdx.x; i < count; i += blockDim.x) ext_merge(ex, in[i]);
@@ -183,7 +183,7 @@ __global__ void extreme_finalize_kernel(const Extreme* __restrict__ in, long lon
 }
 
 // Sums `count` interleaved partials (stride `stride` doubles) in a fixed order.
-__global__ void sum_partials_kernel(const double* __restrict__ in, int count, int stride, double* __restrict__ out) {
+static __global__ void sum_partials_kernel(const double* __restrict__ in, int count, int stride, double* __restrict__ out) {
   const int c = threadIdx.x;
   if (c < stride) {
     double s = 0.0;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) block_sum_kernel(const typename Cx<Real>:
 
 // Exclusive scan of `count` doubles into pre[0..count] (pre[count] = total),
 // one CTA of 1024 threads, fixed order: each thread scans a contiguous chunk.
-__global__ void __launch_bounds__(1024) scan_kernel(const double* __restrict__ s, long long count,
+static __global__ void __launch_bounds__(1024) scan_kernel(const double* __restrict__ s, long long count,
                                                     double* __restrict__ pre) {
   __shared__ double part[1024];
   const long long chunk = (count + 1023) / 1024;

@@ -1,0 +1,128 @@
+"""Adjoint gradient on the GPU vs the oracle's exact parameter-shift gradient
+and central finite differences.
+
+Tolerances: complex128 adjoint vs oracle parameter shift (exact up to
+rounding): 1e-8 relative to the largest component; vs central differences of
+the GPU's own complex128 forward (h = 1e-5): 1e-6 relative. complex64 adjoint
+vs the complex128 adjoint: 2e-3 relative (single-precision state, gradient
+components are sums of ~2^n terms of mixed sign).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_26423_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+S = 0.1
+
+
+def sim(*a, **k):
+    from paper_2604_26423_b300.qaoa import Simulator
+    return Simulator(*a, **k)
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.max(np.abs(a - b)) / max(1e-30, np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("n,p,density", [(4, 1, 1.0), (7, 2, 0.6), (9, 3, 1.0), (10, 2, 0.5)])
+def test_grad_small_vs_param_shift(n, p, density):
+    u, v, w = inputs.complete_graph(n, 900 + n)
+    if density < 1:
+        keep = inputs.uniforms(901 + n, len(u)) < density
+        keep[0] = True
+        u, v, w = u[keep], v[keep], w[keep]
+    g, b = oracle.lr_schedule(p, 0.6, 0.3)
+    ps_g, ps_b = oracle.grad_param_shift(n, u, v, w, S, g, b)
+    with sim(n, u, v, w, S, "c128") as s:
+        out = s.grad_angles(g, b)
+    scale = max(np.max(np.abs(ps_g)), np.max(np.abs(ps_b)))
+    assert np.max(np.abs(out["g_gamma"] - ps_g)) <= 1e-8 * scale
+    assert np.max(np.abs(out["g_beta"] - ps_b)) <= 1e-8 * scale
+
+
+@pytest.mark.parametrize("n,p,prec", [(12, 2, "c128"), (13, 3, "c128"), (15, 2, "c128"), (16, 3, "c128"),
+                                      (17, 2, "c128"), (20, 3, "c128")])
+def test_grad_pass_kernel_vs_oracle_fd(n, p, prec):
+    u, v, w = inputs.complete_graph(n, 950 + n)
+    g, b = oracle.lr_schedule(p, 0.6, 0.3)
+    fd_g, fd_b = oracle.grad_fd(n, u, v, w, S, g, b)
+    with sim(n, u, v, w, S, prec) as s:
+        out = s.grad_angles(g, b)
+        ref = oracle.run(n, u, v, w, S, g, b)
+    scale = max(np.max(np.abs(fd_g)), np.max(np.abs(fd_b)))
+    assert np.max(np.abs(out["g_gamma"] - fd_g)) <= 1e-6 * scale
+    assert np.max(np.abs(out["g_beta"] - fd_b)) <= 1e-6 * scale
+    assert abs(out["exp_c"] - ref["exp_c"]) <= 1e-10 * ref["exp_c"]
+
+
+@pytest.mark.parametrize("n", [14, 18])
+def test_grad_wide_angles_and_stream_mode(n):
+    # |beta| > pi/4 takes the plain butterfly form; stream mode reads the diagonal
+    u, v, w = inputs.complete_graph(n, 960 + n)
+    gamma = np.array([0.4, -0.9, 1.7])
+    beta = np.array([1.1, 0.3, -2.4])
+    fd_g, fd_b = oracle.grad_fd(n, u, v, w, S, gamma, beta)
+    scale = max(np.max(np.abs(fd_g)), np.max(np.abs(fd_b)))
+    for mode in ("recompute", "stream"):
+        with sim(n, u, v, w, S, "c128", cost_mode=mode) as s:
+            out = s.grad_angles(gamma, beta)
+        assert np.max(np.abs(out["g_gamma"] - fd_g)) <= 1e-6 * scale, mode
+        assert np.max(np.abs(out["g_beta"] - fd_b)) <= 1e-6 * scale, mode
+
+
+@pytest.mark.parametrize("n,p", [(24, 5), (28, 5)])
+def test_grad_config_sizes_vs_gpu_fd(n, p):
+    # n = 24 and 28, K_n: the adjoint against central differences of the GPU's
+    # own complex128 forward (the oracle would take minutes per evaluation here)
+    u, v, w = inputs.complete_graph(n, 970 + n)
+    dg, db, h = 0.6, 0.3, 1e-5
+    with sim(n, u, v, w, S, "c128", with_grad=True) as s:
+        out = s.grad(p, dg, db)
+
+        def f(a, bb):
+            s.run(p, a, bb)
+            return s.expect()["exp_c"]
+
+        fdg = (f(dg + h, db) - f(dg - h, db)) / (2 * h)
+        fdb = (f(dg, db + h) - f(dg, db - h)) / (2 * h)
+    assert abs(out["d_dgamma"] - fdg) <= 1e-6 * max(abs(fdg), abs(fdb))
+    assert abs(out["d_dbeta"] - fdb) <= 1e-6 * max(abs(fdg), abs(fdb))
+
+
+@pytest.mark.parametrize("n,p", [(16, 3), (22, 5)])
+def test_grad_c64_vs_c128(n, p):
+    u, v, w = inputs.complete_graph(n, 980 + n)
+    outs = {}
+    for prec in ("c128", "c64"):
+        with sim(n, u, v, w, S, prec) as s:
+            outs[prec] = s.grad(p, 0.6, 0.3)
+    ref = np.concatenate([outs["c128"]["g_gamma"], outs["c128"]["g_beta"]])
+    got = np.concatenate([outs["c64"]["g_gamma"], outs["c64"]["g_beta"]])
+    assert rel(got, ref) <= 2e-3
+    assert abs(outs["c64"]["exp_c"] - outs["c128"]["exp_c"]) <= 2e-5 * outs["c128"]["exp_c"]
+
+
+def test_lr_chain_rule_matches_oracle():
+    n, p = 8, 3
+    u, v, w = inputs.complete_graph(n, 990)
+    gg, gb = oracle.grad_param_shift(n, u, v, w, S, *oracle.lr_schedule(p, 0.6, 0.3))
+    cdg, cdb = oracle.lr_chain(gg, gb)
+    with sim(n, u, v, w, S, "c128") as s:
+        out = s.grad(p, 0.6, 0.3)
+    assert abs(out["d_dgamma"] - cdg) <= 1e-8 * abs(cdg)
+    assert abs(out["d_dbeta"] - cdb) <= 1e-8 * abs(cdb)
+
+
+def test_state_after_grad_needs_rerun():
+    from paper_2604_26423_b300.qaoa import QaoaError
+    n = 14
+    u, v, w = inputs.complete_graph(n, 995)
+    with sim(n, u, v, w, S, "c64") as s:
+        s.grad(2, 0.6, 0.3)
+        with pytest.raises(QaoaError):
+            s.sample(8)
+        s.run(2, 0.6, 0.3)
+        assert len(s.sample(8)) == 8
