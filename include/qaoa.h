@@ -149,6 +149,33 @@ int qaoa_grad_angles(qaoa_ctx *ctx, int p, const double *gamma, const double *be
  */
 int qaoa_cost_diag(qaoa_ctx *ctx, int32_t *out_dev);
 
+/*
+ * Shots from a state vector without allocating any device memory. The paper
+ * has no counterpart: this serves callers that must not call cudaMalloc while
+ * they run (plugins whose host framework owns all device memory, serving
+ * loops with a fixed memory budget, code between stream-capture begin and end).
+ *   state_dev     2^n amplitudes on the current device (complex64 or
+ *                 complex128 per `precision`), read only.
+ *   uniforms_dev  `shots` doubles in [0, 1) on the device, or NULL to draw u_i
+ *                 from SplitMix64 stream `seed` exactly as qaoa_sample does.
+ *   out_dev       `shots` uint64 indices on the device (written).
+ * Same rule as qaoa_sample: shot i is the smallest x whose cumulative |psi|^2
+ * exceeds u_i * total. Blocks of 2^12 amplitudes are used while the number of
+ * blocks stays within QAOA_NOALLOC_MAX_BLOCKS, larger blocks beyond.
+ * Scratch: one file-scope device array of 2 * QAOA_NOALLOC_MAX_BLOCKS + 1
+ * doubles (about 1 MiB per GPU, held until exit), shared by every call. The
+ * first call on a device looks up the array's address, so make that first
+ * call before any stream capture. Calls whose GPU work overlaps (e.g. on two
+ * streams) race on the shared scratch. Work is queued on cuda_stream and not
+ * waited for. Errors: EINVAL (precision, n outside [1,
+ * QAOA_NOALLOC_MAX_QUBITS], shots < 0, NULL buffers), ECUDA.
+ */
+#define QAOA_NOALLOC_MAX_BLOCKS 65536
+#define QAOA_NOALLOC_MAX_QUBITS 34
+int qaoa_sample_state_noalloc(const void *state_dev, int n, int precision, int shots,
+                              const double *uniforms_dev, uint64_t seed, uint64_t *out_dev,
+                              void *cuda_stream);
+
 /* Device pointer of the context's state vector (interleaved re, im). */
 void *qaoa_state_ptr(qaoa_ctx *ctx);
 
