@@ -26,7 +26,6 @@
 #include "aux_kernels.cuh"
 #include "small_kernel.cuh"
 #include "adj_kernel.cuh"
-#include "pipe_kernel.cuh"
 
 using namespace qaoa;
 
@@ -296,33 +295,6 @@ int launch_pass(qaoa_ctx* c, const PassDev& pd, const PassArgs& pa, size_t smem,
   return QAOA_OK;
 }
 
-template <bool FAST>
-int launch_pipe(qaoa_ctx* c, const PassDev& pd, const PassArgs& pa, size_t smem, int grid) {
-  auto kern = fwd_pipe_kernel<kR, kWB, FAST>;
-  CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, 32 << kWB, smem, c->stream>>>(pd, pa);
-  if (c->prof_on) ++c->nlaunch;
-  CUDA_TRY(c, cudaGetLastError());
-  return QAOA_OK;
-}
-
-template <bool FAST>
-int pipe_blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
-  auto kern = fwd_pipe_kernel<kR, kWB, FAST>;
-  CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, 32 << kWB, smem));
-  if (*nb < 1) return c->set_err(QAOA_ECUDA, "pipelined kernel does not fit on an SM (smem %zu)", smem);
-  return QAOA_OK;
-}
-
-// complex64 passes use the cp.async double-buffered kernel unless
-// QAOA_FWD_KERNEL=plain selects the single-buffer kernel
-bool use_pipe(const qaoa_ctx* c) {
-  if (c->prec != QAOA_C64) return false;
-  const char* e = getenv("QAOA_FWD_KERNEL");
-  return !(e && strcmp(e, "plain") == 0);
-}
-
 template <typename Real, bool FAST>
 int blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
   auto kern = fwd_pass_kernel<Real, kR, kWB, FAST>;
@@ -396,9 +368,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   const bool stream = c->cost_mode == QAOA_COST_STREAM;
   const long long nc = c->c_hi - c->c_lo + 1;
   // shared memory: tile | weights + tile consts | phase table (if it fits)
-  const bool pipe = use_pipe(c);
-  const size_t base_smem =
-      (((size_t(pipe ? 2 : 1) << T) * ab + size_t(n * n + 32) * 4 + 15) & ~size_t(15));
+  const size_t base_smem = (((size_t(1) << T) * ab + size_t(n * n + 32) * 4 + 15) & ~size_t(15));
   const size_t with_tab = base_smem + size_t(nc) * ab;
   int dev = 0, max_smem = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
@@ -470,17 +440,13 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     pa.ctabs = (const int32_t*)c->d_ctabs.p;
     pa.phase_in_smem = tab_smem ? 1 : 0;
     int bps = 0;
-    if (pipe)
-      rc = fast ? pipe_blocks_per_sm<true>(c, smem, &bps) : pipe_blocks_per_sm<false>(c, smem, &bps);
-    else if (c->prec == QAOA_C128)
+    if (c->prec == QAOA_C128)
       rc = fast ? blocks_per_sm<double, true>(c, smem, &bps) : blocks_per_sm<double, false>(c, smem, &bps);
     else
       rc = fast ? blocks_per_sm<float, true>(c, smem, &bps) : blocks_per_sm<float, false>(c, smem, &bps);
     if (rc) return rc;
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
-    // the pipelined kernel takes super-tiles in pairs
-    const long long work = pipe ? (long long)((pd.n_units + 1) / 2) : (long long)pd.n_units;
-    const int grid = (int)std::min<long long>(want, work);
+    const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
     pa.partial = pp.reduce ? (double*)c->d_partial.p : nullptr;
     {
       // algorithmic HBM bytes: one read (none for the |+> pass) and one write of
@@ -490,9 +456,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
       if (stream)
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 0, bytes);
-      if (pipe)
-        rc = fast ? launch_pipe<true>(c, pd, pa, smem, grid) : launch_pipe<false>(c, pd, pa, smem, grid);
-      else if (c->prec == QAOA_C128)
+      if (c->prec == QAOA_C128)
         rc = fast ? launch_pass<double, true>(c, pd, pa, smem, grid) : launch_pass<double, false>(c, pd, pa, smem, grid);
       else
         rc = fast ? launch_pass<float, true>(c, pd, pa, smem, grid) : launch_pass<float, false>(c, pd, pa, smem, grid);
