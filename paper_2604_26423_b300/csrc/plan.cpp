@@ -3,8 +3,10 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <set>
 #include <sstream>
 #include <stdexcept>
+#include <tuple>
 
 namespace qaoa {
 namespace {
@@ -26,137 +28,113 @@ uint8_t regmask(const RoundPlan& rp, int R, uint32_t m) {
   return r;
 }
 
-// Fills lanes / warps / filler registers for a round whose essential register
-// bits are `x`. Global-facing rounds put lanes 0..3 on tile bits 0..3 (global
-// index bits 0..3 in every geometry) so each warp access covers whole
-// 128/256-byte runs; other rounds pick lanes 0..3 (0..2 for 16-byte
-// amplitudes) on bits of distinct swizzle classes so shared memory is
-// conflict-free.
-bool layout_round(const TileShape& sh, uint32_t x, bool global, RoundPlan& rp) {
+}  // namespace
+
+bool menu_layout(const TileShape& sh, int id, RoundPlan& rp) {
   const int T = sh.T(), R = sh.R, WB = sh.WB;
-  if (popc(x) > R) return false;
-  uint32_t used = x;
-  int lanes[5];
-  if (global) {
-    if (x & 0xFu) return false;
-    for (int i = 0; i < 4; ++i) lanes[i] = i;
-    used |= 0xFu;
-    int l4 = -1;
-    if (!(used >> 4 & 1u)) l4 = 4;
-    else
-      for (int b = 5; b < T; ++b)
-        if (!(used >> b & 1u)) { l4 = b; break; }
-    if (l4 < 0) return false;
-    lanes[4] = l4;
-    used |= 1u << l4;
-  } else {
-    const int ncls = sh.amp_bytes == 8 ? 4 : 3;
-    for (int c = 0; c < ncls; ++c) {
-      int pick = -1;
-      for (int b = 0; b < T; ++b)
-        if (!(used >> b & 1u) && swizzle_class(b, sh.amp_bytes) == c) { pick = b; break; }
-      if (pick < 0) return false;
-      lanes[c] = pick;
-      used |= 1u << pick;
-    }
-    for (int i = ncls; i < 5; ++i) {
-      int pick = -1;
-      for (int b = 0; b < T; ++b)
-        if (!(used >> b & 1u)) { pick = b; break; }
-      if (pick < 0) return false;
-      lanes[i] = pick;
-      used |= 1u << pick;
-    }
+  std::vector<int> regs, lanes, warps;
+  switch (id) {
+    case 0:
+      for (int i = 0; i < R; ++i) regs.push_back(5 + i);
+      for (int i = 0; i < 5; ++i) lanes.push_back(i);
+      for (int b = 5 + R; b < T; ++b) warps.push_back(b);
+      break;
+    case 1:
+      for (int i = 0; i < R; ++i) regs.push_back(T - R + i);
+      for (int i = 0; i < 5; ++i) lanes.push_back(i);
+      for (int b = 5; b < T - R; ++b) warps.push_back(b);
+      break;
+    case 2:
+      for (int i = 0; i < R; ++i) regs.push_back(i);
+      for (int i = 0; i < 5; ++i) lanes.push_back(R + i);
+      for (int b = R + 5; b < T; ++b) warps.push_back(b);
+      break;
+    case 3:
+      regs.push_back(4);
+      for (int i = 1; i < R; ++i) regs.push_back(T - R + i);
+      for (int i = 0; i < 4; ++i) lanes.push_back(i);
+      lanes.push_back(T - R);
+      for (int b = 5; b < T - R; ++b) warps.push_back(b);
+      break;
+    default:
+      return false;
   }
-  // registers: essential bits first (ascending), then fillers
-  std::vector<int> regs = bits_of(x);
-  for (int b = T - 1; b >= 0 && (int)regs.size() < R; --b)
-    if (!(used >> b & 1u)) { regs.push_back(b); used |= 1u << b; }
-  if ((int)regs.size() != R) return false;
-  std::sort(regs.begin(), regs.end());
-  std::vector<int> warps;
-  for (int b = 0; b < T; ++b)
-    if (!(used >> b & 1u)) warps.push_back(b);
-  if ((int)warps.size() != WB) return false;
-  for (int i = 0; i < R; ++i) rp.reg[i] = int8_t(regs[i]);
-  for (int i = R; i < 5; ++i) rp.reg[i] = 0;
+  if ((int)regs.size() != R || (int)warps.size() != WB || (int)lanes.size() != 5) return false;
+  for (int i = 0; i < 5; ++i) rp.reg[i] = i < R ? int8_t(regs[i]) : 0;
   for (int i = 0; i < 5; ++i) rp.lane[i] = int8_t(lanes[i]);
-  for (int i = 0; i < WB; ++i) rp.warp[i] = int8_t(warps[i]);
-  for (int i = WB; i < 4; ++i) rp.warp[i] = 0;
-  rp.global_facing = global;
+  for (int i = 0; i < 4; ++i) rp.warp[i] = i < WB ? int8_t(warps[i]) : 0;
+  rp.layout = uint8_t(id);
+  rp.global_facing = id != 2;
   return true;
 }
 
-// Picks up to R bits from `cand`, bits 0..3 first, then the rest ascending.
-uint32_t pick_bits(uint32_t cand, int R, uint32_t already) {
-  uint32_t x = already;
-  for (int b : bits_of(cand & 0xFu))
-    if (popc(x) < R) x |= 1u << b;
-  for (int b : bits_of(cand & ~0xFu))
-    if (popc(x) < R) x |= 1u << b;
-  return x;
-}
-
-}  // namespace
-
 std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool cost, uint32_t b_bits,
                                    bool reduce, uint8_t first_src, bool lam) {
+  // Breadth-first search over (bits left for mixer A, bits left for mixer B,
+  // cost applied) for the fewest rounds drawn from the layout menu. A round
+  // applies mixer A on its register bits; once A is complete it applies the
+  // cost phase (if pending) and mixer B on its register bits. The last round
+  // must be global-facing (it stores the tile); so must the first when it
+  // loads from global memory. Without a cost phase here, mixer B continues a
+  // layer whose cost phase was applied in an earlier sub-pass.
   const int R = sh.R;
-  std::vector<RoundPlan> out;
-  uint32_t remA = a_bits, remB = b_bits;
-  // without a cost phase here, mixer B continues a layer whose cost phase was
-  // applied in an earlier sub-pass
-  bool cost_done = !cost;
-  bool first = true;
-  auto apply = [&](RoundPlan& rp, uint32_t x) {
-    rp.mixA = regmask(rp, R, x & remA);
-    remA &= ~x;
-    if (remA == 0) {
-      if (!cost_done) { rp.cost = 1; cost_done = true; }
-      rp.mixB = regmask(rp, R, x & remB);
-      remB &= ~x;
+  struct Node { uint32_t remA, remB; bool cost_done; int parent; int layout; uint8_t mA, mB, c; };
+  std::vector<Node> nodes;
+  nodes.push_back({a_bits, b_bits, !cost, -1, -1, 0, 0, 0});
+  std::set<std::tuple<uint32_t, uint32_t, bool>> seen;
+  size_t head = 0;
+  for (int depth = 0; depth < kMaxRounds; ++depth) {
+    const size_t level_end = nodes.size();
+    for (size_t ni = head; ni < level_end; ++ni) {
+      for (int id = 0; id < kNumLayouts; ++id) {
+        RoundPlan rp;
+        if (!menu_layout(sh, id, rp)) continue;
+        if (depth == 0 && first_src == SRC_GLOBAL && !rp.global_facing) continue;
+        Node nd = nodes[ni];
+        uint32_t x = 0;
+        for (int i = 0; i < R; ++i) x |= 1u << rp.reg[i];
+        nd.mA = regmask(rp, R, x & nd.remA);
+        nd.remA &= ~x;
+        nd.c = 0;
+        nd.mB = 0;
+        if (nd.remA == 0) {
+          if (!nd.cost_done) { nd.c = 1; nd.cost_done = true; }
+          nd.mB = regmask(rp, R, x & nd.remB);
+          nd.remB &= ~x;
+        }
+        nd.parent = (int)ni;
+        nd.layout = id;
+        const bool done = nd.remA == 0 && nd.remB == 0 && nd.cost_done;
+        if (done && rp.global_facing) {
+          nodes.push_back(nd);
+          std::vector<int> chain;
+          for (int k = (int)nodes.size() - 1; nodes[k].parent >= 0; k = nodes[k].parent) chain.push_back(k);
+          std::reverse(chain.begin(), chain.end());
+          std::vector<RoundPlan> out;
+          for (size_t r = 0; r < chain.size(); ++r) {
+            const Node& q = nodes[chain[r]];
+            RoundPlan rr;
+            menu_layout(sh, q.layout, rr);
+            rr.mixA = q.mA;
+            rr.cost = q.c;
+            rr.mixB = q.mB;
+            rr.src = r == 0 ? first_src : SRC_SMEM;
+            rr.dst = r + 1 == chain.size() ? DST_GLOBAL : DST_SMEM;
+            rr.reduce = (reduce && r + 1 == chain.size()) ? 1 : 0;
+            rr.lam = (lam && r == 0) ? 1 : 0;
+            out.push_back(rr);
+          }
+          return out;
+        }
+        auto key = std::make_tuple(nd.remA, nd.remB, nd.cost_done);
+        if (seen.count(key)) continue;
+        seen.insert(key);
+        nodes.push_back(nd);
+      }
     }
-  };
-  for (int guard = 0; guard < kMaxRounds; ++guard) {
-    RoundPlan rp;
-    rp.src = first ? first_src : SRC_SMEM;
-    const uint32_t need = remA | remB;
-    // can everything left be done in one global-facing round (load/store)?
-    if (popc(need) <= R && !(need & 0xFu)) {
-      if (!layout_round(sh, need, true, rp)) throw std::runtime_error("plan_rounds: final layout");
-      apply(rp, need);
-      rp.reduce = reduce ? 1 : 0;
-      rp.lam = (lam && out.empty()) ? 1 : 0;
-      rp.dst = DST_GLOBAL;
-      out.push_back(rp);
-      return out;
-    }
-    uint32_t x;
-    bool global = false;
-    if (rp.src == SRC_GLOBAL) {
-      // coalesced load round: registers may only hold bits >= 4
-      global = true;
-      uint32_t cand = remA ? remA : remB;
-      cand &= ~0xFu;
-      x = 0;
-      for (int b : bits_of(cand & ~0x1Fu))
-        if (popc(x) < R) x |= 1u << b;
-      if (popc(x) < R && (cand >> 4 & 1u)) x |= 1u << 4;
-      // if A finishes here, B bits (>= 4) may ride along
-      if (remA && (remA & ~x) == 0) x = x | (pick_bits(remB & ~0xFu, R, x) & ~x);
-    } else {
-      uint32_t cand = remA ? remA : remB;
-      x = pick_bits(cand, R, 0);
-      if (remA && (remA & ~x) == 0) x = pick_bits(remB, R, x);
-    }
-    if (!layout_round(sh, x, global, rp)) throw std::runtime_error("plan_rounds: layout");
-    apply(rp, x);
-    rp.lam = (lam && out.empty()) ? 1 : 0;
-    rp.dst = DST_SMEM;
-    out.push_back(rp);
-    first = false;
+    head = level_end;
   }
-  throw std::runtime_error("plan_rounds: too many rounds");
+  throw std::runtime_error("plan_rounds: no round sequence from the layout menu");
 }
 
 std::string validate_rounds(const TileShape& sh, const std::vector<RoundPlan>& rounds, uint32_t a_bits,

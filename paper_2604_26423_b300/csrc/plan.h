@@ -50,6 +50,7 @@ struct RoundPlan {
   uint8_t reduce = 0; // then accumulate norm and <C> (final pass)
   uint8_t lam = 0;    // adjoint: load psi only and set lambda = C(x) psi first
   uint8_t src = SRC_SMEM, dst = DST_SMEM;
+  uint8_t layout = 0; // menu layout id (see menu_layout)
   bool global_facing = false;
 };
 
@@ -109,6 +110,18 @@ std::vector<RoundPlan> plan_rounds(const TileShape& shape, uint32_t a_bits, bool
 std::string validate(const Plan& plan);
 std::string validate_rounds(const TileShape& shape, const std::vector<RoundPlan>& rounds,
                             uint32_t a_bits, bool cost, uint32_t b_bits, bool reduce);
+
+// The fixed menu of round layouts for a tile shape (T = R + 5 + WB):
+//   0 "G1": registers on bits 5..R+4, lanes on 0..4, warps on the rest
+//   1 "G2": registers on the top R bits, lanes on 0..4, warps on the rest
+//   2 "S":  registers on bits 0..R-1, lanes on R..R+4, warps on the rest
+//   3 "G3": registers on bit 4 and the top R-1 bits, lanes on 0..3 and T-R
+// G1, G2 and G3 keep lanes 0..3 on tile bits 0..3 (coalesced global access);
+// all four keep lanes 0..3 (0..2 for 16-byte amplitudes) on bits of distinct
+// residue classes, so shared-memory accesses are conflict-free. Kernels
+// instantiate one code path per menu entry with compile-time offsets.
+constexpr int kNumLayouts = 4;
+bool menu_layout(const TileShape& sh, int id, RoundPlan& rp);
 
 // Residue class of tile bit j in the shared-memory swizzle: rows of 16 c64 or 8
 // c128 amplitudes, XOR-swizzled so that lanes on bits of distinct classes never
