@@ -15,6 +15,7 @@
 // is one HBM pass reading and writing both vectors.
 #pragma once
 #include "device.cuh"
+#include "pass_kernel.cuh"
 
 namespace qaoa {
 
@@ -82,34 +83,128 @@ __device__ __forceinline__ Real pow_bits(Real c, uint8_t mask) {
   return r;
 }
 
-// Shared memory: psi tile[2^T] | lambda tile[2^T] | wmat[n*n] | tile consts | phase table
+template <typename Real, int R, int WB, int L, bool FAST>
+__device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, const SubDev& sp, const RoundDev& rd,
+                                          typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, uint64_t gbase,
+                                          const int* tconst, const typename Cx<Real>::T* phase, int lane, int warp,
+                                          double& gA, double& gC, double& gB) {
+  using C2 = typename Cx<Real>::T;
+  using Y = Lay<R, WB, L>;
+  constexpr int NA = 1 << R;
+  constexpr int AB = sizeof(C2);
+  C2* gpsi = reinterpret_cast<C2*>(A.psi);
+  C2* glam = reinterpret_cast<C2*>(A.lam);
+  const bool stream = A.diag != nullptr;
+  const RoundGeo<R, WB, L, AB> geo(sp, gbase, lane, warp);
+  const bool need_c = rd.cost || rd.lam;
+  RoundCost<R, WB> rcost;
+  if (need_c && !stream) {
+    int8_t lb[5], wb[WB], rb[R];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) lb[i] = int8_t(Y::lane(i));
+#pragma unroll
+    for (int i = 0; i < WB; ++i) wb[i] = int8_t(Y::warp(i));
+#pragma unroll
+    for (int i = 0; i < R; ++i) rb[i] = int8_t(Y::reg(i));
+    rcost.setup(A.ctabs + rd.ctab, tconst, lb, wb, rb, lane, warp);
+  }
+  auto for_costs = [&](auto&& f) {
+    if (stream) {
+      gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { f(j, __ldcg(A.diag + g)); });
+    } else {
+      int lin = rcost.kappa;
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        const int j = k ^ (k >> 1);
+        if (k) {
+          const int b = ctz_c(k);
+          lin += (j >> b & 1) ? rcost.e[b] : -rcost.e[b];
+        }
+        f(j, lin + __ldg(rcost.cp + j));
+      }
+    }
+  };
+
+  C2 v[NA], l[NA];
+  if (rd.src == SRC_GLOBAL_D) {
+    gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { v[j] = __ldcg(gpsi + g); });
+    if (rd.lam) {
+      // lambda = C(x) psi (the operator whose expectation is differentiated)
+      for_costs([&](int j, int c) {
+        l[j].x = Real(c) * v[j].x;
+        l[j].y = Real(c) * v[j].y;
+      });
+    } else {
+      gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { l[j] = __ldcg(glam + g); });
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const uint32_t o = geo.sbase + padi<AB>(Y::toff(j));
+      v[j] = tv[o];
+      l[j] = tl[o];
+    }
+  }
+
+  Real ga = 0, gc = 0, gbv = 0;
+  inverse_mixer<R>(v, l, rd.mixA, Real(P.tauA), Real(P.alphaA), FAST, pow_bits(Real(P.cA), rd.mixA), ga);
+  if (rd.cost) {
+    for_costs([&](int j, int c) {
+      const Real h = Real(P.wsum - 2 * c);
+      gc = fma(fma(l[j].x, v[j].y, -l[j].y * v[j].x), h, gc);
+      const C2 ph = phase[min(max(c - P.c_lo, 0), P.ncost - 1)];
+      // multiply both vectors by the conjugate phase (inverse cost unitary)
+      const Real vr = v[j].x, vi = v[j].y, lr = l[j].x, li = l[j].y;
+      v[j].x = vr * ph.x + vi * ph.y;
+      v[j].y = vi * ph.x - vr * ph.y;
+      l[j].x = lr * ph.x + li * ph.y;
+      l[j].y = li * ph.x - lr * ph.y;
+    });
+  }
+  inverse_mixer<R>(v, l, rd.mixB, Real(P.tauB), Real(P.alphaB), FAST, pow_bits(Real(P.cB), rd.mixB), gbv);
+  gA += double(ga);
+  gC += double(gc);
+  gB += double(gbv);
+
+  if (rd.dst == DST_GLOBAL_D) {
+    if (sp.store) {
+      gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) {
+        __stcg(gpsi + g, v[j]);
+        __stcg(glam + g, l[j]);
+      });
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const uint32_t o = geo.sbase + padi<AB>(Y::toff(j));
+      tv[o] = v[j];
+      tl[o] = l[j];
+    }
+  }
+}
+
+// Shared memory: psi tile (padded 2^T) | lambda tile | tile consts | phase table
 template <typename Real, int R, int WB, bool FAST>
 __global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
 adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
-  constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
+  constexpr uint32_t TILE = padded_size<AB>(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tv = reinterpret_cast<C2*>(smem_raw);
-  C2* tl = tv + (1 << T);
-  int* wsm = reinterpret_cast<int*>(tl + (1 << T));
-  int* tconst = wsm + P.n * P.n;
-  C2* ptab = reinterpret_cast<C2*>(smem_raw +
-                                   (((size_t(2) << T) * AB + size_t(P.n * P.n + 32) * 4 + 15) & ~size_t(15)));
+  C2* tl = tv + TILE;
+  int* tconst = reinterpret_cast<int*>(tl + TILE);
+  C2* ptab = reinterpret_cast<C2*>(smem_raw + ((size_t(2 * TILE) * AB + 32 * 4 + 15) & ~size_t(15)));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = P.n;
-  for (int i = tid; i < n * n; i += NT) wsm[i] = A.wmat[i];
   const C2* phase = reinterpret_cast<const C2*>(A.phase);
   if (A.phase_in_smem && A.phase) {
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
     phase = ptab;
   }
-  C2* gpsi = reinterpret_cast<C2*>(A.psi);
-  C2* glam = reinterpret_cast<C2*>(A.lam);
   const bool stream = A.diag != nullptr;
-  const Real tauA = Real(P.tauA), alphaA = Real(P.alphaA), tauB = Real(P.tauB), alphaB = Real(P.alphaB);
   double gA = 0.0, gC = 0.0, gB = 0.0;
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
@@ -120,100 +215,18 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
       for (uint64_t ti = 0; ti < ntiles; ++ti) {
         const uint64_t gbase = ubase | scatter_bits(ti, sp.inner, sp.ninner);
         __syncthreads();
-        if (sp.needs_c && !stream && warp == 0) tile_consts<T>(sp.pos, gbase, wsm, n, tconst, lane);
-        if (sp.needs_c && !stream) __syncthreads();
+        if (sp.needs_c && !stream) {
+          if (warp == 0) tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane);
+          __syncthreads();
+        }
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          uint32_t tb = 0;
-          uint64_t gb = gbase;
-#pragma unroll
-          for (int i = 0; i < 5; ++i)
-            if (lane >> i & 1) { tb |= 1u << rd.lane[i]; gb |= 1ull << sp.pos[rd.lane[i]]; }
-#pragma unroll
-          for (int i = 0; i < WB; ++i)
-            if (warp >> i & 1) { tb |= 1u << rd.warp[i]; gb |= 1ull << sp.pos[rd.warp[i]]; }
-          uint32_t sstr[R];
-          uint64_t gstr[R];
-#pragma unroll
-          for (int i = 0; i < R; ++i) {
-            sstr[i] = swz<AB>(1u << rd.reg[i]);
-            gstr[i] = 1ull << sp.pos[rd.reg[i]];
-          }
-          const uint32_t sb0 = swz<AB>(tb);
-          auto soff = [&](int j) {
-            uint32_t o = sb0;
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-              if (j >> i & 1) o ^= sstr[i];
-            return o;
-          };
-          auto goff = [&](int j) {
-            uint64_t o = gb;
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-              if (j >> i & 1) o |= gstr[i];
-            return o;
-          };
-          const bool need_c = rd.cost || rd.lam;
-          RoundCost<R, WB> rcost;
-          if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
-          auto cv = [&](int j) { return stream ? __ldcg(A.diag + goff(j)) : rcost(j); };
-
-          C2 v[NA], l[NA];
-          if (rd.src == SRC_GLOBAL_D) {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) v[j] = __ldcg(gpsi + goff(j));
-            if (rd.lam) {
-              // lambda = C(x) psi (the operator whose expectation is differentiated)
-#pragma unroll
-              for (int j = 0; j < NA; ++j) {
-                const Real c = Real(cv(j));
-                l[j].x = c * v[j].x;
-                l[j].y = c * v[j].y;
-              }
-            } else {
-#pragma unroll
-              for (int j = 0; j < NA; ++j) l[j] = __ldcg(glam + goff(j));
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) { v[j] = tv[soff(j)]; l[j] = tl[soff(j)]; }
-          }
-
-          Real ga = 0, gc = 0, gbv = 0;
-          inverse_mixer<R>(v, l, rd.mixA, tauA, alphaA, FAST, pow_bits(Real(P.cA), rd.mixA), ga);
-          if (rd.cost) {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) {
-              const int c = cv(j);
-              const Real h = Real(P.wsum - 2 * c);
-              gc = fma(fma(l[j].x, v[j].y, -l[j].y * v[j].x), h, gc);
-              const C2 ph = phase[min(max(c - P.c_lo, 0), P.ncost - 1)];
-              // multiply both vectors by the conjugate phase (inverse cost unitary)
-              const Real vr = v[j].x, vi = v[j].y, lr = l[j].x, li = l[j].y;
-              v[j].x = vr * ph.x + vi * ph.y;
-              v[j].y = vi * ph.x - vr * ph.y;
-              l[j].x = lr * ph.x + li * ph.y;
-              l[j].y = li * ph.x - lr * ph.y;
-            }
-          }
-          inverse_mixer<R>(v, l, rd.mixB, tauB, alphaB, FAST, pow_bits(Real(P.cB), rd.mixB), gbv);
-          gA += double(ga);
-          gC += double(gc);
-          gB += double(gbv);
-
-          if (rd.dst == DST_GLOBAL_D) {
-            if (sp.store) {
-#pragma unroll
-              for (int j = 0; j < NA; ++j) {
-                __stcg(gpsi + goff(j), v[j]);
-                __stcg(glam + goff(j), l[j]);
-              }
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) { tv[soff(j)] = v[j]; tl[soff(j)] = l[j]; }
+          switch (rd.layout) {
+            case 0: adj_round<Real, R, WB, 0, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB); break;
+            case 1: adj_round<Real, R, WB, 1, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB); break;
+            case 2: adj_round<Real, R, WB, 2, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB); break;
+            default: adj_round<Real, R, WB, 3, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB); break;
           }
         }
       }

@@ -220,7 +220,7 @@ void to_round_dev(const RoundPlan& rp, RoundDev& rd) {
   rd.src = rp.src;
   rd.dst = rp.dst;
   rd.lam = rp.lam;
-  rd.pad = 0;
+  rd.layout = rp.layout;
   rd.ctab = -1;
 }
 
@@ -368,7 +368,8 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   const bool stream = c->cost_mode == QAOA_COST_STREAM;
   const long long nc = c->c_hi - c->c_lo + 1;
   // shared memory: tile | weights + tile consts | phase table (if it fits)
-  const size_t base_smem = (((size_t(1) << T) * ab + size_t(n * n + 32) * 4 + 15) & ~size_t(15));
+  const size_t tile_amps = ab == 8 ? padded_size<8>(T) : padded_size<16>(T);
+  const size_t base_smem = ((tile_amps * ab + 32 * 4 + 15) & ~size_t(15));
   const size_t with_tab = base_smem + size_t(nc) * ab;
   int dev = 0, max_smem = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
@@ -422,6 +423,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
       sd.scale = fast ? pow(cos(ba), sp.nA) * pow(cos(bb), sp.nB) : 1.0;
       for (int r = 0; r < sd.nrounds; ++r) {
         to_round_dev(sp.rounds[r], sd.rd[r]);
+        sd.rd[r].layout = sp.rounds[r].layout;
         if ((sd.rd[r].cost || sd.rd[r].reduce) && !stream) sd.rd[r].ctab = table_offset(c, sh, sd.pos, sd.rd[r]);
       }
     }
@@ -575,7 +577,8 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   }
   const bool stream = c->cost_mode == QAOA_COST_STREAM;
   const long long nc = c->c_hi - c->c_lo + 1;
-  const size_t base_smem = (((size_t(2) << T) * ab + size_t(n * n + 32) * 4 + 15) & ~size_t(15));
+  const size_t tile_amps = ab == 8 ? padded_size<8>(T) : padded_size<16>(T);
+  const size_t base_smem = ((2 * tile_amps * ab + 32 * 4 + 15) & ~size_t(15));
   const size_t with_tab = base_smem + size_t(nc) * ab;
   int dev = 0, max_smem = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
@@ -626,6 +629,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
       sd.scale = 1.0;
       for (int r = 0; r < sd.nrounds; ++r) {
         to_round_dev(sp.rounds[r], sd.rd[r]);
+        sd.rd[r].layout = sp.rounds[r].layout;
         if ((sd.rd[r].cost || sd.rd[r].lam) && !stream) sd.rd[r].ctab = table_offset(c, sh, sd.pos, sd.rd[r]);
       }
     }

@@ -14,8 +14,8 @@ constexpr int kMaxBits = 40;
 struct RoundDev {
   int8_t reg[5], lane[5], warp[4];
   uint8_t mixA, cost, mixB, reduce, src, dst;
-  uint8_t lam;   // adjoint: load psi only and create lambda = C(x) psi first
-  uint8_t pad;
+  uint8_t lam;     // adjoint: load psi only and create lambda = C(x) psi first
+  uint8_t layout;  // menu layout id (plan.h, menu_layout)
   int32_t ctab;  // offset (in ints) of this round's cost tables, -1 if none
 };
 
@@ -55,16 +55,21 @@ template <typename Real> struct Cx;
 template <> struct Cx<float> { using T = float2; };
 template <> struct Cx<double> { using T = double2; };
 
-// Shared-memory XOR swizzle over tile indices. For 8-byte amplitudes the
-// bank group of a half-warp access is (index mod 16); bits 4k..4k+3 are folded
-// onto bits 0..3, so tile bit j lands in class j mod 4. For 16-byte
-// amplitudes a quarter-warp covers 8 slots; bits are folded in groups of 3,
-// giving class j mod 3. The map is linear over XOR, so
-// swz(a | b) = swz(a) ^ swz(b) for disjoint a, b.
-template <int AMP_BYTES>
-__device__ __forceinline__ uint32_t swz(uint32_t t) {
-  if (AMP_BYTES == 8) return t ^ (((t >> 4) ^ (t >> 8) ^ (t >> 12)) & 15u);
-  return t ^ (((t >> 3) ^ (t >> 6) ^ (t >> 9) ^ (t >> 12)) & 7u);
+// Padded shared-memory slot of tile index t. For 8-byte amplitudes a
+// half-warp access is conflict-free when the 16 slots are distinct mod 16;
+// padi adds t >> 4 and t >> 8, so tile bit j shifts the slot by 2^(j mod 4)
+// mod 16 for j < 12. For 16-byte amplitudes a quarter-warp covers 8 slots and
+// the fold is by 3 bits (class j mod 3). Lanes 0..3 (0..2) on bits of distinct
+// classes therefore never share a bank. padi is additive over disjoint bit
+// sets (no carries), so padi(a | b) = padi(a) + padi(b): register offsets are
+// compile-time constants.
+template <int AB>
+__host__ __device__ constexpr uint32_t padi(uint32_t t) {
+  return AB == 8 ? t + (t >> 4) + (t >> 8) : t + (t >> 3) + (t >> 6) + (t >> 9) + (t >> 12);
+}
+template <int AB>
+__host__ __device__ constexpr uint32_t padded_size(int T) {
+  return padi<AB>((1u << T) - 1) + 1;
 }
 
 // Per-tile constants over the fixed (non-tile) index bits F, computed by one
@@ -73,8 +78,8 @@ __device__ __forceinline__ uint32_t swz(uint32_t t) {
 //   base    = C restricted to F + sum_j sum_{g in F} w[pos_j][g] f_g
 // so that C(x) = base + sum_j t_j delta_j + C_tile(t) for tile index t.
 template <int T>
-__device__ __forceinline__ void tile_consts(const int8_t* pos, uint64_t gbase, const int* wsm, int n, int* tconst,
-                                            int lane) {
+__device__ __forceinline__ void tile_consts(const int8_t* pos, uint64_t gbase, const int* __restrict__ wsm, int n,
+                                            int* tconst, int lane) {
   uint64_t tbits = 0;
   for (int j = 0; j < T; ++j) tbits |= 1ull << pos[j];
   int a = 0;

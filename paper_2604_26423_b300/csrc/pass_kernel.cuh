@@ -5,13 +5,18 @@
 // tiles global -> registers -> (shared memory -> registers)* -> global, and in
 // each round applies, on the thread's 2^R register amplitudes:
 //   mixer of layer a   exp(+i beta_a X_q) on the round's target bits (Eq. UB)
-//   cost phase         exp(-i gamma_b s h(x)), h = W - 2 C(x)  (Eqs. H_C, UC)
+//   cost phase         exp(-i gamma_c s h(x)), h = W - 2 C(x)  (Eqs. H_C, UC)
 //   mixer of layer b   on the round's target bits
 //   reduction          |psi_x|^2 and |psi_x|^2 C(x) (final pass)
 // The mixer rotation [[c, i s], [i s, c]] is applied as c * [[1, i t], [i t, 1]]
 // (t = tan beta) so each butterfly costs four FMAs; the accumulated factor c^k
 // is folded into one multiply before the store ("fast" form). Angles with
 // |tan beta| > 1 use the plain form.
+//
+// Rounds are compiled once per entry of the planner's layout menu
+// (menu_layout in plan.h), so register bit positions are constants: shared
+// memory offsets become immediates through the additive padded layout `padi`,
+// and global offsets are walked in Gray-code order (one XOR per amplitude).
 #pragma once
 #include "device.cuh"
 
@@ -23,12 +28,36 @@ enum : uint8_t { DST_SMEM_D = 0, DST_GLOBAL_D = 1 };
 struct PassArgs {
   void* state;            // 2^n amplitudes, interleaved (re, im)
   const int32_t* diag;    // int32 C(x) for all x (stream mode) or nullptr
-  const void* phase;      // phase table of layer b: ncost complex entries
+  const void* phase;      // phase table of the cost layer: ncost complex entries
   const int32_t* wmat;    // n x n symmetric integer weights
   const int32_t* ctabs;   // per-round cost tables (recompute mode)
   double* partial;        // per-CTA [norm, <C>] partial sums (final pass)
   int phase_in_smem;      // copy the phase table into shared memory
 };
+
+// Compile-time copy of the planner's layout menu (plan.cpp, menu_layout).
+template <int R, int WB, int L>
+struct Lay {
+  static constexpr int T = R + 5 + WB;
+  __host__ __device__ static constexpr int reg(int i) {
+    return L == 0 ? 5 + i : L == 1 ? T - R + i : L == 2 ? i : (i == 0 ? 4 : T - R + i);
+  }
+  __host__ __device__ static constexpr int lane(int i) { return L == 2 ? R + i : (L == 3 && i == 4) ? T - R : i; }
+  __host__ __device__ static constexpr int warp(int i) { return L == 0 ? 5 + R + i : L == 2 ? R + 5 + i : 5 + i; }
+  // tile-index offset of register amplitude j
+  __host__ __device__ static constexpr uint32_t toff(int j) {
+    uint32_t o = 0;
+    for (int i = 0; i < R; ++i)
+      if (j >> i & 1) o |= 1u << reg(i);
+    return o;
+  }
+};
+
+__host__ __device__ constexpr int ctz_c(int k) {
+  int b = 0;
+  while (!(k >> b & 1)) ++b;
+  return b;
+}
 
 template <typename Real>
 __device__ __forceinline__ void bfly(typename Cx<Real>::T& a, typename Cx<Real>::T& b, Real tau, Real alpha,
@@ -59,34 +88,161 @@ __device__ __forceinline__ void apply_mixer(V* v, uint8_t mask, Real tau, Real a
   }
 }
 
+// Per-round thread geometry: the tile index of the thread's amplitude 0, its
+// padded shared-memory slot, its global index and the global strides of the
+// register bits.
+template <int R, int WB, int L, int AB>
+struct RoundGeo {
+  uint32_t tb, sbase;
+  uint64_t gb;
+  uint64_t gstr[R];
+  __device__ __forceinline__ RoundGeo(const SubDev& sp, uint64_t gbase, int lane, int warp) {
+    using Y = Lay<R, WB, L>;
+    tb = 0;
+    gb = gbase;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (lane >> i & 1) { tb |= 1u << Y::lane(i); gb |= 1ull << sp.pos[Y::lane(i)]; }
+#pragma unroll
+    for (int i = 0; i < WB; ++i)
+      if (warp >> i & 1) { tb |= 1u << Y::warp(i); gb |= 1ull << sp.pos[Y::warp(i)]; }
+#pragma unroll
+    for (int i = 0; i < R; ++i) gstr[i] = 1ull << sp.pos[Y::reg(i)];
+    sbase = padi<AB>(tb);
+  }
+};
+
+// Calls f(j, global index of register amplitude j) for j in Gray-code order.
+template <int R, typename F>
+__device__ __forceinline__ void gray_walk(uint64_t g0, const uint64_t* gstr, F&& f) {
+  uint64_t g = g0;
+#pragma unroll
+  for (int k = 0; k < (1 << R); ++k) {
+    if (k) g ^= gstr[ctz_c(k)];
+    f(k ^ (k >> 1), g);
+  }
+}
+
+template <typename Real, int R, int WB, int L, bool FAST>
+__device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, const SubDev& sp, const RoundDev& rd,
+                                          typename Cx<Real>::T* tile, uint64_t gbase, const int* tconst,
+                                          const typename Cx<Real>::T* phase, int lane, int warp, double& accN,
+                                          double& accC) {
+  using C2 = typename Cx<Real>::T;
+  using Y = Lay<R, WB, L>;
+  constexpr int NA = 1 << R;
+  constexpr int AB = sizeof(C2);
+  C2* gstate = reinterpret_cast<C2*>(A.state);
+  const bool stream = A.diag != nullptr;
+  const RoundGeo<R, WB, L, AB> geo(sp, gbase, lane, warp);
+  C2 v[NA];
+  if (rd.src == SRC_INIT_D) {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
+  } else if (rd.src == SRC_GLOBAL_D) {
+    gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { v[j] = __ldcg(gstate + g); });
+  } else {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) v[j] = tile[geo.sbase + padi<AB>(Y::toff(j))];
+  }
+
+  apply_mixer<R>(v, rd.mixA, Real(P.tauA), Real(P.alphaA), FAST);
+
+  if (rd.cost | rd.reduce) {
+    // C(x) of register amplitude j: streamed from the diagonal, or
+    // kappa + CP[j] + sum_{i: j_i = 1} e_i from the round's tables
+    RoundCost<R, WB> rc;
+    if (!stream) {
+      int8_t lb[5], wb[WB], rb[R];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) lb[i] = int8_t(Y::lane(i));
+#pragma unroll
+      for (int i = 0; i < WB; ++i) wb[i] = int8_t(Y::warp(i));
+#pragma unroll
+      for (int i = 0; i < R; ++i) rb[i] = int8_t(Y::reg(i));
+      rc.setup(A.ctabs + rd.ctab, tconst, lb, wb, rb, lane, warp);
+    }
+    auto for_costs = [&](auto&& f) {
+      if (stream) {
+        gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { f(j, __ldcg(A.diag + g)); });
+      } else {
+        int lin = rc.kappa;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          const int j = k ^ (k >> 1);
+          if (k) {
+            const int b = ctz_c(k);
+            lin += (j >> b & 1) ? rc.e[b] : -rc.e[b];
+          }
+          f(j, lin + __ldg(rc.cp + j));
+        }
+      }
+    };
+    if (rd.cost) {
+      for_costs([&](int j, int c) {
+        const C2 ph = phase[min(max(c - P.c_lo, 0), P.ncost - 1)];
+        const Real xr = v[j].x, xi = v[j].y;
+        v[j].x = xr * ph.x - xi * ph.y;
+        v[j].y = xr * ph.y + xi * ph.x;
+      });
+    }
+    apply_mixer<R>(v, rd.mixB, Real(P.tauB), Real(P.alphaB), FAST);
+    if (rd.dst == DST_GLOBAL_D && sp.scale != 1.0) {
+      const Real sc = Real(sp.scale);
+#pragma unroll
+      for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
+    }
+    if (rd.reduce) {
+      Real sn = 0, scc = 0;
+      for_costs([&](int j, int c) {
+        const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
+        sn += pr;
+        scc = fma(pr, Real(c), scc);
+      });
+      accN += double(sn);
+      accC += double(scc);
+    }
+  } else {
+    apply_mixer<R>(v, rd.mixB, Real(P.tauB), Real(P.alphaB), FAST);
+    if (rd.dst == DST_GLOBAL_D && sp.scale != 1.0) {
+      const Real sc = Real(sp.scale);
+#pragma unroll
+      for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
+    }
+  }
+
+  if (rd.dst == DST_GLOBAL_D) {
+    gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { __stcg(gstate + g, v[j]); });
+  } else {
+#pragma unroll
+    for (int j = 0; j < NA; ++j) tile[geo.sbase + padi<AB>(Y::toff(j))] = v[j];
+  }
+}
+
 // Shared-memory layout of the dynamic buffer:
-//   tile[2^T] complex | wmat[n*n] int | tile consts [16] int + base | phase table
+//   tile[padded 2^T] complex | tile consts [16] int + base | phase table
+// (the weight matrix is read through the L1 cache by one warp per tile)
 template <typename Real, int R, int WB, bool FAST>
 __global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
 fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
-  constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
+  constexpr uint32_t TILE = padded_size<AB>(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tile = reinterpret_cast<C2*>(smem_raw);
-  int* wsm = reinterpret_cast<int*>(tile + (1 << T));
-  int* tconst = wsm + P.n * P.n;  // delta[0..15], base at [16]
-  C2* ptab = reinterpret_cast<C2*>(smem_raw +
-                                   (((size_t(1) << T) * AB + size_t(P.n * P.n + 32) * 4 + 15) & ~size_t(15)));
+  int* tconst = reinterpret_cast<int*>(tile + TILE);  // delta[0..15], base at [16]
+  C2* ptab = reinterpret_cast<C2*>(smem_raw + ((size_t(TILE) * AB + 32 * 4 + 15) & ~size_t(15)));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = P.n;
-  for (int i = tid; i < n * n; i += NT) wsm[i] = A.wmat[i];
   const C2* phase = reinterpret_cast<const C2*>(A.phase);
   if (A.phase_in_smem && A.phase) {
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
     phase = ptab;
   }
-  C2* gstate = reinterpret_cast<C2*>(A.state);
   const bool stream = A.diag != nullptr;
-
   double accN = 0.0, accC = 0.0;
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
@@ -97,106 +253,18 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
       for (uint64_t ti = 0; ti < ntiles; ++ti) {
         const uint64_t gbase = ubase | scatter_bits(ti, sp.inner, sp.ninner);
         __syncthreads();  // previous tile finished with shared memory
-        if (sp.needs_c && !stream && warp == 0) tile_consts<T>(sp.pos, gbase, wsm, n, tconst, lane);
-        if (sp.needs_c && !stream) __syncthreads();
-
+        if (sp.needs_c && !stream) {
+          if (warp == 0) tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane);
+          __syncthreads();
+        }
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          // thread's tile index over its lane / warp bits, and the matching
-          // global offset and shared-memory slot
-          uint32_t tb = 0;
-          uint64_t gb = gbase;
-#pragma unroll
-          for (int i = 0; i < 5; ++i)
-            if (lane >> i & 1) { tb |= 1u << rd.lane[i]; gb |= 1ull << sp.pos[rd.lane[i]]; }
-#pragma unroll
-          for (int i = 0; i < WB; ++i)
-            if (warp >> i & 1) { tb |= 1u << rd.warp[i]; gb |= 1ull << sp.pos[rd.warp[i]]; }
-          uint32_t sstr[R];
-          uint64_t gstr[R];
-#pragma unroll
-          for (int i = 0; i < R; ++i) {
-            sstr[i] = swz<AB>(1u << rd.reg[i]);
-            gstr[i] = 1ull << sp.pos[rd.reg[i]];
-          }
-          const uint32_t sb0 = swz<AB>(tb);
-          auto soff = [&](int j) {
-            uint32_t o = sb0;
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-              if (j >> i & 1) o ^= sstr[i];
-            return o;
-          };
-          auto goff = [&](int j) {
-            uint64_t o = gb;
-#pragma unroll
-            for (int i = 0; i < R; ++i)
-              if (j >> i & 1) o |= gstr[i];
-            return o;
-          };
-
-          C2 v[NA];
-          if (rd.src == SRC_INIT_D) {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
-          } else if (rd.src == SRC_GLOBAL_D) {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) v[j] = __ldcg(gstate + goff(j));
-          } else {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) v[j] = tile[soff(j)];
-          }
-
-          apply_mixer<R>(v, rd.mixA, Real(P.tauA), Real(P.alphaA), FAST);
-
-          if (rd.cost | rd.reduce) {
-            // C(x) of register amplitude j: streamed from the diagonal, or
-            // kappa + CP[j] + sum_{i: j_i = 1} e_i from the round's tables
-            RoundCost<R, WB> rc;
-            if (!stream) rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
-            auto cv = [&](int j) { return stream ? __ldcg(A.diag + goff(j)) : rc(j); };
-            if (rd.cost) {
-#pragma unroll
-              for (int j = 0; j < NA; ++j) {
-                const C2 ph = phase[min(max(cv(j) - P.c_lo, 0), P.ncost - 1)];
-                const Real xr = v[j].x, xi = v[j].y;
-                v[j].x = xr * ph.x - xi * ph.y;
-                v[j].y = xr * ph.y + xi * ph.x;
-              }
-            }
-            apply_mixer<R>(v, rd.mixB, Real(P.tauB), Real(P.alphaB), FAST);
-            if (rd.dst == DST_GLOBAL_D && sp.scale != 1.0) {
-              const Real sc = Real(sp.scale);
-#pragma unroll
-              for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
-            }
-            if (rd.reduce) {
-              Real sn = 0, sc = 0;
-#pragma unroll
-              for (int j = 0; j < NA; ++j) {
-                const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
-                sn += pr;
-                sc = fma(pr, Real(cv(j)), sc);
-              }
-              accN += double(sn);
-              accC += double(sc);
-            }
-          } else {
-            apply_mixer<R>(v, rd.mixB, Real(P.tauB), Real(P.alphaB), FAST);
-            if (rd.dst == DST_GLOBAL_D && sp.scale != 1.0) {
-              const Real sc = Real(sp.scale);
-#pragma unroll
-              for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
-            }
-          }
-
-          if (rd.dst == DST_GLOBAL_D) {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) __stcg(gstate + goff(j), v[j]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < NA; ++j) tile[soff(j)] = v[j];
+          switch (rd.layout) {
+            case 0: fwd_round<Real, R, WB, 0, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC); break;
+            case 1: fwd_round<Real, R, WB, 1, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC); break;
+            case 2: fwd_round<Real, R, WB, 2, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC); break;
+            default: fwd_round<Real, R, WB, 3, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC); break;
           }
         }
       }
