@@ -149,10 +149,18 @@ struct ProfScope {
   }
 };
 
+// Forward tile shape: 2^5 registers x 8 warps (default), or 2^4 registers x
+// 16 warps when QAOA_FWD_SHAPE=4x4 (complex64 only; twice the warps per SM).
+bool fwd_wide(int prec) {
+  if (prec != QAOA_C64) return false;
+  const char* e = getenv("QAOA_FWD_SHAPE");
+  return e && strcmp(e, "4x4") == 0;
+}
+
 TileShape fwd_shape(int prec) {
   TileShape s;
-  s.R = kR;
-  s.WB = kWB;
+  s.R = fwd_wide(prec) ? 4 : kR;
+  s.WB = fwd_wide(prec) ? 4 : kWB;
   s.amp_bytes = amp_bytes(prec);
   return s;
 }
@@ -285,21 +293,21 @@ const Plan* get_plan(qaoa_ctx* c, int p) {
   return r;
 }
 
-template <typename Real, bool FAST>
+template <typename Real, bool FAST, int R = kR, int WB = kWB>
 int launch_pass(qaoa_ctx* c, const PassDev& pd, const PassArgs& pa, size_t smem, int grid) {
-  auto kern = fwd_pass_kernel<Real, kR, kWB, FAST>;
+  auto kern = fwd_pass_kernel<Real, R, WB, FAST>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, 32 << kWB, smem, c->stream>>>(pd, pa);
+  kern<<<grid, 32 << WB, smem, c->stream>>>(pd, pa);
   if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   return QAOA_OK;
 }
 
-template <typename Real, bool FAST>
+template <typename Real, bool FAST, int R = kR, int WB = kWB>
 int blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
-  auto kern = fwd_pass_kernel<Real, kR, kWB, FAST>;
+  auto kern = fwd_pass_kernel<Real, R, WB, FAST>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, 32 << kWB, smem));
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, 32 << WB, smem));
   if (*nb < 1) return c->set_err(QAOA_ECUDA, "pass kernel does not fit on an SM (smem %zu)", smem);
   return QAOA_OK;
 }
@@ -442,8 +450,11 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     pa.ctabs = (const int32_t*)c->d_ctabs.p;
     pa.phase_in_smem = tab_smem ? 1 : 0;
     int bps = 0;
+    const bool wide = fwd_wide(c->prec);
     if (c->prec == QAOA_C128)
       rc = fast ? blocks_per_sm<double, true>(c, smem, &bps) : blocks_per_sm<double, false>(c, smem, &bps);
+    else if (wide)
+      rc = fast ? blocks_per_sm<float, true, 4, 4>(c, smem, &bps) : blocks_per_sm<float, false, 4, 4>(c, smem, &bps);
     else
       rc = fast ? blocks_per_sm<float, true>(c, smem, &bps) : blocks_per_sm<float, false>(c, smem, &bps);
     if (rc) return rc;
@@ -460,6 +471,9 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
       ProfScope ps(c, 0, bytes);
       if (c->prec == QAOA_C128)
         rc = fast ? launch_pass<double, true>(c, pd, pa, smem, grid) : launch_pass<double, false>(c, pd, pa, smem, grid);
+      else if (wide)
+        rc = fast ? launch_pass<float, true, 4, 4>(c, pd, pa, smem, grid)
+                  : launch_pass<float, false, 4, 4>(c, pd, pa, smem, grid);
       else
         rc = fast ? launch_pass<float, true>(c, pd, pa, smem, grid) : launch_pass<float, false>(c, pd, pa, smem, grid);
     }

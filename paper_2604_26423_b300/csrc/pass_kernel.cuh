@@ -123,11 +123,21 @@ __device__ __forceinline__ void gray_walk(uint64_t g0, const uint64_t* gstr, F&&
   }
 }
 
+// Issues the global loads of a round whose source is global memory.
+template <typename Real, int R, int WB, int L>
+__device__ __forceinline__ void fwd_load(const SubDev& sp, const typename Cx<Real>::T* gstate, uint64_t gbase,
+                                         int lane, int warp, typename Cx<Real>::T* v) {
+  const RoundGeo<R, WB, L, int(sizeof(typename Cx<Real>::T))> geo(sp, gbase, lane, warp);
+  gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { v[j] = __ldcg(gstate + g); });
+}
+
+// One round. For a round whose source is global memory, v already holds the
+// loaded amplitudes (fwd_load, issued before the tile's barrier).
 template <typename Real, int R, int WB, int L, bool FAST>
 __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tile, uint64_t gbase, const int* tconst,
                                           const typename Cx<Real>::T* phase, int lane, int warp, double& accN,
-                                          double& accC) {
+                                          double& accC, typename Cx<Real>::T* v) {
   using C2 = typename Cx<Real>::T;
   using Y = Lay<R, WB, L>;
   constexpr int NA = 1 << R;
@@ -135,12 +145,11 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   C2* gstate = reinterpret_cast<C2*>(A.state);
   const bool stream = A.diag != nullptr;
   const RoundGeo<R, WB, L, AB> geo(sp, gbase, lane, warp);
-  C2 v[NA];
   if (rd.src == SRC_INIT_D) {
 #pragma unroll
     for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
   } else if (rd.src == SRC_GLOBAL_D) {
-    gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { v[j] = __ldcg(gstate + g); });
+    // loaded by fwd_load
   } else {
 #pragma unroll
     for (int j = 0; j < NA; ++j) v[j] = tile[geo.sbase + padi<AB>(Y::toff(j))];
@@ -244,6 +253,7 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   }
   const bool stream = A.diag != nullptr;
   double accN = 0.0, accC = 0.0;
+  C2 v[1 << R];
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
     const uint64_t ubase = scatter_bits(unit, P.outer, P.nouter);
@@ -252,6 +262,17 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
       const uint64_t ntiles = 1ull << sp.ninner;
       for (uint64_t ti = 0; ti < ntiles; ++ti) {
         const uint64_t gbase = ubase | scatter_bits(ti, sp.inner, sp.ninner);
+        // issue the tile's global loads first: their latency overlaps the
+        // barrier below and the tile constants
+        if (sp.rd[0].src == SRC_GLOBAL_D) {
+          const C2* gs = reinterpret_cast<const C2*>(A.state);
+          switch (sp.rd[0].layout) {
+            case 0: fwd_load<Real, R, WB, 0>(sp, gs, gbase, lane, warp, v); break;
+            case 1: fwd_load<Real, R, WB, 1>(sp, gs, gbase, lane, warp, v); break;
+            case 2: fwd_load<Real, R, WB, 2>(sp, gs, gbase, lane, warp, v); break;
+            default: fwd_load<Real, R, WB, 3>(sp, gs, gbase, lane, warp, v); break;
+          }
+        }
         __syncthreads();  // previous tile finished with shared memory
         if (sp.needs_c && !stream) {
           if (warp == 0) tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane);
@@ -261,10 +282,10 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
           switch (rd.layout) {
-            case 0: fwd_round<Real, R, WB, 0, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC); break;
-            case 1: fwd_round<Real, R, WB, 1, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC); break;
-            case 2: fwd_round<Real, R, WB, 2, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC); break;
-            default: fwd_round<Real, R, WB, 3, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC); break;
+            case 0: fwd_round<Real, R, WB, 0, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC, v); break;
+            case 1: fwd_round<Real, R, WB, 1, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC, v); break;
+            case 2: fwd_round<Real, R, WB, 2, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC, v); break;
+            default: fwd_round<Real, R, WB, 3, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC, v); break;
           }
         }
       }
