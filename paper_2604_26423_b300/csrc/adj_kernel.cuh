@@ -216,7 +216,9 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
         const uint64_t gbase = ubase | scatter_bits(ti, sp.inner, sp.ninner);
         __syncthreads();
         if (sp.needs_c && !stream) {
-          if (warp == 0) tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane);
+          if (tid == 0) tconst[16] = 0;
+          __syncthreads();
+          tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
           __syncthreads();
         }
         for (int r = 0; r < sp.nrounds; ++r) {

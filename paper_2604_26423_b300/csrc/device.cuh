@@ -72,42 +72,51 @@ __host__ __device__ constexpr uint32_t padded_size(int T) {
   return padi<AB>((1u << T) - 1) + 1;
 }
 
-// Per-tile constants over the fixed (non-tile) index bits F, computed by one
-// warp into tconst[0..T-1] (delta) and tconst[16] (base):
+// Per-tile constants over the fixed (non-tile) index bits F, computed by all
+// warps of the CTA into tconst[0..T-1] (delta) and tconst[16] (base):
 //   delta_j = sum_{g in F} w[pos_j][g] (1 - 2 f_g)
 //   base    = C restricted to F + sum_j sum_{g in F} w[pos_j][g] f_g
 // so that C(x) = base + sum_j t_j delta_j + C_tile(t) for tile index t.
+// Warp k takes tile bits j = k, k + nwarps, ... and rows g = k, k + nwarps, ...
+// of the fixed-bit pairs; lanes split the inner sums; base is accumulated with
+// shared-memory atomics, so tconst[16] must be zero on entry and a barrier
+// must separate this call from the first use.
 template <int T>
-__device__ __forceinline__ void tile_consts(const int8_t* pos, uint64_t gbase, const int* __restrict__ wsm, int n,
-                                            int* tconst, int lane) {
+__device__ __forceinline__ void tile_consts(const int8_t* pos, uint64_t gbase, const int* __restrict__ w, int n,
+                                            int* tconst, int lane, int warp, int nwarps) {
   uint64_t tbits = 0;
   for (int j = 0; j < T; ++j) tbits |= 1ull << pos[j];
-  int a = 0;
-  if (lane < T) {
-    const int pj = pos[lane];
-    int d = 0;
-    for (int g = 0; g < n; ++g) {
+  int base = 0;
+  for (int j = warp; j < T; j += nwarps) {
+    const int pj = pos[j];
+    int d = 0, a = 0;
+    for (int g = lane; g < n; g += 32) {
       if (tbits >> g & 1ull) continue;
-      const int wg = wsm[pj * n + g];
+      const int wg = __ldg(w + pj * n + g);
       const int fg = int(gbase >> g & 1ull);
       d += fg ? -wg : wg;
       a += fg ? wg : 0;
     }
-    tconst[lane] = d;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      d += __shfl_xor_sync(0xffffffffu, d, o);
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+    }
+    if (lane == 0) tconst[j] = d;
+    base += a;  // identical in every lane after the reduction
   }
   int cf = 0;
-  for (int g = lane; g < n; g += 32) {
+  for (int g = warp; g < n; g += nwarps) {
     if (tbits >> g & 1ull) continue;
     const int fg = int(gbase >> g & 1ull);
-    for (int h = g + 1; h < n; ++h) {
+    for (int h = g + 1 + lane; h < n; h += 32) {
       if (tbits >> h & 1ull) continue;
-      if (fg != int(gbase >> h & 1ull)) cf += wsm[g * n + h];
+      if (fg != int(gbase >> h & 1ull)) cf += __ldg(w + g * n + h);
     }
   }
-  int tot = a + cf;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-  if (lane == 0) tconst[16] = tot;
+  for (int o = 16; o > 0; o >>= 1) cf += __shfl_xor_sync(0xffffffffu, cf, o);
+  if (lane == 0 && (base | cf)) atomicAdd(tconst + 16, base + cf);
 }
 
 // C(x) of the 2^R register amplitudes of a round from its host-built tables:
