@@ -284,10 +284,18 @@ int upload_phases(qaoa_ctx* c, int p, const double* gamma) {
   return QAOA_OK;
 }
 
+// Largest super-tile (index bits kept together through L2 by one CTA);
+// QAOA_SMAX overrides the default (13 disables multi-tile super-tiles).
+int smax_fwd() {
+  const char* e = getenv("QAOA_SMAX");
+  const int v = e ? atoi(e) : kSmax;
+  return v >= 12 && v <= 20 ? v : kSmax;
+}
+
 const Plan* get_plan(qaoa_ctx* c, int p) {
   auto it = c->plans.find(p);
   if (it != c->plans.end()) return it->second.get();
-  auto pl = std::make_unique<Plan>(plan_forward(c->n, p, fwd_shape(c->prec), kSmax, kMinUnitsLog2));
+  auto pl = std::make_unique<Plan>(plan_forward(c->n, p, fwd_shape(c->prec), smax_fwd(), kMinUnitsLog2));
   const Plan* r = pl.get();
   c->plans[p] = std::move(pl);
   return r;
@@ -970,7 +978,7 @@ int qaoa_describe_plan(int n, int precision, int p, int adjoint, char* out, int 
   std::string s;
   try {
     Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), kSmaxAdj, kMinUnitsLog2)
-                      : plan_forward(n, p, fwd_shape(precision), kSmax, kMinUnitsLog2);
+                      : plan_forward(n, p, fwd_shape(precision), smax_fwd(), kMinUnitsLog2);
     std::string e = validate(pl);
     s = pl.describe();
     if (!e.empty()) s += "INVALID: " + e + "\n";
