@@ -83,31 +83,21 @@ __device__ __forceinline__ Real pow_bits(Real c, uint8_t mask) {
   return r;
 }
 
-template <typename Real, int R, int WB, int L, bool FAST>
+template <typename Real, int R, int WB, bool FAST>
 __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, uint64_t gbase,
                                           const int* tconst, const typename Cx<Real>::T* phase, int lane, int warp,
                                           double& gA, double& gC, double& gB) {
   using C2 = typename Cx<Real>::T;
-  using Y = Lay<R, WB, L>;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
   C2* gpsi = reinterpret_cast<C2*>(A.psi);
   C2* glam = reinterpret_cast<C2*>(A.lam);
   const bool stream = A.diag != nullptr;
-  const RoundGeo<R, WB, L, AB> geo(sp, gbase, lane, warp);
+  const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
   const bool need_c = rd.cost || rd.lam;
   RoundCost<R, WB> rcost;
-  if (need_c && !stream) {
-    int8_t lb[5], wb[WB], rb[R];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) lb[i] = int8_t(Y::lane(i));
-#pragma unroll
-    for (int i = 0; i < WB; ++i) wb[i] = int8_t(Y::warp(i));
-#pragma unroll
-    for (int i = 0; i < R; ++i) rb[i] = int8_t(Y::reg(i));
-    rcost.setup(A.ctabs + rd.ctab, tconst, lb, wb, rb, lane, warp);
-  }
+  if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
   auto for_costs = [&](auto&& f) {
     if (stream) {
       gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { f(j, __ldcg(A.diag + g)); });
@@ -138,12 +128,8 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { l[j] = __ldcg(glam + g); });
     }
   } else {
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      const uint32_t o = geo.sbase + padi<AB>(Y::toff(j));
-      v[j] = tv[o];
-      l[j] = tl[o];
-    }
+    smem_load<R, WB, AB>(rd.layout, tv, geo.sbase, v);
+    smem_load<R, WB, AB>(rd.layout, tl, geo.sbase, l);
   }
 
   Real ga = 0, gc = 0, gbv = 0;
@@ -174,12 +160,8 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       });
     }
   } else {
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      const uint32_t o = geo.sbase + padi<AB>(Y::toff(j));
-      tv[o] = v[j];
-      tl[o] = l[j];
-    }
+    smem_store<R, WB, AB>(rd.layout, tv, geo.sbase, v);
+    smem_store<R, WB, AB>(rd.layout, tl, geo.sbase, l);
   }
 }
 
@@ -224,12 +206,7 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          switch (rd.layout) {
-            case 0: adj_round<Real, R, WB, 0, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB); break;
-            case 1: adj_round<Real, R, WB, 1, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB); break;
-            case 2: adj_round<Real, R, WB, 2, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB); break;
-            default: adj_round<Real, R, WB, 3, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB); break;
-          }
+          adj_round<Real, R, WB, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB);
         }
       }
       __syncthreads();

@@ -88,26 +88,25 @@ __device__ __forceinline__ void apply_mixer(V* v, uint8_t mask, Real tau, Real a
   }
 }
 
-// Per-round thread geometry: the tile index of the thread's amplitude 0, its
-// padded shared-memory slot, its global index and the global strides of the
-// register bits.
-template <int R, int WB, int L, int AB>
+// Per-round thread geometry (runtime): the tile index of the thread's
+// amplitude 0, its padded shared-memory slot, its global index and the global
+// strides of the register bits.
+template <int R, int WB, int AB>
 struct RoundGeo {
-  uint32_t tb, sbase;
+  uint32_t sbase;
   uint64_t gb;
   uint64_t gstr[R];
-  __device__ __forceinline__ RoundGeo(const SubDev& sp, uint64_t gbase, int lane, int warp) {
-    using Y = Lay<R, WB, L>;
-    tb = 0;
+  __device__ __forceinline__ RoundGeo(const SubDev& sp, const RoundDev& rd, uint64_t gbase, int lane, int warp) {
+    uint32_t tb = 0;
     gb = gbase;
 #pragma unroll
     for (int i = 0; i < 5; ++i)
-      if (lane >> i & 1) { tb |= 1u << Y::lane(i); gb |= 1ull << sp.pos[Y::lane(i)]; }
+      if (lane >> i & 1) { tb |= 1u << rd.lane[i]; gb |= 1ull << sp.pos[rd.lane[i]]; }
 #pragma unroll
     for (int i = 0; i < WB; ++i)
-      if (warp >> i & 1) { tb |= 1u << Y::warp(i); gb |= 1ull << sp.pos[Y::warp(i)]; }
+      if (warp >> i & 1) { tb |= 1u << rd.warp[i]; gb |= 1ull << sp.pos[rd.warp[i]]; }
 #pragma unroll
-    for (int i = 0; i < R; ++i) gstr[i] = 1ull << sp.pos[Y::reg(i)];
+    for (int i = 0; i < R; ++i) gstr[i] = 1ull << sp.pos[rd.reg[i]];
     sbase = padi<AB>(tb);
   }
 };
@@ -123,36 +122,56 @@ __device__ __forceinline__ void gray_walk(uint64_t g0, const uint64_t* gstr, F&&
   }
 }
 
-// Issues the global loads of a round whose source is global memory.
-template <typename Real, int R, int WB, int L>
-__device__ __forceinline__ void fwd_load(const SubDev& sp, const typename Cx<Real>::T* gstate, uint64_t gbase,
-                                         int lane, int warp, typename Cx<Real>::T* v) {
-  const RoundGeo<R, WB, L, int(sizeof(typename Cx<Real>::T))> geo(sp, gbase, lane, warp);
-  gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { v[j] = __ldcg(gstate + g); });
+// Shared-memory loads / stores of the register amplitudes: the only code that
+// depends on the layout, compiled with constant offsets per menu entry.
+template <int R, int WB, int L, int AB, typename C2>
+__device__ __forceinline__ void smem_load_l(const C2* tile, uint32_t sbase, C2* v) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) v[j] = tile[sbase + padi<AB>(Lay<R, WB, L>::toff(j))];
+}
+template <int R, int WB, int L, int AB, typename C2>
+__device__ __forceinline__ void smem_store_l(C2* tile, uint32_t sbase, const C2* v) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) tile[sbase + padi<AB>(Lay<R, WB, L>::toff(j))] = v[j];
+}
+template <int R, int WB, int AB, typename C2>
+__device__ __forceinline__ void smem_load(int layout, const C2* tile, uint32_t sbase, C2* v) {
+  switch (layout) {
+    case 0: smem_load_l<R, WB, 0, AB>(tile, sbase, v); break;
+    case 1: smem_load_l<R, WB, 1, AB>(tile, sbase, v); break;
+    case 2: smem_load_l<R, WB, 2, AB>(tile, sbase, v); break;
+    default: smem_load_l<R, WB, 3, AB>(tile, sbase, v); break;
+  }
+}
+template <int R, int WB, int AB, typename C2>
+__device__ __forceinline__ void smem_store(int layout, C2* tile, uint32_t sbase, const C2* v) {
+  switch (layout) {
+    case 0: smem_store_l<R, WB, 0, AB>(tile, sbase, v); break;
+    case 1: smem_store_l<R, WB, 1, AB>(tile, sbase, v); break;
+    case 2: smem_store_l<R, WB, 2, AB>(tile, sbase, v); break;
+    default: smem_store_l<R, WB, 3, AB>(tile, sbase, v); break;
+  }
 }
 
 // One round. For a round whose source is global memory, v already holds the
-// loaded amplitudes (fwd_load, issued before the tile's barrier).
-template <typename Real, int R, int WB, int L, bool FAST>
+// loaded amplitudes (issued before the tile's barrier). Reduction partials are
+// added to the warp's slot in wacc (lane 0 writes).
+template <typename Real, int R, int WB, bool FAST>
 __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tile, uint64_t gbase, const int* tconst,
-                                          const typename Cx<Real>::T* phase, int lane, int warp, double& accN,
-                                          double& accC, typename Cx<Real>::T* v) {
+                                          const typename Cx<Real>::T* phase, int lane, int warp, double* wacc,
+                                          typename Cx<Real>::T* v) {
   using C2 = typename Cx<Real>::T;
-  using Y = Lay<R, WB, L>;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
   C2* gstate = reinterpret_cast<C2*>(A.state);
   const bool stream = A.diag != nullptr;
-  const RoundGeo<R, WB, L, AB> geo(sp, gbase, lane, warp);
+  const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
   if (rd.src == SRC_INIT_D) {
 #pragma unroll
     for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
-  } else if (rd.src == SRC_GLOBAL_D) {
-    // loaded by fwd_load
-  } else {
-#pragma unroll
-    for (int j = 0; j < NA; ++j) v[j] = tile[geo.sbase + padi<AB>(Y::toff(j))];
+  } else if (rd.src == SRC_SMEM_D) {
+    smem_load<R, WB, AB>(rd.layout, tile, geo.sbase, v);
   }
 
   apply_mixer<R>(v, rd.mixA, Real(P.tauA), Real(P.alphaA), FAST);
@@ -161,16 +180,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     // C(x) of register amplitude j: streamed from the diagonal, or
     // kappa + CP[j] + sum_{i: j_i = 1} e_i from the round's tables
     RoundCost<R, WB> rc;
-    if (!stream) {
-      int8_t lb[5], wb[WB], rb[R];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) lb[i] = int8_t(Y::lane(i));
-#pragma unroll
-      for (int i = 0; i < WB; ++i) wb[i] = int8_t(Y::warp(i));
-#pragma unroll
-      for (int i = 0; i < R; ++i) rb[i] = int8_t(Y::reg(i));
-      rc.setup(A.ctabs + rd.ctab, tconst, lb, wb, rb, lane, warp);
-    }
+    if (!stream) rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
     auto for_costs = [&](auto&& f) {
       if (stream) {
         gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { f(j, __ldcg(A.diag + g)); });
@@ -208,8 +218,13 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
         sn += pr;
         scc = fma(pr, Real(c), scc);
       });
-      accN += double(sn);
-      accC += double(scc);
+      double dn = double(sn), dc = double(scc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        dn += __shfl_xor_sync(0xffffffffu, dn, o);
+        dc += __shfl_xor_sync(0xffffffffu, dc, o);
+      }
+      if (lane == 0) { wacc[2 * warp] += dn; wacc[2 * warp + 1] += dc; }
     }
   } else {
     apply_mixer<R>(v, rd.mixB, Real(P.tauB), Real(P.alphaB), FAST);
@@ -223,8 +238,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   if (rd.dst == DST_GLOBAL_D) {
     gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { __stcg(gstate + g, v[j]); });
   } else {
-#pragma unroll
-    for (int j = 0; j < NA; ++j) tile[geo.sbase + padi<AB>(Y::toff(j))] = v[j];
+    smem_store<R, WB, AB>(rd.layout, tile, geo.sbase, v);
   }
 }
 
@@ -252,7 +266,8 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
     phase = ptab;
   }
   const bool stream = A.diag != nullptr;
-  double accN = 0.0, accC = 0.0;
+  __shared__ double wacc[2 * NT / 32];  // per-warp reduction slots
+  if (lane == 0) { wacc[2 * warp] = 0.0; wacc[2 * warp + 1] = 0.0; }
   C2 v[1 << R];
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
@@ -265,13 +280,9 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
         // issue the tile's global loads first: their latency overlaps the
         // barrier below and the tile constants
         if (sp.rd[0].src == SRC_GLOBAL_D) {
+          const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp);
           const C2* gs = reinterpret_cast<const C2*>(A.state);
-          switch (sp.rd[0].layout) {
-            case 0: fwd_load<Real, R, WB, 0>(sp, gs, gbase, lane, warp, v); break;
-            case 1: fwd_load<Real, R, WB, 1>(sp, gs, gbase, lane, warp, v); break;
-            case 2: fwd_load<Real, R, WB, 2>(sp, gs, gbase, lane, warp, v); break;
-            default: fwd_load<Real, R, WB, 3>(sp, gs, gbase, lane, warp, v); break;
-          }
+          gray_walk<R>(g0.gb, g0.gstr, [&](int j, uint64_t g) { v[j] = __ldcg(gs + g); });
         }
         __syncthreads();  // previous tile finished with shared memory
         if (sp.needs_c && !stream) {
@@ -283,12 +294,7 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          switch (rd.layout) {
-            case 0: fwd_round<Real, R, WB, 0, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC, v); break;
-            case 1: fwd_round<Real, R, WB, 1, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC, v); break;
-            case 2: fwd_round<Real, R, WB, 2, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC, v); break;
-            default: fwd_round<Real, R, WB, 3, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, accN, accC, v); break;
-          }
+          fwd_round<Real, R, WB, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, wacc, v);
         }
       }
       __syncthreads();  // sub-pass boundary: this CTA's global writes are visible to it
@@ -296,17 +302,11 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   }
 
   if (A.partial) {
-    // block reduction of the FP64 partial sums
-    __shared__ double red[2][32];
-    for (int o = 16; o > 0; o >>= 1) {
-      accN += __shfl_xor_sync(0xffffffffu, accN, o);
-      accC += __shfl_xor_sync(0xffffffffu, accC, o);
-    }
-    if (lane == 0) { red[0][warp] = accN; red[1][warp] = accC; }
+    // block sum of the per-warp FP64 partials, in warp order
     __syncthreads();
     if (tid == 0) {
       double sN = 0, sC = 0;
-      for (int w = 0; w < NT / 32; ++w) { sN += red[0][w]; sC += red[1][w]; }
+      for (int w = 0; w < NT / 32; ++w) { sN += wacc[2 * w]; sC += wacc[2 * w + 1]; }
       A.partial[2 * blockIdx.x] = sN;
       A.partial[2 * blockIdx.x + 1] = sC;
     }
