@@ -190,12 +190,12 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
   double gA = 0.0, gC = 0.0, gB = 0.0;
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
-    const uint64_t ubase = scatter_bits(unit, P.outer, P.nouter);
+    const uint64_t ubase = P.outer_runs.scatter(unit);
     for (int s = 0; s < P.nsub; ++s) {
       const SubDev& sp = P.sub[s];
       const uint64_t ntiles = 1ull << sp.ninner;
       for (uint64_t ti = 0; ti < ntiles; ++ti) {
-        const uint64_t gbase = ubase | scatter_bits(ti, sp.inner, sp.ninner);
+        const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
         __syncthreads();
         if (sp.needs_c && !stream) {
           if (tid == 0) tconst[16] = 0;

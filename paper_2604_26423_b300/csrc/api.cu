@@ -217,6 +217,31 @@ std::vector<int32_t> build_round_tables(const qaoa_ctx* c, const TileShape& sh, 
   return t;
 }
 
+// Runs of consecutive global bits in a sorted list (for BitRuns::scatter).
+BitRuns make_runs(const std::vector<int>& bits) {
+  BitRuns r;
+  memset(&r, 0, sizeof r);
+  int k = 0;
+  for (size_t i = 0; i < bits.size();) {
+    size_t j = i;
+    while (j + 1 < bits.size() && bits[j + 1] == bits[j] + 1) ++j;
+    r.src[k] = int8_t(i);
+    r.dst[k] = int8_t(bits[i]);
+    r.len[k] = int8_t(j - i + 1);
+    ++k;
+    i = j + 1;
+  }
+  r.n = int8_t(k);
+  return r;
+}
+
+// Global index bits of a round's register / lane / warp tile bits.
+void fill_round_globals(RoundDev& rd, const int8_t* pos) {
+  for (int i = 0; i < 5; ++i) rd.greg[i] = pos[rd.reg[i]];
+  for (int i = 0; i < 5; ++i) rd.glane[i] = pos[rd.lane[i]];
+  for (int i = 0; i < 4; ++i) rd.gwarp[i] = pos[rd.warp[i]];
+}
+
 void to_round_dev(const RoundPlan& rp, RoundDev& rd) {
   memcpy(rd.reg, rp.reg, 5);
   memcpy(rd.lane, rp.lane, 5);
@@ -406,6 +431,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     if (pd.nsub > kMaxSubDev) return c->set_err(QAOA_EINVAL, "plan has too many sub-passes");
     pd.nouter = (int)pp.outer.size();
     for (int i = 0; i < pd.nouter; ++i) pd.outer[i] = (int8_t)pp.outer[i];
+    pd.outer_runs = make_runs(pp.outer);
     pd.n_units = 1ull << pd.nouter;
     const double ba = pp.layer_a >= 0 ? beta[pp.layer_a] : 0.0;
     const double bb = pp.layer_b >= 0 ? beta[pp.layer_b] : 0.0;  // forward: mixer B shares the cost's layer
@@ -431,6 +457,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
       }
       sd.ninner = (int)inner.size();
       for (int i = 0; i < sd.ninner; ++i) sd.inner[i] = (int8_t)inner[i];
+      sd.inner_runs = make_runs(inner);
       sd.nrounds = (int)sp.rounds.size();
       if (sd.nrounds > kMaxRoundsDev) return c->set_err(QAOA_EINVAL, "plan has too many rounds");
       sd.init = sp.init;
@@ -440,6 +467,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
       for (int r = 0; r < sd.nrounds; ++r) {
         to_round_dev(sp.rounds[r], sd.rd[r]);
         sd.rd[r].layout = sp.rounds[r].layout;
+        fill_round_globals(sd.rd[r], sd.pos);
         if ((sd.rd[r].cost || sd.rd[r].reduce) && !stream) sd.rd[r].ctab = table_offset(c, sh, sd.pos, sd.rd[r]);
       }
     }
@@ -620,6 +648,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     if (pd.nsub > kMaxSubDev) return c->set_err(QAOA_EINVAL, "adjoint plan has too many sub-passes");
     pd.nouter = (int)pp.outer.size();
     for (int i = 0; i < pd.nouter; ++i) pd.outer[i] = (int8_t)pp.outer[i];
+    pd.outer_runs = make_runs(pp.outer);
     pd.n_units = 1ull << pd.nouter;
     const double ba = pp.layer_a >= 0 ? beta[pp.layer_a] : 0.0;
     const double bb = pp.layer_b >= 0 ? beta[pp.layer_b] : 0.0;
@@ -644,6 +673,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
       }
       sd.ninner = (int)inner.size();
       for (int i = 0; i < sd.ninner; ++i) sd.inner[i] = (int8_t)inner[i];
+      sd.inner_runs = make_runs(inner);
       sd.nrounds = (int)sp.rounds.size();
       if (sd.nrounds > kMaxRoundsDev) return c->set_err(QAOA_EINVAL, "adjoint plan has too many rounds");
       sd.needs_c = sp.needs_c;
@@ -652,6 +682,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
       for (int r = 0; r < sd.nrounds; ++r) {
         to_round_dev(sp.rounds[r], sd.rd[r]);
         sd.rd[r].layout = sp.rounds[r].layout;
+        fill_round_globals(sd.rd[r], sd.pos);
         if ((sd.rd[r].cost || sd.rd[r].lam) && !stream) sd.rd[r].ctab = table_offset(c, sh, sd.pos, sd.rd[r]);
       }
     }

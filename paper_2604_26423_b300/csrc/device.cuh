@@ -13,15 +13,29 @@ constexpr int kMaxBits = 40;
 // ops, and the offset of its precomputed cost tables.
 struct RoundDev {
   int8_t reg[5], lane[5], warp[4];
+  int8_t greg[5], glane[5], gwarp[4];  // global index bits of reg / lane / warp tile bits
   uint8_t mixA, cost, mixB, reduce, src, dst;
   uint8_t lam;     // adjoint: load psi only and create lambda = C(x) psi first
   uint8_t layout;  // menu layout id (plan.h, menu_layout)
   int32_t ctab;  // offset (in ints) of this round's cost tables, -1 if none
 };
 
+// Contiguous runs of a sorted bit list: bits [src, src+len) of an index go to
+// global bits [dst, dst+len).
+struct BitRuns {
+  int8_t src[6], dst[6], len[6];
+  int8_t n;
+  __device__ __forceinline__ uint64_t scatter(uint64_t idx) const {
+    uint64_t g = 0;
+    for (int i = 0; i < n; ++i) g |= ((idx >> src[i]) & ((1ull << len[i]) - 1)) << dst[i];
+    return g;
+  }
+};
+
 struct SubDev {
   int8_t pos[16];          // tile bit -> global index bit
   int8_t inner[kMaxBits];  // global bits enumerating tiles inside a super-tile
+  BitRuns inner_runs;
   int32_t ninner;
   int32_t nrounds;
   double scale;            // product of butterfly normalisations applied here
@@ -32,6 +46,7 @@ struct SubDev {
 struct PassDev {
   int32_t n, T, nsub, nouter;
   int8_t outer[kMaxBits];  // global bits enumerating super-tiles
+  BitRuns outer_runs;
   uint64_t n_units;        // number of super-tiles
   double tauA, alphaA;     // mixer of layer a: a' = alpha a + i tau b
   double tauB, alphaB;     // mixer of layer b (after the cost phase)

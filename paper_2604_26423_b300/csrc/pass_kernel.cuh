@@ -101,13 +101,23 @@ struct RoundGeo {
     gb = gbase;
 #pragma unroll
     for (int i = 0; i < 5; ++i)
-      if (lane >> i & 1) { tb |= 1u << rd.lane[i]; gb |= 1ull << sp.pos[rd.lane[i]]; }
+      if (lane >> i & 1) { tb |= 1u << rd.lane[i]; gb |= 1ull << rd.glane[i]; }
 #pragma unroll
     for (int i = 0; i < WB; ++i)
-      if (warp >> i & 1) { tb |= 1u << rd.warp[i]; gb |= 1ull << sp.pos[rd.warp[i]]; }
+      if (warp >> i & 1) { tb |= 1u << rd.warp[i]; gb |= 1ull << rd.gwarp[i]; }
 #pragma unroll
-    for (int i = 0; i < R; ++i) gstr[i] = 1ull << sp.pos[rd.reg[i]];
+    for (int i = 0; i < R; ++i) gstr[i] = 1ull << rd.greg[i];
     sbase = padi<AB>(tb);
+  }
+  __device__ __forceinline__ static uint32_t sbase_of(const RoundDev& rd, int lane, int warp) {
+    uint32_t tb = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+      if (lane >> i & 1) tb |= 1u << rd.lane[i];
+#pragma unroll
+    for (int i = 0; i < WB; ++i)
+      if (warp >> i & 1) tb |= 1u << rd.warp[i];
+    return padi<AB>(tb);
   }
 };
 
@@ -166,12 +176,13 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   constexpr int AB = sizeof(C2);
   C2* gstate = reinterpret_cast<C2*>(A.state);
   const bool stream = A.diag != nullptr;
-  const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
+  // the round's geometry is rebuilt where needed instead of being kept live
+  // across the butterflies (register pressure)
   if (rd.src == SRC_INIT_D) {
 #pragma unroll
     for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
   } else if (rd.src == SRC_SMEM_D) {
-    smem_load<R, WB, AB>(rd.layout, tile, geo.sbase, v);
+    smem_load<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp), v);
   }
 
   apply_mixer<R>(v, rd.mixA, Real(P.tauA), Real(P.alphaA), FAST);
@@ -183,6 +194,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     if (!stream) rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
     auto for_costs = [&](auto&& f) {
       if (stream) {
+        const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
         gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { f(j, __ldcg(A.diag + g)); });
       } else {
         int lin = rc.kappa;
@@ -236,9 +248,10 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   }
 
   if (rd.dst == DST_GLOBAL_D) {
+    const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
     gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { __stcg(gstate + g, v[j]); });
   } else {
-    smem_store<R, WB, AB>(rd.layout, tile, geo.sbase, v);
+    smem_store<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp), v);
   }
 }
 
@@ -271,12 +284,12 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   C2 v[1 << R];
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
-    const uint64_t ubase = scatter_bits(unit, P.outer, P.nouter);
+    const uint64_t ubase = P.outer_runs.scatter(unit);
     for (int s = 0; s < P.nsub; ++s) {
       const SubDev& sp = P.sub[s];
       const uint64_t ntiles = 1ull << sp.ninner;
       for (uint64_t ti = 0; ti < ntiles; ++ti) {
-        const uint64_t gbase = ubase | scatter_bits(ti, sp.inner, sp.ninner);
+        const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
         // issue the tile's global loads first: their latency overlaps the
         // barrier below and the tile constants
         if (sp.rd[0].src == SRC_GLOBAL_D) {
