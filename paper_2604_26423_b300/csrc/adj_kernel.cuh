@@ -100,7 +100,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
   auto for_costs = [&](auto&& f) {
     if (stream) {
-      gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { f(j, __ldcg(A.diag + g)); });
+      gray_ptr_walk<R>(A.diag, geo.gb, geo.gstr, [&](int j, const int32_t* q) { f(j, __ldcg(q)); });
     } else {
       int lin = rcost.kappa;
 #pragma unroll
@@ -117,7 +117,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
 
   C2 v[NA], l[NA];
   if (rd.src == SRC_GLOBAL_D) {
-    gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { v[j] = __ldcg(gpsi + g); });
+    gray_ptr_walk<R>(gpsi, geo.gb, geo.gstr, [&](int j, const C2* q) { v[j] = __ldcg(q); });
     if (rd.lam) {
       // lambda = C(x) psi (the operator whose expectation is differentiated)
       for_costs([&](int j, int c) {
@@ -125,7 +125,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
         l[j].y = Real(c) * v[j].y;
       });
     } else {
-      gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { l[j] = __ldcg(glam + g); });
+      gray_ptr_walk<R>(glam, geo.gb, geo.gstr, [&](int j, const C2* q) { l[j] = __ldcg(q); });
     }
   } else {
     smem_load<R, WB, AB>(rd.layout, tv, geo.sbase, v);
@@ -154,10 +154,8 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
 
   if (rd.dst == DST_GLOBAL_D) {
     if (sp.store) {
-      gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) {
-        __stcg(gpsi + g, v[j]);
-        __stcg(glam + g, l[j]);
-      });
+      gray_ptr_walk<R>(gpsi, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
+      gray_ptr_walk<R>(glam, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, l[j]); });
     }
   } else {
     smem_store<R, WB, AB>(rd.layout, tv, geo.sbase, v);

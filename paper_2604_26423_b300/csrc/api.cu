@@ -463,6 +463,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
       sd.init = sp.init;
       sd.needs_c = sp.needs_c;
       sd.store = sp.store;
+      sd.keep = s + 1 < pd.nsub;
       sd.scale = fast ? pow(cos(ba), sp.nA) * pow(cos(bb), sp.nB) : 1.0;
       for (int r = 0; r < sd.nrounds; ++r) {
         to_round_dev(sp.rounds[r], sd.rd[r]);
@@ -485,6 +486,10 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     pa.wmat = (const int32_t*)c->d_wmat.p;
     pa.ctabs = (const int32_t*)c->d_ctabs.p;
     pa.phase_in_smem = tab_smem ? 1 : 0;
+    {
+      const char* e = getenv("QAOA_L2HINT");
+      pa.l2hint = (e && atoi(e) != 0) ? 1 : 0;
+    }
     int bps = 0;
     const bool wide = fwd_wide(c->prec);
     if (c->prec == QAOA_C128)

@@ -39,7 +39,7 @@ struct SubDev {
   int32_t ninner;
   int32_t nrounds;
   double scale;            // product of butterfly normalisations applied here
-  uint8_t init, needs_c, store, pad[5];
+  uint8_t init, needs_c, store, keep, pad[4];  // keep: a later sub-pass reads this one's output
   RoundDev rd[kMaxRoundsDev];
 };
 
@@ -64,6 +64,34 @@ __device__ __forceinline__ uint64_t scatter_bits(uint64_t idx, const int8_t* pos
   uint64_t g = 0;
   for (int i = 0; i < k; ++i) g |= ((idx >> i) & 1ull) << pos[i];
   return g;
+}
+
+// L2 eviction-priority hints (per access; no device setting is changed).
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float2 ld_hint(const float2* a, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_hint(const double2* a, uint64_t pol) {
+  double2 v;
+  asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(double2* a, double2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
 }
 
 template <typename Real> struct Cx;

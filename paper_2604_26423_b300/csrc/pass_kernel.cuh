@@ -33,6 +33,7 @@ struct PassArgs {
   const int32_t* ctabs;   // per-round cost tables (recompute mode)
   double* partial;        // per-CTA [norm, <C>] partial sums (final pass)
   int phase_in_smem;      // copy the phase table into shared memory
+  int l2hint;             // L2 priorities: keep sub-pass outputs that are read back
 };
 
 // Compile-time copy of the planner's layout menu (plan.cpp, menu_layout).
@@ -132,6 +133,23 @@ __device__ __forceinline__ void gray_walk(uint64_t g0, const uint64_t* gstr, F&&
   }
 }
 
+// Calls f(j, pointer to register amplitude j) for j in Gray-code order. Step k
+// flips bit ctz(k) of j; whether it turns on or off is known at compile time,
+// so the pointer moves by +-stride with one 64-bit add.
+template <int R, typename T, typename F>
+__device__ __forceinline__ void gray_ptr_walk(T* base, uint64_t g0, const uint64_t* gstr, F&& f) {
+  T* q = base + g0;
+#pragma unroll
+  for (int k = 0; k < (1 << R); ++k) {
+    if (k) {
+      const int b = ctz_c(k);
+      const int j = k ^ (k >> 1);
+      if (j >> b & 1) q += gstr[b]; else q -= gstr[b];
+    }
+    f(k ^ (k >> 1), q);
+  }
+}
+
 // Shared-memory loads / stores of the register amplitudes: the only code that
 // depends on the layout, compiled with constant offsets per menu entry.
 template <int R, int WB, int L, int AB, typename C2>
@@ -195,7 +213,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     auto for_costs = [&](auto&& f) {
       if (stream) {
         const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
-        gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { f(j, __ldcg(A.diag + g)); });
+        gray_ptr_walk<R>(A.diag, geo.gb, geo.gstr, [&](int j, const int32_t* q) { f(j, __ldcg(q)); });
       } else {
         int lin = rc.kappa;
 #pragma unroll
@@ -249,7 +267,13 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
 
   if (rd.dst == DST_GLOBAL_D) {
     const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
-    gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t g) { __stcg(gstate + g, v[j]); });
+    if (A.l2hint) {
+      // outputs of a sub-pass that a later sub-pass reads back stay in L2
+      const uint64_t pol = sp.keep ? l2_policy_evict_last() : l2_policy_evict_first();
+      gray_ptr_walk<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { st_hint(q, v[j], pol); });
+    } else {
+      gray_ptr_walk<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
+    }
   } else {
     smem_store<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp), v);
   }
@@ -295,7 +319,12 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
         if (sp.rd[0].src == SRC_GLOBAL_D) {
           const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp);
           const C2* gs = reinterpret_cast<const C2*>(A.state);
-          gray_walk<R>(g0.gb, g0.gstr, [&](int j, uint64_t g) { v[j] = __ldcg(gs + g); });
+          if (A.l2hint) {
+            const uint64_t pol = l2_policy_evict_first();
+            gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = ld_hint(q, pol); });
+          } else {
+            gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = __ldcg(q); });
+          }
         }
         __syncthreads();  // previous tile finished with shared memory
         if (sp.needs_c && !stream) {
