@@ -32,7 +32,7 @@ using namespace qaoa;
 namespace {
 
 constexpr int kR = 5, kWB = 3;           // forward tile: 2^5 registers x 32 lanes x 8 warps
-constexpr int kSmax = 15;                // super-tile bits (L2-resident working set)
+constexpr int kSmax = 13;                // super-tile bits: 13 = one tile (L2 sub-passes measured slower)
 constexpr int kRAdj = 4, kWBAdj = 3;     // adjoint tile: psi and lambda, 2^4 registers each
 constexpr int kSmaxAdj = 14;             // adjoint super-tile (two vectors in L2)
 constexpr int kMinUnitsLog2 = 9;         // keep >= 512 super-tiles when n allows
