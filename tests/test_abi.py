@@ -97,10 +97,13 @@ def test_plans_valid(lib, n, p, prec):
         assert passes == p
 
 
-def test_n33_three_groups(lib):
-    # 33 qubits: one group of 15 low qubits, two of high qubits -> 7 HBM passes at p = 3
-    text = qaoa.describe_plan(33, 3, "c64")
-    assert "groups=3 passes=7" in text
+def test_n33_groups(lib, monkeypatch):
+    # default: one 2^13-amplitude tile per CTA and no L2 sub-passes -> 4 qubit
+    # groups (13 + 9 + 9 + 2) and 10 HBM passes at p = 3; with 2^15 super-tiles
+    # 3 groups (15 + 10 + 8) and 7 passes
+    assert "groups=4 passes=10" in qaoa.describe_plan(33, 3, "c64")
+    monkeypatch.setenv("QAOA_SMAX", "15")
+    assert "groups=3 passes=7" in qaoa.describe_plan(33, 3, "c64")
 
 
 @pytest.mark.parametrize("n", [12, 16, 24, 28, 33])
