@@ -34,7 +34,7 @@ namespace {
 constexpr int kR = 5, kWB = 3;           // forward tile: 2^5 registers x 32 lanes x 8 warps
 constexpr int kSmax = 13;                // super-tile bits: 13 = one tile (L2 sub-passes measured slower)
 constexpr int kRAdj = 4, kWBAdj = 3;     // adjoint tile: psi and lambda, 2^4 registers each
-constexpr int kSmaxAdj = 14;             // adjoint super-tile (two vectors in L2)
+constexpr int kSmaxAdj = 12;             // adjoint super-tile: one tile of psi and lambda
 constexpr int kMinUnitsLog2 = 9;         // keep >= 512 super-tiles when n allows
 constexpr long long kMaxAbsWeightSum = 1 << 20;
 constexpr int kMaxGrid = 4096;           // persistent grid cap (partial-sum buffer size)
@@ -311,6 +311,12 @@ int upload_phases(qaoa_ctx* c, int p, const double* gamma) {
 
 // Largest super-tile (index bits kept together through L2 by one CTA);
 // QAOA_SMAX overrides the default (13 disables multi-tile super-tiles).
+int smax_adj() {
+  const char* e = getenv("QAOA_SMAX_ADJ");
+  const int v = e ? atoi(e) : kSmaxAdj;
+  return v >= 12 && v <= 20 ? v : kSmaxAdj;
+}
+
 int smax_fwd() {
   const char* e = getenv("QAOA_SMAX");
   const int v = e ? atoi(e) : kSmax;
@@ -534,7 +540,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
 const Plan* get_bplan(qaoa_ctx* c, int p) {
   auto it = c->bplans.find(p);
   if (it != c->bplans.end()) return it->second.get();
-  auto pl = std::make_unique<Plan>(plan_backward(c->n, p, adj_shape(c->prec), kSmaxAdj, kMinUnitsLog2));
+  auto pl = std::make_unique<Plan>(plan_backward(c->n, p, adj_shape(c->prec), smax_adj(), kMinUnitsLog2));
   const Plan* r = pl.get();
   c->bplans[p] = std::move(pl);
   return r;
@@ -1013,7 +1019,7 @@ void* qaoa_state_ptr(qaoa_ctx* c) { return c ? c->state : nullptr; }
 int qaoa_describe_plan(int n, int precision, int p, int adjoint, char* out, int cap) {
   std::string s;
   try {
-    Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), kSmaxAdj, kMinUnitsLog2)
+    Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), smax_adj(), kMinUnitsLog2)
                       : plan_forward(n, p, fwd_shape(precision), smax_fwd(), kMinUnitsLog2);
     std::string e = validate(pl);
     s = pl.describe();

@@ -119,9 +119,13 @@ def test_adjoint_plans_valid(lib, n, p, prec):
     assert passes == (1 + p * (groups - 1) if groups > 1 else p)
 
 
-def test_adjoint_matches_forward_group_count_at_config_sizes(lib):
-    # the adjoint keeps as many qubit groups as the forward at 24, 28 and 33 qubits
-    for n in (24, 28, 33):
-        f = int(re.search(r"groups=(\d+)", qaoa.describe_plan(n, 5, "c64")).group(1))
-        b = int(re.search(r"groups=(\d+)", qaoa.describe_plan(n, 5, "c64", adjoint=True)).group(1))
-        assert b == f, (n, f, b)
+def test_adjoint_group_counts(lib, monkeypatch):
+    # one tile of psi and lambda per CTA (2^12 amplitudes): 3 groups at 24 and
+    # 28 qubits, 4 at 33; with 2^14 super-tiles through L2: 2, 3 and 3
+    got = [int(re.search(r"groups=(\d+)", qaoa.describe_plan(n, 5, "c64", adjoint=True)).group(1))
+           for n in (24, 28, 33)]
+    assert got == [3, 3, 4]
+    monkeypatch.setenv("QAOA_SMAX_ADJ", "14")
+    got = [int(re.search(r"groups=(\d+)", qaoa.describe_plan(n, 5, "c64", adjoint=True)).group(1))
+           for n in (24, 28, 33)]
+    assert got == [2, 3, 3]
