@@ -15,6 +15,11 @@ phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
 * ``roofline``: the fused pass kernel's algorithmic bytes (one read and one
   write of the state per pass; no read in the |+> pass) over its event-timed
   duration, against the measured HBM copy bandwidth.
+* ``grad``: the adjoint gradient's cost relative to the forward run on the
+  gradient workload (K_28, complex64, p = 10): t(qaoa_grad: forward, <C>,
+  backward, all 2p layer derivatives) / t(qaoa_run + qaoa_expect).
+* ``--qubits n`` runs the same step on K_n (smaller cases for profiling; the
+  JSON line then names that workload).
 * ``cpu_baseline`` / ``--impl reference``: the gate-by-gate complex128 oracle on
   the host cores, timed on one LR-QAOA layer of K_nc (nc chosen so the sample
   takes seconds), scaled to one layer of K_33 by amplitude count times gate
@@ -44,6 +49,7 @@ sys.path.insert(0, ROOT)
 
 N_QUBITS, P, DGAMMA, DBETA, SCALE, SEED, SHOTS = 33, 3, 0.6, 0.3, 0.1, 33, 4096
 METRIC = "LR-QAOA layers/s at n=33 (complex64, K_33, p=3)"
+GRAD_N, GRAD_P, GRAD_DGAMMA, GRAD_DBETA = 28, 10, 0.6, 0.3
 PROFILE_JSON = os.path.join(ROOT, "profiles", "fwd_pass_kernel_traffic.json")
 KERNEL_SOURCES = ["paper_2604_26423_b300/csrc/pass_kernel.cuh", "paper_2604_26423_b300/csrc/device.cuh"]
 
@@ -174,6 +180,40 @@ def cpu_baseline(budget_s: float = 12.0):
 
 
 # ------------------------------------------------------------------ GPU arm
+def grad_ratio(args, stream, reps: int = 3):
+    """Adjoint gradient time over forward time on K_28, complex64, p = 10."""
+    import torch
+    from paper_2604_26423_b300 import inputs
+    from paper_2604_26423_b300.qaoa import Simulator
+
+    u, v, w = inputs.complete_graph(GRAD_N, SEED)
+    with Simulator(GRAD_N, u, v, w, SCALE, "c64", cost_mode=args.cost_mode, with_grad=True) as s:
+        def fwd():
+            s.run(GRAD_P, GRAD_DGAMMA, GRAD_DBETA)
+            return s.expect()
+
+        def bwd():
+            return s.grad(GRAD_P, GRAD_DGAMMA, GRAD_DBETA)
+
+        times = {}
+        for name, f in (("forward", fwd), ("grad", bwd)):
+            for _ in range(3):
+                f()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                r = f()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[name] = e0.elapsed_time(e1) / reps
+        return {"workload": f"K_{GRAD_N} complex64, p={GRAD_P}, dgamma={GRAD_DGAMMA}, dbeta={GRAD_DBETA}",
+                "forward_ms": times["forward"], "grad_ms": times["grad"],
+                "ratio": times["grad"] / times["forward"], "exp_c": r["exp_c"],
+                "d_dgamma": r["d_dgamma"], "d_dbeta": r["d_dbeta"]}
+
+
 def run_gpu(args):
     import torch
     from paper_2604_26423_b300 import inputs
@@ -184,9 +224,10 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    u, v, w = inputs.complete_graph(N_QUBITS, SEED)
+    nq = args.qubits
+    u, v, w = inputs.complete_graph(nq, SEED)
     stream = torch.cuda.current_stream()
-    sim = Simulator(N_QUBITS, u, v, w, SCALE, "c64", cost_mode=args.cost_mode)
+    sim = Simulator(nq, u, v, w, SCALE, "c64", cost_mode=args.cost_mode)
     state_buf = sim._state_t
 
     def step():
@@ -223,21 +264,25 @@ def run_gpu(args):
     sim.close()
 
     def e2e_step():
-        s2 = Simulator(N_QUBITS, uh, vh, wh, SCALE, "c64", cost_mode=args.cost_mode, state=state_buf)
+        s2 = Simulator(nq, uh, vh, wh, SCALE, "c64", cost_mode=args.cost_mode, state=state_buf)
         s2.run(P, DGAMMA, DBETA)
         r2 = s2.expect()
         sh = s2.sample(SHOTS, seed=SEED + 1)
         s2.close()
         return r2, sh
 
-    e2e_step()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
+    e2e_s = float("nan")
+    if args.e2e_steps > 0:
         e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = reduce_max(time.perf_counter() - t0, world)
-    barrier(world)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = reduce_max(time.perf_counter() - t0, world)
+        barrier(world)
+    del state_buf
+    grad = None if args.no_grad else grad_ratio(args, stream)
 
     peak, peak_kind = measured_peak()
     achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else 0.0
@@ -250,17 +295,19 @@ def run_gpu(args):
     except Exception:
         pass
     layers = P * args.steps * world
+    metric = METRIC if nq == N_QUBITS else METRIC.replace("33", str(nq))
     out = {
-        "metric": METRIC, "value": layers / (ms * 1e-3), "unit": "layers/s", "n_gpus": world,
+        "metric": metric, "value": layers / (ms * 1e-3), "unit": "layers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 pairs), fp64 reductions",
         "data": "synthetic: SplitMix64 K_33 weights in {1..10}",
-        "config": {"workload": "LR-QAOA K_33 weighted MaxCut, complex64 (64 GiB state), p=3, dgamma=0.6, "
-                               "dbeta=0.3, <C>, r and 4096 shots per step",
-                   "n": N_QUBITS, "p": P, "precision": "complex64", "cost_mode": args.cost_mode,
-                   "state_bytes": 8 << N_QUBITS, "l2": "state 64 GiB >> 126 MB L2 (no flush needed)",
+        "config": {"workload": f"LR-QAOA K_{nq} weighted MaxCut, complex64 ({(8 << nq) >> 20} MiB state), p=3, "
+                               "dgamma=0.6, dbeta=0.3, <C>, r and 4096 shots per step",
+                   "n": nq, "p": P, "precision": "complex64", "cost_mode": args.cost_mode,
+                   "state_bytes": 8 << nq,
+                   "l2": f"state {(8 << nq) >> 20} MiB vs 126 MB L2" + (" (no flush needed)" if nq >= 25 else ""),
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": P * args.e2e_steps * world / e2e_s, "unit": "layers/s",
+        "e2e": None if args.e2e_steps <= 0 else {"value": P * args.e2e_steps * world / e2e_s, "unit": "layers/s",
                 "h2d_bytes_per_step": int(u.nbytes + v.nbytes + w.nbytes + 16),
                 "d2h_bytes_per_step": int(SHOTS * 8 + 7 * 8)},
         "gpu_launches": int(launches_all) if launches_all else int(launches),
@@ -272,6 +319,8 @@ def run_gpu(args):
         "result": {"exp_c": res["exp_c"], "r": res["r"], "norm": res["norm"], "c_max": res["c_max"]},
         "clocks": clk.summary(),
     }
+    if grad is not None:
+        out["grad"] = grad
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     if rank == 0:
@@ -316,6 +365,8 @@ def main(argv=None):
     ap.add_argument("--cost-mode", default="recompute", choices=["recompute", "stream"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--qubits", type=int, default=N_QUBITS)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -208,6 +208,65 @@ const char *qaoa_last_error(const qaoa_ctx *ctx);
 /* Releases the context and every buffer the library allocated for it. */
 void qaoa_free(qaoa_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Batched instances: many independent LR-QAOA MaxCut problems (complex64) in
+ * one persistent kernel replayed from a CUDA graph. Each instance i has n[i]
+ * qubits (2..24), depth p[i] (1..64), edges u/v/w[edge_off[i] .. edge_off[i+1])
+ * (vertex indices local to the instance; the checks of qaoa_init_graph apply),
+ * and the LR schedule of Sec. II-B with its own dgamma[i], dbeta[i]. Outputs
+ * per instance: <C>, r (exhaustive C_min / C_max, Eq. r), the norm, and with
+ * with_grad the exact adjoint gradient d<C>/d(gamma_k, beta_k) and its chain
+ * rule to d<C>/d(dgamma, dbeta). The paper has no batched interface; it runs
+ * its instances one at a time (Sec. III).
+ */
+typedef struct qaoa_batch qaoa_batch;
+
+/* Scheduling knobs (0 = default). solo_max_n: instances below this many
+ * qubits run all their passes in one CTA (default 16); window_items / window_mb:
+ * large instances are interleaved pass by pass until their next passes hold at
+ * least this many work items (default 2 per CTA) or their states this many MiB
+ * (default 96, sized for L2); max_units: super-tiles per work item (default 8);
+ * ctas_per_sm: persistent CTAs per SM (default: occupancy, at most 2). */
+typedef struct qaoa_batch_opts {
+  int solo_max_n, window_items, window_mb, max_units, ctas_per_sm;
+} qaoa_batch_opts;
+
+/* Validates and plans the batch, allocates its device memory (all states, and
+ * the adjoint vectors with with_grad), uploads weights, phase and cost tables,
+ * and captures one run (counter resets, the persistent kernel, the per-instance
+ * finalisation) into a CUDA graph. Host arrays are copied; opts may be NULL.
+ * Errors: EINVAL (sizes, graphs, angles), ENOMEM, ECUDA. On failure *out is
+ * NULL and qaoa_batch_last_error(NULL) describes it. */
+int qaoa_batch_create(qaoa_batch **out, int count, const int32_t *n, const int32_t *p,
+                      const int64_t *edge_off, const int32_t *u, const int32_t *v, const int32_t *w,
+                      const double *dgamma, const double *dbeta, double weight_scale, int with_grad,
+                      const qaoa_batch_opts *opts, void *cuda_stream);
+
+/* Replays the batch's graph on its stream (asynchronous). Each run recomputes
+ * every instance from |+>. */
+int qaoa_batch_run(qaoa_batch *b);
+
+/* Waits for the stream and copies results to host arrays (either may be NULL):
+ * out[9 i + 0..8] = {<C>, r, norm, C_min, C_max, argmin, argmax,
+ * d<C>/d dgamma, d<C>/d dbeta} (the last two are 0 without gradient);
+ * grads = per instance g_gamma[p_i] then g_beta[p_i], concatenated in instance
+ * order (sum of 2 p_i doubles). Returns ETIMEOUT if a dependency wait in the
+ * persistent kernel gave up (results are then invalid), ESTATE before a run. */
+int qaoa_batch_results(qaoa_batch *b, double *out, double *grads);
+
+/* Device pointer to instance i's final state (2^n[i] complex64); ESTATE for a
+ * gradient batch, whose states have been walked back by the adjoint sweep. */
+int qaoa_batch_state(qaoa_batch *b, int i, void **state_dev);
+
+/* Human-readable plan summary (instances per mode, items, grid, bytes). */
+int qaoa_batch_describe(const qaoa_batch *b, char *out, size_t cap);
+
+/* Algorithmic HBM-or-L2 bytes of one run (state reads and writes of all passes). */
+double qaoa_batch_bytes(const qaoa_batch *b);
+
+const char *qaoa_batch_last_error(const qaoa_batch *b);
+void qaoa_batch_free(qaoa_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,7 +87,7 @@ template <typename Real, int R, int WB, bool FAST>
 __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, uint64_t gbase,
                                           const int* tconst, const typename Cx<Real>::T* phase, int lane, int warp,
-                                          double& gA, double& gC, double& gB) {
+                                          Real& ga, Real& gc, Real& gbv) {
   using C2 = typename Cx<Real>::T;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
@@ -132,13 +132,13 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     smem_load<R, WB, AB>(rd.layout, tl, geo.sbase, l);
   }
 
-  Real ga = 0, gc = 0, gbv = 0;
-  inverse_mixer<R>(v, l, rd.mixA, Real(P.tauA), Real(P.alphaA), FAST, pow_bits(Real(P.cA), rd.mixA), ga);
+  inverse_mixer<R>(v, l, rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA), FAST,
+                   pow_bits(pick<Real>(P.cA, P.fcA), rd.mixA), ga);
   if (rd.cost) {
     for_costs([&](int j, int c) {
       const Real h = Real(P.wsum - 2 * c);
       gc = fma(fma(l[j].x, v[j].y, -l[j].y * v[j].x), h, gc);
-      const C2 ph = phase[min(max(c - P.c_lo, 0), P.ncost - 1)];
+      const C2 ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
       // multiply both vectors by the conjugate phase (inverse cost unitary)
       const Real vr = v[j].x, vi = v[j].y, lr = l[j].x, li = l[j].y;
       v[j].x = vr * ph.x + vi * ph.y;
@@ -147,10 +147,8 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       l[j].y = li * ph.x - lr * ph.y;
     });
   }
-  inverse_mixer<R>(v, l, rd.mixB, Real(P.tauB), Real(P.alphaB), FAST, pow_bits(Real(P.cB), rd.mixB), gbv);
-  gA += double(ga);
-  gC += double(gc);
-  gB += double(gbv);
+  inverse_mixer<R>(v, l, rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB), FAST,
+                   pow_bits(pick<Real>(P.cB, P.fcB), rd.mixB), gbv);
 
   if (rd.dst == DST_GLOBAL_D) {
     if (sp.store) {
@@ -160,6 +158,54 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   } else {
     smem_store<R, WB, AB>(rd.layout, tv, geo.sbase, v);
     smem_store<R, WB, AB>(rd.layout, tl, geo.sbase, l);
+  }
+}
+
+// One super-tile (unit) of an adjoint pass; the gradient terms of this
+// thread's amplitudes are added to gA, gC, gB.
+template <typename Real, int R, int WB, bool FAST>
+__device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uint64_t unit,
+                                         typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, int* tconst,
+                                         const typename Cx<Real>::T* phase, double& gA, double& gC, double& gB) {
+  constexpr int T = R + 5 + WB;
+  constexpr int NT = 32 << WB;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = P.n;
+  const bool stream = A.diag != nullptr;
+  const uint64_t ubase = P.outer_runs.scatter(unit);
+  for (int s = 0; s < P.nsub; ++s) {
+    const SubDev& sp = P.sub[s];
+    const uint64_t ntiles = 1ull << sp.ninner;
+    for (uint64_t ti = 0; ti < ntiles; ++ti) {
+      const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
+      __syncthreads();
+      if (sp.needs_c && !stream) {
+        if (tid == 0) tconst[16] = 0;
+        __syncthreads();
+        tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
+        __syncthreads();
+      }
+      if constexpr (sizeof(Real) == 8) {
+        for (int r = 0; r < sp.nrounds; ++r) {
+          const RoundDev& rd = sp.rd[r];
+          if (rd.src == SRC_SMEM_D) __syncthreads();
+          adj_round<Real, R, WB, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB);
+        }
+      } else {
+        // fp32: the terms of one tile are summed in fp32, then added in FP64
+        // (keeps fp64 conversions out of the rounds)
+        Real ga = 0, gc = 0, gbv = 0;
+        for (int r = 0; r < sp.nrounds; ++r) {
+          const RoundDev& rd = sp.rd[r];
+          if (rd.src == SRC_SMEM_D) __syncthreads();
+          adj_round<Real, R, WB, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, ga, gc, gbv);
+        }
+        gA += double(ga);
+        gC += double(gc);
+        gB += double(gbv);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -178,38 +224,15 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
   int* tconst = reinterpret_cast<int*>(tl + TILE);
   C2* ptab = reinterpret_cast<C2*>(smem_raw + ((size_t(2 * TILE) * AB + 32 * 4 + 15) & ~size_t(15)));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n = P.n;
   const C2* phase = reinterpret_cast<const C2*>(A.phase);
   if (A.phase_in_smem && A.phase) {
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
     phase = ptab;
   }
-  const bool stream = A.diag != nullptr;
   double gA = 0.0, gC = 0.0, gB = 0.0;
 
-  for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
-    const uint64_t ubase = P.outer_runs.scatter(unit);
-    for (int s = 0; s < P.nsub; ++s) {
-      const SubDev& sp = P.sub[s];
-      const uint64_t ntiles = 1ull << sp.ninner;
-      for (uint64_t ti = 0; ti < ntiles; ++ti) {
-        const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
-        __syncthreads();
-        if (sp.needs_c && !stream) {
-          if (tid == 0) tconst[16] = 0;
-          __syncthreads();
-          tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
-          __syncthreads();
-        }
-        for (int r = 0; r < sp.nrounds; ++r) {
-          const RoundDev& rd = sp.rd[r];
-          if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB);
-        }
-      }
-      __syncthreads();
-    }
-  }
+  for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
+    adj_unit<Real, R, WB, FAST>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB);
 
   __shared__ double red[3][32];
   for (int o = 16; o > 0; o >>= 1) {

@@ -21,6 +21,7 @@
 
 #include "qaoa.h"
 #include "plan.h"
+#include "desc.h"
 #include "device.cuh"
 #include "pass_kernel.cuh"
 #include "aux_kernels.cuh"
@@ -77,9 +78,7 @@ struct qaoa_ctx {
   DevBuf d_wmat, d_ctabs, d_phase, d_partial, d_result, d_ext, d_ext_part;
   DevBuf d_sums, d_pre, d_shots, d_uni, d_ang;
   DevBuf d_lambda, d_gacc;                                            // adjoint vector (if no aux), per-pass sums
-  std::vector<int32_t> h_ctabs;                                        // host copy of all cost tables
-  std::map<std::pair<int, std::vector<int8_t>>, int> ctab_index;       // (shape, pos + layout) -> offset
-  bool ctabs_dirty = false;
+  TableStore tabs;                                                     // host copy of all cost tables
   std::map<int, std::unique_ptr<Plan>> plans;                         // forward plans by p
   std::map<int, std::unique_ptr<Plan>> bplans;                        // adjoint plans by p
   // per-kernel CUDA-event timing (qaoa_profile_enable / qaoa_profile_read)
@@ -174,112 +173,13 @@ TileShape adj_shape(int prec) {
   return s;
 }
 
-// Cost tables of one round (recompute mode), for tile bits at global
-// positions pos[] and the round's register / lane / warp split:
-//   CQ[q]     = sum_{k<l in Q} w [q_k != q_l]          (q: lane bits, then warp bits)
-//   AJ[q][i]  = sum_{k in Q, q_k = 1} w[reg_i][k]
-//   D[i]      = sum_{k in Q} w[reg_i][k]
-//   CP[j]     = sum_{i<i'} w[reg_i][reg_i'] [j_i != j_i']
-std::vector<int32_t> build_round_tables(const qaoa_ctx* c, const TileShape& sh, const int8_t* pos,
-                                        const RoundDev& rd) {
-  const int R = sh.R, WB = sh.WB, QB = 5 + WB;
-  const int QN = 1 << QB;
-  auto W = [&](int tj, int tk) { return c->wmat[pos[tj] * c->n + pos[tk]]; };
-  int qbits[16];
-  for (int i = 0; i < 5; ++i) qbits[i] = rd.lane[i];
-  for (int i = 0; i < WB; ++i) qbits[5 + i] = rd.warp[i];
-  std::vector<int32_t> t(QN + QN * R + R + (1 << R));
-  for (int q = 0; q < QN; ++q) {
-    int cq = 0;
-    for (int k = 0; k < QB; ++k)
-      for (int l = k + 1; l < QB; ++l)
-        if ((q >> k & 1) != (q >> l & 1)) cq += W(qbits[k], qbits[l]);
-    t[q] = cq;
-    for (int i = 0; i < R; ++i) {
-      int a = 0;
-      for (int k = 0; k < QB; ++k)
-        if (q >> k & 1) a += W(rd.reg[i], qbits[k]);
-      t[QN + q * R + i] = a;
-    }
-  }
-  for (int i = 0; i < R; ++i) {
-    int d = 0;
-    for (int k = 0; k < QB; ++k) d += W(rd.reg[i], qbits[k]);
-    t[QN + QN * R + i] = d;
-  }
-  for (int j = 0; j < (1 << R); ++j) {
-    int cp = 0;
-    for (int i = 0; i < R; ++i)
-      for (int i2 = i + 1; i2 < R; ++i2)
-        if ((j >> i & 1) != (j >> i2 & 1)) cp += W(rd.reg[i], rd.reg[i2]);
-    t[QN + QN * R + R + j] = cp;
-  }
-  return t;
-}
-
-// Runs of consecutive global bits in a sorted list (for BitRuns::scatter).
-BitRuns make_runs(const std::vector<int>& bits) {
-  BitRuns r;
-  memset(&r, 0, sizeof r);
-  int k = 0;
-  for (size_t i = 0; i < bits.size();) {
-    size_t j = i;
-    while (j + 1 < bits.size() && bits[j + 1] == bits[j] + 1) ++j;
-    r.src[k] = int8_t(i);
-    r.dst[k] = int8_t(bits[i]);
-    r.len[k] = int8_t(j - i + 1);
-    ++k;
-    i = j + 1;
-  }
-  r.n = int8_t(k);
-  return r;
-}
-
-// Global index bits of a round's register / lane / warp tile bits.
-void fill_round_globals(RoundDev& rd, const int8_t* pos) {
-  for (int i = 0; i < 5; ++i) rd.greg[i] = pos[rd.reg[i]];
-  for (int i = 0; i < 5; ++i) rd.glane[i] = pos[rd.lane[i]];
-  for (int i = 0; i < 4; ++i) rd.gwarp[i] = pos[rd.warp[i]];
-}
-
-void to_round_dev(const RoundPlan& rp, RoundDev& rd) {
-  memcpy(rd.reg, rp.reg, 5);
-  memcpy(rd.lane, rp.lane, 5);
-  memcpy(rd.warp, rp.warp, 4);
-  rd.mixA = rp.mixA;
-  rd.cost = rp.cost;
-  rd.mixB = rp.mixB;
-  rd.reduce = rp.reduce;
-  rd.src = rp.src;
-  rd.dst = rp.dst;
-  rd.lam = rp.lam;
-  rd.layout = rp.layout;
-  rd.ctab = -1;
-}
-
-int32_t table_offset(qaoa_ctx* c, const TileShape& sh, const int8_t* pos, const RoundDev& rd) {
-  std::vector<int8_t> key(pos, pos + sh.T());
-  key.insert(key.end(), rd.reg, rd.reg + 5);
-  key.insert(key.end(), rd.lane, rd.lane + 5);
-  key.insert(key.end(), rd.warp, rd.warp + 4);
-  auto k = std::make_pair(sh.R * 100 + sh.WB, key);
-  auto it = c->ctab_index.find(k);
-  if (it != c->ctab_index.end()) return it->second;
-  std::vector<int32_t> t = build_round_tables(c, sh, pos, rd);
-  const int32_t off = (int32_t)c->h_ctabs.size();
-  c->h_ctabs.insert(c->h_ctabs.end(), t.begin(), t.end());
-  c->ctab_index[k] = off;
-  c->ctabs_dirty = true;
-  return off;
-}
-
 int upload_ctabs(qaoa_ctx* c) {
-  if (!c->ctabs_dirty) return QAOA_OK;
-  const size_t bytes = std::max<size_t>(4, c->h_ctabs.size() * 4);
+  if (!c->tabs.dirty) return QAOA_OK;
+  const size_t bytes = std::max<size_t>(4, c->tabs.h.size() * 4);
   CUDA_TRY(c, c->d_ctabs.ensure(bytes));
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_ctabs.p, c->h_ctabs.data(), c->h_ctabs.size() * 4, cudaMemcpyHostToDevice,
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_ctabs.p, c->tabs.h.data(), c->tabs.h.size() * 4, cudaMemcpyHostToDevice,
                               c->stream));
-  c->ctabs_dirty = false;
+  c->tabs.dirty = false;
   return QAOA_OK;
 }
 
@@ -351,13 +251,6 @@ int blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
   return QAOA_OK;
 }
 
-// mixer exp(+i beta X): a' = cos(beta) a + i sin(beta) b (and symmetric); the
-// fast form divides by cos(beta) when |tan(beta)| <= 1.
-void mixer_coeffs(double beta, bool fast, double* tau, double* alpha) {
-  if (fast) { *tau = tan(beta); *alpha = 1.0; }
-  else { *tau = sin(beta); *alpha = cos(beta); }
-}
-
 int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   const int n = c->n;
   CUDA_TRY(c, c->d_ang.ensure(sizeof(double) * 2 * std::max(1, p)));
@@ -427,57 +320,20 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   // build every pass descriptor (and its cost tables) before launching
   std::vector<PassDev> pds(plan->passes.size());
   std::vector<char> fasts(plan->passes.size());
+  PassInputs in;
+  in.n = n;
+  in.beta = beta;
+  in.c_lo = c->c_lo;
+  in.ncost = nc;
+  in.W = c->W;
+  in.wmat = c->wmat.data();
+  in.stream = stream;
+  in.adjoint = false;
   for (size_t pi = 0; pi < plan->passes.size(); ++pi) {
-    const PassPlan& pp = plan->passes[pi];
-    PassDev& pd = pds[pi];
-    memset(&pd, 0, sizeof pd);
-    pd.n = n;
-    pd.T = T;
-    pd.nsub = (int)pp.subs.size();
-    if (pd.nsub > kMaxSubDev) return c->set_err(QAOA_EINVAL, "plan has too many sub-passes");
-    pd.nouter = (int)pp.outer.size();
-    for (int i = 0; i < pd.nouter; ++i) pd.outer[i] = (int8_t)pp.outer[i];
-    pd.outer_runs = make_runs(pp.outer);
-    pd.n_units = 1ull << pd.nouter;
-    const double ba = pp.layer_a >= 0 ? beta[pp.layer_a] : 0.0;
-    const double bb = pp.layer_b >= 0 ? beta[pp.layer_b] : 0.0;  // forward: mixer B shares the cost's layer
-    const bool fast = fabs(cos(ba)) >= fabs(sin(ba)) && fabs(cos(bb)) >= fabs(sin(bb));
+    bool fast = true;
+    const std::string why = fill_pass_dev(plan->passes[pi], sh, in, c->tabs, pds[pi], fast);
+    if (!why.empty()) return c->set_err(QAOA_EINVAL, "%s", why.c_str());
     fasts[pi] = fast;
-    mixer_coeffs(ba, fast, &pd.tauA, &pd.alphaA);
-    mixer_coeffs(bb, fast, &pd.tauB, &pd.alphaB);
-    pd.amp0 = pow(2.0, -0.5 * n);
-    pd.c_lo = (int32_t)c->c_lo;
-    pd.ncost = (int32_t)nc;
-    pd.wsum = (int32_t)c->W;
-    pd.cA = cos(ba);
-    pd.cB = cos(bb);
-    for (int s = 0; s < pd.nsub; ++s) {
-      const SubPassPlan& sp = pp.subs[s];
-      SubDev& sd = pd.sub[s];
-      for (int j = 0; j < T; ++j) sd.pos[j] = sp.pos[j];
-      std::vector<int> inner;
-      for (int b : pp.sb) {
-        bool in_tile = false;
-        for (int j = 0; j < T; ++j) in_tile |= sp.pos[j] == b;
-        if (!in_tile) inner.push_back(b);
-      }
-      sd.ninner = (int)inner.size();
-      for (int i = 0; i < sd.ninner; ++i) sd.inner[i] = (int8_t)inner[i];
-      sd.inner_runs = make_runs(inner);
-      sd.nrounds = (int)sp.rounds.size();
-      if (sd.nrounds > kMaxRoundsDev) return c->set_err(QAOA_EINVAL, "plan has too many rounds");
-      sd.init = sp.init;
-      sd.needs_c = sp.needs_c;
-      sd.store = sp.store;
-      sd.keep = s + 1 < pd.nsub;
-      sd.scale = fast ? pow(cos(ba), sp.nA) * pow(cos(bb), sp.nB) : 1.0;
-      for (int r = 0; r < sd.nrounds; ++r) {
-        to_round_dev(sp.rounds[r], sd.rd[r]);
-        sd.rd[r].layout = sp.rounds[r].layout;
-        fill_round_globals(sd.rd[r], sd.pos);
-        if ((sd.rd[r].cost || sd.rd[r].reduce) && !stream) sd.rd[r].ctab = table_offset(c, sh, sd.pos, sd.rd[r]);
-      }
-    }
   }
   rc = upload_ctabs(c);
   if (rc) return rc;
@@ -649,54 +505,20 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   const size_t npass = plan->passes.size();
   std::vector<PassDev> pds(npass);
   std::vector<char> fasts(npass);
+  PassInputs in;
+  in.n = n;
+  in.beta = beta;
+  in.c_lo = c->c_lo;
+  in.ncost = nc;
+  in.W = c->W;
+  in.wmat = c->wmat.data();
+  in.stream = stream;
+  in.adjoint = true;
   for (size_t pi = 0; pi < npass; ++pi) {
-    const PassPlan& pp = plan->passes[pi];
-    PassDev& pd = pds[pi];
-    memset(&pd, 0, sizeof pd);
-    pd.n = n;
-    pd.T = T;
-    pd.nsub = (int)pp.subs.size();
-    if (pd.nsub > kMaxSubDev) return c->set_err(QAOA_EINVAL, "adjoint plan has too many sub-passes");
-    pd.nouter = (int)pp.outer.size();
-    for (int i = 0; i < pd.nouter; ++i) pd.outer[i] = (int8_t)pp.outer[i];
-    pd.outer_runs = make_runs(pp.outer);
-    pd.n_units = 1ull << pd.nouter;
-    const double ba = pp.layer_a >= 0 ? beta[pp.layer_a] : 0.0;
-    const double bb = pp.layer_b >= 0 ? beta[pp.layer_b] : 0.0;
-    const bool fast = fabs(cos(ba)) >= fabs(sin(ba)) && fabs(cos(bb)) >= fabs(sin(bb));
+    bool fast = true;
+    const std::string why = fill_pass_dev(plan->passes[pi], sh, in, c->tabs, pds[pi], fast);
+    if (!why.empty()) return c->set_err(QAOA_EINVAL, "%s", why.c_str());
     fasts[pi] = fast;
-    mixer_coeffs(ba, fast, &pd.tauA, &pd.alphaA);
-    mixer_coeffs(bb, fast, &pd.tauB, &pd.alphaB);
-    pd.c_lo = (int32_t)c->c_lo;
-    pd.ncost = (int32_t)nc;
-    pd.wsum = (int32_t)c->W;
-    pd.cA = cos(ba);
-    pd.cB = cos(bb);
-    for (int s = 0; s < pd.nsub; ++s) {
-      const SubPassPlan& sp = pp.subs[s];
-      SubDev& sd = pd.sub[s];
-      for (int j = 0; j < T; ++j) sd.pos[j] = sp.pos[j];
-      std::vector<int> inner;
-      for (int b : pp.sb) {
-        bool in_tile = false;
-        for (int j = 0; j < T; ++j) in_tile |= sp.pos[j] == b;
-        if (!in_tile) inner.push_back(b);
-      }
-      sd.ninner = (int)inner.size();
-      for (int i = 0; i < sd.ninner; ++i) sd.inner[i] = (int8_t)inner[i];
-      sd.inner_runs = make_runs(inner);
-      sd.nrounds = (int)sp.rounds.size();
-      if (sd.nrounds > kMaxRoundsDev) return c->set_err(QAOA_EINVAL, "adjoint plan has too many rounds");
-      sd.needs_c = sp.needs_c;
-      sd.store = sp.store;
-      sd.scale = 1.0;
-      for (int r = 0; r < sd.nrounds; ++r) {
-        to_round_dev(sp.rounds[r], sd.rd[r]);
-        sd.rd[r].layout = sp.rounds[r].layout;
-        fill_round_globals(sd.rd[r], sd.pos);
-        if ((sd.rd[r].cost || sd.rd[r].lam) && !stream) sd.rd[r].ctab = table_offset(c, sh, sd.pos, sd.rd[r]);
-      }
-    }
   }
   rc = upload_ctabs(c);
   if (rc) return rc;
@@ -822,17 +644,11 @@ int qaoa_init_graph(qaoa_ctx** out, int n, int m, const int32_t* u, const int32_
   if (m < 0 || (m > 0 && (!u || !v || !w))) return fail(QAOA_EINVAL, "bad edge arrays");
   if (!(weight_scale > 0.0) || !std::isfinite(weight_scale)) return fail(QAOA_EINVAL, "weight_scale must be > 0");
   if (cost_mode < QAOA_COST_AUTO || cost_mode > QAOA_COST_STREAM) return fail(QAOA_EINVAL, "bad cost_mode");
-  std::set<std::pair<int, int>> seen;
+  std::vector<int32_t> wmat;
   long long W = 0, pos = 0, neg = 0;
-  for (int e = 0; e < m; ++e) {
-    if (u[e] < 0 || u[e] >= n || v[e] < 0 || v[e] >= n) return fail(QAOA_EINVAL, "edge vertex out of range");
-    if (u[e] == v[e]) return fail(QAOA_EINVAL, "self loop");
-    if (w[e] == 0) return fail(QAOA_EINVAL, "zero weight");
-    auto key = std::make_pair(std::min(u[e], v[e]), std::max(u[e], v[e]));
-    if (!seen.insert(key).second) return fail(QAOA_EINVAL, "repeated edge");
-    W += w[e];
-    if (w[e] > 0) pos += w[e]; else neg += w[e];
-    if (pos - neg > kMaxAbsWeightSum) return fail(QAOA_EINVAL, "sum of |w| exceeds 2^20");
+  {
+    const std::string why = check_graph(n, m, u, v, w, kMaxAbsWeightSum, wmat, W, neg, pos);
+    if (!why.empty()) return fail(QAOA_EINVAL, why);
   }
   if (state_dev && state_bytes != sb)
     return fail(QAOA_ENOMEM, "state buffer size must equal qaoa_state_bytes(n, precision)");
@@ -853,11 +669,7 @@ int qaoa_init_graph(qaoa_ctx** out, int n, int m, const int32_t* u, const int32_
   c->u.assign(u, u + m);
   c->v.assign(v, v + m);
   c->w.assign(w, w + m);
-  c->wmat.assign((size_t)n * n, 0);
-  for (int e = 0; e < m; ++e) {
-    c->wmat[u[e] * n + v[e]] = w[e];
-    c->wmat[v[e] * n + u[e]] = w[e];
-  }
+  c->wmat = std::move(wmat);
   c->W = W;
   c->c_lo = neg;
   c->c_hi = pos;

@@ -1,0 +1,208 @@
+// desc.cu -- pass descriptors and per-round cost tables (see desc.h).
+#include "desc.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <set>
+
+namespace qaoa {
+
+namespace {
+
+// Cost tables of one round (recompute mode), for tile bits at global
+// positions pos[] and the round's register / lane / warp split:
+//   CQ[q]     = sum_{k<l in Q} w [q_k != q_l]          (q: lane bits, then warp bits)
+//   AJ[q][i]  = sum_{k in Q, q_k = 1} w[reg_i][k]
+//   D[i]      = sum_{k in Q} w[reg_i][k]
+//   CP[j]     = sum_{i<i'} w[reg_i][reg_i'] [j_i != j_i']
+std::vector<int32_t> build_round_tables(const int32_t* wmat, int n, const TileShape& sh, const int8_t* pos,
+                                        const RoundDev& rd) {
+  const int R = sh.R, WB = sh.WB, QB = 5 + WB;
+  const int QN = 1 << QB;
+  auto W = [&](int tj, int tk) { return wmat[pos[tj] * n + pos[tk]]; };
+  int qbits[16];
+  for (int i = 0; i < 5; ++i) qbits[i] = rd.lane[i];
+  for (int i = 0; i < WB; ++i) qbits[5 + i] = rd.warp[i];
+  std::vector<int32_t> t(QN + QN * R + R + (1 << R));
+  for (int q = 0; q < QN; ++q) {
+    int cq = 0;
+    for (int k = 0; k < QB; ++k)
+      for (int l = k + 1; l < QB; ++l)
+        if ((q >> k & 1) != (q >> l & 1)) cq += W(qbits[k], qbits[l]);
+    t[q] = cq;
+    for (int i = 0; i < R; ++i) {
+      int a = 0;
+      for (int k = 0; k < QB; ++k)
+        if (q >> k & 1) a += W(rd.reg[i], qbits[k]);
+      t[QN + q * R + i] = a;
+    }
+  }
+  for (int i = 0; i < R; ++i) {
+    int d = 0;
+    for (int k = 0; k < QB; ++k) d += W(rd.reg[i], qbits[k]);
+    t[QN + QN * R + i] = d;
+  }
+  for (int j = 0; j < (1 << R); ++j) {
+    int cp = 0;
+    for (int i = 0; i < R; ++i)
+      for (int i2 = i + 1; i2 < R; ++i2)
+        if ((j >> i & 1) != (j >> i2 & 1)) cp += W(rd.reg[i], rd.reg[i2]);
+    t[QN + QN * R + R + j] = cp;
+  }
+  return t;
+}
+
+// Global index bits of a round's register / lane / warp tile bits.
+void fill_round_globals(RoundDev& rd, const int8_t* pos) {
+  for (int i = 0; i < 5; ++i) rd.greg[i] = pos[rd.reg[i]];
+  for (int i = 0; i < 5; ++i) rd.glane[i] = pos[rd.lane[i]];
+  for (int i = 0; i < 4; ++i) rd.gwarp[i] = pos[rd.warp[i]];
+}
+
+void to_round_dev(const RoundPlan& rp, RoundDev& rd) {
+  memcpy(rd.reg, rp.reg, 5);
+  memcpy(rd.lane, rp.lane, 5);
+  memcpy(rd.warp, rp.warp, 4);
+  rd.mixA = rp.mixA;
+  rd.cost = rp.cost;
+  rd.mixB = rp.mixB;
+  rd.reduce = rp.reduce;
+  rd.src = rp.src;
+  rd.dst = rp.dst;
+  rd.lam = rp.lam;
+  rd.layout = rp.layout;
+  rd.ctab = -1;
+}
+
+}  // namespace
+
+int32_t TableStore::offset(const int32_t* wmat, int n, const TileShape& sh, const int8_t* pos, const RoundDev& rd) {
+  std::vector<int8_t> key(pos, pos + sh.T());
+  key.insert(key.end(), rd.reg, rd.reg + 5);
+  key.insert(key.end(), rd.lane, rd.lane + 5);
+  key.insert(key.end(), rd.warp, rd.warp + 4);
+  auto k = std::make_pair(sh.R * 100 + sh.WB, key);
+  auto it = index.find(k);
+  if (it != index.end()) return it->second;
+  std::vector<int32_t> t = build_round_tables(wmat, n, sh, pos, rd);
+  const int32_t off = (int32_t)h.size();
+  h.insert(h.end(), t.begin(), t.end());
+  index[k] = off;
+  dirty = true;
+  return off;
+}
+
+std::string check_graph(int n, int m, const int32_t* u, const int32_t* v, const int32_t* w, long long max_abs,
+                        std::vector<int32_t>& wmat, long long& W, long long& c_lo, long long& c_hi) {
+  if (m < 0 || (m > 0 && (!u || !v || !w))) return "bad edge arrays";
+  std::set<std::pair<int, int>> seen;
+  W = 0;
+  c_lo = 0;
+  c_hi = 0;
+  for (int e = 0; e < m; ++e) {
+    if (u[e] < 0 || u[e] >= n || v[e] < 0 || v[e] >= n) return "edge vertex out of range";
+    if (u[e] == v[e]) return "self loop";
+    if (w[e] == 0) return "zero weight";
+    auto key = std::make_pair(std::min(u[e], v[e]), std::max(u[e], v[e]));
+    if (!seen.insert(key).second) return "repeated edge";
+    W += w[e];
+    if (w[e] > 0) c_hi += w[e]; else c_lo += w[e];
+    if (c_hi - c_lo > max_abs) return "sum of |w| exceeds 2^20";
+  }
+  wmat.assign((size_t)n * n, 0);
+  for (int e = 0; e < m; ++e) {
+    wmat[u[e] * n + v[e]] = w[e];
+    wmat[v[e] * n + u[e]] = w[e];
+  }
+  return "";
+}
+
+BitRuns make_runs(const std::vector<int>& bits) {
+  BitRuns r;
+  memset(&r, 0, sizeof r);
+  int k = 0;
+  for (size_t i = 0; i < bits.size();) {
+    size_t j = i;
+    while (j + 1 < bits.size() && bits[j + 1] == bits[j] + 1) ++j;
+    r.src[k] = int8_t(i);
+    r.dst[k] = int8_t(bits[i]);
+    r.len[k] = int8_t(j - i + 1);
+    ++k;
+    i = j + 1;
+  }
+  r.n = int8_t(k);
+  return r;
+}
+
+void mixer_coeffs(double beta, bool fast, double* tau, double* alpha) {
+  if (fast) { *tau = tan(beta); *alpha = 1.0; }
+  else { *tau = sin(beta); *alpha = cos(beta); }
+}
+
+std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInputs& in, TableStore& tabs,
+                          PassDev& pd, bool& fast) {
+  const int T = sh.T();
+  memset(&pd, 0, sizeof pd);
+  pd.n = in.n;
+  pd.T = T;
+  pd.nsub = (int)pp.subs.size();
+  if (pd.nsub > kMaxSubDev) return "plan has too many sub-passes";
+  pd.nouter = (int)pp.outer.size();
+  for (int i = 0; i < pd.nouter; ++i) pd.outer[i] = (int8_t)pp.outer[i];
+  pd.outer_runs = make_runs(pp.outer);
+  pd.n_units = 1ull << pd.nouter;
+  const double ba = pp.layer_a >= 0 ? in.beta[pp.layer_a] : 0.0;
+  const double bb = pp.layer_b >= 0 ? in.beta[pp.layer_b] : 0.0;
+  fast = !in.plain && fabs(cos(ba)) >= fabs(sin(ba)) && fabs(cos(bb)) >= fabs(sin(bb));
+  mixer_coeffs(ba, fast, &pd.tauA, &pd.alphaA);
+  mixer_coeffs(bb, fast, &pd.tauB, &pd.alphaB);
+  pd.amp0 = in.adjoint ? 0.0 : pow(2.0, -0.5 * in.n);
+  pd.c_lo = (int32_t)in.c_lo;
+  pd.ncost = (int32_t)in.ncost;
+  pd.wsum = (int32_t)in.W;
+  pd.cA = cos(ba);
+  pd.cB = cos(bb);
+  pd.ftauA = float(pd.tauA);
+  pd.falphaA = float(pd.alphaA);
+  pd.ftauB = float(pd.tauB);
+  pd.falphaB = float(pd.alphaB);
+  pd.fcA = float(pd.cA);
+  pd.fcB = float(pd.cB);
+  for (int s = 0; s < pd.nsub; ++s) {
+    const SubPassPlan& sp = pp.subs[s];
+    SubDev& sd = pd.sub[s];
+    for (int j = 0; j < T; ++j) sd.pos[j] = sp.pos[j];
+    std::vector<int> inner;
+    for (int b : pp.sb) {
+      bool in_tile = false;
+      for (int j = 0; j < T; ++j) in_tile |= sp.pos[j] == b;
+      if (!in_tile) inner.push_back(b);
+    }
+    sd.ninner = (int)inner.size();
+    for (int i = 0; i < sd.ninner; ++i) sd.inner[i] = (int8_t)inner[i];
+    sd.inner_runs = make_runs(inner);
+    sd.nrounds = (int)sp.rounds.size();
+    if (sd.nrounds > kMaxRoundsDev) return "plan has too many rounds";
+    sd.needs_c = sp.needs_c;
+    sd.store = sp.store;
+    if (in.adjoint) {
+      sd.scale = 1.0;
+    } else {
+      sd.init = sp.init;
+      sd.keep = s + 1 < pd.nsub;
+      sd.scale = fast ? pow(cos(ba), sp.nA) * pow(cos(bb), sp.nB) : 1.0;
+    }
+    sd.fscale = float(sd.scale);
+    sd.rescale = sd.scale != 1.0;
+    for (int r = 0; r < sd.nrounds; ++r) {
+      to_round_dev(sp.rounds[r], sd.rd[r]);
+      fill_round_globals(sd.rd[r], sd.pos);
+      const bool wants = in.adjoint ? (sd.rd[r].cost || sd.rd[r].lam) : (sd.rd[r].cost || sd.rd[r].reduce);
+      if (wants && !in.stream) sd.rd[r].ctab = tabs.offset(in.wmat, in.n, sh, sd.pos, sd.rd[r]);
+    }
+  }
+  return "";
+}
+
+}  // namespace qaoa

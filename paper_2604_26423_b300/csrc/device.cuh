@@ -40,6 +40,8 @@ struct SubDev {
   int32_t nrounds;
   double scale;            // product of butterfly normalisations applied here
   uint8_t init, needs_c, store, keep, pad[4];  // keep: a later sub-pass reads this one's output
+  float fscale;            // scale rounded to fp32 (complex64 kernels)
+  int32_t rescale;         // scale != 1
   RoundDev rd[kMaxRoundsDev];
 };
 
@@ -56,6 +58,7 @@ struct PassDev {
   int32_t wsum;            // W = sum of the weights (h(x) = W - 2 C(x))
   int32_t pad0;
   double cA, cB;           // cos(beta) of layers a / b (adjoint per-round rescaling)
+  float ftauA, falphaA, ftauB, falphaB, fcA, fcB;  // the same rounded to fp32
   SubDev sub[kMaxSubDev];
 };
 
@@ -93,6 +96,12 @@ __device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
 __device__ __forceinline__ void st_hint(double2* a, double2 v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
 }
+
+// fp32 kernels take the host-rounded fp32 copies of the pass coefficients (no
+// fp64 conversions in the kernels); fp64 kernels the doubles.
+template <typename Real> __device__ __forceinline__ Real pick(double d, float f);
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
 template <typename Real> struct Cx;
 template <> struct Cx<float> { using T = float2; };

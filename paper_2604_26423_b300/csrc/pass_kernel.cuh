@@ -203,7 +203,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     smem_load<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp), v);
   }
 
-  apply_mixer<R>(v, rd.mixA, Real(P.tauA), Real(P.alphaA), FAST);
+  apply_mixer<R>(v, rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA), FAST);
 
   if (rd.cost | rd.reduce) {
     // C(x) of register amplitude j: streamed from the diagonal, or
@@ -229,15 +229,15 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     };
     if (rd.cost) {
       for_costs([&](int j, int c) {
-        const C2 ph = phase[min(max(c - P.c_lo, 0), P.ncost - 1)];
+        const C2 ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
         const Real xr = v[j].x, xi = v[j].y;
         v[j].x = xr * ph.x - xi * ph.y;
         v[j].y = xr * ph.y + xi * ph.x;
       });
     }
-    apply_mixer<R>(v, rd.mixB, Real(P.tauB), Real(P.alphaB), FAST);
-    if (rd.dst == DST_GLOBAL_D && sp.scale != 1.0) {
-      const Real sc = Real(sp.scale);
+    apply_mixer<R>(v, rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB), FAST);
+    if (rd.dst == DST_GLOBAL_D && sp.rescale) {
+      const Real sc = pick<Real>(sp.scale, sp.fscale);
 #pragma unroll
       for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
     }
@@ -257,9 +257,9 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       if (lane == 0) { wacc[2 * warp] += dn; wacc[2 * warp + 1] += dc; }
     }
   } else {
-    apply_mixer<R>(v, rd.mixB, Real(P.tauB), Real(P.alphaB), FAST);
-    if (rd.dst == DST_GLOBAL_D && sp.scale != 1.0) {
-      const Real sc = Real(sp.scale);
+    apply_mixer<R>(v, rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB), FAST);
+    if (rd.dst == DST_GLOBAL_D && sp.rescale) {
+      const Real sc = pick<Real>(sp.scale, sp.fscale);
 #pragma unroll
       for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
     }
@@ -276,6 +276,55 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     }
   } else {
     smem_store<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp), v);
+  }
+}
+
+// One super-tile (unit) of a forward pass: every tile of each of its sub-passes.
+// All threads of the CTA take part; shared memory is free again on return.
+template <typename Real, int R, int WB, bool FAST>
+__device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, uint64_t unit,
+                                         typename Cx<Real>::T* tile, int* tconst,
+                                         const typename Cx<Real>::T* phase, double* wacc) {
+  using C2 = typename Cx<Real>::T;
+  constexpr int T = R + 5 + WB;
+  constexpr int NT = 32 << WB;
+  constexpr int AB = sizeof(C2);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = P.n;
+  const bool stream = A.diag != nullptr;
+  C2 v[1 << R];
+  const uint64_t ubase = P.outer_runs.scatter(unit);
+  for (int s = 0; s < P.nsub; ++s) {
+    const SubDev& sp = P.sub[s];
+    const uint64_t ntiles = 1ull << sp.ninner;
+    for (uint64_t ti = 0; ti < ntiles; ++ti) {
+      const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
+      // issue the tile's global loads first: their latency overlaps the
+      // barrier below and the tile constants
+      if (sp.rd[0].src == SRC_GLOBAL_D) {
+        const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp);
+        const C2* gs = reinterpret_cast<const C2*>(A.state);
+        if (A.l2hint) {
+          const uint64_t pol = l2_policy_evict_first();
+          gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = ld_hint(q, pol); });
+        } else {
+          gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = __ldcg(q); });
+        }
+      }
+      __syncthreads();  // previous tile finished with shared memory
+      if (sp.needs_c && !stream) {
+        if (tid == 0) tconst[16] = 0;
+        __syncthreads();
+        tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
+        __syncthreads();
+      }
+      for (int r = 0; r < sp.nrounds; ++r) {
+        const RoundDev& rd = sp.rd[r];
+        if (rd.src == SRC_SMEM_D) __syncthreads();
+        fwd_round<Real, R, WB, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, wacc, v);
+      }
+    }
+    __syncthreads();  // sub-pass boundary: this CTA's global writes are visible to it
   }
 }
 
@@ -296,52 +345,16 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   C2* ptab = reinterpret_cast<C2*>(smem_raw + ((size_t(TILE) * AB + 32 * 4 + 15) & ~size_t(15)));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n = P.n;
   const C2* phase = reinterpret_cast<const C2*>(A.phase);
   if (A.phase_in_smem && A.phase) {
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
     phase = ptab;
   }
-  const bool stream = A.diag != nullptr;
   __shared__ double wacc[2 * NT / 32];  // per-warp reduction slots
   if (lane == 0) { wacc[2 * warp] = 0.0; wacc[2 * warp + 1] = 0.0; }
-  C2 v[1 << R];
 
-  for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
-    const uint64_t ubase = P.outer_runs.scatter(unit);
-    for (int s = 0; s < P.nsub; ++s) {
-      const SubDev& sp = P.sub[s];
-      const uint64_t ntiles = 1ull << sp.ninner;
-      for (uint64_t ti = 0; ti < ntiles; ++ti) {
-        const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
-        // issue the tile's global loads first: their latency overlaps the
-        // barrier below and the tile constants
-        if (sp.rd[0].src == SRC_GLOBAL_D) {
-          const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp);
-          const C2* gs = reinterpret_cast<const C2*>(A.state);
-          if (A.l2hint) {
-            const uint64_t pol = l2_policy_evict_first();
-            gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = ld_hint(q, pol); });
-          } else {
-            gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = __ldcg(q); });
-          }
-        }
-        __syncthreads();  // previous tile finished with shared memory
-        if (sp.needs_c && !stream) {
-          if (tid == 0) tconst[16] = 0;
-          __syncthreads();
-          tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
-          __syncthreads();
-        }
-        for (int r = 0; r < sp.nrounds; ++r) {
-          const RoundDev& rd = sp.rd[r];
-          if (rd.src == SRC_SMEM_D) __syncthreads();
-          fwd_round<Real, R, WB, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, wacc, v);
-        }
-      }
-      __syncthreads();  // sub-pass boundary: this CTA's global writes are visible to it
-    }
-  }
+  for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
+    fwd_unit<Real, R, WB, FAST>(P, A, unit, tile, tconst, phase, wacc);
 
   if (A.partial) {
     // block sum of the per-warp FP64 partials, in warp order

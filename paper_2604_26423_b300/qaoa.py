@@ -27,7 +27,9 @@ _ERRNAME = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE"}
 EXPORTS = ("qaoa_state_bytes", "qaoa_aux_bytes", "qaoa_init_graph", "qaoa_run", "qaoa_run_angles",
            "qaoa_expect", "qaoa_sample", "qaoa_grad", "qaoa_grad_angles", "qaoa_cost_diag",
            "qaoa_state_ptr", "qaoa_describe_plan", "qaoa_profile_enable", "qaoa_profile_read",
-           "qaoa_last_error", "qaoa_free")
+           "qaoa_last_error", "qaoa_free", "qaoa_sample_state_noalloc",
+           "qaoa_batch_create", "qaoa_batch_run", "qaoa_batch_results", "qaoa_batch_state",
+           "qaoa_batch_describe", "qaoa_batch_bytes", "qaoa_batch_last_error", "qaoa_batch_free")
 PROFILE_KINDS = {"pass": 0, "adjoint": 1, "cost": 2, "sample": 3, "small": 4}
 
 _lib = None
@@ -78,6 +80,18 @@ def load():
     lib.qaoa_last_error.restype = ctypes.c_char_p
     lib.qaoa_free.argtypes = [vp]
     lib.qaoa_free.restype = None
+    lib.qaoa_batch_create.argtypes = [P(vp), ctypes.c_int, i32p, i32p, i64p, i32p, i32p, i32p, f64p, f64p,
+                                      ctypes.c_double, ctypes.c_int, vp, vp]
+    lib.qaoa_batch_run.argtypes = [vp]
+    lib.qaoa_batch_results.argtypes = [vp, f64p, f64p]
+    lib.qaoa_batch_state.argtypes = [vp, ctypes.c_int, P(vp)]
+    lib.qaoa_batch_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.qaoa_batch_bytes.argtypes = [vp]
+    lib.qaoa_batch_bytes.restype = ctypes.c_double
+    lib.qaoa_batch_last_error.argtypes = [vp]
+    lib.qaoa_batch_last_error.restype = ctypes.c_char_p
+    lib.qaoa_batch_free.argtypes = [vp]
+    lib.qaoa_batch_free.restype = None
     _lib = lib
     return lib
 
@@ -269,3 +283,109 @@ class Simulator:
         """The state vector (torch complex tensor on the GPU, shares memory)."""
         self.stream.synchronize()
         return self._state_t
+
+
+class BatchOpts(ctypes.Structure):
+    """Scheduling knobs of ``qaoa_batch_create`` (0 = library default)."""
+    _fields_ = [("solo_max_n", ctypes.c_int), ("window_items", ctypes.c_int), ("window_mb", ctypes.c_int),
+                ("max_units", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
+BATCH_FIELDS = ("exp_c", "r", "norm", "c_min", "c_max", "argmin", "argmax", "d_dgamma", "d_dbeta")
+
+
+class Batch:
+    """Many independent LR-QAOA instances (complex64) run by one persistent
+    kernel per phase, replayed from a CUDA graph (``qaoa_batch_*``).
+
+    ``instances``: dicts with keys n, p, dgamma, dbeta, u, v, w (the shape
+    ``inputs.batch_instances`` returns). ``opts``: dict of ``BatchOpts`` fields.
+    """
+
+    def __init__(self, instances, scale=0.1, with_grad=False, opts=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise QaoaError(QAOA_ECUDA, "no CUDA device")
+        self._lib = load()
+        self.count = len(instances)
+        self.with_grad = bool(with_grad)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.n = np.array([d["n"] for d in instances], dtype=np.int32)
+        self.p = np.array([d["p"] for d in instances], dtype=np.int32)
+        off = np.zeros(self.count + 1, dtype=np.int64)
+        off[1:] = np.cumsum([len(d["u"]) for d in instances])
+        cat = lambda k: (np.ascontiguousarray(np.concatenate([np.asarray(d[k], dtype=np.int32) for d in instances]))
+                         if off[-1] else np.zeros(1, dtype=np.int32))
+        u, v, w = cat("u"), cat("v"), cat("w")
+        dg = np.array([d["dgamma"] for d in instances], dtype=np.float64)
+        db = np.array([d["dbeta"] for d in instances], dtype=np.float64)
+        o = BatchOpts(**(opts or {}))
+        P = ctypes.POINTER
+        ip = lambda a: a.ctypes.data_as(P(ctypes.c_int32))
+        h = ctypes.c_void_p()
+        rc = self._lib.qaoa_batch_create(ctypes.byref(h), self.count, ip(self.n), ip(self.p),
+                                         off.ctypes.data_as(P(ctypes.c_int64)), ip(u), ip(v), ip(w),
+                                         dg.ctypes.data_as(P(ctypes.c_double)), db.ctypes.data_as(P(ctypes.c_double)),
+                                         float(scale), int(self.with_grad), ctypes.byref(o),
+                                         ctypes.c_void_p(self.stream.cuda_stream))
+        if rc != QAOA_OK:
+            raise QaoaError(rc, self._lib.qaoa_batch_last_error(None).decode())
+        self._h = h
+        self._gsz = int(2 * self.p.sum())
+
+    def _check(self, rc):
+        if rc != QAOA_OK:
+            raise QaoaError(rc, self._lib.qaoa_batch_last_error(self._h).decode())
+
+    def run(self):
+        self._check(self._lib.qaoa_batch_run(self._h))
+
+    def results(self) -> dict:
+        out = np.zeros(9 * self.count)
+        g = np.zeros(max(1, self._gsz))
+        self._check(self._lib.qaoa_batch_results(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 g.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        out = out.reshape(self.count, 9)
+        res = {k: out[:, i].copy() for i, k in enumerate(BATCH_FIELDS)}
+        splits = np.cumsum(2 * self.p)[:-1]
+        res["grads"] = [(a[:len(a) // 2], a[len(a) // 2:]) for a in np.split(g[:self._gsz], splits)]
+        return res
+
+    def state(self, i: int):
+        """Copy of instance i's final state as a torch complex64 tensor (forward batches)."""
+        import torch
+        ptr = ctypes.c_void_p()
+        self._check(self._lib.qaoa_batch_state(self._h, int(i), ctypes.byref(ptr)))
+        n = int(self.n[i])
+
+        class _View:  # the library's buffer, seen through the CUDA array interface
+            __cuda_array_interface__ = {"shape": (1 << n,), "typestr": "<c8", "data": (ptr.value, True),
+                                        "version": 2, "strides": None}
+
+        self.stream.synchronize()
+        return torch.as_tensor(_View(), device="cuda").clone()
+
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(512)
+        self._lib.qaoa_batch_describe(self._h, buf, 512)
+        return buf.value.decode()
+
+    def bytes(self) -> float:
+        return float(self._lib.qaoa_batch_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.qaoa_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,80 @@
+"""CPU tests of qaoa_batch_create's argument checks (they run before any CUDA
+call) and of the batch workload generator."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2604_26423_b300 import build, inputs, qaoa
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_library()
+    return qaoa.load()
+
+
+def _create(lib, n, p, edges, dg=None, db=None, scale=0.1):
+    count = len(n)
+    n = np.asarray(n, dtype=np.int32)
+    p = np.asarray(p, dtype=np.int32)
+    off = np.zeros(count + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(e) for e in edges])
+    flat = [x for e in edges for x in e] or [(0, 1, 1)]
+    u = np.array([x[0] for x in flat], dtype=np.int32)
+    v = np.array([x[1] for x in flat], dtype=np.int32)
+    w = np.array([x[2] for x in flat], dtype=np.int32)
+    dg = np.full(count, 0.6) if dg is None else np.asarray(dg, dtype=np.float64)
+    db = np.full(count, 0.3) if db is None else np.asarray(db, dtype=np.float64)
+    P = ctypes.POINTER
+    ip = lambda a: a.ctypes.data_as(P(ctypes.c_int32))
+    h = ctypes.c_void_p()
+    rc = lib.qaoa_batch_create(ctypes.byref(h), count, ip(n), ip(p), off.ctypes.data_as(P(ctypes.c_int64)),
+                               ip(u), ip(v), ip(w), dg.ctypes.data_as(P(ctypes.c_double)),
+                               db.ctypes.data_as(P(ctypes.c_double)), scale, 0, None, None)
+    return rc, lib.qaoa_batch_last_error(None).decode()
+
+
+@pytest.mark.parametrize("case,expect", [
+    (dict(n=[1], p=[1], edges=[[]]), "n out of"),
+    (dict(n=[25], p=[1], edges=[[(0, 1, 1)]]), "n out of"),
+    (dict(n=[4], p=[0], edges=[[(0, 1, 1)]]), "p out of"),
+    (dict(n=[4], p=[65], edges=[[(0, 1, 1)]]), "p out of"),
+    (dict(n=[4, 4], p=[1, 1], edges=[[(0, 1, 1)], [(2, 2, 1)]]), "self loop"),
+    (dict(n=[4], p=[1], edges=[[(0, 4, 1)]]), "out of range"),
+    (dict(n=[4], p=[1], edges=[[(0, 1, 1), (1, 0, 2)]]), "repeated edge"),
+    (dict(n=[4], p=[1], edges=[[(0, 1, 0)]]), "zero weight"),
+    (dict(n=[4], p=[1], edges=[[(0, 1, 1)]], dg=[np.nan]), "finite"),
+    (dict(n=[4], p=[1], edges=[[(0, 1, 1)]], scale=0.0), "weight_scale"),
+])
+def test_create_rejects(lib, case, expect):
+    rc, msg = _create(lib, **case)
+    assert rc == qaoa.QAOA_EINVAL
+    assert expect in msg
+
+
+def test_create_rejects_null_output(lib):
+    n = np.array([4], dtype=np.int32)
+    rc = lib.qaoa_batch_create(None, 1, n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None, None, None, None,
+                               None, None, None, 0.1, 0, None, None)
+    assert rc == qaoa.QAOA_EINVAL
+
+
+def test_batch_instances_shape():
+    b = inputs.batch_instances(300, 7)
+    assert len(b) == 300
+    kinds = [d["kind"] for d in b]
+    assert kinds.count("complete") == kinds.count("chain") == kinds.count("3-regular") == 100
+    for d in b:
+        assert 10 <= d["n"] <= 22 and 1 <= d["p"] <= 10
+        assert 0.2 <= d["dgamma"] <= 1.2 and 0.1 <= d["dbeta"] <= 0.6
+        m = len(d["u"])
+        if d["kind"] == "complete":
+            assert m == d["n"] * (d["n"] - 1) // 2
+        elif d["kind"] == "chain":
+            assert m == d["n"] - 1
+        else:
+            assert d["n"] % 2 == 0 and m == 3 * d["n"] // 2
+            deg = np.bincount(np.concatenate([d["u"], d["v"]]), minlength=d["n"])
+            assert (deg == 3).all()
+        assert ((np.asarray(d["w"]) >= 1) & (np.asarray(d["w"]) <= 10)).all()

@@ -1,0 +1,147 @@
+"""Batched instances (qaoa_batch_*) against the single-instance path and the
+oracle: every instance of a mixed batch must give the <C>, r, norm, extremes,
+state and adjoint gradient that qaoa_init_graph / qaoa_run / qaoa_grad give
+for it alone (same kernels' arithmetic, different scheduling), and the oracle
+on the sizes it finishes quickly."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_26423_b300 import inputs
+from paper_2604_26423_b300.qaoa import Batch, Simulator
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed(seed, ns, ps, dbeta=0.3):
+    out = []
+    for i, (n, p) in enumerate(zip(ns, ps)):
+        kind = i % 3
+        if kind == 0:
+            u, v, w = inputs.complete_graph(n, seed + i)
+        elif kind == 1:
+            u, v, w = inputs.chain_graph(n, seed + i)
+        else:
+            n += n % 2
+            u, v, w = inputs.regular3_graph(n, seed + i)
+        out.append(dict(n=n, p=p, dgamma=0.4 + 0.05 * i % 0.8, dbeta=dbeta + 0.01 * (i % 7), u=u, v=v, w=w))
+    return out
+
+
+def _single(d, with_grad=False):
+    with Simulator(d["n"], d["u"], d["v"], d["w"], 0.1, "c64", with_grad=with_grad) as s:
+        s.run(d["p"], d["dgamma"], d["dbeta"])
+        r = s.expect()
+        r["state"] = s.state().cpu().numpy()
+        if with_grad:
+            r["grad"] = s.grad(d["p"], d["dgamma"], d["dbeta"])
+        return r
+
+
+NS = [4, 9, 12, 13, 14, 15, 16, 17, 18, 19, 20, 13, 16, 10, 11, 12, 18, 14]
+PS = [1, 3, 5, 2, 4, 1, 3, 2, 5, 1, 2, 6, 1, 7, 2, 3, 1, 4]
+
+
+@pytest.mark.parametrize("opts", [None, dict(solo_max_n=13, max_units=1), dict(solo_max_n=20, window_items=4)])
+def test_batch_forward_matches_single_path(opts):
+    batch = _mixed(11, NS, PS)
+    with Batch(batch, opts=opts) as b:
+        b.run()
+        res = b.results()
+        for i, d in enumerate(batch):
+            ref = _single(d)
+            assert res["c_min"][i] == ref["c_min"] and res["c_max"][i] == ref["c_max"], i
+            assert res["argmin"][i] == ref["argmin"] and res["argmax"][i] == ref["argmax"], i
+            assert abs(res["exp_c"][i] - ref["exp_c"]) <= 1e-6 * max(1.0, abs(ref["exp_c"])), (i, d["n"])
+            assert abs(res["r"][i] - ref["r"]) <= 1e-6, i
+            assert abs(res["norm"][i] - ref["norm"]) <= 1e-6, i
+            st = b.state(i).cpu().numpy()
+            err = np.linalg.norm(st - ref["state"])
+            assert err <= 2e-6, (i, d["n"], err)
+
+
+def test_batch_forward_matches_oracle_small():
+    batch = _mixed(23, [5, 8, 10, 12, 13, 14], [2, 3, 1, 2, 3, 2])
+    with Batch(batch, opts=dict(solo_max_n=14)) as b:
+        b.run()
+        res = b.results()
+        for i, d in enumerate(batch):
+            o = oracle.run(d["n"], d["u"], d["v"], d["w"], 0.1, *oracle.lr_schedule(d["p"], d["dgamma"], d["dbeta"]))
+            assert abs(res["exp_c"][i] - o["exp_c"]) <= 2e-5 * abs(o["exp_c"]), i
+            assert abs(res["r"][i] - o["r"]) <= 2e-5, i
+            assert res["c_max"][i] == o["c_max"] and res["c_min"][i] == o["c_min"], i
+            psi = b.state(i).cpu().numpy().astype(np.complex128)
+            assert np.linalg.norm(psi - o["psi"]) <= 1e-5, i
+
+
+@pytest.mark.parametrize("opts", [None, dict(solo_max_n=13, max_units=2)])
+def test_batch_gradient_matches_single_path(opts):
+    batch = _mixed(31, [5, 11, 12, 13, 14, 16, 17, 18], [3, 2, 4, 2, 3, 2, 1, 3])
+    with Batch(batch, with_grad=True, opts=opts) as b:
+        b.run()
+        res = b.results()
+        for i, d in enumerate(batch):
+            ref = _single(d, with_grad=True)
+            g = ref["grad"]
+            gg, gb = res["grads"][i]
+            scale = max(1.0, np.abs(g["g_gamma"]).max(), np.abs(g["g_beta"]).max())
+            assert np.abs(gg - g["g_gamma"]).max() <= 2e-4 * scale, (i, d["n"])
+            assert np.abs(gb - g["g_beta"]).max() <= 2e-4 * scale, (i, d["n"])
+            assert abs(res["d_dgamma"][i] - g["d_dgamma"]) <= 2e-4 * scale, i
+            assert abs(res["d_dbeta"][i] - g["d_dbeta"]) <= 2e-4 * scale, i
+            assert abs(res["exp_c"][i] - ref["exp_c"]) <= 1e-6 * abs(ref["exp_c"]), i
+
+
+def test_batch_gradient_matches_oracle_finite_difference():
+    batch = _mixed(41, [6, 12, 13], [2, 3, 2])
+    with Batch(batch, with_grad=True, opts=dict(solo_max_n=13)) as b:
+        b.run()
+        res = b.results()
+    for i, d in enumerate(batch):
+        g, bt = oracle.lr_schedule(d["p"], d["dgamma"], d["dbeta"])
+        fd = oracle.lr_chain(*oracle.grad_fd(d["n"], d["u"], d["v"], d["w"], 0.1, g, bt))
+        assert abs(res["d_dgamma"][i] - fd[0]) <= 1e-3 * max(1.0, abs(fd[0])), (i, fd)
+        assert abs(res["d_dbeta"][i] - fd[1]) <= 1e-3 * max(1.0, abs(fd[1])), (i, fd)
+
+
+def test_batch_plain_mixer_form():
+    # dbeta = 1.3: beta_0 = 1.3 has |tan| > 1, so the whole batch takes the cos/sin form
+    batch = _mixed(51, [8, 13, 15, 17], [2, 2, 3, 2], dbeta=1.3)
+    with Batch(batch, with_grad=True) as b:
+        assert "fast=0" in b.describe()
+        b.run()
+        res = b.results()
+        for i, d in enumerate(batch):
+            ref = _single(d, with_grad=True)
+            assert abs(res["exp_c"][i] - ref["exp_c"]) <= 1e-6 * abs(ref["exp_c"]), i
+            assert abs(res["d_dbeta"][i] - ref["grad"]["d_dbeta"]) <= 2e-4 * max(1, abs(ref["grad"]["d_dbeta"])), i
+
+
+def test_batch_replays_are_identical():
+    batch = _mixed(61, [10, 14, 17, 19, 21], [3, 2, 4, 2, 1])
+    with Batch(batch, with_grad=True, opts=dict(solo_max_n=15)) as b:
+        b.run()
+        r1 = b.results()
+        b.run()
+        b.run()
+        r2 = b.results()
+    for k in ("exp_c", "r", "norm", "d_dgamma", "d_dbeta"):
+        assert np.array_equal(r1[k], r2[k]), k
+
+
+def test_batch_workload_sample_matches_single_path():
+    # the 4096-instance mix (n 10..22, p 1..10, K_n / chain / 3-regular): every
+    # instance's extremes and r checked for validity, a sample against the
+    # single-instance path
+    batch = inputs.batch_instances(4096, 2604)
+    with Batch(batch, with_grad=False) as b:
+        b.run()
+        res = b.results()
+    assert np.all(np.abs(res["norm"] - 1.0) <= 1e-4)
+    assert np.all((res["r"] >= -1e-6) & (res["r"] <= 1 + 1e-6))
+    rng = np.random.default_rng(5)
+    for i in rng.choice(4096, 48, replace=False):
+        d = batch[i]
+        ref = _single(d)
+        assert res["c_max"][i] == ref["c_max"] and res["c_min"][i] == ref["c_min"], i
+        assert abs(res["exp_c"][i] - ref["exp_c"]) <= 1e-6 * abs(ref["exp_c"]), (i, d["n"], d["p"])
