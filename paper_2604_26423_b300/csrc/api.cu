@@ -76,7 +76,7 @@ struct qaoa_ctx {
   size_t aux_bytes = 0;
   DevBuf aux_own;
   DevBuf d_wmat, d_ctabs, d_phase, d_partial, d_result, d_ext, d_ext_part;
-  DevBuf d_sums, d_pre, d_shots, d_uni, d_ang;
+  DevBuf d_sums, d_pre, d_pre2, d_shots, d_uni, d_ang;
   DevBuf d_lambda, d_gacc;                                            // adjoint vector (if no aux), per-pass sums
   TableStore tabs;                                                     // host copy of all cost tables
   std::map<int, std::unique_ptr<Plan>> plans;                         // forward plans by p
@@ -232,9 +232,9 @@ const Plan* get_plan(qaoa_ctx* c, int p) {
   return r;
 }
 
-template <typename Real, bool FAST, int R = kR, int WB = kWB>
+template <typename Real, bool FAST, bool CC, int R = kR, int WB = kWB>
 int launch_pass(qaoa_ctx* c, const PassDev& pd, const PassArgs& pa, size_t smem, int grid) {
-  auto kern = fwd_pass_kernel<Real, R, WB, FAST>;
+  auto kern = fwd_pass_kernel<Real, R, WB, FAST, CC>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, 32 << WB, smem, c->stream>>>(pd, pa);
   if (c->prof_on) ++c->nlaunch;
@@ -242,13 +242,34 @@ int launch_pass(qaoa_ctx* c, const PassDev& pd, const PassArgs& pa, size_t smem,
   return QAOA_OK;
 }
 
-template <typename Real, bool FAST, int R = kR, int WB = kWB>
+template <typename Real, bool FAST, bool CC, int R = kR, int WB = kWB>
 int blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
-  auto kern = fwd_pass_kernel<Real, R, WB, FAST>;
+  auto kern = fwd_pass_kernel<Real, R, WB, FAST, CC>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, 32 << WB, smem));
   if (*nb < 1) return c->set_err(QAOA_ECUDA, "pass kernel does not fit on an SM (smem %zu)", smem);
   return QAOA_OK;
+}
+
+// Instantiation for (precision, tile shape, mixer form, C(x) code): occupancy
+// query when `launch` is false, else the launch.
+template <bool FAST, bool CC>
+int pass_dispatch(qaoa_ctx* c, bool wide, bool launch, const PassDev& pd, const PassArgs& pa, size_t smem, int grid,
+                  int* bps) {
+  if (c->prec == QAOA_C128)
+    return launch ? launch_pass<double, FAST, CC>(c, pd, pa, smem, grid) : blocks_per_sm<double, FAST, CC>(c, smem, bps);
+  if (wide)
+    return launch ? launch_pass<float, FAST, CC, 4, 4>(c, pd, pa, smem, grid)
+                  : blocks_per_sm<float, FAST, CC, 4, 4>(c, smem, bps);
+  return launch ? launch_pass<float, FAST, CC>(c, pd, pa, smem, grid) : blocks_per_sm<float, FAST, CC>(c, smem, bps);
+}
+
+int pass_any(qaoa_ctx* c, bool fast, bool cc, bool wide, bool launch, const PassDev& pd, const PassArgs& pa,
+             size_t smem, int grid, int* bps) {
+  if (fast) return cc ? pass_dispatch<true, true>(c, wide, launch, pd, pa, smem, grid, bps)
+                      : pass_dispatch<true, false>(c, wide, launch, pd, pa, smem, grid, bps);
+  return cc ? pass_dispatch<false, true>(c, wide, launch, pd, pa, smem, grid, bps)
+            : pass_dispatch<false, false>(c, wide, launch, pd, pa, smem, grid, bps);
 }
 
 int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
@@ -354,12 +375,9 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     }
     int bps = 0;
     const bool wide = fwd_wide(c->prec);
-    if (c->prec == QAOA_C128)
-      rc = fast ? blocks_per_sm<double, true>(c, smem, &bps) : blocks_per_sm<double, false>(c, smem, &bps);
-    else if (wide)
-      rc = fast ? blocks_per_sm<float, true, 4, 4>(c, smem, &bps) : blocks_per_sm<float, false, 4, 4>(c, smem, &bps);
-    else
-      rc = fast ? blocks_per_sm<float, true>(c, smem, &bps) : blocks_per_sm<float, false>(c, smem, &bps);
+    bool cc = false;
+    for (const SubPassPlan& sp : pp.subs) cc = cc || sp.needs_c || sp.init;
+    rc = pass_any(c, fast, cc, wide, false, pd, pa, smem, 0, &bps);
     if (rc) return rc;
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
@@ -372,13 +390,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
       if (stream)
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 0, bytes);
-      if (c->prec == QAOA_C128)
-        rc = fast ? launch_pass<double, true>(c, pd, pa, smem, grid) : launch_pass<double, false>(c, pd, pa, smem, grid);
-      else if (wide)
-        rc = fast ? launch_pass<float, true, 4, 4>(c, pd, pa, smem, grid)
-                  : launch_pass<float, false, 4, 4>(c, pd, pa, smem, grid);
-      else
-        rc = fast ? launch_pass<float, true>(c, pd, pa, smem, grid) : launch_pass<float, false>(c, pd, pa, smem, grid);
+      rc = pass_any(c, fast, cc, wide, true, pd, pa, smem, grid, nullptr);
     }
     if (rc) return rc;
     if (pp.reduce) {
@@ -802,16 +814,27 @@ int qaoa_sample(qaoa_ctx* c, int shots, const double* uniforms, uint64_t seed, u
     block_sum_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((const float2*)c->state, B, (double*)c->d_sums.p);
   if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
-  scan_kernel<<<1, 1024, 0, c->stream>>>((const double*)c->d_sums.p, nb, (double*)c->d_pre.p);
-  if (c->prof_on) ++c->nlaunch;
+  if (nb <= kScanChunk) {
+    scan_kernel<<<1, 1024, 0, c->stream>>>((const double*)c->d_sums.p, nb, (double*)c->d_pre.p);
+    if (c->prof_on) ++c->nlaunch;
+  } else {
+    const long long nch = (nb + kScanChunk - 1) / kScanChunk;
+    CUDA_TRY(c, c->d_pre2.ensure(sizeof(double) * (2 * nch + 1)));
+    double* tot = (double*)c->d_pre2.p;
+    double* pre2 = tot + nch;
+    scan_chunk_kernel<<<(unsigned)nch, 512, 0, c->stream>>>((const double*)c->d_sums.p, nb, (double*)c->d_pre.p, tot);
+    scan_kernel<<<1, 1024, 0, c->stream>>>(tot, nch, pre2);
+    scan_offset_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, c->stream>>>((double*)c->d_pre.p, nb, pre2, nch);
+    if (c->prof_on) c->nlaunch += 3;
+  }
   CUDA_TRY(c, cudaGetLastError());
-  const int tb = 128, gb = (shots + tb - 1) / tb;
+  const int wpb = 4, gb = (shots + wpb - 1) / wpb;
   if (c->prec == QAOA_C128)
-    shot_kernel<double><<<gb, tb, 0, c->stream>>>((const double2*)c->state, B, (const double*)c->d_pre.p, nb, shots,
-                                                  d_uni, seed, (unsigned long long*)c->d_shots.p);
+    shot_warp_kernel<double><<<gb, 32 * wpb, 0, c->stream>>>((const double2*)c->state, B, (const double*)c->d_pre.p,
+                                                              nb, shots, d_uni, seed, (unsigned long long*)c->d_shots.p);
   else
-    shot_kernel<float><<<gb, tb, 0, c->stream>>>((const float2*)c->state, B, (const double*)c->d_pre.p, nb, shots,
-                                                 d_uni, seed, (unsigned long long*)c->d_shots.p);
+    shot_warp_kernel<float><<<gb, 32 * wpb, 0, c->stream>>>((const float2*)c->state, B, (const double*)c->d_pre.p,
+                                                             nb, shots, d_uni, seed, (unsigned long long*)c->d_shots.p);
   if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, cudaMemcpyAsync(out, c->d_shots.p, sizeof(uint64_t) * shots, cudaMemcpyDeviceToHost, c->stream));
@@ -898,7 +921,7 @@ void qaoa_free(qaoa_ctx* c) {
   if (c->own_state && c->state) cudaFree(c->state);
   c->aux_own.release();
   DevBuf* bufs[] = {&c->d_wmat, &c->d_ctabs, &c->d_phase, &c->d_partial, &c->d_result, &c->d_ext,
-                    &c->d_ext_part, &c->d_sums, &c->d_pre, &c->d_shots, &c->d_uni, &c->d_ang,
+                    &c->d_ext_part, &c->d_sums, &c->d_pre, &c->d_pre2, &c->d_shots, &c->d_uni, &c->d_ang,
                     &c->d_lambda, &c->d_gacc};
   for (DevBuf* b : bufs) b->release();
   for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }

@@ -244,6 +244,58 @@ static __global__ void __launch_bounds__(1024) scan_kernel(const double* __restr
   for (long long i = lo; i < hi; ++i) { pre[i] = run; run += s[i]; }
 }
 
+// Multi-CTA exclusive scan for long block-sum arrays. Level 1: CTA b takes
+// s[b * 4096 ..) (each thread 8 consecutive values, then warp and block
+// prefixes, a fixed order), writes the chunk-local exclusive prefix to pre and
+// its total to tot[b]. Level 2 scans tot with scan_kernel; level 3 adds the
+// chunk offsets and sets pre[count] = total.
+constexpr int kScanChunk = 4096;
+static __global__ void __launch_bounds__(512) scan_chunk_kernel(const double* __restrict__ s, long long count,
+                                                                 double* __restrict__ pre, double* __restrict__ tot) {
+  __shared__ double buf[kScanChunk + kScanChunk / 32];
+  __shared__ double wsum[16];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long base = (long long)blockIdx.x * kScanChunk;
+  auto slot = [](int i) { return i + (i >> 5); };  // padding: 8 consecutive values per thread without conflicts
+  for (int k = 0; k < 8; ++k) {
+    const int i = k * 512 + tid;
+    buf[slot(i)] = base + i < count ? s[base + i] : 0.0;
+  }
+  __syncthreads();
+  double v[8], run = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) { v[k] = run; run += buf[slot(tid * 8 + k)]; }
+  double x = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (tid == 0) {
+    double r = 0.0;
+    for (int w = 0; w < 16; ++w) { const double t = wsum[w]; wsum[w] = r; r += t; }
+    tot[blockIdx.x] = r;
+  }
+  __syncthreads();
+  const double off = wsum[warp] + (x - run);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) buf[slot(tid * 8 + k)] = off + v[k];
+  __syncthreads();
+  for (int k = 0; k < 8; ++k) {
+    const int i = k * 512 + tid;
+    if (base + i < count) pre[base + i] = buf[slot(i)];
+  }
+}
+
+static __global__ void scan_offset_kernel(double* __restrict__ pre, long long count, const double* __restrict__ pre2,
+                                          long long nchunks) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) pre[i] += pre2[i / kScanChunk];
+  if (i == 0) pre[count] = pre2[nchunks];
+}
+
 // Draw k of the SplitMix64 stream `seed` (Steele, Lea and Flood 2014) as a
 // double in [0, 1): mix(seed + (k+1) * golden gamma) >> 11, times 2^-53.
 __device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long k) {
@@ -288,6 +340,74 @@ __global__ void shot_kernel(const typename Cx<Real>::T* __restrict__ psi, int B,
   }
   if (pick < 0) pick = last_nz;
   out[i] = (unsigned long long)(base + pick);
+}
+
+// One warp per shot: the same block and in-block rules as shot_kernel, with a
+// 32-way search over the prefix array (identical answer: the predicate
+// pre[j + 1] > t is monotone in j) and the in-block running sum taken 32
+// amplitudes at a time (warp prefix sums; a different FP64 summation order
+// inside the block than the sequential loop).
+template <typename Real>
+__global__ void __launch_bounds__(128) shot_warp_kernel(const typename Cx<Real>::T* __restrict__ psi, int B,
+                                                        const double* __restrict__ pre, long long nb, int shots,
+                                                        const double* __restrict__ uni, unsigned long long seed,
+                                                        unsigned long long* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= shots) return;
+  const double u = uni ? uni[i] : splitmix_uniform(seed, (unsigned long long)i);
+  const double total = pre[nb];
+  const double t = u * total;
+  // smallest j in [lo, hi) with pre[j + 1] > t, or hi if none
+  long long lo = 0, hi = nb;
+  while (hi - lo > 32) {
+    const long long step = (hi - lo + 31) / 32;
+    const long long piv = lo + (long long)lane * step;  // lane 0's pivot is lo
+    const bool f = piv < hi && pre[piv + 1] > t;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    const int k = m ? __ffs(m) - 1 : 32;      // first pivot where the predicate holds
+    const long long nlo = k == 0 ? lo : lo + (long long)(k - 1) * step + 1;
+    const long long nhi = k == 32 ? hi : lo + (long long)k * step;
+    lo = nlo;
+    hi = nhi < hi ? nhi : hi;
+  }
+  {
+    const long long piv = lo + lane;
+    const bool f = piv < hi && pre[piv + 1] > t;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    lo = m ? lo + __ffs(m) - 1 : hi;
+  }
+  long long j = lo;
+  if (j >= nb) {  // rounding pushed t to the total: last block with mass
+    j = nb - 1;
+    while (j > 0 && !(pre[j + 1] > pre[j])) --j;
+  }
+  const double tr = t - pre[j];
+  const size_t base = (size_t)j << B;
+  const int len = 1 << B;
+  double carry = 0.0;
+  long long pick = -1, last_nz = 0;
+  for (int k0 = 0; k0 < len; k0 += 32) {
+    const int k = k0 + lane;
+    double pr = 0.0;
+    if (k < len) {
+      const typename Cx<Real>::T a = __ldcg(psi + base + k);
+      pr = double(a.x) * double(a.x) + double(a.y) * double(a.y);
+    }
+    double x = pr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const unsigned nz = __ballot_sync(0xffffffffu, pr > 0.0);
+    if (nz) last_nz = k0 + 31 - __clz(nz);
+    const unsigned hit = __ballot_sync(0xffffffffu, carry + x > tr);
+    if (hit) { pick = k0 + __ffs(hit) - 1; break; }
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (pick < 0) pick = last_nz;
+  if (lane == 0) out[i] = (unsigned long long)(base + pick);
 }
 
 }  // namespace qaoa

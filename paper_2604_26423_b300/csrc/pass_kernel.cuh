@@ -77,8 +77,19 @@ __device__ __forceinline__ void bfly(typename Cx<Real>::T& a, typename Cx<Real>:
   }
 }
 
+// Butterflies on the register bits in `mask`. The all-bits case is straight-line
+// code: a branch per bit would make the compiler restore the registers' roles
+// after every bit (a move per amplitude per bit).
 template <int R, typename V, typename Real>
 __device__ __forceinline__ void apply_mixer(V* v, uint8_t mask, Real tau, Real alpha, bool fast) {
+  if (mask == (1u << R) - 1) {
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+      for (int j = 0; j < (1 << R); ++j)
+        if (!(j >> i & 1)) bfly<Real>(v[j], v[j | (1 << i)], tau, alpha, fast);
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     if (mask >> i & 1) {
@@ -184,7 +195,10 @@ __device__ __forceinline__ void smem_store(int layout, C2* tile, uint32_t sbase,
 // One round. For a round whose source is global memory, v already holds the
 // loaded amplitudes (issued before the tile's barrier). Reduction partials are
 // added to the warp's slot in wacc (lane 0 writes).
-template <typename Real, int R, int WB, bool FAST>
+// CC: the kernel contains the C(x) code (cost phase, |+> initialisation and
+// reductions); passes without any of them run an instantiation without it
+// (smaller code, measured faster).
+template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tile, uint64_t gbase, const int* tconst,
                                           const typename Cx<Real>::T* phase, int lane, int warp, double* wacc,
@@ -196,7 +210,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   const bool stream = A.diag != nullptr;
   // the round's geometry is rebuilt where needed instead of being kept live
   // across the butterflies (register pressure)
-  if (rd.src == SRC_INIT_D) {
+  if (CC && rd.src == SRC_INIT_D) {
 #pragma unroll
     for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
   } else if (rd.src == SRC_SMEM_D) {
@@ -205,7 +219,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
 
   apply_mixer<R>(v, rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA), FAST);
 
-  if (rd.cost | rd.reduce) {
+  if (CC && (rd.cost | rd.reduce)) {
     // C(x) of register amplitude j: streamed from the diagonal, or
     // kappa + CP[j] + sum_{i: j_i = 1} e_i from the round's tables
     RoundCost<R, WB> rc;
@@ -281,7 +295,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
 
 // One super-tile (unit) of a forward pass: every tile of each of its sub-passes.
 // All threads of the CTA take part; shared memory is free again on return.
-template <typename Real, int R, int WB, bool FAST>
+template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tile, int* tconst,
                                          const typename Cx<Real>::T* phase, double* wacc) {
@@ -312,7 +326,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         }
       }
       __syncthreads();  // previous tile finished with shared memory
-      if (sp.needs_c && !stream) {
+      if (CC && sp.needs_c && !stream) {
         if (tid == 0) tconst[16] = 0;
         __syncthreads();
         tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
@@ -321,7 +335,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       for (int r = 0; r < sp.nrounds; ++r) {
         const RoundDev& rd = sp.rd[r];
         if (rd.src == SRC_SMEM_D) __syncthreads();
-        fwd_round<Real, R, WB, FAST>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, wacc, v);
+        fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, wacc, v);
       }
     }
     __syncthreads();  // sub-pass boundary: this CTA's global writes are visible to it
@@ -331,7 +345,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
 // Shared-memory layout of the dynamic buffer:
 //   tile[padded 2^T] complex | tile consts [16] int + base | phase table
 // (the weight matrix is read through the L1 cache by one warp per tile)
-template <typename Real, int R, int WB, bool FAST>
+template <typename Real, int R, int WB, bool FAST, bool CC>
 __global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
 fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   using C2 = typename Cx<Real>::T;
@@ -354,7 +368,7 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   if (lane == 0) { wacc[2 * warp] = 0.0; wacc[2 * warp + 1] = 0.0; }
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    fwd_unit<Real, R, WB, FAST>(P, A, unit, tile, tconst, phase, wacc);
+    fwd_unit<Real, R, WB, FAST, CC>(P, A, unit, tile, tconst, phase, wacc);
 
   if (A.partial) {
     // block sum of the per-warp FP64 partials, in warp order

@@ -359,7 +359,7 @@ class Batch:
         n = int(self.n[i])
 
         class _View:  # the library's buffer, seen through the CUDA array interface
-            __cuda_array_interface__ = {"shape": (1 << n,), "typestr": "<c8", "data": (ptr.value, True),
+            __cuda_array_interface__ = {"shape": (1 << n,), "typestr": "<c8", "data": (ptr.value, False),
                                         "version": 2, "strides": None}
 
         self.stream.synchronize()

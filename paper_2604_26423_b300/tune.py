@@ -1,0 +1,126 @@
+"""Autotuner for the kernel configuration choices.
+
+Forward path: the cost mode (C(x) recomputed in each tile from the weight
+matrix, or streamed from a precomputed int32 diagonal) and the tile shape and
+super-tile size of the pass kernels are timed on the caller's instance and the
+fastest is kept. Batched path: the scheduling knobs of ``qaoa_batch_create``
+(which instances run all their passes in one CTA, items per pass, CTAs per SM)
+are timed on the caller's batch.
+
+Every candidate runs the full computation (same plan semantics, same results
+up to FP32 summation order); timing is by CUDA events on the launching stream
+after a warm-up run. Choices are cached in memory per workload key.
+"""
+from __future__ import annotations
+
+import contextlib
+import itertools
+import os
+
+_cache: dict = {}
+
+# tile shape of the complex64 forward kernel: 2^R registers x 2^WB warps
+FWD_SHAPES = {"5x3": None, "4x4": "4x4"}
+# largest super-tile (index bits kept together through L2 by one CTA)
+SUPER_TILES = (13, 14, 15)
+
+
+@contextlib.contextmanager
+def _env(settings: dict):
+    old = {k: os.environ.get(k) for k in settings}
+    try:
+        for k, v in settings.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = str(v)
+        yield
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def forward_candidates(n: int, precision: str = "c64", modes=("recompute", "stream"), shapes=None,
+                       super_tiles=SUPER_TILES):
+    """Configurations to time for one instance: cost mode x tile shape x super-tile bits."""
+    if shapes is None:
+        shapes = tuple(FWD_SHAPES) if precision == "c64" else ("5x3",)
+    out = []
+    for mode, shape, st in itertools.product(modes, shapes, super_tiles):
+        if st > n:
+            continue
+        out.append({"cost_mode": mode, "shape": shape, "super_tile": st})
+    return out
+
+
+def config_env(cfg: dict) -> dict:
+    """Environment settings that select a forward configuration in the library."""
+    return {"QAOA_FWD_SHAPE": FWD_SHAPES[cfg["shape"]], "QAOA_SMAX": cfg["super_tile"]}
+
+
+def _time_ms(fn, stream, reps: int) -> float:
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_forward(n, u, v, w, p, dgamma, dbeta, scale=0.1, precision="c64", candidates=None, reps=1, key=None):
+    """Times qaoa_run (p LR layers) under each candidate; returns (best, timings)."""
+    import torch
+    from .qaoa import Simulator
+    key = key or ("fwd", n, precision, p, len(u))
+    if key in _cache:
+        return _cache[key]
+    cands = candidates or forward_candidates(n, precision)
+    stream = torch.cuda.current_stream()
+    timings = []
+    state = None
+    for cfg in cands:
+        with _env(config_env(cfg)):
+            s = Simulator(n, u, v, w, scale, precision, cost_mode=cfg["cost_mode"], state=state)
+            try:
+                state = s._state_t
+                ms = _time_ms(lambda: s.run(p, dgamma, dbeta), stream, reps)
+            finally:
+                s.close()
+        timings.append(dict(cfg, ms=ms))
+    best = min(timings, key=lambda t: t["ms"])
+    _cache[key] = (best, timings)
+    return best, timings
+
+
+def batch_candidates(solo=(13, 16, 20, 25), units=(1, 2, 4), ctas=(2,)):
+    return [dict(solo_max_n=a, max_units=b, ctas_per_sm=c) for a, b, c in itertools.product(solo, units, ctas)]
+
+
+def tune_batch(instances, with_grad=False, scale=0.1, candidates=None, reps=1, key=None):
+    """Times one replay of the batch graph under each scheduling candidate; returns (best, timings)."""
+    import torch
+    from .qaoa import Batch
+    key = key or ("batch", len(instances), bool(with_grad),
+                  tuple(int(d["n"]) for d in instances[:64]), tuple(int(d["p"]) for d in instances[:64]))
+    if key in _cache:
+        return _cache[key]
+    stream = torch.cuda.current_stream()
+    timings = []
+    for opts in candidates or batch_candidates():
+        b = Batch(instances, scale=scale, with_grad=with_grad, opts=opts)
+        try:
+            ms = _time_ms(b.run, stream, reps)
+        finally:
+            b.close()
+        timings.append(dict(opts=opts, ms=ms))
+    best = min(timings, key=lambda t: t["ms"])
+    _cache[key] = (best, timings)
+    return best, timings

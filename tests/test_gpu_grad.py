@@ -126,3 +126,38 @@ def test_state_after_grad_needs_rerun():
             s.sample(8)
         s.run(2, 0.6, 0.3)
         assert len(s.sample(8)) == 8
+
+
+def test_autograd_function_matches_adjoint_and_fd():
+    import torch
+    from paper_2604_26423_b300.autograd import lr_expectation, expectation
+    n, p = 14, 4
+    u, v, w = inputs.complete_graph(n, 1414)
+    with sim(n, u, v, w, 0.1, "c128", with_grad=True) as s:
+        dg = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
+        db = torch.tensor(0.3, dtype=torch.float64, requires_grad=True)
+        e = lr_expectation(s, p, dg, db)
+        e.backward()
+        ref = s.grad(p, 0.6, 0.3)
+        assert abs(e.item() - ref["exp_c"]) <= 1e-9 * abs(ref["exp_c"])
+        assert abs(dg.grad.item() - ref["d_dgamma"]) <= 1e-9 * max(1.0, abs(ref["d_dgamma"]))
+        assert abs(db.grad.item() - ref["d_dbeta"]) <= 1e-9 * max(1.0, abs(ref["d_dbeta"]))
+        # FP64 central differences of the oracle in (dgamma, dbeta)
+        h = 1e-5
+        cut = oracle.cut_values(n, u, v, w)
+        f = lambda a, b: oracle.expectation(oracle.simulate(n, u, v, w, 0.1, *oracle.lr_schedule(p, a, b)), cut)[0]
+        fd_g = (f(0.6 + h, 0.3) - f(0.6 - h, 0.3)) / (2 * h)
+        fd_b = (f(0.6, 0.3 + h) - f(0.6, 0.3 - h)) / (2 * h)
+        assert abs(dg.grad.item() - fd_g) <= 1e-6 * max(1.0, abs(fd_g))
+        assert abs(db.grad.item() - fd_b) <= 1e-6 * max(1.0, abs(fd_b))
+        # explicit angles: gradient per layer
+        g = torch.tensor([0.1, 0.2, 0.35, 0.5], dtype=torch.float64, requires_grad=True)
+        b = torch.tensor([0.4, 0.3, 0.2, 0.1], dtype=torch.float64, requires_grad=True)
+        expectation(s, g, b).backward()
+        r2 = s.grad_angles(g.detach().numpy(), b.detach().numpy())
+        assert np.allclose(g.grad.numpy(), r2["g_gamma"], rtol=1e-12, atol=1e-12)
+        assert np.allclose(b.grad.numpy(), r2["g_beta"], rtol=1e-12, atol=1e-12)
+        # no gradient requested: plain forward
+        with torch.no_grad():
+            e2 = lr_expectation(s, p, torch.tensor(0.6, dtype=torch.float64), torch.tensor(0.3, dtype=torch.float64))
+        assert abs(e2.item() - ref["exp_c"]) <= 1e-9 * abs(ref["exp_c"])
