@@ -18,6 +18,11 @@ phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
 * ``grad``: the adjoint gradient's cost relative to the forward run on the
   gradient workload (K_28, complex64, p = 10): t(qaoa_grad: forward, <C>,
   backward, all 2p layer derivatives) / t(qaoa_run + qaoa_expect).
+* ``batch``: the batched workload (4096 seeded instances, n uniform in 10..22,
+  p in 1..10, 1/3 K_n, 1/3 chains, 1/3 random 3-regular graphs, complex64,
+  forward with <C>, r and extremes, and forward + adjoint gradients): instances/s
+  of one CUDA-graph replay of the persistent batch kernels, scheduling knobs
+  picked by the autotuner; ``--batch-reps`` replays are timed.
 * ``--qubits n`` runs the same step on K_n (smaller cases for profiling; the
   JSON line then names that workload).
 * ``cpu_baseline`` / ``--impl reference``: the gate-by-gate complex128 oracle on
@@ -50,6 +55,7 @@ sys.path.insert(0, ROOT)
 N_QUBITS, P, DGAMMA, DBETA, SCALE, SEED, SHOTS = 33, 3, 0.6, 0.3, 0.1, 33, 4096
 METRIC = "LR-QAOA layers/s at n=33 (complex64, K_33, p=3)"
 GRAD_N, GRAD_P, GRAD_DGAMMA, GRAD_DBETA = 28, 10, 0.6, 0.3
+BATCH_COUNT, BATCH_SEED = 4096, 2604
 PROFILE_JSON = os.path.join(ROOT, "profiles", "fwd_pass_kernel_traffic.json")
 KERNEL_SOURCES = ["paper_2604_26423_b300/csrc/pass_kernel.cuh", "paper_2604_26423_b300/csrc/device.cuh"]
 
@@ -214,6 +220,40 @@ def grad_ratio(args, stream, reps: int = 3):
                 "d_dgamma": r["d_dgamma"], "d_dbeta": r["d_dbeta"]}
 
 
+def batch_bench(args, stream):
+    """Instances/s of the 4096-instance batch (forward, and forward + adjoint)."""
+    import torch
+    from paper_2604_26423_b300 import inputs, tune
+    from paper_2604_26423_b300.qaoa import Batch
+
+    batch = inputs.batch_instances(BATCH_COUNT, BATCH_SEED)
+    out = {"workload": f"{BATCH_COUNT} instances, n in 10..22, p in 1..10, K_n / chain / 3-regular, complex64"}
+    for grad in (False, True):
+        best, timings = tune.tune_batch(batch, with_grad=grad,
+                                        candidates=tune.batch_candidates(solo=(16, 25), units=(1, 2), ctas=(2,)))
+        b = Batch(batch, with_grad=grad, opts=best["opts"])
+        try:
+            for _ in range(2):
+                b.run()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.batch_reps):
+                b.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.batch_reps
+            res = b.results()
+            key = "grad" if grad else "forward"
+            out[key] = {"instances_per_s": BATCH_COUNT / ms * 1e3, "ms": ms, "opts": best["opts"],
+                        "state_gbytes": b.bytes() / 1e9, "state_gbps": b.bytes() / ms / 1e6,
+                        "mean_r": float(res["r"].mean()), "describe": b.describe()}
+        finally:
+            b.close()
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_2604_26423_b300 import inputs
@@ -282,7 +322,9 @@ def run_gpu(args):
         e2e_s = reduce_max(time.perf_counter() - t0, world)
         barrier(world)
     del state_buf
+    torch.cuda.empty_cache()
     grad = None if args.no_grad else grad_ratio(args, stream)
+    batch = None if args.no_batch else batch_bench(args, stream)
 
     peak, peak_kind = measured_peak()
     achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else 0.0
@@ -321,6 +363,8 @@ def run_gpu(args):
     }
     if grad is not None:
         out["grad"] = grad
+    if batch is not None:
+        out["batch"] = batch
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     if rank == 0:
@@ -366,6 +410,8 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -33,12 +33,13 @@ using namespace qaoa;
 namespace {
 
 constexpr int kR = 5, kWB = 3;           // forward tile: 2^5 registers x 32 lanes x 8 warps
-constexpr int kSmax = 13;                // super-tile bits: 13 = one tile (L2 sub-passes measured slower)
+
 constexpr int kRAdj = 4, kWBAdj = 3;     // adjoint tile: psi and lambda, 2^4 registers each
 constexpr int kSmaxAdj = 12;             // adjoint super-tile: one tile of psi and lambda
 constexpr int kMinUnitsLog2 = 9;         // keep >= 512 super-tiles when n allows
 constexpr long long kMaxAbsWeightSum = 1 << 20;
 constexpr int kMaxGrid = 4096;           // persistent grid cap (partial-sum buffer size)
+constexpr int kFuseSumsMinQubits = 26;   // final pass writes sampling block sums from here on
 
 thread_local std::string g_init_error;
 
@@ -92,6 +93,7 @@ struct qaoa_ctx {
   Extreme ext{};
   bool have_result = false;
   bool state_ready = false;
+  bool sums_ready = false;  // d_sums holds the sampling block sums of the current state
   std::string err;
   int set_err(int code, const char* fmt, ...) {
     char buf[512];
@@ -148,18 +150,26 @@ struct ProfScope {
   }
 };
 
-// Forward tile shape: 2^5 registers x 8 warps (default), or 2^4 registers x
-// 16 warps when QAOA_FWD_SHAPE=4x4 (complex64 only; twice the warps per SM).
-bool fwd_wide(int prec) {
-  if (prec != QAOA_C64) return false;
+// Forward tile shape (complex64 only; complex128 always uses 5x3):
+//   0 "5x3": 2^5 registers x 8 warps, T = 13, 2 CTAs per SM (default)
+//   1 "4x4": 2^4 registers x 16 warps, T = 13
+//   2 "5x2": 2^5 registers x 4 warps, T = 12, 4 CTAs per SM
+// selected by QAOA_FWD_SHAPE.
+int fwd_shape_id(int prec) {
+  if (prec != QAOA_C64) return 0;
   const char* e = getenv("QAOA_FWD_SHAPE");
-  return e && strcmp(e, "4x4") == 0;
+  if (!e) return 0;
+  if (strcmp(e, "4x4") == 0) return 1;
+  if (strcmp(e, "5x2") == 0) return 2;
+  return 0;
 }
 
 TileShape fwd_shape(int prec) {
+  static const int R[3] = {kR, 4, 5}, WB[3] = {kWB, 4, 2};
+  const int id = fwd_shape_id(prec);
   TileShape s;
-  s.R = fwd_wide(prec) ? 4 : kR;
-  s.WB = fwd_wide(prec) ? 4 : kWB;
+  s.R = R[id];
+  s.WB = WB[id];
   s.amp_bytes = amp_bytes(prec);
   return s;
 }
@@ -217,16 +227,16 @@ int smax_adj() {
   return v >= 12 && v <= 20 ? v : kSmaxAdj;
 }
 
-int smax_fwd() {
+int smax_fwd(int T) {
   const char* e = getenv("QAOA_SMAX");
-  const int v = e ? atoi(e) : kSmax;
-  return v >= 12 && v <= 20 ? v : kSmax;
+  const int v = e ? atoi(e) : T;
+  return v >= T && v <= 20 ? v : T;
 }
 
 const Plan* get_plan(qaoa_ctx* c, int p) {
   auto it = c->plans.find(p);
   if (it != c->plans.end()) return it->second.get();
-  auto pl = std::make_unique<Plan>(plan_forward(c->n, p, fwd_shape(c->prec), smax_fwd(), kMinUnitsLog2));
+  auto pl = std::make_unique<Plan>(plan_forward(c->n, p, fwd_shape(c->prec), smax_fwd(fwd_shape(c->prec).T()), kMinUnitsLog2));
   const Plan* r = pl.get();
   c->plans[p] = std::move(pl);
   return r;
@@ -254,17 +264,20 @@ int blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
 // Instantiation for (precision, tile shape, mixer form, C(x) code): occupancy
 // query when `launch` is false, else the launch.
 template <bool FAST, bool CC>
-int pass_dispatch(qaoa_ctx* c, bool wide, bool launch, const PassDev& pd, const PassArgs& pa, size_t smem, int grid,
+int pass_dispatch(qaoa_ctx* c, int shape, bool launch, const PassDev& pd, const PassArgs& pa, size_t smem, int grid,
                   int* bps) {
   if (c->prec == QAOA_C128)
     return launch ? launch_pass<double, FAST, CC>(c, pd, pa, smem, grid) : blocks_per_sm<double, FAST, CC>(c, smem, bps);
-  if (wide)
+  if (shape == 1)
     return launch ? launch_pass<float, FAST, CC, 4, 4>(c, pd, pa, smem, grid)
                   : blocks_per_sm<float, FAST, CC, 4, 4>(c, smem, bps);
+  if (shape == 2)
+    return launch ? launch_pass<float, FAST, CC, 5, 2>(c, pd, pa, smem, grid)
+                  : blocks_per_sm<float, FAST, CC, 5, 2>(c, smem, bps);
   return launch ? launch_pass<float, FAST, CC>(c, pd, pa, smem, grid) : blocks_per_sm<float, FAST, CC>(c, smem, bps);
 }
 
-int pass_any(qaoa_ctx* c, bool fast, bool cc, bool wide, bool launch, const PassDev& pd, const PassArgs& pa,
+int pass_any(qaoa_ctx* c, bool fast, bool cc, int wide, bool launch, const PassDev& pd, const PassArgs& pa,
              size_t smem, int grid, int* bps) {
   if (fast) return cc ? pass_dispatch<true, true>(c, wide, launch, pd, pa, smem, grid, bps)
                       : pass_dispatch<true, false>(c, wide, launch, pd, pa, smem, grid, bps);
@@ -312,6 +325,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   const int ab = amp_bytes(c->prec);
   c->state_ready = false;
   c->have_result = false;
+  c->sums_ready = false;
   int rc = upload_phases(c, p, gamma);
   if (rc) return rc;
   if (n < T) {
@@ -341,6 +355,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   // build every pass descriptor (and its cost tables) before launching
   std::vector<PassDev> pds(plan->passes.size());
   std::vector<char> fasts(plan->passes.size());
+  bool fused_sums = false;
   PassInputs in;
   in.n = n;
   in.beta = beta;
@@ -374,7 +389,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
       pa.l2hint = (e && atoi(e) != 0) ? 1 : 0;
     }
     int bps = 0;
-    const bool wide = fwd_wide(c->prec);
+    const int wide = fwd_shape_id(c->prec);
     bool cc = false;
     for (const SubPassPlan& sp : pp.subs) cc = cc || sp.needs_c || sp.init;
     rc = pass_any(c, fast, cc, wide, false, pd, pa, smem, 0, &bps);
@@ -382,6 +397,21 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
     pa.partial = pp.reduce ? (double*)c->d_partial.p : nullptr;
+    // the final pass writes the sampling block sums when its tile is the 2^T
+    // lowest index bits (T = 12 or 13, one sub-pass) and the state is large
+    // enough for the separate block-sum read to matter (their FP32 grouping
+    // differs from block_sum_kernel's, so shots near a CDF step may differ in
+    // the last bits between the two; both are valid draws)
+    pa.bsum = nullptr;
+    if (pp.reduce && n >= kFuseSumsMinQubits && (T == 12 || T == 13) && pp.subs.size() == 1) {
+      bool contiguous = true;
+      for (int j = 0; j < T; ++j) contiguous = contiguous && pp.subs[0].pos[j] == j;
+      if (contiguous) {
+        CUDA_TRY(c, c->d_sums.ensure(sizeof(double) * (size_t(1) << (n - 12))));
+        pa.bsum = (double*)c->d_sums.p;
+        fused_sums = true;
+      }
+    }
     {
       // algorithmic HBM bytes: one read (none for the |+> pass) and one write of
       // the state, plus one int32 diagonal read per sub-pass needing C(x)
@@ -401,6 +431,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   }
   c->have_result = true;
   c->state_ready = true;
+  c->sums_ready = fused_sums;
   return QAOA_OK;
 }
 
@@ -491,6 +522,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     if (exp_c) *exp_c = h[2 * p];
     c->state_ready = false;
     c->have_result = false;
+    c->sums_ready = false;
     return QAOA_OK;
   }
   // forward: psi_p and <C>
@@ -590,6 +622,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   if (g_beta) memcpy(g_beta, gbt.data(), sizeof(double) * p);
   if (exp_c) *exp_c = res[1];
   c->state_ready = false;  // psi has been walked back towards |+>
+  c->sums_ready = false;
   return QAOA_OK;
 }
 
@@ -807,13 +840,15 @@ int qaoa_sample(qaoa_ctx* c, int shots, const double* uniforms, uint64_t seed, u
     CUDA_TRY(c, cudaMemcpyAsync(c->d_uni.p, uniforms, sizeof(double) * shots, cudaMemcpyHostToDevice, c->stream));
     d_uni = (const double*)c->d_uni.p;
   }
-  ProfScope ps(c, 3, double(1ull << n) * amp_bytes(c->prec));
-  if (c->prec == QAOA_C128)
-    block_sum_kernel<double><<<(unsigned)nb, 256, 0, c->stream>>>((const double2*)c->state, B, (double*)c->d_sums.p);
-  else
-    block_sum_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((const float2*)c->state, B, (double*)c->d_sums.p);
-  if (c->prof_on) ++c->nlaunch;
-  CUDA_TRY(c, cudaGetLastError());
+  ProfScope ps(c, 3, c->sums_ready ? 0.0 : double(1ull << n) * amp_bytes(c->prec));
+  if (!c->sums_ready) {  // else the final forward pass has written them
+    if (c->prec == QAOA_C128)
+      block_sum_kernel<double><<<(unsigned)nb, 256, 0, c->stream>>>((const double2*)c->state, B, (double*)c->d_sums.p);
+    else
+      block_sum_kernel<float><<<(unsigned)nb, 256, 0, c->stream>>>((const float2*)c->state, B, (double*)c->d_sums.p);
+    if (c->prof_on) ++c->nlaunch;
+    CUDA_TRY(c, cudaGetLastError());
+  }
   if (nb <= kScanChunk) {
     scan_kernel<<<1, 1024, 0, c->stream>>>((const double*)c->d_sums.p, nb, (double*)c->d_pre.p);
     if (c->prof_on) ++c->nlaunch;
@@ -855,7 +890,7 @@ int qaoa_describe_plan(int n, int precision, int p, int adjoint, char* out, int 
   std::string s;
   try {
     Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), smax_adj(), kMinUnitsLog2)
-                      : plan_forward(n, p, fwd_shape(precision), smax_fwd(), kMinUnitsLog2);
+                      : plan_forward(n, p, fwd_shape(precision), smax_fwd(fwd_shape(precision).T()), kMinUnitsLog2);
     std::string e = validate(pl);
     s = pl.describe();
     if (!e.empty()) s += "INVALID: " + e + "\n";

@@ -356,6 +356,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     A.wmat = I.wmat;
     A.ctabs = I.ctabs;
     A.partial = nullptr;
+    A.bsum = nullptr;
     A.phase_in_smem = 0;
     A.l2hint = 0;
     constexpr int TILE = padded_size<8>(kBatchR + 5 + kBatchWB);
@@ -435,7 +436,7 @@ __device__ __noinline__ void batch_solo_small(const BatchArgs& B, const BatchIns
 template <bool FAST, bool ADJ>
 __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double wacc[2 * kBatchThreads / 32];
+  __shared__ double wacc[4 * kBatchThreads / 32];
   __shared__ double red[kBatchThreads / 32];
   __shared__ Extreme ered[kBatchThreads / 32];
   __shared__ PassDev sP;

@@ -32,6 +32,8 @@ struct PassArgs {
   const int32_t* wmat;    // n x n symmetric integer weights
   const int32_t* ctabs;   // per-round cost tables (recompute mode)
   double* partial;        // per-CTA [norm, <C>] partial sums (final pass)
+  double* bsum;           // sampling block sums (2^12 consecutive amplitudes) written by
+                          // the final pass when its tiles are index-contiguous, or nullptr
   int phase_in_smem;      // copy the phase table into shared memory
   int l2hint;             // L2 priorities: keep sub-pass outputs that are read back
 };
@@ -53,6 +55,10 @@ struct Lay {
     return o;
   }
 };
+
+// warps per CTA of a shape
+template <int WB>
+constexpr int NT32 = 1 << WB;
 
 __host__ __device__ constexpr int ctz_c(int k) {
   int b = 0;
@@ -257,11 +263,36 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     }
     if (rd.reduce) {
       Real sn = 0, scc = 0;
-      for_costs([&](int j, int c) {
-        const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
-        sn += pr;
-        scc = fma(pr, Real(c), scc);
-      });
+      if (A.bsum) {
+        // also |psi|^2 per sampling block: tile bit 12 (if any) splits the tile
+        int hreg = -1, hthr = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i) hreg = rd.reg[i] == 12 ? i : hreg;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) hthr |= rd.lane[i] == 12 ? (lane >> i & 1) : 0;
+#pragma unroll
+        for (int i = 0; i < WB; ++i) hthr |= rd.warp[i] == 12 ? (warp >> i & 1) : 0;
+        Real s0 = 0, s1 = 0;
+        for_costs([&](int j, int c) {
+          const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
+          sn += pr;
+          scc = fma(pr, Real(c), scc);
+          if (hreg >= 0 ? (j >> hreg & 1) : hthr) s1 += pr; else s0 += pr;
+        });
+        double d0 = double(s0), d1 = double(s1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        }
+        if (lane == 0) { wacc[2 * (NT32<WB>) + 2 * warp] = d0; wacc[2 * (NT32<WB>) + 2 * warp + 1] = d1; }
+      } else {
+        for_costs([&](int j, int c) {
+          const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
+          sn += pr;
+          scc = fma(pr, Real(c), scc);
+        });
+      }
       double dn = double(sn), dc = double(scc);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -337,6 +368,15 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         if (rd.src == SRC_SMEM_D) __syncthreads();
         fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, wacc, v);
       }
+      if (CC && A.bsum && sp.rd[sp.nrounds - 1].reduce) {
+        // this tile is 2^T consecutive amplitudes: its 2^(T-12) block sums, in warp order
+        __syncthreads();
+        if (tid < (1 << (T - 12))) {
+          double b = 0.0;
+          for (int w = 0; w < NT / 32; ++w) b += wacc[2 * (NT / 32) + 2 * w + tid];
+          A.bsum[(gbase >> 12) + tid] = b;
+        }
+      }
     }
     __syncthreads();  // sub-pass boundary: this CTA's global writes are visible to it
   }
@@ -346,7 +386,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
 //   tile[padded 2^T] complex | tile consts [16] int + base | phase table
 // (the weight matrix is read through the L1 cache by one warp per tile)
 template <typename Real, int R, int WB, bool FAST, bool CC>
-__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (WB == 2 ? 4 : 2) : 1)
 fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
@@ -364,7 +404,7 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
     phase = ptab;
   }
-  __shared__ double wacc[2 * NT / 32];  // per-warp reduction slots
+  __shared__ double wacc[4 * NT / 32];  // per-warp reduction slots: [norm, <C>], block sums
   if (lane == 0) { wacc[2 * warp] = 0.0; wacc[2 * warp + 1] = 0.0; }
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)

@@ -402,19 +402,25 @@ Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2,
   const std::vector<Group> groups = make_groups(n, S);
   for (auto& g : groups) plan.groups.push_back(g.targets);
   const int G = (int)groups.size();
+  // Forward group order of layer k: alternating between layers so consecutive
+  // layers meet on one group, and chosen so that the last layer ends on group
+  // 0 (the low, index-contiguous bits): the final pass then sees whole
+  // contiguous blocks (sampling block sums) and, for odd p, the write-only
+  // first pass gets the smaller top group.
+  auto fwd_grp = [&](int k, int i) { return ((p - 1 - k) % 2 == 0) ? G - 1 - i : i; };
   std::vector<Op> ops;
   if (!backward) {
-    // [init] then per layer k: cost k, mixer k over the groups (alternating order)
+    // [init] then per layer k: cost k, mixer k over the groups
     for (int k = 0; k < p; ++k) {
       ops.push_back({OP_COST, k, -1});
-      for (int i = 0; i < G; ++i) ops.push_back({OP_MIX, k, (k % 2 == 0) ? i : G - 1 - i});
+      for (int i = 0; i < G; ++i) ops.push_back({OP_MIX, k, fwd_grp(k, i)});
     }
   } else {
     // [lambda] then per layer k = p-1..0: inverse mixer k over the groups in the
     // reverse of the forward order of layer k, then inverse cost k
     for (int j = 0; j < p; ++j) {
       const int k = p - 1 - j;
-      for (int i = 0; i < G; ++i) ops.push_back({OP_MIX, k, (k % 2 == 0) ? G - 1 - i : i});
+      for (int i = 0; i < G; ++i) ops.push_back({OP_MIX, k, fwd_grp(k, G - 1 - i)});
       ops.push_back({OP_COST, k, -1});
     }
   }

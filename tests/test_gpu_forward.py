@@ -160,6 +160,26 @@ def test_shots_rule_on_gpu_state_c64():
     assert ok.all(), f"{(~ok).sum()} shot mismatches"
 
 
+def test_shots_with_fused_block_sums_c64():
+    # from 26 qubits the final pass writes the sampling block sums; every shot
+    # must fall in its FP64 CDF interval of the GPU's own state (up to the
+    # rounding of FP32 partial sums, far below one block's mass)
+    n, p = 26, 3
+    u, v, w = graph("complete", n, 2626)
+    uni = inputs.uniforms(2627, 4096)
+    with sim(n, u, v, w, S, "c64") as s:
+        s.run(p, 0.6, 0.3)
+        got = s.sample(4096, uniforms=uni).astype(np.int64)
+        psi = state_np(s)
+    pr = np.abs(psi.astype(np.complex128)) ** 2
+    F = np.cumsum(pr)
+    t = uni * F[-1]
+    lo = np.where(got > 0, F[np.maximum(got - 1, 0)], 0.0)
+    tol = 1e-8 * F[-1]
+    assert np.all(lo - tol <= t) and np.all(t <= F[got] + tol)
+    assert np.all(pr[got] > 0)
+
+
 def test_config_n16_full():
     # n=16, K_16 (120 edges), w in {1..10}, s = 1/10, p = 3, dgamma 0.6, dbeta 0.3,
     # complex128, <C>, r from exhaustive C_min / C_max, 1024 shots
