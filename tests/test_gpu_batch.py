@@ -145,3 +145,22 @@ def test_batch_workload_sample_matches_single_path():
         ref = _single(d)
         assert res["c_max"][i] == ref["c_max"] and res["c_min"][i] == ref["c_min"], i
         assert abs(res["exp_c"][i] - ref["exp_c"]) <= 1e-6 * abs(ref["exp_c"]), (i, d["n"], d["p"])
+
+
+def test_batch_c64_vs_single_c128():
+    # the batched complex64 form against the plain complex128 single-instance path
+    batch = _mixed(71, [10, 13, 16, 19], [3, 2, 3, 2])
+    with Batch(batch, with_grad=True, opts=dict(solo_max_n=16)) as b:
+        b.run()
+        res = b.results()
+    worst = {"exp_c": 0.0, "r": 0.0, "d_dgamma": 0.0}
+    for i, d in enumerate(batch):
+        with Simulator(d["n"], d["u"], d["v"], d["w"], 0.1, "c128", with_grad=True) as s:
+            s.run(d["p"], d["dgamma"], d["dbeta"])
+            e = s.expect()
+            g = s.grad(d["p"], d["dgamma"], d["dbeta"])
+        worst["exp_c"] = max(worst["exp_c"], abs(res["exp_c"][i] - e["exp_c"]) / e["exp_c"])
+        worst["r"] = max(worst["r"], abs(res["r"][i] - e["r"]))
+        worst["d_dgamma"] = max(worst["d_dgamma"], abs(res["d_dgamma"][i] - g["d_dgamma"]) / max(1, abs(g["d_dgamma"])))
+    print(f"\nbatch c64 vs single c128: {worst}")
+    assert worst["exp_c"] <= 2e-5 and worst["r"] <= 1e-5 and worst["d_dgamma"] <= 2e-3

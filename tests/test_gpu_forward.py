@@ -223,3 +223,21 @@ def test_errors_reported():
         s.run(1, 0.6, 0.3)
         with pytest.raises(QaoaError):
             s.sample(10, uniforms=np.array([0.1] * 9 + [1.5]))
+
+
+@pytest.mark.parametrize("n", [16, 20, 22])
+def test_c64_error_vs_oracle(n):
+    # stated accuracy of the complex64 path against the FP64 oracle (K_n, p = 3)
+    p = 3
+    u, v, w = inputs.complete_graph(n, 7000 + n)
+    g, b = oracle.lr_schedule(p, 0.6, 0.3)
+    ref = oracle.run(n, u, v, w, S, g, b)
+    with sim(n, u, v, w, S, "c64") as s:
+        s.run(p, 0.6, 0.3)
+        res = s.expect()
+        psi = state_np(s)
+    l2 = float(np.linalg.norm(psi - ref["psi"]))
+    e_rel = abs(res["exp_c"] - ref["exp_c"]) / ref["exp_c"]
+    r_abs = abs(res["r"] - ref["r"])
+    print(f"\nc64 vs oracle n={n}: state L2 {l2:.2e}, <C> rel {e_rel:.2e}, |r - r_oracle| {r_abs:.2e}")
+    assert l2 <= 1e-4 and e_rel <= 2e-5 and r_abs <= 1e-6
