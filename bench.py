@@ -226,8 +226,9 @@ def batch_bench(args, stream):
     from paper_2604_26423_b300 import inputs, tune
     from paper_2604_26423_b300.qaoa import Batch
 
-    batch = inputs.batch_instances(BATCH_COUNT, BATCH_SEED)
-    out = {"workload": f"{BATCH_COUNT} instances, n in 10..22, p in 1..10, K_n / chain / 3-regular, complex64"}
+    count = args.batch_count
+    batch = inputs.batch_instances(count, BATCH_SEED)
+    out = {"workload": f"{count} instances, n in 10..22, p in 1..10, K_n / chain / 3-regular, complex64"}
     for grad in (False, True):
         best, timings = tune.tune_batch(batch, with_grad=grad,
                                         candidates=tune.batch_candidates(solo=(16, 25), units=(1, 2), ctas=(2,)))
@@ -246,7 +247,7 @@ def batch_bench(args, stream):
             ms = e0.elapsed_time(e1) / args.batch_reps
             res = b.results()
             key = "grad" if grad else "forward"
-            out[key] = {"instances_per_s": BATCH_COUNT / ms * 1e3, "ms": ms, "opts": best["opts"],
+            out[key] = {"instances_per_s": count / ms * 1e3, "ms": ms, "opts": best["opts"],
                         "state_gbytes": b.bytes() / 1e9, "state_gbps": b.bytes() / ms / 1e6,
                         "mean_r": float(res["r"].mean()), "describe": b.describe()}
         finally:
@@ -412,6 +413,7 @@ def main(argv=None):
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-reps", type=int, default=3)
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -83,7 +83,7 @@ __device__ __forceinline__ Real pow_bits(Real c, uint8_t mask) {
   return r;
 }
 
-template <typename Real, int R, int WB, bool FAST>
+template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, uint64_t gbase,
                                           const int* tconst, const typename Cx<Real>::T* phase, int lane, int warp,
@@ -95,7 +95,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   C2* glam = reinterpret_cast<C2*>(A.lam);
   const bool stream = A.diag != nullptr;
   const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
-  const bool need_c = rd.cost || rd.lam;
+  const bool need_c = CC && (rd.cost || rd.lam);
   RoundCost<R, WB> rcost;
   if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
   auto for_costs = [&](auto&& f) {
@@ -118,7 +118,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   C2 v[NA], l[NA];
   if (rd.src == SRC_GLOBAL_D) {
     gray_ptr_walk<R>(gpsi, geo.gb, geo.gstr, [&](int j, const C2* q) { v[j] = __ldcg(q); });
-    if (rd.lam) {
+    if (CC && rd.lam) {
       // lambda = C(x) psi (the operator whose expectation is differentiated)
       for_costs([&](int j, int c) {
         l[j].x = Real(c) * v[j].x;
@@ -134,11 +134,13 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
 
   inverse_mixer<R>(v, l, rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA), FAST,
                    pow_bits(pick<Real>(P.cA, P.fcA), rd.mixA), ga);
-  if (rd.cost) {
+  if (CC && rd.cost) {
     for_costs([&](int j, int c) {
       const Real h = Real(P.wsum - 2 * c);
       gc = fma(fma(l[j].x, v[j].y, -l[j].y * v[j].x), h, gc);
-      const C2 ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
+      C2 ph;
+      if constexpr (sizeof(Real) == 4) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo));
+      else ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
       // multiply both vectors by the conjugate phase (inverse cost unitary)
       const Real vr = v[j].x, vi = v[j].y, lr = l[j].x, li = l[j].y;
       v[j].x = vr * ph.x + vi * ph.y;
@@ -163,7 +165,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
 
 // One super-tile (unit) of an adjoint pass; the gradient terms of this
 // thread's amplitudes are added to gA, gC, gB.
-template <typename Real, int R, int WB, bool FAST>
+template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, int* tconst,
                                          const typename Cx<Real>::T* phase, double& gA, double& gC, double& gB) {
@@ -179,7 +181,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
     for (uint64_t ti = 0; ti < ntiles; ++ti) {
       const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
       __syncthreads();
-      if (sp.needs_c && !stream) {
+      if (CC && sp.needs_c && !stream) {
         if (tid == 0) tconst[16] = 0;
         __syncthreads();
         tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
@@ -189,7 +191,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB);
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB);
         }
       } else {
         // fp32: the terms of one tile are summed in fp32, then added in FP64
@@ -198,7 +200,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, ga, gc, gbv);
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, ga, gc, gbv);
         }
         gA += double(ga);
         gC += double(gc);
@@ -210,7 +212,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
 }
 
 // Shared memory: psi tile (padded 2^T) | lambda tile | tile consts | phase table
-template <typename Real, int R, int WB, bool FAST>
+template <typename Real, int R, int WB, bool FAST, bool CC>
 __global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
 adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
   using C2 = typename Cx<Real>::T;
@@ -232,7 +234,7 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
   double gA = 0.0, gC = 0.0, gB = 0.0;
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    adj_unit<Real, R, WB, FAST>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB);
+    adj_unit<Real, R, WB, FAST, CC>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB);
 
   __shared__ double red[3][32];
   for (int o = 16; o > 0; o >>= 1) {

@@ -349,7 +349,8 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   int dev = 0, max_smem = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
   CUDA_TRY(c, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const bool tab_smem = with_tab + 1024 <= (size_t)max_smem;
+  // complex64 kernels compute the phase (phase_turns); complex128 reads the table
+  const bool tab_smem = c->prec == QAOA_C128 && with_tab + 1024 <= (size_t)max_smem;
   const size_t smem = tab_smem ? with_tab : base_smem;
 
   // build every pass descriptor (and its cost tables) before launching
@@ -359,6 +360,8 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   PassInputs in;
   in.n = n;
   in.beta = beta;
+  in.gamma = gamma;
+  in.scale = c->scale;
   in.c_lo = c->c_lo;
   in.ncost = nc;
   in.W = c->W;
@@ -445,23 +448,33 @@ const Plan* get_bplan(qaoa_ctx* c, int p) {
   return r;
 }
 
-template <typename Real, bool FAST>
+template <typename Real, bool FAST, bool CC>
 int adj_blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
-  auto kern = adj_pass_kernel<Real, kRAdj, kWBAdj, FAST>;
+  auto kern = adj_pass_kernel<Real, kRAdj, kWBAdj, FAST, CC>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, 32 << kWBAdj, smem));
   if (*nb < 1) return c->set_err(QAOA_ECUDA, "adjoint kernel does not fit on an SM (smem %zu)", smem);
   return QAOA_OK;
 }
 
-template <typename Real, bool FAST>
+template <typename Real, bool FAST, bool CC>
 int launch_adj(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid) {
-  auto kern = adj_pass_kernel<Real, kRAdj, kWBAdj, FAST>;
+  auto kern = adj_pass_kernel<Real, kRAdj, kWBAdj, FAST, CC>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, 32 << kWBAdj, smem, c->stream>>>(pd, aa);
   if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   return QAOA_OK;
+}
+
+// Adjoint instantiation for (precision, mixer form): occupancy query when
+// `launch` is false, else the launch. Every adjoint pass runs the instantiation
+// with the C(x) code: the one without it spilled and measured slower.
+template <typename Real>
+int adj_any(qaoa_ctx* c, bool fast, bool launch, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid,
+            int* bps) {
+  if (fast) return launch ? launch_adj<Real, true, true>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, true, true>(c, smem, bps);
+  return launch ? launch_adj<Real, false, true>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, false, true>(c, smem, bps);
 }
 
 void* lambda_ptr(qaoa_ctx* c) {
@@ -544,7 +557,8 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   int dev = 0, max_smem = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
   CUDA_TRY(c, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const bool tab_smem = with_tab + 1024 <= (size_t)max_smem;
+  // complex64 kernels compute the phase (phase_turns); complex128 reads the table
+  const bool tab_smem = c->prec == QAOA_C128 && with_tab + 1024 <= (size_t)max_smem;
   const size_t smem = tab_smem ? with_tab : base_smem;
   const size_t npass = plan->passes.size();
   std::vector<PassDev> pds(npass);
@@ -552,6 +566,8 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   PassInputs in;
   in.n = n;
   in.beta = beta;
+  in.gamma = gamma;
+  in.scale = c->scale;
   in.c_lo = c->c_lo;
   in.ncost = nc;
   in.W = c->W;
@@ -581,10 +597,8 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     aa.partial = (double*)c->d_partial.p;
     aa.phase_in_smem = tab_smem ? 1 : 0;
     int bps = 0;
-    if (c->prec == QAOA_C128)
-      rc = fast ? adj_blocks_per_sm<double, true>(c, smem, &bps) : adj_blocks_per_sm<double, false>(c, smem, &bps);
-    else
-      rc = fast ? adj_blocks_per_sm<float, true>(c, smem, &bps) : adj_blocks_per_sm<float, false>(c, smem, &bps);
+    rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, false, pd, aa, smem, 0, &bps)
+                              : adj_any<float>(c, fast, false, pd, aa, smem, 0, &bps);
     if (rc) return rc;
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
@@ -596,10 +610,8 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
       if (stream)
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 1, bytes);
-      if (c->prec == QAOA_C128)
-        rc = fast ? launch_adj<double, true>(c, pd, aa, smem, grid) : launch_adj<double, false>(c, pd, aa, smem, grid);
-      else
-        rc = fast ? launch_adj<float, true>(c, pd, aa, smem, grid) : launch_adj<float, false>(c, pd, aa, smem, grid);
+      rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, true, pd, aa, smem, grid, nullptr)
+                                : adj_any<float>(c, fast, true, pd, aa, smem, grid, nullptr);
     }
     if (rc) return rc;
     sum_partials_kernel<<<1, 32, 0, c->stream>>>((const double*)c->d_partial.p, grid, 3,

@@ -191,6 +191,8 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
     PassInputs in;
     in.n = I.n;
     in.beta = I.beta.data();
+    in.gamma = I.gamma.data();
+    in.scale = weight_scale;
     in.c_lo = I.c_lo;
     in.ncost = I.c_hi - I.c_lo + 1;
     in.W = I.W;

@@ -140,6 +140,17 @@ void mixer_coeffs(double beta, bool fast, double* tau, double* alpha) {
   else { *tau = sin(beta); *alpha = cos(beta); }
 }
 
+namespace {
+
+// frac(x) as a 64-bit fixed-point fraction (x in turns)
+uint64_t turns_fixed(long double x) {
+  x -= floorl(x);
+  const long double f = x * 18446744073709551616.0L;
+  return f >= 18446744073709551615.0L ? ~0ull : (uint64_t)f;
+}
+
+}  // namespace
+
 std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInputs& in, TableStore& tabs,
                           PassDev& pd, bool& fast) {
   const int T = sh.T();
@@ -169,6 +180,14 @@ std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInp
   pd.falphaB = float(pd.alphaB);
   pd.fcA = float(pd.cA);
   pd.fcB = float(pd.cB);
+  if (pp.layer_c >= 0 && in.gamma) {
+    // turns of exp(-i gamma s (W - 2c)) at c = c_lo + u: t0 + u d with
+    // t0 = -gamma s (W - 2 c_lo) / (2 pi), d = gamma s / pi
+    const long double pi = 3.141592653589793238462643383279502884L;
+    const long double g = (long double)in.gamma[pp.layer_c] * (long double)in.scale;
+    pd.ph0 = turns_fixed(-g * (long double)(in.W - 2 * in.c_lo) / (2 * pi));
+    pd.ph1 = turns_fixed(g / pi);
+  }
   for (int s = 0; s < pd.nsub; ++s) {
     const SubPassPlan& sp = pp.subs[s];
     SubDev& sd = pd.sub[s];

@@ -43,6 +43,8 @@ void mixer_coeffs(double beta, bool fast, double* tau, double* alpha);
 struct PassInputs {
   int n = 0;
   const double* beta = nullptr;   // beta_k per layer
+  const double* gamma = nullptr;  // gamma_k per layer (phase constants of the cost layer)
+  double scale = 0.1;             // phase weight scale s
   long long c_lo = 0, ncost = 1;  // phase-table origin and length
   long long W = 0;                // sum of the weights
   const int32_t* wmat = nullptr;  // n x n weights (host)

@@ -59,6 +59,9 @@ struct PassDev {
   int32_t pad0;
   double cA, cB;           // cos(beta) of layers a / b (adjoint per-round rescaling)
   float ftauA, falphaA, ftauB, falphaB, fcA, fcB;  // the same rounded to fp32
+  // cost phase of the pass's cost layer as 64-bit fixed-point turns:
+  // exp(-i gamma s (W - 2c)) = exp(2 pi i (ph0 + (c - c_lo) ph1) / 2^64)
+  uint64_t ph0, ph1;
   SubDev sub[kMaxSubDev];
 };
 
@@ -102,6 +105,19 @@ __device__ __forceinline__ void st_hint(double2* a, double2 v, uint64_t pol) {
 template <typename Real> __device__ __forceinline__ Real pick(double d, float f);
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+
+// exp(2 pi i t / 2^64) for the turn count t = ph0 + u ph1 (mod 2^64), u >= 0:
+// the top 32 bits of t as a signed angle in [-pi, pi), then the hardware sine
+// and cosine (absolute error about 4e-7, below the complex64 state's rounding
+// over a layer). Only the top word of the product is formed.
+__device__ __forceinline__ float2 phase_turns(uint64_t ph0, uint64_t ph1, uint32_t u) {
+  const uint64_t lo = (uint64_t)u * (uint32_t)ph1 + (uint32_t)ph0;
+  const uint32_t hi = (uint32_t)(ph0 >> 32) + u * (uint32_t)(ph1 >> 32) + (uint32_t)(lo >> 32);
+  const float ang = float(int32_t(hi)) * 1.46291807926715968e-9f;  // 2 pi / 2^32
+  float sn, cs;
+  __sincosf(ang, &sn, &cs);
+  return make_float2(cs, sn);
+}
 
 template <typename Real> struct Cx;
 template <> struct Cx<float> { using T = float2; };

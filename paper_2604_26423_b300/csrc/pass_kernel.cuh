@@ -249,7 +249,9 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     };
     if (rd.cost) {
       for_costs([&](int j, int c) {
-        const C2 ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
+        C2 ph;
+        if constexpr (sizeof(Real) == 4) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo));
+        else ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
         const Real xr = v[j].x, xi = v[j].y;
         v[j].x = xr * ph.x - xi * ph.y;
         v[j].y = xr * ph.y + xi * ph.x;
