@@ -9,8 +9,10 @@
 // with h(x) = W - 2 C(x). X_q commutes with every factor exp(+i beta X_q') of
 // the mixer, so <lambda| X_q |psi> may be taken at any point of the mixer's
 // uncomputation; a round evaluates the terms of all its bits first and then
-// applies their inverse butterflies. Each round rescales by cos(beta)^k after
-// its k fast-form butterflies so the next round's terms see normalised vectors.
+// applies their inverse butterflies. In the fast (tan) form the vectors of a
+// tile carry the pending factor cos(beta)^k of the butterflies applied so far;
+// the bilinear terms are corrected by its square and the vectors by the factor
+// itself when the tile is stored.
 // Passes, sub-passes and rounds come from the adjoint plan (plan.h); one launch
 // is one HBM pass reading and writing both vectors.
 #pragma once
@@ -47,32 +49,45 @@ __device__ __forceinline__ Real pair_term(const V* v, const V* l, int i) {
 }
 
 // inverse mixer exp(-i beta X) on both vectors for the bits in `mask`; the
-// gradient terms of those bits are added to `acc` first
+// gradient terms of those bits are taken first. In the fast form the vectors
+// carry a pending factor `sc` (the cos^k of the butterflies applied so far in
+// this tile, restored at the store): the terms, bilinear in the two vectors,
+// are added times sc^2, and sc takes this round's cos^k (`cpow`).
 template <int R, typename V, typename Real>
-__device__ __forceinline__ void inverse_mixer(V* v, V* l, uint8_t mask, Real tau, Real alpha, bool fast, Real scale,
-                                              Real& acc) {
+__device__ __forceinline__ void inverse_mixer(V* v, V* l, uint8_t mask, Real tau, Real alpha, bool fast, Real cpow,
+                                              Real& sc, Real& acc) {
   if (!mask) return;
+  Real t = 0;
+  if (mask == (1u << R) - 1) {
+    // all register bits: straight-line code (no per-bit branches)
 #pragma unroll
-  for (int i = 0; i < R; ++i)
-    if (mask >> i & 1) acc += pair_term<R, V, Real>(v, l, i);
+    for (int i = 0; i < R; ++i) t += pair_term<R, V, Real>(v, l, i);
 #pragma unroll
-  for (int i = 0; i < R; ++i) {
-    if (mask >> i & 1) {
+    for (int i = 0; i < R; ++i)
 #pragma unroll
       for (int j = 0; j < (1 << R); ++j)
         if (!(j >> i & 1)) {
           bfly<Real>(v[j], v[j | (1 << i)], -tau, alpha, fast);
           bfly<Real>(l[j], l[j | (1 << i)], -tau, alpha, fast);
         }
-    }
-  }
-  if (fast) {
+  } else {
 #pragma unroll
-    for (int j = 0; j < (1 << R); ++j) {
-      v[j].x *= scale; v[j].y *= scale;
-      l[j].x *= scale; l[j].y *= scale;
+    for (int i = 0; i < R; ++i)
+      if (mask >> i & 1) t += pair_term<R, V, Real>(v, l, i);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      if (mask >> i & 1) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j)
+          if (!(j >> i & 1)) {
+            bfly<Real>(v[j], v[j | (1 << i)], -tau, alpha, fast);
+            bfly<Real>(l[j], l[j | (1 << i)], -tau, alpha, fast);
+          }
+      }
     }
   }
+  acc = fma(sc * sc, t, acc);
+  if (fast) sc *= cpow;
 }
 
 template <typename Real>
@@ -87,7 +102,7 @@ template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, uint64_t gbase,
                                           const int* tconst, const typename Cx<Real>::T* phase, int lane, int warp,
-                                          Real& ga, Real& gc, Real& gbv) {
+                                          Real& ga, Real& gc, Real& gbv, Real& sc) {
   using C2 = typename Cx<Real>::T;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
@@ -133,11 +148,12 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   }
 
   inverse_mixer<R>(v, l, rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA), FAST,
-                   pow_bits(pick<Real>(P.cA, P.fcA), rd.mixA), ga);
+                   pow_bits(pick<Real>(P.cA, P.fcA), rd.mixA), sc, ga);
   if (CC && rd.cost) {
+    Real tc = 0;
     for_costs([&](int j, int c) {
       const Real h = Real(P.wsum - 2 * c);
-      gc = fma(fma(l[j].x, v[j].y, -l[j].y * v[j].x), h, gc);
+      tc = fma(fma(l[j].x, v[j].y, -l[j].y * v[j].x), h, tc);
       C2 ph;
       if constexpr (sizeof(Real) == 4) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo));
       else ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
@@ -148,12 +164,20 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       l[j].x = lr * ph.x + li * ph.y;
       l[j].y = li * ph.x - lr * ph.y;
     });
+    gc = fma(sc * sc, tc, gc);
   }
   inverse_mixer<R>(v, l, rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB), FAST,
-                   pow_bits(pick<Real>(P.cB, P.fcB), rd.mixB), gbv);
+                   pow_bits(pick<Real>(P.cB, P.fcB), rd.mixB), sc, gbv);
 
   if (rd.dst == DST_GLOBAL_D) {
     if (sp.store) {
+      if (FAST) {
+#pragma unroll
+        for (int j = 0; j < NA; ++j) {
+          v[j].x *= sc; v[j].y *= sc;
+          l[j].x *= sc; l[j].y *= sc;
+        }
+      }
       gray_ptr_walk<R>(gpsi, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
       gray_ptr_walk<R>(glam, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, l[j]); });
     }
@@ -187,11 +211,12 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
         __syncthreads();
       }
+      Real sc = 1;  // pending fast-form factor of this tile's vectors
       if constexpr (sizeof(Real) == 8) {
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB);
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB, sc);
         }
       } else {
         // fp32: the terms of one tile are summed in fp32, then added in FP64
@@ -200,7 +225,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, ga, gc, gbv);
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, ga, gc, gbv, sc);
         }
         gA += double(ga);
         gC += double(gc);
