@@ -232,13 +232,30 @@ static __global__ void __launch_bounds__(1024) scan_kernel(const double* __restr
   const long long hi = lo + chunk < count ? lo + chunk : count;
   double acc = 0.0;
   for (long long i = lo; i < hi; ++i) acc += s[i];
-  part[threadIdx.x] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double run = 0.0;
-    for (int i = 0; i < 1024; ++i) { const double v = part[i]; part[i] = run; run += v; }
-    pre[count] = run;
+  // exclusive prefix of the 1024 chunk sums: warp scans, then a scan of the
+  // 32 warp totals (fixed order)
+  __shared__ double wtot[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double x = acc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
+  if (lane == 31) wtot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    double w = wtot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wtot[lane] = w;  // inclusive
+    if (lane == 31) pre[count] = w;
+  }
+  __syncthreads();
+  part[threadIdx.x] = (warp ? wtot[warp - 1] : 0.0) + (x - acc);
   __syncthreads();
   double run = part[threadIdx.x];
   for (long long i = lo; i < hi; ++i) { pre[i] = run; run += s[i]; }
