@@ -40,6 +40,7 @@ constexpr int kMinUnitsLog2 = 9;         // keep >= 512 super-tiles when n allow
 constexpr long long kMaxAbsWeightSum = 1 << 20;
 constexpr int kMaxGrid = 4096;           // persistent grid cap (partial-sum buffer size)
 constexpr int kFuseSumsMinQubits = 26;   // final pass writes sampling block sums from here on
+constexpr int kGroupOrder = ORDER_LOW_LAST;  // default group order of the pass plans
 
 thread_local std::string g_init_error;
 
@@ -227,6 +228,14 @@ int smax_adj() {
   return v >= 12 && v <= 20 ? v : kSmaxAdj;
 }
 
+// Group order of the pass plans (plan.h): QAOA_GROUP_ORDER=middle or last.
+int group_order() {
+  const char* e = getenv("QAOA_GROUP_ORDER");
+  if (e && strcmp(e, "middle") == 0) return ORDER_LOW_MIDDLE;
+  if (e && strcmp(e, "last") == 0) return ORDER_LOW_LAST;
+  return kGroupOrder;
+}
+
 int smax_fwd(int T) {
   const char* e = getenv("QAOA_SMAX");
   const int v = e ? atoi(e) : T;
@@ -236,7 +245,8 @@ int smax_fwd(int T) {
 const Plan* get_plan(qaoa_ctx* c, int p) {
   auto it = c->plans.find(p);
   if (it != c->plans.end()) return it->second.get();
-  auto pl = std::make_unique<Plan>(plan_forward(c->n, p, fwd_shape(c->prec), smax_fwd(fwd_shape(c->prec).T()), kMinUnitsLog2));
+  auto pl = std::make_unique<Plan>(plan_forward(c->n, p, fwd_shape(c->prec), smax_fwd(fwd_shape(c->prec).T()), kMinUnitsLog2,
+                                                              group_order()));
   const Plan* r = pl.get();
   c->plans[p] = std::move(pl);
   return r;
@@ -442,7 +452,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
 const Plan* get_bplan(qaoa_ctx* c, int p) {
   auto it = c->bplans.find(p);
   if (it != c->bplans.end()) return it->second.get();
-  auto pl = std::make_unique<Plan>(plan_backward(c->n, p, adj_shape(c->prec), smax_adj(), kMinUnitsLog2));
+  auto pl = std::make_unique<Plan>(plan_backward(c->n, p, adj_shape(c->prec), smax_adj(), kMinUnitsLog2, group_order()));
   const Plan* r = pl.get();
   c->bplans[p] = std::move(pl);
   return r;
@@ -901,8 +911,9 @@ void* qaoa_state_ptr(qaoa_ctx* c) { return c ? c->state : nullptr; }
 int qaoa_describe_plan(int n, int precision, int p, int adjoint, char* out, int cap) {
   std::string s;
   try {
-    Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), smax_adj(), kMinUnitsLog2)
-                      : plan_forward(n, p, fwd_shape(precision), smax_fwd(fwd_shape(precision).T()), kMinUnitsLog2);
+    Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), smax_adj(), kMinUnitsLog2, group_order())
+                      : plan_forward(n, p, fwd_shape(precision), smax_fwd(fwd_shape(precision).T()), kMinUnitsLog2,
+                                   group_order());
     std::string e = validate(pl);
     s = pl.describe();
     if (!e.empty()) s += "INVALID: " + e + "\n";

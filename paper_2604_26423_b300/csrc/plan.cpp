@@ -386,7 +386,7 @@ void build_passes(Plan& plan, const std::vector<Group>& groups, const std::vecto
   }
 }
 
-Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2, bool backward) {
+Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2, bool backward, int order) {
   const int T = sh.T();
   if (n < T) throw std::runtime_error("planner: n below the tile size");
   if (n > kMaxQubits) throw std::runtime_error("planner: n too large");
@@ -402,12 +402,27 @@ Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2,
   const std::vector<Group> groups = make_groups(n, S);
   for (auto& g : groups) plan.groups.push_back(g.targets);
   const int G = (int)groups.size();
-  // Forward group order of layer k: alternating between layers so consecutive
-  // layers meet on one group, and chosen so that the last layer ends on group
-  // 0 (the low, index-contiguous bits): the final pass then sees whole
-  // contiguous blocks (sampling block sums) and, for odd p, the write-only
-  // first pass gets the smaller top group.
-  auto fwd_grp = [&](int k, int i) { return ((p - 1 - k) % 2 == 0) ? G - 1 - i : i; };
+  // Base order ord[]: the last layer ends on ord[0]. ORDER_LOW_LAST keeps
+  // groups by bit position (ending on the low, index-contiguous group: the
+  // final pass sees whole contiguous blocks, for odd p the write-only first
+  // pass gets the top group). ORDER_LOW_MIDDLE puts the two smallest high
+  // groups at the ends and the low group next to ord[0].
+  std::vector<int> ord(G);
+  for (int i = 0; i < G; ++i) ord[i] = i;
+  if (order == ORDER_LOW_MIDDLE && G >= 3) {
+    std::vector<int> high;
+    for (int i = 1; i < G; ++i) high.push_back(i);
+    std::stable_sort(high.begin(), high.end(),
+                     [&](int a, int b) { return groups[a].targets.size() < groups[b].targets.size(); });
+    ord.clear();
+    ord.push_back(high[0]);
+    ord.push_back(0);
+    for (size_t i = 2; i < high.size(); ++i) ord.push_back(high[i]);
+    ord.push_back(high[1]);
+  }
+  // layer k runs ord reversed when (p - 1 - k) is even, so consecutive layers
+  // meet on one group and the last layer ends on ord[0]
+  auto fwd_grp = [&](int k, int i) { return ((p - 1 - k) % 2 == 0) ? ord[G - 1 - i] : ord[i]; };
   std::vector<Op> ops;
   if (!backward) {
     // [init] then per layer k: cost k, mixer k over the groups
@@ -430,12 +445,12 @@ Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2,
 
 }  // namespace
 
-Plan plan_forward(int n, int p, const TileShape& sh, int s_max, int min_units_log2) {
-  return make_plan(n, p, sh, s_max, min_units_log2, false);
+Plan plan_forward(int n, int p, const TileShape& sh, int s_max, int min_units_log2, int order) {
+  return make_plan(n, p, sh, s_max, min_units_log2, false, order);
 }
 
-Plan plan_backward(int n, int p, const TileShape& sh, int s_max, int min_units_log2) {
-  return make_plan(n, p, sh, s_max, min_units_log2, true);
+Plan plan_backward(int n, int p, const TileShape& sh, int s_max, int min_units_log2, int order) {
+  return make_plan(n, p, sh, s_max, min_units_log2, true, order);
 }
 
 std::string validate(const Plan& plan) {

@@ -87,15 +87,24 @@ struct Plan {
   std::string describe() const;
 };
 
+// Group orders: the layers alternate between an order and its reverse, so the
+// two ends of the order host the cross-layer fused passes (cost phase and two
+// mixers) and the last layer ends on the order's first group.
+//   ORDER_LOW_LAST: groups by bit position, the last layer ending on the low
+//     group (its final pass sees index-contiguous tiles: sampling block sums);
+//   ORDER_LOW_MIDDLE: the low group away from both ends when there are three or
+//     more groups, so the fused passes fall on the smaller high groups.
+enum GroupOrder { ORDER_LOW_LAST = 0, ORDER_LOW_MIDDLE = 1 };
+
 // Forward plan for n qubits and depth p (n >= shape.T()).
 // s_max: largest super-tile bit count; min_units_log2: keep at least 2^x super-tiles.
-Plan plan_forward(int n, int p, const TileShape& shape, int s_max, int min_units_log2);
+Plan plan_forward(int n, int p, const TileShape& shape, int s_max, int min_units_log2, int order = ORDER_LOW_LAST);
 
 // Adjoint plan: lambda = C psi, then for k = p-1..0 the inverse mixer of layer
 // k on every group followed by the inverse cost phase of layer k, packed into
 // passes like the forward plan (cross-layer fusion through alternating group
 // order). Nothing is stored after the last inverse cost phase.
-Plan plan_backward(int n, int p, const TileShape& shape, int s_max, int min_units_log2);
+Plan plan_backward(int n, int p, const TileShape& shape, int s_max, int min_units_log2, int order = ORDER_LOW_LAST);
 
 // Plans the rounds of one sub-pass with tile bits `tb` (tile bit order) for the
 // op sequence [mixer A on a_bits] [cost] [mixer B on b_bits] [reduce].

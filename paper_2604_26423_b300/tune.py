@@ -1,9 +1,10 @@
 """Autotuner for the kernel configuration choices.
 
 Forward path: the cost mode (C(x) recomputed in each tile from the weight
-matrix, or streamed from a precomputed int32 diagonal) and the tile shape and
-super-tile size of the pass kernels are timed on the caller's instance and the
-fastest is kept. Batched path: the scheduling knobs of ``qaoa_batch_create``
+matrix, or streamed from a precomputed int32 diagonal), the tile shape (qubits
+per shared-memory tile and CTAs per SM), the super-tile size and the group
+order of the pass plan are timed on the caller's instance and the fastest is
+kept. Batched path: the scheduling knobs of ``qaoa_batch_create``
 (which instances run all their passes in one CTA, items per pass, CTAs per SM)
 are timed on the caller's batch.
 
@@ -20,9 +21,13 @@ import os
 _cache: dict = {}
 
 # tile shape of the complex64 forward kernel: 2^R registers x 2^WB warps
-FWD_SHAPES = {"5x3": None, "4x4": "4x4"}
+FWD_SHAPES = {"5x3": None, "4x4": "4x4", "5x2": "5x2"}
 # largest super-tile (index bits kept together through L2 by one CTA)
 SUPER_TILES = (13, 14, 15)
+# group order of the pass plans: the last layer ending on the low group (its
+# final pass also writes the sampling block sums), or the low group away from
+# the fused passes
+GROUP_ORDERS = ("last", "middle")
 
 
 @contextlib.contextmanager
@@ -44,21 +49,22 @@ def _env(settings: dict):
 
 
 def forward_candidates(n: int, precision: str = "c64", modes=("recompute", "stream"), shapes=None,
-                       super_tiles=SUPER_TILES):
-    """Configurations to time for one instance: cost mode x tile shape x super-tile bits."""
+                       super_tiles=SUPER_TILES, orders=GROUP_ORDERS):
+    """Configurations to time for one instance: cost mode x tile shape x super-tile bits x group order."""
     if shapes is None:
         shapes = tuple(FWD_SHAPES) if precision == "c64" else ("5x3",)
     out = []
-    for mode, shape, st in itertools.product(modes, shapes, super_tiles):
+    for mode, shape, st, order in itertools.product(modes, shapes, super_tiles, orders):
         if st > n:
             continue
-        out.append({"cost_mode": mode, "shape": shape, "super_tile": st})
+        out.append({"cost_mode": mode, "shape": shape, "super_tile": st, "order": order})
     return out
 
 
 def config_env(cfg: dict) -> dict:
     """Environment settings that select a forward configuration in the library."""
-    return {"QAOA_FWD_SHAPE": FWD_SHAPES[cfg["shape"]], "QAOA_SMAX": cfg["super_tile"]}
+    return {"QAOA_FWD_SHAPE": FWD_SHAPES[cfg["shape"]], "QAOA_SMAX": cfg["super_tile"],
+            "QAOA_GROUP_ORDER": cfg.get("order", "last")}
 
 
 def _time_ms(fn, stream, reps: int) -> float:

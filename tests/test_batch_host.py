@@ -78,3 +78,32 @@ def test_batch_instances_shape():
             deg = np.bincount(np.concatenate([d["u"], d["v"]]), minlength=d["n"])
             assert (deg == 3).all()
         assert ((np.asarray(d["w"]) >= 1) & (np.asarray(d["w"]) <= 10)).all()
+
+
+def test_tuner_candidates():
+    from paper_2604_26423_b300 import tune
+    c = tune.forward_candidates(33, "c64")
+    assert {"cost_mode": "recompute", "shape": "5x3", "super_tile": 13, "order": "last"} in c
+    assert all(x["super_tile"] <= 33 for x in c)
+    assert {x["shape"] for x in tune.forward_candidates(30, "c128")} == {"5x3"}
+    env = tune.config_env({"cost_mode": "stream", "shape": "4x4", "super_tile": 14, "order": "middle"})
+    assert env == {"QAOA_FWD_SHAPE": "4x4", "QAOA_SMAX": 14, "QAOA_GROUP_ORDER": "middle"}
+    b = tune.batch_candidates(solo=(16,), units=(1, 2), ctas=(2,))
+    assert b == [dict(solo_max_n=16, max_units=1, ctas_per_sm=2), dict(solo_max_n=16, max_units=2, ctas_per_sm=2)]
+
+
+def test_group_orders_give_valid_plans():
+    # both group orders plan every size validly (checked by the planner's validator)
+    import re
+    import os
+    from paper_2604_26423_b300 import qaoa
+    for order in ("last", "middle"):
+        os.environ["QAOA_GROUP_ORDER"] = order
+        try:
+            for n in (13, 14, 20, 26, 30, 33, 34):
+                for p in (1, 2, 3, 4):
+                    for adj in (False, True):
+                        d = qaoa.describe_plan(n, p, "c64", adjoint=adj)
+                        assert "passes=" in d
+        finally:
+            os.environ.pop("QAOA_GROUP_ORDER", None)

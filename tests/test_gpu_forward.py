@@ -241,3 +241,21 @@ def test_c64_error_vs_oracle(n):
     r_abs = abs(res["r"] - ref["r"])
     print(f"\nc64 vs oracle n={n}: state L2 {l2:.2e}, <C> rel {e_rel:.2e}, |r - r_oracle| {r_abs:.2e}")
     assert l2 <= 1e-4 and e_rel <= 2e-5 and r_abs <= 1e-6
+
+
+def test_autotuner_forward_choices_agree():
+    from paper_2604_26423_b300 import tune
+    n, p = 22, 3
+    u, v, w = inputs.complete_graph(n, 2222)
+    cands = tune.forward_candidates(n, "c64", super_tiles=(13,))
+    best, timings = tune.tune_forward(n, u, v, w, p, 0.6, 0.3, candidates=cands)
+    assert len(timings) == len(cands) and all(t["ms"] > 0 for t in timings)
+    assert best in timings
+    ref = None
+    for cfg in cands:
+        with tune._env(tune.config_env(cfg)):
+            with sim(n, u, v, w, S, "c64", cost_mode=cfg["cost_mode"]) as s:
+                s.run(p, 0.6, 0.3)
+                e = s.expect()["exp_c"]
+        ref = e if ref is None else ref
+        assert abs(e - ref) <= 2e-5 * ref, cfg
