@@ -244,6 +244,32 @@ def grad_param_shift(n: int, u, v, w, scale: float, gamma, beta):
     return gg, gb
 
 
+def analytic_p1_zz(n: int, J, gamma: float, beta: float, a: int, b: int) -> float:
+    """<Z_a Z_b> after one layer exp(+i beta B) exp(-i gamma sum J ZZ) on |+>^n.
+
+    Closed form for single-layer QAOA on ZZ Ising models without fields
+    (Ozaeta, van Dam and McMahon 2022; Wang et al. 2018), in the sign
+    convention of the paper's Eqs. UC and UB; J is the n x n coupling matrix
+    (the weights times the phase scale s).
+    """
+    others = [c for c in range(n) if c not in (a, b)]
+    pa = np.prod([math.cos(2 * gamma * J[a, c]) for c in others]) if others else 1.0
+    pb = np.prod([math.cos(2 * gamma * J[b, c]) for c in others]) if others else 1.0
+    pplus = np.prod([math.cos(2 * gamma * (J[a, c] + J[b, c])) for c in others]) if others else 1.0
+    pminus = np.prod([math.cos(2 * gamma * (J[a, c] - J[b, c])) for c in others]) if others else 1.0
+    return (-0.5 * math.sin(4 * beta) * math.sin(2 * gamma * J[a, b]) * (pa + pb)
+            - 0.5 * math.sin(2 * beta) ** 2 * (pplus - pminus))
+
+
+def analytic_p1_expectation(n: int, u, v, w, scale: float, gamma: float, beta: float) -> float:
+    """<C> after one layer, from the closed-form <Z_u Z_v> of every edge:
+    <C> = sum_e w_e (1 - <Z_u Z_v>) / 2 (C(x) counts w_e when x_u != x_v)."""
+    J = np.zeros((n, n))
+    for a, b, wt in zip(u, v, w):
+        J[a, b] = J[b, a] = scale * wt
+    return float(sum(wt * (1 - analytic_p1_zz(n, J, gamma, beta, a, b)) / 2 for a, b, wt in zip(u, v, w)))
+
+
 def lr_chain(g_gamma, g_beta):
     """d<C>/d dgamma = sum_k (k+1)/p g_gamma[k]; d<C>/d dbeta = sum_k (1 - k/p) g_beta[k]."""
     p = len(g_gamma)

@@ -81,8 +81,8 @@ struct qaoa_ctx {
   DevBuf d_sums, d_pre, d_pre2, d_shots, d_uni, d_ang;
   DevBuf d_lambda, d_gacc;                                            // adjoint vector (if no aux), per-pass sums
   TableStore tabs;                                                     // host copy of all cost tables
-  std::map<int, std::unique_ptr<Plan>> plans;                         // forward plans by p
-  std::map<int, std::unique_ptr<Plan>> bplans;                        // adjoint plans by p
+  std::map<std::pair<int, int>, std::unique_ptr<Plan>> plans;         // forward plans by (p, group order)
+  std::map<std::pair<int, int>, std::unique_ptr<Plan>> bplans;        // adjoint plans by (p, group order)
   // per-kernel CUDA-event timing (qaoa_profile_enable / qaoa_profile_read)
   struct ProfRec { int kind; cudaEvent_t a, b; double bytes; };
   bool prof_on = false;
@@ -155,6 +155,7 @@ struct ProfScope {
 //   0 "5x3": 2^5 registers x 8 warps, T = 13, 2 CTAs per SM (default)
 //   1 "4x4": 2^4 registers x 16 warps, T = 13
 //   2 "5x2": 2^5 registers x 4 warps, T = 12, 4 CTAs per SM
+//   3 "4x3": 2^4 registers x 8 warps, T = 12, 4 CTAs per SM
 // selected by QAOA_FWD_SHAPE.
 int fwd_shape_id(int prec) {
   if (prec != QAOA_C64) return 0;
@@ -162,11 +163,12 @@ int fwd_shape_id(int prec) {
   if (!e) return 0;
   if (strcmp(e, "4x4") == 0) return 1;
   if (strcmp(e, "5x2") == 0) return 2;
+  if (strcmp(e, "4x3") == 0) return 3;
   return 0;
 }
 
 TileShape fwd_shape(int prec) {
-  static const int R[3] = {kR, 4, 5}, WB[3] = {kWB, 4, 2};
+  static const int R[4] = {kR, 4, 5, 4}, WB[4] = {kWB, 4, 2, 3};
   const int id = fwd_shape_id(prec);
   TileShape s;
   s.R = R[id];
@@ -236,19 +238,30 @@ int group_order() {
   return kGroupOrder;
 }
 
+// group orders of the gradient's forward and adjoint plans (QAOA_GRAD_ORDER
+// overrides both)
+int grad_fwd_order() {
+  const char* e = getenv("QAOA_GRAD_ORDER");
+  if (e && strcmp(e, "last") == 0) return ORDER_LOW_LAST;
+  if (e && strcmp(e, "middle") == 0) return ORDER_LOW_MIDDLE;
+  return ORDER_LOW_MIDDLE;
+}
+int grad_bwd_order() { return grad_fwd_order(); }
+
 int smax_fwd(int T) {
   const char* e = getenv("QAOA_SMAX");
   const int v = e ? atoi(e) : T;
   return v >= T && v <= 20 ? v : T;
 }
 
-const Plan* get_plan(qaoa_ctx* c, int p) {
-  auto it = c->plans.find(p);
+const Plan* get_plan(qaoa_ctx* c, int p, int order) {
+  const auto key = std::make_pair(p, order);
+  auto it = c->plans.find(key);
   if (it != c->plans.end()) return it->second.get();
-  auto pl = std::make_unique<Plan>(plan_forward(c->n, p, fwd_shape(c->prec), smax_fwd(fwd_shape(c->prec).T()), kMinUnitsLog2,
-                                                              group_order()));
+  auto pl = std::make_unique<Plan>(
+      plan_forward(c->n, p, fwd_shape(c->prec), smax_fwd(fwd_shape(c->prec).T()), kMinUnitsLog2, order));
   const Plan* r = pl.get();
-  c->plans[p] = std::move(pl);
+  c->plans[key] = std::move(pl);
   return r;
 }
 
@@ -284,6 +297,9 @@ int pass_dispatch(qaoa_ctx* c, int shape, bool launch, const PassDev& pd, const 
   if (shape == 2)
     return launch ? launch_pass<float, FAST, CC, 5, 2>(c, pd, pa, smem, grid)
                   : blocks_per_sm<float, FAST, CC, 5, 2>(c, smem, bps);
+  if (shape == 3)
+    return launch ? launch_pass<float, FAST, CC, 4, 3>(c, pd, pa, smem, grid)
+                  : blocks_per_sm<float, FAST, CC, 4, 3>(c, smem, bps);
   return launch ? launch_pass<float, FAST, CC>(c, pd, pa, smem, grid) : blocks_per_sm<float, FAST, CC>(c, smem, bps);
 }
 
@@ -328,7 +344,7 @@ int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   return QAOA_OK;
 }
 
-int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
+int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int order) {
   const int n = c->n;
   const TileShape sh = fwd_shape(c->prec);
   const int T = sh.T();
@@ -346,7 +362,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   }
   const Plan* plan;
   try {
-    plan = get_plan(c, p);
+    plan = get_plan(c, p, order);
   } catch (std::exception& ex) {
     return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
   }
@@ -449,12 +465,13 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
 }
 
 // ---------------------------------------------------------------- adjoint
-const Plan* get_bplan(qaoa_ctx* c, int p) {
-  auto it = c->bplans.find(p);
+const Plan* get_bplan(qaoa_ctx* c, int p, int order) {
+  const auto key = std::make_pair(p, order);
+  auto it = c->bplans.find(key);
   if (it != c->bplans.end()) return it->second.get();
-  auto pl = std::make_unique<Plan>(plan_backward(c->n, p, adj_shape(c->prec), smax_adj(), kMinUnitsLog2, group_order()));
+  auto pl = std::make_unique<Plan>(plan_backward(c->n, p, adj_shape(c->prec), smax_adj(), kMinUnitsLog2, order));
   const Plan* r = pl.get();
-  c->bplans[p] = std::move(pl);
+  c->bplans[key] = std::move(pl);
   return r;
 }
 
@@ -549,13 +566,15 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     return QAOA_OK;
   }
   // forward: psi_p and <C>
-  int rc = run_forward(c, p, gamma, beta);
+  // the gradient's forward run samples nothing: the plan without the
+  // block-sum constraint keeps the fused passes on the small groups
+  int rc = run_forward(c, p, gamma, beta, grad_fwd_order());
   if (rc) return rc;
   void* lam = lambda_ptr(c);
   if (!lam) return c->set_err(QAOA_ENOMEM, "allocation of the adjoint vector failed");
   const Plan* plan;
   try {
-    plan = get_bplan(c, p);
+    plan = get_bplan(c, p, grad_bwd_order());
   } catch (std::exception& ex) {
     return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
   }
@@ -806,7 +825,7 @@ int qaoa_run_angles(qaoa_ctx* c, int p, const double* gamma, const double* beta)
   if (p < 0 || (p > 0 && (!gamma || !beta))) return c->set_err(QAOA_EINVAL, "bad p or angle arrays");
   for (int k = 0; k < p; ++k)
     if (!std::isfinite(gamma[k]) || !std::isfinite(beta[k])) return c->set_err(QAOA_EINVAL, "non-finite angle");
-  return run_forward(c, p, gamma, beta);
+  return run_forward(c, p, gamma, beta, group_order());
 }
 
 int qaoa_run(qaoa_ctx* c, int p, double dgamma, double dbeta) {

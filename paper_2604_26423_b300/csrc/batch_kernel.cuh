@@ -362,13 +362,14 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     constexpr int TILE = padded_size<8>(kBatchR + 5 + kBatchWB);
     float2* tile = reinterpret_cast<float2*>(smem);
     int* tconst = reinterpret_cast<int*>(tile + TILE);
-    if (lane == 0) { wacc[2 * warp] = 0.0; wacc[2 * warp + 1] = 0.0; }
+    wacc[2 * tid] = 0.0;
+    wacc[2 * tid + 1] = 0.0;
     for (uint32_t u = u0; u < u1; ++u) fwd_unit<float, kBatchR, kBatchWB, FAST>(P, A, u, tile, tconst, phase, wacc);
     if (M.reduce) {
       __syncthreads();
+      double sN, sC;
+      reduce_thread_sums<kBatchThreads>(wacc, sN, sC);
       if (tid == 0) {
-        double sN = 0, sC = 0;
-        for (int w = 0; w < kBatchThreads / 32; ++w) { sN += wacc[2 * w]; sC += wacc[2 * w + 1]; }
         B.slots[slot] = sN;
         B.slots[slot + 1] = sC;
       }
@@ -436,7 +437,7 @@ __device__ __noinline__ void batch_solo_small(const BatchArgs& B, const BatchIns
 template <bool FAST, bool ADJ>
 __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double wacc[4 * kBatchThreads / 32];
+  __shared__ double wacc[2 * kBatchThreads + 2 * kBatchThreads / 32];
   __shared__ double red[kBatchThreads / 32];
   __shared__ Extreme ered[kBatchThreads / 32];
   __shared__ PassDev sP;

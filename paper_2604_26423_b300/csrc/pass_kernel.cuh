@@ -198,9 +198,27 @@ __device__ __forceinline__ void smem_store(int layout, C2* tile, uint32_t sbase,
   }
 }
 
+// CTA total of the per-thread FP64 [norm, <C>] sums in wacc (fixed order: each
+// lane of warp 0 adds a strided set, then a shuffle tree); valid in thread 0.
+// A barrier must precede the call.
+template <int NT>
+__device__ __forceinline__ void reduce_thread_sums(const double* wacc, double& sN, double& sC) {
+  sN = 0.0;
+  sC = 0.0;
+  if (threadIdx.x < 32) {
+    for (int t = threadIdx.x; t < NT; t += 32) { sN += wacc[2 * t]; sC += wacc[2 * t + 1]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sN += __shfl_xor_sync(0xffffffffu, sN, o);
+      sC += __shfl_xor_sync(0xffffffffu, sC, o);
+    }
+  }
+}
+
 // One round. For a round whose source is global memory, v already holds the
-// loaded amplitudes (issued before the tile's barrier). Reduction partials are
-// added to the warp's slot in wacc (lane 0 writes).
+// loaded amplitudes (issued before the tile's barrier). Reduction partials:
+// wacc[2 t], wacc[2 t + 1] hold thread t's FP64 running [norm, <C>] sums;
+// wacc[2 NT + 2 w + h] the FP32 warp totals of sampling block h of the tile.
 // CC: the kernel contains the C(x) code (cost phase, |+> initialisation and
 // reductions); passes without any of them run an instantiation without it
 // (smaller code, measured faster).
@@ -281,13 +299,17 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
           scc = fma(pr, Real(c), scc);
           if (hreg >= 0 ? (j >> hreg & 1) : hthr) s1 += pr; else s0 += pr;
         });
-        double d0 = double(s0), d1 = double(s1);
+        // block sums: warp totals in the state precision (errors relative to
+        // the block's own mass), added in FP64 across warps by the caller
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
         }
-        if (lane == 0) { wacc[2 * (NT32<WB>) + 2 * warp] = d0; wacc[2 * (NT32<WB>) + 2 * warp + 1] = d1; }
+        if (lane == 0) {
+          wacc[2 * (32 << WB) + 2 * warp] = double(s0);
+          wacc[2 * (32 << WB) + 2 * warp + 1] = double(s1);
+        }
       } else {
         for_costs([&](int j, int c) {
           const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
@@ -295,13 +317,11 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
           scc = fma(pr, Real(c), scc);
         });
       }
-      double dn = double(sn), dc = double(scc);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        dn += __shfl_xor_sync(0xffffffffu, dn, o);
-        dc += __shfl_xor_sync(0xffffffffu, dc, o);
-      }
-      if (lane == 0) { wacc[2 * warp] += dn; wacc[2 * warp + 1] += dc; }
+      // <C> and norm: this thread's FP64 running sums (one add per tile), the
+      // cross-thread FP64 reduction runs once at the end (reduce_thread_sums)
+      const int tid = (warp << 5) | lane;
+      wacc[2 * tid] += double(sn);
+      wacc[2 * tid + 1] += double(scc);
     }
   } else {
     apply_mixer<R>(v, rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB), FAST);
@@ -375,7 +395,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         __syncthreads();
         if (tid < (1 << (T - 12))) {
           double b = 0.0;
-          for (int w = 0; w < NT / 32; ++w) b += wacc[2 * (NT / 32) + 2 * w + tid];
+          for (int w = 0; w < NT / 32; ++w) b += wacc[2 * NT + 2 * w + tid];
           A.bsum[(gbase >> 12) + tid] = b;
         }
       }
@@ -388,7 +408,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
 //   tile[padded 2^T] complex | tile consts [16] int + base | phase table
 // (the weight matrix is read through the L1 cache by one warp per tile)
 template <typename Real, int R, int WB, bool FAST, bool CC>
-__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (WB == 2 ? 4 : 2) : 1)
+__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : 2) : 1)
 fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
@@ -406,18 +426,19 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
     phase = ptab;
   }
-  __shared__ double wacc[4 * NT / 32];  // per-warp reduction slots: [norm, <C>], block sums
-  if (lane == 0) { wacc[2 * warp] = 0.0; wacc[2 * warp + 1] = 0.0; }
+  // per-thread FP64 running sums [norm, <C>], then per-warp block sums
+  __shared__ double wacc[2 * NT + 2 * NT / 32];
+  wacc[2 * tid] = 0.0;
+  wacc[2 * tid + 1] = 0.0;
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
     fwd_unit<Real, R, WB, FAST, CC>(P, A, unit, tile, tconst, phase, wacc);
 
   if (A.partial) {
-    // block sum of the per-warp FP64 partials, in warp order
     __syncthreads();
+    double sN, sC;
+    reduce_thread_sums<NT>(wacc, sN, sC);
     if (tid == 0) {
-      double sN = 0, sC = 0;
-      for (int w = 0; w < NT / 32; ++w) { sN += wacc[2 * w]; sC += wacc[2 * w + 1]; }
       A.partial[2 * blockIdx.x] = sN;
       A.partial[2 * blockIdx.x + 1] = sC;
     }

@@ -259,3 +259,18 @@ def test_autotuner_forward_choices_agree():
                 e = s.expect()["exp_c"]
         ref = e if ref is None else ref
         assert abs(e - ref) <= 2e-5 * ref, cfg
+
+
+@pytest.mark.parametrize("n,prec", [(30, "c64"), (30, "c128"), (32, "c128"), (34, "c64")])
+def test_single_layer_vs_closed_form_at_large_n(n, prec):
+    # independent of any simulation: <C> after one layer from the closed-form
+    # <Z_u Z_v> (Ozaeta-van Dam-McMahon), up to the memory limit (n = 34
+    # complex64: 128 GiB; n = 32 complex128: 64 GiB)
+    u, v, w = inputs.complete_graph(n, 3400 + n)
+    ref = oracle.analytic_p1_expectation(n, u, v, w, S, 0.6, 0.3)
+    with sim(n, u, v, w, S, prec) as s:
+        s.run(1, 0.6, 0.3)
+        res = s.expect()
+    tol = 2e-6 if prec == "c64" else 1e-11
+    assert abs(res["exp_c"] - ref) <= tol * ref, (res["exp_c"], ref)
+    assert abs(res["norm"] - 1.0) <= (1e-5 if prec == "c64" else 1e-12)

@@ -51,20 +51,7 @@ def dense_state(n, u, v, w, s, gamma, beta):
     return psi
 
 
-def analytic_p1_zz(n, J, gamma, beta, a, b):
-    """<Z_a Z_b> after one layer exp(+i beta B) exp(-i gamma sum J ZZ) on |+>^n.
-
-    Closed form for single-layer QAOA on ZZ Ising models without fields
-    (Ozaeta, van Dam and McMahon 2022; Wang et al. 2018), in the sign
-    convention of the paper's Eqs. UC and UB.
-    """
-    others = [c for c in range(n) if c not in (a, b)]
-    pa = np.prod([math.cos(2 * gamma * J[a, c]) for c in others]) if others else 1.0
-    pb = np.prod([math.cos(2 * gamma * J[b, c]) for c in others]) if others else 1.0
-    pplus = np.prod([math.cos(2 * gamma * (J[a, c] + J[b, c])) for c in others]) if others else 1.0
-    pminus = np.prod([math.cos(2 * gamma * (J[a, c] - J[b, c])) for c in others]) if others else 1.0
-    return (-0.5 * math.sin(4 * beta) * math.sin(2 * gamma * J[a, b]) * (pa + pb)
-            - 0.5 * math.sin(2 * beta) ** 2 * (pplus - pminus))
+analytic_p1_zz = oracle.analytic_p1_zz
 
 
 def random_graph(n, seed, density=1.0):
@@ -301,3 +288,13 @@ def test_inputs_splitmix_reference_values():
     # (state advanced by the golden gamma before mixing)
     x = inputs.splitmix64(0, 3)
     assert [int(t) for t in x] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_analytic_p1_expectation_matches_simulation():
+    # the edge sum of the closed form equals the simulated single-layer <C>
+    n = 7
+    u, v, w = random_graph(n, 77, 0.6)
+    for gamma, beta in [(0.3, 0.2), (1.1, -0.4)]:
+        cut = oracle.cut_values(n, u, v, w)
+        e = oracle.expectation(oracle.simulate(n, u, v, w, 0.1, [gamma], [beta]), cut)[0]
+        assert abs(oracle.analytic_p1_expectation(n, u, v, w, 0.1, gamma, beta) - e) <= 1e-10 * abs(e)
