@@ -132,8 +132,10 @@ int qaoa_sample(qaoa_ctx *ctx, int shots, const double *uniforms, uint64_t seed,
  * and the chain rule d<C>/d dgamma = sum_k (k+1)/p g_gamma[k],
  * d<C>/d dbeta = sum_k (1 - k/p) g_beta[k]. Holds two state vectors (psi in
  * state_dev, lambda in the aux buffer). Any output may be NULL; g_gamma and
- * g_beta hold p doubles. Leaves the context without a prepared state (the
- * walk back ends near |+>), so call qaoa_run again before qaoa_sample.
+ * g_beta hold p doubles; exp_c receives <C> = <psi_p|lambda> (taken in the
+ * first adjoint pass). Leaves the context without a prepared state or result
+ * (the walk back ends near |+>), so call qaoa_run again before qaoa_sample or
+ * qaoa_expect (which then returns ESTATE).
  * Errors: EINVAL (p < 1), ENOMEM, ECUDA.
  */
 int qaoa_grad(qaoa_ctx *ctx, int p, double dgamma, double dbeta, double *g_gamma,

@@ -28,7 +28,7 @@ struct AdjArgs {
   const void* phase;      // phase table of the cost layer (ncost entries)
   const int32_t* wmat;    // n x n weights
   const int32_t* ctabs;   // per-round cost tables
-  double* partial;        // per-CTA [dA, dC, dB] partial sums
+  double* partial;        // per-CTA [dA, dC, dB, <C> (first pass)] partial sums
   int phase_in_smem;
 };
 
@@ -102,7 +102,8 @@ template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, uint64_t gbase,
                                           const int* tconst, const typename Cx<Real>::T* phase, int lane, int warp,
-                                          Real& ga, Real& gc, Real& gbv, Real& sc) {
+                                          Real& ga, Real& gc, Real& gbv, Real& ge, Real& sc,
+                                          typename Cx<Real>::T* v, typename Cx<Real>::T* l) {
   using C2 = typename Cx<Real>::T;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
@@ -130,17 +131,17 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     }
   };
 
-  C2 v[NA], l[NA];
+  // a global round's loads were issued by the caller before the tile barrier
   if (rd.src == SRC_GLOBAL_D) {
-    gray_ptr_walk<R>(gpsi, geo.gb, geo.gstr, [&](int j, const C2* q) { v[j] = __ldcg(q); });
     if (CC && rd.lam) {
-      // lambda = C(x) psi (the operator whose expectation is differentiated)
+      // lambda = C(x) psi (the operator whose expectation is differentiated);
+      // <psi|lambda> = <C> on the way
       for_costs([&](int j, int c) {
-        l[j].x = Real(c) * v[j].x;
-        l[j].y = Real(c) * v[j].y;
+        const Real cr = Real(c);
+        l[j].x = cr * v[j].x;
+        l[j].y = cr * v[j].y;
+        ge = fma(cr, fma(v[j].x, v[j].x, v[j].y * v[j].y), ge);
       });
-    } else {
-      gray_ptr_walk<R>(glam, geo.gb, geo.gstr, [&](int j, const C2* q) { l[j] = __ldcg(q); });
     }
   } else {
     smem_load<R, WB, AB>(rd.layout, tv, geo.sbase, v);
@@ -192,7 +193,9 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
 template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, int* tconst,
-                                         const typename Cx<Real>::T* phase, double& gA, double& gC, double& gB) {
+                                         const typename Cx<Real>::T* phase, double& gA, double& gC, double& gB,
+                                         double& gE) {
+  using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -204,6 +207,17 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
     const uint64_t ntiles = 1ull << sp.ninner;
     for (uint64_t ti = 0; ti < ntiles; ++ti) {
       const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
+      // issue the first round's global loads first: their latency overlaps the
+      // barrier below and the tile constants
+      C2 v[1 << R], l[1 << R];
+      if (sp.rd[0].src == SRC_GLOBAL_D) {
+        const RoundGeo<R, WB, sizeof(C2)> g0(sp, sp.rd[0], gbase, lane, warp);
+        gray_ptr_walk<R>(reinterpret_cast<const C2*>(A.psi), g0.gb, g0.gstr,
+                         [&](int j, const C2* q) { v[j] = __ldcg(q); });
+        if (!(CC && sp.rd[0].lam))
+          gray_ptr_walk<R>(reinterpret_cast<const C2*>(A.lam), g0.gb, g0.gstr,
+                           [&](int j, const C2* q) { l[j] = __ldcg(q); });
+      }
       __syncthreads();
       if (CC && sp.needs_c && !stream) {
         if (tid == 0) tconst[16] = 0;
@@ -216,20 +230,23 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB, sc);
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB, gE, sc,
+                                           v, l);
         }
       } else {
         // fp32: the terms of one tile are summed in fp32, then added in FP64
         // (keeps fp64 conversions out of the rounds)
-        Real ga = 0, gc = 0, gbv = 0;
+        Real ga = 0, gc = 0, gbv = 0, ge = 0;
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, ga, gc, gbv, sc);
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, ga, gc, gbv, ge, sc,
+                                           v, l);
         }
         gA += double(ga);
         gC += double(gc);
         gB += double(gbv);
+        gE += double(ge);
       }
     }
     __syncthreads();
@@ -256,25 +273,27 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
     phase = ptab;
   }
-  double gA = 0.0, gC = 0.0, gB = 0.0;
+  double gA = 0.0, gC = 0.0, gB = 0.0, gE = 0.0;
 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    adj_unit<Real, R, WB, FAST, CC>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB);
+    adj_unit<Real, R, WB, FAST, CC>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE);
 
-  __shared__ double red[3][32];
+  __shared__ double red[4][32];
   for (int o = 16; o > 0; o >>= 1) {
     gA += __shfl_xor_sync(0xffffffffu, gA, o);
     gC += __shfl_xor_sync(0xffffffffu, gC, o);
     gB += __shfl_xor_sync(0xffffffffu, gB, o);
+    gE += __shfl_xor_sync(0xffffffffu, gE, o);
   }
-  if (lane == 0) { red[0][warp] = gA; red[1][warp] = gC; red[2][warp] = gB; }
+  if (lane == 0) { red[0][warp] = gA; red[1][warp] = gC; red[2][warp] = gB; red[3][warp] = gE; }
   __syncthreads();
   if (tid == 0) {
-    double s0 = 0, s1 = 0, s2 = 0;
-    for (int w = 0; w < NT / 32; ++w) { s0 += red[0][w]; s1 += red[1][w]; s2 += red[2][w]; }
-    A.partial[3 * blockIdx.x] = s0;
-    A.partial[3 * blockIdx.x + 1] = s1;
-    A.partial[3 * blockIdx.x + 2] = s2;
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    for (int w = 0; w < NT / 32; ++w) { s0 += red[0][w]; s1 += red[1][w]; s2 += red[2][w]; s3 += red[3][w]; }
+    A.partial[4 * blockIdx.x] = s0;
+    A.partial[4 * blockIdx.x + 1] = s1;
+    A.partial[4 * blockIdx.x + 2] = s2;
+    A.partial[4 * blockIdx.x + 3] = s3;
   }
 }
 

@@ -344,7 +344,9 @@ int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   return QAOA_OK;
 }
 
-int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int order) {
+// reduce = false: the final pass skips <C> and norm (the gradient takes <C>
+// from the adjoint's first pass instead).
+int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int order, bool reduce = true) {
   const int n = c->n;
   const TileShape sh = fwd_shape(c->prec);
   const int T = sh.T();
@@ -394,11 +396,24 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
   in.wmat = c->wmat.data();
   in.stream = stream;
   in.adjoint = false;
+  std::vector<char> ccs(plan->passes.size());
   for (size_t pi = 0; pi < plan->passes.size(); ++pi) {
     bool fast = true;
     const std::string why = fill_pass_dev(plan->passes[pi], sh, in, c->tabs, pds[pi], fast);
     if (!why.empty()) return c->set_err(QAOA_EINVAL, "%s", why.c_str());
     fasts[pi] = fast;
+    bool cc = false;
+    for (int si = 0; si < pds[pi].nsub; ++si) {
+      SubDev& sd = pds[pi].sub[si];
+      bool need = false;
+      for (int r = 0; r < sd.nrounds; ++r) {
+        if (!reduce) sd.rd[r].reduce = 0;
+        need = need || sd.rd[r].cost || sd.rd[r].reduce;
+      }
+      if (!reduce) sd.needs_c = need;
+      cc = cc || sd.needs_c || sd.init;
+    }
+    ccs[pi] = cc;
   }
   rc = upload_ctabs(c);
   if (rc) return rc;
@@ -419,20 +434,20 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
     }
     int bps = 0;
     const int wide = fwd_shape_id(c->prec);
-    bool cc = false;
-    for (const SubPassPlan& sp : pp.subs) cc = cc || sp.needs_c || sp.init;
+    const bool cc = ccs[pi];
+    const bool red = pp.reduce && reduce;
     rc = pass_any(c, fast, cc, wide, false, pd, pa, smem, 0, &bps);
     if (rc) return rc;
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
-    pa.partial = pp.reduce ? (double*)c->d_partial.p : nullptr;
+    pa.partial = red ? (double*)c->d_partial.p : nullptr;
     // the final pass writes the sampling block sums when its tile is the 2^T
     // lowest index bits (T = 12 or 13, one sub-pass) and the state is large
     // enough for the separate block-sum read to matter (their FP32 grouping
     // differs from block_sum_kernel's, so shots near a CDF step may differ in
     // the last bits between the two; both are valid draws)
     pa.bsum = nullptr;
-    if (pp.reduce && n >= kFuseSumsMinQubits && (T == 12 || T == 13) && pp.subs.size() == 1) {
+    if (red && n >= kFuseSumsMinQubits && (T == 12 || T == 13) && pp.subs.size() == 1) {
       bool contiguous = true;
       for (int j = 0; j < T; ++j) contiguous = contiguous && pp.subs[0].pos[j] == j;
       if (contiguous) {
@@ -452,13 +467,13 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       rc = pass_any(c, fast, cc, wide, true, pd, pa, smem, grid, nullptr);
     }
     if (rc) return rc;
-    if (pp.reduce) {
+    if (red) {
       sum_partials_kernel<<<1, 32, 0, c->stream>>>((const double*)c->d_partial.p, grid, 2, (double*)c->d_result.p);
       if (c->prof_on) ++c->nlaunch;
       CUDA_TRY(c, cudaGetLastError());
     }
   }
-  c->have_result = true;
+  c->have_result = reduce;
   c->state_ready = true;
   c->sums_ready = fused_sums;
   return QAOA_OK;
@@ -494,14 +509,18 @@ int launch_adj(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, size_t smem, i
   return QAOA_OK;
 }
 
-// Adjoint instantiation for (precision, mixer form): occupancy query when
-// `launch` is false, else the launch. Every adjoint pass runs the instantiation
-// with the C(x) code: the one without it spilled and measured slower.
+// Adjoint instantiation for (precision, mixer form, C(x) code): occupancy query
+// when `launch` is false, else the launch. Plain inverse-mixer passes run the
+// instantiation without the C(x) code.
 template <typename Real>
-int adj_any(qaoa_ctx* c, bool fast, bool launch, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid,
+int adj_any(qaoa_ctx* c, bool fast, bool cc, bool launch, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid,
             int* bps) {
-  if (fast) return launch ? launch_adj<Real, true, true>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, true, true>(c, smem, bps);
-  return launch ? launch_adj<Real, false, true>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, false, true>(c, smem, bps);
+  if (fast) {
+    if (cc) return launch ? launch_adj<Real, true, true>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, true, true>(c, smem, bps);
+    return launch ? launch_adj<Real, true, false>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, true, false>(c, smem, bps);
+  }
+  if (cc) return launch ? launch_adj<Real, false, true>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, false, true>(c, smem, bps);
+  return launch ? launch_adj<Real, false, false>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, false, false>(c, smem, bps);
 }
 
 void* lambda_ptr(qaoa_ctx* c) {
@@ -568,7 +587,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   // forward: psi_p and <C>
   // the gradient's forward run samples nothing: the plan without the
   // block-sum constraint keeps the fused passes on the small groups
-  int rc = run_forward(c, p, gamma, beta, grad_fwd_order());
+  int rc = run_forward(c, p, gamma, beta, grad_fwd_order(), false);
   if (rc) return rc;
   void* lam = lambda_ptr(c);
   if (!lam) return c->set_err(QAOA_ENOMEM, "allocation of the adjoint vector failed");
@@ -611,7 +630,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   }
   rc = upload_ctabs(c);
   if (rc) return rc;
-  CUDA_TRY(c, c->d_gacc.ensure(sizeof(double) * 3 * npass));
+  CUDA_TRY(c, c->d_gacc.ensure(sizeof(double) * 4 * npass));
   for (size_t pi = 0; pi < npass; ++pi) {
     const PassPlan& pp = plan->passes[pi];
     const PassDev& pd = pds[pi];
@@ -626,8 +645,10 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     aa.partial = (double*)c->d_partial.p;
     aa.phase_in_smem = tab_smem ? 1 : 0;
     int bps = 0;
-    rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, false, pd, aa, smem, 0, &bps)
-                              : adj_any<float>(c, fast, false, pd, aa, smem, 0, &bps);
+    bool cc = false;
+    for (const SubPassPlan& sp : pp.subs) cc = cc || sp.needs_c || sp.linit;
+    rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, false, pd, aa, smem, 0, &bps)
+                              : adj_any<float>(c, fast, cc, false, pd, aa, smem, 0, &bps);
     if (rc) return rc;
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
@@ -639,29 +660,27 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
       if (stream)
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 1, bytes);
-      rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, true, pd, aa, smem, grid, nullptr)
-                                : adj_any<float>(c, fast, true, pd, aa, smem, grid, nullptr);
+      rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, true, pd, aa, smem, grid, nullptr)
+                                : adj_any<float>(c, fast, cc, true, pd, aa, smem, grid, nullptr);
     }
     if (rc) return rc;
-    sum_partials_kernel<<<1, 32, 0, c->stream>>>((const double*)c->d_partial.p, grid, 3,
-                                                 (double*)c->d_gacc.p + 3 * pi);
+    sum_partials_kernel<<<1, 32, 0, c->stream>>>((const double*)c->d_partial.p, grid, 4,
+                                                 (double*)c->d_gacc.p + 4 * pi);
     if (c->prof_on) ++c->nlaunch;
     CUDA_TRY(c, cudaGetLastError());
   }
-  std::vector<double> h(3 * npass);
-  double res[2];
+  std::vector<double> h(4 * npass);
   CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->d_gacc.p, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(res, c->d_result.p, sizeof res, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   for (size_t pi = 0; pi < npass; ++pi) {
     const PassPlan& pp = plan->passes[pi];
-    if (pp.layer_a >= 0) gbt[pp.layer_a] += -2.0 * h[3 * pi];
-    if (pp.layer_c >= 0) gg[pp.layer_c] += 2.0 * c->scale * h[3 * pi + 1];
-    if (pp.layer_b >= 0) gbt[pp.layer_b] += -2.0 * h[3 * pi + 2];
+    if (pp.layer_a >= 0) gbt[pp.layer_a] += -2.0 * h[4 * pi];
+    if (pp.layer_c >= 0) gg[pp.layer_c] += 2.0 * c->scale * h[4 * pi + 1];
+    if (pp.layer_b >= 0) gbt[pp.layer_b] += -2.0 * h[4 * pi + 2];
   }
   if (g_gamma) memcpy(g_gamma, gg.data(), sizeof(double) * p);
   if (g_beta) memcpy(g_beta, gbt.data(), sizeof(double) * p);
-  if (exp_c) *exp_c = res[1];
+  if (exp_c) *exp_c = h[3];  // <psi_p|C psi_p> from the first adjoint pass
   c->state_ready = false;  // psi has been walked back towards |+>
   c->sums_ready = false;
   return QAOA_OK;

@@ -339,7 +339,7 @@ template <bool FAST, bool ADJ>
 __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& I, int pass, int slot, uint32_t u0,
                                            uint32_t u1, unsigned char* smem, double* wacc, double* red, PassDev& P) {
   const PassMeta& M = B.pmeta[pass];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   {
     const uint32_t* src = reinterpret_cast<const uint32_t*>(B.passes + pass);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&P);
@@ -388,9 +388,9 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     float2* tv = reinterpret_cast<float2*>(smem);
     float2* tl = tv + TILE;
     int* tconst = reinterpret_cast<int*>(tl + TILE);
-    double gA = 0.0, gC = 0.0, gB = 0.0;
+    double gA = 0.0, gC = 0.0, gB = 0.0, gE = 0.0;
     for (uint32_t u = u0; u < u1; ++u)
-      adj_unit<float, kBatchRAdj, kBatchWBAdj, FAST>(P, A, u, tv, tl, tconst, phase, gA, gC, gB);
+      adj_unit<float, kBatchRAdj, kBatchWBAdj, FAST>(P, A, u, tv, tl, tconst, phase, gA, gC, gB, gE);
     gA = block_sum(gA, red);
     gC = block_sum(gC, red);
     gB = block_sum(gB, red);

@@ -420,7 +420,7 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   int* tconst = reinterpret_cast<int*>(tile + TILE);  // delta[0..15], base at [16]
   C2* ptab = reinterpret_cast<C2*>(smem_raw + ((size_t(TILE) * AB + 32 * 4 + 15) & ~size_t(15)));
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const C2* phase = reinterpret_cast<const C2*>(A.phase);
   if (A.phase_in_smem && A.phase) {
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];

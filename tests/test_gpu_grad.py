@@ -161,3 +161,16 @@ def test_autograd_function_matches_adjoint_and_fd():
         with torch.no_grad():
             e2 = lr_expectation(s, p, torch.tensor(0.6, dtype=torch.float64), torch.tensor(0.3, dtype=torch.float64))
         assert abs(e2.item() - ref["exp_c"]) <= 1e-9 * abs(ref["exp_c"])
+
+
+def test_grad_exp_c_matches_forward_and_expect_needs_rerun():
+    from paper_2604_26423_b300.qaoa import QaoaError
+    n, p = 20, 3
+    u, v, w = inputs.complete_graph(n, 2020)
+    with sim(n, u, v, w, S, "c64", with_grad=True) as s:
+        s.run(p, 0.6, 0.3)
+        e = s.expect()["exp_c"]
+        g = s.grad(p, 0.6, 0.3)
+        assert abs(g["exp_c"] - e) <= 2e-6 * e
+        with pytest.raises(QaoaError):
+            s.expect()
