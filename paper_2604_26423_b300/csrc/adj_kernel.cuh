@@ -110,7 +110,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   C2* gpsi = reinterpret_cast<C2*>(A.psi);
   C2* glam = reinterpret_cast<C2*>(A.lam);
   const bool stream = A.diag != nullptr;
-  const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
+  const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
   const bool need_c = CC && (rd.cost || rd.lam);
   RoundCost<R, WB> rcost;
   if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
@@ -211,7 +211,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
       // barrier below and the tile constants
       C2 v[1 << R], l[1 << R];
       if (sp.rd[0].src == SRC_GLOBAL_D) {
-        const RoundGeo<R, WB, sizeof(C2)> g0(sp, sp.rd[0], gbase, lane, warp);
+        const RoundGeo<R, WB, sizeof(C2)> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
         gray_ptr_walk<R>(reinterpret_cast<const C2*>(A.psi), g0.gb, g0.gstr,
                          [&](int j, const C2* q) { v[j] = __ldcg(q); });
         if (!(CC && sp.rd[0].lam))

@@ -265,6 +265,7 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
     InstPlan& I = ip[i];
     w_off[i] = h_w.size();
     h_w.insert(h_w.end(), I.wmat.begin(), I.wmat.end());
+    if (h_ct.size() & 1) h_ct.push_back(0);  // the geometry tables hold 64-bit words
     ct_off[i] = h_ct.size();
     h_ct.insert(h_ct.end(), I.tabs.h.begin(), I.tabs.h.end());
     ph_off[i] = h_ph.size();

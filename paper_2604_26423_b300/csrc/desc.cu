@@ -118,6 +118,36 @@ std::string check_graph(int n, int m, const int32_t* u, const int32_t* v, const 
   return "";
 }
 
+int32_t TableStore::geom_offset(const TileShape& sh, const int8_t* pos, const RoundDev& rd) {
+  std::vector<int8_t> key(pos, pos + sh.T());
+  key.insert(key.end(), rd.lane, rd.lane + 5);
+  key.insert(key.end(), rd.warp, rd.warp + 4);
+  key.push_back(int8_t(sh.amp_bytes));
+  auto k = std::make_pair(1000 + sh.R * 100 + sh.WB, key);
+  auto it = index.find(k);
+  if (it != index.end()) return it->second;
+  const int NT = 32 << sh.WB;
+  if (h.size() & 1) h.push_back(0);  // 8-byte alignment of the offsets part
+  const int32_t off = (int32_t)h.size();
+  h.resize(h.size() + 3 * NT, 0);
+  for (int tid = 0; tid < NT; ++tid) {
+    const int lane = tid & 31, warp = tid >> 5;
+    uint32_t tb = 0;
+    uint64_t g = 0;
+    for (int i = 0; i < 5; ++i)
+      if (lane >> i & 1) { tb |= 1u << rd.lane[i]; g |= 1ull << pos[rd.lane[i]]; }
+    for (int i = 0; i < sh.WB; ++i)
+      if (warp >> i & 1) { tb |= 1u << rd.warp[i]; g |= 1ull << pos[rd.warp[i]]; }
+    const uint32_t sb = sh.amp_bytes == 8 ? padi<8>(tb) : padi<16>(tb);
+    h[off + tid] = (int32_t)sb;
+    h[off + NT + 2 * tid] = (int32_t)(uint32_t)(g & 0xffffffffull);
+    h[off + NT + 2 * tid + 1] = (int32_t)(uint32_t)(g >> 32);
+  }
+  index[k] = off;
+  dirty = true;
+  return off;
+}
+
 BitRuns make_runs(const std::vector<int>& bits) {
   BitRuns r;
   memset(&r, 0, sizeof r);
@@ -217,6 +247,7 @@ std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInp
     for (int r = 0; r < sd.nrounds; ++r) {
       to_round_dev(sp.rounds[r], sd.rd[r]);
       fill_round_globals(sd.rd[r], sd.pos);
+      sd.rd[r].gtab = tabs.geom_offset(sh, sd.pos, sd.rd[r]);
       const bool wants = in.adjoint ? (sd.rd[r].cost || sd.rd[r].lam) : (sd.rd[r].cost || sd.rd[r].reduce);
       if (wants && !in.stream) sd.rd[r].ctab = tabs.offset(in.wmat, in.n, sh, sd.pos, sd.rd[r]);
     }

@@ -22,6 +22,9 @@ struct TableStore {
   // Offset of the tables for a round of shape `sh` over tile bits `pos`, built
   // from the n x n weight matrix `wmat` on first use.
   int32_t offset(const int32_t* wmat, int n, const TileShape& sh, const int8_t* pos, const RoundDev& rd);
+  // Offset (even) of the per-thread geometry table of a round over tile bits
+  // `pos`: NT padded shared-memory slots, then NT 64-bit global offsets.
+  int32_t geom_offset(const TileShape& sh, const int8_t* pos, const RoundDev& rd);
   void clear() { h.clear(); index.clear(); dirty = false; }
 };
 

@@ -18,6 +18,9 @@ struct RoundDev {
   uint8_t lam;     // adjoint: load psi only and create lambda = C(x) psi first
   uint8_t layout;  // menu layout id (plan.h, menu_layout)
   int32_t ctab;  // offset (in ints) of this round's cost tables, -1 if none
+  int32_t gtab;  // offset (in ints, even) of this round's per-thread geometry:
+                 // padded shared-memory slot (NT ints), then the global index
+                 // offset of the thread's lane and warp bits (NT 64-bit words)
 };
 
 // Contiguous runs of a sorted bit list: bits [src, src+len) of an index go to

@@ -106,36 +106,25 @@ __device__ __forceinline__ void apply_mixer(V* v, uint8_t mask, Real tau, Real a
   }
 }
 
-// Per-round thread geometry (runtime): the tile index of the thread's
-// amplitude 0, its padded shared-memory slot, its global index and the global
-// strides of the register bits.
+// Per-round thread geometry: the padded shared-memory slot of the thread's
+// amplitude 0 and its global index (tile base | the thread's lane and warp
+// bits), both read from the round's host-built table (one entry per thread),
+// and the global strides of the register bits.
 template <int R, int WB, int AB>
 struct RoundGeo {
   uint32_t sbase;
   uint64_t gb;
   uint64_t gstr[R];
-  __device__ __forceinline__ RoundGeo(const SubDev& sp, const RoundDev& rd, uint64_t gbase, int lane, int warp) {
-    uint32_t tb = 0;
-    gb = gbase;
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-      if (lane >> i & 1) { tb |= 1u << rd.lane[i]; gb |= 1ull << rd.glane[i]; }
-#pragma unroll
-    for (int i = 0; i < WB; ++i)
-      if (warp >> i & 1) { tb |= 1u << rd.warp[i]; gb |= 1ull << rd.gwarp[i]; }
+  __device__ __forceinline__ RoundGeo(const SubDev& sp, const RoundDev& rd, uint64_t gbase, int lane, int warp,
+                                      const int32_t* tabs) {
+    const int tid = (warp << 5) | lane;
+    sbase = (uint32_t)__ldg(tabs + rd.gtab + tid);
+    gb = gbase | __ldg(reinterpret_cast<const unsigned long long*>(tabs + rd.gtab + (32 << WB)) + tid);
 #pragma unroll
     for (int i = 0; i < R; ++i) gstr[i] = 1ull << rd.greg[i];
-    sbase = padi<AB>(tb);
   }
-  __device__ __forceinline__ static uint32_t sbase_of(const RoundDev& rd, int lane, int warp) {
-    uint32_t tb = 0;
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-      if (lane >> i & 1) tb |= 1u << rd.lane[i];
-#pragma unroll
-    for (int i = 0; i < WB; ++i)
-      if (warp >> i & 1) tb |= 1u << rd.warp[i];
-    return padi<AB>(tb);
+  __device__ __forceinline__ static uint32_t sbase_of(const RoundDev& rd, int lane, int warp, const int32_t* tabs) {
+    return (uint32_t)__ldg(tabs + rd.gtab + ((warp << 5) | lane));
   }
 };
 
@@ -238,7 +227,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
 #pragma unroll
     for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
   } else if (rd.src == SRC_SMEM_D) {
-    smem_load<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp), v);
+    smem_load<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp, A.ctabs), v);
   }
 
   apply_mixer<R>(v, rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA), FAST);
@@ -250,7 +239,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     if (!stream) rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
     auto for_costs = [&](auto&& f) {
       if (stream) {
-        const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
+        const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
         gray_ptr_walk<R>(A.diag, geo.gb, geo.gstr, [&](int j, const int32_t* q) { f(j, __ldcg(q)); });
       } else {
         int lin = rc.kappa;
@@ -333,7 +322,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   }
 
   if (rd.dst == DST_GLOBAL_D) {
-    const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp);
+    const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
     if (A.l2hint) {
       // outputs of a sub-pass that a later sub-pass reads back stay in L2
       const uint64_t pol = sp.keep ? l2_policy_evict_last() : l2_policy_evict_first();
@@ -342,7 +331,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       gray_ptr_walk<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
     }
   } else {
-    smem_store<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp), v);
+    smem_store<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp, A.ctabs), v);
   }
 }
 
@@ -369,7 +358,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       // issue the tile's global loads first: their latency overlaps the
       // barrier below and the tile constants
       if (sp.rd[0].src == SRC_GLOBAL_D) {
-        const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp);
+        const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
         const C2* gs = reinterpret_cast<const C2*>(A.state);
         if (A.l2hint) {
           const uint64_t pol = l2_policy_evict_first();
