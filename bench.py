@@ -23,6 +23,8 @@ phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
   forward with <C>, r and extremes, and forward + adjoint gradients): instances/s
   of one CUDA-graph replay of the persistent batch kernels, scheduling knobs
   picked by the autotuner; ``--batch-reps`` replays are timed.
+* ``configs``: qaoa_run + qaoa_expect once each on K_30 (complex128 and
+  complex64), K_32 complex128 and K_33 complex64 with the streamed cost diagonal.
 * ``--qubits n`` runs the same step on K_n (smaller cases for profiling; the
   JSON line then names that workload).
 * ``cpu_baseline`` / ``--impl reference``: the gate-by-gate complex128 oracle on
@@ -220,6 +222,37 @@ def grad_ratio(args, stream, reps: int = 3):
                 "d_dgamma": r["d_dgamma"], "d_dbeta": r["d_dbeta"]}
 
 
+def config_bench(args, stream):
+    """The other workloads of the method, timed once each (qaoa_run + qaoa_expect):
+    K_30 p=3 in complex128 and complex64 (16 GB / 8 GB states), K_32 complex128
+    (64 GiB, FP64-ALU-bound), and K_33 complex64 with the streamed int32 cost
+    diagonal instead of recomputed cut values."""
+    import torch
+    from paper_2604_26423_b300 import inputs
+    from paper_2604_26423_b300.qaoa import Simulator
+
+    out = []
+    for n, prec, mode in ((30, "c128", "recompute"), (30, "c64", "recompute"), (32, "c128", "recompute"),
+                          (33, "c64", "stream")):
+        u, v, w = inputs.complete_graph(n, SEED)
+        with Simulator(n, u, v, w, SCALE, prec, cost_mode=mode) as s:
+            s.run(P, DGAMMA, DBETA)
+            s.expect()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.run(P, DGAMMA, DBETA)
+            r = s.expect()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+        torch.cuda.empty_cache()
+        out.append({"n": n, "precision": prec, "cost_mode": mode, "p": P, "ms": ms, "layers_per_s": P / ms * 1e3,
+                    "r": r["r"], "exp_c": r["exp_c"]})
+    return out
+
+
 def batch_bench(args, stream):
     """Instances/s of the 4096-instance batch (forward, and forward + adjoint)."""
     import torch
@@ -326,6 +359,7 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     grad = None if args.no_grad else grad_ratio(args, stream)
     batch = None if args.no_batch else batch_bench(args, stream)
+    configs = None if args.no_configs else config_bench(args, stream)
 
     peak, peak_kind = measured_peak()
     achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else 0.0
@@ -366,6 +400,8 @@ def run_gpu(args):
         out["grad"] = grad
     if batch is not None:
         out["batch"] = batch
+    if configs is not None:
+        out["configs"] = configs
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     if rank == 0:
@@ -412,6 +448,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
