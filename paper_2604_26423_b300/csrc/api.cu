@@ -41,6 +41,8 @@ constexpr long long kMaxAbsWeightSum = 1 << 20;
 constexpr int kMaxGrid = 4096;           // persistent grid cap (partial-sum buffer size)
 constexpr int kFuseSumsMinQubits = 26;   // final pass writes sampling block sums from here on
 constexpr int kGroupOrder = ORDER_LOW_LAST;  // default group order of the pass plans
+constexpr int kFloatLanes = PLAN_FLOAT_LANES;  // default: lane bits float to a plain pass
+constexpr size_t kTileTableMaxBytes = size_t(1) << 30;  // per-context cap on per-tile constant tables
 
 thread_local std::string g_init_error;
 
@@ -81,6 +83,8 @@ struct qaoa_ctx {
   DevBuf d_sums, d_pre, d_pre2, d_shots, d_uni, d_ang;
   DevBuf d_lambda, d_gacc;                                            // adjoint vector (if no aux), per-pass sums
   TableStore tabs;                                                     // host copy of all cost tables
+  std::map<std::vector<int8_t>, DevBuf> tct_tabs;                     // per-tile constant tables by sub-pass layout
+  size_t tct_bytes = 0;
   std::map<std::pair<int, int>, std::unique_ptr<Plan>> plans;         // forward plans by (p, group order)
   std::map<std::pair<int, int>, std::unique_ptr<Plan>> bplans;        // adjoint plans by (p, group order)
   // per-kernel CUDA-event timing (qaoa_profile_enable / qaoa_profile_read)
@@ -196,6 +200,56 @@ int upload_ctabs(qaoa_ctx* c) {
   return QAOA_OK;
 }
 
+// Per-tile constant table of a forward sub-pass (tile_const_table_kernel),
+// built on first use and kept per layout (tile bits, super-tile bits); nullptr
+// (the kernel computes the constants per tile) when QAOA_TILE_TABLES=0 or the
+// context's tables would pass kTileTableMaxBytes.
+int tile_const_table(qaoa_ctx* c, const PassDev& pd, SubDev& sd) {
+  sd.tct = nullptr;
+  const char* e = getenv("QAOA_TILE_TABLES");
+  if (e && strcmp(e, "0") == 0) return QAOA_OK;
+  std::vector<int8_t> key(sd.pos, sd.pos + pd.T);
+  key.push_back(-1);
+  key.insert(key.end(), pd.outer, pd.outer + pd.nouter);
+  key.push_back(-2);
+  key.insert(key.end(), sd.inner, sd.inner + sd.ninner);
+  auto it = c->tct_tabs.find(key);
+  if (it != c->tct_tabs.end()) {
+    sd.tct = (const int32_t*)it->second.p;
+    return QAOA_OK;
+  }
+  const uint64_t ntiles = pd.n_units << sd.ninner;
+  const size_t bytes = size_t(ntiles) * kTileConstInts * 4;
+  if (c->tct_bytes + bytes > kTileTableMaxBytes) return QAOA_OK;
+  DevBuf b;
+  if (b.ensure(bytes) != cudaSuccess) {
+    cudaGetLastError();  // out of memory: fall back to the in-kernel constants
+    return QAOA_OK;
+  }
+  TileConstArgs a;
+  memset(&a, 0, sizeof a);
+  for (int j = 0; j < pd.T; ++j) a.pos[j] = sd.pos[j];
+  a.outer = pd.outer_runs;
+  a.inner = sd.inner_runs;
+  a.T = pd.T;
+  a.n = c->n;
+  a.ninner = sd.ninner;
+  a.ntiles = ntiles;
+  a.wmat = (const int32_t*)c->d_wmat.p;
+  a.out = (int32_t*)b.p;
+  tile_const_table_kernel<<<(unsigned)((ntiles + 255) / 256), 256, 0, c->stream>>>(a);
+  if (c->prof_on) ++c->nlaunch;
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) {
+    b.release();
+    return c->set_err(QAOA_ECUDA, "tile_const_table_kernel: %s", cudaGetErrorString(le));
+  }
+  c->tct_bytes += bytes;
+  sd.tct = (const int32_t*)b.p;
+  c->tct_tabs[key] = b;
+  return QAOA_OK;
+}
+
 // Phase tables exp(-i gamma_k s (W - 2c)) for c in [c_lo, c_hi], FP64 on the
 // host, rounded to the state precision (h(x) = W - 2 C(x), Eqs. H_C and UC).
 int upload_phases(qaoa_ctx* c, int p, const double* gamma) {
@@ -230,12 +284,22 @@ int smax_adj() {
   return v >= 12 && v <= 20 ? v : kSmaxAdj;
 }
 
-// Group order of the pass plans (plan.h): QAOA_GROUP_ORDER=middle or last.
+// Floating lane bits in the forward plans (PLAN_FLOAT_LANES): QAOA_FLOAT_LANES=0 or 1.
+int float_lanes_flag() {
+  const char* e = getenv("QAOA_FLOAT_LANES");
+  if (e && strcmp(e, "0") == 0) return 0;
+  if (e && strcmp(e, "1") == 0) return PLAN_FLOAT_LANES;
+  return kFloatLanes;
+}
+
+// Group order of the pass plans (plan.h): QAOA_GROUP_ORDER=middle or last,
+// with the floating-lane flag.
 int group_order() {
   const char* e = getenv("QAOA_GROUP_ORDER");
-  if (e && strcmp(e, "middle") == 0) return ORDER_LOW_MIDDLE;
-  if (e && strcmp(e, "last") == 0) return ORDER_LOW_LAST;
-  return kGroupOrder;
+  int o = kGroupOrder;
+  if (e && strcmp(e, "middle") == 0) o = ORDER_LOW_MIDDLE;
+  if (e && strcmp(e, "last") == 0) o = ORDER_LOW_LAST;
+  return o | float_lanes_flag();
 }
 
 // group orders of the gradient's forward and adjoint plans (QAOA_GRAD_ORDER
@@ -372,7 +436,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
   const long long nc = c->c_hi - c->c_lo + 1;
   // shared memory: tile | weights + tile consts | phase table (if it fits)
   const size_t tile_amps = ab == 8 ? padded_size<8>(T) : padded_size<16>(T);
-  const size_t base_smem = ((tile_amps * ab + 32 * 4 + 15) & ~size_t(15));
+  const size_t base_smem = ((tile_amps * ab + kTconstSmemInts * 4 + 15) & ~size_t(15));
   const size_t with_tab = base_smem + size_t(nc) * ab;
   int dev = 0, max_smem = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
@@ -412,6 +476,10 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       }
       if (!reduce) sd.needs_c = need;
       cc = cc || sd.needs_c || sd.init;
+      if (sd.needs_c && !stream) {
+        rc = tile_const_table(c, pds[pi], sd);
+        if (rc) return rc;
+      }
     }
     ccs[pi] = cc;
   }
@@ -1020,6 +1088,7 @@ void qaoa_free(qaoa_ctx* c) {
                     &c->d_ext_part, &c->d_sums, &c->d_pre, &c->d_pre2, &c->d_shots, &c->d_uni, &c->d_ang,
                     &c->d_lambda, &c->d_gacc};
   for (DevBuf* b : bufs) b->release();
+  for (auto& kv : c->tct_tabs) kv.second.release();
   for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;

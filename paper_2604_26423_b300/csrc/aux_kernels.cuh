@@ -140,6 +140,55 @@ cost_block_kernel(int n, const int32_t* __restrict__ wmat, int32_t* __restrict__
   }
 }
 
+// Per-tile constants of the pass kernels' C(x) tables (the quantities of
+// tile_consts in device.cuh) for every tile of one sub-pass, one thread per
+// tile. Tile t (kernel order: unit = t >> ninner, inner index t & (2^ninner-1))
+// has fixed index bits gbase = outer(unit) | inner(t); its row holds
+//   delta_j = sum_{g fixed} w[pos_j][g] (1 - 2 f_g)      at [j], j < T
+//   base    = sum_{g<h fixed} w_gh [f_g != f_h] + sum_j sum_{g fixed} w[pos_j][g] f_g   at [15]
+// so that C(x) = base + sum_j t_j delta_j + C_tile(t) for tile index t.
+struct TileConstArgs {
+  int8_t pos[16];
+  BitRuns outer, inner;
+  int T, n, ninner;
+  uint64_t ntiles;
+  const int32_t* wmat;
+  int32_t* out;
+};
+
+static __global__ void __launch_bounds__(256) tile_const_table_kernel(const TileConstArgs a) {
+  const uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
+  if (t >= a.ntiles) return;
+  const uint64_t gbase = a.outer.scatter(t >> a.ninner) | a.inner.scatter(t & ((1ull << a.ninner) - 1));
+  uint64_t tbits = 0;
+  for (int j = 0; j < a.T; ++j) tbits |= 1ull << a.pos[j];
+  int32_t row[kTileConstInts];
+  for (int i = 0; i < kTileConstInts; ++i) row[i] = 0;
+  int base = 0;
+  for (int j = 0; j < a.T; ++j) {
+    const int* wr = a.wmat + a.pos[j] * a.n;
+    int d = 0;
+    for (int g = 0; g < a.n; ++g) {
+      if (tbits >> g & 1ull) continue;
+      const int wg = __ldg(wr + g);
+      if (gbase >> g & 1ull) { d -= wg; base += wg; } else { d += wg; }
+    }
+    row[j] = d;
+  }
+  for (int g = 0; g < a.n; ++g) {
+    if (tbits >> g & 1ull) continue;
+    const uint64_t fg = gbase >> g & 1ull;
+    for (int h = g + 1; h < a.n; ++h) {
+      if (tbits >> h & 1ull) continue;
+      if (fg != (gbase >> h & 1ull)) base += __ldg(a.wmat + g * a.n + h);
+    }
+  }
+  row[15] = base;
+  int4* o = reinterpret_cast<int4*>(a.out + t * kTileConstInts);
+#pragma unroll
+  for (int i = 0; i < kTileConstInts / 4; ++i) o[i] = make_int4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
+}
+
 // Small n (< 15): one CTA, one thread per x, direct sum over all index pairs.
 static __global__ void cost_small_kernel(int n, const int32_t* __restrict__ wmat, int32_t* __restrict__ diag,
                                   Extreme* __restrict__ out) {

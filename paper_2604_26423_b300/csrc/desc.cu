@@ -218,6 +218,8 @@ std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInp
     pd.ph0 = turns_fixed(-g * (long double)(in.W - 2 * in.c_lo) / (2 * pi));
     pd.ph1 = turns_fixed(g / pi);
   }
+  pd.famp0 = float(pd.amp0);
+  int cost_rounds = 0;
   for (int s = 0; s < pd.nsub; ++s) {
     const SubPassPlan& sp = pp.subs[s];
     SubDev& sd = pd.sub[s];
@@ -245,11 +247,26 @@ std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInp
     sd.fscale = float(sd.scale);
     sd.rescale = sd.scale != 1.0;
     for (int r = 0; r < sd.nrounds; ++r) {
-      to_round_dev(sp.rounds[r], sd.rd[r]);
-      fill_round_globals(sd.rd[r], sd.pos);
-      sd.rd[r].gtab = tabs.geom_offset(sh, sd.pos, sd.rd[r]);
-      const bool wants = in.adjoint ? (sd.rd[r].cost || sd.rd[r].lam) : (sd.rd[r].cost || sd.rd[r].reduce);
-      if (wants && !in.stream) sd.rd[r].ctab = tabs.offset(in.wmat, in.n, sh, sd.pos, sd.rd[r]);
+      RoundDev& rd = sd.rd[r];
+      to_round_dev(sp.rounds[r], rd);
+      fill_round_globals(rd, sd.pos);
+      rd.gtab = tabs.geom_offset(sh, sd.pos, rd);
+      const bool wants = in.adjoint ? (rd.cost || rd.lam) : (rd.cost || rd.reduce);
+      if (wants && !in.stream) rd.ctab = tabs.offset(in.wmat, in.n, sh, sd.pos, rd);
+      if (in.adjoint || in.stream || rd.ctab < 0) continue;
+      // the forward kernels take the register-pair part CP[j] of the pass's
+      // cost round and reduction round from the descriptor
+      const int QN = 1 << (5 + sh.WB);
+      const int32_t* cp = tabs.h.data() + rd.ctab + QN + QN * sh.R + sh.R;
+      if (rd.cost) {
+        if (cost_rounds++) return "plan has two cost rounds in one pass";
+        for (int j = 0; j < (1 << sh.R); ++j) {
+          pd.cpc[j] = cp[j];
+          pd.cpt[j] = uint32_t(((uint64_t)(int64_t)cp[j] * pd.ph1) >> 32);
+        }
+      }
+      if (rd.reduce)
+        for (int j = 0; j < (1 << sh.R); ++j) pd.cpr[j] = cp[j];
     }
   }
   return "";

@@ -45,8 +45,17 @@ struct SubDev {
   uint8_t init, needs_c, store, keep, pad[4];  // keep: a later sub-pass reads this one's output
   float fscale;            // scale rounded to fp32 (complex64 kernels)
   int32_t rescale;         // scale != 1
+  // per-tile constants of the C(x) tables, one row of kTileConstInts ints per
+  // tile in the kernel's order (unit * 2^ninner + tile): delta_j for tile bit
+  // j at [j], the fixed-bit base at [15]; nullptr: computed in the kernel
+  const int32_t* tct;
   RoundDev rd[kMaxRoundsDev];
 };
+
+constexpr int kTileConstInts = 16;
+// shared-memory ints reserved for the tile constants (two buffers of 32:
+// delta[0..15], base at [16])
+constexpr int kTconstSmemInts = 64;
 
 struct PassDev {
   int32_t n, T, nsub, nouter;
@@ -65,6 +74,14 @@ struct PassDev {
   // cost phase of the pass's cost layer as 64-bit fixed-point turns:
   // exp(-i gamma s (W - 2c)) = exp(2 pi i (ph0 + (c - c_lo) ph1) / 2^64)
   uint64_t ph0, ph1;
+  float famp0;             // amp0 rounded to fp32
+  int32_t pad1;
+  // register-pair part CP[j] of C(x) (see RoundCost) for the pass's cost round
+  // (cpc) and reduction round (cpr), and cpt[j] = top 32 bits of CP[j] ph1 mod
+  // 2^64 (the cost round's phase increment in 2^-32 turns); in the parameter
+  // space, so the kernels take them as constant operands
+  int32_t cpc[32], cpr[32];
+  uint32_t cpt[32];
   SubDev sub[kMaxSubDev];
 };
 
@@ -109,6 +126,14 @@ template <typename Real> __device__ __forceinline__ Real pick(double d, float f)
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
+// exp(2 pi i t / 2^32) for a 32-bit turn count t (the signed angle in [-pi, pi)).
+__device__ __forceinline__ float2 phase_turns32(uint32_t t) {
+  const float ang = float(int32_t(t)) * 1.46291807926715968e-9f;  // 2 pi / 2^32
+  float sn, cs;
+  __sincosf(ang, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
 // exp(2 pi i t / 2^64) for the turn count t = ph0 + u ph1 (mod 2^64), u >= 0:
 // the top 32 bits of t as a signed angle in [-pi, pi), then the hardware sine
 // and cosine (absolute error about 4e-7, below the complex64 state's rounding
@@ -116,10 +141,7 @@ template <> __device__ __forceinline__ double pick<double>(double d, float) { re
 __device__ __forceinline__ float2 phase_turns(uint64_t ph0, uint64_t ph1, uint32_t u) {
   const uint64_t lo = (uint64_t)u * (uint32_t)ph1 + (uint32_t)ph0;
   const uint32_t hi = (uint32_t)(ph0 >> 32) + u * (uint32_t)(ph1 >> 32) + (uint32_t)(lo >> 32);
-  const float ang = float(int32_t(hi)) * 1.46291807926715968e-9f;  // 2 pi / 2^32
-  float sn, cs;
-  __sincosf(ang, &sn, &cs);
-  return make_float2(cs, sn);
+  return phase_turns32(hi);
 }
 
 template <typename Real> struct Cx;
@@ -216,6 +238,17 @@ struct RoundCost {
       e[i] = tconst[regbits[i]] + __ldg(tab + QN + QN * R + i) - 2 * aj;
     }
     cp = tab + QN + QN * R + R;
+  }
+  // Phase increments in 2^-32 turns for the cost layer with turn constants
+  // (ph0, ph1) (see PassDev): returns t0 = top32(ph0 + (kappa - c_lo) ph1) and
+  // E[i] = top32(e_i ph1) (products mod 2^64), so that the 32-bit turn count
+  // of register amplitude j is t0 + sum_{i: j_i = 1} E[i] + cpt[j]. Against the
+  // exact top32(ph0 + (C(j) - c_lo) ph1) it lacks the carries of the dropped
+  // low words: 0 to 6 units of 2^-32 turns (below 1e-8 rad).
+  __device__ __forceinline__ uint32_t turns(uint64_t ph0, uint64_t ph1, int c_lo, uint32_t* E) const {
+#pragma unroll
+    for (int i = 0; i < R; ++i) E[i] = uint32_t(((uint64_t)(int64_t)e[i] * ph1) >> 32);
+    return uint32_t((ph0 + (uint64_t)(int64_t)(kappa - c_lo) * ph1) >> 32);
   }
   __device__ __forceinline__ int operator()(int j) const {
     int c = kappa + __ldg(cp + j);

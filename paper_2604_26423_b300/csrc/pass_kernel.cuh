@@ -223,9 +223,16 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   const bool stream = A.diag != nullptr;
   // the round's geometry is rebuilt where needed instead of being kept live
   // across the butterflies (register pressure)
-  if (CC && rd.src == SRC_INIT_D) {
+  // complex64 with C(x) from the tables: the phase from 32-bit turn increments
+  constexpr bool kTurns = sizeof(Real) == 4;
+  const bool init = CC && rd.src == SRC_INIT_D;
+  if (init) {
+    // |+>: every amplitude amp0; with the turn path the cost round writes
+    // amp0 times the phase directly
+    if (!kTurns || stream || !rd.cost) {
 #pragma unroll
-    for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
+      for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
+    }
   } else if (rd.src == SRC_SMEM_D) {
     smem_load<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp, A.ctabs), v);
   }
@@ -235,13 +242,17 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   if (CC && (rd.cost | rd.reduce)) {
     // C(x) of register amplitude j: streamed from the diagonal, or
     // kappa + CP[j] + sum_{i: j_i = 1} e_i from the round's tables
-    RoundCost<R, WB> rc;
-    if (!stream) rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
-    auto for_costs = [&](auto&& f) {
+    // C(x) of each register amplitude (streamed, or from the round's tables;
+    // cp: the round's register-pair table CP[j], of the pass's cost or
+    // reduction round). The tables are set up separately for the cost phase
+    // and for the reduction so that neither keeps them live across the other.
+    auto for_costs = [&](const int32_t* cp, auto&& f) {
       if (stream) {
         const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
         gray_ptr_walk<R>(A.diag, geo.gb, geo.gstr, [&](int j, const int32_t* q) { f(j, __ldcg(q)); });
       } else {
+        RoundCost<R, WB> rc;
+        rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
         int lin = rc.kappa;
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
@@ -250,19 +261,47 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
             const int b = ctz_c(k);
             lin += (j >> b & 1) ? rc.e[b] : -rc.e[b];
           }
-          f(j, lin + __ldg(rc.cp + j));
+          f(j, lin + cp[j]);
         }
       }
     };
     if (rd.cost) {
-      for_costs([&](int j, int c) {
-        C2 ph;
-        if constexpr (sizeof(Real) == 4) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo));
-        else ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
-        const Real xr = v[j].x, xi = v[j].y;
-        v[j].x = xr * ph.x - xi * ph.y;
-        v[j].y = xr * ph.y + xi * ph.x;
-      });
+      if (kTurns && !stream) {
+        // turn count of amplitude j: t0 + sum_{i: j_i} E_i + cpt[j] (Gray order)
+        uint32_t E[R];
+        uint32_t t;
+        {
+          RoundCost<R, WB> rc;
+          rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
+          t = rc.turns(P.ph0, P.ph1, P.c_lo, E);
+        }
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          const int j = k ^ (k >> 1);
+          if (k) {
+            const int b = ctz_c(k);
+            t += (j >> b & 1) ? E[b] : 0u - E[b];
+          }
+          const float2 ph = phase_turns32(t + P.cpt[j]);
+          if (init) {
+            v[j].x = P.famp0 * ph.x;
+            v[j].y = P.famp0 * ph.y;
+          } else {
+            const Real xr = v[j].x, xi = v[j].y;
+            v[j].x = xr * ph.x - xi * ph.y;
+            v[j].y = xr * ph.y + xi * ph.x;
+          }
+        }
+      } else {
+        for_costs(P.cpc, [&](int j, int c) {
+          C2 ph;
+          if constexpr (sizeof(Real) == 4) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo));
+          else ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
+          const Real xr = v[j].x, xi = v[j].y;
+          v[j].x = xr * ph.x - xi * ph.y;
+          v[j].y = xr * ph.y + xi * ph.x;
+        });
+      }
     }
     apply_mixer<R>(v, rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB), FAST);
     if (rd.dst == DST_GLOBAL_D && sp.rescale) {
@@ -282,7 +321,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
 #pragma unroll
         for (int i = 0; i < WB; ++i) hthr |= rd.warp[i] == 12 ? (warp >> i & 1) : 0;
         Real s0 = 0, s1 = 0;
-        for_costs([&](int j, int c) {
+        for_costs(P.cpr, [&](int j, int c) {
           const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
           sn += pr;
           scc = fma(pr, Real(c), scc);
@@ -300,7 +339,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
           wacc[2 * (32 << WB) + 2 * warp + 1] = double(s1);
         }
       } else {
-        for_costs([&](int j, int c) {
+        for_costs(P.cpr, [&](int j, int c) {
           const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
           sn += pr;
           scc = fma(pr, Real(c), scc);
@@ -337,10 +376,13 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
 
 // One super-tile (unit) of a forward pass: every tile of each of its sub-passes.
 // All threads of the CTA take part; shared memory is free again on return.
+// tcount: the CTA's running tile count (selects the tile-constant buffer when
+// the constants come from a table); may be null when no sub-pass has a table.
 template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tile, int* tconst,
-                                         const typename Cx<Real>::T* phase, double* wacc) {
+                                         const typename Cx<Real>::T* phase, double* wacc,
+                                         uint32_t* tcount = nullptr) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -367,8 +409,18 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
           gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = __ldcg(q); });
         }
       }
+      // tile constants from the table: into the buffer the previous tile did
+      // not use, published by the barrier below
+      int* tc = tconst;
+      const bool tab = CC && sp.needs_c && !stream && sp.tct != nullptr;
+      if (tab) {
+        tc = tconst + 32 * (*tcount & 1u);
+        *tcount += 1;
+        if (tid < kTileConstInts)
+          tc[tid == 15 ? 16 : tid] = __ldg(sp.tct + (((unit << sp.ninner) + ti) * kTileConstInts + tid));
+      }
       __syncthreads();  // previous tile finished with shared memory
-      if (CC && sp.needs_c && !stream) {
+      if (CC && sp.needs_c && !stream && !tab) {
         if (tid == 0) tconst[16] = 0;
         __syncthreads();
         tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
@@ -377,7 +429,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       for (int r = 0; r < sp.nrounds; ++r) {
         const RoundDev& rd = sp.rd[r];
         if (rd.src == SRC_SMEM_D) __syncthreads();
-        fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, tconst, phase, lane, warp, wacc, v);
+        fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, tc, phase, lane, warp, wacc, v);
       }
       if (CC && A.bsum && sp.rd[sp.nrounds - 1].reduce) {
         // this tile is 2^T consecutive amplitudes: its 2^(T-12) block sums, in warp order
@@ -394,7 +446,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
 }
 
 // Shared-memory layout of the dynamic buffer:
-//   tile[padded 2^T] complex | tile consts [16] int + base | phase table
+//   tile[padded 2^T] complex | tile consts (two buffers) | phase table
 // (the weight matrix is read through the L1 cache by one warp per tile)
 template <typename Real, int R, int WB, bool FAST, bool CC>
 __global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : 2) : 1)
@@ -406,8 +458,8 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   constexpr uint32_t TILE = padded_size<AB>(T);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2* tile = reinterpret_cast<C2*>(smem_raw);
-  int* tconst = reinterpret_cast<int*>(tile + TILE);  // delta[0..15], base at [16]
-  C2* ptab = reinterpret_cast<C2*>(smem_raw + ((size_t(TILE) * AB + 32 * 4 + 15) & ~size_t(15)));
+  int* tconst = reinterpret_cast<int*>(tile + TILE);  // 2 x (delta[0..15], base at [16])
+  C2* ptab = reinterpret_cast<C2*>(smem_raw + ((size_t(TILE) * AB + kTconstSmemInts * 4 + 15) & ~size_t(15)));
 
   const int tid = threadIdx.x;
   const C2* phase = reinterpret_cast<const C2*>(A.phase);
@@ -420,8 +472,9 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   wacc[2 * tid] = 0.0;
   wacc[2 * tid + 1] = 0.0;
 
+  uint32_t tcount = 0;
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    fwd_unit<Real, R, WB, FAST, CC>(P, A, unit, tile, tconst, phase, wacc);
+    fwd_unit<Real, R, WB, FAST, CC>(P, A, unit, tile, tconst, phase, wacc, &tcount);
 
   if (A.partial) {
     __syncthreads();

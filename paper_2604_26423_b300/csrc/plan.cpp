@@ -322,12 +322,19 @@ std::vector<Proto> pack_ops(const std::vector<Op>& ops) {
   return out;
 }
 
-void build_passes(Plan& plan, const std::vector<Group>& groups, const std::vector<Proto>& protos, bool backward) {
+// extra[pi]: qubits whose mixer pass pi applies besides its group's (floating
+// lane bits, see PLAN_FLOAT_LANES), or empty.
+void build_passes(Plan& plan, const std::vector<Group>& groups, const std::vector<Proto>& protos, bool backward,
+                  const std::vector<std::vector<int>>& extra) {
   const int n = plan.n, T = plan.shape.T();
   for (size_t pi = 0; pi < protos.size(); ++pi) {
     const Proto& pr = protos[pi];
     PassPlan pp;
-    const Group& g = groups[pr.grp];
+    Group g = groups[pr.grp];
+    if (!extra[pi].empty()) {
+      g.targets.insert(g.targets.end(), extra[pi].begin(), extra[pi].end());
+      std::sort(g.targets.begin(), g.targets.end());
+    }
     pp.sb = g.sb;
     for (int b = 0; b < n; ++b)
       if (std::find(g.sb.begin(), g.sb.end(), b) == g.sb.end()) pp.outer.push_back(b);
@@ -399,9 +406,9 @@ Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2,
   int S = std::min(s_max, std::max(T, n - min_units_log2));
   S = std::min(S, n);
   plan.S = S;
-  const std::vector<Group> groups = make_groups(n, S);
-  for (auto& g : groups) plan.groups.push_back(g.targets);
+  std::vector<Group> groups = make_groups(n, S);
   const int G = (int)groups.size();
+  const int base_order = order & 3;
   // Base order ord[]: the last layer ends on ord[0]. ORDER_LOW_LAST keeps
   // groups by bit position (ending on the low, index-contiguous group: the
   // final pass sees whole contiguous blocks, for odd p the write-only first
@@ -409,7 +416,7 @@ Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2,
   // groups at the ends and the low group next to ord[0].
   std::vector<int> ord(G);
   for (int i = 0; i < G; ++i) ord[i] = i;
-  if (order == ORDER_LOW_MIDDLE && G >= 3) {
+  if (base_order == ORDER_LOW_MIDDLE && G >= 3) {
     std::vector<int> high;
     for (int i = 1; i < G; ++i) high.push_back(i);
     std::stable_sort(high.begin(), high.end(),
@@ -439,7 +446,36 @@ Plan make_plan(int n, int p, const TileShape& sh, int s_max, int min_units_log2,
       ops.push_back({OP_COST, k, -1});
     }
   }
-  build_passes(plan, groups, pack_ops(ops), backward);
+  const std::vector<Proto> protos = pack_ops(ops);
+  std::vector<std::vector<int>> extra(protos.size());
+  if (!backward && (order & PLAN_FLOAT_LANES) && G >= 3) {
+    // bits that every high group's tiles carry: 0..r-1
+    int r = 32;
+    for (int gi = 1; gi < G; ++gi) {
+      int k = 0;
+      while (k < (int)groups[gi].sb.size() && groups[gi].sb[k] == k) ++k;
+      r = std::min(r, k);
+    }
+    // host of layer k: its plain pass on the high group with the fewest targets
+    std::vector<int> host(p, -1);
+    for (size_t pi = 0; pi < protos.size(); ++pi) {
+      const Proto& pr = protos[pi];
+      if (pr.a < 0 || pr.cost >= 0 || pr.b >= 0 || pr.grp == 0) continue;
+      int& h = host[pr.a];
+      if (h < 0 || groups[pr.grp].targets.size() < groups[protos[h].grp].targets.size()) h = (int)pi;
+    }
+    const bool ok = r > 0 && std::all_of(host.begin(), host.end(), [](int h) { return h >= 0; });
+    if (ok) {
+      std::vector<int> lanes;
+      for (int b = 0; b < r; ++b) lanes.push_back(b);
+      auto& t0 = groups[0].targets;
+      t0.erase(std::remove_if(t0.begin(), t0.end(), [&](int b) { return b < r; }), t0.end());
+      for (int k = 0; k < p; ++k) extra[host[k]] = lanes;
+      plan.float_lanes = r;
+    }
+  }
+  for (auto& g : groups) plan.groups.push_back(g.targets);
+  build_passes(plan, groups, protos, backward, extra);
   return plan;
 }
 
@@ -524,7 +560,9 @@ std::string validate(const Plan& plan) {
 std::string Plan::describe() const {
   std::ostringstream os;
   os << "n=" << n << " p=" << p << " S=" << S << " T=" << shape.T() << " R=" << shape.R
-     << " WB=" << shape.WB << " groups=" << groups.size() << " passes=" << passes.size() << "\n";
+     << " WB=" << shape.WB << " groups=" << groups.size() << " passes=" << passes.size();
+  if (float_lanes) os << " float_lanes=" << float_lanes;
+  os << "\n";
   for (size_t g = 0; g < groups.size(); ++g) {
     os << "group " << g << ":";
     for (int q : groups[g]) os << " " << q;

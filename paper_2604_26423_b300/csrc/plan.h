@@ -83,6 +83,7 @@ struct Plan {
   bool backward = false;
   TileShape shape;
   std::vector<std::vector<int>> groups; // qubit groups (one pass each per layer)
+  int float_lanes = 0;                  // bits 0..float_lanes-1 float (PLAN_FLOAT_LANES)
   std::vector<PassPlan> passes;
   std::string describe() const;
 };
@@ -95,6 +96,16 @@ struct Plan {
 //   ORDER_LOW_MIDDLE: the low group away from both ends when there are three or
 //     more groups, so the fused passes fall on the smaller high groups.
 enum GroupOrder { ORDER_LOW_LAST = 0, ORDER_LOW_MIDDLE = 1 };
+
+// Flag or-ed into the order argument of plan_forward: the index bits that
+// every tile carries for coalescing (bits 0..4, or 0..3) leave the low group,
+// and each layer applies their mixer in one of its plain passes (no cost
+// phase) on a high group, whose tile holds them anyway. The fused passes and
+// the final pass then work on the low group's remaining bits only (fewer
+// butterflies and shared-memory rounds where the pass is instruction-bound);
+// the plain pass that takes them gains a round. Applies when every layer has
+// a plain pass on a high group (three or more groups); otherwise ignored.
+constexpr int PLAN_FLOAT_LANES = 4;
 
 // Forward plan for n qubits and depth p (n >= shape.T()).
 // s_max: largest super-tile bit count; min_units_log2: keep at least 2^x super-tiles.

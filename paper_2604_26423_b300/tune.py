@@ -28,6 +28,9 @@ SUPER_TILES = (13, 14, 15)
 # final pass also writes the sampling block sums), or the low group away from
 # the fused passes
 GROUP_ORDERS = ("last", "middle")
+# coalescing bits 0..4 applied in a plain high-group pass of each layer (1) or
+# with the low group (0)
+FLOAT_LANES = (1, 0)
 
 
 @contextlib.contextmanager
@@ -49,22 +52,23 @@ def _env(settings: dict):
 
 
 def forward_candidates(n: int, precision: str = "c64", modes=("recompute", "stream"), shapes=None,
-                       super_tiles=SUPER_TILES, orders=GROUP_ORDERS):
-    """Configurations to time for one instance: cost mode x tile shape x super-tile bits x group order."""
+                       super_tiles=SUPER_TILES, orders=GROUP_ORDERS, float_lanes=FLOAT_LANES):
+    """Configurations to time for one instance: cost mode x tile shape x super-tile bits x group order x
+    floating lane bits."""
     if shapes is None:
         shapes = tuple(FWD_SHAPES) if precision == "c64" else ("5x3",)
     out = []
-    for mode, shape, st, order in itertools.product(modes, shapes, super_tiles, orders):
+    for mode, shape, st, order, fl in itertools.product(modes, shapes, super_tiles, orders, float_lanes):
         if st > n:
             continue
-        out.append({"cost_mode": mode, "shape": shape, "super_tile": st, "order": order})
+        out.append({"cost_mode": mode, "shape": shape, "super_tile": st, "order": order, "float_lanes": fl})
     return out
 
 
 def config_env(cfg: dict) -> dict:
     """Environment settings that select a forward configuration in the library."""
     return {"QAOA_FWD_SHAPE": FWD_SHAPES[cfg["shape"]], "QAOA_SMAX": cfg["super_tile"],
-            "QAOA_GROUP_ORDER": cfg.get("order", "last")}
+            "QAOA_GROUP_ORDER": cfg.get("order", "last"), "QAOA_FLOAT_LANES": int(cfg.get("float_lanes", 1))}
 
 
 def _time_ms(fn, stream, reps: int) -> float:

@@ -83,27 +83,76 @@ def test_batch_instances_shape():
 def test_tuner_candidates():
     from paper_2604_26423_b300 import tune
     c = tune.forward_candidates(33, "c64")
-    assert {"cost_mode": "recompute", "shape": "5x3", "super_tile": 13, "order": "last"} in c
+    assert {"cost_mode": "recompute", "shape": "5x3", "super_tile": 13, "order": "last", "float_lanes": 1} in c
+    assert {"cost_mode": "recompute", "shape": "5x3", "super_tile": 13, "order": "last", "float_lanes": 0} in c
     assert all(x["super_tile"] <= 33 for x in c)
     assert {x["shape"] for x in tune.forward_candidates(30, "c128")} == {"5x3"}
-    env = tune.config_env({"cost_mode": "stream", "shape": "4x4", "super_tile": 14, "order": "middle"})
-    assert env == {"QAOA_FWD_SHAPE": "4x4", "QAOA_SMAX": 14, "QAOA_GROUP_ORDER": "middle"}
+    env = tune.config_env({"cost_mode": "stream", "shape": "4x4", "super_tile": 14, "order": "middle",
+                           "float_lanes": 0})
+    assert env == {"QAOA_FWD_SHAPE": "4x4", "QAOA_SMAX": 14, "QAOA_GROUP_ORDER": "middle", "QAOA_FLOAT_LANES": 0}
     b = tune.batch_candidates(solo=(16,), units=(1, 2), ctas=(2,))
     assert b == [dict(solo_max_n=16, max_units=1, ctas_per_sm=2), dict(solo_max_n=16, max_units=2, ctas_per_sm=2)]
 
 
 def test_group_orders_give_valid_plans():
-    # both group orders plan every size validly (checked by the planner's validator)
-    import re
+    # both group orders, with and without floating lane bits, plan every size
+    # validly (checked by the planner's validator)
     import os
     from paper_2604_26423_b300 import qaoa
     for order in ("last", "middle"):
-        os.environ["QAOA_GROUP_ORDER"] = order
-        try:
-            for n in (13, 14, 20, 26, 30, 33, 34):
-                for p in (1, 2, 3, 4):
-                    for adj in (False, True):
-                        d = qaoa.describe_plan(n, p, "c64", adjoint=adj)
-                        assert "passes=" in d
-        finally:
-            os.environ.pop("QAOA_GROUP_ORDER", None)
+        for fl in ("0", "1"):
+            os.environ["QAOA_GROUP_ORDER"] = order
+            os.environ["QAOA_FLOAT_LANES"] = fl
+            try:
+                for n in (13, 14, 20, 22, 26, 30, 33, 34):
+                    for p in (1, 2, 3, 4):
+                        for adj in (False, True):
+                            for prec in ("c64", "c128"):
+                                d = qaoa.describe_plan(n, p, prec, adjoint=adj)
+                                assert "passes=" in d and "INVALID" not in d and "error" not in d, d
+            finally:
+                os.environ.pop("QAOA_GROUP_ORDER", None)
+                os.environ.pop("QAOA_FLOAT_LANES", None)
+
+
+def test_float_lanes_plan_shape():
+    # n = 33, p = 3: the coalescing bits 0..4 leave the low group; each layer
+    # applies them once in a plain pass on a high group; the fused low-group pass
+    # and the final pass lose a shared-memory round trip each; the pass count
+    # is unchanged
+    import os
+    import re
+    from paper_2604_26423_b300 import qaoa
+    os.environ["QAOA_FLOAT_LANES"] = "1"
+    try:
+        d = qaoa.describe_plan(33, 3, "c64")
+    finally:
+        os.environ.pop("QAOA_FLOAT_LANES", None)
+    os.environ["QAOA_FLOAT_LANES"] = "0"
+    try:
+        d0 = qaoa.describe_plan(33, 3, "c64")
+    finally:
+        os.environ.pop("QAOA_FLOAT_LANES", None)
+    assert "float_lanes=5" in d and "float_lanes" not in d0
+    assert "group 0: 5 6 7 8 9 10 11 12\n" in d
+    assert "passes=10" in d and "passes=10" in d0
+
+    def rounds(desc):
+        out, cur = [], None
+        for line in desc.splitlines():
+            if line.startswith("pass "):
+                cur = [line, 0, 0]
+                out.append(cur)
+            m = re.match(r"  sub \d+ tile=.* nA=(\d+) nB=(\d+)", line)
+            if m:
+                cur[2] += int(m.group(1)) + int(m.group(2))
+            if line.startswith("    round"):
+                cur[1] += 1
+        return out
+    r1, r0 = rounds(d), rounds(d0)
+    # total butterflies per amplitude and layer count unchanged: 33 qubits x 3 layers
+    assert sum(x[2] for x in r1) == sum(x[2] for x in r0) == 99
+    fused = [i for i, x in enumerate(r1) if " c=" in x[0] and " c=-1" not in x[0] and "init" not in x[0]]
+    for i in fused + [len(r1) - 1]:
+        assert r1[i][1] <= r0[i][1]
+    assert r1[3][1] == 3 and r0[3][1] == 5 and r1[9][1] == 2 and r0[9][1] == 3

@@ -105,14 +105,39 @@ def test_explicit_angles_wide_range(n, prec):
 
 
 @pytest.mark.parametrize("n", [14, 18])
-def test_stream_equals_recompute_bitwise(n):
+def test_stream_vs_recompute(n):
+    # complex128: both cost modes index the same phase table with the same
+    # integer C(x): bitwise equal. complex64: the recompute path sums 32-bit
+    # turn increments whose dropped carries move a phase by < 1e-8 rad against
+    # the streamed diagonal's exact turn count, so the states agree to FP32
+    # rounding of the phase factors
     u, v, w = graph("complete", n, 400 + n)
+    for prec in ("c128", "c64"):
+        outs = []
+        for mode in ("recompute", "stream"):
+            with sim(n, u, v, w, S, prec, cost_mode=mode) as s:
+                s.run(3, 0.6, 0.3)
+                outs.append(s.state().cpu().numpy().copy())
+        if prec == "c128":
+            assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
+        else:
+            assert float(np.linalg.norm(outs[0].astype(np.complex128) - outs[1])) <= 2e-6
+
+
+@pytest.mark.parametrize("n,prec", [(22, "c64"), (22, "c128"), (26, "c64")])
+def test_tile_tables_bitwise(n, prec, monkeypatch):
+    # per-tile constants from the precomputed table or from the in-kernel
+    # computation are the same integers: identical states, <C> and block sums
+    u, v, w = graph("complete", n, 500 + n)
     outs = []
-    for mode in ("recompute", "stream"):
-        with sim(n, u, v, w, S, "c64", cost_mode=mode) as s:
+    for tab in ("1", "0"):
+        monkeypatch.setenv("QAOA_TILE_TABLES", tab)
+        with sim(n, u, v, w, S, prec) as s:
             s.run(3, 0.6, 0.3)
-            outs.append(s.state().cpu().numpy().copy())
-    assert np.array_equal(outs[0].view(np.uint64), outs[1].view(np.uint64))
+            outs.append((s.state().cpu().numpy().copy(), s.expect()["exp_c"], s.sample(512, seed=3)))
+    (a, ea, sa), (b, eb, sb) = outs
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    assert ea == eb and np.array_equal(sa, sb)
 
 
 def _boundary(psi, uni, tol=1e-9):
@@ -274,3 +299,32 @@ def test_single_layer_vs_closed_form_at_large_n(n, prec):
     tol = 2e-6 if prec == "c64" else 1e-11
     assert abs(res["exp_c"] - ref) <= tol * ref, (res["exp_c"], ref)
     assert abs(res["norm"] - 1.0) <= (1e-5 if prec == "c64" else 1e-12)
+
+
+_plan_ref = {}
+
+
+@pytest.mark.parametrize("n,p", [(22, 3), (23, 4)])
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("order", ["last", "middle"])
+@pytest.mark.parametrize("float_lanes", ["0", "1"])
+def test_plan_options_vs_oracle(n, p, prec, order, float_lanes, monkeypatch):
+    # every plan option (group order, coalescing bits floated to a plain pass)
+    # gives the oracle's state; three groups at these sizes, so each layer has
+    # a plain high-group pass that can host the floating bits
+    monkeypatch.setenv("QAOA_GROUP_ORDER", order)
+    monkeypatch.setenv("QAOA_FLOAT_LANES", float_lanes)
+    u, v, w = inputs.complete_graph(n, 8100 + n)
+    if (n, p) not in _plan_ref:
+        g, b = oracle.lr_schedule(p, 0.6, 0.3)
+        _plan_ref[(n, p)] = oracle.run(n, u, v, w, S, g, b)
+    ref = _plan_ref[(n, p)]
+    with sim(n, u, v, w, S, prec) as s:
+        s.run(p, 0.6, 0.3)
+        res = s.expect()
+        psi = state_np(s)
+    l2 = float(np.linalg.norm(psi - ref["psi"]))
+    if prec == "c64":
+        assert l2 <= 1e-4 and abs(res["r"] - ref["r"]) <= 1e-5
+    else:
+        assert l2 <= 1e-12 and abs(res["r"] - ref["r"]) <= 1e-9
