@@ -114,7 +114,9 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   const bool need_c = CC && (rd.cost || rd.lam);
   RoundCost<R, WB> rcost;
   if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
-  auto for_costs = [&](auto&& f) {
+  // cp: the register-pair table CP[j] of the pass's cost round (P.cpc) or
+  // lambda-creation round (P.cpr), from the descriptor
+  auto for_costs = [&](const int32_t* cp, auto&& f) {
     if (stream) {
       gray_ptr_walk<R>(A.diag, geo.gb, geo.gstr, [&](int j, const int32_t* q) { f(j, __ldcg(q)); });
     } else {
@@ -126,7 +128,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
           const int b = ctz_c(k);
           lin += (j >> b & 1) ? rcost.e[b] : -rcost.e[b];
         }
-        f(j, lin + __ldg(rcost.cp + j));
+        f(j, lin + cp[j]);
       }
     }
   };
@@ -136,7 +138,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     if (CC && rd.lam) {
       // lambda = C(x) psi (the operator whose expectation is differentiated);
       // <psi|lambda> = <C> on the way
-      for_costs([&](int j, int c) {
+      for_costs(P.cpr, [&](int j, int c) {
         const Real cr = Real(c);
         l[j].x = cr * v[j].x;
         l[j].y = cr * v[j].y;
@@ -152,7 +154,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
                    pow_bits(pick<Real>(P.cA, P.fcA), rd.mixA), sc, ga);
   if (CC && rd.cost) {
     Real tc = 0;
-    for_costs([&](int j, int c) {
+    for_costs(P.cpc, [&](int j, int c) {
       const Real h = Real(P.wsum - 2 * c);
       tc = fma(fma(l[j].x, v[j].y, -l[j].y * v[j].x), h, tc);
       C2 ph;
@@ -190,11 +192,13 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
 
 // One super-tile (unit) of an adjoint pass; the gradient terms of this
 // thread's amplitudes are added to gA, gC, gB.
+// tcount: the CTA's running tile count (tile-constant buffer when the
+// constants come from a table); may be null when no sub-pass has a table.
 template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, int* tconst,
                                          const typename Cx<Real>::T* phase, double& gA, double& gC, double& gB,
-                                         double& gE) {
+                                         double& gE, uint32_t* tcount = nullptr) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -218,8 +222,16 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
           gray_ptr_walk<R>(reinterpret_cast<const C2*>(A.lam), g0.gb, g0.gstr,
                            [&](int j, const C2* q) { l[j] = __ldcg(q); });
       }
+      int* tc = tconst;
+      const bool tab = CC && sp.needs_c && !stream && sp.tct != nullptr;
+      if (tab) {
+        tc = tconst + 32 * (*tcount & 1u);
+        *tcount += 1;
+        if (tid < kTileConstInts)
+          tc[tid == 15 ? 16 : tid] = __ldg(sp.tct + (((unit << sp.ninner) + ti) * kTileConstInts + tid));
+      }
       __syncthreads();
-      if (CC && sp.needs_c && !stream) {
+      if (CC && sp.needs_c && !stream && !tab) {
         if (tid == 0) tconst[16] = 0;
         __syncthreads();
         tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
@@ -230,7 +242,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, gA, gC, gB, gE, sc,
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tc, phase, lane, warp, gA, gC, gB, gE, sc,
                                            v, l);
         }
       } else {
@@ -240,7 +252,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tconst, phase, lane, warp, ga, gc, gbv, ge, sc,
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tc, phase, lane, warp, ga, gc, gbv, ge, sc,
                                            v, l);
         }
         gA += double(ga);
@@ -253,7 +265,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
   }
 }
 
-// Shared memory: psi tile (padded 2^T) | lambda tile | tile consts | phase table
+// Shared memory: psi tile (padded 2^T) | lambda tile | tile consts (two buffers) | phase table
 template <typename Real, int R, int WB, bool FAST, bool CC>
 __global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
 adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
@@ -266,7 +278,7 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
   C2* tv = reinterpret_cast<C2*>(smem_raw);
   C2* tl = tv + TILE;
   int* tconst = reinterpret_cast<int*>(tl + TILE);
-  C2* ptab = reinterpret_cast<C2*>(smem_raw + ((size_t(2 * TILE) * AB + 32 * 4 + 15) & ~size_t(15)));
+  C2* ptab = reinterpret_cast<C2*>(smem_raw + ((size_t(2 * TILE) * AB + kTconstSmemInts * 4 + 15) & ~size_t(15)));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const C2* phase = reinterpret_cast<const C2*>(A.phase);
   if (A.phase_in_smem && A.phase) {
@@ -275,8 +287,9 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
   }
   double gA = 0.0, gC = 0.0, gB = 0.0, gE = 0.0;
 
+  uint32_t tcount = 0;
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    adj_unit<Real, R, WB, FAST, CC>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE);
+    adj_unit<Real, R, WB, FAST, CC>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE, &tcount);
 
   __shared__ double red[4][32];
   for (int o = 16; o > 0; o >>= 1) {

@@ -668,7 +668,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   const bool stream = c->cost_mode == QAOA_COST_STREAM;
   const long long nc = c->c_hi - c->c_lo + 1;
   const size_t tile_amps = ab == 8 ? padded_size<8>(T) : padded_size<16>(T);
-  const size_t base_smem = ((2 * tile_amps * ab + 32 * 4 + 15) & ~size_t(15));
+  const size_t base_smem = ((2 * tile_amps * ab + kTconstSmemInts * 4 + 15) & ~size_t(15));
   const size_t with_tab = base_smem + size_t(nc) * ab;
   int dev = 0, max_smem = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
@@ -695,6 +695,12 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     const std::string why = fill_pass_dev(plan->passes[pi], sh, in, c->tabs, pds[pi], fast);
     if (!why.empty()) return c->set_err(QAOA_EINVAL, "%s", why.c_str());
     fasts[pi] = fast;
+    for (int si = 0; si < pds[pi].nsub && !stream; ++si) {
+      SubDev& sd = pds[pi].sub[si];
+      if (!sd.needs_c) continue;
+      rc = tile_const_table(c, pds[pi], sd);
+      if (rc) return rc;
+    }
   }
   rc = upload_ctabs(c);
   if (rc) return rc;

@@ -219,7 +219,7 @@ std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInp
     pd.ph1 = turns_fixed(g / pi);
   }
   pd.famp0 = float(pd.amp0);
-  int cost_rounds = 0;
+  int cost_rounds = 0, c_rounds = 0;
   for (int s = 0; s < pd.nsub; ++s) {
     const SubPassPlan& sp = pp.subs[s];
     SubDev& sd = pd.sub[s];
@@ -253,9 +253,10 @@ std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInp
       rd.gtab = tabs.geom_offset(sh, sd.pos, rd);
       const bool wants = in.adjoint ? (rd.cost || rd.lam) : (rd.cost || rd.reduce);
       if (wants && !in.stream) rd.ctab = tabs.offset(in.wmat, in.n, sh, sd.pos, rd);
-      if (in.adjoint || in.stream || rd.ctab < 0) continue;
-      // the forward kernels take the register-pair part CP[j] of the pass's
-      // cost round and reduction round from the descriptor
+      if (in.stream || rd.ctab < 0) continue;
+      // the kernels take the register-pair part CP[j] of the pass's cost
+      // round (cpc, cpt) and of its reduction round (forward) or
+      // lambda-creation round (adjoint) (cpr) from the descriptor
       const int QN = 1 << (5 + sh.WB);
       const int32_t* cp = tabs.h.data() + rd.ctab + QN + QN * sh.R + sh.R;
       if (rd.cost) {
@@ -265,8 +266,10 @@ std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInp
           pd.cpt[j] = uint32_t(((uint64_t)(int64_t)cp[j] * pd.ph1) >> 32);
         }
       }
-      if (rd.reduce)
+      if (in.adjoint ? rd.lam : rd.reduce) {
+        if (c_rounds++) return "plan has two reduction rounds in one pass";
         for (int j = 0; j < (1 << sh.R); ++j) pd.cpr[j] = cp[j];
+      }
     }
   }
   return "";
