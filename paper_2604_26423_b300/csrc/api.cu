@@ -156,19 +156,23 @@ struct ProfScope {
 };
 
 // Forward tile shape (complex64 only; complex128 always uses 5x3):
-//   0 "5x3": 2^5 registers x 8 warps, T = 13, 2 CTAs per SM (default)
+//   0 "5x3": 2^5 registers x 8 warps, T = 13, 2 CTAs per SM
 //   1 "4x4": 2^4 registers x 16 warps, T = 13
 //   2 "5x2": 2^5 registers x 4 warps, T = 12, 4 CTAs per SM
-//   3 "4x3": 2^4 registers x 8 warps, T = 12, 4 CTAs per SM
+//   3 "4x3": 2^4 registers x 8 warps, T = 12, 4 CTAs per SM (default: four
+//      tiles in flight per SM keep HBM busier than two larger ones)
 // selected by QAOA_FWD_SHAPE.
+constexpr int kFwdShapeC64 = 3;
+constexpr int kSmallMaxQubits = 12;  // n <= 12: whole circuit in one CTA (small_circuit_kernel)
 int fwd_shape_id(int prec) {
   if (prec != QAOA_C64) return 0;
   const char* e = getenv("QAOA_FWD_SHAPE");
-  if (!e) return 0;
+  if (!e) return kFwdShapeC64;
+  if (strcmp(e, "5x3") == 0) return 0;
   if (strcmp(e, "4x4") == 0) return 1;
   if (strcmp(e, "5x2") == 0) return 2;
   if (strcmp(e, "4x3") == 0) return 3;
-  return 0;
+  return kFwdShapeC64;
 }
 
 TileShape fwd_shape(int prec) {
@@ -304,13 +308,14 @@ int group_order() {
 
 // group orders of the gradient's forward and adjoint plans (QAOA_GRAD_ORDER
 // overrides both)
-int grad_fwd_order() {
+int grad_base_order() {
   const char* e = getenv("QAOA_GRAD_ORDER");
   if (e && strcmp(e, "last") == 0) return ORDER_LOW_LAST;
   if (e && strcmp(e, "middle") == 0) return ORDER_LOW_MIDDLE;
   return ORDER_LOW_MIDDLE;
 }
-int grad_bwd_order() { return grad_fwd_order(); }
+int grad_fwd_order() { return grad_base_order() | float_lanes_flag(); }
+int grad_bwd_order() { return grad_base_order(); }
 
 int smax_fwd(int T) {
   const char* e = getenv("QAOA_SMAX");
@@ -420,7 +425,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
   c->sums_ready = false;
   int rc = upload_phases(c, p, gamma);
   if (rc) return rc;
-  if (n < T) {
+  if (n < std::max(T, kSmallMaxQubits + 1)) {
     rc = run_small(c, p, gamma, beta);
     if (rc) return rc;
     c->have_result = c->state_ready = true;

@@ -21,9 +21,9 @@ import os
 _cache: dict = {}
 
 # tile shape of the complex64 forward kernel: 2^R registers x 2^WB warps
-FWD_SHAPES = {"5x3": None, "4x4": "4x4", "5x2": "5x2", "4x3": "4x3"}
+FWD_SHAPES = {"5x3": "5x3", "4x4": "4x4", "5x2": "5x2", "4x3": "4x3"}
 # largest super-tile (index bits kept together through L2 by one CTA)
-SUPER_TILES = (13, 14, 15)
+SUPER_TILES = (12, 13, 14, 15)
 # group order of the pass plans: the last layer ending on the low group (its
 # final pass also writes the sampling block sums), or the low group away from
 # the fused passes
