@@ -98,19 +98,31 @@ __device__ __forceinline__ Real pow_bits(Real c, uint8_t mask) {
   return r;
 }
 
+// Asynchronous tile prefetch state of an adjoint pass (complex64, one tile per
+// super-tile): the tile's vectors were copied into shared memory while the
+// previous tile finished; the last round, once every thread has read its
+// amplitudes, starts the copy of the next tile (super-tile gnext).
+struct AdjPrefetch {
+  bool on;      // this pass copies tiles asynchronously
+  bool next;    // a next tile exists for this CTA
+  uint64_t gnext;
+};
+
 template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, uint64_t gbase,
                                           const int* tconst, const typename Cx<Real>::T* phase, int lane, int warp,
                                           Real& ga, Real& gc, Real& gbv, Real& ge, Real& sc,
-                                          typename Cx<Real>::T* v, typename Cx<Real>::T* l) {
+                                          typename Cx<Real>::T* v, typename Cx<Real>::T* l, const AdjPrefetch& pf) {
   using C2 = typename Cx<Real>::T;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
   C2* gpsi = reinterpret_cast<C2*>(A.psi);
   C2* glam = reinterpret_cast<C2*>(A.lam);
   const bool stream = A.diag != nullptr;
-  const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
+  // the round's geometry is rebuilt where it is used instead of being kept
+  // live across the butterflies (register pressure)
+  using Geo = RoundGeo<R, WB, AB>;
   const bool need_c = CC && (rd.cost || rd.lam);
   RoundCost<R, WB> rcost;
   if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
@@ -118,6 +130,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   // lambda-creation round (P.cpr), from the descriptor
   auto for_costs = [&](const int32_t* cp, auto&& f) {
     if (stream) {
+      const Geo geo(sp, rd, gbase, lane, warp, A.ctabs);
       gray_ptr_walk<R>(A.diag, geo.gb, geo.gstr, [&](int j, const int32_t* q) { f(j, __ldcg(q)); });
     } else {
       int lin = rcost.kappa;
@@ -133,7 +146,13 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     }
   };
 
-  // a global round's loads were issued by the caller before the tile barrier
+  // a global round's loads were issued by the caller before the tile barrier,
+  // or copied into shared memory (prefetch)
+  if (rd.src == SRC_GLOBAL_D && pf.on) {
+    const uint32_t sb = Geo::sbase_of(rd, lane, warp, A.ctabs);
+    smem_load<R, WB, AB>(rd.layout, tv, sb, v);
+    if (!(CC && rd.lam)) smem_load<R, WB, AB>(rd.layout, tl, sb, l);
+  }
   if (rd.src == SRC_GLOBAL_D) {
     if (CC && rd.lam) {
       // lambda = C(x) psi (the operator whose expectation is differentiated);
@@ -146,8 +165,23 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       });
     }
   } else {
-    smem_load<R, WB, AB>(rd.layout, tv, geo.sbase, v);
-    smem_load<R, WB, AB>(rd.layout, tl, geo.sbase, l);
+    const uint32_t sb = Geo::sbase_of(rd, lane, warp, A.ctabs);
+    smem_load<R, WB, AB>(rd.layout, tv, sb, v);
+    smem_load<R, WB, AB>(rd.layout, tl, sb, l);
+  }
+
+  if constexpr (sizeof(Real) == 4) {
+    if (pf.on && rd.dst == DST_GLOBAL_D) {
+      // every thread has read its amplitudes: the tiles are free for the next copy
+      __syncthreads();
+      if (pf.next) {
+        const int tid = (warp << 5) | lane;
+        tile_copy_async<R, WB>(tv, reinterpret_cast<const float2*>(A.psi), pf.gnext, sp, tid, A.ctabs);
+        if (!(CC && sp.rd[0].lam))
+          tile_copy_async<R, WB>(tl, reinterpret_cast<const float2*>(A.lam), pf.gnext, sp, tid, A.ctabs);
+        cp_async_commit();
+      }
+    }
   }
 
   inverse_mixer<R>(v, l, rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA), FAST,
@@ -181,12 +215,14 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
           l[j].x *= sc; l[j].y *= sc;
         }
       }
+      const Geo geo(sp, rd, gbase, lane, warp, A.ctabs);
       gray_ptr_walk<R>(gpsi, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
       gray_ptr_walk<R>(glam, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, l[j]); });
     }
   } else {
-    smem_store<R, WB, AB>(rd.layout, tv, geo.sbase, v);
-    smem_store<R, WB, AB>(rd.layout, tl, geo.sbase, l);
+    const uint32_t sb = Geo::sbase_of(rd, lane, warp, A.ctabs);
+    smem_store<R, WB, AB>(rd.layout, tv, sb, v);
+    smem_store<R, WB, AB>(rd.layout, tl, sb, l);
   }
 }
 
@@ -209,12 +245,16 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
   for (int s = 0; s < P.nsub; ++s) {
     const SubDev& sp = P.sub[s];
     const uint64_t ntiles = 1ull << sp.ninner;
+    AdjPrefetch pf;
+    pf.on = sizeof(Real) == 4 && sp.cgtab >= 0;  // one sub-pass of one tile per unit
+    pf.next = pf.on && unit + gridDim.x < P.n_units;
+    pf.gnext = pf.next ? P.outer_runs.scatter(unit + gridDim.x) : 0;
     for (uint64_t ti = 0; ti < ntiles; ++ti) {
       const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
       // issue the first round's global loads first: their latency overlaps the
       // barrier below and the tile constants
       C2 v[1 << R], l[1 << R];
-      if (sp.rd[0].src == SRC_GLOBAL_D) {
+      if (sp.rd[0].src == SRC_GLOBAL_D && !pf.on) {
         const RoundGeo<R, WB, sizeof(C2)> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
         gray_ptr_walk<R>(reinterpret_cast<const C2*>(A.psi), g0.gb, g0.gstr,
                          [&](int j, const C2* q) { v[j] = __ldcg(q); });
@@ -230,6 +270,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         if (tid < kTileConstInts)
           tc[tid == 15 ? 16 : tid] = __ldg(sp.tct + (((unit << sp.ninner) + ti) * kTileConstInts + tid));
       }
+      if (pf.on) cp_async_wait_all();  // this tile's copies (issued by this thread)
       __syncthreads();
       if (CC && sp.needs_c && !stream && !tab) {
         if (tid == 0) tconst[16] = 0;
@@ -243,7 +284,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
           adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tc, phase, lane, warp, gA, gC, gB, gE, sc,
-                                           v, l);
+                                           v, l, pf);
         }
       } else {
         // fp32: the terms of one tile are summed in fp32, then added in FP64
@@ -253,7 +294,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
           adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tc, phase, lane, warp, ga, gc, gbv, ge, sc,
-                                           v, l);
+                                           v, l, pf);
         }
         gA += double(ga);
         gC += double(gc);
@@ -288,6 +329,16 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
   double gA = 0.0, gC = 0.0, gB = 0.0, gE = 0.0;
 
   uint32_t tcount = 0;
+  if constexpr (sizeof(Real) == 4) {
+    // asynchronous tile copies: the first tile's copy before the loop
+    const SubDev& sp0 = P.sub[0];
+    if (sp0.cgtab >= 0 && blockIdx.x < P.n_units) {
+      const uint64_t g0 = P.outer_runs.scatter(blockIdx.x);
+      tile_copy_async<R, WB>(tv, reinterpret_cast<const float2*>(A.psi), g0, sp0, tid, A.ctabs);
+      if (!(CC && sp0.rd[0].lam)) tile_copy_async<R, WB>(tl, reinterpret_cast<const float2*>(A.lam), g0, sp0, tid, A.ctabs);
+      cp_async_commit();
+    }
+  }
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
     adj_unit<Real, R, WB, FAST, CC>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE, &tcount);
 

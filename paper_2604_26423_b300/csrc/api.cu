@@ -185,6 +185,7 @@ TileShape fwd_shape(int prec) {
   return s;
 }
 
+// Adjoint tile shape: two vectors per thread, 2^4 registers each x 8 warps (T = 12).
 TileShape adj_shape(int prec) {
   TileShape s;
   s.R = kRAdj;
@@ -308,6 +309,12 @@ int group_order() {
 
 // group orders of the gradient's forward and adjoint plans (QAOA_GRAD_ORDER
 // overrides both)
+// Asynchronous tile copies in the adjoint passes (QAOA_ADJ_PREFETCH=0 disables).
+bool adj_prefetch() {
+  const char* e = getenv("QAOA_ADJ_PREFETCH");
+  return !(e && strcmp(e, "0") == 0);
+}
+
 int grad_base_order() {
   const char* e = getenv("QAOA_GRAD_ORDER");
   if (e && strcmp(e, "last") == 0) return ORDER_LOW_LAST;
@@ -563,23 +570,33 @@ const Plan* get_bplan(qaoa_ctx* c, int p, int order) {
   return r;
 }
 
-template <typename Real, bool FAST, bool CC>
-int adj_blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
-  auto kern = adj_pass_kernel<Real, kRAdj, kWBAdj, FAST, CC>;
+template <typename Real, bool FAST, bool CC, int R, int WB>
+int adj_blocks_per_sm_rw(qaoa_ctx* c, size_t smem, int* nb) {
+  auto kern = adj_pass_kernel<Real, R, WB, FAST, CC>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, 32 << kWBAdj, smem));
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, 32 << WB, smem));
   if (*nb < 1) return c->set_err(QAOA_ECUDA, "adjoint kernel does not fit on an SM (smem %zu)", smem);
   return QAOA_OK;
 }
 
-template <typename Real, bool FAST, bool CC>
-int launch_adj(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid) {
-  auto kern = adj_pass_kernel<Real, kRAdj, kWBAdj, FAST, CC>;
+template <typename Real, bool FAST, bool CC, int R, int WB>
+int launch_adj_rw(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid) {
+  auto kern = adj_pass_kernel<Real, R, WB, FAST, CC>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, 32 << kWBAdj, smem, c->stream>>>(pd, aa);
+  kern<<<grid, 32 << WB, smem, c->stream>>>(pd, aa);
   if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   return QAOA_OK;
+}
+
+template <typename Real, bool FAST, bool CC>
+int adj_blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
+  return adj_blocks_per_sm_rw<Real, FAST, CC, kRAdj, kWBAdj>(c, smem, nb);
+}
+
+template <typename Real, bool FAST, bool CC>
+int launch_adj(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid) {
+  return launch_adj_rw<Real, FAST, CC, kRAdj, kWBAdj>(c, pd, aa, smem, grid);
 }
 
 // Adjoint instantiation for (precision, mixer form, C(x) code): occupancy query
@@ -706,6 +723,10 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
       rc = tile_const_table(c, pds[pi], sd);
       if (rc) return rc;
     }
+    // complex64, one tile per super-tile: tiles are copied asynchronously,
+    // the next one during the current one's last round
+    if (c->prec == QAOA_C64 && pds[pi].nsub == 1 && pds[pi].sub[0].ninner == 0 && adj_prefetch())
+      pds[pi].sub[0].cgtab = copy_geom_offset(c->tabs, sh, pds[pi].sub[0].pos);
   }
   rc = upload_ctabs(c);
   if (rc) return rc;

@@ -148,6 +148,14 @@ int32_t TableStore::geom_offset(const TileShape& sh, const int8_t* pos, const Ro
   return off;
 }
 
+int32_t copy_geom_offset(TableStore& tabs, const TileShape& sh, const int8_t* pos) {
+  RoundDev rd;
+  memset(&rd, 0, sizeof rd);
+  for (int i = 0; i < 5; ++i) rd.lane[i] = int8_t(i);
+  for (int i = 0; i < sh.WB; ++i) rd.warp[i] = int8_t(5 + i);
+  return tabs.geom_offset(sh, pos, rd);
+}
+
 BitRuns make_runs(const std::vector<int>& bits) {
   BitRuns r;
   memset(&r, 0, sizeof r);
@@ -233,6 +241,7 @@ std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInp
     sd.ninner = (int)inner.size();
     for (int i = 0; i < sd.ninner; ++i) sd.inner[i] = (int8_t)inner[i];
     sd.inner_runs = make_runs(inner);
+    sd.cgtab = -1;
     sd.nrounds = (int)sp.rounds.size();
     if (sd.nrounds > kMaxRoundsDev) return "plan has too many rounds";
     sd.needs_c = sp.needs_c;

@@ -35,6 +35,11 @@ struct TableStore {
 std::string check_graph(int n, int m, const int32_t* u, const int32_t* v, const int32_t* w, long long max_abs,
                         std::vector<int32_t>& wmat, long long& W, long long& c_lo, long long& c_hi);
 
+// Offset of the per-thread geometry table of the asynchronous tile copy
+// (complex64): lanes on tile bits 0..4, warps on tile bits 5..4+WB (see
+// tile_copy_async in pass_kernel.cuh).
+int32_t copy_geom_offset(TableStore& tabs, const TileShape& sh, const int8_t* pos);
+
 // Contiguous runs of a sorted bit list.
 BitRuns make_runs(const std::vector<int>& bits);
 

@@ -49,6 +49,12 @@ struct SubDev {
   // tile in the kernel's order (unit * 2^ninner + tile): delta_j for tile bit
   // j at [j], the fixed-bit base at [15]; nullptr: computed in the kernel
   const int32_t* tct;
+  // asynchronous tile copy (complex64 kernels, one tile per super-tile):
+  // offset of the per-thread geometry table of the copy mapping (lanes on
+  // tile bits 0..4, warps on the next WB bits, one amplitude per 8-byte
+  // copy), -1 if the sub-pass is not copied asynchronously
+  int32_t cgtab;
+  int32_t pad2;
   RoundDev rd[kMaxRoundsDev];
 };
 
@@ -119,6 +125,15 @@ __device__ __forceinline__ void st_hint(float2* a, float2 v, uint64_t pol) {
 __device__ __forceinline__ void st_hint(double2* a, double2 v, uint64_t pol) {
   asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(a), "d"(v.x), "d"(v.y), "l"(pol) : "memory");
 }
+
+// Asynchronous global -> shared copies of 8 bytes (both addresses 8-byte
+// aligned), committed as one group per tile; the consumer waits for all of them.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // fp32 kernels take the host-rounded fp32 copies of the pass coefficients (no
 // fp64 conversions in the kernels); fp64 kernels the doubles.

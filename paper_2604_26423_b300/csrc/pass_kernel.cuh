@@ -156,6 +156,26 @@ __device__ __forceinline__ void gray_ptr_walk(T* base, uint64_t g0, const uint64
   }
 }
 
+// Issues the asynchronous copy of one vector's tile (complex64, global indices
+// gbase | scatter(t) for tile index t) into its padded shared-memory tile:
+// thread (lane, warp) copies the amplitudes at tile indices
+// lane | warp << 5 | k << (5 + WB) for the 2^R values of k, 8 bytes each
+// (lanes on tile bits 0..4, i.e. global bits 0..4: 256-byte runs per warp).
+// Its slot and global offset come from the sub-pass's copy-geometry table.
+template <int R, int WB>
+__device__ __forceinline__ void tile_copy_async(float2* tile, const float2* g, uint64_t gbase, const SubDev& sp,
+                                                int tid, const int32_t* tabs) {
+  constexpr int NT = 32 << WB;
+  const uint32_t sb = (uint32_t)__ldg(tabs + sp.cgtab + tid);
+  const uint64_t gb = gbase | __ldg(reinterpret_cast<const unsigned long long*>(tabs + sp.cgtab + NT) + tid);
+  uint64_t gstr[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) gstr[i] = 1ull << sp.pos[5 + WB + i];
+  gray_ptr_walk<R>(g, gb, gstr, [&](int k, const float2* q) {
+    cp_async8(tile + sb + padi<8>(uint32_t(k) << (5 + WB)), q);
+  });
+}
+
 // Shared-memory loads / stores of the register amplitudes: the only code that
 // depends on the layout, compiled with constant offsets per menu entry.
 template <int R, int WB, int L, int AB, typename C2>

@@ -95,14 +95,16 @@ def test_tuner_candidates():
 
 
 def test_group_orders_give_valid_plans():
-    # both group orders, with and without floating lane bits, plan every size
-    # validly (checked by the planner's validator)
+    # both group orders, with and without floating lane bits, both main tile
+    # shapes, plan every size validly (checked by the planner's validator)
+    import itertools
     import os
     from paper_2604_26423_b300 import qaoa
-    for order in ("last", "middle"):
-        for fl in ("0", "1"):
+    for order, fl, shape in itertools.product(("last", "middle"), ("0", "1"), ("4x3", "5x3")):
+        if True:
             os.environ["QAOA_GROUP_ORDER"] = order
             os.environ["QAOA_FLOAT_LANES"] = fl
+            os.environ["QAOA_FWD_SHAPE"] = shape
             try:
                 for n in (13, 14, 20, 22, 26, 30, 33, 34):
                     for p in (1, 2, 3, 4):
@@ -113,6 +115,7 @@ def test_group_orders_give_valid_plans():
             finally:
                 os.environ.pop("QAOA_GROUP_ORDER", None)
                 os.environ.pop("QAOA_FLOAT_LANES", None)
+                os.environ.pop("QAOA_FWD_SHAPE", None)
 
 
 def test_float_lanes_plan_shape():
@@ -120,19 +123,19 @@ def test_float_lanes_plan_shape():
     # applies them once in a plain pass on a high group; the fused low-group pass
     # and the final pass lose a shared-memory round trip each; the pass count
     # is unchanged
+    # (5x3 tile shape: T = 13, 2^5 registers per thread)
     import os
     import re
     from paper_2604_26423_b300 import qaoa
-    os.environ["QAOA_FLOAT_LANES"] = "1"
+    os.environ["QAOA_FWD_SHAPE"] = "5x3"
     try:
+        os.environ["QAOA_FLOAT_LANES"] = "1"
         d = qaoa.describe_plan(33, 3, "c64")
-    finally:
-        os.environ.pop("QAOA_FLOAT_LANES", None)
-    os.environ["QAOA_FLOAT_LANES"] = "0"
-    try:
+        os.environ["QAOA_FLOAT_LANES"] = "0"
         d0 = qaoa.describe_plan(33, 3, "c64")
     finally:
         os.environ.pop("QAOA_FLOAT_LANES", None)
+        os.environ.pop("QAOA_FWD_SHAPE", None)
     assert "float_lanes=5" in d and "float_lanes" not in d0
     assert "group 0: 5 6 7 8 9 10 11 12\n" in d
     assert "passes=10" in d and "passes=10" in d0
