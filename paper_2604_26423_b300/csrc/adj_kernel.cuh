@@ -90,6 +90,48 @@ __device__ __forceinline__ void inverse_mixer(V* v, V* l, uint8_t mask, Real tau
   if (fast) sc *= cpow;
 }
 
+// Swapped storage (complex64, see pass_kernel.cuh): gradient terms of the bits
+// in `mask`, then their inverse butterflies on both vectors. For a register
+// pair (j, k = j | bit) with n its plain and w its swapped member,
+//   Im conj(l_j) v_k + Im conj(l_k) v_j = (P.x - M.x) - (P.y - M.y)
+// for the packed products P = l_n * v_w and M = l_w * v_n. The products are
+// summed by the parity of j (pa: l_j v_k for even j, l_k v_j for odd j; pb the
+// others), which gives (P, M) = (pa, pb) for s = 0 and (pb, pa) for s = 1.
+template <int R>
+__device__ __forceinline__ void inverse_mixer_sw(float2* v, float2* l, uint8_t mask, float tau, float alpha,
+                                                 bool fast, float cpow, float& sc, float& acc, int s) {
+  if (!mask) return;
+  float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
+  auto terms = [&](int i) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) {
+      if (j >> i & 1) continue;
+      const int k = j | (1 << i);
+      if (parity_c(j) == 0) {
+        pa = __ffma2_rn(l[j], v[k], pa);
+        pb = __ffma2_rn(l[k], v[j], pb);
+      } else {
+        pb = __ffma2_rn(l[j], v[k], pb);
+        pa = __ffma2_rn(l[k], v[j], pa);
+      }
+    }
+  };
+  if (mask == (1u << R) - 1) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) terms(i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+      if (mask >> i & 1) terms(i);
+  }
+  const float t0 = (pa.x - pb.x) - (pa.y - pb.y);
+  const float t = s ? -t0 : t0;
+  apply_mixer_sw<R>(v, mask, -tau, alpha, fast, s);
+  apply_mixer_sw<R>(l, mask, -tau, alpha, fast, s);
+  acc = fmaf(sc * sc, t, acc);
+  if (fast) sc *= cpow;
+}
+
 template <typename Real>
 __device__ __forceinline__ Real pow_bits(Real c, uint8_t mask) {
   Real r = 1;
@@ -111,7 +153,8 @@ struct AdjPrefetch {
 template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, uint64_t gbase,
-                                          const int* tconst, const typename Cx<Real>::T* phase, int lane, int warp,
+                                          int gpar, const int* tconst, const typename Cx<Real>::T* phase, int lane,
+                                          int warp,
                                           Real& ga, Real& gc, Real& gbv, Real& ge, Real& sc,
                                           typename Cx<Real>::T* v, typename Cx<Real>::T* l, const AdjPrefetch& pf) {
   using C2 = typename Cx<Real>::T;
@@ -123,6 +166,11 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   // the round's geometry is rebuilt where it is used instead of being kept
   // live across the butterflies (register pressure)
   using Geo = RoundGeo<R, WB, AB>;
+  // complex64: swapped storage; s = parity of the thread's amplitude 0
+  constexpr bool kSw = sizeof(Real) == 4;
+  const uint32_t entry = Geo::entry_of(rd, lane, warp, A.ctabs);
+  const uint32_t sb = entry & 0x7fffffffu;
+  const int s = kSw ? int(entry >> 31) ^ gpar : 0;
   const bool need_c = CC && (rd.cost || rd.lam);
   RoundCost<R, WB> rcost;
   if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
@@ -149,9 +197,13 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   // a global round's loads were issued by the caller before the tile barrier,
   // or copied into shared memory (prefetch)
   if (rd.src == SRC_GLOBAL_D && pf.on) {
-    const uint32_t sb = Geo::sbase_of(rd, lane, warp, A.ctabs);
     smem_load<R, WB, AB>(rd.layout, tv, sb, v);
     if (!(CC && rd.lam)) smem_load<R, WB, AB>(rd.layout, tl, sb, l);
+  }
+  if constexpr (kSw) {
+    // the first sub-pass reads the forward run's plain amplitudes (psi only:
+    // lambda is created from it)
+    if (rd.src == SRC_GLOBAL_D && sp.ld_plain) swap_odd<R>(reinterpret_cast<float2*>(v), s);
   }
   if (rd.src == SRC_GLOBAL_D) {
     if (CC && rd.lam) {
@@ -165,7 +217,6 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       });
     }
   } else {
-    const uint32_t sb = Geo::sbase_of(rd, lane, warp, A.ctabs);
     smem_load<R, WB, AB>(rd.layout, tv, sb, v);
     smem_load<R, WB, AB>(rd.layout, tl, sb, l);
   }
@@ -184,15 +235,28 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     }
   }
 
-  inverse_mixer<R>(v, l, rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA), FAST,
-                   pow_bits(pick<Real>(P.cA, P.fcA), rd.mixA), sc, ga);
+  auto inv_mixer = [&](uint8_t mask, Real tau, Real alpha, Real cpow, Real& acc) {
+    if constexpr (kSw)
+      inverse_mixer_sw<R>(reinterpret_cast<float2*>(v), reinterpret_cast<float2*>(l), mask, tau, alpha, FAST, cpow,
+                          sc, acc, s);
+    else
+      inverse_mixer<R>(v, l, mask, tau, alpha, FAST, cpow, sc, acc);
+  };
+  inv_mixer(rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA),
+            pow_bits(pick<Real>(P.cA, P.fcA), rd.mixA), ga);
   if (CC && rd.cost) {
-    Real tc = 0;
+    // Im conj(l) v of a swapped pair of amplitudes has the opposite sign: the
+    // terms are summed by the parity of j and combined with the thread's s;
+    // a swapped amplitude takes the conjugate phase in the plain product
+    // formula (angle scale k1 = -k0)
+    Real tc0 = 0, tc1 = 0;
+    const float k0 = s ? -kTurn32 : kTurn32, k1 = -k0;
     for_costs(P.cpc, [&](int j, int c) {
       const Real h = Real(P.wsum - 2 * c);
-      tc = fma(fma(l[j].x, v[j].y, -l[j].y * v[j].x), h, tc);
+      const Real q = fma(l[j].x, v[j].y, -l[j].y * v[j].x);
+      if (parity_c(j)) tc1 = fma(q, h, tc1); else tc0 = fma(q, h, tc0);
       C2 ph;
-      if constexpr (sizeof(Real) == 4) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo));
+      if constexpr (kSw) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo), parity_c(j) ? k1 : k0);
       else ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
       // multiply both vectors by the conjugate phase (inverse cost unitary)
       const Real vr = v[j].x, vi = v[j].y, lr = l[j].x, li = l[j].y;
@@ -201,10 +265,11 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       l[j].x = lr * ph.x + li * ph.y;
       l[j].y = li * ph.x - lr * ph.y;
     });
+    const Real tc = !kSw ? tc0 + tc1 : s ? tc1 - tc0 : tc0 - tc1;
     gc = fma(sc * sc, tc, gc);
   }
-  inverse_mixer<R>(v, l, rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB), FAST,
-                   pow_bits(pick<Real>(P.cB, P.fcB), rd.mixB), sc, gbv);
+  inv_mixer(rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB),
+            pow_bits(pick<Real>(P.cB, P.fcB), rd.mixB), gbv);
 
   if (rd.dst == DST_GLOBAL_D) {
     if (sp.store) {
@@ -220,7 +285,6 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       gray_ptr_walk<R>(glam, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, l[j]); });
     }
   } else {
-    const uint32_t sb = Geo::sbase_of(rd, lane, warp, A.ctabs);
     smem_store<R, WB, AB>(rd.layout, tv, sb, v);
     smem_store<R, WB, AB>(rd.layout, tl, sb, l);
   }
@@ -279,12 +343,13 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         __syncthreads();
       }
       Real sc = 1;  // pending fast-form factor of this tile's vectors
+      const int gpar = __popcll(gbase) & 1;
       if constexpr (sizeof(Real) == 8) {
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tc, phase, lane, warp, gA, gC, gB, gE, sc,
-                                           v, l, pf);
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, gpar, tc, phase, lane, warp, gA, gC, gB, gE,
+                                           sc, v, l, pf);
         }
       } else {
         // fp32: the terms of one tile are summed in fp32, then added in FP64
@@ -293,8 +358,8 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, tc, phase, lane, warp, ga, gc, gbv, ge, sc,
-                                           v, l, pf);
+          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, gpar, tc, phase, lane, warp, ga, gc, gbv, ge,
+                                           sc, v, l, pf);
         }
         gA += double(ga);
         gC += double(gc);

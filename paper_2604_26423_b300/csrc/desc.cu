@@ -139,7 +139,8 @@ int32_t TableStore::geom_offset(const TileShape& sh, const int8_t* pos, const Ro
     for (int i = 0; i < sh.WB; ++i)
       if (warp >> i & 1) { tb |= 1u << rd.warp[i]; g |= 1ull << pos[rd.warp[i]]; }
     const uint32_t sb = sh.amp_bytes == 8 ? padi<8>(tb) : padi<16>(tb);
-    h[off + tid] = (int32_t)sb;
+    // bit 31: parity of the thread's global index offset (swapped storage)
+    h[off + tid] = (int32_t)(sb | (uint32_t(__builtin_popcountll(g) & 1) << 31));
     h[off + NT + 2 * tid] = (int32_t)(uint32_t)(g & 0xffffffffull);
     h[off + NT + 2 * tid + 1] = (int32_t)(uint32_t)(g >> 32);
   }
@@ -242,6 +243,10 @@ std::string fill_pass_dev(const PassPlan& pp, const TileShape& sh, const PassInp
     for (int i = 0; i < sd.ninner; ++i) sd.inner[i] = (int8_t)inner[i];
     sd.inner_runs = make_runs(inner);
     sd.cgtab = -1;
+    // complex64 storage: a forward run ends in plain (re, im) amplitudes; the
+    // adjoint starts from them (swapped storage in between, pass_kernel.cuh)
+    sd.st_plain = !in.adjoint && pp.reduce && s + 1 == pd.nsub;
+    sd.ld_plain = in.adjoint && pp.linit && s == 0;
     sd.nrounds = (int)sp.rounds.size();
     if (sd.nrounds > kMaxRoundsDev) return "plan has too many rounds";
     sd.needs_c = sp.needs_c;

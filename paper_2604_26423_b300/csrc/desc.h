@@ -23,7 +23,8 @@ struct TableStore {
   // from the n x n weight matrix `wmat` on first use.
   int32_t offset(const int32_t* wmat, int n, const TileShape& sh, const int8_t* pos, const RoundDev& rd);
   // Offset (even) of the per-thread geometry table of a round over tile bits
-  // `pos`: NT padded shared-memory slots, then NT 64-bit global offsets.
+  // `pos`: NT padded shared-memory slots (bit 31: parity of the thread's
+  // global index offset), then NT 64-bit global offsets.
   int32_t geom_offset(const TileShape& sh, const int8_t* pos, const RoundDev& rd);
   void clear() { h.clear(); index.clear(); dirty = false; }
 };

@@ -19,7 +19,8 @@ struct RoundDev {
   uint8_t layout;  // menu layout id (plan.h, menu_layout)
   int32_t ctab;  // offset (in ints) of this round's cost tables, -1 if none
   int32_t gtab;  // offset (in ints, even) of this round's per-thread geometry:
-                 // padded shared-memory slot (NT ints), then the global index
+                 // padded shared-memory slot (NT ints; bit 31 holds the parity
+                 // of the thread's global index offset), then the global index
                  // offset of the thread's lane and warp bits (NT 64-bit words)
 };
 
@@ -54,7 +55,10 @@ struct SubDev {
   // tile bits 0..4, warps on the next WB bits, one amplitude per 8-byte
   // copy), -1 if the sub-pass is not copied asynchronously
   int32_t cgtab;
-  int32_t pad2;
+  // complex64 storage between passes (see swapped storage in pass_kernel.cuh):
+  // the sub-pass reads plain (re, im) amplitudes (ld_plain: the adjoint's first
+  // sub-pass) or writes them (st_plain: a forward run's last sub-pass)
+  uint8_t ld_plain, st_plain, pad2[2];
   RoundDev rd[kMaxRoundsDev];
 };
 
@@ -141,9 +145,12 @@ template <typename Real> __device__ __forceinline__ Real pick(double d, float f)
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 
-// exp(2 pi i t / 2^32) for a 32-bit turn count t (the signed angle in [-pi, pi)).
-__device__ __forceinline__ float2 phase_turns32(uint32_t t) {
-  const float ang = float(int32_t(t)) * 1.46291807926715968e-9f;  // 2 pi / 2^32
+constexpr float kTurn32 = 1.46291807926715968e-9f;  // 2 pi / 2^32
+
+// exp(2 pi i t / 2^32) for a 32-bit turn count t (the signed angle in [-pi,
+// pi)); k = -kTurn32 gives the conjugate (the sine's sign flipped exactly).
+__device__ __forceinline__ float2 phase_turns32(uint32_t t, float k = kTurn32) {
+  const float ang = float(int32_t(t)) * k;
   float sn, cs;
   __sincosf(ang, &sn, &cs);
   return make_float2(cs, sn);
@@ -153,10 +160,10 @@ __device__ __forceinline__ float2 phase_turns32(uint32_t t) {
 // the top 32 bits of t as a signed angle in [-pi, pi), then the hardware sine
 // and cosine (absolute error about 4e-7, below the complex64 state's rounding
 // over a layer). Only the top word of the product is formed.
-__device__ __forceinline__ float2 phase_turns(uint64_t ph0, uint64_t ph1, uint32_t u) {
+__device__ __forceinline__ float2 phase_turns(uint64_t ph0, uint64_t ph1, uint32_t u, float k = kTurn32) {
   const uint64_t lo = (uint64_t)u * (uint32_t)ph1 + (uint32_t)ph0;
   const uint32_t hi = (uint32_t)(ph0 >> 32) + u * (uint32_t)(ph1 >> 32) + (uint32_t)(lo >> 32);
-  return phase_turns32(hi);
+  return phase_turns32(hi, k);
 }
 
 template <typename Real> struct Cx;

@@ -106,6 +106,71 @@ __device__ __forceinline__ void apply_mixer(V* v, uint8_t mask, Real tau, Real a
   }
 }
 
+// ---------------------------------------------------------------------------
+// Swapped storage (complex64). Between the passes of a run, the amplitude of
+// index x is held as (re, im) when x has an even number of set bits and as
+// (im, re) when it has an odd number. A butterfly on any bit pairs one plain
+// amplitude a with one swapped amplitude b~ = (b.y, b.x), and the rotation
+// a' = a + i t b, b' = b + i t a becomes two packed FMAs (fma.rn.f32x2, one
+// issue slot for two FP32 FMAs) with no register moves:
+//   a'  = a  + (-t,  t) * b~,      b~' = b~ + ( t, -t) * a
+// (the same FP32 operations as the plain form, so the results are identical).
+// In a round, register amplitude j of a thread is swapped when parity(j) xor s,
+// s being the parity of the thread's amplitude 0 (tile base and the thread's
+// lane / warp offset). The first forward pass writes this form; the last
+// forward sub-pass writes plain amplitudes (st_plain); the adjoint's first
+// sub-pass reads plain ones (ld_plain). complex128 kernels keep plain storage.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int parity_c(int j) { return __builtin_popcount(unsigned(j)) & 1; }
+
+// Butterflies on the register bits in `mask` of swapped-storage amplitudes.
+// kp = (-tau, tau) for a thread with s = 0, (tau, -tau) for s = 1 (the
+// coefficient of the update of a parity-0 amplitude), kn = -kp; fast form
+// a' = a + i tau b, else a' = alpha a + i tau b.
+template <int R>
+__device__ __forceinline__ void bfly_sw(float2& a, float2& b, float2 ca, float2 cb, float2 al, bool fast) {
+  const float2 a0 = a, b0 = b;
+  if (fast) {
+    a = __ffma2_rn(ca, b0, a0);
+    b = __ffma2_rn(cb, a0, b0);
+  } else {
+    a = __ffma2_rn(al, a0, __fmul2_rn(ca, b0));
+    b = __ffma2_rn(al, b0, __fmul2_rn(cb, a0));
+  }
+}
+template <int R>
+__device__ __forceinline__ void apply_mixer_sw(float2* v, uint8_t mask, float tau, float alpha, bool fast, int s) {
+  if (!mask) return;
+  const float2 kp = s ? make_float2(tau, -tau) : make_float2(-tau, tau);
+  const float2 kn = make_float2(-kp.x, -kp.y);
+  const float2 al = make_float2(alpha, alpha);
+  auto bit = [&](int i) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j)
+      if (!(j >> i & 1)) {
+        if (parity_c(j) == 0) bfly_sw<R>(v[j], v[j | (1 << i)], kp, kn, al, fast);
+        else bfly_sw<R>(v[j], v[j | (1 << i)], kn, kp, al, fast);
+      }
+  };
+  if (mask == (1u << R) - 1) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) bit(i);
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < R; ++i)
+    if (mask >> i & 1) bit(i);
+}
+
+// Exchanges the components of the register amplitudes stored swapped (plain
+// <-> swapped storage at the edges of a run).
+template <int R>
+__device__ __forceinline__ void swap_odd(float2* v, int s) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j)
+    if (parity_c(j) ^ s) v[j] = make_float2(v[j].y, v[j].x);
+}
+
 // Per-round thread geometry: the padded shared-memory slot of the thread's
 // amplitude 0 and its global index (tile base | the thread's lane and warp
 // bits), both read from the round's host-built table (one entry per thread),
@@ -118,12 +183,16 @@ struct RoundGeo {
   __device__ __forceinline__ RoundGeo(const SubDev& sp, const RoundDev& rd, uint64_t gbase, int lane, int warp,
                                       const int32_t* tabs) {
     const int tid = (warp << 5) | lane;
-    sbase = (uint32_t)__ldg(tabs + rd.gtab + tid);
+    sbase = (uint32_t)__ldg(tabs + rd.gtab + tid) & 0x7fffffffu;
     gb = gbase | __ldg(reinterpret_cast<const unsigned long long*>(tabs + rd.gtab + (32 << WB)) + tid);
 #pragma unroll
     for (int i = 0; i < R; ++i) gstr[i] = 1ull << rd.greg[i];
   }
   __device__ __forceinline__ static uint32_t sbase_of(const RoundDev& rd, int lane, int warp, const int32_t* tabs) {
+    return (uint32_t)__ldg(tabs + rd.gtab + ((warp << 5) | lane)) & 0x7fffffffu;
+  }
+  // slot and the parity of the thread's global index offset (bit 31 of the entry)
+  __device__ __forceinline__ static uint32_t entry_of(const RoundDev& rd, int lane, int warp, const int32_t* tabs) {
     return (uint32_t)__ldg(tabs + rd.gtab + ((warp << 5) | lane));
   }
 };
@@ -166,7 +235,7 @@ template <int R, int WB>
 __device__ __forceinline__ void tile_copy_async(float2* tile, const float2* g, uint64_t gbase, const SubDev& sp,
                                                 int tid, const int32_t* tabs) {
   constexpr int NT = 32 << WB;
-  const uint32_t sb = (uint32_t)__ldg(tabs + sp.cgtab + tid);
+  const uint32_t sb = (uint32_t)__ldg(tabs + sp.cgtab + tid) & 0x7fffffffu;
   const uint64_t gb = gbase | __ldg(reinterpret_cast<const unsigned long long*>(tabs + sp.cgtab + NT) + tid);
   uint64_t gstr[R];
 #pragma unroll
@@ -233,39 +302,50 @@ __device__ __forceinline__ void reduce_thread_sums(const double* wacc, double& s
 // (smaller code, measured faster).
 template <typename Real, int R, int WB, bool FAST, bool CC = true>
 __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, const SubDev& sp, const RoundDev& rd,
-                                          typename Cx<Real>::T* tile, uint64_t gbase, const int* tconst,
+                                          typename Cx<Real>::T* tile, uint64_t gbase, int gpar, const int* tconst,
                                           const typename Cx<Real>::T* phase, int lane, int warp, double* wacc,
                                           typename Cx<Real>::T* v) {
   using C2 = typename Cx<Real>::T;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
+  // complex64: swapped storage (packed butterflies) and the cost phase from
+  // 32-bit turn increments; complex128: plain storage, phase table
+  constexpr bool kSw = sizeof(Real) == 4;
   C2* gstate = reinterpret_cast<C2*>(A.state);
   const bool stream = A.diag != nullptr;
-  // the round's geometry is rebuilt where needed instead of being kept live
-  // across the butterflies (register pressure)
-  // complex64 with C(x) from the tables: the phase from 32-bit turn increments
-  constexpr bool kTurns = sizeof(Real) == 4;
   const bool init = CC && rd.src == SRC_INIT_D;
+  // the round's geometry is rebuilt where needed instead of being kept live
+  // across the butterflies (register pressure); s: parity of the thread's
+  // amplitude 0 (register amplitude j is stored swapped when parity(j) ^ s)
+  const uint32_t entry = RoundGeo<R, WB, AB>::entry_of(rd, lane, warp, A.ctabs);
+  const int s = kSw ? int(entry >> 31) ^ gpar : 0;
   if (init) {
     // |+>: every amplitude amp0; with the turn path the cost round writes
     // amp0 times the phase directly
-    if (!kTurns || stream || !rd.cost) {
+    if (!kSw || stream || !rd.cost) {
 #pragma unroll
-      for (int j = 0; j < NA; ++j) { v[j].x = Real(P.amp0); v[j].y = Real(0); }
+      for (int j = 0; j < NA; ++j) {
+        const bool sw = kSw && (parity_c(j) ^ s);
+        v[j].x = sw ? Real(0) : Real(P.amp0);
+        v[j].y = sw ? Real(P.amp0) : Real(0);
+      }
     }
   } else if (rd.src == SRC_SMEM_D) {
-    smem_load<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp, A.ctabs), v);
+    smem_load<R, WB, AB>(rd.layout, tile, entry & 0x7fffffffu, v);
   }
 
-  apply_mixer<R>(v, rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA), FAST);
+  auto mixer = [&](uint8_t mask, Real tau, Real alpha) {
+    if constexpr (kSw) apply_mixer_sw<R>(v, mask, tau, alpha, FAST, s);
+    else apply_mixer<R>(v, mask, tau, alpha, FAST);
+  };
+  mixer(rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA));
 
   if (CC && (rd.cost | rd.reduce)) {
-    // C(x) of register amplitude j: streamed from the diagonal, or
-    // kappa + CP[j] + sum_{i: j_i = 1} e_i from the round's tables
-    // C(x) of each register amplitude (streamed, or from the round's tables;
-    // cp: the round's register-pair table CP[j], of the pass's cost or
-    // reduction round). The tables are set up separately for the cost phase
-    // and for the reduction so that neither keeps them live across the other.
+    // C(x) of each register amplitude (streamed, or kappa + CP[j] +
+    // sum_{i: j_i = 1} e_i from the round's tables; cp: the round's
+    // register-pair table CP[j], of the pass's cost or reduction round). The
+    // tables are set up separately for the cost phase and for the reduction
+    // so that neither keeps them live across the other.
     auto for_costs = [&](const int32_t* cp, auto&& f) {
       if (stream) {
         const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
@@ -286,7 +366,11 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       }
     };
     if (rd.cost) {
-      if (kTurns && !stream) {
+      // a swapped amplitude takes the conjugate phase in the plain product
+      // formula: the angle scale is -2pi/2^32 for it (k1) and +2pi/2^32 for
+      // a plain one (k0)
+      const float k0 = s ? -kTurn32 : kTurn32, k1 = -k0;
+      if (kSw && !stream) {
         // turn count of amplitude j: t0 + sum_{i: j_i} E_i + cpt[j] (Gray order)
         uint32_t E[R];
         uint32_t t;
@@ -295,6 +379,10 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
           rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
           t = rc.turns(P.ph0, P.ph1, P.c_lo, E);
         }
+        // |+> round: a swapped amplitude is amp0 (sin, cos) = amp0 exp(i (pi/2 - angle)):
+        // turn count 2^30 - t (quarter turn), i.e. t * m + q with (m, q) = (-1, 2^30)
+        const uint32_t m0 = s ? 0xffffffffu : 1u, q0 = s ? (1u << 30) : 0u;
+        const uint32_t m1 = s ? 1u : 0xffffffffu, q1 = s ? 0u : (1u << 30);
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
           const int j = k ^ (k >> 1);
@@ -302,11 +390,13 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
             const int b = ctz_c(k);
             t += (j >> b & 1) ? E[b] : 0u - E[b];
           }
-          const float2 ph = phase_turns32(t + P.cpt[j]);
+          const uint32_t tj = t + P.cpt[j];
           if (init) {
+            const float2 ph = parity_c(j) ? phase_turns32(tj * m1 + q1) : phase_turns32(tj * m0 + q0);
             v[j].x = P.famp0 * ph.x;
             v[j].y = P.famp0 * ph.y;
           } else {
+            const float2 ph = phase_turns32(tj, parity_c(j) ? k1 : k0);
             const Real xr = v[j].x, xi = v[j].y;
             v[j].x = xr * ph.x - xi * ph.y;
             v[j].y = xr * ph.y + xi * ph.x;
@@ -315,7 +405,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       } else {
         for_costs(P.cpc, [&](int j, int c) {
           C2 ph;
-          if constexpr (sizeof(Real) == 4) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo));
+          if constexpr (kSw) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo), parity_c(j) ? k1 : k0);
           else ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
           const Real xr = v[j].x, xi = v[j].y;
           v[j].x = xr * ph.x - xi * ph.y;
@@ -323,13 +413,14 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
         });
       }
     }
-    apply_mixer<R>(v, rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB), FAST);
+    mixer(rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB));
     if (rd.dst == DST_GLOBAL_D && sp.rescale) {
       const Real sc = pick<Real>(sp.scale, sp.fscale);
 #pragma unroll
       for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
     }
     if (rd.reduce) {
+      // |psi|^2 and C(x) do not depend on the storage order of (re, im)
       Real sn = 0, scc = 0;
       if (A.bsum) {
         // also |psi|^2 per sampling block: tile bit 12 (if any) splits the tile
@@ -372,7 +463,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       wacc[2 * tid + 1] += double(scc);
     }
   } else {
-    apply_mixer<R>(v, rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB), FAST);
+    mixer(rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB));
     if (rd.dst == DST_GLOBAL_D && sp.rescale) {
       const Real sc = pick<Real>(sp.scale, sp.fscale);
 #pragma unroll
@@ -381,6 +472,9 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   }
 
   if (rd.dst == DST_GLOBAL_D) {
+    if constexpr (kSw) {
+      if (sp.st_plain) swap_odd<R>(reinterpret_cast<float2*>(v), s);  // a run's output: plain storage
+    }
     const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
     if (A.l2hint) {
       // outputs of a sub-pass that a later sub-pass reads back stay in L2
@@ -390,7 +484,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       gray_ptr_walk<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
     }
   } else {
-    smem_store<R, WB, AB>(rd.layout, tile, RoundGeo<R, WB, AB>::sbase_of(rd, lane, warp, A.ctabs), v);
+    smem_store<R, WB, AB>(rd.layout, tile, entry & 0x7fffffffu, v);
   }
 }
 
@@ -446,10 +540,11 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         tile_consts<T>(sp.pos, gbase, A.wmat, n, tconst, lane, warp, NT / 32);
         __syncthreads();
       }
+      const int gpar = __popcll(gbase) & 1;
       for (int r = 0; r < sp.nrounds; ++r) {
         const RoundDev& rd = sp.rd[r];
         if (rd.src == SRC_SMEM_D) __syncthreads();
-        fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, tc, phase, lane, warp, wacc, v);
+        fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, gpar, tc, phase, lane, warp, wacc, v);
       }
       if (CC && A.bsum && sp.rd[sp.nrounds - 1].reduce) {
         // this tile is 2^T consecutive amplitudes: its 2^(T-12) block sums, in warp order
