@@ -27,6 +27,7 @@
 #include "aux_kernels.cuh"
 #include "small_kernel.cuh"
 #include "adj_kernel.cuh"
+#include "spec.h"
 
 using namespace qaoa;
 
@@ -309,6 +310,12 @@ int group_order() {
 
 // group orders of the gradient's forward and adjoint plans (QAOA_GRAD_ORDER
 // overrides both)
+// Specialised pass kernels (spec.h; QAOA_SPEC=0 selects the generic ones).
+bool spec_enabled() {
+  const char* e = getenv("QAOA_SPEC");
+  return !(e && strcmp(e, "0") == 0);
+}
+
 // Asynchronous tile copies in the adjoint passes (QAOA_ADJ_PREFETCH=0 disables).
 bool adj_prefetch() {
   const char* e = getenv("QAOA_ADJ_PREFETCH");
@@ -516,8 +523,18 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
     const int wide = fwd_shape_id(c->prec);
     const bool cc = ccs[pi];
     const bool red = pp.reduce && reduce;
-    rc = pass_any(c, fast, cc, wide, false, pd, pa, smem, 0, &bps);
-    if (rc) return rc;
+    // a specialised kernel when one was compiled for this pass's rounds
+    FwdPassKernel spec = nullptr;
+    if (c->prec == QAOA_C64 && wide == 3 && fast && pd.nsub == 1 && pd.sub[0].ninner == 0 && spec_enabled())
+      spec = find_fwd_spec(pd.sub[0]);
+    if (spec) {
+      CUDA_TRY(c, cudaFuncSetAttribute((const void*)spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)spec, 32 << kWB, smem));
+      if (bps < 1) return c->set_err(QAOA_ECUDA, "pass kernel does not fit on an SM (smem %zu)", smem);
+    } else {
+      rc = pass_any(c, fast, cc, wide, false, pd, pa, smem, 0, &bps);
+      if (rc) return rc;
+    }
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
     pa.partial = red ? (double*)c->d_partial.p : nullptr;
@@ -544,7 +561,14 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       if (stream)
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 0, bytes);
-      rc = pass_any(c, fast, cc, wide, true, pd, pa, smem, grid, nullptr);
+      if (spec) {
+        spec<<<grid, 32 << kWB, smem, c->stream>>>(pd, pa);
+        if (c->prof_on) ++c->nlaunch;
+        const cudaError_t le = cudaGetLastError();
+        rc = le == cudaSuccess ? QAOA_OK : c->set_err(QAOA_ECUDA, "specialised pass kernel: %s", cudaGetErrorString(le));
+      } else {
+        rc = pass_any(c, fast, cc, wide, true, pd, pa, smem, grid, nullptr);
+      }
     }
     if (rc) return rc;
     if (red) {

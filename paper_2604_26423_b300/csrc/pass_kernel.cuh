@@ -18,6 +18,8 @@
 // memory offsets become immediates through the additive padded layout `padi`,
 // and global offsets are walked in Gray-code order (one XOR per amplitude).
 #pragma once
+#include <type_traits>
+
 #include "device.cuh"
 
 namespace qaoa {
@@ -300,7 +302,36 @@ __device__ __forceinline__ void reduce_thread_sums(const double* wacc, double& s
 // CC: the kernel contains the C(x) code (cost phase, |+> initialisation and
 // reductions); passes without any of them run an instantiation without it
 // (smaller code, measured faster).
-template <typename Real, int R, int WB, bool FAST, bool CC = true>
+// Operations of a round: compile-time constants taken from a round signature
+// (SIG != 0, plan.h round_sig: the specialised pass kernels) or the round
+// descriptor's fields read at run time (SIG == 0, the generic kernels).
+template <uint32_t SIG>
+struct RoundOps {
+  static constexpr bool kConst = SIG != 0;
+  int layout, src;
+  bool dstg, cost, reduce, lam;
+  uint8_t mixA, mixB;
+  __device__ __forceinline__ explicit RoundOps(const RoundDev& rd)
+      : layout(kConst ? int(SIG & 3u) : int(rd.layout)),
+        src(kConst ? int(SIG >> 2 & 3u) : int(rd.src)),
+        dstg(kConst ? bool(SIG >> 4 & 1u) : rd.dst == DST_GLOBAL_D),
+        cost(kConst ? bool(SIG >> 5 & 1u) : rd.cost != 0),
+        reduce(kConst ? bool(SIG >> 6 & 1u) : rd.reduce != 0),
+        lam(kConst ? bool(SIG >> 7 & 1u) : rd.lam != 0),
+        mixA(kConst ? uint8_t(SIG >> 8 & 31u) : rd.mixA),
+        mixB(kConst ? uint8_t(SIG >> 13 & 31u) : rd.mixB) {}
+};
+
+// Whether a signature sequence needs the C(x) code (cost, reduction, |+>,
+// lambda creation).
+template <uint32_t... RS>
+constexpr bool sigs_need_c() {
+  return ((((RS >> 5 & 1u) | (RS >> 6 & 1u) | (RS >> 7 & 1u)) != 0 || (RS >> 2 & 3u) == 2u) || ...);
+}
+template <uint32_t S0, uint32_t... RS>
+constexpr uint32_t first_sig() { return S0; }
+
+template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t SIG = 0>
 __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tile, uint64_t gbase, int gpar, const int* tconst,
                                           const typename Cx<Real>::T* phase, int lane, int warp, double* wacc,
@@ -313,7 +344,8 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   constexpr bool kSw = sizeof(Real) == 4;
   C2* gstate = reinterpret_cast<C2*>(A.state);
   const bool stream = A.diag != nullptr;
-  const bool init = CC && rd.src == SRC_INIT_D;
+  const RoundOps<SIG> op(rd);
+  const bool init = CC && op.src == SRC_INIT_D;
   // the round's geometry is rebuilt where needed instead of being kept live
   // across the butterflies (register pressure); s: parity of the thread's
   // amplitude 0 (register amplitude j is stored swapped when parity(j) ^ s)
@@ -322,7 +354,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   if (init) {
     // |+>: every amplitude amp0; with the turn path the cost round writes
     // amp0 times the phase directly
-    if (!kSw || stream || !rd.cost) {
+    if (!kSw || stream || !op.cost) {
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
         const bool sw = kSw && (parity_c(j) ^ s);
@@ -330,17 +362,17 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
         v[j].y = sw ? Real(P.amp0) : Real(0);
       }
     }
-  } else if (rd.src == SRC_SMEM_D) {
-    smem_load<R, WB, AB>(rd.layout, tile, entry & 0x7fffffffu, v);
+  } else if (op.src == SRC_SMEM_D) {
+    smem_load<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
   }
 
   auto mixer = [&](uint8_t mask, Real tau, Real alpha) {
     if constexpr (kSw) apply_mixer_sw<R>(v, mask, tau, alpha, FAST, s);
     else apply_mixer<R>(v, mask, tau, alpha, FAST);
   };
-  mixer(rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA));
+  mixer(op.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA));
 
-  if (CC && (rd.cost | rd.reduce)) {
+  if (CC && (op.cost || op.reduce)) {
     // C(x) of each register amplitude (streamed, or kappa + CP[j] +
     // sum_{i: j_i = 1} e_i from the round's tables; cp: the round's
     // register-pair table CP[j], of the pass's cost or reduction round). The
@@ -365,7 +397,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
         }
       }
     };
-    if (rd.cost) {
+    if (op.cost) {
       // a swapped amplitude takes the conjugate phase in the plain product
       // formula: the angle scale is -2pi/2^32 for it (k1) and +2pi/2^32 for
       // a plain one (k0)
@@ -413,13 +445,13 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
         });
       }
     }
-    mixer(rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB));
-    if (rd.dst == DST_GLOBAL_D && sp.rescale) {
+    mixer(op.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB));
+    if (op.dstg && sp.rescale) {
       const Real sc = pick<Real>(sp.scale, sp.fscale);
 #pragma unroll
       for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
     }
-    if (rd.reduce) {
+    if (op.reduce) {
       // |psi|^2 and C(x) do not depend on the storage order of (re, im)
       Real sn = 0, scc = 0;
       if (A.bsum) {
@@ -463,15 +495,15 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       wacc[2 * tid + 1] += double(scc);
     }
   } else {
-    mixer(rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB));
-    if (rd.dst == DST_GLOBAL_D && sp.rescale) {
+    mixer(op.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB));
+    if (op.dstg && sp.rescale) {
       const Real sc = pick<Real>(sp.scale, sp.fscale);
 #pragma unroll
       for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
     }
   }
 
-  if (rd.dst == DST_GLOBAL_D) {
+  if (op.dstg) {
     if constexpr (kSw) {
       if (sp.st_plain) swap_odd<R>(reinterpret_cast<float2*>(v), s);  // a run's output: plain storage
     }
@@ -484,7 +516,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       gray_ptr_walk<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
     }
   } else {
-    smem_store<R, WB, AB>(rd.layout, tile, entry & 0x7fffffffu, v);
+    smem_store<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
   }
 }
 
@@ -492,7 +524,9 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
 // All threads of the CTA take part; shared memory is free again on return.
 // tcount: the CTA's running tile count (selects the tile-constant buffer when
 // the constants come from a table); may be null when no sub-pass has a table.
-template <typename Real, int R, int WB, bool FAST, bool CC = true>
+// RS: the round signatures of a specialised kernel (one sub-pass of one tile
+// per unit, rounds compiled from the signatures), empty for the generic kernel.
+template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t... RS>
 __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tile, int* tconst,
                                          const typename Cx<Real>::T* phase, double* wacc,
@@ -501,19 +535,23 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
   constexpr int AB = sizeof(C2);
+  constexpr bool kSpec = sizeof...(RS) > 0;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = P.n;
   const bool stream = A.diag != nullptr;
   C2 v[1 << R];
   const uint64_t ubase = P.outer_runs.scatter(unit);
-  for (int s = 0; s < P.nsub; ++s) {
+  for (int s = 0; s < (kSpec ? 1 : P.nsub); ++s) {
     const SubDev& sp = P.sub[s];
-    const uint64_t ntiles = 1ull << sp.ninner;
+    const uint64_t ntiles = kSpec ? 1 : 1ull << sp.ninner;
     for (uint64_t ti = 0; ti < ntiles; ++ti) {
-      const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
+      const uint64_t gbase = kSpec ? ubase : ubase | sp.inner_runs.scatter(ti);
       // issue the tile's global loads first: their latency overlaps the
       // barrier below and the tile constants
-      if (sp.rd[0].src == SRC_GLOBAL_D) {
+      bool load0;
+      if constexpr (kSpec) load0 = (first_sig<RS...>() >> 2 & 3u) == SRC_GLOBAL_D;
+      else load0 = sp.rd[0].src == SRC_GLOBAL_D;
+      if (load0) {
         const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
         const C2* gs = reinterpret_cast<const C2*>(A.state);
         if (A.l2hint) {
@@ -541,12 +579,27 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         __syncthreads();
       }
       const int gpar = __popcll(gbase) & 1;
-      for (int r = 0; r < sp.nrounds; ++r) {
-        const RoundDev& rd = sp.rd[r];
-        if (rd.src == SRC_SMEM_D) __syncthreads();
-        fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, gpar, tc, phase, lane, warp, wacc, v);
+      bool red_last;
+      if constexpr (kSpec) {
+        // rounds unrolled from the signatures
+        int r = 0;
+        auto run = [&](auto sigc) {
+          constexpr uint32_t S = decltype(sigc)::value;
+          if constexpr ((S >> 2 & 3u) == SRC_SMEM_D) __syncthreads();
+          fwd_round<Real, R, WB, FAST, CC, S>(P, A, sp, sp.rd[r], tile, gbase, gpar, tc, phase, lane, warp, wacc, v);
+          ++r;
+        };
+        (run(std::integral_constant<uint32_t, RS>{}), ...);
+        red_last = ((RS >> 6 & 1u) | ...) != 0;  // the reduction is in the last round
+      } else {
+        for (int r = 0; r < sp.nrounds; ++r) {
+          const RoundDev& rd = sp.rd[r];
+          if (rd.src == SRC_SMEM_D) __syncthreads();
+          fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, gpar, tc, phase, lane, warp, wacc, v);
+        }
+        red_last = sp.rd[sp.nrounds - 1].reduce != 0;
       }
-      if (CC && A.bsum && sp.rd[sp.nrounds - 1].reduce) {
+      if (CC && A.bsum && red_last) {
         // this tile is 2^T consecutive amplitudes: its 2^(T-12) block sums, in warp order
         __syncthreads();
         if (tid < (1 << (T - 12))) {
@@ -560,12 +613,10 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
   }
 }
 
-// Shared-memory layout of the dynamic buffer:
+// Body of the forward pass kernels. Shared-memory layout of the dynamic buffer:
 //   tile[padded 2^T] complex | tile consts (two buffers) | phase table
-// (the weight matrix is read through the L1 cache by one warp per tile)
-template <typename Real, int R, int WB, bool FAST, bool CC>
-__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : 2) : 1)
-fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
+template <typename Real, int R, int WB, bool FAST, bool CC, uint32_t... RS>
+__device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& A) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -589,7 +640,7 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
 
   uint32_t tcount = 0;
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    fwd_unit<Real, R, WB, FAST, CC>(P, A, unit, tile, tconst, phase, wacc, &tcount);
+    fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount);
 
   if (A.partial) {
     __syncthreads();
@@ -600,6 +651,22 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
       A.partial[2 * blockIdx.x + 1] = sC;
     }
   }
+}
+
+// Generic forward pass: rounds decoded from the descriptor at run time.
+template <typename Real, int R, int WB, bool FAST, bool CC>
+__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : 2) : 1)
+fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
+  fwd_pass_body<Real, R, WB, FAST, CC>(P, A);
+}
+
+// Specialised complex64 forward pass for one round-signature sequence RS
+// (one sub-pass of one tile per super-tile): the rounds' operations, layouts
+// and masks are compile-time constants.
+template <int R, int WB, bool FAST, uint32_t... RS>
+__global__ void __launch_bounds__(32 << WB, R + WB <= 7 ? 4 : 2)
+fwd_spec_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
+  fwd_pass_body<float, R, WB, FAST, sigs_need_c<RS...>(), RS...>(P, A);
 }
 
 }  // namespace qaoa

@@ -68,6 +68,12 @@ bool menu_layout(const TileShape& sh, int id, RoundPlan& rp) {
   return true;
 }
 
+uint32_t round_sig(const RoundPlan& rp) {
+  return kSigValid | uint32_t(rp.layout & 3) | uint32_t(rp.src & 3) << 2 | uint32_t(rp.dst == DST_GLOBAL) << 4 |
+         uint32_t(rp.cost != 0) << 5 | uint32_t(rp.reduce != 0) << 6 | uint32_t(rp.lam != 0) << 7 |
+         uint32_t(rp.mixA & 31) << 8 | uint32_t(rp.mixB & 31) << 13;
+}
+
 std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool cost, uint32_t b_bits,
                                    bool reduce, uint8_t first_src, bool lam) {
   // Breadth-first search over (bits left for mixer A, bits left for mixer B,

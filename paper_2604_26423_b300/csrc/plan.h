@@ -131,6 +131,13 @@ std::string validate(const Plan& plan);
 std::string validate_rounds(const TileShape& shape, const std::vector<RoundPlan>& rounds,
                             uint32_t a_bits, bool cost, uint32_t b_bits, bool reduce);
 
+// Compile-time signature of a round (the kernels' specialised instantiations,
+// kSigValid set): bits 0-1 layout, 2-3 source, 4 stores to global memory,
+// 5 cost phase, 6 reduction, 7 lambda creation, 8-12 mixer A mask, 13-17
+// mixer B mask. 0 is never a valid signature (it selects runtime decoding).
+constexpr uint32_t kSigValid = 1u << 31;
+uint32_t round_sig(const RoundPlan& rp);
+
 // The fixed menu of round layouts for a tile shape (T = R + 5 + WB):
 //   0 "G1": registers on bits 5..R+4, lanes on 0..4, warps on the rest
 //   1 "G2": registers on the top R bits, lanes on 0..4, warps on the rest

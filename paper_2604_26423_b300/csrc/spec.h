@@ -1,0 +1,21 @@
+// spec.h -- registry of the specialised complex64 pass kernels (tile shape
+// 4x3, fast mixer form) compiled for the round-signature sequences listed in
+// pass_sigs.inc (generated at build time by gen_sigs.cpp from the planner).
+#pragma once
+#include <cstdint>
+
+#include "device.cuh"
+#include "pass_kernel.cuh"
+
+namespace qaoa {
+
+using FwdPassKernel = void (*)(PassDev, PassArgs);
+
+// Round signature (plan.h, round_sig) of a round descriptor.
+uint32_t round_sig_dev(const RoundDev& rd);
+
+// The specialised forward pass kernel for the rounds of a single-sub-pass
+// descriptor (its round signatures), or nullptr if none was compiled.
+FwdPassKernel find_fwd_spec(const SubDev& sd);
+
+}  // namespace qaoa

@@ -328,3 +328,20 @@ def test_plan_options_vs_oracle(n, p, prec, order, float_lanes, monkeypatch):
         assert l2 <= 1e-4 and abs(res["r"] - ref["r"]) <= 1e-5
     else:
         assert l2 <= 1e-12 and abs(res["r"] - ref["r"]) <= 1e-9
+
+
+@pytest.mark.parametrize("n,p,order", [(22, 3, "last"), (25, 4, "middle"), (27, 2, "last")])
+def test_specialised_kernels_bitwise(n, p, order, monkeypatch):
+    # the specialised pass kernels (rounds compiled from their signatures) do
+    # the generic kernel's arithmetic: identical states, <C> and block sums
+    monkeypatch.setenv("QAOA_GROUP_ORDER", order)
+    u, v, w = graph("complete", n, 600 + n)
+    outs = []
+    for spec in ("1", "0"):
+        monkeypatch.setenv("QAOA_SPEC", spec)
+        with sim(n, u, v, w, S, "c64") as s:
+            s.run(p, 0.6, 0.3)
+            outs.append((s.state().cpu().numpy().copy(), s.expect()["exp_c"], s.sample(256, seed=5)))
+    (a, ea, sa), (b, eb, sb) = outs
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
+    assert ea == eb and np.array_equal(sa, sb)
