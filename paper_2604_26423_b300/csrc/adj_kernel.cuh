@@ -150,7 +150,7 @@ struct AdjPrefetch {
   uint64_t gnext;
 };
 
-template <typename Real, int R, int WB, bool FAST, bool CC = true>
+template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t SIG = 0>
 __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, uint64_t gbase,
                                           int gpar, const int* tconst, const typename Cx<Real>::T* phase, int lane,
@@ -171,7 +171,8 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   const uint32_t entry = Geo::entry_of(rd, lane, warp, A.ctabs);
   const uint32_t sb = entry & 0x7fffffffu;
   const int s = kSw ? int(entry >> 31) ^ gpar : 0;
-  const bool need_c = CC && (rd.cost || rd.lam);
+  const RoundOps<SIG> op(rd);
+  const bool need_c = CC && (op.cost || op.lam);
   RoundCost<R, WB> rcost;
   if (need_c && !stream) rcost.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
   // cp: the register-pair table CP[j] of the pass's cost round (P.cpc) or
@@ -196,17 +197,17 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
 
   // a global round's loads were issued by the caller before the tile barrier,
   // or copied into shared memory (prefetch)
-  if (rd.src == SRC_GLOBAL_D && pf.on) {
-    smem_load<R, WB, AB>(rd.layout, tv, sb, v);
-    if (!(CC && rd.lam)) smem_load<R, WB, AB>(rd.layout, tl, sb, l);
+  if (op.src == SRC_GLOBAL_D && pf.on) {
+    smem_load<R, WB, AB>(op.layout, tv, sb, v);
+    if (!(CC && op.lam)) smem_load<R, WB, AB>(op.layout, tl, sb, l);
   }
   if constexpr (kSw) {
     // the first sub-pass reads the forward run's plain amplitudes (psi only:
     // lambda is created from it)
-    if (rd.src == SRC_GLOBAL_D && sp.ld_plain) swap_odd<R>(reinterpret_cast<float2*>(v), s);
+    if (op.src == SRC_GLOBAL_D && sp.ld_plain) swap_odd<R>(reinterpret_cast<float2*>(v), s);
   }
-  if (rd.src == SRC_GLOBAL_D) {
-    if (CC && rd.lam) {
+  if (op.src == SRC_GLOBAL_D) {
+    if (CC && op.lam) {
       // lambda = C(x) psi (the operator whose expectation is differentiated);
       // <psi|lambda> = <C> on the way
       for_costs(P.cpr, [&](int j, int c) {
@@ -217,12 +218,12 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       });
     }
   } else {
-    smem_load<R, WB, AB>(rd.layout, tv, sb, v);
-    smem_load<R, WB, AB>(rd.layout, tl, sb, l);
+    smem_load<R, WB, AB>(op.layout, tv, sb, v);
+    smem_load<R, WB, AB>(op.layout, tl, sb, l);
   }
 
   if constexpr (sizeof(Real) == 4) {
-    if (pf.on && rd.dst == DST_GLOBAL_D) {
+    if (pf.on && op.dstg) {
       // every thread has read its amplitudes: the tiles are free for the next copy
       __syncthreads();
       if (pf.next) {
@@ -242,9 +243,9 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     else
       inverse_mixer<R>(v, l, mask, tau, alpha, FAST, cpow, sc, acc);
   };
-  inv_mixer(rd.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA),
-            pow_bits(pick<Real>(P.cA, P.fcA), rd.mixA), ga);
-  if (CC && rd.cost) {
+  inv_mixer(op.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA),
+            pow_bits(pick<Real>(P.cA, P.fcA), op.mixA), ga);
+  if (CC && op.cost) {
     // Im conj(l) v of a swapped pair of amplitudes has the opposite sign: the
     // terms are summed by the parity of j and combined with the thread's s;
     // a swapped amplitude takes the conjugate phase in the plain product
@@ -268,10 +269,10 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     const Real tc = !kSw ? tc0 + tc1 : s ? tc1 - tc0 : tc0 - tc1;
     gc = fma(sc * sc, tc, gc);
   }
-  inv_mixer(rd.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB),
-            pow_bits(pick<Real>(P.cB, P.fcB), rd.mixB), gbv);
+  inv_mixer(op.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB),
+            pow_bits(pick<Real>(P.cB, P.fcB), op.mixB), gbv);
 
-  if (rd.dst == DST_GLOBAL_D) {
+  if (op.dstg) {
     if (sp.store) {
       if (FAST) {
 #pragma unroll
@@ -285,8 +286,8 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
       gray_ptr_walk<R>(glam, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, l[j]); });
     }
   } else {
-    smem_store<R, WB, AB>(rd.layout, tv, sb, v);
-    smem_store<R, WB, AB>(rd.layout, tl, sb, l);
+    smem_store<R, WB, AB>(op.layout, tv, sb, v);
+    smem_store<R, WB, AB>(op.layout, tl, sb, l);
   }
 }
 
@@ -294,7 +295,9 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
 // thread's amplitudes are added to gA, gC, gB.
 // tcount: the CTA's running tile count (tile-constant buffer when the
 // constants come from a table); may be null when no sub-pass has a table.
-template <typename Real, int R, int WB, bool FAST, bool CC = true>
+// RS: the round signatures of a specialised kernel (one sub-pass of one tile
+// per unit), empty for the generic kernel.
+template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t... RS>
 __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, int* tconst,
                                          const typename Cx<Real>::T* phase, double& gA, double& gC, double& gB,
@@ -305,20 +308,24 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = P.n;
   const bool stream = A.diag != nullptr;
+  constexpr bool kSpec = sizeof...(RS) > 0;
   const uint64_t ubase = P.outer_runs.scatter(unit);
-  for (int s = 0; s < P.nsub; ++s) {
+  for (int s = 0; s < (kSpec ? 1 : P.nsub); ++s) {
     const SubDev& sp = P.sub[s];
-    const uint64_t ntiles = 1ull << sp.ninner;
+    const uint64_t ntiles = kSpec ? 1 : 1ull << sp.ninner;
     AdjPrefetch pf;
     pf.on = sizeof(Real) == 4 && sp.cgtab >= 0;  // one sub-pass of one tile per unit
     pf.next = pf.on && unit + gridDim.x < P.n_units;
     pf.gnext = pf.next ? P.outer_runs.scatter(unit + gridDim.x) : 0;
     for (uint64_t ti = 0; ti < ntiles; ++ti) {
-      const uint64_t gbase = ubase | sp.inner_runs.scatter(ti);
+      const uint64_t gbase = kSpec ? ubase : ubase | sp.inner_runs.scatter(ti);
       // issue the first round's global loads first: their latency overlaps the
       // barrier below and the tile constants
       C2 v[1 << R], l[1 << R];
-      if (sp.rd[0].src == SRC_GLOBAL_D && !pf.on) {
+      bool load0;
+      if constexpr (kSpec) load0 = (first_sig<RS...>() >> 2 & 3u) == SRC_GLOBAL_D;
+      else load0 = sp.rd[0].src == SRC_GLOBAL_D;
+      if (load0 && !pf.on) {
         const RoundGeo<R, WB, sizeof(C2)> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
         gray_ptr_walk<R>(reinterpret_cast<const C2*>(A.psi), g0.gb, g0.gstr,
                          [&](int j, const C2* q) { v[j] = __ldcg(q); });
@@ -355,11 +362,24 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
         // fp32: the terms of one tile are summed in fp32, then added in FP64
         // (keeps fp64 conversions out of the rounds)
         Real ga = 0, gc = 0, gbv = 0, ge = 0;
-        for (int r = 0; r < sp.nrounds; ++r) {
-          const RoundDev& rd = sp.rd[r];
-          if (rd.src == SRC_SMEM_D) __syncthreads();
-          adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, gpar, tc, phase, lane, warp, ga, gc, gbv, ge,
-                                           sc, v, l, pf);
+        if constexpr (kSpec) {
+          // rounds unrolled from the signatures
+          int r = 0;
+          auto run = [&](auto sigc) {
+            constexpr uint32_t S = decltype(sigc)::value;
+            if constexpr ((S >> 2 & 3u) == SRC_SMEM_D) __syncthreads();
+            adj_round<Real, R, WB, FAST, CC, S>(P, A, sp, sp.rd[r], tv, tl, gbase, gpar, tc, phase, lane, warp, ga,
+                                                gc, gbv, ge, sc, v, l, pf);
+            ++r;
+          };
+          (run(std::integral_constant<uint32_t, RS>{}), ...);
+        } else {
+          for (int r = 0; r < sp.nrounds; ++r) {
+            const RoundDev& rd = sp.rd[r];
+            if (rd.src == SRC_SMEM_D) __syncthreads();
+            adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, gpar, tc, phase, lane, warp, ga, gc, gbv,
+                                             ge, sc, v, l, pf);
+          }
         }
         gA += double(ga);
         gC += double(gc);
@@ -371,10 +391,10 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
   }
 }
 
+// Body of the adjoint pass kernels.
 // Shared memory: psi tile (padded 2^T) | lambda tile | tile consts (two buffers) | phase table
-template <typename Real, int R, int WB, bool FAST, bool CC>
-__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
-adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
+template <typename Real, int R, int WB, bool FAST, bool CC, uint32_t... RS>
+__device__ __forceinline__ void adj_pass_body(const PassDev& P, const AdjArgs& A) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -405,7 +425,7 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
     }
   }
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    adj_unit<Real, R, WB, FAST, CC>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE, &tcount);
+    adj_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE, &tcount);
 
   __shared__ double red[4][32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -424,6 +444,21 @@ adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
     A.partial[4 * blockIdx.x + 2] = s2;
     A.partial[4 * blockIdx.x + 3] = s3;
   }
+}
+
+// Generic adjoint pass: rounds decoded from the descriptor at run time.
+template <typename Real, int R, int WB, bool FAST, bool CC>
+__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
+adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
+  adj_pass_body<Real, R, WB, FAST, CC>(P, A);
+}
+
+// Specialised complex64 adjoint pass for one round-signature sequence RS (one
+// sub-pass of one tile per super-tile).
+template <int R, int WB, bool FAST, uint32_t... RS>
+__global__ void __launch_bounds__(32 << WB, 2)
+adj_spec_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
+  adj_pass_body<float, R, WB, FAST, sigs_need_c<RS...>(), RS...>(P, A);
 }
 
 }  // namespace qaoa

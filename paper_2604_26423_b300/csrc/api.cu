@@ -771,9 +771,19 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     int bps = 0;
     bool cc = false;
     for (const SubPassPlan& sp : pp.subs) cc = cc || sp.needs_c || sp.linit;
-    rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, false, pd, aa, smem, 0, &bps)
-                              : adj_any<float>(c, fast, cc, false, pd, aa, smem, 0, &bps);
-    if (rc) return rc;
+    // a specialised kernel when one was compiled for this pass's rounds
+    AdjPassKernel spec = nullptr;
+    if (c->prec == QAOA_C64 && fast && pd.nsub == 1 && pd.sub[0].ninner == 0 && spec_enabled())
+      spec = find_adj_spec(pd.sub[0]);
+    if (spec) {
+      CUDA_TRY(c, cudaFuncSetAttribute((const void*)spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)spec, 32 << kWBAdj, smem));
+      if (bps < 1) return c->set_err(QAOA_ECUDA, "adjoint kernel does not fit on an SM (smem %zu)", smem);
+    } else {
+      rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, false, pd, aa, smem, 0, &bps)
+                                : adj_any<float>(c, fast, cc, false, pd, aa, smem, 0, &bps);
+      if (rc) return rc;
+    }
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
     {
@@ -784,8 +794,15 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
       if (stream)
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 1, bytes);
-      rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, true, pd, aa, smem, grid, nullptr)
-                                : adj_any<float>(c, fast, cc, true, pd, aa, smem, grid, nullptr);
+      if (spec) {
+        spec<<<grid, 32 << kWBAdj, smem, c->stream>>>(pd, aa);
+        if (c->prof_on) ++c->nlaunch;
+        const cudaError_t le = cudaGetLastError();
+        rc = le == cudaSuccess ? QAOA_OK : c->set_err(QAOA_ECUDA, "specialised adjoint kernel: %s", cudaGetErrorString(le));
+      } else {
+        rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, true, pd, aa, smem, grid, nullptr)
+                                  : adj_any<float>(c, fast, cc, true, pd, aa, smem, grid, nullptr);
+      }
     }
     if (rc) return rc;
     sum_partials_kernel<<<1, 32, 0, c->stream>>>((const double*)c->d_partial.p, grid, 4,

@@ -4,12 +4,14 @@
 #pragma once
 #include <cstdint>
 
+#include "adj_kernel.cuh"
 #include "device.cuh"
 #include "pass_kernel.cuh"
 
 namespace qaoa {
 
 using FwdPassKernel = void (*)(PassDev, PassArgs);
+using AdjPassKernel = void (*)(PassDev, AdjArgs);
 
 // Round signature (plan.h, round_sig) of a round descriptor.
 uint32_t round_sig_dev(const RoundDev& rd);
@@ -17,5 +19,8 @@ uint32_t round_sig_dev(const RoundDev& rd);
 // The specialised forward pass kernel for the rounds of a single-sub-pass
 // descriptor (its round signatures), or nullptr if none was compiled.
 FwdPassKernel find_fwd_spec(const SubDev& sd);
+
+// The same for the adjoint pass kernel (4x3 tiles of psi and lambda).
+AdjPassKernel find_adj_spec(const SubDev& sd);
 
 }  // namespace qaoa

@@ -174,3 +174,21 @@ def test_grad_exp_c_matches_forward_and_expect_needs_rerun():
         assert abs(g["exp_c"] - e) <= 2e-6 * e
         with pytest.raises(QaoaError):
             s.expect()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,p", [(20, 3), (24, 5)])
+def test_specialised_adjoint_kernels_identical(n, p, monkeypatch):
+    # the specialised adjoint kernels do the generic kernel's arithmetic:
+    # identical gradients
+    from paper_2604_26423_b300 import inputs
+    from paper_2604_26423_b300.qaoa import Simulator
+    u, v, w = inputs.complete_graph(n, 900 + n)
+    res = []
+    for spec in ("1", "0"):
+        monkeypatch.setenv("QAOA_SPEC", spec)
+        with Simulator(n, u, v, w, 0.1, "c64", with_grad=True) as s:
+            res.append(s.grad(p, 0.6, 0.3))
+    a, b = res
+    assert np.array_equal(a["g_gamma"], b["g_gamma"]) and np.array_equal(a["g_beta"], b["g_beta"])
+    assert a["exp_c"] == b["exp_c"]
