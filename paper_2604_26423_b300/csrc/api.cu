@@ -316,10 +316,11 @@ bool spec_enabled() {
   return !(e && strcmp(e, "0") == 0);
 }
 
-// Asynchronous tile copies in the adjoint passes (QAOA_ADJ_PREFETCH=0 disables).
+// Asynchronous tile copies in the adjoint passes (QAOA_ADJ_PREFETCH=1 enables;
+// measured slower than the register loads with the specialised kernels).
 bool adj_prefetch() {
   const char* e = getenv("QAOA_ADJ_PREFETCH");
-  return !(e && strcmp(e, "0") == 0);
+  return e && strcmp(e, "1") == 0;
 }
 
 int grad_base_order() {

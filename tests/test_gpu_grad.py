@@ -192,3 +192,19 @@ def test_specialised_adjoint_kernels_identical(n, p, monkeypatch):
     a, b = res
     assert np.array_equal(a["g_gamma"], b["g_gamma"]) and np.array_equal(a["g_beta"], b["g_beta"])
     assert a["exp_c"] == b["exp_c"]
+
+
+@pytest.mark.gpu
+def test_adjoint_tile_prefetch_identical(monkeypatch):
+    # asynchronous copies of the next tile (optional) give the same gradients
+    from paper_2604_26423_b300 import inputs
+    from paper_2604_26423_b300.qaoa import Simulator
+    n, p = 22, 3
+    u, v, w = inputs.complete_graph(n, 922)
+    res = []
+    for pf in ("1", "0"):
+        monkeypatch.setenv("QAOA_ADJ_PREFETCH", pf)
+        with Simulator(n, u, v, w, 0.1, "c64", with_grad=True) as s:
+            res.append(s.grad(p, 0.6, 0.3))
+    a, b = res
+    assert np.array_equal(a["g_gamma"], b["g_gamma"]) and np.array_equal(a["g_beta"], b["g_beta"])
