@@ -59,7 +59,10 @@ METRIC = "LR-QAOA layers/s at n=33 (complex64, K_33, p=3)"
 GRAD_N, GRAD_P, GRAD_DGAMMA, GRAD_DBETA = 28, 10, 0.6, 0.3
 BATCH_COUNT, BATCH_SEED = 4096, 2604
 PROFILE_JSON = os.path.join(ROOT, "profiles", "fwd_pass_kernel_traffic.json")
-KERNEL_SOURCES = ["paper_2604_26423_b300/csrc/pass_kernel.cuh", "paper_2604_26423_b300/csrc/device.cuh"]
+# sources that determine the forward pass kernels' DRAM traffic (kernels, plans, descriptors, dispatch)
+KERNEL_SOURCES = ["paper_2604_26423_b300/csrc/pass_kernel.cuh", "paper_2604_26423_b300/csrc/device.cuh",
+                  "paper_2604_26423_b300/csrc/plan.cpp", "paper_2604_26423_b300/csrc/desc.cu",
+                  "paper_2604_26423_b300/csrc/spec_fwd.cu", "paper_2604_26423_b300/csrc/api.cu"]
 
 
 def kernel_hash() -> str:
@@ -390,7 +393,7 @@ def run_gpu(args):
         "gpu_launches": int(launches_all) if launches_all else int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "fwd_pass_kernel", "launches": prof["launches"],
+                     "kernel": "forward pass kernels (fwd_spec_kernel, fwd_pass_kernel)", "launches": prof["launches"],
                      "bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
                      "ms_per_launch": prof["ms"] / max(1, prof["launches"])},
         "result": {"exp_c": res["exp_c"], "r": res["r"], "norm": res["norm"], "c_max": res["c_max"]},
