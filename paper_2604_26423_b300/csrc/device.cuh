@@ -166,6 +166,10 @@ __device__ __forceinline__ float2 phase_turns(uint64_t ph0, uint64_t ph1, uint32
   return phase_turns32(hi, k);
 }
 
+// Scales both components of an amplitude (packed for complex64).
+__device__ __forceinline__ void scale_amp(float2& v, float s) { v = __fmul2_rn(v, make_float2(s, s)); }
+__device__ __forceinline__ void scale_amp(double2& v, double s) { v.x *= s; v.y *= s; }
+
 template <typename Real> struct Cx;
 template <> struct Cx<float> { using T = float2; };
 template <> struct Cx<double> { using T = double2; };

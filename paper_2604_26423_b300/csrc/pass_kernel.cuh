@@ -449,7 +449,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     if (op.dstg && sp.rescale) {
       const Real sc = pick<Real>(sp.scale, sp.fscale);
 #pragma unroll
-      for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
+      for (int j = 0; j < NA; ++j) scale_amp(v[j], sc);
     }
     if (op.reduce) {
       // |psi|^2 and C(x) do not depend on the storage order of (re, im)
@@ -499,7 +499,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     if (op.dstg && sp.rescale) {
       const Real sc = pick<Real>(sp.scale, sp.fscale);
 #pragma unroll
-      for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
+      for (int j = 0; j < NA; ++j) scale_amp(v[j], sc);
     }
   }
 
