@@ -252,20 +252,46 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     // formula (angle scale k1 = -k0)
     Real tc0 = 0, tc1 = 0;
     const float k0 = s ? -kTurn32 : kTurn32, k1 = -k0;
-    for_costs(P.cpc, [&](int j, int c) {
-      const Real h = Real(P.wsum - 2 * c);
+    auto apply = [&](int j, Real h, C2 ph) {
       const Real q = fma(l[j].x, v[j].y, -l[j].y * v[j].x);
       if (parity_c(j)) tc1 = fma(q, h, tc1); else tc0 = fma(q, h, tc0);
-      C2 ph;
-      if constexpr (kSw) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo), parity_c(j) ? k1 : k0);
-      else ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
       // multiply both vectors by the conjugate phase (inverse cost unitary)
       const Real vr = v[j].x, vi = v[j].y, lr = l[j].x, li = l[j].y;
       v[j].x = vr * ph.x + vi * ph.y;
       v[j].y = vi * ph.x - vr * ph.y;
       l[j].x = lr * ph.x + li * ph.y;
       l[j].y = li * ph.x - lr * ph.y;
-    });
+    };
+    bool walked = false;
+    if constexpr (kSw) {
+      if (!stream) {
+        // complex64 from the tables: h(x) = W - 2 C(x) and the phase's 32-bit
+        // turn count both follow the Gray walk (see fwd_round)
+        walked = true;
+        uint32_t E[R];
+        uint32_t t = rcost.turns(P.ph0, P.ph1, P.c_lo, E);
+        int lin = rcost.kappa;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          const int j = k ^ (k >> 1);
+          if (k) {
+            const int b = ctz_c(k);
+            lin += (j >> b & 1) ? rcost.e[b] : -rcost.e[b];
+            t += (j >> b & 1) ? E[b] : 0u - E[b];
+          }
+          const C2 ph = phase_turns32(t + P.cpt[j], parity_c(j) ? k1 : k0);
+          apply(j, Real(P.wsum - 2 * (lin + P.cpc[j])), ph);
+        }
+      }
+    }
+    if (!walked) {
+      for_costs(P.cpc, [&](int j, int c) {
+        C2 ph;
+        if constexpr (kSw) ph = phase_turns(P.ph0, P.ph1, uint32_t(c - P.c_lo), parity_c(j) ? k1 : k0);
+        else ph = phase[min(unsigned(c - P.c_lo), unsigned(P.ncost - 1))];
+        apply(j, Real(P.wsum - 2 * c), ph);
+      });
+    }
     const Real tc = !kSw ? tc0 + tc1 : s ? tc1 - tc0 : tc0 - tc1;
     gc = fma(sc * sc, tc, gc);
   }
