@@ -84,9 +84,12 @@ size_t qaoa_aux_bytes(int n, int precision, int cost_mode, int with_grad);
  *   aux_dev      device buffer of aux_bytes >= qaoa_aux_bytes(...) or NULL
  *                (the library allocates lazily when first needed).
  *   cuda_stream  cudaStream_t to order all work on (NULL = legacy stream).
- * Computes the exhaustive C_min / C_max (with smallest argmin / argmax) on the
- * GPU before returning. Errors: EINVAL (bad graph or sizes), ENOMEM (buffer too
- * small or allocation failure), ECUDA. On failure *ctx is NULL.
+ * Stream mode writes the int32 diagonal and computes the exhaustive C_min /
+ * C_max (with smallest argmin / argmax) on the GPU before returning; recompute
+ * mode obtains them with the first run (its |+> pass visits every index once)
+ * or, when qaoa_expect asks for them before any run, with the exhaustive
+ * kernel. Errors: EINVAL (bad graph or sizes), ENOMEM (buffer too small or
+ * allocation failure), ECUDA. On failure *ctx is NULL.
  */
 int qaoa_init_graph(qaoa_ctx **ctx, int n, int n_edges, const int32_t *u, const int32_t *v,
                     const int32_t *w, double weight_scale, int precision, int cost_mode,
@@ -107,7 +110,8 @@ int qaoa_run_angles(qaoa_ctx *ctx, int p, const double *gamma, const double *bet
  * Results of the last run (any output pointer may be NULL): <C> and the norm
  * (FP64 reductions), r = (<C> - C_min)/(C_max - C_min) (Eq. r with the exact
  * mean; 1 when C_max == C_min), and the exhaustive extremes with their smallest
- * indices. Synchronises the stream. Errors: ESTATE (no run yet), ECUDA.
+ * indices (available before any run: then only the extremes may be requested).
+ * Synchronises the stream. Errors: ESTATE (<C>, r or norm before a run), ECUDA.
  */
 int qaoa_expect(qaoa_ctx *ctx, double *exp_c, double *r, double *norm, int64_t *c_min,
                 int64_t *c_max, uint64_t *argmin, uint64_t *argmax);

@@ -80,7 +80,7 @@ struct qaoa_ctx {
   void* aux = nullptr;
   size_t aux_bytes = 0;
   DevBuf aux_own;
-  DevBuf d_wmat, d_ctabs, d_phase, d_partial, d_result, d_ext, d_ext_part;
+  DevBuf d_wmat, d_ctabs, d_phase, d_partial, d_result, d_ext, d_ext_part, d_ext_keys;
   DevBuf d_sums, d_pre, d_pre2, d_shots, d_uni, d_ang;
   DevBuf d_lambda, d_gacc;                                            // adjoint vector (if no aux), per-pass sums
   TableStore tabs;                                                     // host copy of all cost tables
@@ -97,6 +97,8 @@ struct qaoa_ctx {
   long long prof_n[5] = {0, 0, 0, 0, 0};
   long long nlaunch = 0;  // every kernel launch while profiling is enabled
   Extreme ext{};
+  bool ext_ready = false;    // ext holds C_min / C_max and their indices
+  bool ext_pending = false;  // d_ext_keys holds them (written by a run's first pass)
   bool have_result = false;
   bool state_ready = false;
   bool sums_ready = false;  // d_sums holds the sampling block sums of the current state
@@ -520,6 +522,15 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       const char* e = getenv("QAOA_L2HINT");
       pa.l2hint = (e && atoi(e) != 0) ? 1 : 0;
     }
+    // the first pass visits every index once: the extremes come with it when
+    // they are not known yet
+    pa.ext_keys = nullptr;
+    const RoundDev& r0 = pd.sub[0].rd[0];
+    if (pp.init && !c->ext_ready && !c->ext_pending && (r0.cost || r0.reduce)) {
+      CUDA_TRY(c, c->d_ext_keys.ensure(2 * sizeof(unsigned long long)));
+      CUDA_TRY(c, cudaMemsetAsync(c->d_ext_keys.p, 0xff, 2 * sizeof(unsigned long long), c->stream));
+      pa.ext_keys = (unsigned long long*)c->d_ext_keys.p;
+    }
     int bps = 0;
     const int wide = fwd_shape_id(c->prec);
     const bool cc = ccs[pi];
@@ -572,6 +583,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       }
     }
     if (rc) return rc;
+    if (pa.ext_keys) c->ext_pending = true;
     if (red) {
       sum_partials_kernel<<<1, 32, 0, c->stream>>>((const double*)c->d_partial.p, grid, 2, (double*)c->d_result.p);
       if (c->prof_on) ++c->nlaunch;
@@ -854,6 +866,30 @@ int compute_extremes(qaoa_ctx* c, int32_t* diag_out, bool restrict_half) {
   return QAOA_OK;
 }
 
+// C_min / C_max and their smallest indices on the host: from the keys of a
+// run's first pass when it computed them, else from the exhaustive kernel.
+int ensure_extremes(qaoa_ctx* c) {
+  if (c->ext_ready) return QAOA_OK;
+  if (c->ext_pending) {
+    unsigned long long k[2];
+    CUDA_TRY(c, cudaMemcpyAsync(k, c->d_ext_keys.p, sizeof k, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const unsigned long long mask = (1ull << 34) - 1;
+    c->ext.vmin = c->c_lo + (long long)(k[0] >> 34);
+    c->ext.amin = k[0] & mask;
+    c->ext.vmax = c->c_hi - (long long)(k[1] >> 34);
+    c->ext.amax = k[1] & mask;
+  } else {
+    int rc = compute_extremes(c, nullptr, true);
+    if (rc) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(&c->ext, c->d_ext.p, sizeof(Extreme), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  c->ext_ready = true;
+  c->ext_pending = false;
+  return QAOA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -964,19 +1000,23 @@ int qaoa_init_graph(qaoa_ctx** out, int n, int m, const int32_t* u, const int32_
       c->aux_bytes = need;
     }
     diag = (int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n)));
+    // the diagonal is needed by every pass: it is written now, with the extremes
+    int rc = compute_extremes(c.get(), diag, true);
+    if (rc) {
+      std::string msg = c->err;
+      qaoa_free(c.release());
+      return fail(rc, msg);
+    }
+    if (cudaMemcpyAsync(&c->ext, c->d_ext.p, sizeof(Extreme), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+      std::string msg = std::string("extremes transfer failed: ") + cudaGetErrorString(cudaGetLastError());
+      qaoa_free(c.release());
+      return fail(QAOA_ECUDA, msg);
+    }
+    c->ext_ready = true;
   }
-  int rc = compute_extremes(c.get(), diag, true);
-  if (rc) {
-    std::string msg = c->err;
-    qaoa_free(c.release());
-    return fail(rc, msg);
-  }
-  if (cudaMemcpyAsync(&c->ext, c->d_ext.p, sizeof(Extreme), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-      cudaStreamSynchronize(c->stream) != cudaSuccess) {
-    std::string msg = std::string("extremes transfer failed: ") + cudaGetErrorString(cudaGetLastError());
-    qaoa_free(c.release());
-    return fail(QAOA_ECUDA, msg);
-  }
+  // recompute mode: the extremes come from the first run's |+> pass (every
+  // index visited once), or from the exhaustive kernel when asked for first
   *out = c.release();
   return QAOA_OK;
 }
@@ -1003,6 +1043,10 @@ int qaoa_run(qaoa_ctx* c, int p, double dgamma, double dbeta) {
 int qaoa_expect(qaoa_ctx* c, double* exp_c, double* r, double* norm, int64_t* c_min, int64_t* c_max,
                 uint64_t* argmin, uint64_t* argmax) {
   if (!c) return QAOA_EINVAL;
+  if (c_min || c_max || argmin || argmax || r) {
+    const int rc = ensure_extremes(c);
+    if (rc) return rc;
+  }
   if (c_min) *c_min = c->ext.vmin;
   if (c_max) *c_max = c->ext.vmax;
   if (argmin) *argmin = c->ext.amin;
@@ -1159,7 +1203,7 @@ void qaoa_free(qaoa_ctx* c) {
   if (c->own_state && c->state) cudaFree(c->state);
   c->aux_own.release();
   DevBuf* bufs[] = {&c->d_wmat, &c->d_ctabs, &c->d_phase, &c->d_partial, &c->d_result, &c->d_ext,
-                    &c->d_ext_part, &c->d_sums, &c->d_pre, &c->d_pre2, &c->d_shots, &c->d_uni, &c->d_ang,
+                    &c->d_ext_part, &c->d_ext_keys, &c->d_sums, &c->d_pre, &c->d_pre2, &c->d_shots, &c->d_uni, &c->d_ang,
                     &c->d_lambda, &c->d_gacc};
   for (DevBuf* b : bufs) b->release();
   for (auto& kv : c->tct_tabs) kv.second.release();

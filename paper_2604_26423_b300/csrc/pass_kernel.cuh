@@ -38,6 +38,11 @@ struct PassArgs {
                           // the final pass when its tiles are index-contiguous, or nullptr
   int phase_in_smem;      // copy the phase table into shared memory
   int l2hint;             // L2 priorities: keep sub-pass outputs that are read back
+  // exhaustive extremes in the |+> round (every index visited once): packed
+  // keys [(C - c_lo) << 34 | x, (c_hi - C) << 34 | x], each the minimum over
+  // all x (smallest C, resp. largest C, then smallest index); must hold ~0 on
+  // entry; nullptr: not computed in this pass
+  unsigned long long* ext_keys;
 };
 
 // Compile-time copy of the planner's layout menu (plan.cpp, menu_layout).
@@ -335,7 +340,7 @@ template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t SIG 
 __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tile, uint64_t gbase, int gpar, const int* tconst,
                                           const typename Cx<Real>::T* phase, int lane, int warp, double* wacc,
-                                          typename Cx<Real>::T* v) {
+                                          typename Cx<Real>::T* v, unsigned long long* ext_s) {
   using C2 = typename Cx<Real>::T;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
@@ -364,6 +369,49 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     }
   } else if (op.src == SRC_SMEM_D) {
     smem_load<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
+  }
+
+  if (CC && init && A.ext_keys && (op.cost || op.reduce)) {
+    // exhaustive extremes: packed keys of this thread's amplitudes (C(x) and
+    // x along one Gray walk), warp minimum, shared-memory minimum per CTA
+    const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
+    unsigned long long kmin = ~0ull, kmax = ~0ull;
+    const int c_top = P.ncost - 1;
+    auto key = [&](int c, uint64_t x) {
+      const unsigned long long a = (unsigned long long)(c - P.c_lo) << 34 | x;
+      const unsigned long long b = (unsigned long long)(c_top - (c - P.c_lo)) << 34 | x;
+      kmin = a < kmin ? a : kmin;
+      kmax = b < kmax ? b : kmax;
+    };
+    if (stream) {
+      gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t x) { key(__ldcg(A.diag + x), x); });
+    } else {
+      RoundCost<R, WB> rc;
+      rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
+      int lin = rc.kappa;
+      uint64_t x = geo.gb;
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        const int j = k ^ (k >> 1);
+        if (k) {
+          const int b = ctz_c(k);
+          lin += (j >> b & 1) ? rc.e[b] : -rc.e[b];
+          x ^= geo.gstr[b];
+        }
+        key(lin + (op.cost ? P.cpc[j] : P.cpr[j]), x);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmin, o);
+      const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmax, o);
+      kmin = a < kmin ? a : kmin;
+      kmax = b < kmax ? b : kmax;
+    }
+    if (lane == 0) {
+      atomicMin(ext_s, kmin);
+      atomicMin(ext_s + 1, kmax);
+    }
   }
 
   auto mixer = [&](uint8_t mask, Real tau, Real alpha) {
@@ -530,7 +578,7 @@ template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t... R
 __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tile, int* tconst,
                                          const typename Cx<Real>::T* phase, double* wacc,
-                                         uint32_t* tcount = nullptr) {
+                                         uint32_t* tcount = nullptr, unsigned long long* ext_s = nullptr) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -586,7 +634,8 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         auto run = [&](auto sigc) {
           constexpr uint32_t S = decltype(sigc)::value;
           if constexpr ((S >> 2 & 3u) == SRC_SMEM_D) __syncthreads();
-          fwd_round<Real, R, WB, FAST, CC, S>(P, A, sp, sp.rd[r], tile, gbase, gpar, tc, phase, lane, warp, wacc, v);
+          fwd_round<Real, R, WB, FAST, CC, S>(P, A, sp, sp.rd[r], tile, gbase, gpar, tc, phase, lane, warp, wacc, v,
+                                              ext_s);
           ++r;
         };
         (run(std::integral_constant<uint32_t, RS>{}), ...);
@@ -595,7 +644,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, gpar, tc, phase, lane, warp, wacc, v);
+          fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, gpar, tc, phase, lane, warp, wacc, v, ext_s);
         }
         red_last = sp.rd[sp.nrounds - 1].reduce != 0;
       }
@@ -638,9 +687,18 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
   wacc[2 * tid] = 0.0;
   wacc[2 * tid + 1] = 0.0;
 
+  // exhaustive extremes (optional): this CTA's minimum keys
+  __shared__ unsigned long long ext_s[2];
+  if (tid < 2) ext_s[tid] = ~0ull;  // published by the first tile's barrier
+
   uint32_t tcount = 0;
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount);
+    fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount, ext_s);
+
+  if (CC && A.ext_keys) {
+    __syncthreads();
+    if (tid < 2) atomicMin(A.ext_keys + tid, ext_s[tid]);
+  }
 
   if (A.partial) {
     __syncthreads();

@@ -345,3 +345,21 @@ def test_specialised_kernels_bitwise(n, p, order, monkeypatch):
     (a, ea, sa), (b, eb, sb) = outs
     assert np.array_equal(a.view(np.uint64), b.view(np.uint64))
     assert ea == eb and np.array_equal(sa, sb)
+
+
+@pytest.mark.parametrize("n,kind,prec", [(13, "complete", "c64"), (17, "signed", "c64"), (20, "sparse", "c128"),
+                                         (23, "complete", "c64")])
+def test_extremes_from_first_pass(n, kind, prec):
+    # recompute mode takes C_min / C_max and their smallest indices from the
+    # run's |+> pass; they equal the exhaustive kernel's (asked before a run)
+    # and the oracle's
+    u, v, w = graph(kind, n, 700 + n)
+    with sim(n, u, v, w, S, prec) as s:
+        before = s.extremes()
+    with sim(n, u, v, w, S, prec) as s:
+        s.run(2, 0.6, 0.3)
+        after = s.extremes()
+    ref = oracle.cut_values(n, u, v, w)
+    cmin, cmax, amin, amax = oracle.extremes(n, ref)
+    for ext in (before, after):
+        assert (ext["c_min"], ext["c_max"], ext["argmin"], ext["argmax"]) == (cmin, cmax, amin, amax)
