@@ -373,9 +373,12 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
 
   if (CC && init && A.ext_keys && (op.cost || op.reduce)) {
     // exhaustive extremes: packed keys of this thread's amplitudes (C(x) and
-    // x along one Gray walk), warp minimum, shared-memory minimum per CTA
+    // x along one Gray walk), warp minimum, shared-memory minimum per CTA.
+    // C(x) = C(~x), so the smallest index of every value has bit n-1 clear:
+    // a thread whose amplitudes all have it set skips the scan.
     const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
     unsigned long long kmin = ~0ull, kmax = ~0ull;
+    const bool upper = (geo.gb >> (P.n - 1) & 1ull) != 0;
     const int c_top = P.ncost - 1;
     auto key = [&](int c, uint64_t x) {
       const unsigned long long a = (unsigned long long)(c - P.c_lo) << 34 | x;
@@ -383,7 +386,8 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       kmin = a < kmin ? a : kmin;
       kmax = b < kmax ? b : kmax;
     };
-    if (stream) {
+    if (upper) {
+    } else if (stream) {
       gray_walk<R>(geo.gb, geo.gstr, [&](int j, uint64_t x) { key(__ldcg(A.diag + x), x); });
     } else {
       RoundCost<R, WB> rc;
