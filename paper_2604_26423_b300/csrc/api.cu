@@ -158,7 +158,7 @@ struct ProfScope {
   }
 };
 
-// Forward tile shape (complex64 only; complex128 always uses 5x3):
+// Forward tile shape of complex64 (complex128: see the branch below):
 //   0 "5x3": 2^5 registers x 8 warps, T = 13, 2 CTAs per SM
 //   1 "4x4": 2^4 registers x 16 warps, T = 13
 //   2 "5x2": 2^5 registers x 4 warps, T = 12, 4 CTAs per SM
@@ -166,9 +166,17 @@ struct ProfScope {
 //      tiles in flight per SM keep HBM busier than two larger ones)
 // selected by QAOA_FWD_SHAPE.
 constexpr int kFwdShapeC64 = 3;
+constexpr int kFwdShapeC128 = 3;  // measured 6% faster than 5x3 at K_32 (FP64-bound)
 constexpr int kSmallMaxQubits = 12;  // n <= 12: whole circuit in one CTA (small_circuit_kernel)
 int fwd_shape_id(int prec) {
-  if (prec != QAOA_C64) return 0;
+  if (prec != QAOA_C64) {
+    // complex128: 5x3 (one CTA per SM, phase table in shared memory) or 4x3
+    // (two CTAs per SM, phase table read through L1)
+    const char* e = getenv("QAOA_FWD_SHAPE_C128");
+    if (e && strcmp(e, "4x3") == 0) return 3;
+    if (e && strcmp(e, "5x3") == 0) return 0;
+    return kFwdShapeC128;
+  }
   const char* e = getenv("QAOA_FWD_SHAPE");
   if (!e) return kFwdShapeC64;
   if (strcmp(e, "5x3") == 0) return 0;
@@ -375,8 +383,12 @@ int blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
 template <bool FAST, bool CC>
 int pass_dispatch(qaoa_ctx* c, int shape, bool launch, const PassDev& pd, const PassArgs& pa, size_t smem, int grid,
                   int* bps) {
-  if (c->prec == QAOA_C128)
+  if (c->prec == QAOA_C128) {
+    if (shape == 3)
+      return launch ? launch_pass<double, FAST, CC, 4, 3>(c, pd, pa, smem, grid)
+                    : blocks_per_sm<double, FAST, CC, 4, 3>(c, smem, bps);
     return launch ? launch_pass<double, FAST, CC>(c, pd, pa, smem, grid) : blocks_per_sm<double, FAST, CC>(c, smem, bps);
+  }
   if (shape == 1)
     return launch ? launch_pass<float, FAST, CC, 4, 4>(c, pd, pa, smem, grid)
                   : blocks_per_sm<float, FAST, CC, 4, 4>(c, smem, bps);
@@ -464,7 +476,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
   CUDA_TRY(c, cudaGetDevice(&dev));
   CUDA_TRY(c, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   // complex64 kernels compute the phase (phase_turns); complex128 reads the table
-  const bool tab_smem = c->prec == QAOA_C128 && with_tab + 1024 <= (size_t)max_smem;
+  const bool tab_smem = c->prec == QAOA_C128 && fwd_shape_id(c->prec) == 0 && with_tab + 1024 <= (size_t)max_smem;
   const size_t smem = tab_smem ? with_tab : base_smem;
 
   // build every pass descriptor (and its cost tables) before launching

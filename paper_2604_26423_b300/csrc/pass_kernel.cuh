@@ -717,7 +717,7 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
 
 // Generic forward pass: rounds decoded from the descriptor at run time.
 template <typename Real, int R, int WB, bool FAST, bool CC>
-__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : 2) : 1)
+__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : 2) : (R + WB <= 7 ? 2 : 1))
 fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   fwd_pass_body<Real, R, WB, FAST, CC>(P, A);
 }
