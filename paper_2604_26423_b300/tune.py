@@ -20,7 +20,8 @@ import os
 
 _cache: dict = {}
 
-# tile shape of the complex64 forward kernel: 2^R registers x 2^WB warps
+# tile shape of the forward kernel: 2^R registers x 2^WB warps (complex128:
+# 4x3 or 5x3)
 FWD_SHAPES = {"5x3": "5x3", "4x4": "4x4", "5x2": "5x2", "4x3": "4x3"}
 # largest super-tile (index bits kept together through L2 by one CTA)
 SUPER_TILES = (12, 13, 14, 15)
@@ -56,7 +57,7 @@ def forward_candidates(n: int, precision: str = "c64", modes=("recompute", "stre
     """Configurations to time for one instance: cost mode x tile shape x super-tile bits x group order x
     floating lane bits."""
     if shapes is None:
-        shapes = tuple(FWD_SHAPES) if precision == "c64" else ("5x3",)
+        shapes = tuple(FWD_SHAPES) if precision == "c64" else ("4x3", "5x3")
     out = []
     for mode, shape, st, order, fl in itertools.product(modes, shapes, super_tiles, orders, float_lanes):
         if st > n:
@@ -67,8 +68,10 @@ def forward_candidates(n: int, precision: str = "c64", modes=("recompute", "stre
 
 def config_env(cfg: dict) -> dict:
     """Environment settings that select a forward configuration in the library."""
-    return {"QAOA_FWD_SHAPE": FWD_SHAPES[cfg["shape"]], "QAOA_SMAX": cfg["super_tile"],
-            "QAOA_GROUP_ORDER": cfg.get("order", "last"), "QAOA_FLOAT_LANES": int(cfg.get("float_lanes", 1))}
+    return {"QAOA_FWD_SHAPE": FWD_SHAPES[cfg["shape"]],
+            "QAOA_FWD_SHAPE_C128": cfg["shape"] if cfg["shape"] in ("4x3", "5x3") else None,
+            "QAOA_SMAX": cfg["super_tile"], "QAOA_GROUP_ORDER": cfg.get("order", "last"),
+            "QAOA_FLOAT_LANES": int(cfg.get("float_lanes", 1))}
 
 
 def _time_ms(fn, stream, reps: int) -> float:
