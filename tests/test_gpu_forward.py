@@ -347,12 +347,15 @@ def test_specialised_kernels_bitwise(n, p, order, monkeypatch):
     assert ea == eb and np.array_equal(sa, sb)
 
 
-@pytest.mark.parametrize("n,kind,prec", [(13, "complete", "c64"), (17, "signed", "c64"), (20, "sparse", "c128"),
-                                         (23, "complete", "c64")])
-def test_extremes_from_first_pass(n, kind, prec):
+@pytest.mark.parametrize("n,kind,prec,smax", [(13, "complete", "c64", None), (17, "signed", "c64", None),
+                                              (20, "sparse", "c128", None), (23, "complete", "c64", None),
+                                              (21, "signed", "c64", "14")])
+def test_extremes_from_first_pass(n, kind, prec, smax, monkeypatch):
     # recompute mode takes C_min / C_max and their smallest indices from the
-    # run's |+> pass; they equal the exhaustive kernel's (asked before a run)
-    # and the oracle's
+    # run's |+> pass (also with super-tiles of several tiles); they equal the
+    # exhaustive kernel's (asked before a run) and the oracle's
+    if smax:
+        monkeypatch.setenv("QAOA_SMAX", smax)
     u, v, w = graph(kind, n, 700 + n)
     with sim(n, u, v, w, S, prec) as s:
         before = s.extremes()
