@@ -370,7 +370,8 @@ def run_gpu(args):
     try:
         with open(PROFILE_JSON) as f:
             pj = json.load(f)
-        if pj.get("kernel_hash") == kernel_hash():
+        # the counters were scaled to the K_33 recompute-mode step: other workloads get null
+        if pj.get("kernel_hash") == kernel_hash() and nq == N_QUBITS and args.cost_mode == "recompute":
             traffic = pj.get("dram_bytes_per_launch_n33")
     except Exception:
         pass
@@ -380,7 +381,7 @@ def run_gpu(args):
         "metric": metric, "value": layers / (ms * 1e-3), "unit": "layers/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 pairs), fp64 reductions",
-        "data": "synthetic: SplitMix64 K_33 weights in {1..10}",
+        "data": f"synthetic: SplitMix64 K_{nq} weights in {{1..10}}",
         "config": {"workload": f"LR-QAOA K_{nq} weighted MaxCut, complex64 ({(8 << nq) >> 20} MiB state), p=3, "
                                "dgamma=0.6, dbeta=0.3, <C>, r and 4096 shots per step",
                    "n": nq, "p": P, "precision": "complex64", "cost_mode": args.cost_mode,
