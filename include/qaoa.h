@@ -135,7 +135,13 @@ int qaoa_sample(qaoa_ctx *ctx, int shots, const double *uniforms, uint64_t seed,
  *   g_gamma[k] = 2 Re <lambda| -i s H_C |psi>     (at layer k's cost phase)
  * and the chain rule d<C>/d dgamma = sum_k (k+1)/p g_gamma[k],
  * d<C>/d dbeta = sum_k (1 - k/p) g_beta[k]. Holds two state vectors (psi in
- * state_dev, lambda in the aux buffer). Any output may be NULL; g_gamma and
+ * state_dev, lambda in the aux buffer). When the adjoint's passes retrace the
+ * forward's and half of the free device memory holds (passes - 1) more states,
+ * the forward instead keeps every pass's output in library-owned device memory
+ * (held until qaoa_free; reused by later calls) and the adjoint reads psi from
+ * it rather than writing the uncomputed psi back: one state write fewer per
+ * adjoint pass. QAOA_GRAD_CHECKPOINT=0 in the environment turns this off.
+ * Any output may be NULL; g_gamma and
  * g_beta hold p doubles; exp_c receives <C> = <psi_p|lambda> (taken in the
  * first adjoint pass). Leaves the context without a prepared state or result
  * (the walk back ends near |+>), so call qaoa_run again before qaoa_sample or

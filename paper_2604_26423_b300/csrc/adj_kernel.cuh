@@ -23,6 +23,8 @@ namespace qaoa {
 
 struct AdjArgs {
   void* psi;              // 2^n amplitudes (state)
+  int psi_store;          // 1: write the uncomputed psi back; 0: psi is read from a
+                          // stored forward state and only lambda is written
   void* lam;              // 2^n amplitudes (adjoint vector)
   const int32_t* diag;    // int32 C(x) (stream mode) or nullptr
   const void* phase;      // phase table of the cost layer (ncost entries)
@@ -300,15 +302,18 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
 
   if (op.dstg) {
     if (sp.store) {
+      const Geo geo(sp, rd, gbase, lane, warp, A.ctabs);
+      if (A.psi_store) {
+        if (FAST) {
+#pragma unroll
+          for (int j = 0; j < NA; ++j) { v[j].x *= sc; v[j].y *= sc; }
+        }
+        gray_ptr_walk<R>(gpsi, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
+      }
       if (FAST) {
 #pragma unroll
-        for (int j = 0; j < NA; ++j) {
-          v[j].x *= sc; v[j].y *= sc;
-          l[j].x *= sc; l[j].y *= sc;
-        }
+        for (int j = 0; j < NA; ++j) { l[j].x *= sc; l[j].y *= sc; }
       }
-      const Geo geo(sp, rd, gbase, lane, warp, A.ctabs);
-      gray_ptr_walk<R>(gpsi, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
       gray_ptr_walk<R>(glam, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, l[j]); });
     }
   } else {

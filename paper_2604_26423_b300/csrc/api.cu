@@ -83,6 +83,7 @@ struct qaoa_ctx {
   DevBuf d_wmat, d_ctabs, d_phase, d_partial, d_result, d_ext, d_ext_part, d_ext_keys;
   DevBuf d_sums, d_pre, d_pre2, d_shots, d_uni, d_ang;
   DevBuf d_lambda, d_gacc;                                            // adjoint vector (if no aux), per-pass sums
+  DevBuf d_ckpt;                                                      // the gradient's stored forward states
   TableStore tabs;                                                     // host copy of all cost tables
   std::map<std::vector<int8_t>, DevBuf> tct_tabs;                     // per-tile constant tables by sub-pass layout
   size_t tct_bytes = 0;
@@ -318,8 +319,6 @@ int group_order() {
   return o | float_lanes_flag();
 }
 
-// group orders of the gradient's forward and adjoint plans (QAOA_GRAD_ORDER
-// overrides both)
 // Specialised pass kernels (spec.h; QAOA_SPEC=0 selects the generic ones).
 bool spec_enabled() {
   const char* e = getenv("QAOA_SPEC");
@@ -333,6 +332,8 @@ bool adj_prefetch() {
   return e && strcmp(e, "1") == 0;
 }
 
+// group orders of the gradient's forward and adjoint plans (QAOA_GRAD_ORDER
+// overrides both)
 int grad_base_order() {
   const char* e = getenv("QAOA_GRAD_ORDER");
   if (e && strcmp(e, "last") == 0) return ORDER_LOW_LAST;
@@ -341,6 +342,12 @@ int grad_base_order() {
 }
 int grad_fwd_order() { return grad_base_order() | float_lanes_flag(); }
 int grad_bwd_order() { return grad_base_order(); }
+
+// Stored forward states in the gradient (QAOA_GRAD_CHECKPOINT=0 disables).
+bool grad_checkpoint() {
+  const char* e = getenv("QAOA_GRAD_CHECKPOINT");
+  return !(e && strcmp(e, "0") == 0);
+}
 
 int smax_fwd(int T) {
   const char* e = getenv("QAOA_SMAX");
@@ -443,8 +450,11 @@ int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
 }
 
 // reduce = false: the final pass skips <C> and norm (the gradient takes <C>
-// from the adjoint's first pass instead).
-int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int order, bool reduce = true) {
+// from the adjoint's first pass instead). outs: null (every pass in place on
+// the state) or one output buffer per pass of the plan, the last being the
+// state; pass k then reads outs[k-1] and writes outs[k].
+int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int order, bool reduce = true,
+                void* const* outs = nullptr) {
   const int n = c->n;
   const TileShape sh = fwd_shape(c->prec);
   const int T = sh.T();
@@ -524,7 +534,8 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
     const PassDev& pd = pds[pi];
     const bool fast = fasts[pi];
     PassArgs pa;
-    pa.state = c->state;
+    pa.state = outs && pi > 0 ? outs[pi - 1] : c->state;
+    pa.out = outs ? outs[pi] : c->state;
     pa.diag = stream ? (const int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n))) : nullptr;
     pa.phase = pp.layer_c >= 0 ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_c) * nc * ab) : nullptr;
     pa.wmat = (const int32_t*)c->d_wmat.p;
@@ -723,19 +734,55 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     c->sums_ready = false;
     return QAOA_OK;
   }
-  // forward: psi_p and <C>
-  // the gradient's forward run samples nothing: the plan without the
-  // block-sum constraint keeps the fused passes on the small groups
-  int rc = run_forward(c, p, gamma, beta, grad_fwd_order(), false);
-  if (rc) return rc;
-  void* lam = lambda_ptr(c);
-  if (!lam) return c->set_err(QAOA_ENOMEM, "allocation of the adjoint vector failed");
   const Plan* plan;
   try {
     plan = get_bplan(c, p, grad_bwd_order());
   } catch (std::exception& ex) {
     return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
   }
+  // the gradient's forward run samples nothing: the plan without the
+  // block-sum constraint keeps the fused passes on the small groups
+  int fwd_order = grad_fwd_order();
+  // stored forward states: when the adjoint plan retraces the forward plan
+  // pass by pass and half of the free device memory holds one state per
+  // forward pass, the forward writes each pass's output to its own buffer and
+  // adjoint pass j reads psi at its start from the output of forward pass
+  // P-1-j instead of uncomputing it, which saves one state write per adjoint
+  // pass (the in-tile uncompute of psi for the gradient terms stays)
+  std::vector<void*> outs;
+  if (grad_checkpoint() && n >= std::max(fwd_shape(c->prec).T(), kSmallMaxQubits + 1)) {
+    try {
+      const Plan* fp = get_plan(c, p, fwd_order);
+      if (!plans_mirror(*fp, *plan) && fwd_order != grad_bwd_order()) {
+        fwd_order = grad_bwd_order();
+        fp = get_plan(c, p, fwd_order);
+      }
+      if (plans_mirror(*fp, *plan)) {
+        const size_t sb = qaoa_state_bytes(n, c->prec);
+        const size_t np = fp->passes.size();
+        const size_t need = (np - 1) * sb;
+        size_t fr = 0, tot = 0;
+        bool ok = c->d_ckpt.p && c->d_ckpt.bytes >= need;
+        if (!ok && cudaMemGetInfo(&fr, &tot) == cudaSuccess && need <= fr / 2) {
+          ok = c->d_ckpt.ensure(need) == cudaSuccess;
+          if (!ok) cudaGetLastError();  // out of memory: in-place forward, psi uncomputed
+        }
+        if (ok) {
+          for (size_t k = 0; k + 1 < np; ++k) outs.push_back((char*)c->d_ckpt.p + k * sb);
+          outs.push_back(c->state);
+        }
+      } else {
+        fwd_order = grad_fwd_order();
+      }
+    } catch (std::exception& ex) {
+      return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
+    }
+  }
+  // forward: psi_p (and the stored states)
+  int rc = run_forward(c, p, gamma, beta, fwd_order, false, outs.empty() ? nullptr : outs.data());
+  if (rc) return rc;
+  void* lam = lambda_ptr(c);
+  if (!lam) return c->set_err(QAOA_ENOMEM, "allocation of the adjoint vector failed");
   const bool stream = c->cost_mode == QAOA_COST_STREAM;
   const long long nc = c->c_hi - c->c_lo + 1;
   const size_t tile_amps = ab == 8 ? padded_size<8>(T) : padded_size<16>(T);
@@ -785,7 +832,8 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     const PassDev& pd = pds[pi];
     const bool fast = fasts[pi];
     AdjArgs aa;
-    aa.psi = c->state;
+    aa.psi = outs.empty() ? c->state : outs[npass - 1 - pi];
+    aa.psi_store = outs.empty() ? 1 : 0;
     aa.lam = lam;
     aa.diag = stream ? (const int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n))) : nullptr;
     aa.phase = pp.layer_c >= 0 ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_c) * nc * ab) : nullptr;
@@ -813,9 +861,10 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
     {
       // algorithmic bytes: both vectors read (psi only when lambda is created)
-      // and both written (nothing in the final pass)
+      // and both written (lambda only with stored forward states; nothing in
+      // the final pass)
       const double N = double(1ull << n);
-      double bytes = (pp.linit ? 1.0 : 2.0) * N * ab + (pp.store ? 2.0 * N * ab : 0.0);
+      double bytes = (pp.linit ? 1.0 : 2.0) * N * ab + (pp.store ? (aa.psi_store ? 2.0 : 1.0) * N * ab : 0.0);
       if (stream)
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 1, bytes);
@@ -847,7 +896,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   if (g_gamma) memcpy(g_gamma, gg.data(), sizeof(double) * p);
   if (g_beta) memcpy(g_beta, gbt.data(), sizeof(double) * p);
   if (exp_c) *exp_c = h[3];  // <psi_p|C psi_p> from the first adjoint pass
-  c->state_ready = false;  // psi has been walked back towards |+>
+  c->state_ready = false;  // psi walked back towards |+> (or psi_p, with stored forward states)
   c->sums_ready = false;
   return QAOA_OK;
 }
@@ -1216,7 +1265,7 @@ void qaoa_free(qaoa_ctx* c) {
   c->aux_own.release();
   DevBuf* bufs[] = {&c->d_wmat, &c->d_ctabs, &c->d_phase, &c->d_partial, &c->d_result, &c->d_ext,
                     &c->d_ext_part, &c->d_ext_keys, &c->d_sums, &c->d_pre, &c->d_pre2, &c->d_shots, &c->d_uni, &c->d_ang,
-                    &c->d_lambda, &c->d_gacc};
+                    &c->d_lambda, &c->d_gacc, &c->d_ckpt};
   for (DevBuf* b : bufs) b->release();
   for (auto& kv : c->tct_tabs) kv.second.release();
   for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }

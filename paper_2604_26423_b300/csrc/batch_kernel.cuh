@@ -351,6 +351,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
   if constexpr (!ADJ) {
     PassArgs A;
     A.state = I.psi;
+    A.out = I.psi;
     A.diag = nullptr;
     A.phase = phase;
     A.wmat = I.wmat;
@@ -378,6 +379,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
   } else {
     AdjArgs A;
     A.psi = I.psi;
+    A.psi_store = 1;
     A.lam = I.lam;
     A.diag = nullptr;
     A.phase = phase;

@@ -28,7 +28,9 @@ enum : uint8_t { SRC_SMEM_D = 0, SRC_GLOBAL_D = 1, SRC_INIT_D = 2 };
 enum : uint8_t { DST_SMEM_D = 0, DST_GLOBAL_D = 1 };
 
 struct PassArgs {
-  void* state;            // 2^n amplitudes, interleaved (re, im)
+  void* state;            // 2^n amplitudes, interleaved (re, im): the pass's input
+  void* out;              // where the pass writes its output: `state` (in place) or
+                          // another 2^n buffer (the gradient's stored forward states)
   const int32_t* diag;    // int32 C(x) for all x (stream mode) or nullptr
   const void* phase;      // phase table of the cost layer: ncost complex entries
   const int32_t* wmat;    // n x n symmetric integer weights
@@ -347,7 +349,7 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   // complex64: swapped storage (packed butterflies) and the cost phase from
   // 32-bit turn increments; complex128: plain storage, phase table
   constexpr bool kSw = sizeof(Real) == 4;
-  C2* gstate = reinterpret_cast<C2*>(A.state);
+  C2* gstate = reinterpret_cast<C2*>(A.out);
   const bool stream = A.diag != nullptr;
   const RoundOps<SIG> op(rd);
   const bool init = CC && op.src == SRC_INIT_D;
@@ -605,7 +607,8 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       else load0 = sp.rd[0].src == SRC_GLOBAL_D;
       if (load0) {
         const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
-        const C2* gs = reinterpret_cast<const C2*>(A.state);
+        // later sub-passes read what the earlier ones wrote
+        const C2* gs = reinterpret_cast<const C2*>(s == 0 ? A.state : A.out);
         if (A.l2hint) {
           const uint64_t pol = l2_policy_evict_first();
           gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = ld_hint(q, pol); });

@@ -563,6 +563,45 @@ std::string validate(const Plan& plan) {
   return "";
 }
 
+namespace {
+
+// The gates a pass applies: (layer, qubit) of every mixer and (layer, -1) of
+// the cost phase, sorted.
+std::vector<std::pair<int, int>> pass_gates(const Plan& pl, const PassPlan& pp) {
+  std::vector<std::pair<int, int>> g;
+  for (const SubPassPlan& sp : pp.subs) {
+    uint32_t am = 0, bm = 0;
+    bool c = false;
+    for (const RoundPlan& rp : sp.rounds) {
+      for (int i = 0; i < pl.shape.R; ++i) {
+        if (rp.mixA >> i & 1u) am |= 1u << rp.reg[i];
+        if (rp.mixB >> i & 1u) bm |= 1u << rp.reg[i];
+      }
+      c |= rp.cost != 0;
+    }
+    for (int j = 0; j < sp.T; ++j) {
+      if (am >> j & 1u) g.emplace_back(pp.layer_a, sp.pos[j]);
+      if (bm >> j & 1u) g.emplace_back(pp.layer_b, sp.pos[j]);
+    }
+    if (c) g.emplace_back(pp.layer_c, -1);
+  }
+  std::sort(g.begin(), g.end());
+  return g;
+}
+
+}  // namespace
+
+bool plans_mirror(const Plan& fwd, const Plan& bwd) {
+  const size_t np = fwd.passes.size();
+  if (fwd.backward || !bwd.backward || fwd.n != bwd.n || fwd.p != bwd.p || bwd.passes.size() != np) return false;
+  for (size_t j = 0; j < np; ++j) {
+    const PassPlan& b = bwd.passes[j];
+    if (b.subs.size() != 1) return false;
+    if (pass_gates(bwd, b) != pass_gates(fwd, fwd.passes[np - 1 - j])) return false;
+  }
+  return true;
+}
+
 std::string Plan::describe() const {
   std::ostringstream os;
   os << "n=" << n << " p=" << p << " S=" << S << " T=" << shape.T() << " R=" << shape.R

@@ -131,6 +131,14 @@ std::string validate(const Plan& plan);
 std::string validate_rounds(const TileShape& shape, const std::vector<RoundPlan>& rounds,
                             uint32_t a_bits, bool cost, uint32_t b_bits, bool reduce);
 
+// True when the adjoint plan `bwd` retraces the forward plan `fwd` pass by
+// pass: equal pass counts, one sub-pass in every adjoint pass, and adjoint pass
+// j applying the inverses of exactly the gates of forward pass P-1-j (the same
+// mixer qubits of the same layers and the same cost layer). The state at the
+// start of adjoint pass j is then the forward's output of pass P-1-j, so the
+// adjoint can read it from a stored copy instead of uncomputing it.
+bool plans_mirror(const Plan& fwd, const Plan& bwd);
+
 // Compile-time signature of a round (the kernels' specialised instantiations,
 // kSigValid set): bits 0-1 layout, 2-3 source, 4 stores to global memory,
 // 5 cost phase, 6 reduction, 7 lambda creation, 8-12 mixer A mask, 13-17

@@ -208,3 +208,54 @@ def test_adjoint_tile_prefetch_identical(monkeypatch):
             res.append(s.grad(p, 0.6, 0.3))
     a, b = res
     assert np.array_equal(a["g_gamma"], b["g_gamma"]) and np.array_equal(a["g_beta"], b["g_beta"])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,p,prec", [(14, 3, "c128"), (21, 1, "c64"), (22, 4, "c64"), (20, 3, "c128"),
+                                      (29, 2, "c64")])
+def test_grad_stored_forward_states(n, p, prec, monkeypatch):
+    # the adjoint reading psi from the forward's stored pass outputs gives the
+    # gradients of the adjoint that uncomputes psi, up to rounding, with one
+    # state write fewer per adjoint pass (the algorithmic bytes show which
+    # path ran); n = 21, p = 1 and n = 29 take the forward plan without
+    # floating lane bits so that the adjoint retraces it
+    u, v, w = inputs.complete_graph(n, 990 + n)
+    res, adj_bytes = [], []
+    for ck in ("1", "0"):
+        monkeypatch.setenv("QAOA_GRAD_CHECKPOINT", ck)
+        with sim(n, u, v, w, S, prec, with_grad=True) as s:
+            s.profile(True)
+            res.append(s.grad(p, 0.6, 0.3))
+            adj_bytes.append(s.profile_read("adjoint")["bytes"])
+    a, b = res
+    tol = 1e-11 if prec == "c128" else 2e-4
+    scale = max(np.max(np.abs(b["g_gamma"])), np.max(np.abs(b["g_beta"])))
+    assert np.max(np.abs(a["g_gamma"] - b["g_gamma"])) <= tol * scale
+    assert np.max(np.abs(a["g_beta"] - b["g_beta"])) <= tol * scale
+    assert abs(a["exp_c"] - b["exp_c"]) <= tol * abs(b["exp_c"])
+    # passes - 1 adjoint passes store lambda only (the last one stores nothing)
+    sb = (8 if prec == "c64" else 16) << n
+    npass = round((adj_bytes[1] - adj_bytes[0]) / sb) + 1
+    assert npass >= 2 and adj_bytes[1] - adj_bytes[0] == (npass - 1) * sb
+
+
+@pytest.mark.gpu
+def test_grad_stored_states_vs_oracle_fd():
+    # complex128 with stored forward states against the oracle's central
+    # differences (the default path when memory allows)
+    n, p = 16, 4
+    u, v, w = inputs.complete_graph(n, 1016)
+    g, b = oracle.lr_schedule(p, 0.6, 0.3)
+    fd_g, fd_b = oracle.grad_fd(n, u, v, w, S, g, b)
+    with sim(n, u, v, w, S, "c128", with_grad=True) as s:
+        s.profile(True)
+        out = s.grad_angles(g, b)
+        by = s.profile_read("adjoint")["bytes"]
+    scale = max(np.max(np.abs(fd_g)), np.max(np.abs(fd_b)))
+    assert np.max(np.abs(out["g_gamma"] - fd_g)) <= 1e-6 * scale
+    assert np.max(np.abs(out["g_beta"] - fd_b)) <= 1e-6 * scale
+    # first pass reads psi, writes lambda; middle passes read both, write lambda;
+    # the last reads both: 2 + 3 (P - 2) + 2 states
+    sb = 16 << n
+    npass = (by / sb - 4) / 3 + 2
+    assert npass == round(npass) and npass >= 3
