@@ -192,19 +192,20 @@ def cpu_baseline(budget_s: float = 12.0):
 
 # ------------------------------------------------------------------ GPU arm
 def grad_ratio(args, stream, reps: int = 3):
-    """Adjoint gradient time over forward time on K_28, complex64, p = 10."""
+    """Adjoint gradient time over forward time (by default K_28, complex64, p = 10)."""
     import torch
     from paper_2604_26423_b300 import inputs
     from paper_2604_26423_b300.qaoa import Simulator
 
-    u, v, w = inputs.complete_graph(GRAD_N, SEED)
-    with Simulator(GRAD_N, u, v, w, SCALE, "c64", cost_mode=args.cost_mode, with_grad=True) as s:
+    gn, gp = args.grad_n, args.grad_p
+    u, v, w = inputs.complete_graph(gn, SEED)
+    with Simulator(gn, u, v, w, SCALE, "c64", cost_mode=args.cost_mode, with_grad=True) as s:
         def fwd():
-            s.run(GRAD_P, GRAD_DGAMMA, GRAD_DBETA)
+            s.run(gp, GRAD_DGAMMA, GRAD_DBETA)
             return s.expect()
 
         def bwd():
-            return s.grad(GRAD_P, GRAD_DGAMMA, GRAD_DBETA)
+            return s.grad(gp, GRAD_DGAMMA, GRAD_DBETA)
 
         times = {}
         for name, f in (("forward", fwd), ("grad", bwd)):
@@ -219,7 +220,7 @@ def grad_ratio(args, stream, reps: int = 3):
             e1.record(stream)
             torch.cuda.synchronize()
             times[name] = e0.elapsed_time(e1) / reps
-        return {"workload": f"K_{GRAD_N} complex64, p={GRAD_P}, dgamma={GRAD_DGAMMA}, dbeta={GRAD_DBETA}",
+        return {"workload": f"K_{gn} complex64, p={gp}, dgamma={GRAD_DGAMMA}, dbeta={GRAD_DBETA}",
                 "forward_ms": times["forward"], "grad_ms": times["grad"],
                 "ratio": times["grad"] / times["forward"], "exp_c": r["exp_c"],
                 "d_dgamma": r["d_dgamma"], "d_dbeta": r["d_dbeta"]}
@@ -456,6 +457,8 @@ def main(argv=None):
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
+    ap.add_argument("--grad-n", type=int, default=GRAD_N, help="qubits of the gradient leg (profiling)")
+    ap.add_argument("--grad-p", type=int, default=GRAD_P, help="depth of the gradient leg (profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
