@@ -25,6 +25,11 @@ phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
   picked by the autotuner; ``--batch-reps`` replays are timed.
 * ``configs``: qaoa_run + qaoa_expect once each on K_30 (complex128 and
   complex64), K_32 complex128 and K_33 complex64 with the streamed cost diagonal.
+* ``stats``: the sampling methodology of Sec. II-D on the workload's graph and
+  final state: cut values and ratios of 2^26 uniform random bitstrings (the
+  random sampler; kernel time, bitstrings/s), the ratios of the step's 4096
+  shots, the mean of 100 subsample means at 10 and 100 shots for both, and the
+  regime of the first 10 shots.
 * ``--qubits n`` runs the same step on K_n (smaller cases for profiling; the
   JSON line then names that workload).
 * ``cpu_baseline`` / ``--impl reference``: the gate-by-gate complex128 oracle on
@@ -292,6 +297,47 @@ def batch_bench(args, stream):
     return out
 
 
+def stats_bench(sim, shots, stream, pool: int = 1 << 26):
+    """Sampling methodology (Sec. II-D) on the workload's graph and state: cut
+    values and ratios of a pool of uniform random bitstrings (the random
+    sampler, kernel timed with CUDA events), the ratios of the step's shots, the
+    mean of 100 subsample means at 10 and 100 shots for both pools, and the
+    regime of the first 10 shots against the two distributions."""
+    import torch
+    from paper_2604_26423_b300.qaoa import REGIMES, classify_regime, mean_of_means
+
+    sim.sample_cuts(count=1024, seed=1)  # weight planes built, extremes known
+    sim.profile(True)
+    t0 = time.perf_counter()
+    rand = sim.sample_cuts(count=pool, seed=SEED + 2)
+    wall = time.perf_counter() - t0
+    kern = sim.profile_read("sample")
+    sim.profile(False)
+    r_rand = rand["r"]
+    r_shots = sim.sample_cuts(shots)["r"]
+    n = sim.n
+    out = {"random_sampler": {"bitstrings": pool, "kernel_ms": kern["ms"], "wall_ms": wall * 1e3,
+                              "bitstrings_per_s": pool / (kern["ms"] * 1e-3),
+                              "edge_terms_per_s": pool * n * (n - 1) / 2 / (kern["ms"] * 1e-3),
+                              "mean_r": float(r_rand.mean())},
+           "shots": {"count": int(r_shots.numel()), "mean_r": float(r_shots.mean())}}
+    for ns in (10, 100):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mr = mean_of_means(r_rand, ns, 100, seed=ns)
+        mi = mean_of_means(r_shots, ns, 100, seed=ns + 1)
+        t = time.perf_counter() - t0
+        out[f"ns{ns}"] = {"random": {k: mr[k] for k in ("grand_mean", "sigma", "threshold")},
+                          "noiseless": {k: mi[k] for k in ("grand_mean", "sigma", "threshold")},
+                          "ms_both": t * 1e3}
+    r_obs = float(r_shots[:10].mean())
+    m10 = out["ns10"]
+    reg = classify_regime(r_obs, m10["random"]["grand_mean"], m10["random"]["sigma"],
+                          m10["noiseless"]["grand_mean"], m10["noiseless"]["sigma"])
+    out["regime_first_10_shots"] = {"r_obs": r_obs, "regime": REGIMES.get(reg, reg)}
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_2604_26423_b300 import inputs
@@ -339,6 +385,7 @@ def run_gpu(args):
     uh = torch.from_numpy(u).pin_memory().numpy()
     vh = torch.from_numpy(v).pin_memory().numpy()
     wh = torch.from_numpy(w).pin_memory().numpy()
+    stats = None if args.no_stats else stats_bench(sim, shots, stream)
     sim.close()
 
     def e2e_step():
@@ -407,6 +454,8 @@ def run_gpu(args):
         out["batch"] = batch
     if configs is not None:
         out["configs"] = configs
+    if stats is not None:
+        out["stats"] = stats
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     if rank == 0:
@@ -454,6 +503,7 @@ def main(argv=None):
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-stats", action="store_true")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--qubits", type=int, default=N_QUBITS)

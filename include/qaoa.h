@@ -279,6 +279,59 @@ double qaoa_batch_bytes(const qaoa_batch *b);
 const char *qaoa_batch_last_error(const qaoa_batch *b);
 void qaoa_batch_free(qaoa_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Sampling methodology (Sec. II-D): the approximation ratio of individual
+ * bitstrings, the uniform random sampler, the mean of subsample means and the
+ * three performance regimes. Random draws are SplitMix64 stream draws (the
+ * definition given at qaoa_sample).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Cut value C(x) (Sec. II-B) and approximation ratio r(x) = (C(x) - C_min) /
+ * (C_max - C_min) (Eq. r with one bitstring; 1 when C_max = C_min) of `count`
+ * bitstrings on the context's graph. x_dev: device array of `count` indices
+ * < 2^n, or NULL for the random sampler: x_i = the top n bits of draw i of
+ * stream `seed`. Outputs are device arrays of `count` entries, each optional:
+ * x_out_dev (the bitstrings), c_out_dev (int32 C), r_out_dev (double r).
+ * C_min / C_max are those of qaoa_expect (computed first when not known).
+ * Ordered on the context's stream; returns after the kernel finished.
+ * Errors: EINVAL (count < 0, an index >= 2^n), ENOMEM, ECUDA.
+ */
+int qaoa_sample_cuts(qaoa_ctx *ctx, int64_t count, const uint64_t *x_dev, uint64_t seed,
+                     uint64_t *x_out_dev, int32_t *c_out_dev, double *r_out_dev);
+
+/*
+ * Mean of subsample means (Sec. II-D). From the pool r_dev[0..m) (device,
+ * read only), `reps` subsamples of `ns` distinct entries are drawn uniformly
+ * without replacement, each by a partial Fisher-Yates shuffle: step j of
+ * subsample i takes draw k = i*ns + j of stream `seed` and swaps position j
+ * with position j + floor(z_k (m - j) / 2^64); the entry moved to position j
+ * joins the subsample. means_dev[i] (device, reps doubles) = the entries'
+ * FP64 sum in draw order / ns. stats_dev (device, 3 doubles) = {grand mean
+ * <r_bar> (sum of the means in order / reps), sigma (square root of the mean
+ * squared deviation, 1/reps), random threshold <r_bar> + 3 sigma}. No device
+ * memory is allocated. Limits: 1 <= ns <= min(m, 4096), m < 2^32 - 1,
+ * 1 <= reps <= 65535. Asynchronous on `cuda_stream`. Errors: EINVAL, ECUDA.
+ */
+#define QAOA_MOM_MAX_NS 4096
+int qaoa_mean_of_means(const double *r_dev, int64_t m, int ns, int reps, uint64_t seed, double *means_dev,
+                       double *stats_dev, void *cuda_stream);
+
+/*
+ * Performance regime of an observed mean ratio r_obs (Sec. II-D), host only.
+ * QAOA_REGIME_RANDOM when r_obs is within or below the random sampler's
+ * interval (r_obs <= rand_mean + 3 rand_sigma); otherwise, with a noiseless
+ * reference (have_ideal != 0), QAOA_REGIME_NOISE_TOLERANT when r_obs reaches
+ * its interval (r_obs >= ideal_mean - 3 ideal_sigma), else
+ * QAOA_REGIME_TRANSITION; without one, QAOA_REGIME_ABOVE_RANDOM (the result is
+ * statistically meaningful at 99.73% confidence). Returns the regime, or -1
+ * for a NaN or negative sigma.
+ */
+enum { QAOA_REGIME_RANDOM = 0, QAOA_REGIME_TRANSITION = 1, QAOA_REGIME_NOISE_TOLERANT = 2,
+       QAOA_REGIME_ABOVE_RANDOM = 3 };
+int qaoa_classify_regime(double r_obs, double rand_mean, double rand_sigma, int have_ideal, double ideal_mean,
+                         double ideal_sigma);
+
 #ifdef __cplusplus
 }
 #endif

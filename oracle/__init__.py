@@ -19,6 +19,11 @@ Every function names the passage of the paper it follows:
 * ``grad_param_shift`` -- exact two-term shift rule per gate (each gate is
                           exp(-i theta/2 P) with a Pauli product P).
 * ``gate_counts``      -- Sec. II-B, N_2q = p N(N-1)/2 and N_1q = (p+1) N.
+* ``sample_cuts``, ``sample_ratios``, ``random_bitstrings``, ``subsample_indices``,
+  ``mean_of_means``, ``classify_regime`` -- Sec. II-D (sampling methodology):
+  approximation ratio of individual bitstrings, the uniform random sampler,
+  repeated subsampling without replacement, the mean of subsample means with its
+  standard deviation, the random threshold and the three performance regimes.
 
 Pins that tie this oracle to the paper and to mathematics (dense matrix
 exponentials, the uniform-state identity, the closed-form single-layer
@@ -275,3 +280,102 @@ def lr_chain(g_gamma, g_beta):
     p = len(g_gamma)
     k = np.arange(p, dtype=np.float64)
     return float(np.sum((k + 1) / p * np.asarray(g_gamma))), float(np.sum((1 - k / p) * np.asarray(g_beta)))
+
+
+# ------------------------------------------------------------- Sec. II-D
+# The random numbers of the sampling methodology are draws of the SplitMix64
+# stream of ``inputs`` (draw k of stream ``seed``); the CUDA path generates the
+# same draws on the device from the generator's published definition.
+
+def sample_cuts(n: int, u, v, w, xs) -> np.ndarray:
+    """C(x) of each given bitstring, literally sum over edges of w [x_k != x_l] (Sec. II-B)."""
+    xs = [int(x) for x in np.asarray(xs, dtype=np.uint64)]
+    out = np.empty(len(xs), dtype=np.int64)
+    for i, x in enumerate(xs):
+        if x >> n:
+            raise ValueError("bitstring index out of range")
+        out[i] = sum(int(we) for a, b, we in zip(u, v, w) if (x >> int(a) & 1) != (x >> int(b) & 1))
+    return out
+
+
+def sample_ratios(cuts, cmin: int, cmax: int) -> np.ndarray:
+    """Approximation ratio of each sample, (C(x) - C_min) / (C_max - C_min) (Eq. r
+    with a single bitstring in place of the mean; 1 when C_max = C_min)."""
+    cuts = np.asarray(cuts, dtype=np.int64)
+    if cmax == cmin:
+        return np.ones(len(cuts))
+    return np.array([float(c - cmin) / float(cmax - cmin) for c in cuts])
+
+
+def random_bitstrings(n: int, count: int, seed: int) -> np.ndarray:
+    """The random sampler (Sec. II-D): bitstring i is the top n bits of draw i."""
+    from paper_2604_26423_b300 import inputs
+    return inputs.splitmix64(seed, count) >> np.uint64(64 - n)
+
+
+def subsample_indices(m: int, ns: int, reps: int, seed: int) -> np.ndarray:
+    """reps subsets of ns distinct positions of a pool of m samples, each drawn
+    uniformly without replacement (Sec. II-D) by a partial Fisher-Yates shuffle:
+    step j of subset i takes draw k = i*ns + j, swaps position j with position
+    j + floor(z_k (m - j) / 2^64) and keeps the value moved to position j.
+    Returns an (reps, ns) array of pool positions in draw order."""
+    from paper_2604_26423_b300 import inputs
+    if not (1 <= ns <= m):
+        raise ValueError("need 1 <= ns <= m")
+    z = inputs.splitmix64(seed, reps * ns)
+    out = np.empty((reps, ns), dtype=np.int64)
+    for i in range(reps):
+        pool = {}  # positions whose content differs from the identity
+        for j in range(ns):
+            k = j + (int(z[i * ns + j]) * (m - j) >> 64)
+            vj, vk = pool.get(j, j), pool.get(k, k)
+            pool[k] = vj
+            pool[j] = vk
+            out[i, j] = vk
+    return out
+
+
+def mean_of_means(r, ns: int, reps: int, seed: int):
+    """Sec. II-D: the mean ratio of each subsample (summed in draw order), their
+    grand mean <r_bar> and standard deviation sigma (over the reps means, 1/reps
+    normalisation), and the random threshold <r_bar> + 3 sigma."""
+    r = np.asarray(r, dtype=np.float64)
+    idx = subsample_indices(len(r), ns, reps, seed)
+    means = np.empty(reps)
+    for i in range(reps):
+        acc = 0.0
+        for k in idx[i]:
+            acc += float(r[k])
+        means[i] = acc / ns
+    g = 0.0
+    for mu in means:
+        g += float(mu)
+    g /= reps
+    var = 0.0
+    for mu in means:
+        d = float(mu) - g
+        var += d * d
+    sigma = math.sqrt(var / reps)
+    return dict(means=means, grand_mean=g, sigma=sigma, threshold=g + 3.0 * sigma)
+
+
+REGIME_RANDOM, REGIME_TRANSITION, REGIME_NOISE_TOLERANT, REGIME_ABOVE_RANDOM = 0, 1, 2, 3
+
+
+def classify_regime(r_obs: float, rand_mean: float, rand_sigma: float, ideal_mean=None, ideal_sigma=None) -> int:
+    """Sec. II-D: random when r_obs lies within or below the random sampler's 3-sigma
+    interval (not above its threshold); otherwise noise-tolerant when r_obs reaches
+    the noiseless interval (r_obs >= ideal_mean - 3 ideal_sigma), else transition.
+    Without a noiseless reference a result above the threshold is only
+    'statistically meaningful' (REGIME_ABOVE_RANDOM). -1 for a NaN or negative sigma."""
+    if math.isnan(rand_sigma) or rand_sigma < 0:
+        return -1
+    if ideal_mean is not None and (math.isnan(ideal_sigma) or ideal_sigma < 0):
+        return -1
+    if not r_obs > rand_mean + 3.0 * rand_sigma:
+        return REGIME_RANDOM
+    if ideal_mean is None:
+        return REGIME_ABOVE_RANDOM
+    if r_obs >= ideal_mean - 3.0 * ideal_sigma:
+        return REGIME_NOISE_TOLERANT
+    return REGIME_TRANSITION

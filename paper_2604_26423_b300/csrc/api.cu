@@ -25,6 +25,7 @@
 #include "device.cuh"
 #include "pass_kernel.cuh"
 #include "aux_kernels.cuh"
+#include "stats_kernels.cuh"
 #include "small_kernel.cuh"
 #include "adj_kernel.cuh"
 #include "spec.h"
@@ -84,6 +85,8 @@ struct qaoa_ctx {
   DevBuf d_sums, d_pre, d_pre2, d_shots, d_uni, d_ang;
   DevBuf d_lambda, d_gacc;                                            // adjoint vector (if no aux), per-pass sums
   DevBuf d_ckpt;                                                      // the gradient's stored forward states
+  DevBuf d_cutplanes, d_flag;                                         // weight bit planes (qaoa_sample_cuts), error flag
+  int cut_planes = -1;                                                // planes in d_cutplanes (-1: not built)
   TableStore tabs;                                                     // host copy of all cost tables
   std::map<std::vector<int8_t>, DevBuf> tct_tabs;                     // per-tile constant tables by sub-pass layout
   size_t tct_bytes = 0;
@@ -1184,6 +1187,80 @@ int qaoa_sample(qaoa_ctx* c, int shots, const double* uniforms, uint64_t seed, u
   return QAOA_OK;
 }
 
+int qaoa_sample_cuts(qaoa_ctx* c, int64_t count, const uint64_t* x_dev, uint64_t seed, uint64_t* x_out_dev,
+                     int32_t* c_out_dev, double* r_out_dev) {
+  if (!c) return QAOA_EINVAL;
+  if (count < 0) return c->set_err(QAOA_EINVAL, "count must be >= 0");
+  if (count == 0) return QAOA_OK;
+  const int n = c->n;
+  if (c->cut_planes < 0) {
+    // weight bit planes of the upper triangle (j > i), by sign, non-empty only
+    std::vector<unsigned long long> masks;
+    std::vector<long long> coef;
+    for (int sign = 1; sign >= -1; sign -= 2) {
+      for (int t = 0; t < 31; ++t) {
+        std::vector<unsigned long long> pl(n, 0ull);
+        bool any = false;
+        for (int i = 0; i < n; ++i)
+          for (int j = i + 1; j < n; ++j) {
+            const long long wij = c->wmat[size_t(i) * n + j];
+            if (wij * sign > 0 && ((wij * sign) >> t & 1)) {
+              pl[i] |= 1ull << j;
+              any = true;
+            }
+          }
+        if (!any) continue;
+        masks.insert(masks.end(), pl.begin(), pl.end());
+        coef.push_back(sign * (1ll << t));
+      }
+    }
+    const int P = (int)coef.size();
+    if (P > kMaxCutPlanes) return c->set_err(QAOA_EINVAL, "too many weight bit planes");
+    std::vector<unsigned long long> tab(masks);
+    for (long long cf : coef) tab.push_back((unsigned long long)cf);
+    for (int i = 0; i < n; ++i) {
+      long long d = 0;
+      for (int j = 0; j < n; ++j) d += c->wmat[size_t(i) * n + j];
+      tab.push_back((unsigned long long)d);
+    }
+    CUDA_TRY(c, c->d_cutplanes.ensure(tab.size() * 8));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_cutplanes.p, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    c->cut_planes = P;
+  }
+  int rc = ensure_extremes(c);
+  if (rc) return rc;
+  CUDA_TRY(c, c->d_flag.ensure(sizeof(int)));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_flag.p, 0, sizeof(int), c->stream));
+  SampleCutArgs a;
+  a.n = n;
+  a.planes = c->cut_planes;
+  a.tab = (const unsigned long long*)c->d_cutplanes.p;
+  a.count = count;
+  a.x = (const unsigned long long*)x_dev;
+  a.seed = seed;
+  a.c_min = c->ext.vmin;
+  a.c_max = c->ext.vmax;
+  a.x_out = (unsigned long long*)x_out_dev;
+  a.c_out = c_out_dev;
+  a.r_out = r_out_dev;
+  a.bad = (int*)c->d_flag.p;
+  const size_t smem = size_t(a.planes * (n + 1) + n) * 8;
+  const long long want = (long long)c->sms * 8;
+  const int grid = (int)std::max<long long>(1, std::min<long long>(want, (count + 255) / 256));
+  {
+    const double per = (x_dev ? 8.0 : 0.0) + (x_out_dev ? 8.0 : 0.0) + (c_out_dev ? 4.0 : 0.0) + (r_out_dev ? 8.0 : 0.0);
+    ProfScope ps(c, 3, per * double(count));
+    sample_cut_kernel<<<grid, 256, smem, c->stream>>>(a);
+    if (c->prof_on) ++c->nlaunch;
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  int bad = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&bad, c->d_flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (bad) return c->set_err(QAOA_EINVAL, "a bitstring has bits at or above n");
+  return QAOA_OK;
+}
+
 int qaoa_cost_diag(qaoa_ctx* c, int32_t* out_dev) {
   if (!c) return QAOA_EINVAL;
   if (!out_dev) return c->set_err(QAOA_EINVAL, "out_dev is NULL");
@@ -1265,7 +1342,7 @@ void qaoa_free(qaoa_ctx* c) {
   c->aux_own.release();
   DevBuf* bufs[] = {&c->d_wmat, &c->d_ctabs, &c->d_phase, &c->d_partial, &c->d_result, &c->d_ext,
                     &c->d_ext_part, &c->d_ext_keys, &c->d_sums, &c->d_pre, &c->d_pre2, &c->d_shots, &c->d_uni, &c->d_ang,
-                    &c->d_lambda, &c->d_gacc, &c->d_ckpt};
+                    &c->d_lambda, &c->d_gacc, &c->d_ckpt, &c->d_cutplanes, &c->d_flag};
   for (DevBuf* b : bufs) b->release();
   for (auto& kv : c->tct_tabs) kv.second.release();
   for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }

@@ -362,14 +362,18 @@ static __global__ void scan_offset_kernel(double* __restrict__ pre, long long co
   if (i == 0) pre[count] = pre2[nchunks];
 }
 
-// Draw k of the SplitMix64 stream `seed` (Steele, Lea and Flood 2014) as a
-// double in [0, 1): mix(seed + (k+1) * golden gamma) >> 11, times 2^-53.
-__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long k) {
+// Draw k of the SplitMix64 stream `seed` (Steele, Lea and Flood 2014):
+// mix(seed + (k+1) * golden gamma).
+__device__ __forceinline__ unsigned long long splitmix_draw(unsigned long long seed, unsigned long long k) {
   unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z = z ^ (z >> 31);
-  return double(z >> 11) * 0x1.0p-53;
+  return z ^ (z >> 31);
+}
+
+// The same draw as a double in [0, 1): its top 53 bits times 2^-53.
+__device__ __forceinline__ double splitmix_uniform(unsigned long long seed, unsigned long long k) {
+  return double(splitmix_draw(seed, k) >> 11) * 0x1.0p-53;
 }
 
 template <typename Real>

@@ -29,7 +29,8 @@ EXPORTS = ("qaoa_state_bytes", "qaoa_aux_bytes", "qaoa_init_graph", "qaoa_run", 
            "qaoa_state_ptr", "qaoa_describe_plan", "qaoa_profile_enable", "qaoa_profile_read",
            "qaoa_last_error", "qaoa_free", "qaoa_sample_state_noalloc",
            "qaoa_batch_create", "qaoa_batch_run", "qaoa_batch_results", "qaoa_batch_state",
-           "qaoa_batch_describe", "qaoa_batch_bytes", "qaoa_batch_last_error", "qaoa_batch_free")
+           "qaoa_batch_describe", "qaoa_batch_bytes", "qaoa_batch_last_error", "qaoa_batch_free",
+           "qaoa_sample_cuts", "qaoa_mean_of_means", "qaoa_classify_regime")
 PROFILE_KINDS = {"pass": 0, "adjoint": 1, "cost": 2, "sample": 3, "small": 4}
 
 _lib = None
@@ -92,6 +93,10 @@ def load():
     lib.qaoa_batch_last_error.restype = ctypes.c_char_p
     lib.qaoa_batch_free.argtypes = [vp]
     lib.qaoa_batch_free.restype = None
+    lib.qaoa_sample_cuts.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_uint64, vp, vp, vp]
+    lib.qaoa_mean_of_means.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp, vp, vp]
+    lib.qaoa_classify_regime.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_double]
     _lib = lib
     return lib
 
@@ -283,6 +288,58 @@ class Simulator:
         """The state vector (torch complex tensor on the GPU, shares memory)."""
         self.stream.synchronize()
         return self._state_t
+
+    def sample_cuts(self, xs=None, count: int = 0, seed: int = 0) -> dict:
+        """C(x) and r(x) of bitstrings (Sec. II-D): `xs` (uint64, host or device),
+        or `count` draws of the random sampler from stream `seed`. Returns torch
+        device tensors x (int64 view of the uint64 indices), c (int32), r (float64)."""
+        import torch
+        xp = None
+        if xs is not None:
+            xt = torch.as_tensor(np.asarray(xs, dtype=np.uint64).view(np.int64)) if not torch.is_tensor(xs) else xs
+            xt = xt.to(device="cuda", dtype=torch.int64).contiguous()
+            count = xt.numel()
+            xp = ctypes.c_void_p(xt.data_ptr())
+        count = int(count)
+        x = torch.empty(count, dtype=torch.int64, device="cuda")
+        c = torch.empty(count, dtype=torch.int32, device="cuda")
+        r = torch.empty(count, dtype=torch.float64, device="cuda")
+        self._check(self._lib.qaoa_sample_cuts(self._ctx, count, xp, ctypes.c_uint64(seed),
+                                               ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                               ctypes.c_void_p(r.data_ptr())))
+        return dict(x=x, c=c, r=r)
+
+
+def mean_of_means(r, ns: int, reps: int = 100, seed: int = 0, stream=None) -> dict:
+    """Mean of subsample means of a pool of ratios (Sec. II-D): `r` a float64
+    CUDA tensor; returns the reps subsample means (CUDA tensor) and the grand
+    mean, sigma and random threshold (host floats)."""
+    import torch
+    lib = load()
+    if not (torch.is_tensor(r) and r.is_cuda and r.dtype == torch.float64):
+        raise TypeError("r must be a float64 CUDA tensor")
+    r = r.contiguous()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    means = torch.empty(int(reps), dtype=torch.float64, device=r.device)
+    stats = torch.empty(3, dtype=torch.float64, device=r.device)
+    rc = lib.qaoa_mean_of_means(ctypes.c_void_p(r.data_ptr()), r.numel(), int(ns), int(reps), ctypes.c_uint64(seed),
+                                ctypes.c_void_p(means.data_ptr()), ctypes.c_void_p(stats.data_ptr()),
+                                ctypes.c_void_p(st.cuda_stream))
+    if rc:
+        raise QaoaError(rc, "qaoa_mean_of_means rejected its arguments or failed")
+    h = stats.cpu().numpy()
+    return dict(means=means, grand_mean=float(h[0]), sigma=float(h[1]), threshold=float(h[2]))
+
+
+REGIMES = {0: "random", 1: "transition", 2: "noise-tolerant", 3: "above random"}
+
+
+def classify_regime(r_obs: float, rand_mean: float, rand_sigma: float, ideal_mean=None, ideal_sigma=None) -> int:
+    """Performance regime of an observed mean ratio (Sec. II-D); see REGIMES."""
+    have = ideal_mean is not None
+    return int(load().qaoa_classify_regime(float(r_obs), float(rand_mean), float(rand_sigma), int(have),
+                                           float(ideal_mean) if have else 0.0,
+                                           float(ideal_sigma) if have else 0.0))
 
 
 class BatchOpts(ctypes.Structure):

@@ -129,3 +129,28 @@ def test_adjoint_group_counts(lib, monkeypatch):
     got = [int(re.search(r"groups=(\d+)", qaoa.describe_plan(n, 5, "c64", adjoint=True)).group(1))
            for n in (24, 28, 33)]
     assert got == [2, 3, 3]
+
+
+def test_classify_regime_matches_oracle(lib):
+    # host-only entry point: the regime rule on a grid of observations
+    import oracle
+    for r_obs in np.linspace(0.6, 1.0, 81):
+        for rs in (0.0, 0.004, 0.02):
+            for ideal in ((None, None), (0.88, 0.01), (0.81, 0.03)):
+                a = qaoa.classify_regime(r_obs, 0.79, rs, *ideal)
+                b = oracle.classify_regime(float(r_obs), 0.79, rs, *ideal)
+                assert a == b, (r_obs, rs, ideal)
+    assert qaoa.classify_regime(0.9, 0.79, float("nan")) == -1
+
+
+def test_mean_of_means_rejects_bad_sizes(lib):
+    # argument checks come before any device work
+    vp = ctypes.c_void_p
+    one = vp(16)
+    assert lib.qaoa_mean_of_means(None, 10, 2, 2, 0, one, one, None) == qaoa.QAOA_EINVAL
+    assert lib.qaoa_mean_of_means(one, 10, 11, 2, 0, one, one, None) == qaoa.QAOA_EINVAL
+    assert lib.qaoa_mean_of_means(one, 10, 0, 2, 0, one, one, None) == qaoa.QAOA_EINVAL
+    assert lib.qaoa_mean_of_means(one, 10000, 4097, 2, 0, one, one, None) == qaoa.QAOA_EINVAL
+    assert lib.qaoa_mean_of_means(one, 10, 2, 0, 0, one, one, None) == qaoa.QAOA_EINVAL
+    assert lib.qaoa_mean_of_means(one, 1 << 32, 2, 2, 0, one, one, None) == qaoa.QAOA_EINVAL
+    assert lib.qaoa_sample_cuts(None, 1, None, 0, None, None, None) == qaoa.QAOA_EINVAL

@@ -298,3 +298,116 @@ def test_analytic_p1_expectation_matches_simulation():
         cut = oracle.cut_values(n, u, v, w)
         e = oracle.expectation(oracle.simulate(n, u, v, w, 0.1, [gamma], [beta]), cut)[0]
         assert abs(oracle.analytic_p1_expectation(n, u, v, w, 0.1, gamma, beta) - e) <= 1e-10 * abs(e)
+
+
+# ---------------------------------------------------------------- Sec. II-D
+def test_sample_cuts_hand_and_moments():
+    # triangle 0-1 (w 2), 1-2 (w 3), 0-2 (w -1): hand values of C(x)
+    u, v, w = [0, 1, 0], [1, 2, 2], [2, 3, -1]
+    hand = {0: 0, 1: 2 - 1, 2: 2 + 3, 3: 3 - 1, 4: 3 - 1, 5: 2 + 3, 6: 2 - 1, 7: 0}
+    got = oracle.sample_cuts(3, u, v, w, list(hand))
+    assert list(got) == [hand[x] for x in hand]
+    # over all 2^n bitstrings every edge is cut exactly half the time and the
+    # cut indicators of distinct edges are pairwise independent: mean W/2,
+    # variance sum w^2 / 4; C(x) = C(~x)
+    n = 9
+    u, v, w = inputs.complete_graph(n, 4242)
+    xs = np.arange(1 << n, dtype=np.uint64)
+    c = oracle.sample_cuts(n, u, v, w, xs).astype(np.int64)
+    W, Q = int(np.sum(w)), int(np.sum(np.asarray(w, dtype=np.int64) ** 2))
+    assert 2 * int(c.sum()) == W * (1 << n)
+    assert 4 * int(((2 * c - W) ** 2).sum()) == 4 * Q * (1 << n)
+    assert np.array_equal(c, c[::-1])
+    with pytest.raises(ValueError):
+        oracle.sample_cuts(3, [0], [1], [1], [8])
+
+
+def test_random_sampler_moments():
+    n = 12
+    u, v, w = inputs.complete_graph(n, 77)
+    xs = oracle.random_bitstrings(n, 20000, seed=5)
+    assert int(xs.max()) < (1 << n)
+    bits = (xs[:, None] >> np.arange(n, dtype=np.uint64)) & np.uint64(1)
+    freq = bits.mean(axis=0)
+    assert np.all(np.abs(freq - 0.5) < 5 * 0.5 / math.sqrt(len(xs)))
+    c = oracle.sample_cuts(n, u, v, w, xs[:4000]).astype(np.float64)
+    W, Q = float(np.sum(w)), float(np.sum(np.asarray(w, dtype=np.float64) ** 2))
+    assert abs(c.mean() - W / 2) < 5 * math.sqrt(Q / 4 / len(c))
+    # ratios: (C - C_min) / (C_max - C_min), exact per sample
+    cut = oracle.cut_values(n, u, v, w)
+    cmin, cmax, _, _ = oracle.extremes(n, cut)
+    r = oracle.sample_ratios(cut[xs[:50].astype(np.int64)], cmin, cmax)
+    assert np.all((r >= 0) & (r <= 1))
+    assert np.array_equal(oracle.sample_ratios([cmin, cmax], cmin, cmax), [0.0, 1.0])
+    assert np.array_equal(oracle.sample_ratios([5, 5], 5, 5), [1.0, 1.0])
+
+
+def test_subsample_without_replacement():
+    idx = oracle.subsample_indices(50, 20, 30, seed=9)
+    assert idx.shape == (30, 20)
+    for row in idx:
+        assert len(set(row.tolist())) == 20 and row.min() >= 0 and row.max() < 50
+    full = oracle.subsample_indices(17, 17, 5, seed=1)
+    for row in full:
+        assert sorted(row.tolist()) == list(range(17))
+    # every ordered pair of distinct positions is equally likely
+    reps = 12000
+    idx = oracle.subsample_indices(4, 2, reps, seed=3)
+    counts = {}
+    for a, b in idx.tolist():
+        counts[(a, b)] = counts.get((a, b), 0) + 1
+    assert len(counts) == 12
+    mu = reps / 12
+    sd = math.sqrt(reps * (1 / 12) * (11 / 12))
+    assert all(abs(k - mu) < 5 * sd for k in counts.values())
+    with pytest.raises(ValueError):
+        oracle.subsample_indices(5, 6, 1, seed=0)
+
+
+def test_mean_of_means_closed_forms():
+    pool = inputs.uniforms(11, 400)
+    # ns = m: every subsample is the whole pool
+    mm = oracle.mean_of_means(pool, 400, 20, seed=2)
+    assert np.all(np.abs(mm["means"] - pool.mean()) < 1e-14)
+    assert mm["sigma"] < 1e-14 and abs(mm["threshold"] - mm["grand_mean"]) < 1e-13
+    # ns = 1: the means are pool entries
+    mm = oracle.mean_of_means(pool, 1, 50, seed=2)
+    assert set(mm["means"].tolist()) <= set(pool.tolist())
+    # without replacement: Var(mean) = S^2 / ns * (m - ns) / (m - 1) with S^2
+    # the pool's variance (1/m); 4000 subsamples put the estimate within ~5%
+    m, ns, reps = 400, 40, 4000
+    mm = oracle.mean_of_means(pool, ns, reps, seed=4)
+    want = pool.var() / ns * (m - ns) / (m - 1)
+    assert abs(mm["sigma"] ** 2 / want - 1) < 0.15
+    assert abs(mm["grand_mean"] - pool.mean()) < 5 * math.sqrt(want / reps)
+    assert mm["threshold"] == mm["grand_mean"] + 3.0 * mm["sigma"]
+
+
+def test_mean_of_means_shot_scaling_matches_paper():
+    # Sec. II-D: going from 100 to 10 shots widens the random sampler's
+    # mean-of-means distribution by about 3.5 (100 subsamples each); sampling
+    # without replacement from a large pool predicts sqrt(10) ~ 3.2, and the
+    # 100-subsample estimates scatter by ~10%
+    n = 14
+    u, v, w = inputs.complete_graph(n, 140)
+    cut = oracle.cut_values(n, u, v, w)
+    cmin, cmax, _, _ = oracle.extremes(n, cut)
+    xs = oracle.random_bitstrings(n, 5000, seed=8)
+    r = oracle.sample_ratios(cut[xs.astype(np.int64)], cmin, cmax)
+    s10 = oracle.mean_of_means(r, 10, 100, seed=1)["sigma"]
+    s100 = oracle.mean_of_means(r, 100, 100, seed=1)["sigma"]
+    assert abs(s10 / s100 / 3.5 - 1) < 0.25
+
+
+def test_classify_regime_cases():
+    R, T, N, A = (oracle.REGIME_RANDOM, oracle.REGIME_TRANSITION, oracle.REGIME_NOISE_TOLERANT,
+                  oracle.REGIME_ABOVE_RANDOM)
+    # random interval 0.79 +- 0.03 (threshold 0.82), noiseless 0.88 +- 0.03 (from 0.85)
+    assert oracle.classify_regime(0.70, 0.79, 0.01) == R          # below the random interval
+    assert oracle.classify_regime(0.80, 0.79, 0.01, 0.88, 0.01) == R
+    assert oracle.classify_regime(0.83, 0.79, 0.01, 0.88, 0.01) == T
+    assert oracle.classify_regime(0.87, 0.79, 0.01, 0.88, 0.01) == N
+    assert oracle.classify_regime(0.95, 0.79, 0.01, 0.88, 0.01) == N  # above the noiseless interval
+    assert oracle.classify_regime(0.83, 0.79, 0.01) == A
+    assert oracle.classify_regime(0.83, 0.79, float("nan")) == -1
+    assert oracle.classify_regime(0.83, 0.79, 0.01, 0.88, -1.0) == -1
