@@ -539,6 +539,8 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
     PassArgs pa;
     pa.state = outs && pi > 0 ? outs[pi - 1] : c->state;
     pa.out = outs ? outs[pi] : c->state;
+    if (pa.out != pa.state && pd.nsub != 1)
+      return c->set_err(QAOA_EINVAL, "a pass of several sub-passes cannot write to another buffer");
     pa.diag = stream ? (const int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n))) : nullptr;
     pa.phase = pp.layer_c >= 0 ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_c) * nc * ab) : nullptr;
     pa.wmat = (const int32_t*)c->d_wmat.p;
@@ -760,7 +762,9 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
         fwd_order = grad_bwd_order();
         fp = get_plan(c, p, fwd_order);
       }
-      if (plans_mirror(*fp, *plan)) {
+      bool single = true;  // out-of-place passes have one sub-pass
+      for (const PassPlan& pp : fp->passes) single = single && pp.subs.size() == 1;
+      if (single && plans_mirror(*fp, *plan)) {
         const size_t sb = qaoa_state_bytes(n, c->prec);
         const size_t np = fp->passes.size();
         const size_t need = (np - 1) * sb;

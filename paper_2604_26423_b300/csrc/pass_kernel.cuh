@@ -29,8 +29,9 @@ enum : uint8_t { DST_SMEM_D = 0, DST_GLOBAL_D = 1 };
 
 struct PassArgs {
   void* state;            // 2^n amplitudes, interleaved (re, im): the pass's input
-  void* out;              // where the pass writes its output: `state` (in place) or
-                          // another 2^n buffer (the gradient's stored forward states)
+  void* out;              // where the pass writes its output: `state` (in place) or,
+                          // for a pass of one sub-pass, another 2^n buffer (the
+                          // gradient's stored forward states)
   const int32_t* diag;    // int32 C(x) for all x (stream mode) or nullptr
   const void* phase;      // phase table of the cost layer: ncost complex entries
   const int32_t* wmat;    // n x n symmetric integer weights
@@ -607,8 +608,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       else load0 = sp.rd[0].src == SRC_GLOBAL_D;
       if (load0) {
         const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
-        // later sub-passes read what the earlier ones wrote
-        const C2* gs = reinterpret_cast<const C2*>(s == 0 ? A.state : A.out);
+        const C2* gs = reinterpret_cast<const C2*>(A.state);
         if (A.l2hint) {
           const uint64_t pol = l2_policy_evict_first();
           gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = ld_hint(q, pol); });
@@ -617,16 +617,31 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         }
       }
       // tile constants from the table: into the buffer the previous tile did
-      // not use, published by the barrier below
+      // not use, published by the barrier below. The specialised write-only
+      // |+> pass, which has no state load to hide the table read behind,
+      // copies them asynchronously one unit ahead (the CTA's next unit is
+      // unit + gridDim.x). (Passes that load the state measured slower with
+      // the early copy.)
       int* tc = tconst;
       const bool tab = CC && sp.needs_c && !stream && sp.tct != nullptr;
+      bool ahead = false;
+      if constexpr (kSpec) ahead = tab && (first_sig<RS...>() >> 2 & 3u) == SRC_INIT_D;
       if (tab) {
         tc = tconst + 32 * (*tcount & 1u);
-        *tcount += 1;
-        if (tid < kTileConstInts)
+        if (ahead && *tcount != 0) {
+          cp_async_wait_all();  // this tile's constants, copied during the previous tile
+        } else if (tid < kTileConstInts) {
           tc[tid == 15 ? 16 : tid] = __ldg(sp.tct + (((unit << sp.ninner) + ti) * kTileConstInts + tid));
+        }
+        *tcount += 1;
       }
       __syncthreads();  // previous tile finished with shared memory
+      if (ahead) {
+        const uint64_t next = unit + gridDim.x;
+        if (next < P.n_units && tid < kTileConstInts)
+          cp_async4(tconst + 32 * (*tcount & 1u) + (tid == 15 ? 16 : tid), sp.tct + next * kTileConstInts + tid);
+        cp_async_commit();
+      }
       if (CC && sp.needs_c && !stream && !tab) {
         if (tid == 0) tconst[16] = 0;
         __syncthreads();
