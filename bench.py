@@ -30,6 +30,9 @@ phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
   random sampler; kernel time, bitstrings/s), the ratios of the step's 4096
   shots, the mean of 100 subsample means at 10 and 100 shots for both, and the
   regime of the first 10 shots.
+* ``noise``: noisy LR-QAOA (Sec. II-C) on K_12, p = 10, complex128: 4096
+  depolarizing-channel trajectories per rate, trajectories/s of the kernel, the
+  noisy r, r_ovl and the k0 fit of Eq. noise.
 * ``--qubits n`` runs the same step on K_n (smaller cases for profiling; the
   JSON line then names that workload).
 * ``cpu_baseline`` / ``--impl reference``: the gate-by-gate complex128 oracle on
@@ -338,6 +341,40 @@ def stats_bench(sim, shots, stream, pool: int = 1 << 26):
     return out
 
 
+def noise_bench(args, trajectories: int = 4096):
+    """Noisy LR-QAOA (Sec. II-C) on K_12, p = 10: `trajectories` Monte Carlo
+    trajectories per depolarizing rate (complex128, one CTA each, kernel timed
+    with CUDA events), the noisy r, the overlap ratio r_ovl against the
+    noiseless r and the random sampler's, and the fit of Eq. noise."""
+    from paper_2604_26423_b300 import inputs
+    from paper_2604_26423_b300.qaoa import Simulator, fit_k0, lr_angles, overlap_ratio
+
+    n, p = 12, 10
+    u, v, w = inputs.complete_graph(n, SEED)
+    g, b = lr_angles(p, DGAMMA, DBETA)
+    out = {"workload": f"K_{n} (seed {SEED}), p={p}, dgamma={DGAMMA}, dbeta={DBETA}, complex128, "
+                       f"{trajectories} trajectories per rate", "rates": []}
+    with Simulator(n, u, v, w, SCALE, "c128") as s:
+        ext = s.extremes()
+        r_rand = (float(np.sum(w)) / 2 - ext["c_min"]) / (ext["c_max"] - ext["c_min"])
+        s.noisy_expect(g, b, 0.0, 64, seed=1)  # warm-up
+        ideal = s.noisy_expect(g, b, 0.0, 1, seed=1)["r"]
+        a_list, o_list = [], []
+        for eps in (0.0005, 0.002, 0.005, 0.01):
+            s.profile(True)
+            res = s.noisy_expect(g, b, eps, trajectories, seed=SEED)
+            k = s.profile_read("small")
+            s.profile(False)
+            ro = overlap_ratio(res["r"], ideal, r_rand)
+            acc = p * len(u) * eps
+            a_list.append(acc)
+            o_list.append(ro)
+            out["rates"].append({"eps": eps, "eps_acc": acc, "r_noisy": res["r"], "r_ovl": ro,
+                                 "kernel_ms": k["ms"], "trajectories_per_s": trajectories / (k["ms"] * 1e-3)})
+    out.update({"r_ideal": ideal, "r_random": r_rand, "k0": fit_k0(a_list, o_list)})
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_2604_26423_b300 import inputs
@@ -387,6 +424,7 @@ def run_gpu(args):
     wh = torch.from_numpy(w).pin_memory().numpy()
     stats = None if args.no_stats else stats_bench(sim, shots, stream)
     sim.close()
+    noise = None if args.no_noise else noise_bench(args)
 
     def e2e_step():
         s2 = Simulator(nq, uh, vh, wh, SCALE, "c64", cost_mode=args.cost_mode, state=state_buf)
@@ -456,6 +494,8 @@ def run_gpu(args):
         out["configs"] = configs
     if stats is not None:
         out["stats"] = stats
+    if noise is not None:
+        out["noise"] = noise
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_budget)
     if rank == 0:
@@ -504,6 +544,7 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-stats", action="store_true")
+    ap.add_argument("--no-noise", action="store_true")
     ap.add_argument("--batch-reps", type=int, default=3)
     ap.add_argument("--batch-count", type=int, default=BATCH_COUNT)
     ap.add_argument("--qubits", type=int, default=N_QUBITS)

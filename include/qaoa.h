@@ -280,6 +280,40 @@ const char *qaoa_batch_last_error(const qaoa_batch *b);
 void qaoa_batch_free(qaoa_batch *b);
 
 /* ------------------------------------------------------------------------
+ * Noisy LR-QAOA (Sec. II-C): a two-qubit depolarizing channel of rate eps
+ * after every ZZ gate, E(rho) = (1 - eps) rho + eps (I/4 (x) Tr_ij rho), i.e.
+ * with probability eps one of the 16 two-qubit Paulis on (i, j), uniformly.
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Monte Carlo trajectories of the noisy circuit with explicit angles gamma,
+ * beta (p each, host; the LR schedule is qaoa_run's) on the context's graph,
+ * n <= QAOA_NOISY_MAX_QUBITS, complex128 arithmetic. Trajectory t draws, for
+ * gate g = k m + e (layer k, edge e in the order given to qaoa_init_graph),
+ * draw t (p m) + g of SplitMix64 stream `seed`: an error when its top 53 bits
+ * times 2^-53 are below eps, then Pauli (draw & 3) on u_e and ((draw >> 2) & 3)
+ * on v_e (0 I, 1 X, 2 Y, 3 Z). exp_c_dev (device, `trajectories` doubles, or
+ * NULL): each trajectory's <C>_t; *mean_exp_c (host, or NULL): their mean, the
+ * noisy <C> estimate; *r_noisy (host, or NULL): (mean - C_min)/(C_max - C_min).
+ * The context's state is not touched. Returns after the kernels finished.
+ * Errors: EINVAL (n too large, p < 0, eps outside [0, 1], trajectories < 1,
+ * non-finite angles), ENOMEM, ECUDA.
+ */
+#define QAOA_NOISY_MAX_QUBITS 12
+int qaoa_noisy_expect(qaoa_ctx *ctx, int p, const double *gamma, const double *beta, double eps,
+                      int trajectories, uint64_t seed, double *exp_c_dev, double *mean_exp_c, double *r_noisy);
+
+/* r_ovl = (r_noisy - r_random) / (r_ideal - r_random) (Sec. II-C); host only. */
+double qaoa_overlap_ratio(double r_noisy, double r_ideal, double r_random);
+
+/*
+ * k0 of Eq. noise, r_ovl = 2^(-k0 eps_acc) with eps_acc = N_2q eps: the least
+ * squares slope of log2 r_ovl = -k0 eps_acc through the origin over the
+ * `count` points (host arrays) with r_ovl > 0; NaN when none remains.
+ */
+double qaoa_fit_k0(int count, const double *eps_acc, const double *r_ovl);
+
+/* ------------------------------------------------------------------------
  * Sampling methodology (Sec. II-D): the approximation ratio of individual
  * bitstrings, the uniform random sampler, the mean of subsample means and the
  * three performance regimes. Random draws are SplitMix64 stream draws (the

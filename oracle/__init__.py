@@ -19,6 +19,10 @@ Every function names the passage of the paper it follows:
 * ``grad_param_shift`` -- exact two-term shift rule per gate (each gate is
                           exp(-i theta/2 P) with a Pauli product P).
 * ``gate_counts``      -- Sec. II-B, N_2q = p N(N-1)/2 and N_1q = (p+1) N.
+* ``noisy_trajectory``, ``noisy_density`` -- Sec. II-C: LR-QAOA with a
+  two-qubit depolarizing channel after every ZZ gate, as one stochastic
+  trajectory (explicit Pauli errors, gate by gate) and exactly (density matrix,
+  tiny n); ``overlap_ratio`` and ``fit_k0`` -- Eq. noise, r_ovl = 2^(-k0 eps_acc).
 * ``sample_cuts``, ``sample_ratios``, ``random_bitstrings``, ``subsample_indices``,
   ``mean_of_means``, ``classify_regime`` -- Sec. II-D (sampling methodology):
   approximation ratio of individual bitstrings, the uniform random sampler,
@@ -379,3 +383,107 @@ def classify_regime(r_obs: float, rand_mean: float, rand_sigma: float, ideal_mea
     if r_obs >= ideal_mean - 3.0 * ideal_sigma:
         return REGIME_NOISE_TOLERANT
     return REGIME_TRANSITION
+
+
+# ------------------------------------------------------------- Sec. II-C
+# Depolarizing channel on the two qubits (i, j) of every ZZ gate, applied right
+# after the gate: E(rho) = (1 - eps) rho + eps (I/4 (x) Tr_ij rho), i.e. with
+# probability eps one of the 16 two-qubit Paulis (identity included), uniformly.
+# Trajectory t draws, for gate g = k m + e (layer k, edge e in input order),
+# draw t (p m) + g of stream `seed`: an error when its top 53 bits times 2^-53
+# are below eps, the Pauli from its low 4 bits (bits 0-1 on i, 2-3 on j;
+# 0 I, 1 X, 2 Y, 3 Z).
+
+def _apply_pauli(psi, x, q, kind):
+    if kind == 0:
+        return psi
+    b = (x >> q) & 1
+    if kind == 1:
+        return psi[x ^ (1 << q)]
+    if kind == 3:
+        return psi * (1 - 2 * b)
+    return 1j * (2 * b - 1) * psi[x ^ (1 << q)]  # Y = [[0, -i], [i, 0]]
+
+
+def noisy_trajectory(n: int, u, v, w, scale: float, gamma, beta, eps: float, seed: int, t: int) -> np.ndarray:
+    """State of trajectory t: |+>, then per layer every ZZ gate exp(-i gamma_k s w_e Z_i Z_j)
+    followed by its sampled Pauli error, then exp(+i beta_k X_q) on every qubit."""
+    from paper_2604_26423_b300 import inputs
+    gamma = np.atleast_1d(np.asarray(gamma, dtype=np.float64))
+    beta = np.atleast_1d(np.asarray(beta, dtype=np.float64))
+    p, m = len(gamma), len(u)
+    x = np.arange(1 << n, dtype=np.int64)
+    psi = np.full(1 << n, 2.0 ** (-n / 2), dtype=np.complex128)
+    draws = inputs.splitmix64(seed, p * m, offset=t * p * m)
+    for k in range(p):
+        for e in range(m):
+            i, j = int(u[e]), int(v[e])
+            zz = (1 - 2 * ((x >> i) & 1)) * (1 - 2 * ((x >> j) & 1))
+            psi = psi * np.exp(-1j * gamma[k] * scale * float(w[e]) * zz)
+            d = int(draws[k * m + e])
+            if (d >> 11) * 2.0 ** -53 < eps:
+                psi = _apply_pauli(psi, x, i, d & 3)
+                psi = _apply_pauli(psi, x, j, (d >> 2) & 3)
+        c, s_ = math.cos(beta[k]), math.sin(beta[k])
+        for q in range(n):
+            flip = psi[x ^ (1 << q)]
+            psi = c * psi + 1j * s_ * flip
+    return psi
+
+
+def _pauli_matrix(n, q, kind):
+    one = {0: np.eye(2), 1: np.array([[0, 1], [1, 0]]), 2: np.array([[0, -1j], [1j, 0]]),
+           3: np.array([[1, 0], [0, -1]])}[kind]
+    mat = np.array([[1.0]])
+    for b in range(n - 1, -1, -1):  # bit q of the index is qubit q
+        mat = np.kron(mat, one if b == q else np.eye(2))
+    return mat
+
+
+def noisy_density(n: int, u, v, w, scale: float, gamma, beta, eps: float) -> float:
+    """Exact noisy <C> by density-matrix evolution (n <= 6): after every ZZ gate
+    rho -> (1 - eps) rho + eps/16 sum_P P rho P over the 16 Paulis on (i, j)."""
+    gamma = np.atleast_1d(np.asarray(gamma, dtype=np.float64))
+    beta = np.atleast_1d(np.asarray(beta, dtype=np.float64))
+    N = 1 << n
+    x = np.arange(N)
+    plus = np.full(N, 2.0 ** (-n / 2), dtype=np.complex128)
+    rho = np.outer(plus, plus.conj())
+    X = [_pauli_matrix(n, q, 1) for q in range(n)]
+    for k in range(len(gamma)):
+        for e in range(len(u)):
+            i, j = int(u[e]), int(v[e])
+            zz = (1 - 2 * ((x >> i) & 1)) * (1 - 2 * ((x >> j) & 1))
+            d = np.exp(-1j * gamma[k] * scale * float(w[e]) * zz)
+            rho = d[:, None] * rho * d.conj()[None, :]
+            acc = np.zeros_like(rho)
+            for a in range(4):
+                for b in range(4):
+                    P = _pauli_matrix(n, i, a) @ _pauli_matrix(n, j, b)
+                    acc += P @ rho @ P.conj().T
+            rho = (1 - eps) * rho + eps / 16 * acc
+        for q in range(n):
+            U = math.cos(beta[k]) * np.eye(N) + 1j * math.sin(beta[k]) * X[q]
+            rho = U @ rho @ U.conj().T
+    cut = cut_values(n, u, v, w)
+    return float(np.real(np.sum(np.diag(rho) * cut)))
+
+
+def overlap_ratio(r_noisy: float, r_ideal: float, r_random: float) -> float:
+    """r_ovl = (r_QPU - r_random) / (r_ideal - r_random) (Sec. II-C)."""
+    return (r_noisy - r_random) / (r_ideal - r_random)
+
+
+def fit_k0(eps_acc, r_ovl) -> float:
+    """k0 of Eq. noise, r_ovl = 2^(-k0 eps_acc): least squares on log2 r_ovl = -k0 eps_acc
+    (a line through the origin); points with r_ovl <= 0 are left out."""
+    a = np.asarray(eps_acc, dtype=np.float64)
+    r = np.asarray(r_ovl, dtype=np.float64)
+    keep = r > 0
+    a, r = a[keep], r[keep]
+    num = 0.0
+    den = 0.0
+    for ai, ri in zip(a, r):
+        num += ai * math.log2(ri)
+        den += ai * ai
+    return -num / den if den > 0 else float("nan")

@@ -26,6 +26,7 @@
 #include "pass_kernel.cuh"
 #include "aux_kernels.cuh"
 #include "stats_kernels.cuh"
+#include "noise_kernels.cuh"
 #include "small_kernel.cuh"
 #include "adj_kernel.cuh"
 #include "spec.h"
@@ -87,6 +88,7 @@ struct qaoa_ctx {
   DevBuf d_ckpt;                                                      // the gradient's stored forward states
   DevBuf d_cutplanes, d_flag;                                         // weight bit planes (qaoa_sample_cuts), error flag
   int cut_planes = -1;                                                // planes in d_cutplanes (-1: not built)
+  DevBuf d_noisy, d_ntraj;                                            // noisy trajectories: edges + angles, outputs
   TableStore tabs;                                                     // host copy of all cost tables
   std::map<std::vector<int8_t>, DevBuf> tct_tabs;                     // per-tile constant tables by sub-pass layout
   size_t tct_bytes = 0;
@@ -1265,6 +1267,74 @@ int qaoa_sample_cuts(qaoa_ctx* c, int64_t count, const uint64_t* x_dev, uint64_t
   return QAOA_OK;
 }
 
+int qaoa_noisy_expect(qaoa_ctx* c, int p, const double* gamma, const double* beta, double eps, int trajectories,
+                      uint64_t seed, double* exp_c_dev, double* mean_exp_c, double* r_noisy) {
+  if (!c) return QAOA_EINVAL;
+  const int n = c->n, m = c->m;
+  if (n > kNoisyMaxQubits) return c->set_err(QAOA_EINVAL, "noisy trajectories need n <= %d", kNoisyMaxQubits);
+  if (p < 0 || (p > 0 && (!gamma || !beta))) return c->set_err(QAOA_EINVAL, "p < 0 or missing angles");
+  if (!(eps >= 0.0 && eps <= 1.0)) return c->set_err(QAOA_EINVAL, "eps must lie in [0, 1]");
+  if (trajectories < 1) return c->set_err(QAOA_EINVAL, "trajectories must be >= 1");
+  for (int k = 0; k < p; ++k)
+    if (!std::isfinite(gamma[k]) || !std::isfinite(beta[k])) return c->set_err(QAOA_EINVAL, "angles must be finite");
+  int rc = ensure_extremes(c);
+  if (rc) return rc;
+  // device block: u, v, w (int32, m each, padded to 8 bytes) | theta (p x m) | beta (p)
+  const size_t ints = (3 * size_t(m) + 1) & ~size_t(1);
+  std::vector<unsigned char> blk(ints * 4 + (size_t(p) * m + p) * 8 + 8);
+  int32_t* hi = reinterpret_cast<int32_t*>(blk.data());
+  for (int e = 0; e < m; ++e) { hi[e] = c->u[e]; hi[m + e] = c->v[e]; hi[2 * m + e] = c->w[e]; }
+  double* hd = reinterpret_cast<double*>(blk.data() + ints * 4);
+  for (int k = 0; k < p; ++k) {
+    for (int e = 0; e < m; ++e) hd[size_t(k) * m + e] = gamma[k] * c->scale * double(c->w[e]);
+    hd[size_t(p) * m + k] = beta[k];
+  }
+  CUDA_TRY(c, c->d_noisy.ensure(blk.size()));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_noisy.p, blk.data(), blk.size(), cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, c->d_ntraj.ensure(sizeof(double) * (size_t(trajectories) + 1)));
+  double* out = exp_c_dev ? exp_c_dev : (double*)c->d_ntraj.p;
+  NoisyArgs a;
+  a.n = n;
+  a.m = m;
+  a.p = p;
+  a.trajectories = trajectories;
+  a.u = (const int32_t*)c->d_noisy.p;
+  a.v = a.u + m;
+  a.w = a.u + 2 * m;
+  a.theta = (const double*)((const unsigned char*)c->d_noisy.p + ints * 4);
+  a.beta = a.theta + size_t(p) * m;
+  a.eps = eps;
+  a.seed = seed;
+  a.exp_c = out;
+  a.norm = nullptr;
+  const size_t smem = (size_t(1) << n) * (16 + 4);
+  CUDA_TRY(c, cudaFuncSetAttribute(noisy_trajectory_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int bps = 0;
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, noisy_trajectory_kernel, kNoisyThreads, smem));
+  const int grid = std::max(1, std::min(trajectories, std::max(1, bps) * c->sms));
+  {
+    ProfScope ps(c, 4, 0.0);
+    noisy_trajectory_kernel<<<grid, kNoisyThreads, smem, c->stream>>>(a);
+    if (c->prof_on) ++c->nlaunch;
+  }
+  CUDA_TRY(c, cudaGetLastError());
+  // mean over trajectories, summed in trajectory order
+  double* sum_dev = (double*)c->d_ntraj.p + trajectories;
+  sum_partials_kernel<<<1, 32, 0, c->stream>>>(out, trajectories, 1, sum_dev);
+  if (c->prof_on) ++c->nlaunch;
+  CUDA_TRY(c, cudaGetLastError());
+  double sum = 0.0;
+  CUDA_TRY(c, cudaMemcpyAsync(&sum, sum_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const double mean = sum / trajectories;
+  if (mean_exp_c) *mean_exp_c = mean;
+  if (r_noisy) {
+    const double span = double(c->ext.vmax - c->ext.vmin);
+    *r_noisy = span != 0.0 ? (mean - double(c->ext.vmin)) / span : 1.0;
+  }
+  return QAOA_OK;
+}
+
 int qaoa_cost_diag(qaoa_ctx* c, int32_t* out_dev) {
   if (!c) return QAOA_EINVAL;
   if (!out_dev) return c->set_err(QAOA_EINVAL, "out_dev is NULL");
@@ -1346,7 +1416,7 @@ void qaoa_free(qaoa_ctx* c) {
   c->aux_own.release();
   DevBuf* bufs[] = {&c->d_wmat, &c->d_ctabs, &c->d_phase, &c->d_partial, &c->d_result, &c->d_ext,
                     &c->d_ext_part, &c->d_ext_keys, &c->d_sums, &c->d_pre, &c->d_pre2, &c->d_shots, &c->d_uni, &c->d_ang,
-                    &c->d_lambda, &c->d_gacc, &c->d_ckpt, &c->d_cutplanes, &c->d_flag};
+                    &c->d_lambda, &c->d_gacc, &c->d_ckpt, &c->d_cutplanes, &c->d_flag, &c->d_noisy, &c->d_ntraj};
   for (DevBuf* b : bufs) b->release();
   for (auto& kv : c->tct_tabs) kv.second.release();
   for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }

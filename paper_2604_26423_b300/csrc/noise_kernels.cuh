@@ -1,0 +1,152 @@
+// noise_kernels.cuh -- noisy LR-QAOA (Sec. II-C): a two-qubit depolarizing
+// channel after every ZZ gate, sampled as stochastic trajectories, one CTA per
+// trajectory with the complex128 state of n <= 12 qubits in shared memory.
+//
+// A sampled Pauli error is not applied to the state: it is kept in a Pauli
+// frame F (bit masks fx, fz; the state is F|phi> up to a global phase) and
+// the later gates act on |phi> conjugated by the frame, F^dag U F:
+//   exp(-i theta Z_i Z_j) -> exp(-i sigma theta Z_i Z_j), sigma = (-1)^(fx_i + fx_j),
+//   exp(+i beta X_q)      -> exp(+i tau beta X_q),       tau   = (-1)^(fz_q),
+// since X and Y anticommute with Z, and Z and Y with X. A measurement of
+// F|phi> returns x with probability |phi(x ^ fx)|^2, so
+//   <C>_t = sum_y |phi(y)|^2 C(y ^ fx).
+// The error draws (channel and Pauli) follow the rule of the oracle: gate
+// g = k m + e of trajectory t takes draw t (p m) + g of stream `seed`; an
+// error when (draw >> 11) 2^-53 < eps, then Pauli (draw & 3) on qubit u_e and
+// ((draw >> 2) & 3) on v_e (0 I, 1 X, 2 Y, 3 Z).
+#pragma once
+#include <cstdint>
+
+#include "aux_kernels.cuh"
+
+namespace qaoa {
+
+constexpr int kNoisyMaxQubits = 12;
+constexpr int kNoisyMaxEdges = kNoisyMaxQubits * (kNoisyMaxQubits - 1) / 2;
+constexpr int kNoisyThreads = 256;
+
+struct NoisyArgs {
+  int n = 0, m = 0, p = 0, trajectories = 0;
+  const int32_t* u = nullptr;        // m edges (device)
+  const int32_t* v = nullptr;
+  const int32_t* w = nullptr;
+  const double* theta = nullptr;     // p x m: gamma_k s w_e
+  const double* beta = nullptr;      // p
+  double eps = 0.0;
+  unsigned long long seed = 0;
+  double* exp_c = nullptr;           // per trajectory <C>_t
+  double* norm = nullptr;            // per trajectory |phi|^2 (1 up to rounding)
+};
+
+// Dynamic shared memory: 2^n double2 state, 2^n int32 cut values.
+static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(const NoisyArgs a) {
+  extern __shared__ __align__(16) unsigned char nsm[];
+  const int n = a.n, m = a.m, N = 1 << n;
+  double2* phi = reinterpret_cast<double2*>(nsm);
+  int* cut = reinterpret_cast<int*>(phi + N);
+  __shared__ double sig[kNoisyMaxEdges];
+  __shared__ double tau[kNoisyMaxQubits];
+  __shared__ unsigned fxs;
+  __shared__ int su[kNoisyMaxEdges], sv[kNoisyMaxEdges];
+  __shared__ double red[2 * kNoisyThreads / 32];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < m; e += kNoisyThreads) {
+    su[e] = a.u[e];
+    sv[e] = a.v[e];
+  }
+  __syncthreads();
+  for (int x = tid; x < N; x += kNoisyThreads) {
+    int c = 0;
+    for (int e = 0; e < m; ++e) c += ((x >> su[e]) ^ (x >> sv[e])) & 1 ? a.w[e] : 0;
+    cut[x] = c;
+  }
+  for (int t = blockIdx.x; t < a.trajectories; t += gridDim.x) {
+    const double amp0 = exp2(-0.5 * n);
+    for (int x = tid; x < N; x += kNoisyThreads) phi[x] = make_double2(amp0, 0.0);
+    unsigned fx = 0, fz = 0;  // the frame, kept by thread 0
+    for (int k = 0; k < a.p; ++k) {
+      if (tid == 0) {
+        const unsigned long long base = (unsigned long long)t * (unsigned long long)(a.p * m) +
+                                        (unsigned long long)(k * m);
+        for (int e = 0; e < m; ++e) {
+          sig[e] = (((fx >> su[e]) ^ (fx >> sv[e])) & 1u) ? -1.0 : 1.0;
+          const unsigned long long d = splitmix_draw(a.seed, base + (unsigned long long)e);
+          if (double(d >> 11) * 0x1.0p-53 < a.eps) {
+            const unsigned pi = unsigned(d & 3ull), pj = unsigned(d >> 2 & 3ull);
+            // X (1) and Y (2) carry an X part, Z (3) and Y a Z part
+            if (pi == 1 || pi == 2) fx ^= 1u << su[e];
+            if (pi == 2 || pi == 3) fz ^= 1u << su[e];
+            if (pj == 1 || pj == 2) fx ^= 1u << sv[e];
+            if (pj == 2 || pj == 3) fz ^= 1u << sv[e];
+          }
+        }
+        for (int q = 0; q < n; ++q) tau[q] = (fz >> q & 1u) ? -1.0 : 1.0;
+      }
+      __syncthreads();
+      // cost layer with the frame's signs: phi_x *= exp(-i sum_e sigma_e theta_e z_i z_j)
+      const double* th = a.theta + (size_t)k * m;
+      for (int x = tid; x < N; x += kNoisyThreads) {
+        double ang = 0.0;
+        for (int e = 0; e < m; ++e) {
+          const double s = (((x >> su[e]) ^ (x >> sv[e])) & 1) ? -sig[e] : sig[e];
+          ang = fma(s, th[e], ang);
+        }
+        double sn, cs;
+        sincos(ang, &sn, &cs);
+        const double2 f = phi[x];
+        phi[x] = make_double2(f.x * cs + f.y * sn, f.y * cs - f.x * sn);
+      }
+      // mixer exp(+i tau_q beta_k X_q), qubit by qubit
+      double sb, cb;
+      sincos(a.beta[k], &sb, &cb);
+      for (int q = 0; q < n; ++q) {
+        __syncthreads();
+        const double s = tau[q] * sb;
+        for (int pr = tid; pr < N / 2; pr += kNoisyThreads) {
+          const int lo = pr & ((1 << q) - 1);
+          const int xa = ((pr >> q) << (q + 1)) | lo, xb = xa | (1 << q);
+          const double2 pa = phi[xa], pb = phi[xb];
+          // a' = c a + i s b, b' = i s a + c b
+          phi[xa] = make_double2(cb * pa.x - s * pb.y, cb * pa.y + s * pb.x);
+          phi[xb] = make_double2(cb * pb.x - s * pa.y, cb * pb.y + s * pa.x);
+        }
+      }
+      if (tid == 0) fxs = fx;
+      __syncthreads();
+    }
+    if (a.p == 0) {
+      if (tid == 0) fxs = 0;
+      __syncthreads();
+    }
+    // <C>_t = sum_y |phi(y)|^2 C(y ^ fx), and the norm
+    const unsigned f = fxs;
+    double ec = 0.0, nr = 0.0;
+    for (int x = tid; x < N; x += kNoisyThreads) {
+      const double2 z = phi[x];
+      const double pr = z.x * z.x + z.y * z.y;
+      nr += pr;
+      ec += pr * double(cut[x ^ (int)f]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ec += __shfl_xor_sync(0xffffffffu, ec, o);
+      nr += __shfl_xor_sync(0xffffffffu, nr, o);
+    }
+    if ((tid & 31) == 0) {
+      red[2 * (tid >> 5)] = ec;
+      red[2 * (tid >> 5) + 1] = nr;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double se = 0.0, sn = 0.0;
+      for (int wi = 0; wi < kNoisyThreads / 32; ++wi) {
+        se += red[2 * wi];
+        sn += red[2 * wi + 1];
+      }
+      a.exp_c[t] = se;
+      if (a.norm) a.norm[t] = sn;
+    }
+    __syncthreads();  // the next trajectory reuses phi, fxs and red
+  }
+}
+
+}  // namespace qaoa

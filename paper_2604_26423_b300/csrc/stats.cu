@@ -51,4 +51,19 @@ int qaoa_classify_regime(double r_obs, double rand_mean, double rand_sigma, int 
   return r_obs >= ideal_mean - 3.0 * ideal_sigma ? QAOA_REGIME_NOISE_TOLERANT : QAOA_REGIME_TRANSITION;
 }
 
+double qaoa_overlap_ratio(double r_noisy, double r_ideal, double r_random) {
+  return (r_noisy - r_random) / (r_ideal - r_random);
+}
+
+double qaoa_fit_k0(int count, const double* eps_acc, const double* r_ovl) {
+  if (count < 1 || !eps_acc || !r_ovl) return NAN;
+  double num = 0.0, den = 0.0;
+  for (int i = 0; i < count; ++i) {
+    if (!(r_ovl[i] > 0.0)) continue;
+    num += eps_acc[i] * std::log2(r_ovl[i]);
+    den += eps_acc[i] * eps_acc[i];
+  }
+  return den > 0.0 ? -num / den : NAN;
+}
+
 }  // extern "C"

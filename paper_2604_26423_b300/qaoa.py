@@ -30,7 +30,8 @@ EXPORTS = ("qaoa_state_bytes", "qaoa_aux_bytes", "qaoa_init_graph", "qaoa_run", 
            "qaoa_last_error", "qaoa_free", "qaoa_sample_state_noalloc",
            "qaoa_batch_create", "qaoa_batch_run", "qaoa_batch_results", "qaoa_batch_state",
            "qaoa_batch_describe", "qaoa_batch_bytes", "qaoa_batch_last_error", "qaoa_batch_free",
-           "qaoa_sample_cuts", "qaoa_mean_of_means", "qaoa_classify_regime")
+           "qaoa_sample_cuts", "qaoa_mean_of_means", "qaoa_classify_regime", "qaoa_noisy_expect",
+           "qaoa_overlap_ratio", "qaoa_fit_k0")
 PROFILE_KINDS = {"pass": 0, "adjoint": 1, "cost": 2, "sample": 3, "small": 4}
 
 _lib = None
@@ -95,6 +96,12 @@ def load():
     lib.qaoa_batch_free.restype = None
     lib.qaoa_sample_cuts.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_uint64, vp, vp, vp]
     lib.qaoa_mean_of_means.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp, vp, vp]
+    lib.qaoa_noisy_expect.argtypes = [vp, ctypes.c_int, f64p, f64p, ctypes.c_double, ctypes.c_int, ctypes.c_uint64,
+                                      vp, f64p, f64p]
+    lib.qaoa_overlap_ratio.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.qaoa_overlap_ratio.restype = ctypes.c_double
+    lib.qaoa_fit_k0.argtypes = [ctypes.c_int, f64p, f64p]
+    lib.qaoa_fit_k0.restype = ctypes.c_double
     lib.qaoa_classify_regime.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_double]
     _lib = lib
@@ -308,6 +315,35 @@ class Simulator:
                                                ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(c.data_ptr()),
                                                ctypes.c_void_p(r.data_ptr())))
         return dict(x=x, c=c, r=r)
+
+    def noisy_expect(self, gamma, beta, eps: float, trajectories: int, seed: int = 0) -> dict:
+        """Noisy LR-QAOA (Sec. II-C) by `trajectories` Monte Carlo trajectories with
+        explicit angles: the mean <C>, r, and each trajectory's <C> (CUDA tensor)."""
+        import torch
+        g, gp = _f64(gamma)
+        b, bp = _f64(beta)
+        if len(g) != len(b):
+            raise ValueError("gamma and beta must have the same length")
+        per = torch.empty(int(trajectories), dtype=torch.float64, device="cuda")
+        mean, r = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.qaoa_noisy_expect(self._ctx, len(g), gp, bp, float(eps), int(trajectories),
+                                                ctypes.c_uint64(seed), ctypes.c_void_p(per.data_ptr()),
+                                                ctypes.byref(mean), ctypes.byref(r)))
+        return dict(exp_c=mean.value, r=r.value, per_trajectory=per)
+
+
+def overlap_ratio(r_noisy: float, r_ideal: float, r_random: float) -> float:
+    """r_ovl = (r_noisy - r_random) / (r_ideal - r_random) (Sec. II-C)."""
+    return float(load().qaoa_overlap_ratio(float(r_noisy), float(r_ideal), float(r_random)))
+
+
+def fit_k0(eps_acc, r_ovl) -> float:
+    """k0 of Eq. noise (r_ovl = 2^(-k0 eps_acc)), least squares through the origin on log2 r_ovl."""
+    a, ap = _f64(eps_acc)
+    r, rp = _f64(r_ovl)
+    if len(a) != len(r):
+        raise ValueError("eps_acc and r_ovl must have the same length")
+    return float(load().qaoa_fit_k0(len(a), ap, rp))
 
 
 def mean_of_means(r, ns: int, reps: int = 100, seed: int = 0, stream=None) -> dict:

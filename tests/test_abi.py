@@ -154,3 +154,12 @@ def test_mean_of_means_rejects_bad_sizes(lib):
     assert lib.qaoa_mean_of_means(one, 10, 2, 0, 0, one, one, None) == qaoa.QAOA_EINVAL
     assert lib.qaoa_mean_of_means(one, 1 << 32, 2, 2, 0, one, one, None) == qaoa.QAOA_EINVAL
     assert lib.qaoa_sample_cuts(None, 1, None, 0, None, None, None) == qaoa.QAOA_EINVAL
+
+
+def test_overlap_and_k0_match_oracle(lib):
+    import oracle
+    assert qaoa.overlap_ratio(0.85, 0.9, 0.8) == oracle.overlap_ratio(0.85, 0.9, 0.8)
+    a = np.array([0.05, 0.3, 0.7, 1.1, 2.5])
+    r = np.array([0.97, 0.8, 0.61, 0.4, -0.02])
+    assert abs(qaoa.fit_k0(a, r) - oracle.fit_k0(a, r)) < 1e-14
+    assert np.isnan(qaoa.fit_k0([1.0], [-1.0]))

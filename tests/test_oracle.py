@@ -411,3 +411,61 @@ def test_classify_regime_cases():
     assert oracle.classify_regime(0.83, 0.79, 0.01) == A
     assert oracle.classify_regime(0.83, 0.79, float("nan")) == -1
     assert oracle.classify_regime(0.83, 0.79, 0.01, 0.88, -1.0) == -1
+
+
+# ---------------------------------------------------------------- Sec. II-C
+def test_noisy_density_closed_forms():
+    # one edge, p = 1: the channel after the only ZZ gate mixes the ideal state
+    # with I/4, which the mixer leaves alone: <C> = (1 - eps) <C>_ideal + eps w / 2
+    u, v, w = [0], [1], [3]
+    g, b = oracle.lr_schedule(1, 0.6, 0.3)
+    ideal = oracle.run(2, u, v, w, 0.1, g, b)["exp_c"]
+    for eps in (0.0, 0.3, 1.0):
+        assert abs(oracle.noisy_density(2, u, v, w, 0.1, g, b, eps) - ((1 - eps) * ideal + eps * 1.5)) < 1e-12
+    # eps = 0 is the pure-state circuit; eps = 1 on K_n ends maximally mixed (<C> = W/2)
+    n = 4
+    u, v, w = inputs.complete_graph(n, 9)
+    g, b = oracle.lr_schedule(2, 0.6, 0.3)
+    assert abs(oracle.noisy_density(n, u, v, w, 0.1, g, b, 0.0) - oracle.run(n, u, v, w, 0.1, g, b)["exp_c"]) < 1e-11
+    assert abs(oracle.noisy_density(n, u, v, w, 0.1, g, b, 1.0) - np.sum(w) / 2) < 1e-11
+
+
+def test_depolarizing_pauli_sum_is_partial_trace():
+    # (1/16) sum_P P rho P over the Paulis on (i, j) = I/4 (x) Tr_ij rho
+    n, i, j = 3, 0, 2
+    rng = inputs.uniforms(31, 2 * 64).reshape(2, 8, 8)
+    a = rng[0] + 1j * rng[1]
+    rho = a @ a.conj().T
+    rho /= np.trace(rho)
+    acc = np.zeros_like(rho)
+    for pa in range(4):
+        for pb in range(4):
+            P = oracle._pauli_matrix(n, i, pa) @ oracle._pauli_matrix(n, j, pb)
+            acc += P @ rho @ P.conj().T
+    # index bits (b2 b1 b0) = qubits (2, 1, 0); reshape as [q2, q1, q0] x [q2, q1, q0]
+    t = rho.reshape(2, 2, 2, 2, 2, 2)
+    red = np.einsum("abcadc->bd", t)        # trace over qubits 2 and 0, keep qubit 1
+    want = np.einsum("ac,bd,ef->abecdf", np.eye(2) / 2, red, np.eye(2) / 2).reshape(8, 8)
+    assert np.allclose(acc / 16, want, atol=1e-14)
+
+
+def test_noisy_trajectories_average_to_density():
+    n, p, eps = 4, 2, 0.08
+    u, v, w = inputs.complete_graph(n, 5)
+    g, b = oracle.lr_schedule(p, 0.6, 0.3)
+    exact = oracle.noisy_density(n, u, v, w, 0.1, g, b, eps)
+    cut = oracle.cut_values(n, u, v, w)
+    vals = np.array([np.sum(np.abs(oracle.noisy_trajectory(n, u, v, w, 0.1, g, b, eps, 7, t)) ** 2 * cut)
+                     for t in range(3000)])
+    assert abs(vals.mean() - exact) < 5 * vals.std() / math.sqrt(len(vals))
+    # no error at eps = 0: the noiseless state
+    psi = oracle.noisy_trajectory(n, u, v, w, 0.1, g, b, 0.0, 7, 0)
+    assert np.max(np.abs(psi - oracle.simulate(n, u, v, w, 0.1, g, b))) < 1e-12
+
+
+def test_overlap_and_k0_fit():
+    assert oracle.overlap_ratio(0.85, 0.9, 0.8) == (0.85 - 0.8) / (0.9 - 0.8)
+    a = np.array([0.1, 0.5, 1.0, 2.0])
+    assert abs(oracle.fit_k0(a, 2.0 ** (-1.7 * a)) - 1.7) < 1e-12
+    # points at or below zero (random or worse) are left out
+    assert abs(oracle.fit_k0(np.append(a, 3.0), np.append(2.0 ** (-0.4 * a), -0.01)) - 0.4) < 1e-12
