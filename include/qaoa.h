@@ -61,6 +61,25 @@ typedef struct qaoa_ctx qaoa_ctx;
 size_t qaoa_state_bytes(int n, int precision);
 
 /*
+ * Largest sum of |w| that qaoa_init_graph accepts: 2^30 - 1 for complex64 with
+ * n >= 13 (the passes take the cost phase from 64-bit fixed-point turn
+ * products of the integer cut value), 2^20 otherwise (a phase table indexed
+ * by C(x)).
+ */
+int64_t qaoa_max_weight_sum(int n, int precision);
+
+/*
+ * Real-valued weights (Sec. II-G: the paper's instances have weights in
+ * U[0, 1]) as integers for qaoa_init_graph: *unit = sum |w| / (max_abs_sum - m)
+ * and w_int[e] = round(w[e] / unit), so sum |w_int| <= max_abs_sum and every
+ * weight is off by at most unit / 2. Initialise with weight_scale s * unit to
+ * keep the phases exp(-i gamma s w); cut values and <C> from the library are
+ * then in units of `unit`. Host only. Errors: EINVAL (m < 1, a zero or
+ * non-finite weight, a weight below unit / 2, max_abs_sum outside (2m, 2^31)).
+ */
+int qaoa_quantize_weights(int m, const double *w, int64_t max_abs_sum, int32_t *w_int, double *unit);
+
+/*
  * Bytes of the optional auxiliary device buffer: the adjoint vector lambda
  * (one state's worth, needed by qaoa_grad) followed by the int32 cost diagonal
  * (2^n * 4 bytes, needed by QAOA_COST_STREAM). with_grad selects the first part,
@@ -72,7 +91,8 @@ size_t qaoa_aux_bytes(int n, int precision, int cost_mode, int with_grad);
  * Creates a context for one graph (Sec. II-B: weighted MaxCut instance).
  *   n            qubits = vertices, 1 <= n <= QAOA_MAX_QUBITS_*.
  *   n_edges      number of edges m >= 0; u[e] != v[e], both in [0, n), no
- *                repeated pair, w[e] != 0, sum |w| < 2^31. Host arrays of
+ *                repeated pair, w[e] != 0, sum |w| <= qaoa_max_weight_sum(n,
+ *                precision). Host arrays of
  *                length m, copied; the caller keeps ownership.
  *   weight_scale s > 0 in the phases exp(-i gamma s h(x)); <C>, C_min and C_max
  *                are reported in integer weight units.

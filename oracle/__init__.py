@@ -9,7 +9,8 @@ builds the per-gate angles from the paper's schedule and wraps the results.
 Every function names the passage of the paper it follows:
 
 * ``lr_schedule``      -- Sec. II-B, linear schedules for beta_i and gamma_i.
-* ``cut_values``       -- Sec. II-B, Eq. for C(x) (literal double sum).
+* ``cut_values``       -- Sec. II-B, Eq. for C(x) (literal double sum);
+  ``cut_values_real`` the same with real weights (Sec. II-G).
 * ``extremes``         -- Sec. II-B, C(x*) = max cut; here by exhaustive search.
 * ``simulate``         -- Sec. II-B Eqs. H_C, UC, UB; gates as in Sec. II-E.
 * ``expectation``      -- <C> = sum |psi_x|^2 C(x); r as in Eq. r with the
@@ -112,6 +113,16 @@ def cut_values(n: int, u, v, w) -> np.ndarray:
                                    _ptr(w, ctypes.c_int32), _ptr(out, ctypes.c_int64))
     if rc:
         raise ValueError("oracle_cut_values rejected its arguments")
+    return out
+
+
+def cut_values_real(n: int, u, v, w) -> np.ndarray:
+    """C(x) with real weights (Sec. II-G: U[0, 1] in the paper), float64, all x:
+    sum over edges of w_e [x_u != x_v], edge by edge."""
+    x = np.arange(1 << n, dtype=np.int64)
+    out = np.zeros(1 << n)
+    for a, b, we in zip(u, v, w):
+        out += float(we) * (((x >> int(a)) ^ (x >> int(b))) & 1)
     return out
 
 

@@ -40,7 +40,12 @@ constexpr int kR = 5, kWB = 3;           // forward tile: 2^5 registers x 32 lan
 constexpr int kRAdj = 4, kWBAdj = 3;     // adjoint tile: psi and lambda, 2^4 registers each
 constexpr int kSmaxAdj = 12;             // adjoint super-tile: one tile of psi and lambda
 constexpr int kMinUnitsLog2 = 9;         // keep >= 512 super-tiles when n allows
+// Largest sum of |w|: 2^20 where the cost phase comes from a table indexed by
+// C(x) (complex128, and the whole-circuit kernels of n <= 12); 2^30 - 1 for
+// complex64 passes, whose phase comes from 64-bit fixed-point turn products of
+// the integer C(x) (the first pass's extremes keys hold C - C_min in 30 bits).
 constexpr long long kMaxAbsWeightSum = 1 << 20;
+constexpr long long kMaxAbsWeightSumTurns = (1ll << 30) - 1;
 constexpr int kMaxGrid = 4096;           // persistent grid cap (partial-sum buffer size)
 constexpr int kFuseSumsMinQubits = 26;   // final pass writes sampling block sums from here on
 constexpr int kGroupOrder = ORDER_LOW_LAST;  // default group order of the pass plans
@@ -274,7 +279,11 @@ int tile_const_table(qaoa_ctx* c, const PassDev& pd, SubDev& sd) {
 
 // Phase tables exp(-i gamma_k s (W - 2c)) for c in [c_lo, c_hi], FP64 on the
 // host, rounded to the state precision (h(x) = W - 2 C(x), Eqs. H_C and UC).
+// Whether any kernel of this context reads the phase table (see kMaxAbsWeightSum).
+bool phase_table_needed(const qaoa_ctx* c) { return c->prec == QAOA_C128 || c->n <= kSmallMaxQubits; }
+
 int upload_phases(qaoa_ctx* c, int p, const double* gamma) {
+  if (!phase_table_needed(c)) return QAOA_OK;
   const long long nc = c->c_hi - c->c_lo + 1;
   const int ab = amp_bytes(c->prec);
   std::vector<unsigned char> host((size_t)std::max(1, p) * nc * ab);
@@ -544,7 +553,8 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
     if (pa.out != pa.state && pd.nsub != 1)
       return c->set_err(QAOA_EINVAL, "a pass of several sub-passes cannot write to another buffer");
     pa.diag = stream ? (const int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n))) : nullptr;
-    pa.phase = pp.layer_c >= 0 ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_c) * nc * ab) : nullptr;
+    pa.phase = pp.layer_c >= 0 && c->d_phase.p
+                   ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_c) * nc * ab) : nullptr;
     pa.wmat = (const int32_t*)c->d_wmat.p;
     pa.ctabs = (const int32_t*)c->d_ctabs.p;
     pa.phase_in_smem = tab_smem ? 1 : 0;
@@ -845,7 +855,8 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     aa.psi_store = outs.empty() ? 1 : 0;
     aa.lam = lam;
     aa.diag = stream ? (const int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n))) : nullptr;
-    aa.phase = pp.layer_c >= 0 ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_c) * nc * ab) : nullptr;
+    aa.phase = pp.layer_c >= 0 && c->d_phase.p
+                   ? (const void*)((const char*)c->d_phase.p + size_t(pp.layer_c) * nc * ab) : nullptr;
     aa.wmat = (const int32_t*)c->d_wmat.p;
     aa.ctabs = (const int32_t*)c->d_ctabs.p;
     aa.partial = (double*)c->d_partial.p;
@@ -971,6 +982,28 @@ size_t qaoa_state_bytes(int n, int precision) {
   return (size_t(1) << n) * amp_bytes(precision);
 }
 
+int64_t qaoa_max_weight_sum(int n, int precision) {
+  return precision == QAOA_C64 && n > kSmallMaxQubits ? kMaxAbsWeightSumTurns : kMaxAbsWeightSum;
+}
+
+int qaoa_quantize_weights(int m, const double* w, int64_t max_abs_sum, int32_t* w_int, double* unit) {
+  if (m < 1 || !w || !w_int || !unit || max_abs_sum <= 2ll * m || max_abs_sum > INT32_MAX) return QAOA_EINVAL;
+  double sum = 0.0;
+  for (int e = 0; e < m; ++e) {
+    if (!std::isfinite(w[e]) || w[e] == 0.0) return QAOA_EINVAL;
+    sum += std::fabs(w[e]);
+  }
+  // rounding adds at most 1/2 per edge: sum |w_int| <= (max_abs_sum - m) + m / 2
+  const double u = sum / double(max_abs_sum - m);
+  for (int e = 0; e < m; ++e) {
+    const long long q = std::llround(w[e] / u);
+    if (q == 0) return QAOA_EINVAL;  // |w_e| below half a unit: the edge would vanish
+    w_int[e] = (int32_t)q;
+  }
+  *unit = u;
+  return QAOA_OK;
+}
+
 size_t qaoa_aux_bytes(int n, int precision, int cost_mode, int with_grad) {
   const size_t sb = qaoa_state_bytes(n, precision);
   if (!sb) return 0;
@@ -1000,7 +1033,7 @@ int qaoa_init_graph(qaoa_ctx** out, int n, int m, const int32_t* u, const int32_
   std::vector<int32_t> wmat;
   long long W = 0, pos = 0, neg = 0;
   {
-    const std::string why = check_graph(n, m, u, v, w, kMaxAbsWeightSum, wmat, W, neg, pos);
+    const std::string why = check_graph(n, m, u, v, w, qaoa_max_weight_sum(n, precision), wmat, W, neg, pos);
     if (!why.empty()) return fail(QAOA_EINVAL, why);
   }
   if (state_dev && state_bytes != sb)

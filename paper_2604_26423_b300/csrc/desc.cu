@@ -108,7 +108,7 @@ std::string check_graph(int n, int m, const int32_t* u, const int32_t* v, const 
     if (!seen.insert(key).second) return "repeated edge";
     W += w[e];
     if (w[e] > 0) c_hi += w[e]; else c_lo += w[e];
-    if (c_hi - c_lo > max_abs) return "sum of |w| exceeds 2^20";
+    if (c_hi - c_lo > max_abs) return "sum of |w| exceeds the limit " + std::to_string(max_abs);
   }
   wmat.assign((size_t)n * n, 0);
   for (int e = 0; e < m; ++e) {

@@ -31,7 +31,7 @@ EXPORTS = ("qaoa_state_bytes", "qaoa_aux_bytes", "qaoa_init_graph", "qaoa_run", 
            "qaoa_batch_create", "qaoa_batch_run", "qaoa_batch_results", "qaoa_batch_state",
            "qaoa_batch_describe", "qaoa_batch_bytes", "qaoa_batch_last_error", "qaoa_batch_free",
            "qaoa_sample_cuts", "qaoa_mean_of_means", "qaoa_classify_regime", "qaoa_noisy_expect",
-           "qaoa_overlap_ratio", "qaoa_fit_k0")
+           "qaoa_overlap_ratio", "qaoa_fit_k0", "qaoa_max_weight_sum", "qaoa_quantize_weights")
 PROFILE_KINDS = {"pass": 0, "adjoint": 1, "cost": 2, "sample": 3, "small": 4}
 
 _lib = None
@@ -96,6 +96,9 @@ def load():
     lib.qaoa_batch_free.restype = None
     lib.qaoa_sample_cuts.argtypes = [vp, ctypes.c_int64, vp, ctypes.c_uint64, vp, vp, vp]
     lib.qaoa_mean_of_means.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, vp, vp, vp]
+    lib.qaoa_max_weight_sum.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.qaoa_max_weight_sum.restype = ctypes.c_int64
+    lib.qaoa_quantize_weights.argtypes = [ctypes.c_int, f64p, ctypes.c_int64, i32p, f64p]
     lib.qaoa_noisy_expect.argtypes = [vp, ctypes.c_int, f64p, f64p, ctypes.c_double, ctypes.c_int, ctypes.c_uint64,
                                       vp, f64p, f64p]
     lib.qaoa_overlap_ratio.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -129,6 +132,22 @@ def describe_plan(n: int, p: int, precision="c64", adjoint=False) -> str:
     return buf.value.decode()
 
 
+def max_weight_sum(n: int, precision="c64") -> int:
+    return int(load().qaoa_max_weight_sum(int(n), _PREC[precision]))
+
+
+def quantize_weights(w, max_abs_sum: int):
+    """Real weights as integers (``qaoa_quantize_weights``): returns (w_int, unit)."""
+    wa, wp = _f64(w)
+    out = np.empty(len(wa), dtype=np.int32)
+    unit = ctypes.c_double()
+    rc = load().qaoa_quantize_weights(len(wa), wp, int(max_abs_sum),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(unit))
+    if rc:
+        raise QaoaError(rc, "weights cannot be quantised (zero, non-finite or too small against their sum)")
+    return out, unit.value
+
+
 def lr_angles(p: int, dgamma: float, dbeta: float):
     """Linear-ramp angles gamma_k = (k+1)/p dgamma, beta_k = (1 - k/p) dbeta (Sec. II-B)."""
     k = np.arange(p, dtype=np.float64)
@@ -153,6 +172,7 @@ class Simulator:
         self.precision = _PREC[precision]
         self.cost_mode = _COST[cost_mode]
         self.with_grad = bool(with_grad)
+        self.unit = 1.0  # real weight per integer weight unit (from_real_weights)
         u = np.ascontiguousarray(u, dtype=np.int32)
         v = np.ascontiguousarray(v, dtype=np.int32)
         w = np.ascontiguousarray(w, dtype=np.int32)
@@ -185,6 +205,17 @@ class Simulator:
         self._lib = lib
 
     # -- helpers
+    @classmethod
+    def from_real_weights(cls, n, u, v, w_real, scale=1.0, precision="c64", **kw):
+        """An instance with real weights (Sec. II-G, U[0, 1] in the paper): the
+        weights are quantised with the largest integer sum the path accepts,
+        the phase scale absorbs the unit, and ``unit`` converts cut values and
+        <C> back (real = integer x unit). Each weight is off by at most unit / 2."""
+        w_int, unit = quantize_weights(w_real, max_weight_sum(n, precision))
+        sim = cls(n, u, v, w_int, scale * unit, precision, **kw)
+        sim.unit = unit
+        return sim
+
     def _check(self, rc):
         if rc != QAOA_OK:
             raise QaoaError(rc, self._lib.qaoa_last_error(self._ctx).decode())

@@ -163,3 +163,29 @@ def test_overlap_and_k0_match_oracle(lib):
     r = np.array([0.97, 0.8, 0.61, 0.4, -0.02])
     assert abs(qaoa.fit_k0(a, r) - oracle.fit_k0(a, r)) < 1e-14
     assert np.isnan(qaoa.fit_k0([1.0], [-1.0]))
+
+
+def test_weight_limits_and_quantisation(lib):
+    assert qaoa.max_weight_sum(33, "c64") == (1 << 30) - 1
+    assert qaoa.max_weight_sum(12, "c64") == 1 << 20
+    assert qaoa.max_weight_sum(20, "c128") == 1 << 20
+    w = np.concatenate([inputs_uniforms(3, 500), [1e-3, -0.7]])
+    for limit in ((1 << 30) - 1, 1 << 20):
+        wi, unit = qaoa.quantize_weights(w, limit)
+        assert np.abs(wi).sum() <= limit
+        assert np.max(np.abs(wi * unit - w)) <= 0.5 * unit * (1 + 1e-12)
+        assert np.all(np.sign(wi) == np.sign(w))
+    with pytest.raises(qaoa.QaoaError):
+        qaoa.quantize_weights([1.0, 0.0], 1 << 20)
+    with pytest.raises(qaoa.QaoaError):
+        qaoa.quantize_weights([1.0, float("nan")], 1 << 20)
+    with pytest.raises(qaoa.QaoaError):
+        qaoa.quantize_weights([1.0, 1e-9], 1 << 20)   # below half a unit
+    # the limit is enforced at init: 2^20 + 1 on a table path
+    rc, ctx, msg = _init(lib, 5, [0, 1], [1, 2], [1 << 20, 1], 0.1, 0, 1)
+    assert rc == qaoa.QAOA_EINVAL and "exceeds" in msg
+
+
+def inputs_uniforms(seed, count):
+    from paper_2604_26423_b300 import inputs
+    return inputs.uniforms(seed, count)

@@ -10,6 +10,8 @@ Tolerances (from the arithmetic):
 * shots (c128, shared uniforms): identical except where u * total falls within
   1e-9 (relative) of a CDF step, where both answers are valid.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -366,3 +368,46 @@ def test_extremes_from_first_pass(n, kind, prec, smax, monkeypatch):
     cmin, cmax, amin, amax = oracle.extremes(n, ref)
     for ext in (before, after):
         assert (ext["c_min"], ext["c_max"], ext["argmin"], ext["argmax"]) == (cmin, cmax, amin, amax)
+
+
+@pytest.mark.parametrize("n,prec", [(16, "c64"), (20, "c64"), (14, "c128"), (10, "c64")])
+def test_real_weights_vs_oracle(n, prec):
+    # the paper's instances: K_n with weights uniform on [0, 1] and phases
+    # exp(-i gamma w) (s = 1), dgamma = dbeta = 0.2 (Sec. II-G). The library
+    # runs the weights quantised to the largest integer sum its path accepts
+    # (unit u, each weight off by at most u / 2); the oracle runs the real
+    # weights. Phase error per amplitude <= sum_k gamma_k m u / 2.
+    from paper_2604_26423_b300.qaoa import Simulator
+    u, v, _ = inputs.complete_graph(n, 5000 + n)
+    w = inputs.uniforms(5001 + n, len(u))
+    p = 4
+    g, b = oracle.lr_schedule(p, 0.2, 0.2)
+    psi_o = oracle.simulate(n, u, v, w, 1.0, g, b)
+    cut = oracle.cut_values_real(n, u, v, w)
+    exp_o = float(np.sum(np.abs(psi_o) ** 2 * cut))
+    r_o = (exp_o - cut.min()) / (cut.max() - cut.min())
+    with Simulator.from_real_weights(n, u, v, w, 1.0, prec) as s:
+        s.run_angles(g, b)
+        res = s.expect()
+        psi = s.state().cpu().numpy().astype(np.complex128)
+        unit = s.unit
+    bound = float(np.sum(g)) * len(u) * unit / 2
+    tol = bound + (2e-6 if prec == "c64" else 1e-12) * math.sqrt(n)
+    assert np.linalg.norm(psi - psi_o) <= tol
+    assert abs(res["exp_c"] * unit - exp_o) <= 2 * tol * cut.max() + len(u) * unit
+    assert abs(res["r"] - r_o) <= 4 * tol + 2 * len(u) * unit / (cut.max() - cut.min())
+
+
+def test_real_weights_k33_single_layer():
+    # full size: K_33 with U[0, 1] weights, p = 1, against the closed-form
+    # single-layer expectation of the real-weight instance
+    from paper_2604_26423_b300.qaoa import Simulator
+    n = 33
+    u, v, _ = inputs.complete_graph(n, 5033)
+    w = inputs.uniforms(5034, len(u))
+    gamma, beta = 0.35, 0.25
+    want = oracle.analytic_p1_expectation(n, u, v, w, 1.0, gamma, beta)
+    with Simulator.from_real_weights(n, u, v, w, 1.0, "c64") as s:
+        s.run_angles([gamma], [beta])
+        got = s.expect()["exp_c"] * s.unit
+    assert abs(got - want) <= 5e-5 * abs(want)

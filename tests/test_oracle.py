@@ -469,3 +469,12 @@ def test_overlap_and_k0_fit():
     assert abs(oracle.fit_k0(a, 2.0 ** (-1.7 * a)) - 1.7) < 1e-12
     # points at or below zero (random or worse) are left out
     assert abs(oracle.fit_k0(np.append(a, 3.0), np.append(2.0 ** (-0.4 * a), -0.01)) - 0.4) < 1e-12
+
+
+def test_cut_values_real():
+    # integer weights: the integer table; a real-weight triangle by hand
+    n = 6
+    u, v, w = inputs.complete_graph(n, 66)
+    assert np.array_equal(oracle.cut_values_real(n, u, v, w), oracle.cut_values(n, u, v, w).astype(float))
+    c = oracle.cut_values_real(3, [0, 1, 0], [1, 2, 2], [0.25, 0.5, 0.125])
+    assert np.allclose(c, [0, 0.375, 0.75, 0.625, 0.625, 0.75, 0.375, 0])
