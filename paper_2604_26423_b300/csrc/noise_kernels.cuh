@@ -24,6 +24,7 @@ namespace qaoa {
 constexpr int kNoisyMaxQubits = 12;
 constexpr int kNoisyMaxEdges = kNoisyMaxQubits * (kNoisyMaxQubits - 1) / 2;
 constexpr int kNoisyThreads = 256;
+constexpr int kNoisyLowBits = kNoisyMaxQubits - 8;  // log2(2^12 / kNoisyThreads)
 
 struct NoisyArgs {
   int n = 0, m = 0, p = 0, trajectories = 0;
@@ -45,11 +46,15 @@ static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(
   double2* phi = reinterpret_cast<double2*>(nsm);
   int* cut = reinterpret_cast<int*>(phi + N);
   __shared__ double sig[kNoisyMaxEdges];
+  __shared__ double sgn[kNoisyMaxEdges];
+  __shared__ double all[1 << kNoisyLowBits];
   __shared__ double tau[kNoisyMaxQubits];
   __shared__ unsigned fxs;
   __shared__ int su[kNoisyMaxEdges], sv[kNoisyMaxEdges];
   __shared__ double red[2 * kNoisyThreads / 32];
   const int tid = threadIdx.x;
+  // low bits per thread: L = 2^lb consecutive amplitudes (16 at n = 12)
+  const int lb = n > 8 ? n - 8 : 0, L = 1 << lb;
   for (int e = tid; e < m; e += kNoisyThreads) {
     su[e] = a.u[e];
     sv[e] = a.v[e];
@@ -83,18 +88,46 @@ static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(
         for (int q = 0; q < n; ++q) tau[q] = (fz >> q & 1u) ? -1.0 : 1.0;
       }
       __syncthreads();
-      // cost layer with the frame's signs: phi_x *= exp(-i sum_e sigma_e theta_e z_i z_j)
+      // cost layer with the frame's signs: phi_x *= exp(-i sum_e s_e z_a z_b),
+      // s_e = sigma_e theta_e. A thread owns L = 2^lb consecutive x = x0 + j:
+      //   angle = A_hh(x0) + A_ll(j) + sum_{i < lb} z_i(j) h_i(x0)
+      // with A_hh the edges among bits >= lb, A_ll (a table per layer) those
+      // among bits < lb, and h_i the cross edges of low bit i.
       const double* th = a.theta + (size_t)k * m;
-      for (int x = tid; x < N; x += kNoisyThreads) {
-        double ang = 0.0;
+      for (int e = tid; e < m; e += kNoisyThreads) sgn[e] = sig[e] * th[e];
+      __syncthreads();
+      if (tid < L) {
+        double al = 0.0;
+        for (int e = 0; e < m; ++e)
+          if (su[e] < lb && sv[e] < lb) al += (((tid >> su[e]) ^ (tid >> sv[e])) & 1) ? -sgn[e] : sgn[e];
+        all[tid] = al;
+      }
+      __syncthreads();
+      const int x0 = tid * L;
+      if (x0 < N) {
+        double ahh = 0.0, h[kNoisyLowBits] = {0.0, 0.0, 0.0, 0.0};
         for (int e = 0; e < m; ++e) {
-          const double s = (((x >> su[e]) ^ (x >> sv[e])) & 1) ? -sig[e] : sig[e];
-          ang = fma(s, th[e], ang);
+          const int ea = su[e], eb = sv[e];
+          const double se = sgn[e];
+          if (ea >= lb && eb >= lb) {
+            ahh += (((x0 >> ea) ^ (x0 >> eb)) & 1) ? -se : se;
+          } else if (ea >= lb || eb >= lb) {
+            const int lo = ea < lb ? ea : eb, hi = ea < lb ? eb : ea;
+#pragma unroll
+            for (int i = 0; i < kNoisyLowBits; ++i)
+              if (i == lo) h[i] += (x0 >> hi & 1) ? -se : se;
+          }
         }
-        double sn, cs;
-        sincos(ang, &sn, &cs);
-        const double2 f = phi[x];
-        phi[x] = make_double2(f.x * cs + f.y * sn, f.y * cs - f.x * sn);
+        for (int j = 0; j < L; ++j) {
+          double ang = ahh + all[j];
+#pragma unroll
+          for (int i = 0; i < kNoisyLowBits; ++i)
+            if (i < lb) ang += (j >> i & 1) ? -h[i] : h[i];
+          double sn, cs;
+          sincos(ang, &sn, &cs);
+          const double2 f = phi[x0 + j];
+          phi[x0 + j] = make_double2(f.x * cs + f.y * sn, f.y * cs - f.x * sn);
+        }
       }
       // mixer exp(+i tau_q beta_k X_q), qubit by qubit
       double sb, cb;
