@@ -30,8 +30,8 @@ phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
   random sampler; kernel time, bitstrings/s), the ratios of the step's 4096
   shots, the mean of 100 subsample means at 10 and 100 shots for both, and the
   regime of the first 10 shots.
-* ``noise``: noisy LR-QAOA (Sec. II-C) on K_12, p = 10, complex128: 4096
-  depolarizing-channel trajectories per rate, trajectories/s of the kernel, the
+* ``noise``: noisy LR-QAOA (Sec. II-C) on K_12, p = 10, complex64 (one rate
+  also in complex128): 4096 depolarizing-channel trajectories per rate, trajectories/s of the kernel, the
   noisy r, r_ovl and the k0 fit of Eq. noise.
 * ``--qubits n`` runs the same step on K_n (smaller cases for profiling; the
   JSON line then names that workload).
@@ -343,18 +343,27 @@ def stats_bench(sim, shots, stream, pool: int = 1 << 26):
 
 def noise_bench(args, trajectories: int = 4096):
     """Noisy LR-QAOA (Sec. II-C) on K_12, p = 10: `trajectories` Monte Carlo
-    trajectories per depolarizing rate (complex128, one CTA each, kernel timed
+    trajectories per depolarizing rate (complex64, one CTA each, kernel timed
     with CUDA events), the noisy r, the overlap ratio r_ovl against the
-    noiseless r and the random sampler's, and the fit of Eq. noise."""
+    noiseless r and the random sampler's, and the fit of Eq. noise; the same
+    trajectories of one rate also in complex128."""
     from paper_2604_26423_b300 import inputs
     from paper_2604_26423_b300.qaoa import Simulator, fit_k0, lr_angles, overlap_ratio
 
     n, p = 12, 10
     u, v, w = inputs.complete_graph(n, SEED)
     g, b = lr_angles(p, DGAMMA, DBETA)
-    out = {"workload": f"K_{n} (seed {SEED}), p={p}, dgamma={DGAMMA}, dbeta={DBETA}, complex128, "
+    out = {"workload": f"K_{n} (seed {SEED}), p={p}, dgamma={DGAMMA}, dbeta={DBETA}, complex64, "
                        f"{trajectories} trajectories per rate", "rates": []}
     with Simulator(n, u, v, w, SCALE, "c128") as s:
+        s.noisy_expect(g, b, 0.002, 64, seed=1)  # warm-up
+        s.profile(True)
+        res = s.noisy_expect(g, b, 0.002, trajectories, seed=SEED)
+        k = s.profile_read("small")
+        s.profile(False)
+        out["complex128_eps_0.002"] = {"r_noisy": res["r"], "kernel_ms": k["ms"],
+                                       "trajectories_per_s": trajectories / (k["ms"] * 1e-3)}
+    with Simulator(n, u, v, w, SCALE, "c64") as s:
         ext = s.extremes()
         r_rand = (float(np.sum(w)) / 2 - ext["c_min"]) / (ext["c_max"] - ext["c_min"])
         s.noisy_expect(g, b, 0.0, 64, seed=1)  # warm-up

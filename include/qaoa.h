@@ -308,7 +308,8 @@ void qaoa_batch_free(qaoa_batch *b);
 /*
  * Monte Carlo trajectories of the noisy circuit with explicit angles gamma,
  * beta (p each, host; the LR schedule is qaoa_run's) on the context's graph,
- * n <= QAOA_NOISY_MAX_QUBITS, complex128 arithmetic. Trajectory t draws, for
+ * n <= QAOA_NOISY_MAX_QUBITS, in the context's precision (complex64: FP32
+ * phases and butterflies; <C>_t always summed in FP64). Trajectory t draws, for
  * gate g = k m + e (layer k, edge e in the order given to qaoa_init_graph),
  * draw t (p m) + g of SplitMix64 stream `seed`: an error when its top 53 bits
  * times 2^-53 are below eps, then Pauli (draw & 3) on u_e and ((draw >> 2) & 3)

@@ -1304,6 +1304,7 @@ int qaoa_noisy_expect(qaoa_ctx* c, int p, const double* gamma, const double* bet
                       uint64_t seed, double* exp_c_dev, double* mean_exp_c, double* r_noisy) {
   if (!c) return QAOA_EINVAL;
   const int n = c->n, m = c->m;
+  const int ab = amp_bytes(c->prec) / 2;  // bytes per real component
   if (n > kNoisyMaxQubits) return c->set_err(QAOA_EINVAL, "noisy trajectories need n <= %d", kNoisyMaxQubits);
   if (p < 0 || (p > 0 && (!gamma || !beta))) return c->set_err(QAOA_EINVAL, "p < 0 or missing angles");
   if (!(eps >= 0.0 && eps <= 1.0)) return c->set_err(QAOA_EINVAL, "eps must lie in [0, 1]");
@@ -1340,14 +1341,18 @@ int qaoa_noisy_expect(qaoa_ctx* c, int p, const double* gamma, const double* bet
   a.seed = seed;
   a.exp_c = out;
   a.norm = nullptr;
-  const size_t smem = (size_t(1) << n) * (16 + 4);
-  CUDA_TRY(c, cudaFuncSetAttribute(noisy_trajectory_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // complex64 contexts run the trajectories in FP32, complex128 in FP64
+  const bool dbl = c->prec == QAOA_C128;
+  const void* kern = dbl ? (const void*)noisy_trajectory_kernel<double> : (const void*)noisy_trajectory_kernel<float>;
+  const size_t smem = (size_t(1) << n) * (size_t(2 * ab) + 4);
+  CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int bps = 0;
-  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, noisy_trajectory_kernel, kNoisyThreads, smem));
+  CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kNoisyThreads, smem));
   const int grid = std::max(1, std::min(trajectories, std::max(1, bps) * c->sms));
   {
     ProfScope ps(c, 4, 0.0);
-    noisy_trajectory_kernel<<<grid, kNoisyThreads, smem, c->stream>>>(a);
+    if (dbl) noisy_trajectory_kernel<double><<<grid, kNoisyThreads, smem, c->stream>>>(a);
+    else noisy_trajectory_kernel<float><<<grid, kNoisyThreads, smem, c->stream>>>(a);
     if (c->prof_on) ++c->nlaunch;
   }
   CUDA_TRY(c, cudaGetLastError());

@@ -1,6 +1,7 @@
 // noise_kernels.cuh -- noisy LR-QAOA (Sec. II-C): a two-qubit depolarizing
 // channel after every ZZ gate, sampled as stochastic trajectories, one CTA per
-// trajectory with the complex128 state of n <= 12 qubits in shared memory.
+// trajectory with the state of n <= 12 qubits in shared memory (complex128, or
+// complex64 with FP32 phases and butterflies; <C>_t and the norm in FP64).
 //
 // A sampled Pauli error is not applied to the state: it is kept in a Pauli
 // frame F (bit masks fx, fz; the state is F|phi> up to a global phase) and
@@ -39,16 +40,21 @@ struct NoisyArgs {
   double* norm = nullptr;            // per trajectory |phi|^2 (1 up to rounding)
 };
 
-// Dynamic shared memory: 2^n double2 state, 2^n int32 cut values.
-static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(const NoisyArgs a) {
+__device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+
+// Dynamic shared memory: 2^n complex state, 2^n int32 cut values.
+template <typename Real>
+__global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(const NoisyArgs a) {
+  using C2 = typename Cx<Real>::T;
   extern __shared__ __align__(16) unsigned char nsm[];
   const int n = a.n, m = a.m, N = 1 << n;
-  double2* phi = reinterpret_cast<double2*>(nsm);
+  C2* phi = reinterpret_cast<C2*>(nsm);
   int* cut = reinterpret_cast<int*>(phi + N);
-  __shared__ double sig[kNoisyMaxEdges];
-  __shared__ double sgn[kNoisyMaxEdges];
-  __shared__ double all[1 << kNoisyLowBits];
-  __shared__ double tau[kNoisyMaxQubits];
+  __shared__ Real sig[kNoisyMaxEdges];
+  __shared__ Real sgn[kNoisyMaxEdges];
+  __shared__ Real all[1 << kNoisyLowBits];
+  __shared__ Real tau[kNoisyMaxQubits];
   __shared__ unsigned fxs;
   __shared__ int su[kNoisyMaxEdges], sv[kNoisyMaxEdges];
   __shared__ double red[2 * kNoisyThreads / 32];
@@ -66,15 +72,18 @@ static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(
     cut[x] = c;
   }
   for (int t = blockIdx.x; t < a.trajectories; t += gridDim.x) {
-    const double amp0 = exp2(-0.5 * n);
-    for (int x = tid; x < N; x += kNoisyThreads) phi[x] = make_double2(amp0, 0.0);
+    const Real amp0 = Real(exp2(-0.5 * n));
+    for (int x = tid; x < N; x += kNoisyThreads) {
+      phi[x].x = amp0;
+      phi[x].y = Real(0);
+    }
     unsigned fx = 0, fz = 0;  // the frame, kept by thread 0
     for (int k = 0; k < a.p; ++k) {
       if (tid == 0) {
         const unsigned long long base = (unsigned long long)t * (unsigned long long)(a.p * m) +
                                         (unsigned long long)(k * m);
         for (int e = 0; e < m; ++e) {
-          sig[e] = (((fx >> su[e]) ^ (fx >> sv[e])) & 1u) ? -1.0 : 1.0;
+          sig[e] = (((fx >> su[e]) ^ (fx >> sv[e])) & 1u) ? Real(-1) : Real(1);
           const unsigned long long d = splitmix_draw(a.seed, base + (unsigned long long)e);
           if (double(d >> 11) * 0x1.0p-53 < a.eps) {
             const unsigned pi = unsigned(d & 3ull), pj = unsigned(d >> 2 & 3ull);
@@ -85,7 +94,7 @@ static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(
             if (pj == 2 || pj == 3) fz ^= 1u << sv[e];
           }
         }
-        for (int q = 0; q < n; ++q) tau[q] = (fz >> q & 1u) ? -1.0 : 1.0;
+        for (int q = 0; q < n; ++q) tau[q] = (fz >> q & 1u) ? Real(-1) : Real(1);
       }
       __syncthreads();
       // cost layer with the frame's signs: phi_x *= exp(-i sum_e s_e z_a z_b),
@@ -94,10 +103,10 @@ static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(
       // with A_hh the edges among bits >= lb, A_ll (a table per layer) those
       // among bits < lb, and h_i the cross edges of low bit i.
       const double* th = a.theta + (size_t)k * m;
-      for (int e = tid; e < m; e += kNoisyThreads) sgn[e] = sig[e] * th[e];
+      for (int e = tid; e < m; e += kNoisyThreads) sgn[e] = sig[e] * Real(th[e]);
       __syncthreads();
       if (tid < L) {
-        double al = 0.0;
+        Real al = 0;
         for (int e = 0; e < m; ++e)
           if (su[e] < lb && sv[e] < lb) al += (((tid >> su[e]) ^ (tid >> sv[e])) & 1) ? -sgn[e] : sgn[e];
         all[tid] = al;
@@ -105,10 +114,10 @@ static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(
       __syncthreads();
       const int x0 = tid * L;
       if (x0 < N) {
-        double ahh = 0.0, h[kNoisyLowBits] = {0.0, 0.0, 0.0, 0.0};
+        Real ahh = 0, h[kNoisyLowBits] = {0, 0, 0, 0};
         for (int e = 0; e < m; ++e) {
           const int ea = su[e], eb = sv[e];
-          const double se = sgn[e];
+          const Real se = sgn[e];
           if (ea >= lb && eb >= lb) {
             ahh += (((x0 >> ea) ^ (x0 >> eb)) & 1) ? -se : se;
           } else if (ea >= lb || eb >= lb) {
@@ -119,29 +128,33 @@ static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(
           }
         }
         for (int j = 0; j < L; ++j) {
-          double ang = ahh + all[j];
+          Real ang = ahh + all[j];
 #pragma unroll
           for (int i = 0; i < kNoisyLowBits; ++i)
             if (i < lb) ang += (j >> i & 1) ? -h[i] : h[i];
-          double sn, cs;
-          sincos(ang, &sn, &cs);
-          const double2 f = phi[x0 + j];
-          phi[x0 + j] = make_double2(f.x * cs + f.y * sn, f.y * cs - f.x * sn);
+          Real sn, cs;
+          sincos_t(ang, &sn, &cs);
+          const C2 f = phi[x0 + j];
+          phi[x0 + j].x = f.x * cs + f.y * sn;
+          phi[x0 + j].y = f.y * cs - f.x * sn;
         }
       }
       // mixer exp(+i tau_q beta_k X_q), qubit by qubit
-      double sb, cb;
-      sincos(a.beta[k], &sb, &cb);
+      double sbd, cbd;
+      sincos(a.beta[k], &sbd, &cbd);
+      const Real sb = Real(sbd), cb = Real(cbd);
       for (int q = 0; q < n; ++q) {
         __syncthreads();
-        const double s = tau[q] * sb;
+        const Real s = tau[q] * sb;
         for (int pr = tid; pr < N / 2; pr += kNoisyThreads) {
           const int lo = pr & ((1 << q) - 1);
           const int xa = ((pr >> q) << (q + 1)) | lo, xb = xa | (1 << q);
-          const double2 pa = phi[xa], pb = phi[xb];
+          const C2 pa = phi[xa], pb = phi[xb];
           // a' = c a + i s b, b' = i s a + c b
-          phi[xa] = make_double2(cb * pa.x - s * pb.y, cb * pa.y + s * pb.x);
-          phi[xb] = make_double2(cb * pb.x - s * pa.y, cb * pb.y + s * pa.x);
+          phi[xa].x = cb * pa.x - s * pb.y;
+          phi[xa].y = cb * pa.y + s * pb.x;
+          phi[xb].x = cb * pb.x - s * pa.y;
+          phi[xb].y = cb * pb.y + s * pa.x;
         }
       }
       if (tid == 0) fxs = fx;
@@ -155,8 +168,8 @@ static __global__ void __launch_bounds__(kNoisyThreads) noisy_trajectory_kernel(
     const unsigned f = fxs;
     double ec = 0.0, nr = 0.0;
     for (int x = tid; x < N; x += kNoisyThreads) {
-      const double2 z = phi[x];
-      const double pr = z.x * z.x + z.y * z.y;
+      const C2 z = phi[x];
+      const double pr = double(z.x) * z.x + double(z.y) * z.y;
       nr += pr;
       ec += pr * double(cut[x ^ (int)f]);
     }

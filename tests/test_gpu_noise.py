@@ -1,6 +1,7 @@
 """Noisy LR-QAOA (Sec. II-C) on the GPU: each trajectory's <C> against the
-oracle's gate-by-gate trajectory with the same error draws (complex128 both,
-different operation order: 1e-10 relative), the trajectory mean against the
+oracle's gate-by-gate trajectory with the same error draws (complex128:
+1e-10 relative, the operation order differs; complex64 trajectories, FP32
+phases and butterflies: 1e-4 relative), the trajectory mean against the
 oracle's exact density-matrix result (statistical, 5 standard errors), and the
 overlap ratio / k0 fit of Eq. noise on a depth sweep."""
 import math
@@ -20,9 +21,12 @@ def sim(*a, **k):
     return Simulator(*a, **k)
 
 
-@pytest.mark.parametrize("n,p,eps,kind", [(4, 1, 0.05, "complete"), (6, 3, 0.2, "complete"), (9, 2, 0.5, "signed"),
-                                          (12, 3, 0.02, "complete"), (10, 2, 1.0, "sparse"), (7, 0, 0.3, "complete")])
-def test_trajectories_vs_oracle(n, p, eps, kind):
+@pytest.mark.parametrize("n,p,eps,kind,prec", [(4, 1, 0.05, "complete", "c128"), (6, 3, 0.2, "complete", "c128"),
+                                               (9, 2, 0.5, "signed", "c128"), (12, 3, 0.02, "complete", "c128"),
+                                               (10, 2, 1.0, "sparse", "c128"), (7, 0, 0.3, "complete", "c128"),
+                                               (12, 3, 0.02, "complete", "c64"), (9, 4, 0.3, "signed", "c64")])
+def test_trajectories_vs_oracle(n, p, eps, kind, prec):
+    # complex64: FP32 phases (angles up to ~10 rad) and butterflies, 1e-4 relative
     u, v, w = inputs.complete_graph(n, 60 + n)
     if kind == "signed":
         w = np.where(inputs.uniforms(61 + n, len(w)) < 0.3, -w, w).astype(np.int32)
@@ -34,13 +38,13 @@ def test_trajectories_vs_oracle(n, p, eps, kind):
     g, b = g[:p], b[:p]
     T, seed = 37, 1000 + n
     cut = oracle.cut_values(n, u, v, w)
-    with sim(n, u, v, w, S, "c128") as s:
+    with sim(n, u, v, w, S, prec) as s:
         out = s.noisy_expect(g, b, eps, T, seed)
         per = out["per_trajectory"].cpu().numpy()
     want = np.array([np.sum(np.abs(oracle.noisy_trajectory(n, u, v, w, S, g, b, eps, seed, t)) ** 2 * cut)
                      for t in range(T)])
     scale = max(1.0, float(np.max(np.abs(want))))
-    assert np.max(np.abs(per - want)) <= 1e-10 * scale
+    assert np.max(np.abs(per - want)) <= (1e-10 if prec == "c128" else 1e-4) * scale
     assert abs(out["exp_c"] - per.sum() / T) <= 1e-12 * scale
     cmin, cmax, _, _ = oracle.extremes(n, cut)
     assert abs(out["r"] - (out["exp_c"] - cmin) / (cmax - cmin)) < 1e-12
@@ -56,7 +60,8 @@ def test_trajectory_mean_vs_density_matrix(eps):
         out = s.noisy_expect(g, b, eps, T, seed=3)
         per = out["per_trajectory"].cpu().numpy()
     se = per.std() / math.sqrt(T)
-    assert abs(out["exp_c"] - exact) <= 5 * se + 1e-9
+    # complex64 trajectories: FP32 rounding of the state, ~1e-6 relative
+    assert abs(out["exp_c"] - exact) <= 5 * se + 2e-5 * abs(exact)
 
 
 def test_noisy_rejects_bad_arguments():
