@@ -395,17 +395,48 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     } else {
       RoundCost<R, WB> rc;
       rc.setup(A.ctabs + rd.ctab, tconst, rd.lane, rd.warp, rd.reg, lane, warp);
-      int lin = rc.kappa;
-      uint64_t x = geo.gb;
+      const int32_t* cp = op.cost ? P.cpc : P.cpr;
+      // when the register bits' global positions increase with the register
+      // index, x grows with j, and 32-bit keys (C - c_lo) << R | j per thread
+      // order like the 64-bit ones; the thread's two minima are widened once
+      bool ordered = c_top < (1 << 27);
 #pragma unroll
-      for (int k = 0; k < NA; ++k) {
-        const int j = k ^ (k >> 1);
-        if (k) {
-          const int b = ctz_c(k);
-          lin += (j >> b & 1) ? rc.e[b] : -rc.e[b];
-          x ^= geo.gstr[b];
+      for (int i = 1; i < R; ++i) ordered = ordered && rd.greg[i - 1] < rd.greg[i];
+      int lin = rc.kappa;
+      if (ordered) {
+        uint32_t m0 = ~0u, m1 = ~0u;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          const int j = k ^ (k >> 1);
+          if (k) {
+            const int b = ctz_c(k);
+            lin += (j >> b & 1) ? rc.e[b] : -rc.e[b];
+          }
+          const uint32_t d = uint32_t(lin + cp[j] - P.c_lo);
+          m0 = min(m0, d << R | uint32_t(j));
+          m1 = min(m1, uint32_t(c_top - int(d)) << R | uint32_t(j));
         }
-        key(lin + (op.cost ? P.cpc[j] : P.cpr[j]), x);
+        auto x_of = [&](uint32_t j) {
+          uint64_t x = geo.gb;
+#pragma unroll
+          for (int i = 0; i < R; ++i)
+            if (j >> i & 1u) x |= geo.gstr[i];
+          return x;
+        };
+        kmin = (unsigned long long)(m0 >> R) << 34 | x_of(m0 & uint32_t(NA - 1));
+        kmax = (unsigned long long)(m1 >> R) << 34 | x_of(m1 & uint32_t(NA - 1));
+      } else {
+        uint64_t x = geo.gb;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          const int j = k ^ (k >> 1);
+          if (k) {
+            const int b = ctz_c(k);
+            lin += (j >> b & 1) ? rc.e[b] : -rc.e[b];
+            x ^= geo.gstr[b];
+          }
+          key(lin + cp[j], x);
+        }
       }
     }
 #pragma unroll
