@@ -51,16 +51,12 @@ static __global__ void __launch_bounds__(256) sample_cut_kernel(const SampleCutA
     } else {
       x = splitmix_draw(a.seed, (unsigned long long)s) >> (64 - n);
     }
-    long long c = 0;
-    for (int i = 0; i < n; ++i)
-      if (x >> i & 1ull) c += dsum[i];
-    long long q = 0;
-    for (int p = 0; p < P; ++p) {
-      const unsigned long long* mp = masks + p * n;
-      int cnt = 0;
-      for (int i = 0; i < n; ++i)
-        if (x >> i & 1ull) cnt += __popcll(mp[i] & x);
-      q += coef[p] * cnt;
+    // only the vertices with x_i = 1 contribute: walk the set bits of x
+    long long c = 0, q = 0;
+    for (unsigned long long b = x; b; b &= b - 1ull) {
+      const int i = __ffsll((long long)b) - 1;
+      c += dsum[i];
+      for (int p = 0; p < P; ++p) q += coef[p] * __popcll(masks[p * n + i] & x);
     }
     c -= 2 * q;
     if (a.x_out) a.x_out[s] = x;
