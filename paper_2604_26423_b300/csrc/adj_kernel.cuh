@@ -100,8 +100,11 @@ __device__ __forceinline__ void inverse_mixer(V* v, V* l, uint8_t mask, Real tau
 // summed by the parity of j (pa: l_j v_k for even j, l_k v_j for odd j; pb the
 // others), which gives (P, M) = (pa, pb) for s = 0 and (pb, pa) for s = 1.
 template <int R>
+// upd_v = false: psi is not needed after these butterflies (the pass's last
+// mixer when psi is read from a stored forward state); only lambda is updated.
 __device__ __forceinline__ void inverse_mixer_sw(float2* v, float2* l, uint8_t mask, float tau, float alpha,
-                                                 bool fast, float cpow, float& sc, float& acc, int s) {
+                                                 bool fast, float cpow, float& sc, float& acc, int s,
+                                                 bool upd_v = true) {
   if (!mask) return;
   float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
   auto terms = [&](int i) {
@@ -128,7 +131,7 @@ __device__ __forceinline__ void inverse_mixer_sw(float2* v, float2* l, uint8_t m
   }
   const float t0 = (pa.x - pb.x) - (pa.y - pb.y);
   const float t = s ? -t0 : t0;
-  apply_mixer_sw<R>(v, mask, -tau, alpha, fast, s);
+  if (upd_v) apply_mixer_sw<R>(v, mask, -tau, alpha, fast, s);
   apply_mixer_sw<R>(l, mask, -tau, alpha, fast, s);
   acc = fmaf(sc * sc, t, acc);
   if (fast) sc *= cpow;
@@ -238,15 +241,18 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     }
   }
 
-  auto inv_mixer = [&](uint8_t mask, Real tau, Real alpha, Real cpow, Real& acc) {
+  // psi read from a stored forward state is not written back: the pass's last
+  // mixer need not update it (complex64)
+  const bool v_dead = op.dstg && !A.psi_store;
+  auto inv_mixer = [&](uint8_t mask, Real tau, Real alpha, Real cpow, Real& acc, bool upd_v) {
     if constexpr (kSw)
       inverse_mixer_sw<R>(reinterpret_cast<float2*>(v), reinterpret_cast<float2*>(l), mask, tau, alpha, FAST, cpow,
-                          sc, acc, s);
+                          sc, acc, s, upd_v);
     else
       inverse_mixer<R>(v, l, mask, tau, alpha, FAST, cpow, sc, acc);
   };
   inv_mixer(op.mixA, pick<Real>(P.tauA, P.ftauA), pick<Real>(P.alphaA, P.falphaA),
-            pow_bits(pick<Real>(P.cA, P.fcA), op.mixA), ga);
+            pow_bits(pick<Real>(P.cA, P.fcA), op.mixA), ga, !(v_dead && !op.mixB && !(CC && op.cost)));
   if (CC && op.cost) {
     // Im conj(l) v of a swapped pair of amplitudes has the opposite sign: the
     // terms are summed by the parity of j and combined with the thread's s;
@@ -298,7 +304,7 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
     gc = fma(sc * sc, tc, gc);
   }
   inv_mixer(op.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB),
-            pow_bits(pick<Real>(P.cB, P.fcB), op.mixB), gbv);
+            pow_bits(pick<Real>(P.cB, P.fcB), op.mixB), gbv, !v_dead);
 
   if (op.dstg) {
     if (sp.store) {
