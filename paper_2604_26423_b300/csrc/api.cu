@@ -264,7 +264,8 @@ int tile_const_table(qaoa_ctx* c, const PassDev& pd, SubDev& sd) {
   a.ntiles = ntiles;
   a.wmat = (const int32_t*)c->d_wmat.p;
   a.out = (int32_t*)b.p;
-  tile_const_table_kernel<<<(unsigned)((ntiles + 255) / 256), 256, 0, c->stream>>>(a);
+  const uint64_t runs = (ntiles + (1ull << kTileConstRunBits) - 1) >> kTileConstRunBits;  // one per thread
+  tile_const_table_kernel<<<(unsigned)((runs + 255) / 256), 256, 0, c->stream>>>(a);
   if (c->prof_on) ++c->nlaunch;
   const cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess) {

@@ -156,37 +156,81 @@ struct TileConstArgs {
   int32_t* out;
 };
 
+// Tiles per thread of tile_const_table_kernel: a thread visits the tiles
+// t0 | gray(k), k < 2^kTileConstRunBits, so consecutive tiles differ in one
+// index bit and the row is updated in O(n) instead of recomputed in O(n^2).
+constexpr int kTileConstRunBits = 6;
+
 static __global__ void __launch_bounds__(256) tile_const_table_kernel(const TileConstArgs a) {
-  const uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
-  if (t >= a.ntiles) return;
-  const uint64_t gbase = a.outer.scatter(t >> a.ninner) | a.inner.scatter(t & ((1ull << a.ninner) - 1));
+  __shared__ int32_t w[kMaxBits * kMaxBits];
+  const int n = a.n;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) w[i] = a.wmat[i];
+  __syncthreads();
+  const uint64_t t0 = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) << kTileConstRunBits;
+  if (t0 >= a.ntiles) return;
+  auto gbase_of = [&](uint64_t t) {
+    return a.outer.scatter(t >> a.ninner) | a.inner.scatter(t & ((1ull << a.ninner) - 1));
+  };
   uint64_t tbits = 0;
   for (int j = 0; j < a.T; ++j) tbits |= 1ull << a.pos[j];
+  // first tile of the run: the definitions
+  uint64_t gbase = gbase_of(t0);
   int32_t row[kTileConstInts];
+#pragma unroll
   for (int i = 0; i < kTileConstInts; ++i) row[i] = 0;
   int base = 0;
-  for (int j = 0; j < a.T; ++j) {
-    const int* wr = a.wmat + a.pos[j] * a.n;
+#pragma unroll
+  for (int j = 0; j < kTileConstInts - 1; ++j) {
+    if (j >= a.T) break;
+    const int* wr = w + a.pos[j] * n;
     int d = 0;
-    for (int g = 0; g < a.n; ++g) {
+    for (int g = 0; g < n; ++g) {
       if (tbits >> g & 1ull) continue;
-      const int wg = __ldg(wr + g);
-      if (gbase >> g & 1ull) { d -= wg; base += wg; } else { d += wg; }
+      if (gbase >> g & 1ull) { d -= wr[g]; base += wr[g]; } else { d += wr[g]; }
     }
     row[j] = d;
   }
-  for (int g = 0; g < a.n; ++g) {
+  for (int g = 0; g < n; ++g) {
     if (tbits >> g & 1ull) continue;
     const uint64_t fg = gbase >> g & 1ull;
-    for (int h = g + 1; h < a.n; ++h) {
+    for (int h = g + 1; h < n; ++h) {
       if (tbits >> h & 1ull) continue;
-      if (fg != (gbase >> h & 1ull)) base += __ldg(a.wmat + g * a.n + h);
+      if (fg != (gbase >> h & 1ull)) base += w[g * n + h];
     }
   }
-  row[15] = base;
-  int4* o = reinterpret_cast<int4*>(a.out + t * kTileConstInts);
+  for (int k = 0; k < (1 << kTileConstRunBits); ++k) {
+    if (k) {
+      // flip the fixed index bit g of tile-index bit ctz(k)
+      const int b = __ffs(k) - 1;
+      const uint64_t gm = gbase_of(t0 | (1ull << b)) ^ gbase_of(t0);
+      const int g = __ffsll((long long)gm) - 1;
+      const bool was = (gbase >> g & 1ull) != 0;
+      // pairs of fixed bits (g, h): [f_g != f_h] toggles
+      int dpair = 0;
+      for (int h = 0; h < n; ++h) {
+        if (h == g || (tbits >> h & 1ull)) continue;
+        const bool fh = (gbase >> h & 1ull) != 0;
+        dpair += (fh != was) ? -w[g * n + h] : w[g * n + h];
+      }
+      base += dpair;
 #pragma unroll
-  for (int i = 0; i < kTileConstInts / 4; ++i) o[i] = make_int4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
+      for (int j = 0; j < kTileConstInts - 1; ++j) {
+        if (j >= a.T) break;
+        const int wjg = w[a.pos[j] * n + g];
+        // delta_j: w (1 - 2 f_g) changes sign; base: w f_g toggles
+        row[j] += was ? 2 * wjg : -2 * wjg;
+        base += was ? -wjg : wjg;
+      }
+      gbase ^= 1ull << g;
+    }
+    const uint64_t t = t0 | uint64_t(k ^ (k >> 1));
+    if (t >= a.ntiles) continue;
+    row[15] = base;
+    int4* o = reinterpret_cast<int4*>(a.out + t * kTileConstInts);
+#pragma unroll
+    for (int i = 0; i < kTileConstInts / 4; ++i)
+      o[i] = make_int4(row[4 * i], row[4 * i + 1], row[4 * i + 2], row[4 * i + 3]);
+  }
 }
 
 // Small n (< 15): one CTA, one thread per x, direct sum over all index pairs.
