@@ -411,3 +411,34 @@ def test_real_weights_k33_single_layer():
         s.run_angles([gamma], [beta])
         got = s.expect()["exp_c"] * s.unit
     assert abs(got - want) <= 5e-5 * abs(want)
+
+
+def test_bench_workload_k33_properties():
+    # the benchmark's own workload and launch configuration (K_33, weights
+    # 1..10 from seed 33, s = 0.1, p = 3, dgamma = 0.6, dbeta = 0.3, complex64,
+    # recomputed cost): properties that hold at any size, checked at full size
+    from paper_2604_26423_b300.qaoa import Simulator
+    n, p = 33, 3
+    u, v, w = inputs.complete_graph(n, 33)
+    with Simulator(n, u, v, w, S, "c64") as s:
+        s.run(p, 0.6, 0.3)
+        res = s.expect()
+        shots = s.sample(4096, seed=34)
+        cuts = s.sample_cuts(shots[:300])["c"].cpu().numpy().astype(np.int64)
+        shot_cuts = s.sample_cuts(shots)["c"].cpu().numpy().astype(np.float64)
+    # positive weights: C_min = C(0) = 0 at index 0; C(x) = C(~x)
+    assert res["c_min"] == 0 and res["argmin"] == 0
+    assert res["argmax"] >> (n - 1) == 0
+    assert abs(res["norm"] - 1.0) <= 1e-5
+    assert 0.0 < res["r"] < 1.0
+    # the shots' cut values: the oracle's literal edge sums, and their mean
+    # against <C> (4096 draws: within 5 standard errors)
+    assert np.array_equal(cuts, oracle.sample_cuts(n, u, v, w, shots[:300]))
+    assert abs(shot_cuts.mean() - res["exp_c"]) <= 5 * shot_cuts.std() / math.sqrt(len(shot_cuts))
+    # the streamed int32 diagonal gives the same state statistics
+    with Simulator(n, u, v, w, S, "c64", cost_mode="stream") as s2:
+        s2.run(p, 0.6, 0.3)
+        res2 = s2.expect()
+    assert (res2["c_min"], res2["c_max"], res2["argmin"], res2["argmax"]) == \
+        (res["c_min"], res["c_max"], res["argmin"], res["argmax"])
+    assert abs(res2["exp_c"] - res["exp_c"]) <= 2e-6 * res["exp_c"]
