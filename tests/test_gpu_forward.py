@@ -424,16 +424,18 @@ def test_bench_workload_k33_properties():
         s.run(p, 0.6, 0.3)
         res = s.expect()
         shots = s.sample(4096, seed=34)
-        cuts = s.sample_cuts(shots[:300])["c"].cpu().numpy().astype(np.int64)
+        xs = inputs.splitmix64(3300, 300) >> np.uint64(64 - n)
+        cuts = s.sample_cuts(xs)["c"].cpu().numpy().astype(np.int64)
         shot_cuts = s.sample_cuts(shots)["c"].cpu().numpy().astype(np.float64)
     # positive weights: C_min = C(0) = 0 at index 0; C(x) = C(~x)
     assert res["c_min"] == 0 and res["argmin"] == 0
     assert res["argmax"] >> (n - 1) == 0
     assert abs(res["norm"] - 1.0) <= 1e-5
     assert 0.0 < res["r"] < 1.0
-    # the shots' cut values: the oracle's literal edge sums, and their mean
-    # against <C> (4096 draws: within 5 standard errors)
-    assert np.array_equal(cuts, oracle.sample_cuts(n, u, v, w, shots[:300]))
+    # cut values of seeded bitstrings on the full graph: the oracle's literal
+    # edge sums; the shots' mean cut against <C> (4096 draws: within 5
+    # standard errors)
+    assert np.array_equal(cuts, oracle.sample_cuts(n, u, v, w, xs))
     assert abs(shot_cuts.mean() - res["exp_c"]) <= 5 * shot_cuts.std() / math.sqrt(len(shot_cuts))
     # the streamed int32 diagonal gives the same state statistics
     with Simulator(n, u, v, w, S, "c64", cost_mode="stream") as s2:
