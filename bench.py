@@ -12,9 +12,13 @@ phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
 * ``e2e``: the same job through the public C ABI from host arrays: per step
   qaoa_init_graph (edge arrays from pinned host memory, exhaustive extremes),
   qaoa_run, qaoa_expect and qaoa_sample back to host memory, qaoa_free.
-* ``roofline``: the fused pass kernel's algorithmic bytes (one read and one
-  write of the state per pass; no read in the |+> pass) over its event-timed
-  duration, against the measured HBM copy bandwidth.
+* ``roofline``: bytes over the event-timed duration of the fused forward pass
+  kernels, against the measured HBM copy bandwidth. ``achieved`` / ``frac``
+  (= ``frac_alg``) count the algorithmic bytes of the method's pass schedule
+  with three mixer groups per layer at n = 33: N b (2 (1 + 2p) - 1) per step
+  (7 passes, the first write-only; 893 GB at K_33, p = 3); ``frac_floor``
+  counts one read and one write per layer (2 N b p); ``frac_pass`` the bytes
+  the library's own passes move (its plan's pass count).
 * ``grad``: the adjoint gradient's cost relative to the forward run on the
   gradient workload (K_28, complex64, p = 10): t(qaoa_grad: forward, <C>,
   backward, all 2p layer derivatives) / t(qaoa_run + qaoa_expect).
@@ -23,8 +27,11 @@ phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
   forward with <C>, r and extremes, and forward + adjoint gradients): instances/s
   of one CUDA-graph replay of the persistent batch kernels, scheduling knobs
   picked by the autotuner; ``--batch-reps`` replays are timed.
-* ``configs``: qaoa_run + qaoa_expect once each on K_30 (complex128 and
-  complex64), K_32 complex128 and K_33 complex64 with the streamed cost diagonal.
+* ``configs``: qaoa_run + qaoa_expect (event-timed, after one untimed run) on
+  K_30 for p = 1..10 in complex128 and complex64 with 4096 shots each, K_32
+  complex128 with recomputed and streamed cut values, K_32 complex64 with its
+  state error against the complex128 run (also in ``result.c64_err_vs_c128``),
+  K_33 complex64 with the streamed cost diagonal, and K_34 complex64.
 * ``stats``: the sampling methodology of Sec. II-D on the workload's graph and
   final state: cut values and ratios of 2^26 uniform random bitstrings (the
   random sampler; kernel time, bitstrings/s), the ratios of the step's 4096
@@ -234,34 +241,86 @@ def grad_ratio(args, stream, reps: int = 3):
                 "d_dgamma": r["d_dgamma"], "d_dbeta": r["d_dbeta"]}
 
 
+def _l2_dev(a, b, chunk=1 << 27):
+    """L2 distance of two device state vectors (complex64 / complex128), chunked."""
+    import torch
+    acc = 0.0
+    for i in range(0, a.numel(), chunk):
+        d = a[i:i + chunk].to(torch.complex128) - b[i:i + chunk].to(torch.complex128)
+        acc += float(torch.sum(d.real ** 2 + d.imag ** 2))
+    return acc ** 0.5
+
+
 def config_bench(args, stream):
-    """The other workloads of the method, timed once each (qaoa_run + qaoa_expect):
-    K_30 p=3 in complex128 and complex64 (16 GB / 8 GB states), K_32 complex128
-    (64 GiB, FP64-ALU-bound), and K_33 complex64 with the streamed int32 cost
-    diagonal instead of recomputed cut values."""
+    """The other workloads of the method (qaoa_run + qaoa_expect, event-timed
+    after one untimed run):
+    * K_30, p = 1..10, complex128 and complex64 (16 GB / 8 GB states), each
+      with 4096 shots (the single-GPU 30-qubit depth sweep of Sec. III-A);
+    * K_32 complex128 (64 GiB, FP64-ALU-bound) with recomputed and with
+      streamed cut values, and K_32 complex64 against it: the stated error of
+      the precision path where the oracle cannot run (state L2, |r64 - r128|);
+    * K_33 complex64 with the streamed int32 cost diagonal;
+    * K_34 complex64 (128 GiB), p = 3."""
     import torch
     from paper_2604_26423_b300 import inputs
     from paper_2604_26423_b300.qaoa import Simulator
 
-    out = []
-    for n, prec, mode in ((30, "c128", "recompute"), (30, "c64", "recompute"), (32, "c128", "recompute"),
-                          (33, "c64", "stream")):
-        u, v, w = inputs.complete_graph(n, SEED)
-        with Simulator(n, u, v, w, SCALE, prec, cost_mode=mode) as s:
-            s.run(P, DGAMMA, DBETA)
-            s.expect()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            s.run(P, DGAMMA, DBETA)
-            r = s.expect()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
+    def timed(s, p):
+        s.run(p, DGAMMA, DBETA)
+        s.expect()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.run(p, DGAMMA, DBETA)
+        r = s.expect()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def row(n, prec, mode, p, ms, r, **kw):
+        d = {"n": n, "precision": prec, "cost_mode": mode, "p": p, "ms": ms, "layers_per_s": p / ms * 1e3,
+             "r": r["r"], "exp_c": r["exp_c"]}
+        d.update(kw)
+        return d
+
+    out = {"k30_depth_sweep": [], "runs": []}
+    u, v, w = inputs.complete_graph(30, SEED)
+    for prec in ("c128", "c64"):
+        with Simulator(30, u, v, w, SCALE, prec) as s:
+            for p in range(1, 11):
+                ms, r = timed(s, p)
+                t0 = time.perf_counter()
+                shots = s.sample(SHOTS, seed=SEED + p)
+                out["k30_depth_sweep"].append(row(30, prec, "recompute", p, ms, r,
+                                                  shots=len(shots), sample_ms=(time.perf_counter() - t0) * 1e3))
         torch.cuda.empty_cache()
-        out.append({"n": n, "precision": prec, "cost_mode": mode, "p": P, "ms": ms, "layers_per_s": P / ms * 1e3,
-                    "r": r["r"], "exp_c": r["exp_c"]})
+    u, v, w = inputs.complete_graph(32, SEED)
+    with Simulator(32, u, v, w, SCALE, "c128") as s128:
+        ms, r128 = timed(s128, P)
+        out["runs"].append(row(32, "c128", "recompute", P, ms, r128))
+        with Simulator(32, u, v, w, SCALE, "c64") as s64:
+            ms, r64 = timed(s64, P)
+            out["runs"].append(row(32, "c64", "recompute", P, ms, r64))
+            out["c64_err_vs_c128"] = {
+                "workload": "K_32 (seed 33), p=3, dgamma=0.6, dbeta=0.3: complex64 vs complex128 on this GPU",
+                "state_l2": _l2_dev(s64.state(), s128.state()), "r_abs": abs(r64["r"] - r128["r"]),
+                "exp_c_rel": abs(r64["exp_c"] - r128["exp_c"]) / abs(r128["exp_c"])}
+    torch.cuda.empty_cache()
+    with Simulator(32, u, v, w, SCALE, "c128", cost_mode="stream") as s:
+        ms, r = timed(s, P)
+        out["runs"].append(row(32, "c128", "stream", P, ms, r))
+    torch.cuda.empty_cache()
+    u, v, w = inputs.complete_graph(33, SEED)
+    with Simulator(33, u, v, w, SCALE, "c64", cost_mode="stream") as s:
+        ms, r = timed(s, P)
+        out["runs"].append(row(33, "c64", "stream", P, ms, r))
+    torch.cuda.empty_cache()
+    u, v, w = inputs.complete_graph(34, SEED)
+    with Simulator(34, u, v, w, SCALE, "c64") as s:
+        ms, r = timed(s, P)
+        out["runs"].append(row(34, "c64", "recompute", P, ms, r))
+    torch.cuda.empty_cache()
     return out
 
 
@@ -460,7 +519,20 @@ def run_gpu(args):
     configs = None if args.no_configs else config_bench(args, stream)
 
     peak, peak_kind = measured_peak()
-    achieved = prof["bytes"] / (prof["ms"] * 1e-3) / 1e9 if prof["ms"] > 0 else 0.0
+    # three byte counts over the same event-timed forward pass kernels:
+    #   algorithmic (the headline): N b (2 passes - 1) for the pass schedule
+    #     with three mixer groups per layer at n = 33 (1 + 2p passes, the
+    #     first write-only), whatever plan the library runs;
+    #   floor: one read and one write of the state per layer (2 N b p);
+    #   pass: the bytes the plan's passes actually move (its own pass count)
+    nb_state = 8.0 * (1 << nq)
+    alg_passes = 1 + P * (3 - 1)
+    alg_bytes = nb_state * (2 * alg_passes - 1) * args.steps
+    floor_bytes = 2.0 * nb_state * P * args.steps
+    kern_s = prof["ms"] * 1e-3
+    achieved = alg_bytes / kern_s / 1e9 if kern_s > 0 else 0.0
+    achieved_pass = prof["bytes"] / kern_s / 1e9 if kern_s > 0 else 0.0
+    achieved_floor = floor_bytes / kern_s / 1e9 if kern_s > 0 else 0.0
     traffic = None
     try:
         with open(PROFILE_JSON) as f:
@@ -489,6 +561,12 @@ def run_gpu(args):
         "gpu_launches": int(launches_all) if launches_all else int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "frac_alg": achieved / peak, "frac_floor": achieved_floor / peak,
+                     "frac_pass": achieved_pass / peak, "achieved_pass": achieved_pass,
+                     "alg_bytes_per_step": alg_bytes / args.steps, "floor_bytes_per_step": floor_bytes / args.steps,
+                     "pass_bytes_per_step": prof["bytes"] / args.steps,
+                     "passes_per_step": prof["launches"] / args.steps, "alg_passes_per_step": alg_passes,
+                     "kernel_ms_per_step": prof["ms"] / args.steps,
                      "kernel": "forward pass kernels (fwd_spec_kernel, fwd_pass_kernel)", "launches": prof["launches"],
                      "bytes_per_launch": prof["bytes"] / max(1, prof["launches"]),
                      "ms_per_launch": prof["ms"] / max(1, prof["launches"])},
@@ -501,6 +579,8 @@ def run_gpu(args):
         out["batch"] = batch
     if configs is not None:
         out["configs"] = configs
+        if "c64_err_vs_c128" in configs:
+            out["result"]["c64_err_vs_c128"] = configs["c64_err_vs_c128"]
     if stats is not None:
         out["stats"] = stats
     if noise is not None:

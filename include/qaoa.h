@@ -45,13 +45,16 @@ extern "C" {
 #define QAOA_C64 0
 #define QAOA_C128 1
 
-/* how the cost phase obtains C(x): choose automatically, recompute it from the
- * weight matrix inside each tile, or stream a precomputed int32 diagonal */
+/* how the cost phase obtains C(x): choose automatically (the choice recorded
+ * for (n, precision) with qaoa_set_cost_choice, else recompute), recompute it
+ * from the weight matrix inside each tile, or stream a precomputed int32
+ * diagonal */
 #define QAOA_COST_AUTO 0
 #define QAOA_COST_RECOMPUTE 1
 #define QAOA_COST_STREAM 2
 
-/* largest qubit counts accepted (state of 64 GiB each) */
+/* largest qubit counts accepted: 2^34 complex64 amplitudes (128 GiB) and
+ * 2^33 complex128 amplitudes (128 GiB) */
 #define QAOA_MAX_QUBITS_C64 34
 #define QAOA_MAX_QUBITS_C128 33
 
@@ -88,6 +91,16 @@ int qaoa_quantize_weights(int m, const double *w, int64_t max_abs_sum, int32_t *
 size_t qaoa_aux_bytes(int n, int precision, int cost_mode, int with_grad);
 
 /*
+ * Records the cost mode (QAOA_COST_RECOMPUTE or QAOA_COST_STREAM) that
+ * QAOA_COST_AUTO selects for contexts of n qubits in `precision` created after
+ * this call, e.g. the faster one in an autotuner's timing; QAOA_COST_AUTO
+ * forgets the record (AUTO then selects recompute). Process-wide and thread
+ * safe; host only. qaoa_aux_bytes resolves AUTO the same way, so size the aux
+ * buffer after recording. Errors: EINVAL (n or precision out of range, bad mode).
+ */
+int qaoa_set_cost_choice(int n, int precision, int cost_mode);
+
+/*
  * Creates a context for one graph (Sec. II-B: weighted MaxCut instance).
  *   n            qubits = vertices, 1 <= n <= QAOA_MAX_QUBITS_*.
  *   n_edges      number of edges m >= 0; u[e] != v[e], both in [0, n), no
@@ -97,8 +110,8 @@ size_t qaoa_aux_bytes(int n, int precision, int cost_mode, int with_grad);
  *   weight_scale s > 0 in the phases exp(-i gamma s h(x)); <C>, C_min and C_max
  *                are reported in integer weight units.
  *   precision    QAOA_C64 or QAOA_C128.
- *   cost_mode    QAOA_COST_*; AUTO picks recompute unless the autotuner cache
- *                says streaming is faster for (n, precision).
+ *   cost_mode    QAOA_COST_*; AUTO takes the choice recorded for (n,
+ *                precision) by qaoa_set_cost_choice, else recompute.
  *   state_dev    device buffer of exactly qaoa_state_bytes(n, precision)
  *                bytes, 256-byte aligned, or NULL (the library allocates).
  *   aux_dev      device buffer of aux_bytes >= qaoa_aux_bytes(...) or NULL
@@ -115,6 +128,46 @@ int qaoa_init_graph(qaoa_ctx **ctx, int n, int n_edges, const int32_t *u, const 
                     const int32_t *w, double weight_scale, int precision, int cost_mode,
                     void *state_dev, size_t state_bytes, void *aux_dev, size_t aux_bytes,
                     void *cuda_stream);
+
+/*
+ * Kernel configuration of one context. The paper fixes none of these: they
+ * select among equivalent ways to execute the same circuit (results agree to
+ * the state precision's rounding). 0 in a field keeps the library default;
+ * for a field left 0, the environment variable named beside it (read when the
+ * context plans a run) replaces the default, so a process can set defaults
+ * without code changes.
+ */
+#define QAOA_ON 1
+#define QAOA_OFF 2
+#define QAOA_ORDER_LOW_LAST 1   /* the last layer ends on the low index group */
+#define QAOA_ORDER_LOW_MIDDLE 2 /* the low group away from the fused passes */
+#define QAOA_SHAPE_5x3 1        /* 2^5 registers x 8 warps (T = 13) */
+#define QAOA_SHAPE_4x4 2        /* 2^4 registers x 16 warps (T = 13), complex64 */
+#define QAOA_SHAPE_5x2 3        /* 2^5 registers x 4 warps (T = 12), complex64 */
+#define QAOA_SHAPE_4x3 4        /* 2^4 registers x 8 warps (T = 12) */
+#define QAOA_SHAPE_5x4 5        /* 2^5 registers x 16 warps (T = 14), complex64 */
+typedef struct qaoa_opts {
+  int fwd_shape;       /* forward tile, QAOA_SHAPE_* (QAOA_FWD_SHAPE, QAOA_FWD_SHAPE_C128:
+                          "5x3", "4x4", "5x2", "4x3", "5x4"); complex128 takes 5x3 or 4x3 */
+  int super_tile;      /* largest forward super-tile in index bits, T..20 (QAOA_SMAX) */
+  int group_order;     /* QAOA_ORDER_* of qaoa_run's plans (QAOA_GROUP_ORDER: "last", "middle") */
+  int float_lanes;     /* QAOA_ON / QAOA_OFF: coalescing bits applied in a plain high-group
+                          pass (QAOA_FLOAT_LANES: 1, 0) */
+  int specialised;     /* QAOA_ON / QAOA_OFF: kernels compiled per round sequence (QAOA_SPEC) */
+  int tile_tables;     /* QAOA_ON / QAOA_OFF: per-tile C(x) constants from tables (QAOA_TILE_TABLES) */
+  int l2_prefetch;     /* QAOA_ON / QAOA_OFF: next tile prefetched into L2 (QAOA_L2PREFETCH) */
+  int grad_order;      /* QAOA_ORDER_* of qaoa_grad's plans (QAOA_GRAD_ORDER) */
+  int grad_checkpoint; /* QAOA_ON / QAOA_OFF: stored forward states in qaoa_grad
+                          (QAOA_GRAD_CHECKPOINT) */
+} qaoa_opts;
+
+/* Sets the context's configuration (copied); later runs are planned with it.
+ * Errors: EINVAL (NULL arguments or a value outside the encodings above). */
+int qaoa_set_opts(qaoa_ctx *ctx, const qaoa_opts *opts);
+
+/* The configuration in effect (options, else environment, else defaults) for
+ * the context's precision, every field filled in. Errors: EINVAL. */
+int qaoa_get_opts(const qaoa_ctx *ctx, qaoa_opts *opts);
 
 /*
  * Prepares |psi_p> with the linear-ramp schedule (Sec. II-B) and computes <C>
@@ -160,7 +213,7 @@ int qaoa_sample(qaoa_ctx *ctx, int shots, const double *uniforms, uint64_t seed,
  * the forward instead keeps every pass's output in library-owned device memory
  * (held until qaoa_free; reused by later calls) and the adjoint reads psi from
  * it rather than writing the uncomputed psi back: one state write fewer per
- * adjoint pass. QAOA_GRAD_CHECKPOINT=0 in the environment turns this off.
+ * adjoint pass. The grad_checkpoint option (qaoa_set_opts) turns this off.
  * Any output may be NULL; g_gamma and
  * g_beta hold p doubles; exp_c receives <C> = <psi_p|lambda> (taken in the
  * first adjoint pass). Leaves the context without a prepared state or result
@@ -185,7 +238,7 @@ int qaoa_cost_diag(qaoa_ctx *ctx, int32_t *out_dev);
  * Shots from a state vector without allocating any device memory. The paper
  * has no counterpart: this serves callers that must not call cudaMalloc while
  * they run (plugins whose host framework owns all device memory, serving
- * loops with a fixed memory budget, code between stream-capture begin and end).
+ * loops with a fixed memory budget that an allocation would break).
  *   state_dev     2^n amplitudes on the current device (complex64 or
  *                 complex128 per `precision`), read only.
  *   uniforms_dev  `shots` doubles in [0, 1) on the device, or NULL to draw u_i
@@ -196,11 +249,13 @@ int qaoa_cost_diag(qaoa_ctx *ctx, int32_t *out_dev);
  * blocks stays within QAOA_NOALLOC_MAX_BLOCKS, larger blocks beyond.
  * Scratch: one file-scope device array of 2 * QAOA_NOALLOC_MAX_BLOCKS + 1
  * doubles (about 1 MiB per GPU, held until exit), shared by every call. The
- * first call on a device looks up the array's address, so make that first
- * call before any stream capture. Calls whose GPU work overlaps (e.g. on two
- * streams) race on the shared scratch. Work is queued on cuda_stream and not
- * waited for. Errors: EINVAL (precision, n outside [1,
- * QAOA_NOALLOC_MAX_QUBITS], shots < 0, NULL buffers), ECUDA.
+ * first call on a device looks up the array's address (kept until exit), so
+ * make that first call before any stream capture; a device reset makes the
+ * kept address stale, so do not call this again on a device after resetting
+ * it. Calls whose GPU work overlaps (e.g. on two streams) race on the shared
+ * scratch. Work is queued on cuda_stream and not waited for. Errors: EINVAL
+ * (precision, n outside [1, QAOA_NOALLOC_MAX_QUBITS], shots < 0, NULL
+ * buffers), ECUDA.
  */
 #define QAOA_NOALLOC_MAX_BLOCKS 65536
 #define QAOA_NOALLOC_MAX_QUBITS 34
@@ -258,9 +313,14 @@ typedef struct qaoa_batch qaoa_batch;
  * large instances are interleaved pass by pass until their next passes hold at
  * least this many work items (default 2 per CTA) or their states this many MiB
  * (default 96, sized for L2); max_units: super-tiles per work item (default 8);
- * ctas_per_sm: persistent CTAs per SM (default: occupancy, at most 2). */
+ * ctas_per_sm: persistent CTAs per SM (default: occupancy, at most 2);
+ * wait_ns: limit of each device-side dependency wait in nanoseconds (default
+ * 2e9). A wait that reaches the limit sets the batch's error flag and skips
+ * its item, so the run ends and qaoa_batch_results returns ETIMEOUT; a limit
+ * of 1 ns makes any wait give up (a test of that path). */
 typedef struct qaoa_batch_opts {
   int solo_max_n, window_items, window_mb, max_units, ctas_per_sm;
+  int64_t wait_ns;
 } qaoa_batch_opts;
 
 /* Validates and plans the batch, allocates its device memory (all states, and

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <set>
 #include <stdexcept>
 #include <string>
@@ -76,6 +77,7 @@ struct DevBuf {
 
 struct qaoa_ctx {
   int n = 0, m = 0, prec = QAOA_C64, cost_mode = QAOA_COST_RECOMPUTE;
+  qaoa_opts opts{};  // kernel configuration (qaoa_set_opts; 0 = default)
   double scale = 0.1;
   std::vector<int32_t> u, v, w;
   std::vector<int32_t> wmat;  // n x n
@@ -169,43 +171,73 @@ struct ProfScope {
   }
 };
 
-// Forward tile shape of complex64 (complex128: see the branch below):
+// Forward tile shape ids (the kernels' instantiations):
 //   0 "5x3": 2^5 registers x 8 warps, T = 13, 2 CTAs per SM
 //   1 "4x4": 2^4 registers x 16 warps, T = 13
 //   2 "5x2": 2^5 registers x 4 warps, T = 12, 4 CTAs per SM
 //   3 "4x3": 2^4 registers x 8 warps, T = 12, 4 CTAs per SM (default: four
 //      tiles in flight per SM keep HBM busier than two larger ones)
-// selected by QAOA_FWD_SHAPE.
+//   4 "5x4": 2^5 registers x 16 warps, T = 14, 1 CTA per SM (three mixer
+//      groups at n = 33 with 128-byte runs: 7 passes for p = 3 instead of 10)
+// complex128 accepts 5x3 (one CTA per SM, phase table in shared memory) and
+// 4x3 (two CTAs per SM, phase table read through L1).
 constexpr int kFwdShapeC64 = 3;
 constexpr int kFwdShapeC128 = 3;  // measured 6% faster than 5x3 at K_32 (FP64-bound)
 constexpr int kSmallMaxQubits = 12;  // n <= 12: whole circuit in one CTA (small_circuit_kernel)
-int fwd_shape_id(int prec) {
-  if (prec != QAOA_C64) {
-    // complex128: 5x3 (one CTA per SM, phase table in shared memory) or 4x3
-    // (two CTAs per SM, phase table read through L1)
-    const char* e = getenv("QAOA_FWD_SHAPE_C128");
-    if (e && strcmp(e, "4x3") == 0) return 3;
-    if (e && strcmp(e, "5x3") == 0) return 0;
-    return kFwdShapeC128;
-  }
-  const char* e = getenv("QAOA_FWD_SHAPE");
-  if (!e) return kFwdShapeC64;
+
+// A configuration value: the context's option when set (nonzero), else the
+// environment variable `env` when set and recognised, else the default.
+// Options and variables use the qaoa_opts encodings (QAOA_ON / QAOA_OFF, ...).
+int shape_from_name(const char* e) {
+  if (!e) return -1;
   if (strcmp(e, "5x3") == 0) return 0;
   if (strcmp(e, "4x4") == 0) return 1;
   if (strcmp(e, "5x2") == 0) return 2;
   if (strcmp(e, "4x3") == 0) return 3;
-  return kFwdShapeC64;
+  if (strcmp(e, "5x4") == 0) return 4;
+  return -1;
+}
+// QAOA_SHAPE_* (qaoa.h) -> kernel shape id
+int shape_from_opt(int o) {
+  switch (o) {
+    case QAOA_SHAPE_5x3: return 0;
+    case QAOA_SHAPE_4x4: return 1;
+    case QAOA_SHAPE_5x2: return 2;
+    case QAOA_SHAPE_4x3: return 3;
+    case QAOA_SHAPE_5x4: return 4;
+    default: return -1;
+  }
+}
+int on_off(int opt, const char* env, int dflt) {
+  if (opt == QAOA_ON) return 1;
+  if (opt == QAOA_OFF) return 0;
+  const char* e = getenv(env);
+  if (e && strcmp(e, "0") == 0) return 0;
+  if (e && strcmp(e, "1") == 0) return 1;
+  return dflt;
 }
 
-TileShape fwd_shape(int prec) {
-  static const int R[4] = {kR, 4, 5, 4}, WB[4] = {kWB, 4, 2, 3};
-  const int id = fwd_shape_id(prec);
+int fwd_shape_id(const qaoa_ctx* c, int prec) {
+  const int o = c ? shape_from_opt(c->opts.fwd_shape) : -1;
+  if (prec != QAOA_C64) {
+    if (o == 0 || o == 3) return o;
+    const int e = shape_from_name(getenv("QAOA_FWD_SHAPE_C128"));
+    return (e == 0 || e == 3) ? e : kFwdShapeC128;
+  }
+  if (o >= 0) return o;
+  const int e = shape_from_name(getenv("QAOA_FWD_SHAPE"));
+  return e >= 0 ? e : kFwdShapeC64;
+}
+
+TileShape shape_of(int id, int prec) {
+  static const int R[5] = {kR, 4, 5, 4, 5}, WB[5] = {kWB, 4, 2, 3, 4};
   TileShape s;
   s.R = R[id];
   s.WB = WB[id];
   s.amp_bytes = amp_bytes(prec);
   return s;
 }
+TileShape fwd_shape(const qaoa_ctx* c, int prec) { return shape_of(fwd_shape_id(c, prec), prec); }
 
 // Adjoint tile shape: two vectors per thread, 2^4 registers each x 8 warps (T = 12).
 TileShape adj_shape(int prec) {
@@ -233,8 +265,7 @@ int upload_ctabs(qaoa_ctx* c) {
 // context's tables would pass kTileTableMaxBytes.
 int tile_const_table(qaoa_ctx* c, const PassDev& pd, SubDev& sd) {
   sd.tct = nullptr;
-  const char* e = getenv("QAOA_TILE_TABLES");
-  if (e && strcmp(e, "0") == 0) return QAOA_OK;
+  if (!on_off(c->opts.tile_tables, "QAOA_TILE_TABLES", 1)) return QAOA_OK;
   std::vector<int8_t> key(sd.pos, sd.pos + pd.T);
   key.push_back(-1);
   key.insert(key.end(), pd.outer, pd.outer + pd.nouter);
@@ -308,37 +339,38 @@ int upload_phases(qaoa_ctx* c, int p, const double* gamma) {
   return QAOA_OK;
 }
 
-// Largest super-tile (index bits kept together through L2 by one CTA);
-// QAOA_SMAX overrides the default (13 disables multi-tile super-tiles).
+// Largest super-tile (index bits kept together through L2 by one CTA) of the
+// adjoint passes; QAOA_SMAX_ADJ overrides the default (one tile).
 int smax_adj() {
   const char* e = getenv("QAOA_SMAX_ADJ");
   const int v = e ? atoi(e) : kSmaxAdj;
   return v >= 12 && v <= 20 ? v : kSmaxAdj;
 }
 
-// Floating lane bits in the forward plans (PLAN_FLOAT_LANES): QAOA_FLOAT_LANES=0 or 1.
-int float_lanes_flag() {
-  const char* e = getenv("QAOA_FLOAT_LANES");
-  if (e && strcmp(e, "0") == 0) return 0;
-  if (e && strcmp(e, "1") == 0) return PLAN_FLOAT_LANES;
-  return kFloatLanes;
+// Floating lane bits in the forward plans (PLAN_FLOAT_LANES): option
+// float_lanes, QAOA_FLOAT_LANES=0 or 1.
+int float_lanes_flag(const qaoa_ctx* c) {
+  return on_off(c ? c->opts.float_lanes : 0, "QAOA_FLOAT_LANES", kFloatLanes != 0) ? PLAN_FLOAT_LANES : 0;
 }
 
-// Group order of the pass plans (plan.h): QAOA_GROUP_ORDER=middle or last,
-// with the floating-lane flag.
-int group_order() {
-  const char* e = getenv("QAOA_GROUP_ORDER");
-  int o = kGroupOrder;
-  if (e && strcmp(e, "middle") == 0) o = ORDER_LOW_MIDDLE;
-  if (e && strcmp(e, "last") == 0) o = ORDER_LOW_LAST;
-  return o | float_lanes_flag();
+int order_of(int opt, const char* env, int dflt) {
+  if (opt == QAOA_ORDER_LOW_LAST) return ORDER_LOW_LAST;
+  if (opt == QAOA_ORDER_LOW_MIDDLE) return ORDER_LOW_MIDDLE;
+  const char* e = getenv(env);
+  if (e && strcmp(e, "middle") == 0) return ORDER_LOW_MIDDLE;
+  if (e && strcmp(e, "last") == 0) return ORDER_LOW_LAST;
+  return dflt;
 }
 
-// Specialised pass kernels (spec.h; QAOA_SPEC=0 selects the generic ones).
-bool spec_enabled() {
-  const char* e = getenv("QAOA_SPEC");
-  return !(e && strcmp(e, "0") == 0);
+// Group order of the run's pass plans (plan.h): option group_order,
+// QAOA_GROUP_ORDER=middle or last; with the floating-lane flag.
+int group_order(const qaoa_ctx* c) {
+  return order_of(c ? c->opts.group_order : 0, "QAOA_GROUP_ORDER", kGroupOrder) | float_lanes_flag(c);
 }
+
+// Specialised pass kernels (spec.h): option specialised, QAOA_SPEC=0 selects
+// the generic ones.
+bool spec_enabled(const qaoa_ctx* c) { return on_off(c->opts.specialised, "QAOA_SPEC", 1) != 0; }
 
 // Asynchronous tile copies in the adjoint passes (QAOA_ADJ_PREFETCH=1 enables;
 // measured slower than the register loads with the specialised kernels).
@@ -347,26 +379,23 @@ bool adj_prefetch() {
   return e && strcmp(e, "1") == 0;
 }
 
-// group orders of the gradient's forward and adjoint plans (QAOA_GRAD_ORDER
-// overrides both)
-int grad_base_order() {
-  const char* e = getenv("QAOA_GRAD_ORDER");
-  if (e && strcmp(e, "last") == 0) return ORDER_LOW_LAST;
-  if (e && strcmp(e, "middle") == 0) return ORDER_LOW_MIDDLE;
-  return ORDER_LOW_MIDDLE;
-}
-int grad_fwd_order() { return grad_base_order() | float_lanes_flag(); }
-int grad_bwd_order() { return grad_base_order(); }
+// group orders of the gradient's forward and adjoint plans (option
+// grad_order, QAOA_GRAD_ORDER)
+int grad_base_order(const qaoa_ctx* c) { return order_of(c->opts.grad_order, "QAOA_GRAD_ORDER", ORDER_LOW_MIDDLE); }
+int grad_fwd_order(const qaoa_ctx* c) { return grad_base_order(c) | float_lanes_flag(c); }
+int grad_bwd_order(const qaoa_ctx* c) { return grad_base_order(c); }
 
-// Stored forward states in the gradient (QAOA_GRAD_CHECKPOINT=0 disables).
-bool grad_checkpoint() {
-  const char* e = getenv("QAOA_GRAD_CHECKPOINT");
-  return !(e && strcmp(e, "0") == 0);
-}
+// Stored forward states in the gradient (option grad_checkpoint,
+// QAOA_GRAD_CHECKPOINT=0 disables).
+bool grad_checkpoint(const qaoa_ctx* c) { return on_off(c->opts.grad_checkpoint, "QAOA_GRAD_CHECKPOINT", 1) != 0; }
 
-int smax_fwd(int T) {
-  const char* e = getenv("QAOA_SMAX");
-  const int v = e ? atoi(e) : T;
+// Largest forward super-tile: option super_tile, QAOA_SMAX; T (one tile) by default.
+int smax_fwd(const qaoa_ctx* c, int T) {
+  int v = c ? c->opts.super_tile : 0;
+  if (v <= 0) {
+    const char* e = getenv("QAOA_SMAX");
+    v = e ? atoi(e) : T;
+  }
   return v >= T && v <= 20 ? v : T;
 }
 
@@ -374,8 +403,8 @@ const Plan* get_plan(qaoa_ctx* c, int p, int order) {
   const auto key = std::make_pair(p, order);
   auto it = c->plans.find(key);
   if (it != c->plans.end()) return it->second.get();
-  auto pl = std::make_unique<Plan>(
-      plan_forward(c->n, p, fwd_shape(c->prec), smax_fwd(fwd_shape(c->prec).T()), kMinUnitsLog2, order));
+  const TileShape sh = fwd_shape(c, c->prec);
+  auto pl = std::make_unique<Plan>(plan_forward(c->n, p, sh, smax_fwd(c, sh.T()), kMinUnitsLog2, order));
   const Plan* r = pl.get();
   c->plans[key] = std::move(pl);
   return r;
@@ -420,6 +449,9 @@ int pass_dispatch(qaoa_ctx* c, int shape, bool launch, const PassDev& pd, const 
   if (shape == 3)
     return launch ? launch_pass<float, FAST, CC, 4, 3>(c, pd, pa, smem, grid)
                   : blocks_per_sm<float, FAST, CC, 4, 3>(c, smem, bps);
+  if (shape == 4)
+    return launch ? launch_pass<float, FAST, CC, 5, 4>(c, pd, pa, smem, grid)
+                  : blocks_per_sm<float, FAST, CC, 5, 4>(c, smem, bps);
   return launch ? launch_pass<float, FAST, CC>(c, pd, pa, smem, grid) : blocks_per_sm<float, FAST, CC>(c, smem, bps);
 }
 
@@ -471,7 +503,7 @@ int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
 int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int order, bool reduce = true,
                 void* const* outs = nullptr) {
   const int n = c->n;
-  const TileShape sh = fwd_shape(c->prec);
+  const TileShape sh = fwd_shape(c, c->prec);
   const int T = sh.T();
   const int ab = amp_bytes(c->prec);
   c->state_ready = false;
@@ -501,7 +533,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
   CUDA_TRY(c, cudaGetDevice(&dev));
   CUDA_TRY(c, cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   // complex64 kernels compute the phase (phase_turns); complex128 reads the table
-  const bool tab_smem = c->prec == QAOA_C128 && fwd_shape_id(c->prec) == 0 && with_tab + 1024 <= (size_t)max_smem;
+  const bool tab_smem = c->prec == QAOA_C128 && fwd_shape_id(c, c->prec) == 0 && with_tab + 1024 <= (size_t)max_smem;
   const size_t smem = tab_smem ? with_tab : base_smem;
 
   // build every pass descriptor (and its cost tables) before launching
@@ -562,6 +594,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
     {
       const char* e = getenv("QAOA_L2HINT");
       pa.l2hint = (e && atoi(e) != 0) ? 1 : 0;
+      pa.prefetch = on_off(c->opts.l2_prefetch, "QAOA_L2PREFETCH", 0);
     }
     // the first pass visits every index once: the extremes come with it when
     // they are not known yet
@@ -573,16 +606,17 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       pa.ext_keys = (unsigned long long*)c->d_ext_keys.p;
     }
     int bps = 0;
-    const int wide = fwd_shape_id(c->prec);
+    const int wide = fwd_shape_id(c, c->prec);
     const bool cc = ccs[pi];
     const bool red = pp.reduce && reduce;
     // a specialised kernel when one was compiled for this pass's rounds
     FwdPassKernel spec = nullptr;
-    if (c->prec == QAOA_C64 && wide == 3 && fast && pd.nsub == 1 && pd.sub[0].ninner == 0 && spec_enabled())
-      spec = find_fwd_spec(pd.sub[0]);
+    if (c->prec == QAOA_C64 && (wide == 3 || wide == 4) && fast && pd.nsub == 1 && pd.sub[0].ninner == 0 &&
+        spec_enabled(c))
+      spec = find_fwd_spec(pd.sub[0], sh.R, sh.WB);
     if (spec) {
       CUDA_TRY(c, cudaFuncSetAttribute((const void*)spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)spec, 32 << kWB, smem));
+      CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)spec, 32 << sh.WB, smem));
       if (bps < 1) return c->set_err(QAOA_ECUDA, "pass kernel does not fit on an SM (smem %zu)", smem);
     } else {
       rc = pass_any(c, fast, cc, wide, false, pd, pa, smem, 0, &bps);
@@ -592,12 +626,14 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
     const int grid = (int)std::min<long long>(want, (long long)pd.n_units);
     pa.partial = red ? (double*)c->d_partial.p : nullptr;
     // the final pass writes the sampling block sums when its tile is the 2^T
-    // lowest index bits (T = 12 or 13, one sub-pass) and the state is large
-    // enough for the separate block-sum read to matter (their FP32 grouping
-    // differs from block_sum_kernel's, so shots near a CDF step may differ in
-    // the last bits between the two; both are valid draws)
+    // lowest index bits (T = 12..14, one sub-pass) and the state is large
+    // enough for the separate block-sum read to matter (each thread's partial
+    // over its register amplitudes is in the state precision, FP64 from there
+    // on; block_sum_kernel sums every |psi|^2 in FP64, so shots whose
+    // u * total lies within that rounding of a CDF step may differ in the
+    // index between the two; both are valid draws)
     pa.bsum = nullptr;
-    if (red && n >= kFuseSumsMinQubits && (T == 12 || T == 13) && pp.subs.size() == 1) {
+    if (red && n >= kFuseSumsMinQubits && T >= 12 && T <= 14 && pp.subs.size() == 1) {
       bool contiguous = true;
       for (int j = 0; j < T; ++j) contiguous = contiguous && pp.subs[0].pos[j] == j;
       if (contiguous) {
@@ -615,7 +651,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 0, bytes);
       if (spec) {
-        spec<<<grid, 32 << kWB, smem, c->stream>>>(pd, pa);
+        spec<<<grid, 32 << sh.WB, smem, c->stream>>>(pd, pa);
         if (c->prof_on) ++c->nlaunch;
         const cudaError_t le = cudaGetLastError();
         rc = le == cudaSuccess ? QAOA_OK : c->set_err(QAOA_ECUDA, "specialised pass kernel: %s", cudaGetErrorString(le));
@@ -754,13 +790,13 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   }
   const Plan* plan;
   try {
-    plan = get_bplan(c, p, grad_bwd_order());
+    plan = get_bplan(c, p, grad_bwd_order(c));
   } catch (std::exception& ex) {
     return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
   }
   // the gradient's forward run samples nothing: the plan without the
   // block-sum constraint keeps the fused passes on the small groups
-  int fwd_order = grad_fwd_order();
+  int fwd_order = grad_fwd_order(c);
   // stored forward states: when the adjoint plan retraces the forward plan
   // pass by pass and half of the free device memory holds one state per
   // forward pass, the forward writes each pass's output to its own buffer and
@@ -768,11 +804,11 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   // P-1-j instead of uncomputing it, which saves one state write per adjoint
   // pass (the in-tile uncompute of psi for the gradient terms stays)
   std::vector<void*> outs;
-  if (grad_checkpoint() && n >= std::max(fwd_shape(c->prec).T(), kSmallMaxQubits + 1)) {
+  if (grad_checkpoint(c) && n >= std::max(fwd_shape(c, c->prec).T(), kSmallMaxQubits + 1)) {
     try {
       const Plan* fp = get_plan(c, p, fwd_order);
-      if (!plans_mirror(*fp, *plan) && fwd_order != grad_bwd_order()) {
-        fwd_order = grad_bwd_order();
+      if (!plans_mirror(*fp, *plan) && fwd_order != grad_bwd_order(c)) {
+        fwd_order = grad_bwd_order(c);
         fp = get_plan(c, p, fwd_order);
       }
       bool single = true;  // out-of-place passes have one sub-pass
@@ -792,7 +828,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
           outs.push_back(c->state);
         }
       } else {
-        fwd_order = grad_fwd_order();
+        fwd_order = grad_fwd_order(c);
       }
     } catch (std::exception& ex) {
       return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
@@ -867,7 +903,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     for (const SubPassPlan& sp : pp.subs) cc = cc || sp.needs_c || sp.linit;
     // a specialised kernel when one was compiled for this pass's rounds
     AdjPassKernel spec = nullptr;
-    if (c->prec == QAOA_C64 && fast && pd.nsub == 1 && pd.sub[0].ninner == 0 && spec_enabled())
+    if (c->prec == QAOA_C64 && fast && pd.nsub == 1 && pd.sub[0].ninner == 0 && spec_enabled(c))
       spec = find_adj_spec(pd.sub[0]);
     if (spec) {
       CUDA_TRY(c, cudaFuncSetAttribute((const void*)spec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1005,12 +1041,73 @@ int qaoa_quantize_weights(int m, const double* w, int64_t max_abs_sum, int32_t* 
   return QAOA_OK;
 }
 
+namespace {
+// Cost modes recorded for QAOA_COST_AUTO per (n, precision) (qaoa_set_cost_choice).
+std::mutex g_cost_mutex;
+std::map<std::pair<int, int>, int> g_cost_choice;
+
+int resolve_cost_mode(int n, int precision, int cost_mode) {
+  if (cost_mode != QAOA_COST_AUTO) return cost_mode;
+  std::lock_guard<std::mutex> lock(g_cost_mutex);
+  auto it = g_cost_choice.find(std::make_pair(n, precision));
+  return it != g_cost_choice.end() ? it->second : QAOA_COST_RECOMPUTE;
+}
+}  // namespace
+
+int qaoa_set_cost_choice(int n, int precision, int cost_mode) {
+  if (!qaoa_state_bytes(n, precision)) return QAOA_EINVAL;
+  if (cost_mode < QAOA_COST_AUTO || cost_mode > QAOA_COST_STREAM) return QAOA_EINVAL;
+  std::lock_guard<std::mutex> lock(g_cost_mutex);
+  if (cost_mode == QAOA_COST_AUTO) g_cost_choice.erase(std::make_pair(n, precision));
+  else g_cost_choice[std::make_pair(n, precision)] = cost_mode;
+  return QAOA_OK;
+}
+
 size_t qaoa_aux_bytes(int n, int precision, int cost_mode, int with_grad) {
   const size_t sb = qaoa_state_bytes(n, precision);
   if (!sb) return 0;
   size_t b = with_grad ? sb : 0;
-  if (cost_mode == QAOA_COST_STREAM) b += size_t(4) << n;
+  if (resolve_cost_mode(n, precision, cost_mode) == QAOA_COST_STREAM) b += size_t(4) << n;
   return b;
+}
+
+int qaoa_set_opts(qaoa_ctx* c, const qaoa_opts* o) {
+  if (!c) return QAOA_EINVAL;
+  if (!o) return c->set_err(QAOA_EINVAL, "opts is NULL");
+  auto onoff = [](int v) { return v == 0 || v == QAOA_ON || v == QAOA_OFF; };
+  auto order = [](int v) { return v == 0 || v == QAOA_ORDER_LOW_LAST || v == QAOA_ORDER_LOW_MIDDLE; };
+  if (o->fwd_shape != 0 && shape_from_opt(o->fwd_shape) < 0) return c->set_err(QAOA_EINVAL, "bad fwd_shape");
+  if (c->prec == QAOA_C128 && o->fwd_shape != 0 && o->fwd_shape != QAOA_SHAPE_5x3 && o->fwd_shape != QAOA_SHAPE_4x3)
+    return c->set_err(QAOA_EINVAL, "complex128 takes the 5x3 or 4x3 tile");
+  if (o->super_tile != 0 && (o->super_tile < 12 || o->super_tile > 20))
+    return c->set_err(QAOA_EINVAL, "super_tile outside 12..20");
+  if (!order(o->group_order) || !order(o->grad_order)) return c->set_err(QAOA_EINVAL, "bad group order");
+  if (!onoff(o->float_lanes) || !onoff(o->specialised) || !onoff(o->tile_tables) || !onoff(o->l2_prefetch) ||
+      !onoff(o->grad_checkpoint))
+    return c->set_err(QAOA_EINVAL, "on/off fields take 0, QAOA_ON or QAOA_OFF");
+  cudaStreamSynchronize(c->stream);  // queued work may still read the old plans' tables
+  c->opts = *o;
+  c->plans.clear();
+  c->bplans.clear();
+  return QAOA_OK;
+}
+
+int qaoa_get_opts(const qaoa_ctx* c, qaoa_opts* o) {
+  if (!c || !o) return QAOA_EINVAL;
+  static const int kShapeOpt[5] = {QAOA_SHAPE_5x3, QAOA_SHAPE_4x4, QAOA_SHAPE_5x2, QAOA_SHAPE_4x3, QAOA_SHAPE_5x4};
+  const int sid = fwd_shape_id(c, c->prec);
+  qaoa_opts r{};
+  r.fwd_shape = kShapeOpt[sid];
+  r.super_tile = smax_fwd(c, shape_of(sid, c->prec).T());
+  r.group_order = (group_order(c) & 3) == ORDER_LOW_MIDDLE ? QAOA_ORDER_LOW_MIDDLE : QAOA_ORDER_LOW_LAST;
+  r.float_lanes = float_lanes_flag(c) ? QAOA_ON : QAOA_OFF;
+  r.specialised = spec_enabled(c) ? QAOA_ON : QAOA_OFF;
+  r.tile_tables = on_off(c->opts.tile_tables, "QAOA_TILE_TABLES", 1) ? QAOA_ON : QAOA_OFF;
+  r.l2_prefetch = on_off(c->opts.l2_prefetch, "QAOA_L2PREFETCH", 0) ? QAOA_ON : QAOA_OFF;
+  r.grad_order = grad_base_order(c) == ORDER_LOW_MIDDLE ? QAOA_ORDER_LOW_MIDDLE : QAOA_ORDER_LOW_LAST;
+  r.grad_checkpoint = grad_checkpoint(c) ? QAOA_ON : QAOA_OFF;
+  *o = r;
+  return QAOA_OK;
 }
 
 int qaoa_init_graph(qaoa_ctx** out, int n, int m, const int32_t* u, const int32_t* v, const int32_t* w,
@@ -1041,7 +1138,7 @@ int qaoa_init_graph(qaoa_ctx** out, int n, int m, const int32_t* u, const int32_
     return fail(QAOA_ENOMEM, "state buffer size must equal qaoa_state_bytes(n, precision)");
   if (state_dev && (reinterpret_cast<uintptr_t>(state_dev) & 255))
     return fail(QAOA_EINVAL, "state buffer must be 256-byte aligned");
-  const int mode = cost_mode == QAOA_COST_AUTO ? QAOA_COST_RECOMPUTE : cost_mode;
+  const int mode = resolve_cost_mode(n, precision, cost_mode);
   if (aux_dev && aux_bytes < qaoa_aux_bytes(n, precision, mode, 0))
     return fail(QAOA_ENOMEM, "aux buffer smaller than qaoa_aux_bytes");
   if (aux_dev && (reinterpret_cast<uintptr_t>(aux_dev) & 255))
@@ -1130,7 +1227,7 @@ int qaoa_run_angles(qaoa_ctx* c, int p, const double* gamma, const double* beta)
   if (p < 0 || (p > 0 && (!gamma || !beta))) return c->set_err(QAOA_EINVAL, "bad p or angle arrays");
   for (int k = 0; k < p; ++k)
     if (!std::isfinite(gamma[k]) || !std::isfinite(beta[k])) return c->set_err(QAOA_EINVAL, "non-finite angle");
-  return run_forward(c, p, gamma, beta, group_order());
+  return run_forward(c, p, gamma, beta, group_order(c));
 }
 
 int qaoa_run(qaoa_ctx* c, int p, double dgamma, double dbeta) {
@@ -1386,9 +1483,9 @@ void* qaoa_state_ptr(qaoa_ctx* c) { return c ? c->state : nullptr; }
 int qaoa_describe_plan(int n, int precision, int p, int adjoint, char* out, int cap) {
   std::string s;
   try {
-    Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), smax_adj(), kMinUnitsLog2, group_order())
-                      : plan_forward(n, p, fwd_shape(precision), smax_fwd(fwd_shape(precision).T()), kMinUnitsLog2,
-                                   group_order());
+    const TileShape fsh = fwd_shape(nullptr, precision);
+    Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), smax_adj(), kMinUnitsLog2, group_order(nullptr))
+                      : plan_forward(n, p, fsh, smax_fwd(nullptr, fsh.T()), kMinUnitsLog2, group_order(nullptr));
     std::string e = validate(pl);
     s = pl.describe();
     if (!e.empty()) s += "INVALID: " + e + "\n";

@@ -299,12 +299,14 @@ __global__ void __launch_bounds__(256) block_sum_kernel(const typename Cx<Real>:
   __shared__ double red[8];
   const size_t base = (size_t)blockIdx.x << B;
   const int len = 1 << B;
-  Real s = 0;
+  // |psi_x|^2 formed and summed in FP64 exactly as the shot kernels' in-block
+  // walk forms it, so a block sum and the walk over the same block differ only
+  // by FP64 summation order
+  double d = 0.0;
   for (int i = threadIdx.x; i < len; i += 256) {
     const typename Cx<Real>::T a = __ldcg(psi + base + i);
-    s = fma(a.x, a.x, fma(a.y, a.y, s));
+    d += double(a.x) * double(a.x) + double(a.y) * double(a.y);
   }
-  double d = double(s);
   for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = d;
   __syncthreads();

@@ -30,7 +30,7 @@ thread_local std::string g_batch_create_error;
 
 constexpr long long kBatchMaxAbsWeight = 1 << 20;
 constexpr int kBatchMaxP = 64;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per dependency wait
+constexpr unsigned long long kWaitNs = 2000000000ull;  // default limit of a dependency wait: 2 s
 
 struct InstPlan {
   int n = 0, p = 0, mode = 0;
@@ -516,7 +516,7 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
   A.ext_max = d_emax;
   A.grads = d_grads;
   A.error = d_err;
-  A.wait_ns = kWaitNs;
+  A.wait_ns = o.wait_ns > 0 ? (unsigned long long)o.wait_ns : kWaitNs;
   b->grid = std::max(1, std::min(ctas, b->nitems));
   b->args_adj = A;
   b->args_adj.items = d_items_adj;

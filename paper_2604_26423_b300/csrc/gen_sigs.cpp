@@ -8,7 +8,9 @@
 // Configurations: tile shape 4x3 (T = 12), n = 13..34, p = 0..12, the forward
 // group orders of qaoa_run (low group last) and of the gradient (low group in
 // the middle), both with floating coalescing bits; adjoint plans in the
-// gradient's order, p = 1..12.
+// gradient's order, p = 1..12. Tile shape 5x4 (T = 14): forward plans of
+// qaoa_run's order for n = 27..34, p = 0..12 (the sizes where it takes one
+// mixer group fewer than 4x3).
 //
 // Usage: gen_sigs <output file>
 #include <cstdio>
@@ -67,17 +69,26 @@ int main(int argc, char** argv) {
       if (p >= 1) collect(plan_backward(n, p, ash, T, 9, ORDER_LOW_MIDDLE), adj);
     }
   }
+  TileShape sh54 = sh;
+  sh54.R = 5;
+  sh54.WB = 4;
+  std::set<std::vector<uint32_t>> fwd54;
+  for (int n = 27; n <= 34; ++n)
+    for (int p = 0; p <= 12; ++p)
+      collect(plan_forward(n, p, sh54, sh54.T(), 9, ORDER_LOW_LAST | PLAN_FLOAT_LANES), fwd54);
   FILE* f = fopen(argv[1], "w");
   if (!f) {
     perror(argv[1]);
     return 1;
   }
   fprintf(f, "// Generated by gen_sigs.cpp (build step): round-signature sequences of the\n");
-  fprintf(f, "// specialised complex64 4x3 pass kernels. Do not edit.\n");
-  fprintf(f, "// QAOA_FWD_SIG / QAOA_ADJ_SIG(number of rounds, round signatures...)\n");
+  fprintf(f, "// specialised complex64 pass kernels. Do not edit.\n");
+  fprintf(f, "// QAOA_FWD_SIG / QAOA_ADJ_SIG (4x3 tiles), QAOA_FWD_SIG54 (5x4 tiles)\n");
+  fprintf(f, "// (number of rounds, round signatures...)\n");
   emit(f, "QAOA_FWD_SIG", fwd);
   emit(f, "QAOA_ADJ_SIG", adj);
+  emit(f, "QAOA_FWD_SIG54", fwd54);
   fclose(f);
-  printf("%zu forward, %zu adjoint sequences\n", fwd.size(), adj.size());
+  printf("%zu forward, %zu adjoint, %zu forward 5x4 sequences\n", fwd.size(), adj.size(), fwd54.size());
   return 0;
 }

@@ -5,12 +5,12 @@
 // (per-block probability sums and their prefix) in one fixed file-scope device
 // array instead of buffers obtained from cudaMalloc. It is meant for callers
 // that must not allocate while they run: a plugin whose enqueue step runs
-// inside a host framework that owns every device allocation, a serving loop
-// with a preallocated memory budget, or code sitting between stream-capture
-// begin/end calls, where cudaMalloc is not permitted.
+// inside a host framework that owns every device allocation, or a serving loop
+// with a preallocated memory budget that a cudaMalloc would break.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 
 #include "qaoa.h"
@@ -33,7 +33,10 @@ std::mutex g_mutex;
 double* g_scratch_dev[kMaxDevices] = {};
 
 // Looks up (once per device, with that device current) the device address of
-// the scratch array.
+// the scratch array. The address is kept for the life of the process: after a
+// device reset (cudaDeviceReset, or a reset of the primary context) it is
+// stale, so a process that resets a device must not call this entry point on
+// that device again.
 int scratch_for_current_device(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QAOA_ECUDA;
@@ -80,12 +83,18 @@ extern "C" int qaoa_sample_state_noalloc(const void* state_dev, int n, int preci
   else
     block_sum_kernel<float><<<(unsigned)nb, 256, 0, st>>>(static_cast<const float2*>(state_dev), B, sums);
   scan_kernel<<<1, 1024, 0, st>>>(sums, nb, pre);
-  const int tb = 128, gb = (shots + tb - 1) / tb;
+  // one warp per shot, four per block: the search and in-block walk of
+  // qaoa_sample (coalesced 32-amplitude steps, the same FP64 order)
+  constexpr int kWarpsPerBlock = 4;
+  const long long gb = ((long long)shots + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (gb > INT_MAX) return QAOA_EINVAL;
   if (precision == QAOA_C128)
-    shot_kernel<double><<<gb, tb, 0, st>>>(static_cast<const double2*>(state_dev), B, pre, nb, shots, uniforms_dev,
-                                           seed, reinterpret_cast<unsigned long long*>(out_dev));
+    shot_warp_kernel<double><<<(unsigned)gb, 32 * kWarpsPerBlock, 0, st>>>(
+        static_cast<const double2*>(state_dev), B, pre, nb, shots, uniforms_dev, seed,
+        reinterpret_cast<unsigned long long*>(out_dev));
   else
-    shot_kernel<float><<<gb, tb, 0, st>>>(static_cast<const float2*>(state_dev), B, pre, nb, shots, uniforms_dev,
-                                          seed, reinterpret_cast<unsigned long long*>(out_dev));
+    shot_warp_kernel<float><<<(unsigned)gb, 32 * kWarpsPerBlock, 0, st>>>(
+        static_cast<const float2*>(state_dev), B, pre, nb, shots, uniforms_dev, seed,
+        reinterpret_cast<unsigned long long*>(out_dev));
   return cudaGetLastError() == cudaSuccess ? QAOA_OK : QAOA_ECUDA;
 }

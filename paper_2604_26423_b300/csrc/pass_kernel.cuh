@@ -41,6 +41,8 @@ struct PassArgs {
                           // the final pass when its tiles are index-contiguous, or nullptr
   int phase_in_smem;      // copy the phase table into shared memory
   int l2hint;             // L2 priorities: keep sub-pass outputs that are read back
+  int prefetch;           // prefetch the CTA's next tile into L2 while this one runs
+                          // (passes of one tile per super-tile that load the state)
   // exhaustive extremes in the |+> round (every index visited once): packed
   // keys [(C - c_lo) << 34 | x, (c_hi - C) << 34 | x], each the minimum over
   // all x (smallest C, resp. largest C, then smallest index); must hold ~0 on
@@ -69,6 +71,23 @@ struct Lay {
 // warps per CTA of a shape
 template <int WB>
 constexpr int NT32 = 1 << WB;
+
+// Tile bits above the 2^12-amplitude sampling block (0 for T <= 12, at most 2).
+template <int R, int WB>
+constexpr int kBlkBits = R + 5 + WB > 12 ? R + 5 + WB - 12 : 0;
+
+// Tile bit held by register (kind 0), lane (1) or warp (2) position i of a
+// round: a compile-time constant of the layout for a specialised round
+// (SIG != 0), else read from the round descriptor.
+template <int R, int WB, uint32_t SIG>
+__device__ __forceinline__ int tile_bit(const RoundDev& rd, int kind, int i) {
+  if constexpr (SIG != 0) {
+    constexpr int L = int(SIG & 3u);
+    return kind == 0 ? Lay<R, WB, L>::reg(i) : kind == 1 ? Lay<R, WB, L>::lane(i) : Lay<R, WB, L>::warp(i);
+  } else {
+    return kind == 0 ? rd.reg[i] : kind == 1 ? rd.lane[i] : rd.warp[i];
+  }
+}
 
 __host__ __device__ constexpr int ctz_c(int k) {
   int b = 0;
@@ -306,7 +325,7 @@ __device__ __forceinline__ void reduce_thread_sums(const double* wacc, double& s
 // One round. For a round whose source is global memory, v already holds the
 // loaded amplitudes (issued before the tile's barrier). Reduction partials:
 // wacc[2 t], wacc[2 t + 1] hold thread t's FP64 running [norm, <C>] sums;
-// wacc[2 NT + 2 w + h] the FP32 warp totals of sampling block h of the tile.
+// wacc[(2 + h) NT + t] thread t's partial of sampling block h of the tile.
 // CC: the kernel contains the C(x) code (cost phase, |+> initialisation and
 // reductions); passes without any of them run an instantiation without it
 // (smaller code, measured faster).
@@ -541,32 +560,47 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       // |psi|^2 and C(x) do not depend on the storage order of (re, im)
       Real sn = 0, scc = 0;
       if (A.bsum) {
-        // also |psi|^2 per sampling block: tile bit 12 (if any) splits the tile
-        int hreg = -1, hthr = 0;
+        // also |psi|^2 per sampling block of 2^12 amplitudes: tile bits 12
+        // and 13 (if any) select the block; hr[k]: the register position of
+        // tile bit 12 + k, or -1 when a lane or warp bit holds it (hthr)
+        int hr[2] = {-1, -1}, hthr = 0;
 #pragma unroll
-        for (int i = 0; i < R; ++i) hreg = rd.reg[i] == 12 ? i : hreg;
+        for (int i = 0; i < R; ++i) {
+          const int b = tile_bit<R, WB, SIG>(rd, 0, i);
+          if (b >= 12 && b < 12 + kBlkBits<R, WB>) hr[b - 12] = i;
+        }
 #pragma unroll
-        for (int i = 0; i < 5; ++i) hthr |= rd.lane[i] == 12 ? (lane >> i & 1) : 0;
+        for (int i = 0; i < 5; ++i) {
+          const int b = tile_bit<R, WB, SIG>(rd, 1, i);
+          if (b >= 12 && b < 12 + kBlkBits<R, WB>) hthr |= (lane >> i & 1) << (b - 12);
+        }
 #pragma unroll
-        for (int i = 0; i < WB; ++i) hthr |= rd.warp[i] == 12 ? (warp >> i & 1) : 0;
-        Real s0 = 0, s1 = 0;
+        for (int i = 0; i < WB; ++i) {
+          const int b = tile_bit<R, WB, SIG>(rd, 2, i);
+          if (b >= 12 && b < 12 + kBlkBits<R, WB>) hthr |= (warp >> i & 1) << (b - 12);
+        }
+        constexpr int NB = 1 << kBlkBits<R, WB>;
+        Real sb[NB];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) sb[k] = 0;
         for_costs(P.cpr, [&](int j, int c) {
           const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
           sn += pr;
           scc = fma(pr, Real(c), scc);
-          if (hreg >= 0 ? (j >> hreg & 1) : hthr) s1 += pr; else s0 += pr;
-        });
-        // block sums: warp totals in the state precision (errors relative to
-        // the block's own mass), added in FP64 across warps by the caller
+          int h = hthr;
+          if (hr[0] >= 0) h |= j >> hr[0] & 1;
+          if (NB > 2 && hr[1] >= 0) h |= (j >> hr[1] & 1) << 1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        }
-        if (lane == 0) {
-          wacc[2 * (32 << WB) + 2 * warp] = double(s0);
-          wacc[2 * (32 << WB) + 2 * warp + 1] = double(s1);
-        }
+          for (int k = 0; k < NB; ++k)
+            if (h == k) sb[k] += pr;
+        });
+        // block sums: each thread's partial over its register amplitudes
+        // (at most 2^R terms in the state precision), then FP64 from there on:
+        // the partials go to shared memory and the caller adds them in FP64
+        // in a fixed order
+        const int tid = (warp << 5) | lane;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) wacc[(2 + k) * (32 << WB) + tid] = double(sb[k]);
       } else {
         for_costs(P.cpr, [&](int j, int c) {
           const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
@@ -637,6 +671,22 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       bool load0;
       if constexpr (kSpec) load0 = (first_sig<RS...>() >> 2 & 3u) == SRC_GLOBAL_D;
       else load0 = sp.rd[0].src == SRC_GLOBAL_D;
+      if (load0 && A.prefetch && sp.ninner == 0) {
+        // the CTA's next tile (unit + gridDim.x) into L2: its 2^(T-4) runs of
+        // 16 consecutive amplitudes (tile bits 0..3 are global bits 0..3),
+        // one 128-byte line each
+        const uint64_t next = unit + gridDim.x;
+        if (next < P.n_units) {
+          const uint64_t nbase = P.outer_runs.scatter(next);
+          const C2* gs = reinterpret_cast<const C2*>(A.state);
+          for (int r = tid; r < (1 << (T - 4)); r += NT) {
+            uint64_t g = nbase;
+#pragma unroll
+            for (int j = 4; j < T; ++j) g |= uint64_t(r >> (j - 4) & 1) << sp.pos[j];
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(gs + g));
+          }
+        }
+      }
       if (load0) {
         const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
         const C2* gs = reinterpret_cast<const C2*>(A.state);
@@ -702,12 +752,17 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         red_last = sp.rd[sp.nrounds - 1].reduce != 0;
       }
       if (CC && A.bsum && red_last) {
-        // this tile is 2^T consecutive amplitudes: its 2^(T-12) block sums, in warp order
+        // this tile is 2^T consecutive amplitudes: its 2^(T-12) block sums;
+        // warp k adds block k's per-thread partials in FP64 (each lane a
+        // strided set, then a shuffle tree: a fixed order)
+        constexpr int NB = 1 << kBlkBits<R, WB>;
         __syncthreads();
-        if (tid < (1 << (T - 12))) {
+        if (warp < NB) {
           double b = 0.0;
-          for (int w = 0; w < NT / 32; ++w) b += wacc[2 * NT + 2 * w + tid];
-          A.bsum[(gbase >> 12) + tid] = b;
+          for (int t = lane; t < NT; t += 32) b += wacc[(2 + warp) * NT + t];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+          if (lane == 0) A.bsum[(gbase >> 12) + warp] = b;
         }
       }
     }
@@ -735,8 +790,9 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
     phase = ptab;
   }
-  // per-thread FP64 running sums [norm, <C>], then per-warp block sums
-  __shared__ double wacc[2 * NT + 2 * NT / 32];
+  // per-thread FP64 running sums [norm, <C>], then per-thread block-sum
+  // partials (2^(T-12) blocks per tile)
+  __shared__ double wacc[(2 + (1 << kBlkBits<R, WB>)) * NT];
   wacc[2 * tid] = 0.0;
   wacc[2 * tid + 1] = 0.0;
 
@@ -766,7 +822,8 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
 
 // Generic forward pass: rounds decoded from the descriptor at run time.
 template <typename Real, int R, int WB, bool FAST, bool CC>
-__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : 2) : (R + WB <= 7 ? 2 : 1))
+__global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : R + WB <= 8 ? 2 : 1)
+                                                              : (R + WB <= 7 ? 2 : 1))
 fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   fwd_pass_body<Real, R, WB, FAST, CC>(P, A);
 }
@@ -775,7 +832,7 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
 // (one sub-pass of one tile per super-tile): the rounds' operations, layouts
 // and masks are compile-time constants.
 template <int R, int WB, bool FAST, uint32_t... RS>
-__global__ void __launch_bounds__(32 << WB, R + WB <= 7 ? 4 : 2)
+__global__ void __launch_bounds__(32 << WB, R + WB <= 7 ? 4 : R + WB <= 8 ? 2 : 1)
 fwd_spec_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
   fwd_pass_body<float, R, WB, FAST, sigs_need_c<RS...>(), RS...>(P, A);
 }

@@ -14,11 +14,13 @@ struct AdjSpec {
 };
 
 #define QAOA_FWD_SIG(nr, ...)
+#define QAOA_FWD_SIG54(nr, ...)
 #define QAOA_ADJ_SIG(nr, ...) {nr, {__VA_ARGS__}, &adj_spec_kernel<4, 3, true, __VA_ARGS__>},
 const AdjSpec kAdjSpecs[] = {
 #include "pass_sigs.inc"
 };
 #undef QAOA_FWD_SIG
+#undef QAOA_FWD_SIG54
 #undef QAOA_ADJ_SIG
 
 }  // namespace

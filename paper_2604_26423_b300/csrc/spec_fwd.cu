@@ -1,6 +1,6 @@
 // spec_fwd.cu -- specialised forward pass kernels (see spec.h): one
-// instantiation of fwd_spec_kernel<4, 3, fast form, signatures...> per
-// sequence in pass_sigs.inc.
+// instantiation of fwd_spec_kernel<R, WB, fast form, signatures...> per
+// sequence in pass_sigs.inc (4x3 and 5x4 tiles).
 #include "spec.h"
 
 #include "plan.h"
@@ -17,10 +17,20 @@ struct FwdSpec {
 
 #define QAOA_FWD_SIG(nr, ...) {nr, {__VA_ARGS__}, &fwd_spec_kernel<4, 3, true, __VA_ARGS__>},
 #define QAOA_ADJ_SIG(nr, ...)
+#define QAOA_FWD_SIG54(nr, ...)
 const FwdSpec kFwdSpecs[] = {
 #include "pass_sigs.inc"
 };
 #undef QAOA_FWD_SIG
+#undef QAOA_FWD_SIG54
+
+#define QAOA_FWD_SIG(nr, ...)
+#define QAOA_FWD_SIG54(nr, ...) {nr, {__VA_ARGS__}, &fwd_spec_kernel<5, 4, true, __VA_ARGS__>},
+const FwdSpec kFwdSpecs54[] = {
+#include "pass_sigs.inc"
+};
+#undef QAOA_FWD_SIG
+#undef QAOA_FWD_SIG54
 #undef QAOA_ADJ_SIG
 
 }  // namespace
@@ -31,8 +41,18 @@ uint32_t round_sig_dev(const RoundDev& rd) {
          uint32_t(rd.mixA & 31) << 8 | uint32_t(rd.mixB & 31) << 13;
 }
 
-FwdPassKernel find_fwd_spec(const SubDev& sd) {
-  for (const FwdSpec& f : kFwdSpecs) {
+FwdPassKernel find_fwd_spec(const SubDev& sd, int R, int WB) {
+  const FwdSpec* begin = nullptr;
+  const FwdSpec* end = nullptr;
+  if (R == 4 && WB == 3) {
+    begin = kFwdSpecs;
+    end = kFwdSpecs + sizeof(kFwdSpecs) / sizeof(kFwdSpecs[0]);
+  } else if (R == 5 && WB == 4) {
+    begin = kFwdSpecs54;
+    end = kFwdSpecs54 + sizeof(kFwdSpecs54) / sizeof(kFwdSpecs54[0]);
+  }
+  for (const FwdSpec* it = begin; it != end; ++it) {
+    const FwdSpec& f = *it;
     if (f.nr != sd.nrounds) continue;
     bool eq = true;
     for (int r = 0; r < f.nr && eq; ++r) eq = f.rs[r] == round_sig_dev(sd.rd[r]);

@@ -31,7 +31,8 @@ EXPORTS = ("qaoa_state_bytes", "qaoa_aux_bytes", "qaoa_init_graph", "qaoa_run", 
            "qaoa_batch_create", "qaoa_batch_run", "qaoa_batch_results", "qaoa_batch_state",
            "qaoa_batch_describe", "qaoa_batch_bytes", "qaoa_batch_last_error", "qaoa_batch_free",
            "qaoa_sample_cuts", "qaoa_mean_of_means", "qaoa_classify_regime", "qaoa_noisy_expect",
-           "qaoa_overlap_ratio", "qaoa_fit_k0", "qaoa_max_weight_sum", "qaoa_quantize_weights")
+           "qaoa_overlap_ratio", "qaoa_fit_k0", "qaoa_max_weight_sum", "qaoa_quantize_weights",
+           "qaoa_set_opts", "qaoa_get_opts", "qaoa_set_cost_choice")
 PROFILE_KINDS = {"pass": 0, "adjoint": 1, "cost": 2, "sample": 3, "small": 4}
 
 _lib = None
@@ -107,8 +108,41 @@ def load():
     lib.qaoa_fit_k0.restype = ctypes.c_double
     lib.qaoa_classify_regime.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_double]
+    lib.qaoa_set_opts.argtypes = [vp, P(Opts)]
+    lib.qaoa_get_opts.argtypes = [vp, P(Opts)]
+    lib.qaoa_set_cost_choice.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     _lib = lib
     return lib
+
+
+ON, OFF = 1, 2
+ORDERS = {"last": 1, "middle": 2}
+SHAPES = {"5x3": 1, "4x4": 2, "5x2": 3, "4x3": 4, "5x4": 5}
+
+
+class Opts(ctypes.Structure):
+    """Kernel configuration of one context (``qaoa_opts``; 0 = library default)."""
+    _fields_ = [("fwd_shape", ctypes.c_int), ("super_tile", ctypes.c_int), ("group_order", ctypes.c_int),
+                ("float_lanes", ctypes.c_int), ("specialised", ctypes.c_int), ("tile_tables", ctypes.c_int),
+                ("l2_prefetch", ctypes.c_int), ("grad_order", ctypes.c_int), ("grad_checkpoint", ctypes.c_int)]
+
+
+def make_opts(shape=None, super_tile=None, order=None, float_lanes=None, specialised=None, tile_tables=None,
+              l2_prefetch=None, grad_order=None, grad_checkpoint=None) -> Opts:
+    """``Opts`` from readable values: shape "4x3" / "5x4" / ..., order "last" /
+    "middle", booleans for the on/off fields; None keeps the default."""
+    b = lambda x: 0 if x is None else (ON if x else OFF)  # noqa: E731
+    return Opts(fwd_shape=SHAPES[shape] if shape else 0, super_tile=int(super_tile or 0),
+                group_order=ORDERS[order] if order else 0, float_lanes=b(float_lanes), specialised=b(specialised),
+                tile_tables=b(tile_tables), l2_prefetch=b(l2_prefetch),
+                grad_order=ORDERS[grad_order] if grad_order else 0, grad_checkpoint=b(grad_checkpoint))
+
+
+def set_cost_choice(n: int, precision, cost_mode) -> None:
+    """Records the cost mode that QAOA_COST_AUTO selects for (n, precision)."""
+    rc = load().qaoa_set_cost_choice(int(n), _PREC[precision], _COST[cost_mode])
+    if rc != QAOA_OK:
+        raise QaoaError(rc, "qaoa_set_cost_choice")
 
 
 def _f64(a):
@@ -163,7 +197,7 @@ class Simulator:
     """
 
     def __init__(self, n, u, v, w, scale=0.1, precision="c64", cost_mode="recompute", with_grad=False,
-                 state=None, aux=None, stream=None):
+                 state=None, aux=None, stream=None, opts=None):
         import torch
         lib = load()
         if not torch.cuda.is_available():
@@ -203,6 +237,8 @@ class Simulator:
             raise QaoaError(rc, lib.qaoa_last_error(None).decode())
         self._ctx = ctx
         self._lib = lib
+        if opts is not None:
+            self.set_opts(opts)
 
     # -- helpers
     @classmethod
@@ -243,6 +279,17 @@ class Simulator:
         self.close()
 
     # -- API
+    def set_opts(self, opts):
+        """Kernel configuration (``Opts``, or a dict of ``make_opts`` arguments)."""
+        o = opts if isinstance(opts, Opts) else make_opts(**opts)
+        self._check(self._lib.qaoa_set_opts(self._ctx, ctypes.byref(o)))
+
+    def get_opts(self) -> dict:
+        """The configuration in effect, every field resolved."""
+        o = Opts()
+        self._check(self._lib.qaoa_get_opts(self._ctx, ctypes.byref(o)))
+        return {k: getattr(o, k) for k, _ in Opts._fields_}
+
     def run(self, p: int, dgamma: float, dbeta: float):
         self._check(self._lib.qaoa_run(self._ctx, int(p), float(dgamma), float(dbeta)))
 
@@ -412,7 +459,7 @@ def classify_regime(r_obs: float, rand_mean: float, rand_sigma: float, ideal_mea
 class BatchOpts(ctypes.Structure):
     """Scheduling knobs of ``qaoa_batch_create`` (0 = library default)."""
     _fields_ = [("solo_max_n", ctypes.c_int), ("window_items", ctypes.c_int), ("window_mb", ctypes.c_int),
-                ("max_units", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+                ("max_units", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("wait_ns", ctypes.c_int64)]
 
 
 BATCH_FIELDS = ("exp_c", "r", "norm", "c_min", "c_max", "argmin", "argmax", "d_dgamma", "d_dbeta")

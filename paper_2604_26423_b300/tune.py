@@ -2,11 +2,15 @@
 
 Forward path: the cost mode (C(x) recomputed in each tile from the weight
 matrix, or streamed from a precomputed int32 diagonal), the tile shape (qubits
-per shared-memory tile and CTAs per SM), the super-tile size and the group
-order of the pass plan are timed on the caller's instance and the fastest is
-kept. Batched path: the scheduling knobs of ``qaoa_batch_create``
-(which instances run all their passes in one CTA, items per pass, CTAs per SM)
-are timed on the caller's batch.
+per shared-memory tile and CTAs per SM), the super-tile size, the group order
+of the pass plan and the floating coalescing bits are timed on the caller's
+instance and the fastest is kept. Each candidate runs on its own context with
+its configuration set through ``qaoa_set_opts`` (no process-wide state), and
+the winning cost mode is recorded with ``qaoa_set_cost_choice`` so that
+QAOA_COST_AUTO contexts of that size and precision use it. Batched path: the
+scheduling knobs of ``qaoa_batch_create`` (which instances run all their
+passes in one CTA, items per pass, CTAs per SM) are timed on the caller's
+batch.
 
 Every candidate runs the full computation (same plan semantics, same results
 up to FP32 summation order); timing is by CUDA events on the launching stream
@@ -14,50 +18,30 @@ after a warm-up run. Choices are cached in memory per workload key.
 """
 from __future__ import annotations
 
-import contextlib
 import itertools
-import os
 
 _cache: dict = {}
 
 # tile shape of the forward kernel: 2^R registers x 2^WB warps (complex128:
 # 4x3 or 5x3)
-FWD_SHAPES = {"5x3": "5x3", "4x4": "4x4", "5x2": "5x2", "4x3": "4x3"}
+FWD_SHAPES = ("5x3", "4x4", "5x2", "4x3", "5x4")
 # largest super-tile (index bits kept together through L2 by one CTA)
 SUPER_TILES = (12, 13, 14, 15)
 # group order of the pass plans: the last layer ending on the low group (its
 # final pass also writes the sampling block sums), or the low group away from
 # the fused passes
 GROUP_ORDERS = ("last", "middle")
-# coalescing bits 0..4 applied in a plain high-group pass of each layer (1) or
+# coalescing bits applied in a plain high-group pass of each layer (1) or
 # with the low group (0)
 FLOAT_LANES = (1, 0)
-
-
-@contextlib.contextmanager
-def _env(settings: dict):
-    old = {k: os.environ.get(k) for k in settings}
-    try:
-        for k, v in settings.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = str(v)
-        yield
-    finally:
-        for k, v in old.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
 
 
 def forward_candidates(n: int, precision: str = "c64", modes=("recompute", "stream"), shapes=None,
                        super_tiles=SUPER_TILES, orders=GROUP_ORDERS, float_lanes=FLOAT_LANES):
     """Configurations to time for one instance: cost mode x tile shape x super-tile bits x group order x
-    floating lane bits."""
+    floating lane bits (a super-tile below the shape's tile means one tile)."""
     if shapes is None:
-        shapes = tuple(FWD_SHAPES) if precision == "c64" else ("4x3", "5x3")
+        shapes = FWD_SHAPES if precision == "c64" else ("4x3", "5x3")
     out = []
     for mode, shape, st, order, fl in itertools.product(modes, shapes, super_tiles, orders, float_lanes):
         if st > n:
@@ -66,12 +50,10 @@ def forward_candidates(n: int, precision: str = "c64", modes=("recompute", "stre
     return out
 
 
-def config_env(cfg: dict) -> dict:
-    """Environment settings that select a forward configuration in the library."""
-    return {"QAOA_FWD_SHAPE": FWD_SHAPES[cfg["shape"]],
-            "QAOA_FWD_SHAPE_C128": cfg["shape"] if cfg["shape"] in ("4x3", "5x3") else None,
-            "QAOA_SMAX": cfg["super_tile"], "QAOA_GROUP_ORDER": cfg.get("order", "last"),
-            "QAOA_FLOAT_LANES": int(cfg.get("float_lanes", 1))}
+def config_opts(cfg: dict) -> dict:
+    """``qaoa.make_opts`` arguments that select a forward configuration."""
+    return {"shape": cfg["shape"], "super_tile": cfg.get("super_tile"), "order": cfg.get("order", "last"),
+            "float_lanes": bool(cfg.get("float_lanes", 1))}
 
 
 def _time_ms(fn, stream, reps: int) -> float:
@@ -91,7 +73,7 @@ def _time_ms(fn, stream, reps: int) -> float:
 def tune_forward(n, u, v, w, p, dgamma, dbeta, scale=0.1, precision="c64", candidates=None, reps=1, key=None):
     """Times qaoa_run (p LR layers) under each candidate; returns (best, timings)."""
     import torch
-    from .qaoa import Simulator
+    from .qaoa import Simulator, set_cost_choice
     key = key or ("fwd", n, precision, p, len(u))
     if key in _cache:
         return _cache[key]
@@ -100,15 +82,16 @@ def tune_forward(n, u, v, w, p, dgamma, dbeta, scale=0.1, precision="c64", candi
     timings = []
     state = None
     for cfg in cands:
-        with _env(config_env(cfg)):
-            s = Simulator(n, u, v, w, scale, precision, cost_mode=cfg["cost_mode"], state=state)
-            try:
-                state = s._state_t
-                ms = _time_ms(lambda: s.run(p, dgamma, dbeta), stream, reps)
-            finally:
-                s.close()
+        s = Simulator(n, u, v, w, scale, precision, cost_mode=cfg["cost_mode"], state=state, opts=config_opts(cfg))
+        try:
+            state = s._state_t
+            ms = _time_ms(lambda: s.run(p, dgamma, dbeta), stream, reps)
+        finally:
+            s.close()
         timings.append(dict(cfg, ms=ms))
     best = min(timings, key=lambda t: t["ms"])
+    if len({t["cost_mode"] for t in timings}) > 1:
+        set_cost_choice(n, precision, best["cost_mode"])
     _cache[key] = (best, timings)
     return best, timings
 

@@ -87,11 +87,13 @@ def test_tuner_candidates():
     assert {"cost_mode": "recompute", "shape": "5x3", "super_tile": 13, "order": "last", "float_lanes": 0} in c
     assert all(x["super_tile"] <= 33 for x in c)
     assert {x["shape"] for x in tune.forward_candidates(30, "c128")} == {"4x3", "5x3"}
-    env = tune.config_env({"cost_mode": "stream", "shape": "4x4", "super_tile": 14, "order": "middle",
-                           "float_lanes": 0})
-    assert env == {"QAOA_FWD_SHAPE": "4x4", "QAOA_FWD_SHAPE_C128": None, "QAOA_SMAX": 14,
-                   "QAOA_GROUP_ORDER": "middle", "QAOA_FLOAT_LANES": 0}
-    assert tune.config_env({"shape": "5x3", "super_tile": 13})["QAOA_FWD_SHAPE_C128"] == "5x3"
+    assert "5x4" in {x["shape"] for x in c}
+    opts = tune.config_opts({"cost_mode": "stream", "shape": "4x4", "super_tile": 14, "order": "middle",
+                             "float_lanes": 0})
+    assert opts == {"shape": "4x4", "super_tile": 14, "order": "middle", "float_lanes": False}
+    o = qaoa.make_opts(**opts)
+    assert (o.fwd_shape, o.super_tile, o.group_order, o.float_lanes) == (qaoa.SHAPES["4x4"], 14, 2, qaoa.OFF)
+    assert qaoa.make_opts().fwd_shape == 0 and qaoa.make_opts(specialised=True).specialised == qaoa.ON
     b = tune.batch_candidates(solo=(16,), units=(1, 2), ctas=(2,))
     assert b == [dict(solo_max_n=16, max_units=1, ctas_per_sm=2), dict(solo_max_n=16, max_units=2, ctas_per_sm=2)]
 

@@ -1,0 +1,164 @@
+"""The benchmark's plan shape anchored to the oracle and to complex128.
+
+The K_33 benchmark runs plans of four mixer groups (a low shared-memory group
+plus three windows of high bits) with cross-layer fused passes and the
+specialised kernels compiled for those round sequences. From 27 qubits the
+same kind of plan is chosen, and the oracle still finishes in about a minute,
+so these tests compare that plan element by element with the oracle's
+gate-by-gate complex128 state (Sec. II-B, Eqs. UC and UB), in both
+precisions, both cost modes and both group orders.
+
+Where the oracle cannot run (K_32, 64 GiB in complex128), the complex64 path
+is compared with the complex128 path of the same GPU.
+
+Tolerances (the benchmark spec's equivalence rules): complex128 state L2 <= 1e-12;
+complex64 state L2 <= 1e-4; |r - r_oracle| <= 1e-6 for both (stated per run
+on stdout); extremes and their indices exact.
+"""
+import re
+
+import pytest
+
+import oracle
+from paper_2604_26423_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+S = 0.1
+
+@pytest.fixture(scope="module")
+def refs():
+    # one oracle run per size for the whole module (2 GiB and 4 GiB states),
+    # released when the module's tests are done
+    cache = {}
+    yield cache
+    cache.clear()
+
+
+def _oracle(refs, n, p):
+    if (n, p) not in refs:
+        u, v, w = inputs.complete_graph(n, 2700 + n)
+        g, b = oracle.lr_schedule(p, 0.6, 0.3)
+        refs[(n, p)] = (u, v, w, oracle.run(n, u, v, w, S, g, b))
+    return refs[(n, p)]
+
+
+def _groups(n, p, prec):
+    from paper_2604_26423_b300.qaoa import describe_plan
+    text = describe_plan(n, p, prec)
+    return int(re.search(r"groups=(\d+)", text).group(1)), int(re.search(r"passes=(\d+)", text).group(1))
+
+
+@pytest.mark.parametrize("order", ["last", "middle"])
+@pytest.mark.parametrize("cost_mode", ["recompute", "stream"])
+@pytest.mark.parametrize("prec,shape", [("c64", "4x3"), ("c64", "5x4"), ("c128", "4x3")])
+@pytest.mark.parametrize("n", [27, 28])
+def test_benchmark_plan_shape_vs_oracle(n, prec, shape, cost_mode, order, monkeypatch, refs):
+    from paper_2604_26423_b300.qaoa import Simulator
+    p = 3
+    monkeypatch.setenv("QAOA_GROUP_ORDER", order)
+    monkeypatch.setenv("QAOA_FLOAT_LANES", "1")
+    monkeypatch.setenv("QAOA_FWD_SHAPE" if prec == "c64" else "QAOA_FWD_SHAPE_C128", shape)
+    u, v, w, ref = _oracle(refs, n, p)
+    with Simulator(n, u, v, w, S, prec, cost_mode=cost_mode) as s:
+        s.run(p, 0.6, 0.3)
+        res = s.expect()
+        got = s.state()
+        import torch
+        want = torch.from_numpy(ref["psi"]).to(got.device)
+        l2 = float(torch.linalg.vector_norm(got.to(torch.complex128) - want))
+        del want
+    groups, passes = _groups(n, p, prec)
+    r_err = abs(res["r"] - ref["r"])
+    print(f"\nK_{n} p={p} {prec} {shape} {cost_mode} order={order}: {groups} groups, {passes} passes, "
+          f"state L2 {l2:.2e}, |r - r_oracle| {r_err:.2e}")
+    assert l2 <= (1e-12 if prec == "c128" else 1e-4), l2
+    assert r_err <= 1e-6, r_err
+    assert abs(res["exp_c"] - ref["exp_c"]) <= (1e-11 if prec == "c128" else 2e-6) * ref["exp_c"]
+    assert (res["c_min"], res["c_max"], res["argmin"], res["argmax"]) == \
+        (ref["c_min"], ref["c_max"], ref["argmin"], ref["argmax"])
+
+
+def test_benchmark_plans_have_fused_passes():
+    # the plans checked above are of the benchmark's kind: more than two
+    # groups, so each layer boundary is a fused [mixer][cost][mixer] pass
+    from paper_2604_26423_b300.qaoa import describe_plan
+    for n in (27, 28, 33):
+        text = describe_plan(n, 3, "c64")
+        groups = int(re.search(r"groups=(\d+)", text).group(1))
+        assert groups >= 3, text.splitlines()[0]
+        fused = [ln for ln in text.splitlines()
+                 if ln.startswith("pass") and re.search(r" a=(\d+) c=(\d+) b=(\d+)", ln)
+                 and int(re.search(r" a=(-?\d+)", ln).group(1)) >= 0
+                 and int(re.search(r" b=(-?\d+)", ln).group(1)) >= 0]
+        assert len(fused) == 2, text.splitlines()[0]
+
+
+def _l2_dev(a, b, chunk=1 << 27):
+    import torch
+    acc = 0.0
+    for i in range(0, a.numel(), chunk):
+        d = a[i:i + chunk].to(torch.complex128) - b[i:i + chunk].to(torch.complex128)
+        acc += float(torch.sum(d.real ** 2 + d.imag ** 2))
+    return acc ** 0.5
+
+
+def test_c64_vs_c128_k32():
+    # K_32, p = 3 (64 GiB in complex128, 32 GiB in complex64): the precision
+    # path against the plain complex128 path on the same GPU
+    from paper_2604_26423_b300.qaoa import Simulator
+    n, p = 32, 3
+    u, v, w = inputs.complete_graph(n, 3232)
+    with Simulator(n, u, v, w, S, "c128") as s128:
+        s128.run(p, 0.6, 0.3)
+        r128 = s128.expect()
+        with Simulator(n, u, v, w, S, "c64") as s64:
+            s64.run(p, 0.6, 0.3)
+            r64 = s64.expect()
+            l2 = _l2_dev(s64.state(), s128.state())
+    r_err = abs(r64["r"] - r128["r"])
+    print(f"\nK_32 p=3 c64 vs c128: state L2 {l2:.2e}, |r64 - r128| {r_err:.2e}, "
+          f"<C> rel {abs(r64['exp_c'] - r128['exp_c']) / r128['exp_c']:.2e}")
+    assert l2 <= 1e-4 and r_err <= 1e-6
+    assert (r64["c_min"], r64["c_max"], r64["argmin"], r64["argmax"]) == \
+        (r128["c_min"], r128["c_max"], r128["argmin"], r128["argmax"])
+
+
+@pytest.mark.parametrize("n", [30, 33])
+@pytest.mark.parametrize("kind", ["chain", "regular3"])
+def test_sparse_graphs_single_layer_vs_closed_form(n, kind):
+    # sparse instances at large n (chain: n - 1 edges; random 3-regular: 3n/2
+    # edges, n even): <C> after one layer against the closed-form
+    # <Z_u Z_v> of each edge, which holds for any graph (Sec. II-B, p = 1)
+    from paper_2604_26423_b300.qaoa import Simulator
+    if kind == "regular3" and n % 2:
+        n -= 1  # a 3-regular graph needs an even vertex count
+    u, v, w = (inputs.chain_graph if kind == "chain" else inputs.regular3_graph)(n, 3000 + n)
+    gamma, beta = 0.6, 0.3
+    want = oracle.analytic_p1_expectation(n, u, v, w, S, gamma, beta)
+    with Simulator(n, u, v, w, S, "c64") as s:
+        s.run(1, gamma, beta)
+        res = s.expect()
+    err = abs(res["exp_c"] - want) / abs(want)
+    print(f"\n{kind} n={n} ({len(u)} edges) p=1 c64 vs closed form: <C> rel {err:.2e}")
+    assert err <= 2e-6
+    assert abs(res["norm"] - 1.0) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["chain", "regular3"])
+def test_sparse_graphs_k32_c64_vs_c128(kind):
+    # p = 3 on 32-qubit sparse graphs: complex64 against complex128 on the GPU
+    from paper_2604_26423_b300.qaoa import Simulator
+    n, p = 32, 3
+    u, v, w = (inputs.chain_graph if kind == "chain" else inputs.regular3_graph)(n, 3100)
+    with Simulator(n, u, v, w, S, "c128") as s128:
+        s128.run(p, 0.6, 0.3)
+        r128 = s128.expect()
+        with Simulator(n, u, v, w, S, "c64") as s64:
+            s64.run(p, 0.6, 0.3)
+            r64 = s64.expect()
+            l2 = _l2_dev(s64.state(), s128.state())
+    r_err = abs(r64["r"] - r128["r"])
+    print(f"\n{kind} n=32 p=3 c64 vs c128: state L2 {l2:.2e}, |r64 - r128| {r_err:.2e}")
+    assert l2 <= 1e-4 and r_err <= 1e-6
+    assert (r64["c_min"], r64["c_max"], r64["argmin"], r64["argmax"]) == \
+        (r128["c_min"], r128["c_max"], r128["argmin"], r128["argmax"])

@@ -164,3 +164,27 @@ def test_batch_c64_vs_single_c128():
         worst["d_dgamma"] = max(worst["d_dgamma"], abs(res["d_dgamma"][i] - g["d_dgamma"]) / max(1, abs(g["d_dgamma"])))
     print(f"\nbatch c64 vs single c128: {worst}")
     assert worst["exp_c"] <= 2e-5 and worst["r"] <= 1e-5 and worst["d_dgamma"] <= 2e-3
+
+
+def test_batch_wait_limit_gives_etimeout_then_recovers():
+    # the bounded device-side dependency wait: with a 1 ns limit every wait of
+    # a PASS item on its instance's earlier pass gives up at once (sets the
+    # error flag and skips the item), so the run ends and the results call
+    # reports ETIMEOUT; a batch with the default limit then runs correctly on
+    # the same device (the context is still usable)
+    from paper_2604_26423_b300.qaoa import QAOA_ETIMEOUT, QaoaError
+    batch = _mixed(41, [20, 21, 22, 20, 14, 13], [3, 2, 3, 2, 2, 1])
+    with Batch(batch, opts=dict(solo_max_n=13, max_units=1, wait_ns=1)) as b:
+        multi = int(b.describe().split("multi=")[1].split()[0])
+        assert multi >= 4  # the n >= 20 instances run as PASS items across CTAs
+        b.run()
+        with pytest.raises(QaoaError) as ei:
+            b.results()
+        assert ei.value.code == QAOA_ETIMEOUT
+    with Batch(batch, opts=dict(solo_max_n=13, max_units=1)) as b:
+        b.run()
+        res = b.results()
+    for i in (0, 2, 4):
+        ref = _single(batch[i])
+        assert abs(res["exp_c"][i] - ref["exp_c"]) <= 1e-6 * abs(ref["exp_c"]), i
+        assert res["c_max"][i] == ref["c_max"], i

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2604_26423_b300 import inputs
+from paper_2604_26423_b300 import inputs, qaoa
 
 pytestmark = pytest.mark.gpu
 
@@ -283,12 +283,34 @@ def test_autotuner_forward_choices_agree():
     assert best in timings
     ref = None
     for cfg in cands:
-        with tune._env(tune.config_env(cfg)):
-            with sim(n, u, v, w, S, "c64", cost_mode=cfg["cost_mode"]) as s:
-                s.run(p, 0.6, 0.3)
-                e = s.expect()["exp_c"]
+        with sim(n, u, v, w, S, "c64", cost_mode=cfg["cost_mode"], opts=tune.config_opts(cfg)) as s:
+            s.run(p, 0.6, 0.3)
+            e = s.expect()["exp_c"]
+            got = s.get_opts()
+        assert got["fwd_shape"] == qaoa.SHAPES[cfg["shape"]], (cfg, got)
         ref = e if ref is None else ref
         assert abs(e - ref) <= 2e-5 * ref, cfg
+    # the tuned cost mode is what QAOA_COST_AUTO now selects for (n, c64)
+    assert qaoa.aux_bytes(n, "c64", "auto", False) == (4 << n if best["cost_mode"] == "stream" else 0)
+    qaoa.set_cost_choice(n, "c64", "auto")
+    assert qaoa.aux_bytes(n, "c64", "auto", False) == 0
+
+
+def test_context_options_select_kernels_and_agree():
+    # per-context configuration (qaoa_set_opts): two contexts in one process
+    # with different tiles, orders and kernels give the same circuit
+    n, p = 24, 3
+    u, v, w = inputs.complete_graph(n, 2424)
+    outs = []
+    for o in (dict(shape="4x3"), dict(shape="5x4", order="middle", float_lanes=False),
+              dict(shape="5x3", specialised=False, tile_tables=False), dict(shape="4x3", l2_prefetch=True)):
+        with sim(n, u, v, w, S, "c64", opts=o) as s:
+            s.run(p, 0.6, 0.3)
+            outs.append(s.state().cpu().numpy().astype(np.complex128))
+            eff = s.get_opts()
+        assert eff["fwd_shape"] == qaoa.SHAPES[o["shape"]]
+    for x in outs[1:]:
+        assert np.linalg.norm(x - outs[0]) <= 2e-6
 
 
 @pytest.mark.parametrize("n,prec", [(30, "c64"), (30, "c128"), (32, "c128"), (34, "c64")])

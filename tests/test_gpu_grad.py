@@ -3,7 +3,8 @@ and central finite differences.
 
 Tolerances: complex128 adjoint vs oracle parameter shift (exact up to
 rounding): 1e-8 relative to the largest component; vs central differences of
-the GPU's own complex128 forward (h = 1e-5): 1e-6 relative. complex64 adjoint
+the oracle's complex128 <C> (h = 1e-5, K_24) or, at K_28, of the GPU's own
+complex128 forward: 1e-6 relative. complex64 adjoint
 vs the complex128 adjoint: 2e-3 relative (single-precision state, gradient
 components are sums of ~2^n terms of mixed sign).
 """
@@ -73,10 +74,33 @@ def test_grad_wide_angles_and_stream_mode(n):
         assert np.max(np.abs(out["g_beta"] - fd_b)) <= 1e-6 * scale, mode
 
 
-@pytest.mark.parametrize("n,p", [(24, 5), (28, 5)])
-def test_grad_config_sizes_vs_gpu_fd(n, p):
-    # n = 24 and 28, K_n: the adjoint against central differences of the GPU's
-    # own complex128 forward (the oracle would take minutes per evaluation here)
+def test_grad_k24_vs_oracle_fd():
+    # n = 24, K_24, p = 5 (the gradient workload's smaller size): the
+    # complex128 adjoint's d<C>/d(dgamma, dbeta) against central differences
+    # (h = 1e-5) of the oracle's gate-by-gate complex128 <C> (four oracle runs)
+    n, p = 24, 5
+    u, v, w = inputs.complete_graph(n, 970 + n)
+    dg, db, h = 0.6, 0.3, 1e-5
+    cut = oracle.cut_values(n, u, v, w)
+
+    def f(a, bb):
+        return oracle.expectation(oracle.simulate(n, u, v, w, S, *oracle.lr_schedule(p, a, bb)), cut)[0]
+
+    fdg = (f(dg + h, db) - f(dg - h, db)) / (2 * h)
+    fdb = (f(dg, db + h) - f(dg, db - h)) / (2 * h)
+    with sim(n, u, v, w, S, "c128", with_grad=True) as s:
+        out = s.grad(p, dg, db)
+    scale = max(abs(fdg), abs(fdb))
+    err = max(abs(out["d_dgamma"] - fdg), abs(out["d_dbeta"] - fdb)) / scale
+    print(f"\nK_24 p=5 c128 adjoint vs oracle FD: relative error {err:.2e}")
+    assert err <= 1e-6
+
+
+def test_grad_k28_vs_gpu_fd():
+    # n = 28, K_28, p = 5: against central differences of the GPU's own
+    # complex128 forward (a self-consistency check between the adjoint and the
+    # forward kernels; the oracle would take minutes per evaluation here)
+    n, p = 28, 5
     u, v, w = inputs.complete_graph(n, 970 + n)
     dg, db, h = 0.6, 0.3, 1e-5
     with sim(n, u, v, w, S, "c128", with_grad=True) as s:
@@ -101,6 +125,10 @@ def test_grad_c64_vs_c128(n, p):
             outs[prec] = s.grad(p, 0.6, 0.3)
     ref = np.concatenate([outs["c128"]["g_gamma"], outs["c128"]["g_beta"]])
     got = np.concatenate([outs["c64"]["g_gamma"], outs["c64"]["g_beta"]])
+    d_ref = np.array([outs["c128"]["d_dgamma"], outs["c128"]["d_dbeta"]])
+    d_got = np.array([outs["c64"]["d_dgamma"], outs["c64"]["d_dbeta"]])
+    print(f"\nK_{n} p={p} c64 gradient vs c128: per-layer {rel(got, ref):.2e}, "
+          f"d/d(dgamma, dbeta) {rel(d_got, d_ref):.2e} (relative to the largest component)")
     assert rel(got, ref) <= 2e-3
     assert abs(outs["c64"]["exp_c"] - outs["c128"]["exp_c"]) <= 2e-5 * outs["c128"]["exp_c"]
 
