@@ -474,12 +474,16 @@ __global__ void __launch_bounds__(128) shot_warp_kernel(const typename Cx<Real>:
   const double u = uni ? uni[i] : splitmix_uniform(seed, (unsigned long long)i);
   const double total = pre[nb];
   const double t = u * total;
-  // smallest j in [lo, hi) with pre[j + 1] > t, or hi if none
+  // smallest j in [lo, hi) with pre[j + 1] > t, or hi if none; the answer
+  // stays in [lo, hi]. Pivot lane i tests "answer <= lo + i step", which holds
+  // for every pivot at or beyond hi (the answer is at most hi), so the first
+  // pivot that holds bounds the answer from above and its predecessor from
+  // below, also when the last pivots fall beyond hi
   long long lo = 0, hi = nb;
   while (hi - lo > 32) {
     const long long step = (hi - lo + 31) / 32;
     const long long piv = lo + (long long)lane * step;  // lane 0's pivot is lo
-    const bool f = piv < hi && pre[piv + 1] > t;
+    const bool f = piv >= hi || pre[piv + 1] > t;
     const unsigned m = __ballot_sync(0xffffffffu, f);
     const int k = m ? __ffs(m) - 1 : 32;      // first pivot where the predicate holds
     const long long nlo = k == 0 ? lo : lo + (long long)(k - 1) * step + 1;

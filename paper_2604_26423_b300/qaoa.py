@@ -265,6 +265,10 @@ class Simulator:
         if getattr(self, "_ctx", None):
             self._lib.qaoa_free(self._ctx)
             self._ctx = None
+        # the device buffers this object allocated (or was given) are released
+        # with it, not kept alive by a closed simulator
+        self._state_t = None
+        self._aux_t = None
 
     def __del__(self):
         try:

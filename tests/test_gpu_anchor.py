@@ -162,3 +162,27 @@ def test_sparse_graphs_k32_c64_vs_c128(kind):
     assert l2 <= 1e-4 and r_err <= 1e-6
     assert (r64["c_min"], r64["c_max"], r64["argmin"], r64["argmax"]) == \
         (r128["c_min"], r128["c_max"], r128["argmin"], r128["argmax"])
+
+
+def test_benchmark_workload_c64_vs_c128_k33():
+    # the benchmark's own workload at full size (K_33, weights 1..10 from seed
+    # 33, p = 3): the complex64 path in each forward tile shape (4x3: four
+    # mixer groups, 10 passes; 5x4: three groups, 7 passes, with their
+    # specialised kernels) against the complex128 path (128 GiB, the generic
+    # FP64 kernels) on the same GPU
+    from paper_2604_26423_b300.qaoa import Simulator
+    n, p = 33, 3
+    u, v, w = inputs.complete_graph(n, 33)
+    with Simulator(n, u, v, w, S, "c128") as s128:
+        s128.run(p, 0.6, 0.3)
+        r128 = s128.expect()
+        for shape in ("4x3", "5x4"):
+            with Simulator(n, u, v, w, S, "c64", opts=dict(shape=shape)) as s64:
+                s64.run(p, 0.6, 0.3)
+                r64 = s64.expect()
+                l2 = _l2_dev(s64.state(), s128.state())
+            r_err = abs(r64["r"] - r128["r"])
+            print(f"\nK_33 p=3 c64 {shape} vs c128: state L2 {l2:.2e}, |r64 - r128| {r_err:.2e}")
+            assert l2 <= 1e-4 and r_err <= 1e-6, shape
+            assert (r64["c_min"], r64["c_max"], r64["argmin"], r64["argmax"]) == \
+                (r128["c_min"], r128["c_max"], r128["argmin"], r128["argmax"])
