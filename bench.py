@@ -456,7 +456,12 @@ def run_gpu(args):
     nq = args.qubits
     u, v, w = inputs.complete_graph(nq, SEED)
     stream = torch.cuda.current_stream()
-    sim = Simulator(nq, u, v, w, SCALE, "c64", cost_mode=args.cost_mode)
+    fwd_opts = {}
+    if args.fwd_shape:
+        fwd_opts["shape"] = args.fwd_shape
+    if args.l2_prefetch:
+        fwd_opts["l2_prefetch"] = True
+    sim = Simulator(nq, u, v, w, SCALE, "c64", cost_mode=args.cost_mode, opts=fwd_opts or None)
     state_buf = sim._state_t
 
     def step():
@@ -495,7 +500,8 @@ def run_gpu(args):
     noise = None if args.no_noise else noise_bench(args)
 
     def e2e_step():
-        s2 = Simulator(nq, uh, vh, wh, SCALE, "c64", cost_mode=args.cost_mode, state=state_buf)
+        s2 = Simulator(nq, uh, vh, wh, SCALE, "c64", cost_mode=args.cost_mode, state=state_buf,
+                       opts=fwd_opts or None)
         s2.run(P, DGAMMA, DBETA)
         r2 = s2.expect()
         sh = s2.sample(SHOTS, seed=SEED + 1)
@@ -552,6 +558,7 @@ def run_gpu(args):
         "config": {"workload": f"LR-QAOA K_{nq} weighted MaxCut, complex64 ({(8 << nq) >> 20} MiB state), p=3, "
                                "dgamma=0.6, dbeta=0.3, <C>, r and 4096 shots per step",
                    "n": nq, "p": P, "precision": "complex64", "cost_mode": args.cost_mode,
+                   "fwd_opts": fwd_opts,
                    "state_bytes": 8 << nq,
                    "l2": f"state {(8 << nq) >> 20} MiB vs 126 MB L2" + (" (no flush needed)" if nq >= 25 else ""),
                    "parallelism": f"replicas x{world}"},
@@ -639,6 +646,9 @@ def main(argv=None):
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
     ap.add_argument("--grad-n", type=int, default=GRAD_N, help="qubits of the gradient leg (profiling)")
     ap.add_argument("--grad-p", type=int, default=GRAD_P, help="depth of the gradient leg (profiling)")
+    ap.add_argument("--fwd-shape", default=None, choices=["4x3", "5x3", "4x4", "5x2", "5x4"],
+                    help="forward tile shape of the step (profiling; default: the library's)")
+    ap.add_argument("--l2-prefetch", action="store_true", help="prefetch each CTA's next tile into L2 (profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -36,24 +36,32 @@ GROUP_ORDERS = ("last", "middle")
 FLOAT_LANES = (1, 0)
 
 
+# the CTA's next tile prefetched into L2 (measured faster with the one-CTA-per-SM
+# 5x4 tile at 30 qubits, slower at 33)
+L2_PREFETCH = (0, 1)
+
+
 def forward_candidates(n: int, precision: str = "c64", modes=("recompute", "stream"), shapes=None,
-                       super_tiles=SUPER_TILES, orders=GROUP_ORDERS, float_lanes=FLOAT_LANES):
+                       super_tiles=SUPER_TILES, orders=GROUP_ORDERS, float_lanes=FLOAT_LANES,
+                       prefetch=L2_PREFETCH):
     """Configurations to time for one instance: cost mode x tile shape x super-tile bits x group order x
-    floating lane bits (a super-tile below the shape's tile means one tile)."""
+    floating lane bits x L2 prefetch (a super-tile below the shape's tile means one tile)."""
     if shapes is None:
         shapes = FWD_SHAPES if precision == "c64" else ("4x3", "5x3")
     out = []
-    for mode, shape, st, order, fl in itertools.product(modes, shapes, super_tiles, orders, float_lanes):
+    for mode, shape, st, order, fl, pf in itertools.product(modes, shapes, super_tiles, orders, float_lanes,
+                                                            prefetch):
         if st > n:
             continue
-        out.append({"cost_mode": mode, "shape": shape, "super_tile": st, "order": order, "float_lanes": fl})
+        out.append({"cost_mode": mode, "shape": shape, "super_tile": st, "order": order, "float_lanes": fl,
+                    "l2_prefetch": pf})
     return out
 
 
 def config_opts(cfg: dict) -> dict:
     """``qaoa.make_opts`` arguments that select a forward configuration."""
     return {"shape": cfg["shape"], "super_tile": cfg.get("super_tile"), "order": cfg.get("order", "last"),
-            "float_lanes": bool(cfg.get("float_lanes", 1))}
+            "float_lanes": bool(cfg.get("float_lanes", 1)), "l2_prefetch": bool(cfg.get("l2_prefetch", 0))}
 
 
 def _time_ms(fn, stream, reps: int) -> float:

@@ -13,6 +13,19 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "slow: long CPU test")
 
 
+@pytest.fixture(autouse=True)
+def _release_cached_device_memory(request):
+    # large GPU tests leave torch's caching allocator holding tens of GiB; the
+    # library sizes some choices by the device's free memory (the gradient's
+    # stored forward states), so each GPU test starts with the cache released
+    if "gpu" in request.keywords and cuda_available():
+        import gc
+        import torch
+        gc.collect()
+        torch.cuda.empty_cache()
+    yield
+
+
 def cuda_available() -> bool:
     try:
         import torch

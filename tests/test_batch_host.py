@@ -83,14 +83,16 @@ def test_batch_instances_shape():
 def test_tuner_candidates():
     from paper_2604_26423_b300 import tune
     c = tune.forward_candidates(33, "c64")
-    assert {"cost_mode": "recompute", "shape": "5x3", "super_tile": 13, "order": "last", "float_lanes": 1} in c
-    assert {"cost_mode": "recompute", "shape": "5x3", "super_tile": 13, "order": "last", "float_lanes": 0} in c
+    assert {"cost_mode": "recompute", "shape": "5x3", "super_tile": 13, "order": "last", "float_lanes": 1,
+            "l2_prefetch": 0} in c
+    assert {"cost_mode": "recompute", "shape": "5x3", "super_tile": 13, "order": "last", "float_lanes": 0,
+            "l2_prefetch": 1} in c
     assert all(x["super_tile"] <= 33 for x in c)
     assert {x["shape"] for x in tune.forward_candidates(30, "c128")} == {"4x3", "5x3"}
     assert "5x4" in {x["shape"] for x in c}
     opts = tune.config_opts({"cost_mode": "stream", "shape": "4x4", "super_tile": 14, "order": "middle",
                              "float_lanes": 0})
-    assert opts == {"shape": "4x4", "super_tile": 14, "order": "middle", "float_lanes": False}
+    assert opts == {"shape": "4x4", "super_tile": 14, "order": "middle", "float_lanes": False, "l2_prefetch": False}
     o = qaoa.make_opts(**opts)
     assert (o.fwd_shape, o.super_tile, o.group_order, o.float_lanes) == (qaoa.SHAPES["4x4"], 14, 2, qaoa.OFF)
     assert qaoa.make_opts().fwd_shape == 0 and qaoa.make_opts(specialised=True).specialised == qaoa.ON

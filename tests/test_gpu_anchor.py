@@ -1,12 +1,14 @@
 """The benchmark's plan shape anchored to the oracle and to complex128.
 
-The K_33 benchmark runs plans of four mixer groups (a low shared-memory group
-plus three windows of high bits) with cross-layer fused passes and the
-specialised kernels compiled for those round sequences. From 27 qubits the
-same kind of plan is chosen, and the oracle still finishes in about a minute,
-so these tests compare that plan element by element with the oracle's
-gate-by-gate complex128 state (Sec. II-B, Eqs. UC and UB), in both
-precisions, both cost modes and both group orders.
+The K_33 benchmark runs a plan of four mixer groups with the 4x3 tile (a low
+shared-memory group plus three windows of high bits, 256-byte runs) with
+cross-layer fused passes and the specialised kernels compiled for those round
+sequences. At 29 qubits the 4x3 tile takes the same kind of plan (four groups,
+256-byte runs); at 27 and 28 qubits it takes three groups with 128-byte runs,
+and the 5x4 tile three groups with 256-byte runs. The oracle still finishes
+in one to three minutes there, so these tests compare those plans element by
+element with the oracle's gate-by-gate complex128 state (Sec. II-B, Eqs. UC
+and UB), in both precisions, both cost modes and both group orders.
 
 Where the oracle cannot run (K_32, 64 GiB in complex128), the complex64 path
 is compared with the complex128 path of the same GPU.
@@ -27,7 +29,7 @@ S = 0.1
 
 @pytest.fixture(scope="module")
 def refs():
-    # one oracle run per size for the whole module (2 GiB and 4 GiB states),
+    # one oracle run per size for the whole module (2, 4 and 8 GiB states),
     # released when the module's tests are done
     cache = {}
     yield cache
@@ -51,7 +53,7 @@ def _groups(n, p, prec):
 @pytest.mark.parametrize("order", ["last", "middle"])
 @pytest.mark.parametrize("cost_mode", ["recompute", "stream"])
 @pytest.mark.parametrize("prec,shape", [("c64", "4x3"), ("c64", "5x4"), ("c128", "4x3")])
-@pytest.mark.parametrize("n", [27, 28])
+@pytest.mark.parametrize("n", [27, 28, 29])
 def test_benchmark_plan_shape_vs_oracle(n, prec, shape, cost_mode, order, monkeypatch, refs):
     from paper_2604_26423_b300.qaoa import Simulator
     p = 3
@@ -68,6 +70,8 @@ def test_benchmark_plan_shape_vs_oracle(n, prec, shape, cost_mode, order, monkey
         l2 = float(torch.linalg.vector_norm(got.to(torch.complex128) - want))
         del want
     groups, passes = _groups(n, p, prec)
+    if n == 29 and shape == "4x3":
+        assert groups == 4 and passes == 10  # the K_33 benchmark's plan kind
     r_err = abs(res["r"] - ref["r"])
     print(f"\nK_{n} p={p} {prec} {shape} {cost_mode} order={order}: {groups} groups, {passes} passes, "
           f"state L2 {l2:.2e}, |r - r_oracle| {r_err:.2e}")

@@ -469,3 +469,29 @@ def test_bench_workload_k33_properties():
     assert (res2["c_min"], res2["c_max"], res2["argmin"], res2["argmax"]) == \
         (res["c_min"], res["c_max"], res["argmin"], res["argmax"])
     assert abs(res2["exp_c"] - res["exp_c"]) <= 2e-6 * res["exp_c"]
+
+
+@pytest.mark.parametrize("n", [28, 30])
+def test_shots_in_their_fp64_cdf_interval_large_n(n):
+    # every shot x must satisfy F(x - 1) <= u * total < F(x) for the FP64
+    # cumulative |psi|^2 of the GPU's own complex64 state (torch on the
+    # device), up to the rounding of the per-thread partials of the fused
+    # block sums (1e-10 of the total, far below any block's mass): at these
+    # sizes the block search runs over 2^16 and 2^18 blocks
+    import torch
+    u, v, w = graph("complete", n, 2800 + n)
+    uni = inputs.uniforms(2801 + n, 4096)
+    with sim(n, u, v, w, S, "c64") as s:
+        s.run(3, 0.6, 0.3)
+        got = torch.from_numpy(s.sample(4096, uniforms=uni).astype(np.int64)).cuda()
+        st = s.state()
+        pr = st.real.double() ** 2 + st.imag.double() ** 2
+        F = torch.cumsum(pr, 0)
+        del pr
+        total = F[-1]
+        t = torch.from_numpy(uni).cuda() * total
+        lo = torch.where(got > 0, F[(got - 1).clamp(min=0)], torch.zeros_like(t))
+        hi = F[got]
+        tol = 1e-10 * total
+        ok = (lo - tol <= t) & (t < hi + tol)
+        assert bool(ok.all()), f"{int((~ok).sum())} shots outside their CDF interval"
