@@ -21,7 +21,9 @@ phases scaled by 1/10, LR-QAOA p = 3 with dgamma = 0.6, dbeta = 0.3.
   the library's own passes move (its plan's pass count).
 * ``grad``: the adjoint gradient's cost relative to the forward run on the
   gradient workload (K_28, complex64, p = 10): t(qaoa_grad: forward, <C>,
-  backward, all 2p layer derivatives) / t(qaoa_run + qaoa_expect).
+  backward, all 2p layer derivatives) / t(qaoa_run + qaoa_expect), with the
+  forward's pass outputs stored (``ratio``, the default) and with two state
+  vectors only, psi uncomputed (``ratio_two_vectors``).
 * ``batch``: the batched workload (4096 seeded instances, n uniform in 10..22,
   p in 1..10, 1/3 K_n, 1/3 chains, 1/3 random 3-regular graphs, complex64,
   forward with <C>, r and extremes, and forward + adjoint gradients): instances/s
@@ -222,8 +224,7 @@ def grad_ratio(args, stream, reps: int = 3):
         def bwd():
             return s.grad(gp, GRAD_DGAMMA, GRAD_DBETA)
 
-        times = {}
-        for name, f in (("forward", fwd), ("grad", bwd)):
+        def timed(f):
             for _ in range(3):
                 f()
             torch.cuda.synchronize()
@@ -231,14 +232,25 @@ def grad_ratio(args, stream, reps: int = 3):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(reps):
-                r = f()
+                out = f()
             e1.record(stream)
             torch.cuda.synchronize()
-            times[name] = e0.elapsed_time(e1) / reps
+            return e0.elapsed_time(e1) / reps, out
+
+        t_fwd, _ = timed(fwd)
+        # the adjoint with the forward's pass outputs stored (one state sweep
+        # fewer per adjoint pass; the library's default when memory allows)
+        t_grad, r = timed(bwd)
+        # the adjoint that holds two vectors only: psi uncomputed with the
+        # inverse gates and written back in every pass
+        s.set_opts(dict(grad_checkpoint=False))
+        t_grad2, r2 = timed(bwd)
+        s.set_opts(dict())
         return {"workload": f"K_{gn} complex64, p={gp}, dgamma={GRAD_DGAMMA}, dbeta={GRAD_DBETA}",
-                "forward_ms": times["forward"], "grad_ms": times["grad"],
-                "ratio": times["grad"] / times["forward"], "exp_c": r["exp_c"],
-                "d_dgamma": r["d_dgamma"], "d_dbeta": r["d_dbeta"]}
+                "forward_ms": t_fwd, "grad_ms": t_grad, "ratio": t_grad / t_fwd,
+                "grad_ms_two_vectors": t_grad2, "ratio_two_vectors": t_grad2 / t_fwd,
+                "two_vectors_rel_diff": abs(r2["d_dgamma"] - r["d_dgamma"]) / max(1e-30, abs(r["d_dgamma"])),
+                "exp_c": r["exp_c"], "d_dgamma": r["d_dgamma"], "d_dbeta": r["d_dbeta"]}
 
 
 def _l2_dev(a, b, chunk=1 << 27):
@@ -335,7 +347,7 @@ def batch_bench(args, stream):
     out = {"workload": f"{count} instances, n in 10..22, p in 1..10, K_n / chain / 3-regular, complex64"}
     for grad in (False, True):
         best, timings = tune.tune_batch(batch, with_grad=grad,
-                                        candidates=tune.batch_candidates(solo=(16, 25), units=(1, 2), ctas=(2,)))
+                                        candidates=tune.batch_candidates(solo=(25,), units=(1, 2), ctas=(2,)))
         b = Batch(batch, with_grad=grad, opts=best["opts"])
         try:
             for _ in range(2):

@@ -317,10 +317,16 @@ typedef struct qaoa_batch qaoa_batch;
  * wait_ns: limit of each device-side dependency wait in nanoseconds (default
  * 2e9). A wait that reaches the limit sets the batch's error flag and skips
  * its item, so the run ends and qaoa_batch_results returns ETIMEOUT; a limit
- * of 1 ns makes any wait give up (a test of that path). */
+ * of 1 ns makes any wait give up (a test of that path). cost_mode: as at
+ * qaoa_init_graph (AUTO and RECOMPUTE recompute C(x) in each tile; STREAM
+ * reads an int32 diagonal per instance, computed once by qaoa_batch_create:
+ * 2^n * 4 more bytes of device memory per instance with HBM passes).
+ * fwd_shape: tile of the forward passes, QAOA_SHAPE_5x3 (default) or
+ * QAOA_SHAPE_4x3. */
 typedef struct qaoa_batch_opts {
   int solo_max_n, window_items, window_mb, max_units, ctas_per_sm;
   int64_t wait_ns;
+  int cost_mode, fwd_shape;
 } qaoa_batch_opts;
 
 /* Validates and plans the batch, allocates its device memory (all states, and

@@ -60,6 +60,8 @@ struct qaoa_batch {
   BatchArgs args{}, args_adj{};
   double* d_out = nullptr;
   bool fast = true;
+  bool stream = false;  // streamed int32 cost diagonals instead of the cost tables
+  int fwd_r = kBatchR;  // register bits of the forward tile
   int nitems = 0, nitems_adj = 0, grid = 0, grid_adj = 0, ctas_per_sm = 0, nmode[3] = {0, 0, 0};
   size_t smem = 0, dev_bytes = 0, gtotal = 0;
   double bytes = 0;
@@ -132,6 +134,12 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
   const int solo_max_n = std::max(13, o.solo_max_n > 0 ? o.solo_max_n : env_int("QAOA_BATCH_SOLO", 16));
   const int max_units = std::max(1, o.max_units > 0 ? o.max_units : env_int("QAOA_BATCH_UNITS", 8));
   const int window_mb = std::max(1, o.window_mb > 0 ? o.window_mb : env_int("QAOA_BATCH_WINDOW_MB", 96));
+  if (o.cost_mode < QAOA_COST_AUTO || o.cost_mode > QAOA_COST_STREAM) return fail(QAOA_EINVAL, "bad cost_mode");
+  if (o.fwd_shape != 0 && o.fwd_shape != QAOA_SHAPE_5x3 && o.fwd_shape != QAOA_SHAPE_4x3)
+    return fail(QAOA_EINVAL, "the batch's forward tile is QAOA_SHAPE_5x3 or QAOA_SHAPE_4x3");
+  // streamed cost: C(x) of every instance precomputed once (int32 per amplitude)
+  const bool stream = o.cost_mode == QAOA_COST_STREAM;
+  const int fwd_r = o.fwd_shape == QAOA_SHAPE_4x3 ? 4 : kBatchR;
 
   std::unique_ptr<qaoa_batch> b(new qaoa_batch);
   b->count = count;
@@ -141,7 +149,7 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
 
   // ------------------------------------------------------------ plan instances
   TileShape fsh;
-  fsh.R = kBatchR;
+  fsh.R = fwd_r;
   fsh.WB = kBatchWB;
   fsh.amp_bytes = 8;
   TileShape ash;
@@ -161,6 +169,8 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
     }
   }
   b->fast = all_fast;
+  b->stream = stream;
+  b->fwd_r = fwd_r;
   std::vector<InstPlan> ip(count);
   for (int i = 0; i < count; ++i) {
     InstPlan& I = ip[i];
@@ -197,7 +207,7 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
     in.ncost = I.c_hi - I.c_lo + 1;
     in.W = I.W;
     in.wmat = I.wmat.data();
-    in.stream = false;
+    in.stream = stream;
     in.plain = !all_fast;
     try {
       if (!small && I.n >= Tf) {
@@ -255,6 +265,19 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
   b->states = b->dalloc(state_total);
   void* lams = with_grad ? b->dalloc(state_total) : nullptr;
   if (!b->states || (with_grad && !lams)) return fail(QAOA_ENOMEM, "cudaMalloc of the batch states failed");
+  // streamed cost: one int32 diagonal per instance that runs HBM passes
+  std::vector<size_t> diag_off(count, ~size_t(0));
+  int32_t* diags = nullptr;
+  if (stream) {
+    size_t total = 0;
+    for (int i = 0; i < count; ++i)
+      if (!ip[i].fwd.empty() || !ip[i].adj.empty()) {
+        diag_off[i] = total;
+        total += ((size_t(4) << ip[i].n) + 255) & ~size_t(255);
+      }
+    diags = (int32_t*)b->dalloc(std::max<size_t>(total, 256));
+    if (!diags) return fail(QAOA_ENOMEM, "cudaMalloc of the batch cost diagonals failed");
+  }
 
   // per-instance tables: weights, cost tables, phase tables, angles
   std::vector<int32_t> h_w, h_ct;
@@ -309,6 +332,7 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
     D.lam = lams ? (char*)lams + b->state_off[i] : nullptr;
     D.wmat = d_w + w_off[i];
     D.ctabs = d_ct + ct_off[i];
+    D.diag = diag_off[i] != ~size_t(0) ? (const int32_t*)((char*)diags + diag_off[i]) : nullptr;
     D.phase = d_ph + ph_off[i];
     D.ang = d_ang + ang_off[i];
     D.scale = weight_scale;
@@ -345,6 +369,8 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
         units_per_item.push_back(upi);
         b->bytes += double(size_t(8) << I.n) * (adjoint ? ((pp.linit ? 1.0 : 2.0) + (pp.store ? 2.0 : 0.0))
                                                          : ((pp.init ? 1.0 : 2.0)));
+        if (stream)  // the int32 diagonal read by each sub-pass that needs C(x)
+          for (const SubPassPlan& sp : pp.subs) b->bytes += sp.needs_c ? double(size_t(4) << I.n) : 0.0;
       }
     };
     D.fwd_pass0 = (int32_t)h_pass.size();
@@ -382,8 +408,9 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
                               (size_t(8) << kBatchSmallMax) + (size_t(4) << kBatchSmallMax),
                               (size_t(16) << kBatchSmallGradMax) + (size_t(4) << kBatchSmallGradMax)}) +
             32 * 4 + kBatchMaxN * kBatchMaxN * 4;
-  auto fwd_kern = all_fast ? batch_kernel<true, false> : batch_kernel<false, false>;
-  auto adj_kern = all_fast ? batch_kernel<true, true> : batch_kernel<false, true>;
+  auto fwd_kern = fwd_r == 4 ? (all_fast ? batch_kernel<true, false, 4> : batch_kernel<false, false, 4>)
+                             : (all_fast ? batch_kernel<true, false, kBatchR> : batch_kernel<false, false, kBatchR>);
+  auto adj_kern = all_fast ? batch_kernel<true, true, kBatchR> : batch_kernel<false, true, kBatchR>;
   int bps = 0;
   for (auto kern : {fwd_kern, adj_kern}) {
     int nb = 0;
@@ -525,6 +552,26 @@ int qaoa_batch_create(qaoa_batch** out, int count, const int32_t* n, const int32
   b->args_adj.done = d_done + count;
   b->grid_adj = std::max(1, std::min(ctas, b->nitems_adj));
 
+  // ------------------------------------------------------------ cost diagonals
+  // (streamed cost) C(x) of each instance with HBM passes, once per batch: the
+  // diagonal depends on the graph only, every run reads it
+  if (stream) {
+    Extreme* d_scratch = (Extreme*)b->dalloc(sizeof(Extreme) * (size_t(1) << (kBatchMaxN - 15)));
+    if (!d_scratch) return fail(QAOA_ENOMEM, "cudaMalloc of the diagonal scratch failed");
+    for (int i = 0; i < count; ++i) {
+      if (diag_off[i] == ~size_t(0)) continue;
+      int32_t* dg = (int32_t*)((char*)diags + diag_off[i]);
+      const int32_t* wm = d_w + w_off[i];
+      if (ip[i].n < 16) {
+        cost_small_kernel<<<1, 1024>>>(ip[i].n, wm, dg, d_scratch);
+      } else {
+        cost_block_kernel<15><<<(unsigned)(1u << (ip[i].n - 15)), 1024>>>(ip[i].n, wm, dg, d_scratch);
+      }
+    }
+    const cudaError_t de = cudaGetLastError();
+    if (de != cudaSuccess) return fail(QAOA_ECUDA, std::string("cost diagonals: ") + cudaGetErrorString(de));
+  }
+
   // ------------------------------------------------------------ graph
   if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -597,9 +644,10 @@ int qaoa_batch_describe(const qaoa_batch* b, char* out, size_t cap) {
   if (!b || !out || cap == 0) return QAOA_EINVAL;
   snprintf(out, cap,
            "instances=%d small=%d solo=%d multi=%d items=%d adjoint_items=%d grid=%d ctas_per_sm=%d smem=%zu "
-           "device_bytes=%zu state_bytes=%.0f grad=%d fast=%d",
+           "device_bytes=%zu state_bytes=%.0f grad=%d fast=%d tile=%dx%d cost=%s",
            b->count, b->nmode[0], b->nmode[1], b->nmode[2], b->nitems, b->nitems_adj, b->grid, b->ctas_per_sm,
-           b->smem, b->dev_bytes, b->bytes, b->with_grad, b->fast ? 1 : 0);
+           b->smem, b->dev_bytes, b->bytes, b->with_grad, b->fast ? 1 : 0, b->fwd_r, kBatchWB,
+           b->stream ? "stream" : "recompute");
   return QAOA_OK;
 }
 

@@ -32,7 +32,7 @@ namespace qaoa {
 enum : int32_t { BITEM_SMALL = 0, BITEM_SOLO = 1, BITEM_PASS = 2, BITEM_EXT = 3 };
 enum : int32_t { BMODE_SMALL = 0, BMODE_SOLO = 1, BMODE_MULTI = 2 };
 
-constexpr int kBatchR = 5, kBatchWB = 3;        // forward tile (T = 13)
+constexpr int kBatchR = 5, kBatchWB = 3;        // default forward tile (T = 13); 4x3 (T = 12) selectable
 constexpr int kBatchRAdj = 4, kBatchWBAdj = 3;  // adjoint tile (T = 12)
 constexpr int kBatchThreads = 256;
 constexpr int kBatchExtBits = 13;               // configurations per EXT block
@@ -61,6 +61,7 @@ struct BatchInst {
   void* lam;
   const int32_t* wmat;            // n x n
   const int32_t* ctabs;           // this instance's cost tables
+  const int32_t* diag;            // int32 C(x) of all 2^n x (streamed cost), or nullptr
   const float2* phase;            // p tables of ncost entries
   const double* ang;              // (gamma_k, beta_k) interleaved
   double scale;                   // phase weight scale s
@@ -335,7 +336,7 @@ __device__ __noinline__ void batch_ext(const BatchArgs& B, const BatchInst& I, i
 
 // Super-tiles [u0, u1) of one pass (descriptor staged in shared memory P);
 // the pass's partial sums go to `slot`.
-template <bool FAST, bool ADJ>
+template <bool FAST, bool ADJ, int FR>
 __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& I, int pass, int slot, uint32_t u0,
                                            uint32_t u1, unsigned char* smem, double* wacc, double* red, PassDev& P) {
   const PassMeta& M = B.pmeta[pass];
@@ -352,7 +353,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     PassArgs A;
     A.state = I.psi;
     A.out = I.psi;
-    A.diag = nullptr;
+    A.diag = I.diag;
     A.phase = phase;
     A.wmat = I.wmat;
     A.ctabs = I.ctabs;
@@ -362,12 +363,12 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     A.l2hint = 0;
     A.prefetch = 0;
     A.ext_keys = nullptr;
-    constexpr int TILE = padded_size<8>(kBatchR + 5 + kBatchWB);
+    constexpr int TILE = padded_size<8>(FR + 5 + kBatchWB);
     float2* tile = reinterpret_cast<float2*>(smem);
     int* tconst = reinterpret_cast<int*>(tile + TILE);
     wacc[2 * tid] = 0.0;
     wacc[2 * tid + 1] = 0.0;
-    for (uint32_t u = u0; u < u1; ++u) fwd_unit<float, kBatchR, kBatchWB, FAST>(P, A, u, tile, tconst, phase, wacc);
+    for (uint32_t u = u0; u < u1; ++u) fwd_unit<float, FR, kBatchWB, FAST>(P, A, u, tile, tconst, phase, wacc);
     if (M.reduce) {
       __syncthreads();
       double sN, sC;
@@ -382,7 +383,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     A.psi = I.psi;
     A.psi_store = 1;
     A.lam = I.lam;
-    A.diag = nullptr;
+    A.diag = I.diag;
     A.phase = phase;
     A.wmat = I.wmat;
     A.ctabs = I.ctabs;
@@ -438,7 +439,8 @@ __device__ __noinline__ void batch_solo_small(const BatchArgs& B, const BatchIns
 // One phase of the batch (ADJ: the adjoint sweep). Dynamic shared memory:
 // max(forward tile, two adjoint tiles, SMALL state + cuts, EXT weights) + the
 // tile constants.
-template <bool FAST, bool ADJ>
+// FR: register bits of the forward tile (5: 5x3 tiles, T = 13; 4: 4x3, T = 12).
+template <bool FAST, bool ADJ, int FR>
 __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double wacc[2 * kBatchThreads + 2 * kBatchThreads / 32];
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
         }
         for (int pi = p0; pi < p1; ++pi) {
           const bool whole = it.kind == BITEM_SOLO;
-          batch_pass<FAST, ADJ>(B, I, pi, whole ? B.pmeta[pi].slot0 : it.slot, whole ? 0u : it.u0,
+          batch_pass<FAST, ADJ, FR>(B, I, pi, whole ? B.pmeta[pi].slot0 : it.slot, whole ? 0u : it.u0,
                                 whole ? (uint32_t)B.passes[pi].n_units : it.u1, smem_raw, wacc, red, sP);
         }
       } else if constexpr (!ADJ) {

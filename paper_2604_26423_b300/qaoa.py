@@ -463,7 +463,8 @@ def classify_regime(r_obs: float, rand_mean: float, rand_sigma: float, ideal_mea
 class BatchOpts(ctypes.Structure):
     """Scheduling knobs of ``qaoa_batch_create`` (0 = library default)."""
     _fields_ = [("solo_max_n", ctypes.c_int), ("window_items", ctypes.c_int), ("window_mb", ctypes.c_int),
-                ("max_units", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("wait_ns", ctypes.c_int64)]
+                ("max_units", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("wait_ns", ctypes.c_int64),
+                ("cost_mode", ctypes.c_int), ("fwd_shape", ctypes.c_int)]
 
 
 BATCH_FIELDS = ("exp_c", "r", "norm", "c_min", "c_max", "argmin", "argmax", "d_dgamma", "d_dbeta")
@@ -474,7 +475,8 @@ class Batch:
     kernel per phase, replayed from a CUDA graph (``qaoa_batch_*``).
 
     ``instances``: dicts with keys n, p, dgamma, dbeta, u, v, w (the shape
-    ``inputs.batch_instances`` returns). ``opts``: dict of ``BatchOpts`` fields.
+    ``inputs.batch_instances`` returns). ``opts``: dict of ``BatchOpts`` fields
+    (``cost_mode`` may be "recompute" / "stream", ``fwd_shape`` "5x3" / "4x3").
     """
 
     def __init__(self, instances, scale=0.1, with_grad=False, opts=None, stream=None):
@@ -494,7 +496,12 @@ class Batch:
         u, v, w = cat("u"), cat("v"), cat("w")
         dg = np.array([d["dgamma"] for d in instances], dtype=np.float64)
         db = np.array([d["dbeta"] for d in instances], dtype=np.float64)
-        o = BatchOpts(**(opts or {}))
+        o = dict(opts or {})
+        if isinstance(o.get("cost_mode"), str):
+            o["cost_mode"] = _COST[o["cost_mode"]]
+        if isinstance(o.get("fwd_shape"), str):
+            o["fwd_shape"] = SHAPES[o["fwd_shape"]]
+        o = BatchOpts(**o)
         P = ctypes.POINTER
         ip = lambda a: a.ctypes.data_as(P(ctypes.c_int32))
         h = ctypes.c_void_p()

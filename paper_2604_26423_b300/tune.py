@@ -104,8 +104,11 @@ def tune_forward(n, u, v, w, p, dgamma, dbeta, scale=0.1, precision="c64", candi
     return best, timings
 
 
-def batch_candidates(solo=(13, 16, 20, 25), units=(1, 2, 4), ctas=(2,)):
-    return [dict(solo_max_n=a, max_units=b, ctas_per_sm=c) for a, b, c in itertools.product(solo, units, ctas)]
+def batch_candidates(solo=(13, 16, 20, 25), units=(1, 2, 4), ctas=(2,), shapes=("5x3", "4x3"),
+                     modes=("recompute", "stream")):
+    """Batch configurations to time: scheduling knobs x forward tile shape x cost mode."""
+    return [dict(solo_max_n=a, max_units=b, ctas_per_sm=c, fwd_shape=sh, cost_mode=m)
+            for a, b, c, sh, m in itertools.product(solo, units, ctas, shapes, modes)]
 
 
 def tune_batch(instances, with_grad=False, scale=0.1, candidates=None, reps=1, key=None):

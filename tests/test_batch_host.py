@@ -96,8 +96,10 @@ def test_tuner_candidates():
     o = qaoa.make_opts(**opts)
     assert (o.fwd_shape, o.super_tile, o.group_order, o.float_lanes) == (qaoa.SHAPES["4x4"], 14, 2, qaoa.OFF)
     assert qaoa.make_opts().fwd_shape == 0 and qaoa.make_opts(specialised=True).specialised == qaoa.ON
-    b = tune.batch_candidates(solo=(16,), units=(1, 2), ctas=(2,))
-    assert b == [dict(solo_max_n=16, max_units=1, ctas_per_sm=2), dict(solo_max_n=16, max_units=2, ctas_per_sm=2)]
+    b = tune.batch_candidates(solo=(16,), units=(1, 2), ctas=(2,), shapes=("5x3",), modes=("recompute",))
+    assert b == [dict(solo_max_n=16, max_units=1, ctas_per_sm=2, fwd_shape="5x3", cost_mode="recompute"),
+                 dict(solo_max_n=16, max_units=2, ctas_per_sm=2, fwd_shape="5x3", cost_mode="recompute")]
+    assert len(tune.batch_candidates(solo=(16,), units=(1,))) == 4
 
 
 def test_group_orders_give_valid_plans():

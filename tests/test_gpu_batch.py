@@ -42,7 +42,9 @@ NS = [4, 9, 12, 13, 14, 15, 16, 17, 18, 19, 20, 13, 16, 10, 11, 12, 18, 14]
 PS = [1, 3, 5, 2, 4, 1, 3, 2, 5, 1, 2, 6, 1, 7, 2, 3, 1, 4]
 
 
-@pytest.mark.parametrize("opts", [None, dict(solo_max_n=13, max_units=1), dict(solo_max_n=20, window_items=4)])
+@pytest.mark.parametrize("opts", [None, dict(solo_max_n=13, max_units=1), dict(solo_max_n=20, window_items=4),
+                                  dict(solo_max_n=13, cost_mode="stream"), dict(solo_max_n=16, fwd_shape="4x3"),
+                                  dict(solo_max_n=13, max_units=2, fwd_shape="4x3", cost_mode="stream")])
 def test_batch_forward_matches_single_path(opts):
     batch = _mixed(11, NS, PS)
     with Batch(batch, opts=opts) as b:
@@ -74,7 +76,8 @@ def test_batch_forward_matches_oracle_small():
             assert np.linalg.norm(psi - o["psi"]) <= 1e-5, i
 
 
-@pytest.mark.parametrize("opts", [None, dict(solo_max_n=13, max_units=2)])
+@pytest.mark.parametrize("opts", [None, dict(solo_max_n=13, max_units=2), dict(solo_max_n=13, cost_mode="stream"),
+                                  dict(solo_max_n=16, fwd_shape="4x3", cost_mode="stream")])
 def test_batch_gradient_matches_single_path(opts):
     batch = _mixed(31, [5, 11, 12, 13, 14, 16, 17, 18], [3, 2, 4, 2, 3, 2, 1, 3])
     with Batch(batch, with_grad=True, opts=opts) as b:
