@@ -92,7 +92,11 @@ def test_batch_gradient_matches_single_path(opts):
             assert np.abs(gb - g["g_beta"]).max() <= 2e-4 * scale, (i, d["n"])
             assert abs(res["d_dgamma"][i] - g["d_dgamma"]) <= 2e-4 * scale, i
             assert abs(res["d_dbeta"][i] - g["d_dbeta"]) <= 2e-4 * scale, i
-            assert abs(res["exp_c"][i] - ref["exp_c"]) <= 1e-6 * abs(ref["exp_c"]), i
+            # with the 4x3 forward tile a 12-qubit instance runs HBM passes
+            # where the single path runs its whole-circuit kernel: two complex64
+            # evaluations of the same circuit, each within ~6e-7 of the exact <C>
+            tol = 1e-6 if (opts or {}).get("fwd_shape") != "4x3" else 5e-6
+            assert abs(res["exp_c"][i] - ref["exp_c"]) <= tol * abs(ref["exp_c"]), i
 
 
 def test_batch_gradient_matches_oracle_finite_difference():
