@@ -3,6 +3,7 @@
 // Host side of the LR-QAOA simulation: graph validation, the weight matrix,
 // plans and their cost tables, phase tables, launches and result transfer.
 // Every step of the simulation itself runs in the CUDA kernels included below.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -78,6 +79,7 @@ struct DevBuf {
 struct qaoa_ctx {
   int n = 0, m = 0, prec = QAOA_C64, cost_mode = QAOA_COST_RECOMPUTE;
   qaoa_opts opts{};  // kernel configuration (qaoa_set_opts; 0 = default)
+  int shape_force = -1;  // forward tile id while the gradient runs its forward (the adjoint's tile)
   double scale = 0.1;
   std::vector<int32_t> u, v, w;
   std::vector<int32_t> wmat;  // n x n
@@ -217,18 +219,6 @@ int on_off(int opt, const char* env, int dflt) {
   return dflt;
 }
 
-int fwd_shape_id(const qaoa_ctx* c, int prec) {
-  const int o = c ? shape_from_opt(c->opts.fwd_shape) : -1;
-  if (prec != QAOA_C64) {
-    if (o == 0 || o == 3) return o;
-    const int e = shape_from_name(getenv("QAOA_FWD_SHAPE_C128"));
-    return (e == 0 || e == 3) ? e : kFwdShapeC128;
-  }
-  if (o >= 0) return o;
-  const int e = shape_from_name(getenv("QAOA_FWD_SHAPE"));
-  return e >= 0 ? e : kFwdShapeC64;
-}
-
 TileShape shape_of(int id, int prec) {
   static const int R[5] = {kR, 4, 5, 4, 5}, WB[5] = {kWB, 4, 2, 3, 4};
   TileShape s;
@@ -237,7 +227,53 @@ TileShape shape_of(int id, int prec) {
   s.amp_bytes = amp_bytes(prec);
   return s;
 }
+
+// Default complex64 forward tile for n qubits: 5x4 (one CTA per SM, its next
+// tile prefetched into L2) from 27 qubits (its specialised kernels are
+// compiled for n = 27..34) where it needs fewer mixer groups than 4x3 (n = 29
+// .. 34: three instead of four, 7 passes instead of 10 at p = 3; measured 218
+// against 227 ms per K_33 step and 24.4 against 27.9 ms at K_30), else 4x3
+// (four CTAs per SM; equal pass counts favour it).
+int default_shape_c64(int n) {
+  static int cache[kMaxQubits + 1] = {};  // 0 unknown, else id + 1
+  if (n < 27 || n > kMaxQubits) return kFwdShapeC64;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!cache[n]) {
+    int id = kFwdShapeC64;
+    try {
+      const int order = kGroupOrder | kFloatLanes;
+      const TileShape a = shape_of(3, QAOA_C64), b = shape_of(4, QAOA_C64);
+      const size_t ga = plan_forward(n, 1, a, a.T(), kMinUnitsLog2, order).groups.size();
+      const size_t gb = plan_forward(n, 1, b, b.T(), kMinUnitsLog2, order).groups.size();
+      if (gb < ga) id = 4;
+    } catch (std::exception&) {
+    }
+    cache[n] = id + 1;
+  }
+  return cache[n] - 1;
+}
+
+int fwd_shape_id(const qaoa_ctx* c, int prec, int n) {
+  const int o = c ? shape_from_opt(c->opts.fwd_shape) : -1;
+  if (prec != QAOA_C64) {
+    if (o == 0 || o == 3) return o;
+    const int e = shape_from_name(getenv("QAOA_FWD_SHAPE_C128"));
+    return (e == 0 || e == 3) ? e : kFwdShapeC128;
+  }
+  if (c && c->shape_force >= 0) return c->shape_force;
+  if (o >= 0) return o;
+  const int e = shape_from_name(getenv("QAOA_FWD_SHAPE"));
+  return e >= 0 ? e : default_shape_c64(n);
+}
+int fwd_shape_id(const qaoa_ctx* c, int prec) { return fwd_shape_id(c, prec, c ? c->n : 0); }
 TileShape fwd_shape(const qaoa_ctx* c, int prec) { return shape_of(fwd_shape_id(c, prec), prec); }
+
+// L2 prefetch of the next tile: on by default with the one-CTA-per-SM 5x4 tile
+// (measured faster), off with the others (measured slower).
+int l2_prefetch_on(const qaoa_ctx* c, int shape_id) {
+  return on_off(c->opts.l2_prefetch, "QAOA_L2PREFETCH", shape_id == 4 ? 1 : 0);
+}
 
 // Adjoint tile shape: two vectors per thread, 2^4 registers each x 8 warps (T = 12).
 TileShape adj_shape(int prec) {
@@ -400,7 +436,7 @@ int smax_fwd(const qaoa_ctx* c, int T) {
 }
 
 const Plan* get_plan(qaoa_ctx* c, int p, int order) {
-  const auto key = std::make_pair(p, order);
+  const auto key = std::make_pair(p, order | fwd_shape_id(c, c->prec) << 8);
   auto it = c->plans.find(key);
   if (it != c->plans.end()) return it->second.get();
   const TileShape sh = fwd_shape(c, c->prec);
@@ -494,6 +530,75 @@ int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
   }
   CUDA_TRY(c, cudaGetLastError());
   return QAOA_OK;
+}
+
+// Tensor map for the L2 prefetch of a forward pass's tiles (PassArgs, prefetch
+// mode 2): the input state as 8-byte elements over runs of index bits (tile
+// runs cut into dimensions of at most 8 bits, the box extent; every outer run
+// one dimension of box extent 1), at most five dimensions. False when the pass
+// does not fit that form or the driver's encoder is unavailable.
+using TensorMapEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                       const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                       CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+TensorMapEncodeFn tensor_map_encoder() {
+  static TensorMapEncodeFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<TensorMapEncodeFn>(f);
+  }();
+  return fn;
+}
+
+bool prefetch_tensor_map(int n, const PassDev& pd, const void* base, PassArgs& pa) {
+  const TensorMapEncodeFn enc = tensor_map_encoder();
+  if (!enc || pd.nsub != 1 || pd.sub[0].ninner != 0) return false;
+  const SubDev& sd = pd.sub[0];
+  uint64_t tmask = 0;
+  for (int j = 0; j < pd.T; ++j) tmask |= 1ull << sd.pos[j];
+  int dims = 0;
+  int bit[8], len[8];
+  bool tile[8];
+  for (int b = 0; b < n;) {
+    const bool t = (tmask >> b & 1ull) != 0;
+    int e = b;
+    while (e < n && ((tmask >> e & 1ull) != 0) == t) ++e;
+    while (b < e) {
+      const int l = t ? std::min(8, e - b) : e - b;
+      if (dims == 8 || l > 31) return false;
+      bit[dims] = b;
+      len[dims] = l;
+      tile[dims] = t;
+      ++dims;
+      b += l;
+    }
+  }
+  if (dims > 5 || !tile[0] || bit[0] != 0 || len[0] < 1) return false;
+  cuuint64_t gdim[5], gstride[4];
+  cuuint32_t box[5], estr[5];
+  for (int d = 0; d < dims; ++d) {
+    gdim[d] = 1ull << len[d];
+    box[d] = tile[d] ? (cuuint32_t)(1u << len[d]) : 1u;
+    estr[d] = 1;
+    if (d) gstride[d - 1] = 8ull << bit[d];
+  }
+  if ((box[0] * 8) % 16) return false;
+  const CUresult r = enc(&pa.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)dims, const_cast<void*>(base), gdim,
+                         gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  pa.tdims = dims;
+  pa.ttile = 0;
+  for (int d = 0; d < dims; ++d) {
+    pa.tbit[d] = (int8_t)bit[d];
+    pa.tlen[d] = (int8_t)len[d];
+    if (tile[d]) pa.ttile |= uint8_t(1u << d);
+  }
+  return true;
 }
 
 // reduce = false: the final pass skips <C> and norm (the gradient takes <C>
@@ -594,7 +699,15 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
     {
       const char* e = getenv("QAOA_L2HINT");
       pa.l2hint = (e && atoi(e) != 0) ? 1 : 0;
-      pa.prefetch = on_off(c->opts.l2_prefetch, "QAOA_L2PREFETCH", 0);
+      // the next tile into L2: one tensor prefetch per tile where the pass has
+      // a tensor form, else one line per 16-amplitude run
+      pa.prefetch = l2_prefetch_on(c, fwd_shape_id(c, c->prec));
+      pa.tdims = 0;
+      {
+        const char* d = getenv("QAOA_PREFETCH_DIST");
+        pa.pfdist = d ? std::max(1, std::min(4, atoi(d))) : 1;
+      }
+      if (pa.prefetch && !pp.init && prefetch_tensor_map(n, pd, pa.state, pa)) pa.prefetch = 2;
     }
     // the first pass visits every index once: the extremes come with it when
     // they are not known yet
@@ -797,6 +910,13 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   // the gradient's forward run samples nothing: the plan without the
   // block-sum constraint keeps the fused passes on the small groups
   int fwd_order = grad_fwd_order(c);
+  // the gradient's complex64 forward runs the adjoint's tile (4x3), so that the
+  // two plans can retrace each other pass by pass, unless a tile was asked for
+  struct ShapeForce {
+    qaoa_ctx* c;
+    ~ShapeForce() { c->shape_force = -1; }
+  } shape_guard{c};
+  if (c->prec == QAOA_C64 && c->opts.fwd_shape == 0 && !getenv("QAOA_FWD_SHAPE")) c->shape_force = 3;
   // stored forward states: when the adjoint plan retraces the forward plan
   // pass by pass and half of the free device memory holds one state per
   // forward pass, the forward writes each pass's output to its own buffer and
@@ -836,6 +956,7 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
   }
   // forward: psi_p (and the stored states)
   int rc = run_forward(c, p, gamma, beta, fwd_order, false, outs.empty() ? nullptr : outs.data());
+  c->shape_force = -1;
   if (rc) return rc;
   void* lam = lambda_ptr(c);
   if (!lam) return c->set_err(QAOA_ENOMEM, "allocation of the adjoint vector failed");
@@ -1103,7 +1224,7 @@ int qaoa_get_opts(const qaoa_ctx* c, qaoa_opts* o) {
   r.float_lanes = float_lanes_flag(c) ? QAOA_ON : QAOA_OFF;
   r.specialised = spec_enabled(c) ? QAOA_ON : QAOA_OFF;
   r.tile_tables = on_off(c->opts.tile_tables, "QAOA_TILE_TABLES", 1) ? QAOA_ON : QAOA_OFF;
-  r.l2_prefetch = on_off(c->opts.l2_prefetch, "QAOA_L2PREFETCH", 0) ? QAOA_ON : QAOA_OFF;
+  r.l2_prefetch = l2_prefetch_on(c, sid) ? QAOA_ON : QAOA_OFF;
   r.grad_order = grad_base_order(c) == ORDER_LOW_MIDDLE ? QAOA_ORDER_LOW_MIDDLE : QAOA_ORDER_LOW_LAST;
   r.grad_checkpoint = grad_checkpoint(c) ? QAOA_ON : QAOA_OFF;
   *o = r;
@@ -1483,7 +1604,7 @@ void* qaoa_state_ptr(qaoa_ctx* c) { return c ? c->state : nullptr; }
 int qaoa_describe_plan(int n, int precision, int p, int adjoint, char* out, int cap) {
   std::string s;
   try {
-    const TileShape fsh = fwd_shape(nullptr, precision);
+    const TileShape fsh = shape_of(fwd_shape_id(nullptr, precision, n), precision);
     Plan pl = adjoint ? plan_backward(n, p, adj_shape(precision), smax_adj(), kMinUnitsLog2, group_order(nullptr))
                       : plan_forward(n, p, fsh, smax_fwd(nullptr, fsh.T()), kMinUnitsLog2, group_order(nullptr));
     std::string e = validate(pl);

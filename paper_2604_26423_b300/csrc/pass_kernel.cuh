@@ -18,6 +18,8 @@
 // memory offsets become immediates through the additive padded layout `padi`,
 // and global offsets are walked in Gray-code order (one XOR per amplitude).
 #pragma once
+#include <cuda.h>
+
 #include <type_traits>
 
 #include "device.cuh"
@@ -42,7 +44,18 @@ struct PassArgs {
   int phase_in_smem;      // copy the phase table into shared memory
   int l2hint;             // L2 priorities: keep sub-pass outputs that are read back
   int prefetch;           // prefetch the CTA's next tile into L2 while this one runs
-                          // (passes of one tile per super-tile that load the state)
+                          // (passes of one tile per super-tile that load the state):
+                          // 1 one line per 16-amplitude run from every thread, 2 one
+                          // tensor prefetch of the whole tile (tmap) from one thread
+  // tensor prefetch (prefetch == 2): the pass's input state as a tensor of tdims
+  // <= 5 dimensions over runs of index bits (dimension d: bits tbit[d] ..
+  // tbit[d] + tlen[d] - 1, inside the tile when bit d of ttile is set), the box
+  // one tile; the coordinates of a tile are its outer index bits
+  int tdims;
+  int pfdist;             // tensor prefetch distance in the CTA's tiles (1..4)
+  int8_t tbit[5], tlen[5];
+  uint8_t ttile;
+  CUtensorMap tmap;  // 128-byte aligned by its type
   // exhaustive extremes in the |+> round (every index visited once): packed
   // keys [(C - c_lo) << 34 | x, (c_hi - C) << 34 | x], each the minimum over
   // all x (smallest C, resp. largest C, then smallest index); must hold ~0 on
@@ -198,6 +211,37 @@ __device__ __forceinline__ void swap_odd(float2* v, int s) {
 #pragma unroll
   for (int j = 0; j < (1 << R); ++j)
     if (parity_c(j) ^ s) v[j] = make_float2(v[j].y, v[j].x);
+}
+
+// L2 prefetch of one box of a tensor (cp.async.bulk.prefetch.tensor): tmap is a
+// kernel parameter (grid constant) holding a tensor map, c the box's
+// coordinates (innermost first); dims 1..5.
+__device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap* tmap, int dims, const int32_t* c) {
+  const uint64_t t = reinterpret_cast<uint64_t>(tmap);
+  switch (dims) {
+    case 1:
+      asm volatile("cp.async.bulk.prefetch.tensor.1d.L2.global.tile [%0, {%1}];" ::"l"(t), "r"(c[0]) : "memory");
+      break;
+    case 2:
+      asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(t), "r"(c[0]), "r"(c[1])
+                   : "memory");
+      break;
+    case 3:
+      asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(t), "r"(c[0]),
+                   "r"(c[1]), "r"(c[2])
+                   : "memory");
+      break;
+    case 4:
+      asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(t), "r"(c[0]),
+                   "r"(c[1]), "r"(c[2]), "r"(c[3])
+                   : "memory");
+      break;
+    default:
+      asm volatile("cp.async.bulk.prefetch.tensor.5d.L2.global.tile [%0, {%1, %2, %3, %4, %5}];" ::"l"(t),
+                   "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4])
+                   : "memory");
+      break;
+  }
 }
 
 // Per-round thread geometry: the padded shared-memory slot of the thread's
@@ -671,7 +715,24 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       bool load0;
       if constexpr (kSpec) load0 = (first_sig<RS...>() >> 2 & 3u) == SRC_GLOBAL_D;
       else load0 = sp.rd[0].src == SRC_GLOBAL_D;
-      if (load0 && A.prefetch && sp.ninner == 0) {
+      if (load0 && A.prefetch == 2 && sp.ninner == 0) {
+        // the CTA's next tile into L2 by one tensor prefetch (tensor memory
+        // accelerator; no load-store unit instructions)
+        // (pfdist tiles ahead; the CTA's first tile also issues the nearer ones)
+        if (tid == 0) {
+          for (int k = unit == blockIdx.x ? 1 : A.pfdist; k <= A.pfdist; ++k) {
+            const uint64_t next = unit + uint64_t(k) * gridDim.x;
+            if (next >= P.n_units) break;
+            const uint64_t nbase = P.outer_runs.scatter(next);
+            int32_t c[5] = {0, 0, 0, 0, 0};
+#pragma unroll
+            for (int d = 0; d < 5; ++d)
+              if (d < A.tdims && !(A.ttile >> d & 1))
+                c[d] = int32_t(nbase >> A.tbit[d] & ((1ull << A.tlen[d]) - 1));
+            tma_prefetch_l2(&A.tmap, A.tdims, c);
+          }
+        }
+      } else if (load0 && A.prefetch == 1 && sp.ninner == 0) {
         // the CTA's next tile (unit + gridDim.x) into L2: its 2^(T-4) runs of
         // 16 consecutive amplitudes (tile bits 0..3 are global bits 0..3),
         // one 128-byte line each
@@ -824,7 +885,7 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
 template <typename Real, int R, int WB, bool FAST, bool CC>
 __global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : R + WB <= 8 ? 2 : 1)
                                                               : (R + WB <= 7 ? 2 : 1))
-fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
+fwd_pass_kernel(const __grid_constant__ PassDev P, const __grid_constant__ PassArgs A) {
   fwd_pass_body<Real, R, WB, FAST, CC>(P, A);
 }
 
@@ -833,7 +894,7 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
 // and masks are compile-time constants.
 template <int R, int WB, bool FAST, uint32_t... RS>
 __global__ void __launch_bounds__(32 << WB, R + WB <= 7 ? 4 : R + WB <= 8 ? 2 : 1)
-fwd_spec_kernel(const __grid_constant__ PassDev P, const PassArgs A) {
+fwd_spec_kernel(const __grid_constant__ PassDev P, const __grid_constant__ PassArgs A) {
   fwd_pass_body<float, R, WB, FAST, sigs_need_c<RS...>(), RS...>(P, A);
 }
 

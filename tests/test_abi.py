@@ -98,12 +98,23 @@ def test_plans_valid(lib, n, p, prec):
 
 
 def test_n33_groups(lib, monkeypatch):
-    # default: one 2^13-amplitude tile per CTA and no L2 sub-passes -> 4 qubit
-    # groups (13 + 9 + 9 + 2) and 10 HBM passes at p = 3; with 2^15 super-tiles
-    # 3 groups (15 + 10 + 8) and 7 passes
+    # default complex64 tile at 33 qubits: 5x4 (2^14 amplitudes, 128-byte runs)
+    # -> 3 qubit groups and 7 HBM passes at p = 3; the 4x3 tile (2^12
+    # amplitudes, 256-byte runs) -> 4 groups and 10 passes, or with 2^15
+    # super-tiles through L2 3 groups and 7 passes
+    assert "T=14" in qaoa.describe_plan(33, 3, "c64") and "groups=3 passes=7" in qaoa.describe_plan(33, 3, "c64")
+    monkeypatch.setenv("QAOA_FWD_SHAPE", "4x3")
     assert "groups=4 passes=10" in qaoa.describe_plan(33, 3, "c64")
     monkeypatch.setenv("QAOA_SMAX", "15")
     assert "groups=3 passes=7" in qaoa.describe_plan(33, 3, "c64")
+
+
+def test_default_tile_by_size(lib):
+    # 5x4 only where it takes fewer mixer groups than 4x3 (29..34 qubits)
+    for n in range(16, 35):
+        t = qaoa.describe_plan(n, 3, "c64").splitlines()[0]
+        assert ("T=14" in t) == (29 <= n <= 34), t
+    assert "T=12" in qaoa.describe_plan(33, 3, "c128").splitlines()[0]
 
 
 @pytest.mark.parametrize("n", [12, 16, 24, 28, 33])

@@ -495,3 +495,17 @@ def test_shots_in_their_fp64_cdf_interval_large_n(n):
         tol = 1e-10 * total
         ok = (lo - tol <= t) & (t < hi + tol)
         assert bool(ok.all()), f"{int((~ok).sum())} shots outside their CDF interval"
+
+
+@pytest.mark.parametrize("n,shape", [(24, "4x3"), (26, "5x4"), (27, "5x4")])
+def test_l2_prefetch_bitwise(n, shape):
+    # prefetching each CTA's next tile into L2 (one tensor prefetch per tile)
+    # moves no data the kernel computes with: identical states and <C>
+    u, v, w = graph("complete", n, 900 + n)
+    outs = []
+    for pf in (True, False):
+        with sim(n, u, v, w, S, "c64", opts=dict(shape=shape, l2_prefetch=pf)) as s:
+            s.run(3, 0.6, 0.3)
+            outs.append((s.state().cpu().numpy().copy(), s.expect()["exp_c"]))
+    (a, ea), (b, eb) = outs
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64)) and ea == eb
