@@ -210,6 +210,13 @@ int shape_from_opt(int o) {
     default: return -1;
   }
 }
+// The paired global layout in complex64 forward plans (QAOA_PAIRED=0 turns
+// it off: 8-byte accesses only).
+bool paired_layout_enabled() {
+  const char* e = getenv("QAOA_PAIRED");
+  return !(e && strcmp(e, "0") == 0);
+}
+
 int on_off(int opt, const char* env, int dflt) {
   if (opt == QAOA_ON) return 1;
   if (opt == QAOA_OFF) return 0;
@@ -219,12 +226,15 @@ int on_off(int opt, const char* env, int dflt) {
   return dflt;
 }
 
+// Forward tile of a shape id; complex64 forward plans may use the paired
+// global layout (16-byte accesses of two adjacent amplitudes).
 TileShape shape_of(int id, int prec) {
   static const int R[5] = {kR, 4, 5, 4, 5}, WB[5] = {kWB, 4, 2, 3, 4};
   TileShape s;
   s.R = R[id];
   s.WB = WB[id];
   s.amp_bytes = amp_bytes(prec);
+  s.paired = prec == QAOA_C64 && paired_layout_enabled();
   return s;
 }
 

@@ -5,7 +5,8 @@
 // fwd_spec_kernel; adj_kernel.cuh, adj_spec_kernel). Passes whose sequence is
 // not listed run the generic kernels.
 //
-// Configurations: tile shape 4x3 (T = 12), n = 13..34, p = 0..12, the forward
+// Configurations (forward plans with and without the paired global layout):
+// tile shape 4x3 (T = 12), n = 13..34, p = 0..12, the forward
 // group orders of qaoa_run (low group last) and of the gradient (low group in
 // the middle), both with floating coalescing bits; adjoint plans in the
 // gradient's order, p = 1..12. Tile shape 5x4 (T = 14): forward plans of
@@ -60,22 +61,32 @@ int main(int argc, char** argv) {
   sh.amp_bytes = 8;
   TileShape ash = sh;
   ash.nvec = 2;
+  // forward plans may use the paired global layout; both menus are generated
+  // (QAOA_PAIRED=0 selects the unpaired one at run time)
+  TileShape shp = sh;
+  shp.paired = true;
   const int T = sh.T();
   std::set<std::vector<uint32_t>> fwd, adj;
   for (int n = T + 1; n <= 34; ++n) {
     for (int p = 0; p <= 12; ++p) {
-      for (int order : {ORDER_LOW_LAST | PLAN_FLOAT_LANES, ORDER_LOW_MIDDLE | PLAN_FLOAT_LANES})
+      for (int order : {ORDER_LOW_LAST | PLAN_FLOAT_LANES, ORDER_LOW_MIDDLE | PLAN_FLOAT_LANES}) {
         collect(plan_forward(n, p, sh, T, 9, order), fwd);
+        collect(plan_forward(n, p, shp, T, 9, order), fwd);
+      }
       if (p >= 1) collect(plan_backward(n, p, ash, T, 9, ORDER_LOW_MIDDLE), adj);
     }
   }
   TileShape sh54 = sh;
   sh54.R = 5;
   sh54.WB = 4;
+  TileShape sh54p = sh54;
+  sh54p.paired = true;
   std::set<std::vector<uint32_t>> fwd54;
   for (int n = 27; n <= 34; ++n)
-    for (int p = 0; p <= 12; ++p)
+    for (int p = 0; p <= 12; ++p) {
       collect(plan_forward(n, p, sh54, sh54.T(), 9, ORDER_LOW_LAST | PLAN_FLOAT_LANES), fwd54);
+      collect(plan_forward(n, p, sh54p, sh54p.T(), 9, ORDER_LOW_LAST | PLAN_FLOAT_LANES), fwd54);
+    }
   FILE* f = fopen(argv[1], "w");
   if (!f) {
     perror(argv[1]);

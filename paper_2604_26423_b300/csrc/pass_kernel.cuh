@@ -68,10 +68,15 @@ template <int R, int WB, int L>
 struct Lay {
   static constexpr int T = R + 5 + WB;
   __host__ __device__ static constexpr int reg(int i) {
-    return L == 0 ? 5 + i : L == 1 ? T - R + i : L == 2 ? i : (i == 0 ? 4 : T - R + i);
+    return L == 0 ? 5 + i : L == 1 ? T - R + i : L == 2 ? i : L == 3 ? (i == 0 ? 4 : T - R + i)
+                                                                      : (i == 0 ? 0 : T - R + i);
   }
-  __host__ __device__ static constexpr int lane(int i) { return L == 2 ? R + i : (L == 3 && i == 4) ? T - R : i; }
-  __host__ __device__ static constexpr int warp(int i) { return L == 0 ? 5 + R + i : L == 2 ? R + 5 + i : 5 + i; }
+  __host__ __device__ static constexpr int lane(int i) {
+    return L == 2 ? R + i : L == 4 ? 1 + i : (L == 3 && i == 4) ? T - R : i;
+  }
+  __host__ __device__ static constexpr int warp(int i) {
+    return L == 0 ? 5 + R + i : L == 2 ? R + 5 + i : L == 4 ? 6 + i : 5 + i;
+  }
   // tile-index offset of register amplitude j
   __host__ __device__ static constexpr uint32_t toff(int j) {
     uint32_t o = 0;
@@ -85,6 +90,9 @@ struct Lay {
 template <int WB>
 constexpr int NT32 = 1 << WB;
 
+// Layout id of a round signature (plan.h, round_sig: bits 0-1 and 18).
+__host__ __device__ constexpr int sig_layout(uint32_t sig) { return int(sig & 3u) | int(sig >> 18 & 1u) << 2; }
+
 // Tile bits above the 2^12-amplitude sampling block (0 for T <= 12, at most 2).
 template <int R, int WB>
 constexpr int kBlkBits = R + 5 + WB > 12 ? R + 5 + WB - 12 : 0;
@@ -95,7 +103,7 @@ constexpr int kBlkBits = R + 5 + WB > 12 ? R + 5 + WB - 12 : 0;
 template <int R, int WB, uint32_t SIG>
 __device__ __forceinline__ int tile_bit(const RoundDev& rd, int kind, int i) {
   if constexpr (SIG != 0) {
-    constexpr int L = int(SIG & 3u);
+    constexpr int L = sig_layout(SIG);
     return kind == 0 ? Lay<R, WB, L>::reg(i) : kind == 1 ? Lay<R, WB, L>::lane(i) : Lay<R, WB, L>::warp(i);
   } else {
     return kind == 0 ? rd.reg[i] : kind == 1 ? rd.lane[i] : rd.warp[i];
@@ -298,6 +306,40 @@ __device__ __forceinline__ void gray_ptr_walk(T* base, uint64_t g0, const uint64
   }
 }
 
+// As gray_ptr_walk over register bits 1..R-1 only: f(j, pointer to register
+// amplitude j) for the even j (register bit 0 clear), whose partner j | 1 is
+// the next amplitude in memory (register bit 0 on index bit 0).
+template <int R, typename T, typename F>
+__device__ __forceinline__ void gray_ptr_walk_pairs(T* base, uint64_t g0, const uint64_t* gstr, F&& f) {
+  T* q = base + g0;
+#pragma unroll
+  for (int k = 0; k < (1 << (R - 1)); ++k) {
+    if (k) {
+      const int b = ctz_c(k);
+      const int j = k ^ (k >> 1);
+      if (j >> b & 1) q += gstr[b + 1]; else q -= gstr[b + 1];
+    }
+    f((k ^ (k >> 1)) << 1, q);
+  }
+}
+
+// Two adjacent complex64 amplitudes in one 16-byte access (the address is
+// 16-byte aligned: the first has index bit 0 clear). The complex128 forms are
+// never called (the paired layout is complex64 only).
+__device__ __forceinline__ void load_pair(const float2* q, float2& a, float2& b) {
+  const float4 t = __ldcg(reinterpret_cast<const float4*>(q));
+  a = make_float2(t.x, t.y);
+  b = make_float2(t.z, t.w);
+}
+__device__ __forceinline__ void store_pair(float2* q, const float2& a, const float2& b) {
+  __stcg(reinterpret_cast<float4*>(q), make_float4(a.x, a.y, b.x, b.y));
+}
+__device__ __forceinline__ void load_pair(const double2* q, double2& a, double2& b) { a = __ldcg(q); b = __ldcg(q + 1); }
+__device__ __forceinline__ void store_pair(double2* q, const double2& a, const double2& b) {
+  __stcg(q, a);
+  __stcg(q + 1, b);
+}
+
 // Issues the asynchronous copy of one vector's tile (complex64, global indices
 // gbase | scatter(t) for tile index t) into its padded shared-memory tile:
 // thread (lane, warp) copies the amplitudes at tile indices
@@ -336,7 +378,8 @@ __device__ __forceinline__ void smem_load(int layout, const C2* tile, uint32_t s
     case 0: smem_load_l<R, WB, 0, AB>(tile, sbase, v); break;
     case 1: smem_load_l<R, WB, 1, AB>(tile, sbase, v); break;
     case 2: smem_load_l<R, WB, 2, AB>(tile, sbase, v); break;
-    default: smem_load_l<R, WB, 3, AB>(tile, sbase, v); break;
+    case 3: smem_load_l<R, WB, 3, AB>(tile, sbase, v); break;
+    default: smem_load_l<R, WB, 4, AB>(tile, sbase, v); break;
   }
 }
 template <int R, int WB, int AB, typename C2>
@@ -345,7 +388,8 @@ __device__ __forceinline__ void smem_store(int layout, C2* tile, uint32_t sbase,
     case 0: smem_store_l<R, WB, 0, AB>(tile, sbase, v); break;
     case 1: smem_store_l<R, WB, 1, AB>(tile, sbase, v); break;
     case 2: smem_store_l<R, WB, 2, AB>(tile, sbase, v); break;
-    default: smem_store_l<R, WB, 3, AB>(tile, sbase, v); break;
+    case 3: smem_store_l<R, WB, 3, AB>(tile, sbase, v); break;
+    default: smem_store_l<R, WB, 4, AB>(tile, sbase, v); break;
   }
 }
 
@@ -383,7 +427,7 @@ struct RoundOps {
   bool dstg, cost, reduce, lam;
   uint8_t mixA, mixB;
   __device__ __forceinline__ explicit RoundOps(const RoundDev& rd)
-      : layout(kConst ? int(SIG & 3u) : int(rd.layout)),
+      : layout(kConst ? sig_layout(SIG) : int(rd.layout)),
         src(kConst ? int(SIG >> 2 & 3u) : int(rd.src)),
         dstg(kConst ? bool(SIG >> 4 & 1u) : rd.dst == DST_GLOBAL_D),
         cost(kConst ? bool(SIG >> 5 & 1u) : rd.cost != 0),
@@ -677,7 +721,10 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       const uint64_t pol = sp.keep ? l2_policy_evict_last() : l2_policy_evict_first();
       gray_ptr_walk<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { st_hint(q, v[j], pol); });
     } else {
-      gray_ptr_walk<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
+      if (AB == 8 && op.layout == 4)  // paired layout: one 16-byte store per register pair
+        gray_ptr_walk_pairs<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { store_pair(q, v[j], v[j | 1]); });
+      else
+        gray_ptr_walk<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
     }
   } else {
     smem_store<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
@@ -755,7 +802,16 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
           const uint64_t pol = l2_policy_evict_first();
           gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = ld_hint(q, pol); });
         } else {
-          gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = __ldcg(q); });
+          bool paired = false;
+          if constexpr (kSpec) paired = sig_layout(first_sig<RS...>()) == 4;
+          else paired = sp.rd[0].layout == 4;
+          if (AB == 8 && paired) {
+            // paired layout: register bit 0 is index bit 0, one 16-byte load
+            // brings amplitudes j and j | 1
+            gray_ptr_walk_pairs<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { load_pair(q, v[j], v[j | 1]); });
+          } else {
+            gray_ptr_walk<R>(gs, g0.gb, g0.gstr, [&](int j, const C2* q) { v[j] = __ldcg(q); });
+          }
         }
       }
       // tile constants from the table: into the buffer the previous tile did

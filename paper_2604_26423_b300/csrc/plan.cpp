@@ -56,6 +56,13 @@ bool menu_layout(const TileShape& sh, int id, RoundPlan& rp) {
       lanes.push_back(T - R);
       for (int b = 5; b < T - R; ++b) warps.push_back(b);
       break;
+    case 4:
+      if (!sh.paired || sh.amp_bytes != 8) return false;
+      regs.push_back(0);
+      for (int i = 1; i < R; ++i) regs.push_back(T - R + i);
+      for (int i = 1; i <= 5; ++i) lanes.push_back(i);
+      for (int b = 6; b <= T - R; ++b) warps.push_back(b);
+      break;
     default:
       return false;
   }
@@ -69,9 +76,9 @@ bool menu_layout(const TileShape& sh, int id, RoundPlan& rp) {
 }
 
 uint32_t round_sig(const RoundPlan& rp) {
-  return kSigValid | uint32_t(rp.layout & 3) | uint32_t(rp.src & 3) << 2 | uint32_t(rp.dst == DST_GLOBAL) << 4 |
-         uint32_t(rp.cost != 0) << 5 | uint32_t(rp.reduce != 0) << 6 | uint32_t(rp.lam != 0) << 7 |
-         uint32_t(rp.mixA & 31) << 8 | uint32_t(rp.mixB & 31) << 13;
+  return kSigValid | uint32_t(rp.layout & 3) | uint32_t(rp.layout >> 2 & 1) << 18 | uint32_t(rp.src & 3) << 2 |
+         uint32_t(rp.dst == DST_GLOBAL) << 4 | uint32_t(rp.cost != 0) << 5 | uint32_t(rp.reduce != 0) << 6 |
+         uint32_t(rp.lam != 0) << 7 | uint32_t(rp.mixA & 31) << 8 | uint32_t(rp.mixB & 31) << 13;
 }
 
 std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool cost, uint32_t b_bits,
@@ -89,10 +96,17 @@ std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool co
   nodes.push_back({a_bits, b_bits, !cost, -1, -1, 0, 0, 0});
   std::set<std::tuple<uint32_t, uint32_t, bool>> seen;
   size_t head = 0;
+  // among the shortest sequences, the one with the most paired global rounds
+  // (16-byte accesses in the loading first round and the storing last round)
+  std::vector<RoundPlan> best;
+  int best_score = -1;
   for (int depth = 0; depth < kMaxRounds; ++depth) {
     const size_t level_end = nodes.size();
     for (size_t ni = head; ni < level_end; ++ni) {
-      for (int id = 0; id < kNumLayouts; ++id) {
+      for (int k = 0; k < kNumLayouts; ++k) {
+        // the paired layout first: among round sequences of equal length the
+        // one with 16-byte global accesses is found first
+        const int id = (k + kNumLayouts - 1) % kNumLayouts;
         RoundPlan rp;
         if (!menu_layout(sh, id, rp)) continue;
         if (depth == 0 && first_src == SRC_GLOBAL && !rp.global_facing) continue;
@@ -130,7 +144,12 @@ std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool co
             rr.lam = (lam && r == 0) ? 1 : 0;
             out.push_back(rr);
           }
-          return out;
+          const int score = int(out.back().layout == 4) + int(first_src == SRC_GLOBAL && out[0].layout == 4);
+          if (score > best_score) {
+            best_score = score;
+            best = out;
+          }
+          continue;
         }
         auto key = std::make_tuple(nd.remA, nd.remB, nd.cost_done);
         if (seen.count(key)) continue;
@@ -138,6 +157,7 @@ std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool co
         nodes.push_back(nd);
       }
     }
+    if (best_score >= 0) return best;
     head = level_end;
   }
   throw std::runtime_error("plan_rounds: no round sequence from the layout menu");
@@ -158,8 +178,9 @@ std::string validate_rounds(const TileShape& sh, const std::vector<RoundPlan>& r
     if (seen != ((1u << T) - 1) || popc(seen) != T) return "round is not a permutation of tile bits";
     const bool is_last = k + 1 == rounds.size();
     if ((k == 0 && rp.src == SRC_GLOBAL) || is_last) {
+      const bool paired = rp.reg[0] == 0 && rp.lane[0] == 1 && rp.lane[1] == 2 && rp.lane[2] == 3;
       for (int i = 0; i < 4; ++i)
-        if (rp.lane[i] != i) return "global round without lanes 0..3 on tile bits 0..3";
+        if (rp.lane[i] != i && !paired) return "global round without lanes 0..3 (or register 0 and lanes 0..2) on tile bits 0..3";
     }
     if (is_last != (rp.dst == DST_GLOBAL)) return "only the last round stores to global memory";
     if (k > 0 && rp.src != SRC_SMEM) return "only the first round reads global memory";

@@ -35,6 +35,9 @@ enum : uint8_t { DST_SMEM = 0, DST_GLOBAL = 1 };
 // Kernel shape: R register bits, 5 lane bits, WB warp bits; amplitude bytes.
 struct TileShape {
   int R = 5, WB = 3, amp_bytes = 8, nvec = 1;
+  // the menu offers the paired global layout (id 4: register bit 0 on tile bit
+  // 0, so each thread moves two adjacent 8-byte amplitudes per 16-byte access)
+  bool paired = false;
   int T() const { return R + 5 + WB; }
 };
 
@@ -140,9 +143,10 @@ std::string validate_rounds(const TileShape& shape, const std::vector<RoundPlan>
 bool plans_mirror(const Plan& fwd, const Plan& bwd);
 
 // Compile-time signature of a round (the kernels' specialised instantiations,
-// kSigValid set): bits 0-1 layout, 2-3 source, 4 stores to global memory,
-// 5 cost phase, 6 reduction, 7 lambda creation, 8-12 mixer A mask, 13-17
-// mixer B mask. 0 is never a valid signature (it selects runtime decoding).
+// kSigValid set): bits 0-1 and 18 layout, 2-3 source, 4 stores to global
+// memory, 5 cost phase, 6 reduction, 7 lambda creation, 8-12 mixer A mask,
+// 13-17 mixer B mask. 0 is never a valid signature (it selects runtime
+// decoding).
 constexpr uint32_t kSigValid = 1u << 31;
 uint32_t round_sig(const RoundPlan& rp);
 
@@ -151,11 +155,15 @@ uint32_t round_sig(const RoundPlan& rp);
 //   1 "G2": registers on the top R bits, lanes on 0..4, warps on the rest
 //   2 "S":  registers on bits 0..R-1, lanes on R..R+4, warps on the rest
 //   3 "G3": registers on bit 4 and the top R-1 bits, lanes on 0..3 and T-R
+//   4 "GP" (shapes with `paired`): registers on bit 0 and the top R-1 bits,
+//     lanes on 1..5, warps on the rest
 // G1, G2 and G3 keep lanes 0..3 on tile bits 0..3 (coalesced global access);
-// all four keep lanes 0..3 (0..2 for 16-byte amplitudes) on bits of distinct
-// residue classes, so shared-memory accesses are conflict-free. Kernels
-// instantiate one code path per menu entry with compile-time offsets.
-constexpr int kNumLayouts = 4;
+// GP keeps register bit 0 and lanes 0..2 on tile bits 0..3 (each lane moves
+// two adjacent amplitudes, eight lanes one 16-amplitude run); all keep lanes
+// 0..3 (0..2 for 16-byte amplitudes) on bits of distinct residue classes, so
+// shared-memory accesses are conflict-free. Kernels instantiate one code path
+// per menu entry with compile-time offsets.
+constexpr int kNumLayouts = 5;
 bool menu_layout(const TileShape& sh, int id, RoundPlan& rp);
 
 // Residue class of tile bit j in the shared-memory swizzle: rows of 16 c64 or 8

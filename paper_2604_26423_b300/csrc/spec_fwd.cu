@@ -36,9 +36,9 @@ const FwdSpec kFwdSpecs54[] = {
 }  // namespace
 
 uint32_t round_sig_dev(const RoundDev& rd) {
-  return kSigValid | uint32_t(rd.layout & 3) | uint32_t(rd.src & 3) << 2 | uint32_t(rd.dst == DST_GLOBAL_D) << 4 |
-         uint32_t(rd.cost != 0) << 5 | uint32_t(rd.reduce != 0) << 6 | uint32_t(rd.lam != 0) << 7 |
-         uint32_t(rd.mixA & 31) << 8 | uint32_t(rd.mixB & 31) << 13;
+  return kSigValid | uint32_t(rd.layout & 3) | uint32_t(rd.layout >> 2 & 1) << 18 | uint32_t(rd.src & 3) << 2 |
+         uint32_t(rd.dst == DST_GLOBAL_D) << 4 | uint32_t(rd.cost != 0) << 5 | uint32_t(rd.reduce != 0) << 6 |
+         uint32_t(rd.lam != 0) << 7 | uint32_t(rd.mixA & 31) << 8 | uint32_t(rd.mixB & 31) << 13;
 }
 
 FwdPassKernel find_fwd_spec(const SubDev& sd, int R, int WB) {

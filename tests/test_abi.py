@@ -200,3 +200,20 @@ def test_weight_limits_and_quantisation(lib):
 def inputs_uniforms(seed, count):
     from paper_2604_26423_b300 import inputs
     return inputs.uniforms(seed, count)
+
+
+@pytest.mark.parametrize("shape", ["4x3", "5x4"])
+def test_paired_global_layout(lib, monkeypatch, shape):
+    # complex64 forward plans load and store through the paired layout
+    # (register bit 0 on index bit 0, lanes on bits 1..5) where a shortest
+    # round sequence allows it; every plan stays valid; QAOA_PAIRED=0 and the
+    # adjoint plans keep 8-byte accesses
+    monkeypatch.setenv("QAOA_FWD_SHAPE", shape)
+    paired_round = re.compile(r"round src=\d dst=\d reg=0,[^ ]* lane=1,2,3,4,5 ")
+    for n in (29, 30, 33):
+        text = qaoa.describe_plan(n, 3, "c64")
+        assert "INVALID" not in text and paired_round.search(text), n
+        assert not paired_round.search(qaoa.describe_plan(n, 3, "c64", adjoint=True))
+        assert not paired_round.search(qaoa.describe_plan(n, 3, "c128"))
+    monkeypatch.setenv("QAOA_PAIRED", "0")
+    assert not paired_round.search(qaoa.describe_plan(33, 3, "c64"))
