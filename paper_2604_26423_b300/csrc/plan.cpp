@@ -300,11 +300,14 @@ std::vector<Group> make_groups(int n, int S) {
     const int X = S - r;
     for (int a = S; a < n; a += X) {
       const int b = std::min(n, a + X);
-      const int h = std::min(a, n - X);
       Group g;
       for (int q = 0; q < r; ++q) g.sb.push_back(q);
-      for (int q = h; q < h + X; ++q) g.sb.push_back(q);
-      for (int q = a; q < b; ++q) g.targets.push_back(q);
+      // a last window narrower than X is filled with the lowest bits above
+      // the coalescing ones (r, r+1, ...), not the bits just below it: the
+      // tile then spans fewer memory pages (its high bits are the targets
+      // only) and bit r lengthens its contiguous runs
+      for (int q = r; q < r + (X - (b - a)); ++q) g.sb.push_back(q);
+      for (int q = a; q < b; ++q) g.sb.push_back(q), g.targets.push_back(q);
       groups.push_back(g);
     }
   }
