@@ -564,7 +564,7 @@ TensorMapEncodeFn tensor_map_encoder() {
   return fn;
 }
 
-bool prefetch_tensor_map(int n, const PassDev& pd, const void* base, PassArgs& pa) {
+bool prefetch_tensor_map(int n, const PassDev& pd, const void* base, PassArgs& pa, CUtensorMap* map) {
   const TensorMapEncodeFn enc = tensor_map_encoder();
   if (!enc || pd.nsub != 1 || pd.sub[0].ninner != 0) return false;
   const SubDev& sd = pd.sub[0];
@@ -597,7 +597,7 @@ bool prefetch_tensor_map(int n, const PassDev& pd, const void* base, PassArgs& p
     if (d) gstride[d - 1] = 8ull << bit[d];
   }
   if ((box[0] * 8) % 16) return false;
-  const CUresult r = enc(&pa.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)dims, const_cast<void*>(base), gdim,
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, (cuuint32_t)dims, const_cast<void*>(base), gdim,
                          gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return false;
@@ -717,7 +717,20 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
         const char* d = getenv("QAOA_PREFETCH_DIST");
         pa.pfdist = d ? std::max(1, std::min(4, atoi(d))) : 1;
       }
-      if (pa.prefetch && !pp.init && prefetch_tensor_map(n, pd, pa.state, pa)) pa.prefetch = 2;
+      if (pa.prefetch && !pp.init && prefetch_tensor_map(n, pd, pa.state, pa, &pa.tmap)) pa.prefetch = 2;
+      // tensor stores of each tile from shared memory (complex64, one tile
+      // per super-tile): option tma_store, QAOA_TMA_STORE
+      pa.tma_store = 0;
+      if (c->prec == QAOA_C64 && on_off(0, "QAOA_TMA_STORE", 0) && pd.nsub == 1 && pd.sub[0].ninner == 0) {
+        PassArgs probe = pa;
+        if (prefetch_tensor_map(n, pd, pa.out, probe, &pa.smap) &&
+            (pa.prefetch != 2 || (probe.tdims == pa.tdims && probe.ttile == pa.ttile))) {
+          pa.tdims = probe.tdims;
+          pa.ttile = probe.ttile;
+          for (int d = 0; d < 5; ++d) { pa.tbit[d] = probe.tbit[d]; pa.tlen[d] = probe.tlen[d]; }
+          pa.tma_store = 1;
+        }
+      }
     }
     // the first pass visits every index once: the extremes come with it when
     // they are not known yet

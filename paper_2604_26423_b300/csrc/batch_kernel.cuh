@@ -362,6 +362,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     A.phase_in_smem = 0;
     A.l2hint = 0;
     A.prefetch = 0;
+    A.tma_store = 0;
     A.ext_keys = nullptr;
     constexpr int TILE = padded_size<8>(FR + 5 + kBatchWB);
     float2* tile = reinterpret_cast<float2*>(smem);

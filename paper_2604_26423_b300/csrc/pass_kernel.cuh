@@ -55,7 +55,11 @@ struct PassArgs {
   int pfdist;             // tensor prefetch distance in the CTA's tiles (1..4)
   int8_t tbit[5], tlen[5];
   uint8_t ttile;
+  int tma_store;          // the final round writes the tile densely into shared memory
+                          // and one thread stores it with a tensor store (smap: the
+                          // output buffer, the same dimensions as tmap)
   CUtensorMap tmap;  // 128-byte aligned by its type
+  CUtensorMap smap;
   // exhaustive extremes in the |+> round (every index visited once): packed
   // keys [(C - c_lo) << 34 | x, (c_hi - C) << 34 | x], each the minimum over
   // all x (smallest C, resp. largest C, then smallest index); must hold ~0 on
@@ -250,6 +254,63 @@ __device__ __forceinline__ void tma_prefetch_l2(const CUtensorMap* tmap, int dim
                    : "memory");
       break;
   }
+}
+
+// Tensor store of one box from shared memory (cp.async.bulk.tensor, bulk
+// group): tmap a grid-constant tensor map, c the box's coordinates, smem the
+// 128-byte aligned shared-memory address of the dense box.
+__device__ __forceinline__ void tma_store_box(const CUtensorMap* tmap, int dims, const int32_t* c, uint32_t smem) {
+  const uint64_t t = reinterpret_cast<uint64_t>(tmap);
+  switch (dims) {
+    case 1:
+      asm volatile("cp.async.bulk.tensor.1d.global.shared::cta.bulk_group [%0, {%1}], [%2];" ::"l"(t), "r"(c[0]),
+                   "r"(smem)
+                   : "memory");
+      break;
+    case 2:
+      asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(t), "r"(c[0]),
+                   "r"(c[1]), "r"(smem)
+                   : "memory");
+      break;
+    case 3:
+      asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(t),
+                   "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(smem)
+                   : "memory");
+      break;
+    case 4:
+      asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(t),
+                   "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(smem)
+                   : "memory");
+      break;
+    default:
+      asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(t),
+                   "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(smem)
+                   : "memory");
+      break;
+  }
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until the committed tensor stores have read their shared memory
+// (read) or completed (all).
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Makes this thread's shared-memory writes visible to the tensor engine.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Dense (unpadded) view of a tile's shared memory, 128-byte aligned: the box
+// of a tensor store. The padded tile is at least 127 bytes larger than the
+// dense one for every shape, so the view fits inside it.
+template <typename C2>
+__device__ __forceinline__ C2* dense_tile(C2* tile) {
+  return reinterpret_cast<C2*>((reinterpret_cast<uintptr_t>(tile) + 127) & ~uintptr_t(127));
+}
+
+// Tensor coordinates of the tile at global index base (outer dimensions from
+// its bits, tile dimensions 0).
+__device__ __forceinline__ void tile_coords(const PassArgs& A, uint64_t base, int32_t* c) {
+#pragma unroll
+  for (int d = 0; d < 5; ++d)
+    c[d] = (d < A.tdims && !(A.ttile >> d & 1)) ? int32_t(base >> A.tbit[d] & ((1ull << A.tlen[d]) - 1)) : 0;
 }
 
 // Per-round thread geometry: the padded shared-memory slot of the thread's
@@ -715,6 +776,37 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     if constexpr (kSw) {
       if (sp.st_plain) swap_odd<R>(reinterpret_cast<float2*>(v), s);  // a run's output: plain storage
     }
+    if constexpr (AB == 8) {
+     if (A.tma_store) {
+      // the tile densely into shared memory (tile index order, the tensor
+      // store's box) once every thread has read this round's amplitudes from
+      // the padded tile; one thread stores the box after the round
+      __syncthreads();
+      C2* dense = dense_tile(tile);
+      uint32_t tb = 0;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) tb |= uint32_t(lane >> i & 1) << tile_bit<R, WB, SIG>(rd, 1, i);
+#pragma unroll
+      for (int i = 0; i < WB; ++i) tb |= uint32_t(warp >> i & 1) << tile_bit<R, WB, SIG>(rd, 2, i);
+      auto toff = [&](int j) {
+        uint32_t o = 0;
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+          if (j >> i & 1) o |= 1u << tile_bit<R, WB, SIG>(rd, 0, i);
+        return o;
+      };
+      if (op.layout == 4) {
+#pragma unroll
+        for (int j = 0; j < (1 << R); j += 2)
+          *reinterpret_cast<float4*>(dense + tb + toff(j)) = make_float4(v[j].x, v[j].y, v[j + 1].x, v[j + 1].y);
+      } else {
+#pragma unroll
+        for (int j = 0; j < (1 << R); ++j) dense[tb + toff(j)] = v[j];
+      }
+      fence_proxy_async_smem();
+      return;
+     }
+    }
     const RoundGeo<R, WB, AB> geo(sp, rd, gbase, lane, warp, A.ctabs);
     if (A.l2hint) {
       // outputs of a sub-pass that a later sub-pass reads back stay in L2
@@ -770,12 +862,8 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
           for (int k = unit == blockIdx.x ? 1 : A.pfdist; k <= A.pfdist; ++k) {
             const uint64_t next = unit + uint64_t(k) * gridDim.x;
             if (next >= P.n_units) break;
-            const uint64_t nbase = P.outer_runs.scatter(next);
-            int32_t c[5] = {0, 0, 0, 0, 0};
-#pragma unroll
-            for (int d = 0; d < 5; ++d)
-              if (d < A.tdims && !(A.ttile >> d & 1))
-                c[d] = int32_t(nbase >> A.tbit[d] & ((1ull << A.tlen[d]) - 1));
+            int32_t c[5];
+            tile_coords(A, P.outer_runs.scatter(next), c);
             tma_prefetch_l2(&A.tmap, A.tdims, c);
           }
         }
@@ -833,6 +921,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         }
         *tcount += 1;
       }
+      if (AB == 8 && A.tma_store && tid == 0) bulk_wait_read();  // the previous tile's store has read its box
       __syncthreads();  // previous tile finished with shared memory
       if (ahead) {
         const uint64_t next = unit + gridDim.x;
@@ -867,6 +956,14 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
           fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, gpar, tc, phase, lane, warp, wacc, v, ext_s);
         }
         red_last = sp.rd[sp.nrounds - 1].reduce != 0;
+      }
+      if (AB == 8 && A.tma_store) {
+        __syncthreads();  // the dense box is complete (each writer fenced its writes)
+        if (tid == 0) {
+          int32_t c[5];
+          tile_coords(A, gbase, c);
+          tma_store_box(&A.smap, A.tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tile)));
+        }
       }
       if (CC && A.bsum && red_last) {
         // this tile is 2^T consecutive amplitudes: its 2^(T-12) block sums;
@@ -920,6 +1017,7 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
   uint32_t tcount = 0;
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
     fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount, ext_s);
+  if (A.tma_store && tid == 0) bulk_wait_all();  // the last tensor store is complete before the CTA ends
 
   if (CC && A.ext_keys) {
     __syncthreads();
