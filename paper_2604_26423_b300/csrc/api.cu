@@ -457,10 +457,10 @@ const Plan* get_plan(qaoa_ctx* c, int p, int order) {
 }
 
 template <typename Real, bool FAST, bool CC, int R = kR, int WB = kWB>
-int launch_pass(qaoa_ctx* c, const PassDev& pd, const PassArgs& pa, size_t smem, int grid) {
+int launch_pass(qaoa_ctx* c, const PassDev& pd, const PassArgs& pa, const PassTma& pt, size_t smem, int grid) {
   auto kern = fwd_pass_kernel<Real, R, WB, FAST, CC>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, 32 << WB, smem, c->stream>>>(pd, pa);
+  kern<<<grid, 32 << WB, smem, c->stream>>>(pd, pa, pt);
   if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   return QAOA_OK;
@@ -478,35 +478,37 @@ int blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
 // Instantiation for (precision, tile shape, mixer form, C(x) code): occupancy
 // query when `launch` is false, else the launch.
 template <bool FAST, bool CC>
-int pass_dispatch(qaoa_ctx* c, int shape, bool launch, const PassDev& pd, const PassArgs& pa, size_t smem, int grid,
+int pass_dispatch(qaoa_ctx* c, int shape, bool launch, const PassDev& pd, const PassArgs& pa, const PassTma& pt,
+                  size_t smem, int grid,
                   int* bps) {
   if (c->prec == QAOA_C128) {
     if (shape == 3)
-      return launch ? launch_pass<double, FAST, CC, 4, 3>(c, pd, pa, smem, grid)
+      return launch ? launch_pass<double, FAST, CC, 4, 3>(c, pd, pa, pt, smem, grid)
                     : blocks_per_sm<double, FAST, CC, 4, 3>(c, smem, bps);
-    return launch ? launch_pass<double, FAST, CC>(c, pd, pa, smem, grid) : blocks_per_sm<double, FAST, CC>(c, smem, bps);
+    return launch ? launch_pass<double, FAST, CC>(c, pd, pa, pt, smem, grid) : blocks_per_sm<double, FAST, CC>(c, smem, bps);
   }
   if (shape == 1)
-    return launch ? launch_pass<float, FAST, CC, 4, 4>(c, pd, pa, smem, grid)
+    return launch ? launch_pass<float, FAST, CC, 4, 4>(c, pd, pa, pt, smem, grid)
                   : blocks_per_sm<float, FAST, CC, 4, 4>(c, smem, bps);
   if (shape == 2)
-    return launch ? launch_pass<float, FAST, CC, 5, 2>(c, pd, pa, smem, grid)
+    return launch ? launch_pass<float, FAST, CC, 5, 2>(c, pd, pa, pt, smem, grid)
                   : blocks_per_sm<float, FAST, CC, 5, 2>(c, smem, bps);
   if (shape == 3)
-    return launch ? launch_pass<float, FAST, CC, 4, 3>(c, pd, pa, smem, grid)
+    return launch ? launch_pass<float, FAST, CC, 4, 3>(c, pd, pa, pt, smem, grid)
                   : blocks_per_sm<float, FAST, CC, 4, 3>(c, smem, bps);
   if (shape == 4)
-    return launch ? launch_pass<float, FAST, CC, 5, 4>(c, pd, pa, smem, grid)
+    return launch ? launch_pass<float, FAST, CC, 5, 4>(c, pd, pa, pt, smem, grid)
                   : blocks_per_sm<float, FAST, CC, 5, 4>(c, smem, bps);
-  return launch ? launch_pass<float, FAST, CC>(c, pd, pa, smem, grid) : blocks_per_sm<float, FAST, CC>(c, smem, bps);
+  return launch ? launch_pass<float, FAST, CC>(c, pd, pa, pt, smem, grid) : blocks_per_sm<float, FAST, CC>(c, smem, bps);
 }
 
 int pass_any(qaoa_ctx* c, bool fast, bool cc, int wide, bool launch, const PassDev& pd, const PassArgs& pa,
+             const PassTma& pt,
              size_t smem, int grid, int* bps) {
-  if (fast) return cc ? pass_dispatch<true, true>(c, wide, launch, pd, pa, smem, grid, bps)
-                      : pass_dispatch<true, false>(c, wide, launch, pd, pa, smem, grid, bps);
-  return cc ? pass_dispatch<false, true>(c, wide, launch, pd, pa, smem, grid, bps)
-            : pass_dispatch<false, false>(c, wide, launch, pd, pa, smem, grid, bps);
+  if (fast) return cc ? pass_dispatch<true, true>(c, wide, launch, pd, pa, pt, smem, grid, bps)
+                      : pass_dispatch<true, false>(c, wide, launch, pd, pa, pt, smem, grid, bps);
+  return cc ? pass_dispatch<false, true>(c, wide, launch, pd, pa, pt, smem, grid, bps)
+            : pass_dispatch<false, false>(c, wide, launch, pd, pa, pt, smem, grid, bps);
 }
 
 int run_small(qaoa_ctx* c, int p, const double* gamma, const double* beta) {
@@ -564,7 +566,7 @@ TensorMapEncodeFn tensor_map_encoder() {
   return fn;
 }
 
-bool prefetch_tensor_map(int n, const PassDev& pd, const void* base, PassArgs& pa, CUtensorMap* map) {
+bool prefetch_tensor_map(int n, const PassDev& pd, const void* base, PassTma& pt, CUtensorMap* map) {
   const TensorMapEncodeFn enc = tensor_map_encoder();
   if (!enc || pd.nsub != 1 || pd.sub[0].ninner != 0) return false;
   const SubDev& sd = pd.sub[0];
@@ -601,12 +603,12 @@ bool prefetch_tensor_map(int n, const PassDev& pd, const void* base, PassArgs& p
                          gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return false;
-  pa.tdims = dims;
-  pa.ttile = 0;
+  pt.tdims = dims;
+  pt.ttile = 0;
   for (int d = 0; d < dims; ++d) {
-    pa.tbit[d] = (int8_t)bit[d];
-    pa.tlen[d] = (int8_t)len[d];
-    if (tile[d]) pa.ttile |= uint8_t(1u << d);
+    pt.tbit[d] = (int8_t)bit[d];
+    pt.tlen[d] = (int8_t)len[d];
+    if (tile[d]) pt.ttile |= uint8_t(1u << d);
   }
   return true;
 }
@@ -696,6 +698,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
     const PassDev& pd = pds[pi];
     const bool fast = fasts[pi];
     PassArgs pa;
+    PassTma pt;
     pa.state = outs && pi > 0 ? outs[pi - 1] : c->state;
     pa.out = outs ? outs[pi] : c->state;
     if (pa.out != pa.state && pd.nsub != 1)
@@ -712,22 +715,22 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       // the next tile into L2: one tensor prefetch per tile where the pass has
       // a tensor form, else one line per 16-amplitude run
       pa.prefetch = l2_prefetch_on(c, fwd_shape_id(c, c->prec));
-      pa.tdims = 0;
+      memset(&pt, 0, sizeof pt);
       {
         const char* d = getenv("QAOA_PREFETCH_DIST");
-        pa.pfdist = d ? std::max(1, std::min(4, atoi(d))) : 1;
+        pt.pfdist = d ? std::max(1, std::min(4, atoi(d))) : 1;
       }
-      if (pa.prefetch && !pp.init && prefetch_tensor_map(n, pd, pa.state, pa, &pa.tmap)) pa.prefetch = 2;
+      if (pa.prefetch && !pp.init && prefetch_tensor_map(n, pd, pa.state, pt, &pt.tmap)) pa.prefetch = 2;
       // tensor stores of each tile from shared memory (complex64, one tile
       // per super-tile): option tma_store, QAOA_TMA_STORE
       pa.tma_store = 0;
       if (c->prec == QAOA_C64 && on_off(0, "QAOA_TMA_STORE", 0) && pd.nsub == 1 && pd.sub[0].ninner == 0) {
-        PassArgs probe = pa;
-        if (prefetch_tensor_map(n, pd, pa.out, probe, &pa.smap) &&
-            (pa.prefetch != 2 || (probe.tdims == pa.tdims && probe.ttile == pa.ttile))) {
-          pa.tdims = probe.tdims;
-          pa.ttile = probe.ttile;
-          for (int d = 0; d < 5; ++d) { pa.tbit[d] = probe.tbit[d]; pa.tlen[d] = probe.tlen[d]; }
+        PassTma probe = pt;
+        if (prefetch_tensor_map(n, pd, pa.out, probe, &pt.smap) &&
+            (pa.prefetch != 2 || (probe.tdims == pt.tdims && probe.ttile == pt.ttile))) {
+          pt.tdims = probe.tdims;
+          pt.ttile = probe.ttile;
+          for (int d = 0; d < 5; ++d) { pt.tbit[d] = probe.tbit[d]; pt.tlen[d] = probe.tlen[d]; }
           pa.tma_store = 1;
         }
       }
@@ -755,7 +758,7 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)spec, 32 << sh.WB, smem));
       if (bps < 1) return c->set_err(QAOA_ECUDA, "pass kernel does not fit on an SM (smem %zu)", smem);
     } else {
-      rc = pass_any(c, fast, cc, wide, false, pd, pa, smem, 0, &bps);
+      rc = pass_any(c, fast, cc, wide, false, pd, pa, pt, smem, 0, &bps);
       if (rc) return rc;
     }
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
@@ -787,12 +790,12 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 0, bytes);
       if (spec) {
-        spec<<<grid, 32 << sh.WB, smem, c->stream>>>(pd, pa);
+        spec<<<grid, 32 << sh.WB, smem, c->stream>>>(pd, pa, pt);
         if (c->prof_on) ++c->nlaunch;
         const cudaError_t le = cudaGetLastError();
         rc = le == cudaSuccess ? QAOA_OK : c->set_err(QAOA_ECUDA, "specialised pass kernel: %s", cudaGetErrorString(le));
       } else {
-        rc = pass_any(c, fast, cc, wide, true, pd, pa, smem, grid, nullptr);
+        rc = pass_any(c, fast, cc, wide, true, pd, pa, pt, smem, grid, nullptr);
       }
     }
     if (rc) return rc;

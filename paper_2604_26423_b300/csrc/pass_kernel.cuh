@@ -47,24 +47,29 @@ struct PassArgs {
                           // (passes of one tile per super-tile that load the state):
                           // 1 one line per 16-amplitude run from every thread, 2 one
                           // tensor prefetch of the whole tile (tmap) from one thread
-  // tensor prefetch (prefetch == 2): the pass's input state as a tensor of tdims
-  // <= 5 dimensions over runs of index bits (dimension d: bits tbit[d] ..
-  // tbit[d] + tlen[d] - 1, inside the tile when bit d of ttile is set), the box
-  // one tile; the coordinates of a tile are its outer index bits
-  int tdims;
-  int pfdist;             // tensor prefetch distance in the CTA's tiles (1..4)
-  int8_t tbit[5], tlen[5];
-  uint8_t ttile;
   int tma_store;          // the final round writes the tile densely into shared memory
-                          // and one thread stores it with a tensor store (smap: the
-                          // output buffer, the same dimensions as tmap)
-  CUtensorMap tmap;  // 128-byte aligned by its type
-  CUtensorMap smap;
+                          // and one thread stores it with a tensor store (PassTma)
   // exhaustive extremes in the |+> round (every index visited once): packed
   // keys [(C - c_lo) << 34 | x, (c_hi - C) << 34 | x], each the minimum over
   // all x (smallest C, resp. largest C, then smallest index); must hold ~0 on
   // entry; nullptr: not computed in this pass
   unsigned long long* ext_keys;
+};
+
+// Tensor maps of a pass kernel (a separate kernel parameter, so that the
+// persistent batch kernel, which builds its PassArgs locally, carries none):
+// the pass's input state (tmap: next-tile prefetch, PassArgs.prefetch == 2) and
+// output state (smap: tensor stores, PassArgs.tma_store) as tensors of tdims <=
+// 5 dimensions over runs of index bits (dimension d: bits tbit[d] .. tbit[d] +
+// tlen[d] - 1, inside the tile when bit d of ttile is set), the box one tile;
+// the coordinates of a tile are its outer index bits.
+struct PassTma {
+  CUtensorMap tmap;  // 128-byte aligned by its type
+  CUtensorMap smap;
+  int tdims;
+  int pfdist;        // prefetch distance in the CTA's tiles (1..4)
+  int8_t tbit[5], tlen[5];
+  uint8_t ttile;
 };
 
 // Compile-time copy of the planner's layout menu (plan.cpp, menu_layout).
@@ -307,10 +312,10 @@ __device__ __forceinline__ C2* dense_tile(C2* tile) {
 
 // Tensor coordinates of the tile at global index base (outer dimensions from
 // its bits, tile dimensions 0).
-__device__ __forceinline__ void tile_coords(const PassArgs& A, uint64_t base, int32_t* c) {
+__device__ __forceinline__ void tile_coords(const PassTma& M, uint64_t base, int32_t* c) {
 #pragma unroll
   for (int d = 0; d < 5; ++d)
-    c[d] = (d < A.tdims && !(A.ttile >> d & 1)) ? int32_t(base >> A.tbit[d] & ((1ull << A.tlen[d]) - 1)) : 0;
+    c[d] = (d < M.tdims && !(M.ttile >> d & 1)) ? int32_t(base >> M.tbit[d] & ((1ull << M.tlen[d]) - 1)) : 0;
 }
 
 // Per-round thread geometry: the padded shared-memory slot of the thread's
@@ -833,7 +838,8 @@ template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t... R
 __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tile, int* tconst,
                                          const typename Cx<Real>::T* phase, double* wacc,
-                                         uint32_t* tcount = nullptr, unsigned long long* ext_s = nullptr) {
+                                         uint32_t* tcount = nullptr, unsigned long long* ext_s = nullptr,
+                                         const PassTma* M = nullptr) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -859,12 +865,12 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         // accelerator; no load-store unit instructions)
         // (pfdist tiles ahead; the CTA's first tile also issues the nearer ones)
         if (tid == 0) {
-          for (int k = unit == blockIdx.x ? 1 : A.pfdist; k <= A.pfdist; ++k) {
+          for (int k = unit == blockIdx.x ? 1 : M->pfdist; k <= M->pfdist; ++k) {
             const uint64_t next = unit + uint64_t(k) * gridDim.x;
             if (next >= P.n_units) break;
             int32_t c[5];
-            tile_coords(A, P.outer_runs.scatter(next), c);
-            tma_prefetch_l2(&A.tmap, A.tdims, c);
+            tile_coords(*M, P.outer_runs.scatter(next), c);
+            tma_prefetch_l2(&M->tmap, M->tdims, c);
           }
         }
       } else if (load0 && A.prefetch == 1 && sp.ninner == 0) {
@@ -961,8 +967,8 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         __syncthreads();  // the dense box is complete (each writer fenced its writes)
         if (tid == 0) {
           int32_t c[5];
-          tile_coords(A, gbase, c);
-          tma_store_box(&A.smap, A.tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tile)));
+          tile_coords(*M, gbase, c);
+          tma_store_box(&M->smap, M->tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tile)));
         }
       }
       if (CC && A.bsum && red_last) {
@@ -987,7 +993,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
 // Body of the forward pass kernels. Shared-memory layout of the dynamic buffer:
 //   tile[padded 2^T] complex | tile consts (two buffers) | phase table
 template <typename Real, int R, int WB, bool FAST, bool CC, uint32_t... RS>
-__device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& A) {
+__device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& A, const PassTma& M) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -1016,7 +1022,7 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
 
   uint32_t tcount = 0;
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount, ext_s);
+    fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount, ext_s, &M);
   if (A.tma_store && tid == 0) bulk_wait_all();  // the last tensor store is complete before the CTA ends
 
   if (CC && A.ext_keys) {
@@ -1039,8 +1045,8 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
 template <typename Real, int R, int WB, bool FAST, bool CC>
 __global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? (R + WB <= 7 ? 4 : R + WB <= 8 ? 2 : 1)
                                                               : (R + WB <= 7 ? 2 : 1))
-fwd_pass_kernel(const __grid_constant__ PassDev P, const __grid_constant__ PassArgs A) {
-  fwd_pass_body<Real, R, WB, FAST, CC>(P, A);
+fwd_pass_kernel(const __grid_constant__ PassDev P, const PassArgs A, const __grid_constant__ PassTma M) {
+  fwd_pass_body<Real, R, WB, FAST, CC>(P, A, M);
 }
 
 // Specialised complex64 forward pass for one round-signature sequence RS
@@ -1048,8 +1054,8 @@ fwd_pass_kernel(const __grid_constant__ PassDev P, const __grid_constant__ PassA
 // and masks are compile-time constants.
 template <int R, int WB, bool FAST, uint32_t... RS>
 __global__ void __launch_bounds__(32 << WB, R + WB <= 7 ? 4 : R + WB <= 8 ? 2 : 1)
-fwd_spec_kernel(const __grid_constant__ PassDev P, const __grid_constant__ PassArgs A) {
-  fwd_pass_body<float, R, WB, FAST, sigs_need_c<RS...>(), RS...>(P, A);
+fwd_spec_kernel(const __grid_constant__ PassDev P, const PassArgs A, const __grid_constant__ PassTma M) {
+  fwd_pass_body<float, R, WB, FAST, sigs_need_c<RS...>(), RS...>(P, A, M);
 }
 
 }  // namespace qaoa

@@ -11,7 +11,7 @@
 
 namespace qaoa {
 
-using FwdPassKernel = void (*)(PassDev, PassArgs);
+using FwdPassKernel = void (*)(PassDev, PassArgs, PassTma);
 using AdjPassKernel = void (*)(PassDev, AdjArgs);
 
 // Round signature (plan.h, round_sig) of a round descriptor.
