@@ -60,6 +60,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -246,11 +247,22 @@ def grad_ratio(args, stream, reps: int = 3):
         s.set_opts(dict(grad_checkpoint=False))
         t_grad2, r2 = timed(bwd)
         s.set_opts(dict())
-        return {"workload": f"K_{gn} complex64, p={gp}, dgamma={GRAD_DGAMMA}, dbeta={GRAD_DBETA}",
-                "forward_ms": t_fwd, "grad_ms": t_grad, "ratio": t_grad / t_fwd,
-                "grad_ms_two_vectors": t_grad2, "ratio_two_vectors": t_grad2 / t_fwd,
-                "two_vectors_rel_diff": abs(r2["d_dgamma"] - r["d_dgamma"]) / max(1e-30, abs(r["d_dgamma"])),
-                "exp_c": r["exp_c"], "d_dgamma": r["d_dgamma"], "d_dbeta": r["d_dbeta"]}
+    # the same ratios counted in state sweeps (one read or write of 2^n
+    # amplitudes) of the plan's P passes: the forward moves 2P - 1 (its first
+    # pass only writes); the adjoint with stored states 3P - 2 (read psi and
+    # lambda, write lambda; the first reads psi only, the last writes
+    # nothing), with two vectors 4P - 3 (psi written back as well)
+    from paper_2604_26423_b300.qaoa import describe_plan
+    npass = int(re.search(r"passes=(\d+)", describe_plan(gn, gp, "c64")).group(1))
+    sw_f, sw_c, sw_2 = 2 * npass - 1, 3 * npass - 2, 4 * npass - 3
+    return {"workload": f"K_{gn} complex64, p={gp}, dgamma={GRAD_DGAMMA}, dbeta={GRAD_DBETA}",
+            "forward_ms": t_fwd, "grad_ms": t_grad, "ratio": t_grad / t_fwd,
+            "grad_ms_two_vectors": t_grad2, "ratio_two_vectors": t_grad2 / t_fwd,
+            "sweeps": {"passes": npass, "forward": sw_f, "adjoint": sw_c, "adjoint_two_vectors": sw_2,
+                       "ratio_bound": round(1 + sw_c / sw_f, 3),
+                       "ratio_two_vectors_bound": round(1 + sw_2 / sw_f, 3)},
+            "two_vectors_rel_diff": abs(r2["d_dgamma"] - r["d_dgamma"]) / max(1e-30, abs(r["d_dgamma"])),
+            "exp_c": r["exp_c"], "d_dgamma": r["d_dgamma"], "d_dbeta": r["d_dbeta"]}
 
 
 def _l2_dev(a, b, chunk=1 << 27):
@@ -272,7 +284,8 @@ def config_bench(args, stream):
       streamed cut values, and K_32 complex64 against it: the stated error of
       the precision path where the oracle cannot run (state L2, |r64 - r128|);
     * K_33 complex64 with the streamed int32 cost diagonal;
-    * K_34 complex64 (128 GiB), p = 3."""
+    * K_34 complex64 (128 GiB), p = 3;
+    * sparse graphs: random 3-regular on 32 vertices, a chain on 33."""
     import torch
     from paper_2604_26423_b300 import inputs
     from paper_2604_26423_b300.qaoa import Simulator
@@ -333,6 +346,14 @@ def config_bench(args, stream):
         ms, r = timed(s, P)
         out["runs"].append(row(34, "c64", "recompute", P, ms, r))
     torch.cuda.empty_cache()
+    # sparse instances at large n: a random 3-regular graph (48 edges) and a
+    # chain (32 edges) on 32 and 33 vertices
+    for n, kind, make in ((32, "regular3", inputs.regular3_graph), (33, "chain", inputs.chain_graph)):
+        u, v, w = make(n, SEED)
+        with Simulator(n, u, v, w, SCALE, "c64") as s:
+            ms, r = timed(s, P)
+            out["runs"].append(row(n, "c64", "recompute", P, ms, r, graph=kind, edges=len(u)))
+        torch.cuda.empty_cache()
     return out
 
 

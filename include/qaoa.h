@@ -159,6 +159,11 @@ typedef struct qaoa_opts {
   int grad_order;      /* QAOA_ORDER_* of qaoa_grad's plans (QAOA_GRAD_ORDER) */
   int grad_checkpoint; /* QAOA_ON / QAOA_OFF: stored forward states in qaoa_grad
                           (QAOA_GRAD_CHECKPOINT) */
+  int adj_l2_prefetch; /* QAOA_ON / QAOA_OFF: qaoa_grad's adjoint passes prefetch the next
+                          tile of both vectors into L2 (QAOA_ADJ_L2_PREFETCH) */
+  int tma_load;        /* QAOA_ON / QAOA_OFF: complex64 passes with a tensor prefetch load
+                          each tile into shared memory by one tensor load issued during the
+                          previous tile's last round (QAOA_TMA_LOAD) */
 } qaoa_opts;
 
 /* Sets the context's configuration (copied); later runs are planned with it.

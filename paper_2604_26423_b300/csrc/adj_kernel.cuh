@@ -32,6 +32,8 @@ struct AdjArgs {
   const int32_t* ctabs;   // per-round cost tables
   double* partial;        // per-CTA [dA, dC, dB, <C> (first pass)] partial sums
   int phase_in_smem;
+  int prefetch;           // 2: the CTA's next tile of psi (PassTma.tmap) and lambda
+                          // (PassTma.smap) into L2 by tensor prefetches; 0: none
 };
 
 // Sum over the round's register pairs along bit i of Im(conj(l_a) v_b + conj(l_b) v_a).
@@ -338,7 +340,7 @@ template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t... R
 __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, int* tconst,
                                          const typename Cx<Real>::T* phase, double& gA, double& gC, double& gB,
-                                         double& gE, uint32_t* tcount = nullptr) {
+                                         double& gE, uint32_t* tcount = nullptr, const PassTma* M = nullptr) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -362,6 +364,17 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
       bool load0;
       if constexpr (kSpec) load0 = (first_sig<RS...>() >> 2 & 3u) == SRC_GLOBAL_D;
       else load0 = sp.rd[0].src == SRC_GLOBAL_D;
+      if (load0 && A.prefetch == 2 && sp.ninner == 0 && tid == 0) {
+        // the CTA's next tile of both vectors into L2 by tensor prefetches
+        // (tensor memory accelerator; no load-store unit instructions)
+        const uint64_t next = unit + gridDim.x;
+        if (next < P.n_units) {
+          int32_t c[5];
+          tile_coords(*M, P.outer_runs.scatter(next), c);
+          tma_prefetch_l2(&M->tmap, M->tdims, c);
+          if (!(CC && sp.rd[0].lam)) tma_prefetch_l2(&M->smap, M->tdims, c);
+        }
+      }
       if (load0 && !pf.on) {
         const RoundGeo<R, WB, sizeof(C2)> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
         gray_ptr_walk<R>(reinterpret_cast<const C2*>(A.psi), g0.gb, g0.gstr,
@@ -431,7 +444,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
 // Body of the adjoint pass kernels.
 // Shared memory: psi tile (padded 2^T) | lambda tile | tile consts (two buffers) | phase table
 template <typename Real, int R, int WB, bool FAST, bool CC, uint32_t... RS>
-__device__ __forceinline__ void adj_pass_body(const PassDev& P, const AdjArgs& A) {
+__device__ __forceinline__ void adj_pass_body(const PassDev& P, const AdjArgs& A, const PassTma& M) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -462,7 +475,7 @@ __device__ __forceinline__ void adj_pass_body(const PassDev& P, const AdjArgs& A
     }
   }
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    adj_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE, &tcount);
+    adj_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE, &tcount, &M);
 
   __shared__ double red[4][32];
   for (int o = 16; o > 0; o >>= 1) {
@@ -486,16 +499,16 @@ __device__ __forceinline__ void adj_pass_body(const PassDev& P, const AdjArgs& A
 // Generic adjoint pass: rounds decoded from the descriptor at run time.
 template <typename Real, int R, int WB, bool FAST, bool CC>
 __global__ void __launch_bounds__(32 << WB, sizeof(Real) == 4 ? 2 : 1)
-adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
-  adj_pass_body<Real, R, WB, FAST, CC>(P, A);
+adj_pass_kernel(const __grid_constant__ PassDev P, const AdjArgs A, const __grid_constant__ PassTma M) {
+  adj_pass_body<Real, R, WB, FAST, CC>(P, A, M);
 }
 
 // Specialised complex64 adjoint pass for one round-signature sequence RS (one
 // sub-pass of one tile per super-tile).
 template <int R, int WB, bool FAST, uint32_t... RS>
 __global__ void __launch_bounds__(32 << WB, 2)
-adj_spec_kernel(const __grid_constant__ PassDev P, const AdjArgs A) {
-  adj_pass_body<float, R, WB, FAST, sigs_need_c<RS...>(), RS...>(P, A);
+adj_spec_kernel(const __grid_constant__ PassDev P, const AdjArgs A, const __grid_constant__ PassTma M) {
+  adj_pass_body<float, R, WB, FAST, sigs_need_c<RS...>(), RS...>(P, A, M);
 }
 
 }  // namespace qaoa

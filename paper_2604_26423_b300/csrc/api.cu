@@ -49,6 +49,7 @@ constexpr int kMinUnitsLog2 = 9;         // keep >= 512 super-tiles when n allow
 constexpr long long kMaxAbsWeightSum = 1 << 20;
 constexpr long long kMaxAbsWeightSumTurns = (1ll << 30) - 1;
 constexpr int kMaxGrid = 4096;           // persistent grid cap (partial-sum buffer size)
+constexpr size_t kErrWordOffset = 32;    // the kernels' error word in the 64-byte result buffer
 constexpr int kFuseSumsMinQubits = 26;   // final pass writes sampling block sums from here on
 constexpr int kGroupOrder = ORDER_LOW_LAST;  // default group order of the pass plans
 constexpr int kFloatLanes = PLAN_FLOAT_LANES;  // default: lane bits float to a plain pass
@@ -420,6 +421,14 @@ bool spec_enabled(const qaoa_ctx* c) { return on_off(c->opts.specialised, "QAOA_
 
 // Asynchronous tile copies in the adjoint passes (QAOA_ADJ_PREFETCH=1 enables;
 // measured slower than the register loads with the specialised kernels).
+// Tensor loads of whole tiles into shared memory in the forward passes that
+// have a tensor prefetch (option tma_load, QAOA_TMA_LOAD)
+bool tma_load_on(const qaoa_ctx* c) { return on_off(c->opts.tma_load, "QAOA_TMA_LOAD", 1) != 0; }
+
+// Tensor L2 prefetch of the adjoint's next tile (option adj_l2_prefetch,
+// QAOA_ADJ_L2_PREFETCH)
+bool adj_l2_prefetch(const qaoa_ctx* c) { return on_off(c->opts.adj_l2_prefetch, "QAOA_ADJ_L2_PREFETCH", 0) != 0; }
+
 bool adj_prefetch() {
   const char* e = getenv("QAOA_ADJ_PREFETCH");
   return e && strcmp(e, "1") == 0;
@@ -564,6 +573,20 @@ TensorMapEncodeFn tensor_map_encoder() {
     return reinterpret_cast<TensorMapEncodeFn>(f);
   }();
   return fn;
+}
+
+// Whether a pass has the form the tensor tile loads need: one sub-pass of one
+// tile per super-tile, at least two rounds, the first loading the state, the
+// last reading shared memory and writing the state, none other writing it.
+bool tma_load_form(const PassDev& pd) {
+  if (pd.nsub != 1 || pd.sub[0].ninner != 0) return false;
+  const SubDev& sd = pd.sub[0];
+  const int nr = sd.nrounds;
+  if (nr < 2 || sd.rd[0].src != SRC_GLOBAL_D || sd.rd[nr - 1].src != SRC_SMEM_D || sd.rd[nr - 1].dst != DST_GLOBAL_D)
+    return false;
+  for (int r = 0; r + 1 < nr; ++r)
+    if (sd.rd[r].dst != DST_SMEM_D || (r > 0 && sd.rd[r].src != SRC_SMEM_D)) return false;
+  return true;
 }
 
 bool prefetch_tensor_map(int n, const PassDev& pd, const void* base, PassTma& pt, CUtensorMap* map) {
@@ -718,13 +741,15 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       memset(&pt, 0, sizeof pt);
       {
         const char* d = getenv("QAOA_PREFETCH_DIST");
-        pt.pfdist = d ? std::max(1, std::min(4, atoi(d))) : 1;
+        pt.pfdist = d ? std::max(0, std::min(4, atoi(d))) : 1;
       }
       if (pa.prefetch && !pp.init && prefetch_tensor_map(n, pd, pa.state, pt, &pt.tmap)) pa.prefetch = 2;
       // tensor stores of each tile from shared memory (complex64, one tile
       // per super-tile): option tma_store, QAOA_TMA_STORE
       pa.tma_store = 0;
-      if (c->prec == QAOA_C64 && on_off(0, "QAOA_TMA_STORE", 0) && pd.nsub == 1 && pd.sub[0].ninner == 0) {
+      const char* ts = getenv("QAOA_TMA_STORE");  // 1: every eligible pass, 2: the write-only first pass
+      const int tsm = ts ? atoi(ts) : 0;
+      if (c->prec == QAOA_C64 && (tsm == 1 || (tsm == 2 && pp.init)) && pd.nsub == 1 && pd.sub[0].ninner == 0) {
         PassTma probe = pt;
         if (prefetch_tensor_map(n, pd, pa.out, probe, &pt.smap) &&
             (pa.prefetch != 2 || (probe.tdims == pt.tdims && probe.ttile == pt.ttile))) {
@@ -734,7 +759,14 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
           pa.tma_store = 1;
         }
       }
+      // tensor loads of each tile into shared memory (complex64, one tile per
+      // super-tile, the first round loads the state and only the last round,
+      // which reads shared memory, writes it): QAOA_TMA_LOAD
+      pa.tma_load = 0;
+      if (c->prec == QAOA_C64 && pa.prefetch == 2 && !pa.tma_store && tma_load_on(c) && tma_load_form(pd))
+        pa.tma_load = 1;
     }
+    pa.err = (unsigned long long*)((char*)c->d_result.p + kErrWordOffset);
     // the first pass visits every index once: the extremes come with it when
     // they are not known yet
     pa.ext_keys = nullptr;
@@ -833,10 +865,10 @@ int adj_blocks_per_sm_rw(qaoa_ctx* c, size_t smem, int* nb) {
 }
 
 template <typename Real, bool FAST, bool CC, int R, int WB>
-int launch_adj_rw(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid) {
+int launch_adj_rw(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, const PassTma& pt, size_t smem, int grid) {
   auto kern = adj_pass_kernel<Real, R, WB, FAST, CC>;
   CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<grid, 32 << WB, smem, c->stream>>>(pd, aa);
+  kern<<<grid, 32 << WB, smem, c->stream>>>(pd, aa, pt);
   if (c->prof_on) ++c->nlaunch;
   CUDA_TRY(c, cudaGetLastError());
   return QAOA_OK;
@@ -848,22 +880,22 @@ int adj_blocks_per_sm(qaoa_ctx* c, size_t smem, int* nb) {
 }
 
 template <typename Real, bool FAST, bool CC>
-int launch_adj(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid) {
-  return launch_adj_rw<Real, FAST, CC, kRAdj, kWBAdj>(c, pd, aa, smem, grid);
+int launch_adj(qaoa_ctx* c, const PassDev& pd, const AdjArgs& aa, const PassTma& pt, size_t smem, int grid) {
+  return launch_adj_rw<Real, FAST, CC, kRAdj, kWBAdj>(c, pd, aa, pt, smem, grid);
 }
 
 // Adjoint instantiation for (precision, mixer form, C(x) code): occupancy query
 // when `launch` is false, else the launch. Plain inverse-mixer passes run the
 // instantiation without the C(x) code.
 template <typename Real>
-int adj_any(qaoa_ctx* c, bool fast, bool cc, bool launch, const PassDev& pd, const AdjArgs& aa, size_t smem, int grid,
-            int* bps) {
+int adj_any(qaoa_ctx* c, bool fast, bool cc, bool launch, const PassDev& pd, const AdjArgs& aa, const PassTma& pt,
+            size_t smem, int grid, int* bps) {
   if (fast) {
-    if (cc) return launch ? launch_adj<Real, true, true>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, true, true>(c, smem, bps);
-    return launch ? launch_adj<Real, true, false>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, true, false>(c, smem, bps);
+    if (cc) return launch ? launch_adj<Real, true, true>(c, pd, aa, pt, smem, grid) : adj_blocks_per_sm<Real, true, true>(c, smem, bps);
+    return launch ? launch_adj<Real, true, false>(c, pd, aa, pt, smem, grid) : adj_blocks_per_sm<Real, true, false>(c, smem, bps);
   }
-  if (cc) return launch ? launch_adj<Real, false, true>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, false, true>(c, smem, bps);
-  return launch ? launch_adj<Real, false, false>(c, pd, aa, smem, grid) : adj_blocks_per_sm<Real, false, false>(c, smem, bps);
+  if (cc) return launch ? launch_adj<Real, false, true>(c, pd, aa, pt, smem, grid) : adj_blocks_per_sm<Real, false, true>(c, smem, bps);
+  return launch ? launch_adj<Real, false, false>(c, pd, aa, pt, smem, grid) : adj_blocks_per_sm<Real, false, false>(c, smem, bps);
 }
 
 void* lambda_ptr(qaoa_ctx* c) {
@@ -1045,6 +1077,14 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     aa.ctabs = (const int32_t*)c->d_ctabs.p;
     aa.partial = (double*)c->d_partial.p;
     aa.phase_in_smem = tab_smem ? 1 : 0;
+    // the next tile of both vectors into L2 by tensor prefetches (complex64,
+    // one tile per super-tile, no shared-memory tile copies)
+    PassTma pt;
+    memset(&pt, 0, sizeof pt);
+    aa.prefetch = 0;
+    if (c->prec == QAOA_C64 && pd.sub[0].cgtab < 0 && adj_l2_prefetch(c) &&
+        prefetch_tensor_map(n, pd, aa.psi, pt, &pt.tmap) && prefetch_tensor_map(n, pd, aa.lam, pt, &pt.smap))
+      aa.prefetch = 2;
     int bps = 0;
     bool cc = false;
     for (const SubPassPlan& sp : pp.subs) cc = cc || sp.needs_c || sp.linit;
@@ -1057,8 +1097,8 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
       CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)spec, 32 << kWBAdj, smem));
       if (bps < 1) return c->set_err(QAOA_ECUDA, "adjoint kernel does not fit on an SM (smem %zu)", smem);
     } else {
-      rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, false, pd, aa, smem, 0, &bps)
-                                : adj_any<float>(c, fast, cc, false, pd, aa, smem, 0, &bps);
+      rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, false, pd, aa, pt, smem, 0, &bps)
+                                : adj_any<float>(c, fast, cc, false, pd, aa, pt, smem, 0, &bps);
       if (rc) return rc;
     }
     const long long want = std::min<long long>((long long)bps * c->sms, kMaxGrid);
@@ -1073,13 +1113,13 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
         for (const SubPassPlan& sp : pp.subs) bytes += sp.needs_c ? 4.0 * N : 0.0;
       ProfScope ps(c, 1, bytes);
       if (spec) {
-        spec<<<grid, 32 << kWBAdj, smem, c->stream>>>(pd, aa);
+        spec<<<grid, 32 << kWBAdj, smem, c->stream>>>(pd, aa, pt);
         if (c->prof_on) ++c->nlaunch;
         const cudaError_t le = cudaGetLastError();
         rc = le == cudaSuccess ? QAOA_OK : c->set_err(QAOA_ECUDA, "specialised adjoint kernel: %s", cudaGetErrorString(le));
       } else {
-        rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, true, pd, aa, smem, grid, nullptr)
-                                  : adj_any<float>(c, fast, cc, true, pd, aa, smem, grid, nullptr);
+        rc = c->prec == QAOA_C128 ? adj_any<double>(c, fast, cc, true, pd, aa, pt, smem, grid, nullptr)
+                                  : adj_any<float>(c, fast, cc, true, pd, aa, pt, smem, grid, nullptr);
       }
     }
     if (rc) return rc;
@@ -1230,7 +1270,7 @@ int qaoa_set_opts(qaoa_ctx* c, const qaoa_opts* o) {
     return c->set_err(QAOA_EINVAL, "super_tile outside 12..20");
   if (!order(o->group_order) || !order(o->grad_order)) return c->set_err(QAOA_EINVAL, "bad group order");
   if (!onoff(o->float_lanes) || !onoff(o->specialised) || !onoff(o->tile_tables) || !onoff(o->l2_prefetch) ||
-      !onoff(o->grad_checkpoint))
+      !onoff(o->grad_checkpoint) || !onoff(o->adj_l2_prefetch) || !onoff(o->tma_load))
     return c->set_err(QAOA_EINVAL, "on/off fields take 0, QAOA_ON or QAOA_OFF");
   cudaStreamSynchronize(c->stream);  // queued work may still read the old plans' tables
   c->opts = *o;
@@ -1253,6 +1293,8 @@ int qaoa_get_opts(const qaoa_ctx* c, qaoa_opts* o) {
   r.l2_prefetch = l2_prefetch_on(c, sid) ? QAOA_ON : QAOA_OFF;
   r.grad_order = grad_base_order(c) == ORDER_LOW_MIDDLE ? QAOA_ORDER_LOW_MIDDLE : QAOA_ORDER_LOW_LAST;
   r.grad_checkpoint = grad_checkpoint(c) ? QAOA_ON : QAOA_OFF;
+  r.adj_l2_prefetch = adj_l2_prefetch(c) ? QAOA_ON : QAOA_OFF;
+  r.tma_load = tma_load_on(c) ? QAOA_ON : QAOA_OFF;
   *o = r;
   return QAOA_OK;
 }
@@ -1330,6 +1372,10 @@ int qaoa_init_graph(qaoa_ctx** out, int n, int m, const int32_t* u, const int32_
     qaoa_free(c.release());
     return fail(QAOA_ENOMEM, "cudaMalloc failed");
   }
+  if (cudaMemsetAsync(c->d_result.p, 0, 64, c->stream) != cudaSuccess) {  // results and the error word
+    qaoa_free(c.release());
+    return fail(QAOA_ECUDA, "memset failed");
+  }
   if (cudaMemcpyAsync(c->d_wmat.p, c->wmat.data(), sizeof(int32_t) * n * n, cudaMemcpyHostToDevice, c->stream) !=
       cudaSuccess) {
     qaoa_free(c.release());
@@ -1401,9 +1447,16 @@ int qaoa_expect(qaoa_ctx* c, double* exp_c, double* r, double* norm, int64_t* c_
   if (argmax) *argmax = c->ext.amax;
   if (!exp_c && !r && !norm) return QAOA_OK;
   if (!c->have_result) return c->set_err(QAOA_ESTATE, "no run yet");
-  double res[2];
+  // [norm, <C>, -, -, error word]
+  double res[5];
   CUDA_TRY(c, cudaMemcpyAsync(res, c->d_result.p, sizeof res, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  uint64_t err;
+  memcpy(&err, &res[kErrWordOffset / 8], 8);
+  if (err) {
+    CUDA_TRY(c, cudaMemsetAsync((char*)c->d_result.p + kErrWordOffset, 0, 8, c->stream));
+    return c->set_err(QAOA_ETIMEOUT, "a bounded wait for a tensor tile load gave up in a forward pass");
+  }
   if (norm) *norm = res[0];
   if (exp_c) *exp_c = res[1];
   if (r) {

@@ -363,6 +363,8 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     A.l2hint = 0;
     A.prefetch = 0;
     A.tma_store = 0;
+    A.tma_load = 0;
+    A.err = nullptr;
     A.ext_keys = nullptr;
     constexpr int TILE = padded_size<8>(FR + 5 + kBatchWB);
     float2* tile = reinterpret_cast<float2*>(smem);
@@ -390,6 +392,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     A.ctabs = I.ctabs;
     A.partial = nullptr;
     A.phase_in_smem = 0;
+    A.prefetch = 0;
     constexpr int TILE = padded_size<8>(kBatchRAdj + 5 + kBatchWBAdj);
     float2* tv = reinterpret_cast<float2*>(smem);
     float2* tl = tv + TILE;

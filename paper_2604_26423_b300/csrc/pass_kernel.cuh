@@ -49,6 +49,11 @@ struct PassArgs {
                           // tensor prefetch of the whole tile (tmap) from one thread
   int tma_store;          // the final round writes the tile densely into shared memory
                           // and one thread stores it with a tensor store (PassTma)
+  int tma_load;           // complex64, one tile per super-tile: the CTA's next tile is
+                          // loaded into shared memory by one tensor load (PassTma.tmap)
+                          // once every thread has read the current tile's last round,
+                          // and the first round reads it from there
+  unsigned long long* err;  // error word: bit 0 set when a tensor-load wait gave up
   // exhaustive extremes in the |+> round (every index visited once): packed
   // keys [(C - c_lo) << 34 | x, (c_hi - C) << 34 | x], each the minimum over
   // all x (smallest C, resp. largest C, then smallest index); must hold ~0 on
@@ -67,7 +72,8 @@ struct PassTma {
   CUtensorMap tmap;  // 128-byte aligned by its type
   CUtensorMap smap;
   int tdims;
-  int pfdist;        // prefetch distance in the CTA's tiles (1..4)
+  int pfdist;        // prefetch distance in the CTA's tiles (1..4; 0: no L2 prefetches,
+                     // the map serving the tensor tile loads only)
   int8_t tbit[5], tlen[5];
   uint8_t ttile;
 };
@@ -302,6 +308,104 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // Makes this thread's shared-memory writes visible to the tensor engine.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Tensor loads of whole tiles into shared memory, completed on a shared-memory
+// mbarrier (transaction bytes), and the named barrier that frees the tile
+// buffer for them.
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for phase `parity` of the mbarrier, at most limit_ns: false when it
+// gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = timer_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (timer_ns() - t0 > limit_ns) return false;
+  return true;
+}
+// Tensor load of one box (coordinates c, innermost first) into shared memory
+// at smem (128-byte aligned); its bytes complete the mbarrier's transaction.
+__device__ __forceinline__ void tma_load_box(const CUtensorMap* tmap, int dims, const int32_t* c, uint32_t smem,
+                                             uint32_t bar) {
+  const uint64_t t = reinterpret_cast<uint64_t>(tmap);
+  switch (dims) {
+    case 1:
+      asm volatile(
+          "cp.async.bulk.tensor.1d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];" ::"r"(
+              smem),
+          "l"(t), "r"(c[0]), "r"(bar)
+          : "memory");
+      break;
+    case 2:
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+          "[%4];" ::"r"(smem),
+          "l"(t), "r"(c[0]), "r"(c[1]), "r"(bar)
+          : "memory");
+      break;
+    case 3:
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+          "[%5];" ::"r"(smem),
+          "l"(t), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(bar)
+          : "memory");
+      break;
+    case 4:
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+          "%5}], [%6];" ::"r"(smem),
+          "l"(t), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(bar)
+          : "memory");
+      break;
+    default:
+      asm volatile(
+          "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+          "%5, %6}], [%7];" ::"r"(smem),
+          "l"(t), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(bar)
+          : "memory");
+      break;
+  }
+}
+// Named barrier 1 over nthreads threads: sync waits for all of them, arrive
+// only signals (the warps that do not consume the barrier).
+__device__ __forceinline__ void named_bar_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int nthreads) {
+  asm volatile("bar.arrive 1, %0;" ::"r"(nthreads) : "memory");
+}
+// Limit of one wait for a tensor tile load (ns). A wait that gives up sets
+// the error word and the CTA's stop flag (the word after the mbarrier): the
+// CTA then issues no further tensor loads and waits for none, so the pass
+// ends promptly with an invalid output.
+constexpr unsigned long long kTmaWaitNs = 2000000000ull;
+__device__ __forceinline__ bool tma_stopped(uint32_t tbar) {
+  uint32_t f;
+  asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(f) : "r"(tbar + 8) : "memory");
+  return f != 0;
+}
+__device__ __forceinline__ void tma_stop(uint32_t tbar) {
+  asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(tbar + 8), "r"(1u) : "memory");
+}
+
 // Dense (unpadded) view of a tile's shared memory, 128-byte aligned: the box
 // of a tensor store. The padded tile is at least 127 bytes larger than the
 // dense one for every shape, so the view fits inside it.
@@ -511,12 +615,19 @@ constexpr bool sigs_need_c() {
 }
 template <uint32_t S0, uint32_t... RS>
 constexpr uint32_t first_sig() { return S0; }
+// The first signature, 0 for an empty sequence (generic kernels).
+template <uint32_t... RS>
+constexpr uint32_t first_sig_or0() {
+  if constexpr (sizeof...(RS) == 0) return 0u;
+  else return first_sig<RS...>();
+}
 
 template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t SIG = 0>
 __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, const SubDev& sp, const RoundDev& rd,
                                           typename Cx<Real>::T* tile, uint64_t gbase, int gpar, const int* tconst,
                                           const typename Cx<Real>::T* phase, int lane, int warp, double* wacc,
-                                          typename Cx<Real>::T* v, unsigned long long* ext_s) {
+                                          typename Cx<Real>::T* v, unsigned long long* ext_s,
+                                          const PassTma* M = nullptr, uint32_t tbar = 0, uint64_t tnext = ~0ull) {
   using C2 = typename Cx<Real>::T;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
@@ -545,6 +656,25 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     }
   } else if (op.src == SRC_SMEM_D) {
     smem_load<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
+  }
+  if constexpr (AB == 8) {
+    if (A.tma_load && op.dstg && op.src == SRC_SMEM_D) {
+      // every thread has read the tile's last round: the buffer takes the
+      // CTA's next tile by one tensor load; warp 0 waits for the others,
+      // which only signal and go on
+      if (warp == 0) {
+        named_bar_sync(32 << WB);
+        if (lane == 0 && tnext < P.n_units && !tma_stopped(tbar)) {
+          fence_proxy_async_smem();
+          int32_t c[5];
+          tile_coords(*M, P.outer_runs.scatter(tnext), c);
+          mbar_expect_tx(tbar, uint32_t(AB) << (R + 5 + WB));
+          tma_load_box(&M->tmap, M->tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tile)), tbar);
+        }
+      } else {
+        named_bar_arrive(32 << WB);
+      }
+    }
   }
 
   if (CC && init && A.ext_keys && (op.cost || op.reduce)) {
@@ -839,7 +969,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
                                          typename Cx<Real>::T* tile, int* tconst,
                                          const typename Cx<Real>::T* phase, double* wacc,
                                          uint32_t* tcount = nullptr, unsigned long long* ext_s = nullptr,
-                                         const PassTma* M = nullptr) {
+                                         const PassTma* M = nullptr, uint32_t tbar = 0) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -860,7 +990,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       bool load0;
       if constexpr (kSpec) load0 = (first_sig<RS...>() >> 2 & 3u) == SRC_GLOBAL_D;
       else load0 = sp.rd[0].src == SRC_GLOBAL_D;
-      if (load0 && A.prefetch == 2 && sp.ninner == 0) {
+      if (load0 && A.prefetch == 2 && sp.ninner == 0 && M->pfdist > 0) {
         // the CTA's next tile into L2 by one tensor prefetch (tensor memory
         // accelerator; no load-store unit instructions)
         // (pfdist tiles ahead; the CTA's first tile also issues the nearer ones)
@@ -889,7 +1019,8 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
           }
         }
       }
-      if (load0) {
+      const bool tload = AB == 8 && load0 && A.tma_load;
+      if (load0 && !tload) {
         const RoundGeo<R, WB, AB> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
         const C2* gs = reinterpret_cast<const C2*>(A.state);
         if (A.l2hint) {
@@ -928,6 +1059,48 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         *tcount += 1;
       }
       if (AB == 8 && A.tma_store && tid == 0) bulk_wait_read();  // the previous tile's store has read its box
+      if constexpr (AB == 8) {
+        if (tload) {
+          // this tile arrived by a tensor load (the CTA's k-th, mbarrier
+          // phase k & 1): the first round's amplitudes from the dense box
+          // (tile index order); the barrier below ends the reads before the
+          // first round writes the padded tile
+          const uint32_t k = uint32_t((unit - blockIdx.x) / gridDim.x);
+          if (!tma_stopped(tbar) && !mbar_wait_bounded(tbar, k & 1u, kTmaWaitNs)) {
+            tma_stop(tbar);
+            if (lane == 0) atomicOr(A.err, 1ull);
+          }
+          constexpr uint32_t S0 = first_sig_or0<RS...>();
+          const RoundDev& rd0 = sp.rd[0];
+          const C2* dense = dense_tile(tile);
+          uint32_t tb = 0;
+#pragma unroll
+          for (int i = 0; i < 5; ++i) tb |= uint32_t(lane >> i & 1) << tile_bit<R, WB, S0>(rd0, 1, i);
+#pragma unroll
+          for (int i = 0; i < WB; ++i) tb |= uint32_t(warp >> i & 1) << tile_bit<R, WB, S0>(rd0, 2, i);
+          auto toff = [&](int j) {
+            uint32_t o = 0;
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+              if (j >> i & 1) o |= 1u << tile_bit<R, WB, S0>(rd0, 0, i);
+            return o;
+          };
+          bool paired;
+          if constexpr (kSpec) paired = sig_layout(S0) == 4;
+          else paired = rd0.layout == 4;
+          if (paired) {
+#pragma unroll
+            for (int j = 0; j < (1 << R); j += 2) {
+              const float4 q = *reinterpret_cast<const float4*>(dense + tb + toff(j));
+              v[j] = make_float2(q.x, q.y);
+              v[j | 1] = make_float2(q.z, q.w);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < (1 << R); ++j) v[j] = dense[tb + toff(j)];
+          }
+        }
+      }
       __syncthreads();  // previous tile finished with shared memory
       if (ahead) {
         const uint64_t next = unit + gridDim.x;
@@ -950,7 +1123,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
           constexpr uint32_t S = decltype(sigc)::value;
           if constexpr ((S >> 2 & 3u) == SRC_SMEM_D) __syncthreads();
           fwd_round<Real, R, WB, FAST, CC, S>(P, A, sp, sp.rd[r], tile, gbase, gpar, tc, phase, lane, warp, wacc, v,
-                                              ext_s);
+                                              ext_s, M, tbar, unit + gridDim.x);
           ++r;
         };
         (run(std::integral_constant<uint32_t, RS>{}), ...);
@@ -959,7 +1132,8 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
         for (int r = 0; r < sp.nrounds; ++r) {
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
-          fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, gpar, tc, phase, lane, warp, wacc, v, ext_s);
+          fwd_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tile, gbase, gpar, tc, phase, lane, warp, wacc, v, ext_s, M,
+                                           tbar, unit + gridDim.x);
         }
         red_last = sp.rd[sp.nrounds - 1].reduce != 0;
       }
@@ -1020,9 +1194,26 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
   __shared__ unsigned long long ext_s[2];
   if (tid < 2) ext_s[tid] = ~0ull;  // published by the first tile's barrier
 
+  // tensor tile loads: the mbarrier, and the CTA's first tile
+  __shared__ __align__(8) unsigned long long tma_bar[2];  // mbarrier, stop flag
+  const uint32_t tbar = (uint32_t)__cvta_generic_to_shared(tma_bar);
+  if (AB == 8 && A.tma_load) {
+    if (tid == 0) {
+      tma_bar[1] = 0ull;
+      mbar_init(tbar, 1);
+    }
+    __syncthreads();
+    if (tid == 0 && blockIdx.x < P.n_units) {
+      int32_t c[5];
+      tile_coords(M, P.outer_runs.scatter(blockIdx.x), c);
+      mbar_expect_tx(tbar, uint32_t(AB) << T);
+      tma_load_box(&M.tmap, M.tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tile)), tbar);
+    }
+  }
+
   uint32_t tcount = 0;
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount, ext_s, &M);
+    fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount, ext_s, &M, tbar);
   if (A.tma_store && tid == 0) bulk_wait_all();  // the last tensor store is complete before the CTA ends
 
   if (CC && A.ext_keys) {

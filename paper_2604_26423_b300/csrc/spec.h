@@ -12,7 +12,7 @@
 namespace qaoa {
 
 using FwdPassKernel = void (*)(PassDev, PassArgs, PassTma);
-using AdjPassKernel = void (*)(PassDev, AdjArgs);
+using AdjPassKernel = void (*)(PassDev, AdjArgs, PassTma);
 
 // Round signature (plan.h, round_sig) of a round descriptor.
 uint32_t round_sig_dev(const RoundDev& rd);

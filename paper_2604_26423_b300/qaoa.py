@@ -124,18 +124,21 @@ class Opts(ctypes.Structure):
     """Kernel configuration of one context (``qaoa_opts``; 0 = library default)."""
     _fields_ = [("fwd_shape", ctypes.c_int), ("super_tile", ctypes.c_int), ("group_order", ctypes.c_int),
                 ("float_lanes", ctypes.c_int), ("specialised", ctypes.c_int), ("tile_tables", ctypes.c_int),
-                ("l2_prefetch", ctypes.c_int), ("grad_order", ctypes.c_int), ("grad_checkpoint", ctypes.c_int)]
+                ("l2_prefetch", ctypes.c_int), ("grad_order", ctypes.c_int), ("grad_checkpoint", ctypes.c_int),
+                ("adj_l2_prefetch", ctypes.c_int), ("tma_load", ctypes.c_int)]
 
 
 def make_opts(shape=None, super_tile=None, order=None, float_lanes=None, specialised=None, tile_tables=None,
-              l2_prefetch=None, grad_order=None, grad_checkpoint=None) -> Opts:
+              l2_prefetch=None, grad_order=None, grad_checkpoint=None, adj_l2_prefetch=None,
+              tma_load=None) -> Opts:
     """``Opts`` from readable values: shape "4x3" / "5x4" / ..., order "last" /
     "middle", booleans for the on/off fields; None keeps the default."""
     b = lambda x: 0 if x is None else (ON if x else OFF)  # noqa: E731
     return Opts(fwd_shape=SHAPES[shape] if shape else 0, super_tile=int(super_tile or 0),
                 group_order=ORDERS[order] if order else 0, float_lanes=b(float_lanes), specialised=b(specialised),
                 tile_tables=b(tile_tables), l2_prefetch=b(l2_prefetch),
-                grad_order=ORDERS[grad_order] if grad_order else 0, grad_checkpoint=b(grad_checkpoint))
+                grad_order=ORDERS[grad_order] if grad_order else 0, grad_checkpoint=b(grad_checkpoint),
+                adj_l2_prefetch=b(adj_l2_prefetch), tma_load=b(tma_load))
 
 
 def set_cost_choice(n: int, precision, cost_mode) -> None:

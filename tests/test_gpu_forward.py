@@ -509,3 +509,26 @@ def test_l2_prefetch_bitwise(n, shape):
             outs.append((s.state().cpu().numpy().copy(), s.expect()["exp_c"]))
     (a, ea), (b, eb) = outs
     assert np.array_equal(a.view(np.uint64), b.view(np.uint64)) and ea == eb
+
+
+@pytest.mark.parametrize("n,shape", [(24, "4x3"), (27, "5x4"), (29, "5x4"), (30, "5x4")])
+def test_tma_tile_loads_bitwise(n, shape):
+    # each tile loaded into shared memory by one tensor load (issued during
+    # the previous tile's last round) and read from the dense box by the
+    # first round: the same amplitudes as the global loads, so identical
+    # states, <C> and norm
+    import torch
+    u, v, w = graph("complete", n, 950 + n)
+    ref = None
+    for tl in (True, False):
+        with sim(n, u, v, w, S, "c64", opts=dict(shape=shape, l2_prefetch=True, tma_load=tl)) as s:
+            assert s.get_opts()["tma_load"] == (1 if tl else 2)
+            s.run(3, 0.6, 0.3)
+            e = s.expect()
+            st = s.state().view(torch.int64)
+            if ref is None:
+                ref = (st.clone(), e)
+            else:
+                assert torch.equal(ref[0], st)
+                assert (ref[1]["exp_c"], ref[1]["norm"]) == (e["exp_c"], e["norm"])
+    del ref

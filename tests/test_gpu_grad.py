@@ -239,6 +239,27 @@ def test_adjoint_tile_prefetch_identical(monkeypatch):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("ckpt", [True, False])
+@pytest.mark.parametrize("n,p", [(22, 3), (26, 2)])
+def test_adjoint_l2_prefetch_identical(n, p, ckpt):
+    # tensor prefetches of the next tile of psi and lambda into L2 move no
+    # data into the kernel: bitwise identical gradients and <C>, with stored
+    # forward states and with psi uncomputed
+    from paper_2604_26423_b300 import inputs
+    from paper_2604_26423_b300.qaoa import Simulator
+    u, v, w = inputs.complete_graph(n, 960 + n)
+    res = []
+    for pf in (True, False):
+        with Simulator(n, u, v, w, 0.1, "c64", with_grad=True,
+                       opts=dict(adj_l2_prefetch=pf, grad_checkpoint=ckpt)) as s:
+            assert s.get_opts()["adj_l2_prefetch"] == (1 if pf else 2)
+            res.append(s.grad(p, 0.6, 0.3))
+    a, b = res
+    assert np.array_equal(a["g_gamma"], b["g_gamma"]) and np.array_equal(a["g_beta"], b["g_beta"])
+    assert a["exp_c"] == b["exp_c"]
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("n,p,prec", [(14, 3, "c128"), (21, 1, "c64"), (22, 4, "c64"), (20, 3, "c128"),
                                       (29, 2, "c64")])
 def test_grad_stored_forward_states(n, p, prec, monkeypatch):
