@@ -373,6 +373,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     wacc[2 * tid + 1] = 0.0;
     for (uint32_t u = u0; u < u1; ++u) fwd_unit<float, FR, kBatchWB, FAST>(P, A, u, tile, tconst, phase, wacc);
     if (M.reduce) {
+      finish_thread_sums<float>(wacc, tid);
       __syncthreads();
       double sN, sC;
       reduce_thread_sums<kBatchThreads>(wacc, sN, sC);

@@ -384,18 +384,20 @@ __device__ __forceinline__ void tma_load_box(const CUtensorMap* tmap, int dims, 
       break;
   }
 }
-// Named barrier 1 over nthreads threads: sync waits for all of them, arrive
-// only signals (the warps that do not consume the barrier).
-__device__ __forceinline__ void named_bar_sync(int nthreads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+// Count of the warps that have read the current tile's last round (the word
+// at tbar + 12): returns the count before this warp's increment.
+__device__ __forceinline__ uint32_t tile_read_count_add(uint32_t tbar) {
+  uint32_t prev;
+  asm volatile("atom.shared.add.u32 %0, [%1], 1;" : "=r"(prev) : "r"(tbar + 12) : "memory");
+  return prev;
 }
-__device__ __forceinline__ void named_bar_arrive(int nthreads) {
-  asm volatile("bar.arrive 1, %0;" ::"r"(nthreads) : "memory");
+__device__ __forceinline__ void tile_read_count_reset(uint32_t tbar) {
+  asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(tbar + 12), "r"(0u) : "memory");
 }
 // Limit of one wait for a tensor tile load (ns). A wait that gives up sets
-// the error word and the CTA's stop flag (the word after the mbarrier): the
-// CTA then issues no further tensor loads and waits for none, so the pass
-// ends promptly with an invalid output.
+// the error word and the CTA's stop flag (the word at tbar + 8, after the
+// mbarrier): the CTA then issues no further tensor loads and waits for none,
+// so the pass ends promptly with an invalid output.
 constexpr unsigned long long kTmaWaitNs = 2000000000ull;
 __device__ __forceinline__ bool tma_stopped(uint32_t tbar) {
   uint32_t f;
@@ -563,6 +565,43 @@ __device__ __forceinline__ void smem_store(int layout, C2* tile, uint32_t sbase,
   }
 }
 
+// Double-float accumulation (complex64 reductions): a value is held as the
+// unevaluated sum hi + lo of two floats, and a float is added with Knuth's
+// TwoSum, which yields the rounded sum s and its exact rounding error e
+// (s + e == a + b), so hi keeps the rounded running sum and lo collects the
+// errors. This keeps about 48 bits of the sum on the FP32 pipe: the FP64 pipe
+// issues two operations per SM per clock on this part, which made the final
+// pass's per-tile FP64 sums a sixth of its time.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  e = (a - (s - bp)) + (b - bp);
+}
+__device__ __forceinline__ void df_add(float2& acc, float x) {
+  float s, e;
+  two_sum(acc.x, x, s, e);
+  acc.x = s;
+  acc.y += e;
+}
+__device__ __forceinline__ void df_add(float2& acc, float2 y) {
+  float s, e;
+  two_sum(acc.x, y.x, s, e);
+  acc.x = s;
+  acc.y += e + y.y;
+}
+// complex64: thread tid's [norm, <C>] running sums are double-float pairs in
+// the memory of wacc[2 tid], wacc[2 tid + 1] during the passes; this turns
+// them into the FP64 values reduce_thread_sums reads (each thread its own).
+template <typename Real>
+__device__ __forceinline__ void finish_thread_sums(double* wacc, int tid) {
+  if constexpr (sizeof(Real) == 4) {
+    const float2 a = reinterpret_cast<const float2*>(wacc)[2 * tid];
+    const float2 b = reinterpret_cast<const float2*>(wacc)[2 * tid + 1];
+    wacc[2 * tid] = double(a.x) + double(a.y);
+    wacc[2 * tid + 1] = double(b.x) + double(b.y);
+  }
+}
+
 // CTA total of the per-thread FP64 [norm, <C>] sums in wacc (fixed order: each
 // lane of warp 0 adds a strided set, then a shuffle tree); valid in thread 0.
 // A barrier must precede the call.
@@ -659,20 +698,23 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
   }
   if constexpr (AB == 8) {
     if (A.tma_load && op.dstg && op.src == SRC_SMEM_D) {
-      // every thread has read the tile's last round: the buffer takes the
-      // CTA's next tile by one tensor load; warp 0 waits for the others,
-      // which only signal and go on
-      if (warp == 0) {
-        named_bar_sync(32 << WB);
-        if (lane == 0 && tnext < P.n_units && !tma_stopped(tbar)) {
-          fence_proxy_async_smem();
-          int32_t c[5];
-          tile_coords(*M, P.outer_runs.scatter(tnext), c);
-          mbar_expect_tx(tbar, uint32_t(AB) << (R + 5 + WB));
-          tma_load_box(&M->tmap, M->tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tile)), tbar);
+      // once every warp has read the tile's last round, the buffer takes the
+      // CTA's next tile by one tensor load, issued by the last warp to
+      // finish its reads (no warp waits for the others)
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();  // this warp's reads are performed before its count
+        if (tile_read_count_add(tbar) == (1u << WB) - 1) {
+          __threadfence_block();
+          tile_read_count_reset(tbar);
+          if (tnext < P.n_units && !tma_stopped(tbar)) {
+            fence_proxy_async_smem();
+            int32_t c[5];
+            tile_coords(*M, P.outer_runs.scatter(tnext), c);
+            mbar_expect_tx(tbar, uint32_t(AB) << (R + 5 + WB));
+            tma_load_box(&M->tmap, M->tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tile)), tbar);
+          }
         }
-      } else {
-        named_bar_arrive(32 << WB);
       }
     }
   }
@@ -879,12 +921,18 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
             if (h == k) sb[k] += pr;
         });
         // block sums: each thread's partial over its register amplitudes
-        // (at most 2^R terms in the state precision), then FP64 from there on:
-        // the partials go to shared memory and the caller adds them in FP64
-        // in a fixed order
+        // (at most 2^R terms in the state precision), then FP64 (complex64:
+        // double-float) from there on: the partials go to shared memory and
+        // the caller adds them in a fixed order
         const int tid = (warp << 5) | lane;
+        if constexpr (sizeof(Real) == 4) {
+          float* wf = reinterpret_cast<float*>(wacc + 2 * (32 << WB));
 #pragma unroll
-        for (int k = 0; k < NB; ++k) wacc[(2 + k) * (32 << WB) + tid] = double(sb[k]);
+          for (int k = 0; k < NB; ++k) wf[k * (32 << WB) + tid] = sb[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < NB; ++k) wacc[(2 + k) * (32 << WB) + tid] = double(sb[k]);
+        }
       } else {
         for_costs(P.cpr, [&](int j, int c) {
           const Real pr = v[j].x * v[j].x + v[j].y * v[j].y;
@@ -892,11 +940,17 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
           scc = fma(pr, Real(c), scc);
         });
       }
-      // <C> and norm: this thread's FP64 running sums (one add per tile), the
-      // cross-thread FP64 reduction runs once at the end (reduce_thread_sums)
+      // <C> and norm: this thread's running sums (one add per tile; FP64, or
+      // double-float for complex64), the cross-thread FP64 reduction runs once
+      // at the end (finish_thread_sums, reduce_thread_sums)
       const int tid = (warp << 5) | lane;
-      wacc[2 * tid] += double(sn);
-      wacc[2 * tid + 1] += double(scc);
+      if constexpr (sizeof(Real) == 4) {
+        df_add(reinterpret_cast<float2*>(wacc)[2 * tid], sn);
+        df_add(reinterpret_cast<float2*>(wacc)[2 * tid + 1], scc);
+      } else {
+        wacc[2 * tid] += double(sn);
+        wacc[2 * tid + 1] += double(scc);
+      }
     }
   } else {
     mixer(op.mixB, pick<Real>(P.tauB, P.ftauB), pick<Real>(P.alphaB, P.falphaB));
@@ -969,7 +1023,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
                                          typename Cx<Real>::T* tile, int* tconst,
                                          const typename Cx<Real>::T* phase, double* wacc,
                                          uint32_t* tcount = nullptr, unsigned long long* ext_s = nullptr,
-                                         const PassTma* M = nullptr, uint32_t tbar = 0) {
+                                         const PassTma* M = nullptr, uint32_t tbar = 0, uint32_t* tk = nullptr) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -1065,7 +1119,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
           // phase k & 1): the first round's amplitudes from the dense box
           // (tile index order); the barrier below ends the reads before the
           // first round writes the padded tile
-          const uint32_t k = uint32_t((unit - blockIdx.x) / gridDim.x);
+          const uint32_t k = (*tk)++;
           if (!tma_stopped(tbar) && !mbar_wait_bounded(tbar, k & 1u, kTmaWaitNs)) {
             tma_stop(tbar);
             if (lane == 0) atomicOr(A.err, 1ull);
@@ -1147,16 +1201,31 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       }
       if (CC && A.bsum && red_last) {
         // this tile is 2^T consecutive amplitudes: its 2^(T-12) block sums;
-        // warp k adds block k's per-thread partials in FP64 (each lane a
-        // strided set, then a shuffle tree: a fixed order)
+        // warp k adds block k's per-thread partials (each lane a strided set
+        // in two accumulators, then a shuffle tree: a fixed order), in FP64,
+        // or for complex64 in double-float, converted to FP64 once per block
         constexpr int NB = 1 << kBlkBits<R, WB>;
         __syncthreads();
         if (warp < NB) {
-          double b = 0.0;
-          for (int t = lane; t < NT; t += 32) b += wacc[(2 + warp) * NT + t];
+          if constexpr (sizeof(Real) == 4) {
+            const float* wf = reinterpret_cast<const float*>(wacc + 2 * NT) + warp * NT;
+            float2 b0 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);
+            for (int t = lane; t < NT; t += 64) {
+              df_add(b0, wf[t]);
+              df_add(b1, wf[t + 32]);
+            }
+            df_add(b0, b1);
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-          if (lane == 0) A.bsum[(gbase >> 12) + warp] = b;
+            for (int o = 16; o > 0; o >>= 1)
+              df_add(b0, make_float2(__shfl_xor_sync(0xffffffffu, b0.x, o), __shfl_xor_sync(0xffffffffu, b0.y, o)));
+            if (lane == 0) A.bsum[(gbase >> 12) + warp] = double(b0.x) + double(b0.y);
+          } else {
+            double b = 0.0;
+            for (int t = lane; t < NT; t += 32) b += wacc[(2 + warp) * NT + t];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+            if (lane == 0) A.bsum[(gbase >> 12) + warp] = b;
+          }
         }
       }
     }
@@ -1195,7 +1264,7 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
   if (tid < 2) ext_s[tid] = ~0ull;  // published by the first tile's barrier
 
   // tensor tile loads: the mbarrier, and the CTA's first tile
-  __shared__ __align__(8) unsigned long long tma_bar[2];  // mbarrier, stop flag
+  __shared__ __align__(8) unsigned long long tma_bar[2];  // mbarrier; stop flag, warps' read count
   const uint32_t tbar = (uint32_t)__cvta_generic_to_shared(tma_bar);
   if (AB == 8 && A.tma_load) {
     if (tid == 0) {
@@ -1211,9 +1280,9 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
     }
   }
 
-  uint32_t tcount = 0;
+  uint32_t tcount = 0, tk = 0;
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount, ext_s, &M, tbar);
+    fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount, ext_s, &M, tbar, &tk);
   if (A.tma_store && tid == 0) bulk_wait_all();  // the last tensor store is complete before the CTA ends
 
   if (CC && A.ext_keys) {
@@ -1222,6 +1291,7 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
   }
 
   if (A.partial) {
+    finish_thread_sums<Real>(wacc, tid);
     __syncthreads();
     double sN, sC;
     reduce_thread_sums<NT>(wacc, sN, sC);
