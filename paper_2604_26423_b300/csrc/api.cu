@@ -589,6 +589,16 @@ bool tma_load_form(const PassDev& pd) {
   return true;
 }
 
+// Whether a pass's shared-memory rounds can use dense tile-index slots: one
+// sub-pass of one tile per super-tile and no round whose lanes lie above
+// tile bit 5 (menu layout 2, which needs the padding against bank conflicts).
+bool dense_form(const PassDev& pd) {
+  if (pd.nsub != 1 || pd.sub[0].ninner != 0) return false;
+  for (int r = 0; r < pd.sub[0].nrounds; ++r)
+    if (pd.sub[0].rd[r].layout == 2) return false;
+  return true;
+}
+
 bool prefetch_tensor_map(int n, const PassDev& pd, const void* base, PassTma& pt, CUtensorMap* map) {
   const TensorMapEncodeFn enc = tensor_map_encoder();
   if (!enc || pd.nsub != 1 || pd.sub[0].ninner != 0) return false;
@@ -765,6 +775,12 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       pa.tma_load = 0;
       if (c->prec == QAOA_C64 && pa.prefetch == 2 && !pa.tma_store && tma_load_on(c) && tma_load_form(pd))
         pa.tma_load = 1;
+      // dense shared-memory slots (QAOA_DENSE)
+      pa.dense = 0;
+      if (c->prec == QAOA_C64 && on_off(0, "QAOA_DENSE", 1) && dense_form(pd)) {
+        const RoundDev& r0 = pd.sub[0].rd[0];
+        pa.dense = pa.tma_load && !r0.cost && !r0.reduce && !r0.lam && r0.src == SRC_GLOBAL_D ? 2 : 1;
+      }
     }
     pa.err = (unsigned long long*)((char*)c->d_result.p + kErrWordOffset);
     // the first pass visits every index once: the extremes come with it when

@@ -54,6 +54,10 @@ struct PassArgs {
                           // once every thread has read the current tile's last round,
                           // and the first round reads it from there
   unsigned long long* err;  // error word: bit 0 set when a tensor-load wait gave up
+  int dense;              // complex64, one tile per super-tile, no round in menu layout 2:
+                          // shared-memory rounds use dense tile-index slots (1), and
+                          // with tensor tile loads and a first round without tile
+                          // constants the tile's first barrier is dropped (2)
   // exhaustive extremes in the |+> round (every index visited once): packed
   // keys [(C - c_lo) << 34 | x, (c_hi - C) << 34 | x], each the minimum over
   // all x (smallest C, resp. largest C, then smallest index); must hold ~0 on
@@ -544,6 +548,68 @@ __device__ __forceinline__ void smem_store_l(C2* tile, uint32_t sbase, const C2*
 #pragma unroll
   for (int j = 0; j < (1 << R); ++j) tile[sbase + padi<AB>(Lay<R, WB, L>::toff(j))] = v[j];
 }
+// Dense variant (PassArgs.dense): slots in tile-index order without padding,
+// the tensor box's order, for passes none of whose rounds puts its lanes above
+// tile bit 5 (menu layout 2): with lanes on tile bits 0..3 (8-byte accesses)
+// or 1..3 and register bit 0 on tile bit 0 (16-byte accesses of a pair) every
+// access is bank-conflict free. dense: the 128-byte aligned tile.
+template <int R, int WB, int L>
+__device__ __forceinline__ uint32_t dense_base(int lane, int warp) {
+  uint32_t b = 0;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) b |= uint32_t(lane >> i & 1) << Lay<R, WB, L>::lane(i);
+#pragma unroll
+  for (int i = 0; i < WB; ++i) b |= uint32_t(warp >> i & 1) << Lay<R, WB, L>::warp(i);
+  return b;
+}
+template <int R, int WB, int L>
+__device__ __forceinline__ void smem_load_dense_l(const float2* dense, int lane, int warp, float2* v) {
+  const uint32_t b = dense_base<R, WB, L>(lane, warp);
+  if constexpr (L == 4) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); j += 2) {
+      const float4 q = *reinterpret_cast<const float4*>(dense + b + Lay<R, WB, L>::toff(j));
+      v[j] = make_float2(q.x, q.y);
+      v[j | 1] = make_float2(q.z, q.w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) v[j] = dense[b + Lay<R, WB, L>::toff(j)];
+  }
+}
+template <int R, int WB, int L>
+__device__ __forceinline__ void smem_store_dense_l(float2* dense, int lane, int warp, const float2* v) {
+  const uint32_t b = dense_base<R, WB, L>(lane, warp);
+  if constexpr (L == 4) {
+#pragma unroll
+    for (int j = 0; j < (1 << R); j += 2)
+      *reinterpret_cast<float4*>(dense + b + Lay<R, WB, L>::toff(j)) = make_float4(v[j].x, v[j].y, v[j | 1].x, v[j | 1].y);
+  } else {
+#pragma unroll
+    for (int j = 0; j < (1 << R); ++j) dense[b + Lay<R, WB, L>::toff(j)] = v[j];
+  }
+}
+template <int R, int WB>
+__device__ __forceinline__ void smem_load_dense(int layout, const float2* dense, int lane, int warp, float2* v) {
+  switch (layout) {
+    case 0: smem_load_dense_l<R, WB, 0>(dense, lane, warp, v); break;
+    case 1: smem_load_dense_l<R, WB, 1>(dense, lane, warp, v); break;
+    case 2: smem_load_dense_l<R, WB, 2>(dense, lane, warp, v); break;
+    case 3: smem_load_dense_l<R, WB, 3>(dense, lane, warp, v); break;
+    default: smem_load_dense_l<R, WB, 4>(dense, lane, warp, v); break;
+  }
+}
+template <int R, int WB>
+__device__ __forceinline__ void smem_store_dense(int layout, float2* dense, int lane, int warp, const float2* v) {
+  switch (layout) {
+    case 0: smem_store_dense_l<R, WB, 0>(dense, lane, warp, v); break;
+    case 1: smem_store_dense_l<R, WB, 1>(dense, lane, warp, v); break;
+    case 2: smem_store_dense_l<R, WB, 2>(dense, lane, warp, v); break;
+    case 3: smem_store_dense_l<R, WB, 3>(dense, lane, warp, v); break;
+    default: smem_store_dense_l<R, WB, 4>(dense, lane, warp, v); break;
+  }
+}
+
 template <int R, int WB, int AB, typename C2>
 __device__ __forceinline__ void smem_load(int layout, const C2* tile, uint32_t sbase, C2* v) {
   switch (layout) {
@@ -694,7 +760,14 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       }
     }
   } else if (op.src == SRC_SMEM_D) {
-    smem_load<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
+    bool dn = false;
+    if constexpr (AB == 8) {
+      if (A.dense) {
+        smem_load_dense<R, WB>(op.layout, dense_tile(tile), lane, warp, v);
+        dn = true;
+      }
+    }
+    if (!dn) smem_load<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
   }
   if constexpr (AB == 8) {
     if (A.tma_load && op.dstg && op.src == SRC_SMEM_D) {
@@ -1008,7 +1081,14 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
         gray_ptr_walk<R>(gstate, geo.gb, geo.gstr, [&](int j, C2* q) { __stcg(q, v[j]); });
     }
   } else {
-    smem_store<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
+    bool dn = false;
+    if constexpr (AB == 8) {
+      if (A.dense) {
+        smem_store_dense<R, WB>(op.layout, dense_tile(tile), lane, warp, v);
+        dn = true;
+      }
+    }
+    if (!dn) smem_store<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
   }
 }
 
@@ -1155,7 +1235,12 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
           }
         }
       }
-      __syncthreads();  // previous tile finished with shared memory
+      // previous tile finished with shared memory. Not needed when the tile
+      // came by a tensor load into dense slots and the first round reads no
+      // tile constants: every warp read the previous tile's last round before
+      // that load was issued, and the first round writes back only the slots
+      // it read (dense == 2)
+      if (!(AB == 8 && tload && A.dense == 2)) __syncthreads();
       if (ahead) {
         const uint64_t next = unit + gridDim.x;
         if (next < P.n_units && tid < kTileConstInts)

@@ -532,3 +532,25 @@ def test_tma_tile_loads_bitwise(n, shape):
                 assert torch.equal(ref[0], st)
                 assert (ref[1]["exp_c"], ref[1]["norm"]) == (e["exp_c"], e["norm"])
     del ref
+
+
+@pytest.mark.parametrize("n,shape,tma", [(24, "4x3", False), (27, "5x4", True), (30, "5x4", True), (30, "5x4", False)])
+def test_dense_slots_bitwise(n, shape, tma, monkeypatch):
+    # shared-memory rounds in dense tile-index slots (passes without the
+    # padded menu layout; with tensor loads the tile's first barrier goes as
+    # well) move the same amplitudes: identical states, <C> and norm
+    import torch
+    u, v, w = graph("complete", n, 970 + n)
+    ref = None
+    for dense in ("1", "0"):
+        monkeypatch.setenv("QAOA_DENSE", dense)
+        with sim(n, u, v, w, S, "c64", opts=dict(shape=shape, l2_prefetch=tma, tma_load=tma)) as s:
+            s.run(3, 0.6, 0.3)
+            e = s.expect()
+            st = s.state().view(torch.int64)
+            if ref is None:
+                ref = (st.clone(), e)
+            else:
+                assert torch.equal(ref[0], st)
+                assert (ref[1]["exp_c"], ref[1]["norm"]) == (e["exp_c"], e["norm"])
+    del ref
