@@ -236,6 +236,9 @@ TileShape shape_of(int id, int prec) {
   s.WB = WB[id];
   s.amp_bytes = amp_bytes(prec);
   s.paired = prec == QAOA_C64 && paired_layout_enabled();
+  // the 5x4 tile's passes load their tiles by tensor loads (QAOA_PAIRED_STORE=0
+  // keeps the paired first round)
+  s.paired_store_first = s.paired && id == 4 && on_off(0, "QAOA_PAIRED_STORE", 1);
   return s;
 }
 

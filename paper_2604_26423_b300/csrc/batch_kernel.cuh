@@ -370,11 +370,11 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     constexpr int TILE = padded_size<8>(FR + 5 + kBatchWB);
     float2* tile = reinterpret_cast<float2*>(smem);
     int* tconst = reinterpret_cast<int*>(tile + TILE);
-    wacc[2 * tid] = 0.0;
-    wacc[2 * tid + 1] = 0.0;
+    wacc[tid] = 0.0;
+    wacc[kBatchThreads + tid] = 0.0;
     for (uint32_t u = u0; u < u1; ++u) fwd_unit<float, FR, kBatchWB, FAST>(P, A, u, tile, tconst, phase, wacc);
     if (M.reduce) {
-      finish_thread_sums<float>(wacc, tid);
+      finish_thread_sums<float, kBatchThreads>(wacc, tid);
       __syncthreads();
       double sN, sC;
       reduce_thread_sums<kBatchThreads>(wacc, sN, sC);

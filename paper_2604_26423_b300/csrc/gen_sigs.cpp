@@ -11,7 +11,8 @@
 // the middle), both with floating coalescing bits; adjoint plans in the
 // gradient's order, p = 1..12. Tile shape 5x4 (T = 14): forward plans of
 // qaoa_run's order for n = 27..34, p = 0..12 (the sizes where it takes one
-// mixer group fewer than 4x3).
+// mixer group fewer than 4x3), without and with the paired layout, the latter
+// preferring it on the storing last round (the default) or on the first.
 //
 // Usage: gen_sigs <output file>
 #include <cstdio>
@@ -81,11 +82,14 @@ int main(int argc, char** argv) {
   sh54.WB = 4;
   TileShape sh54p = sh54;
   sh54p.paired = true;
+  TileShape sh54s = sh54p;
+  sh54s.paired_store_first = true;  // the library's default 5x4 shape
   std::set<std::vector<uint32_t>> fwd54;
   for (int n = 27; n <= 34; ++n)
     for (int p = 0; p <= 12; ++p) {
       collect(plan_forward(n, p, sh54, sh54.T(), 9, ORDER_LOW_LAST | PLAN_FLOAT_LANES), fwd54);
       collect(plan_forward(n, p, sh54p, sh54p.T(), 9, ORDER_LOW_LAST | PLAN_FLOAT_LANES), fwd54);
+      collect(plan_forward(n, p, sh54s, sh54s.T(), 9, ORDER_LOW_LAST | PLAN_FLOAT_LANES), fwd54);
     }
   FILE* f = fopen(argv[1], "w");
   if (!f) {

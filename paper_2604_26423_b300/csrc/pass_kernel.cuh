@@ -656,15 +656,15 @@ __device__ __forceinline__ void df_add(float2& acc, float2 y) {
   acc.y += e + y.y;
 }
 // complex64: thread tid's [norm, <C>] running sums are double-float pairs in
-// the memory of wacc[2 tid], wacc[2 tid + 1] during the passes; this turns
-// them into the FP64 values reduce_thread_sums reads (each thread its own).
-template <typename Real>
+// the memory of wacc[tid], wacc[NT + tid] during the passes; this turns them
+// into the FP64 values reduce_thread_sums reads (each thread its own).
+template <typename Real, int NT>
 __device__ __forceinline__ void finish_thread_sums(double* wacc, int tid) {
   if constexpr (sizeof(Real) == 4) {
-    const float2 a = reinterpret_cast<const float2*>(wacc)[2 * tid];
-    const float2 b = reinterpret_cast<const float2*>(wacc)[2 * tid + 1];
-    wacc[2 * tid] = double(a.x) + double(a.y);
-    wacc[2 * tid + 1] = double(b.x) + double(b.y);
+    const float2 a = reinterpret_cast<const float2*>(wacc)[tid];
+    const float2 b = reinterpret_cast<const float2*>(wacc)[NT + tid];
+    wacc[tid] = double(a.x) + double(a.y);
+    wacc[NT + tid] = double(b.x) + double(b.y);
   }
 }
 
@@ -676,7 +676,7 @@ __device__ __forceinline__ void reduce_thread_sums(const double* wacc, double& s
   sN = 0.0;
   sC = 0.0;
   if (threadIdx.x < 32) {
-    for (int t = threadIdx.x; t < NT; t += 32) { sN += wacc[2 * t]; sC += wacc[2 * t + 1]; }
+    for (int t = threadIdx.x; t < NT; t += 32) { sN += wacc[t]; sC += wacc[NT + t]; }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       sN += __shfl_xor_sync(0xffffffffu, sN, o);
@@ -687,7 +687,7 @@ __device__ __forceinline__ void reduce_thread_sums(const double* wacc, double& s
 
 // One round. For a round whose source is global memory, v already holds the
 // loaded amplitudes (issued before the tile's barrier). Reduction partials:
-// wacc[2 t], wacc[2 t + 1] hold thread t's FP64 running [norm, <C>] sums;
+// wacc[t], wacc[NT + t] hold thread t's running [norm, <C>] sums;
 // wacc[(2 + h) NT + t] thread t's partial of sampling block h of the tile.
 // CC: the kernel contains the C(x) code (cost phase, |+> initialisation and
 // reductions); passes without any of them run an instantiation without it
@@ -1018,11 +1018,11 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
       // at the end (finish_thread_sums, reduce_thread_sums)
       const int tid = (warp << 5) | lane;
       if constexpr (sizeof(Real) == 4) {
-        df_add(reinterpret_cast<float2*>(wacc)[2 * tid], sn);
-        df_add(reinterpret_cast<float2*>(wacc)[2 * tid + 1], scc);
+        df_add(reinterpret_cast<float2*>(wacc)[tid], sn);
+        df_add(reinterpret_cast<float2*>(wacc)[(32 << WB) + tid], scc);
       } else {
-        wacc[2 * tid] += double(sn);
-        wacc[2 * tid + 1] += double(scc);
+        wacc[tid] += double(sn);
+        wacc[(32 << WB) + tid] += double(scc);
       }
     }
   } else {
@@ -1338,11 +1338,11 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
     for (int i = tid; i < P.ncost; i += NT) ptab[i] = phase[i];
     phase = ptab;
   }
-  // per-thread FP64 running sums [norm, <C>], then per-thread block-sum
-  // partials (2^(T-12) blocks per tile)
+  // per-thread running sums [norm for all threads, <C> for all threads], then
+  // per-thread block-sum partials (2^(T-12) blocks per tile)
   __shared__ double wacc[(2 + (1 << kBlkBits<R, WB>)) * NT];
-  wacc[2 * tid] = 0.0;
-  wacc[2 * tid + 1] = 0.0;
+  wacc[tid] = 0.0;
+  wacc[NT + tid] = 0.0;
 
   // exhaustive extremes (optional): this CTA's minimum keys
   __shared__ unsigned long long ext_s[2];
@@ -1376,7 +1376,7 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
   }
 
   if (A.partial) {
-    finish_thread_sums<Real>(wacc, tid);
+    finish_thread_sums<Real, NT>(wacc, tid);
     __syncthreads();
     double sN, sC;
     reduce_thread_sums<NT>(wacc, sN, sC);

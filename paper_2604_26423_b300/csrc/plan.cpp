@@ -144,7 +144,8 @@ std::vector<RoundPlan> plan_rounds(const TileShape& sh, uint32_t a_bits, bool co
             rr.lam = (lam && r == 0) ? 1 : 0;
             out.push_back(rr);
           }
-          const int score = int(out.back().layout == 4) + int(first_src == SRC_GLOBAL && out[0].layout == 4);
+          const int score = (sh.paired_store_first ? 2 : 1) * int(out.back().layout == 4) +
+                            int(first_src == SRC_GLOBAL && out[0].layout == 4);
           if (score > best_score) {
             best_score = score;
             best = out;

@@ -38,6 +38,10 @@ struct TileShape {
   // the menu offers the paired global layout (id 4: register bit 0 on tile bit
   // 0, so each thread moves two adjacent 8-byte amplitudes per 16-byte access)
   bool paired = false;
+  // among equally short round sequences, a paired storing last round counts
+  // more than a paired loading first round (tiles that arrive by tensor
+  // loads into shared memory: their first round issues no global loads)
+  bool paired_store_first = false;
   int T() const { return R + 5 + WB; }
 };
 
