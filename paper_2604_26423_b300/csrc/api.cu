@@ -778,13 +778,6 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       pa.tma_load = 0;
       if (c->prec == QAOA_C64 && pa.prefetch == 2 && !pa.tma_store && tma_load_on(c) && tma_load_form(pd))
         pa.tma_load = 1;
-      // |+> passes: split release of the tile buffer (QAOA_SPLIT)
-      // (one tile per super-tile, a last round that reads shared memory)
-      pa.split = c->prec == QAOA_C64 && pp.init && pd.nsub == 1 && pd.sub[0].ninner == 0 &&
-                         pd.sub[0].nrounds >= 2 && pd.sub[0].rd[pd.sub[0].nrounds - 1].src == SRC_SMEM_D &&
-                         on_off(0, "QAOA_SPLIT", 1)
-                     ? 1
-                     : 0;
       // dense shared-memory slots (QAOA_DENSE)
       pa.dense = 0;
       if (c->prec == QAOA_C64 && on_off(0, "QAOA_DENSE", 1) && dense_form(pd)) {

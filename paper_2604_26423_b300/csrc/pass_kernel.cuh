@@ -54,11 +54,6 @@ struct PassArgs {
                           // once every thread has read the current tile's last round,
                           // and the first round reads it from there
   unsigned long long* err;  // error word: bit 0 set when a tensor-load wait gave up
-  int split;              // complex64 |+> passes with tile constants copied ahead: each
-                          // warp releases the tile buffer on an mbarrier once it has read
-                          // the last round, and the next tile waits on that instead of a
-                          // barrier (the wait finds the others' reads done, not their
-                          // stores)
   int dense;              // complex64, one tile per super-tile, no round in menu layout 2:
                           // shared-memory rounds use dense tile-index slots (1), and
                           // with tensor tile loads and a first round without tile
@@ -323,9 +318,6 @@ __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.p
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -778,13 +770,6 @@ __device__ __forceinline__ void fwd_round(const PassDev& P, const PassArgs& A, c
     if (!dn) smem_load<R, WB, AB>(op.layout, tile, entry & 0x7fffffffu, v);
   }
   if constexpr (AB == 8) {
-    if (A.split && op.dstg && op.src == SRC_SMEM_D) {
-      // this warp has read the tile's last round; warp 0 also has the next
-      // tile's constants (copied during this tile): release the buffer
-      if (warp == 0) cp_async_wait_all();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tbar + 16);
-    }
     if (A.tma_load && op.dstg && op.src == SRC_SMEM_D) {
       // once every warp has read the tile's last round, the buffer takes the
       // CTA's next tile by one tensor load, issued by the last warp to
@@ -1198,9 +1183,6 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       const bool tab = CC && sp.needs_c && !stream && sp.tct != nullptr;
       bool ahead = false;
       if constexpr (kSpec) ahead = tab && (first_sig<RS...>() >> 2 & 3u) == SRC_INIT_D;
-      const uint32_t tidx = tab ? *tcount : 0u;  // this tile's index in the CTA (tables)
-      bool split = false;
-      if constexpr (AB == 8) split = ahead && A.split && tidx != 0;
       if (tab) {
         tc = tconst + 32 * (*tcount & 1u);
         if (ahead && *tcount != 0) {
@@ -1258,16 +1240,7 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
       // tile constants: every warp read the previous tile's last round before
       // that load was issued, and the first round writes back only the slots
       // it read (dense == 2)
-      if (split) {
-        // the previous tile's last-round reads and this tile's constants
-        // were released by every warp (phase tidx - 1 of the split mbarrier)
-        if (!mbar_wait_bounded(tbar + 16, (tidx - 1u) & 1u, kTmaWaitNs)) {
-          if (lane == 0) atomicOr(A.err, 1ull);
-          __syncthreads();
-        }
-      } else if (!(AB == 8 && tload && A.dense == 2)) {
-        __syncthreads();
-      }
+      if (!(AB == 8 && tload && A.dense == 2)) __syncthreads();
       if (ahead) {
         const uint64_t next = unit + gridDim.x;
         if (next < P.n_units && tid < kTileConstInts)
@@ -1376,13 +1349,8 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
   if (tid < 2) ext_s[tid] = ~0ull;  // published by the first tile's barrier
 
   // tensor tile loads: the mbarrier, and the CTA's first tile
-  // tensor-load mbarrier; stop flag and warps' read count; split-release mbarrier
-  __shared__ __align__(8) unsigned long long tma_bar[3];
+  __shared__ __align__(8) unsigned long long tma_bar[2];  // mbarrier; stop flag, warps' read count
   const uint32_t tbar = (uint32_t)__cvta_generic_to_shared(tma_bar);
-  if (AB == 8 && A.split) {
-    if (tid == 0) mbar_init(tbar + 16, NT / 32);
-    __syncthreads();
-  }
   if (AB == 8 && A.tma_load) {
     if (tid == 0) {
       tma_bar[1] = 0ull;
