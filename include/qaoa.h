@@ -38,7 +38,8 @@ extern "C" {
 #define QAOA_EINVAL 1   /* invalid argument (sizes, graph, angles, shots) */
 #define QAOA_ENOMEM 2   /* allocation failed or a caller buffer is too small */
 #define QAOA_ECUDA 3    /* a CUDA runtime call failed; see qaoa_last_error */
-#define QAOA_ETIMEOUT 4 /* a bounded device-side wait gave up (batched queue) */
+#define QAOA_ETIMEOUT 4 /* a bounded device-side wait gave up (batched queue; a forward
+                           pass's tensor tile load, reported by qaoa_expect) */
 #define QAOA_ESTATE 5   /* call order violated (e.g. qaoa_expect before qaoa_run) */
 
 /* state precision: complex64 (2 x fp32 per amplitude) or complex128 */
@@ -189,7 +190,9 @@ int qaoa_run_angles(qaoa_ctx *ctx, int p, const double *gamma, const double *bet
  * (FP64 reductions), r = (<C> - C_min)/(C_max - C_min) (Eq. r with the exact
  * mean; 1 when C_max == C_min), and the exhaustive extremes with their smallest
  * indices (available before any run: then only the extremes may be requested).
- * Synchronises the stream. Errors: ESTATE (<C>, r or norm before a run), ECUDA.
+ * Synchronises the stream. Errors: ESTATE (<C>, r or norm before a run), ECUDA,
+ * ETIMEOUT (a bounded wait of the run's kernels gave up: the results are invalid;
+ * the error is cleared, so the next run can proceed).
  */
 int qaoa_expect(qaoa_ctx *ctx, double *exp_c, double *r, double *norm, int64_t *c_min,
                 int64_t *c_max, uint64_t *argmin, uint64_t *argmax);

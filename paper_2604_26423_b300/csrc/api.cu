@@ -786,6 +786,12 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
       }
     }
     pa.err = (unsigned long long*)((char*)c->d_result.p + kErrWordOffset);
+    {
+      // limit of one tensor-load wait (QAOA_TMA_WAIT_NS; the tests shorten it)
+      const char* w = getenv("QAOA_TMA_WAIT_NS");
+      const unsigned long long wn = w ? strtoull(w, nullptr, 10) : 0ull;
+      pa.tma_wait_ns = wn > 0 ? wn : kTmaWaitNs;
+    }
     // the first pass visits every index once: the extremes come with it when
     // they are not known yet
     pa.ext_keys = nullptr;

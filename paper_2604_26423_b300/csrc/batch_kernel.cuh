@@ -366,6 +366,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     A.tma_load = 0;
     A.err = nullptr;
     A.dense = 0;
+    A.tma_wait_ns = 0;
     A.ext_keys = nullptr;
     constexpr int TILE = padded_size<8>(FR + 5 + kBatchWB);
     float2* tile = reinterpret_cast<float2*>(smem);

@@ -54,6 +54,7 @@ struct PassArgs {
                           // once every thread has read the current tile's last round,
                           // and the first round reads it from there
   unsigned long long* err;  // error word: bit 0 set when a tensor-load wait gave up
+  unsigned long long tma_wait_ns;  // limit of one tensor-load wait (ns)
   int dense;              // complex64, one tile per super-tile, no round in menu layout 2:
                           // shared-memory rounds use dense tile-index slots (1), and
                           // with tensor tile loads and a first round without tile
@@ -336,10 +337,21 @@ __device__ __forceinline__ unsigned long long timer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // Waits for phase `parity` of the mbarrier, at most limit_ns: false when it
-// gave up.
+// gave up. A limit below 1 us means one non-blocking test (a suspended
+// try_wait could outlast it).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_test_wait(bar, parity)) return true;
+  if (limit_ns < 1000ull) return false;
   const unsigned long long t0 = timer_ns();
   while (!mbar_try_wait(bar, parity))
     if (timer_ns() - t0 > limit_ns) return false;
@@ -398,18 +410,21 @@ __device__ __forceinline__ uint32_t tile_read_count_add(uint32_t tbar) {
 __device__ __forceinline__ void tile_read_count_reset(uint32_t tbar) {
   asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(tbar + 12), "r"(0u) : "memory");
 }
-// Limit of one wait for a tensor tile load (ns). A wait that gives up sets
-// the error word and the CTA's stop flag (the word at tbar + 8, after the
-// mbarrier): the CTA then issues no further tensor loads and waits for none,
-// so the pass ends promptly with an invalid output.
+// Default limit of one wait for a tensor tile load (ns; PassArgs.tma_wait_ns).
+// A wait that gives up sets the error word and the CTA's stop word (at tbar +
+// 8, after the mbarrier: 1 + the parity of the phase it gave up on): the CTA
+// then issues no further tensor loads and waits for none, and before it ends
+// waits (bounded by this default) for the load it gave up on, so that no copy
+// is left in flight into its shared memory; the pass's output is invalid.
 constexpr unsigned long long kTmaWaitNs = 2000000000ull;
-__device__ __forceinline__ bool tma_stopped(uint32_t tbar) {
+__device__ __forceinline__ uint32_t tma_stop_word(uint32_t tbar) {
   uint32_t f;
   asm volatile("ld.volatile.shared.u32 %0, [%1];" : "=r"(f) : "r"(tbar + 8) : "memory");
-  return f != 0;
+  return f;
 }
-__device__ __forceinline__ void tma_stop(uint32_t tbar) {
-  asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(tbar + 8), "r"(1u) : "memory");
+__device__ __forceinline__ bool tma_stopped(uint32_t tbar) { return tma_stop_word(tbar) != 0; }
+__device__ __forceinline__ void tma_stop(uint32_t tbar, uint32_t parity) {
+  asm volatile("st.volatile.shared.u32 [%0], %1;" ::"r"(tbar + 8), "r"(1u + parity) : "memory");
 }
 
 // Dense (unpadded) view of a tile's shared memory, 128-byte aligned: the box
@@ -1200,8 +1215,8 @@ __device__ __forceinline__ void fwd_unit(const PassDev& P, const PassArgs& A, ui
           // (tile index order); the barrier below ends the reads before the
           // first round writes the padded tile
           const uint32_t k = (*tk)++;
-          if (!tma_stopped(tbar) && !mbar_wait_bounded(tbar, k & 1u, kTmaWaitNs)) {
-            tma_stop(tbar);
+          if (!tma_stopped(tbar) && !mbar_wait_bounded(tbar, k & 1u, A.tma_wait_ns)) {
+            tma_stop(tbar, k & 1u);
             if (lane == 0) atomicOr(A.err, 1ull);
           }
           constexpr uint32_t S0 = first_sig_or0<RS...>();
@@ -1369,6 +1384,13 @@ __device__ __forceinline__ void fwd_pass_body(const PassDev& P, const PassArgs& 
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
     fwd_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tile, tconst, phase, wacc, &tcount, ext_s, &M, tbar, &tk);
   if (A.tma_store && tid == 0) bulk_wait_all();  // the last tensor store is complete before the CTA ends
+  if (AB == 8 && A.tma_load) {
+    // a CTA whose wait gave up ends only once the load it gave up on has
+    // landed (bounded)
+    __syncthreads();
+    const uint32_t f = tid == 0 ? tma_stop_word(tbar) : 0u;
+    if (f) mbar_wait_bounded(tbar, f - 1u, kTmaWaitNs);
+  }
 
   if (CC && A.ext_keys) {
     __syncthreads();

@@ -554,3 +554,30 @@ def test_dense_slots_bitwise(n, shape, tma, monkeypatch):
                 assert torch.equal(ref[0], st)
                 assert (ref[1]["exp_c"], ref[1]["norm"]) == (e["exp_c"], e["norm"])
     del ref
+
+
+def test_tma_wait_limit_gives_etimeout_then_recovers(monkeypatch):
+    # the bounded wait for a tensor tile load: with a 1 ns limit the first wait
+    # of each CTA gives up at once (its tile's load was issued just before),
+    # sets the error word and stops the CTA's loads, and the CTA ends only once
+    # that load has landed; qaoa_expect reports ETIMEOUT. With the default
+    # limit the next run on the same device is correct (bitwise equal to the
+    # run without tensor loads)
+    import torch
+    from paper_2604_26423_b300.qaoa import QAOA_ETIMEOUT, QaoaError
+    n = 27
+    u, v, w = graph("complete", n, 1027)
+    opts = dict(shape="5x4", l2_prefetch=True)
+    monkeypatch.setenv("QAOA_TMA_WAIT_NS", "1")
+    with sim(n, u, v, w, S, "c64", opts=dict(opts, tma_load=True)) as s:
+        s.run(3, 0.6, 0.3)
+        with pytest.raises(QaoaError) as ei:
+            s.expect()
+        assert ei.value.code == QAOA_ETIMEOUT
+    monkeypatch.delenv("QAOA_TMA_WAIT_NS")
+    outs = []
+    for tl in (True, False):
+        with sim(n, u, v, w, S, "c64", opts=dict(opts, tma_load=tl)) as s:
+            s.run(3, 0.6, 0.3)
+            outs.append((s.state().view(torch.int64).clone(), s.expect()))
+    assert torch.equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
