@@ -107,8 +107,11 @@ def test_batch_gradient_matches_oracle_finite_difference():
     for i, d in enumerate(batch):
         g, bt = oracle.lr_schedule(d["p"], d["dgamma"], d["dbeta"])
         fd = oracle.lr_chain(*oracle.grad_fd(d["n"], d["u"], d["v"], d["w"], 0.1, g, bt))
-        assert abs(res["d_dgamma"][i] - fd[0]) <= 1e-3 * max(1.0, abs(fd[0])), (i, fd)
-        assert abs(res["d_dbeta"][i] - fd[1]) <= 1e-3 * max(1.0, abs(fd[1])), (i, fd)
+        eg = abs(res["d_dgamma"][i] - fd[0]) / max(1.0, abs(fd[0]))
+        eb = abs(res["d_dbeta"][i] - fd[1]) / max(1.0, abs(fd[1]))
+        print(f"\nbatch instance {i} (n={d['n']}, p={d['p']}) c64 gradient vs oracle FD: "
+              f"d/d dgamma {eg:.2e}, d/d dbeta {eb:.2e} (relative)")
+        assert eg <= 1e-3 and eb <= 1e-3, (i, fd)
 
 
 def test_batch_plain_mixer_form():
