@@ -1,19 +1,20 @@
 """The benchmark's plan shape anchored to the oracle and to complex128.
 
-The K_33 benchmark runs a plan of four mixer groups with the 4x3 tile (a low
-shared-memory group plus three windows of high bits, 256-byte runs) with
-cross-layer fused passes and the specialised kernels compiled for those round
-sequences. At 29 qubits the 4x3 tile takes the same kind of plan (four groups,
-256-byte runs); at 27 and 28 qubits it takes three groups with 128-byte runs,
-and the 5x4 tile three groups with 256-byte runs. The oracle still finishes
-in one to three minutes there, so these tests compare those plans element by
-element with the oracle's gate-by-gate complex128 state (Sec. II-B, Eqs. UC
-and UB), in both precisions, both cost modes and both group orders.
+The K_33 benchmark runs the 5x4 tile's plan: three mixer groups (a low
+shared-memory group plus two windows of high bits), 7 passes at p = 3, with
+cross-layer fused passes, tensor tile loads, dense shared-memory slots and the
+specialised kernels compiled for those round sequences. From 27 to 29 qubits
+the 5x4 tile takes the same kind of plan; the 4x3 tile (the other forward
+shape) takes four groups at 29 qubits and three with 128-byte runs at 27 and
+28. The oracle still finishes in one to three minutes there, so these tests
+compare those plans element by element with the oracle's gate-by-gate
+complex128 state (Sec. II-B, Eqs. UC and UB), in both precisions, both cost
+modes and both group orders.
 
 Where the oracle cannot run (K_32, 64 GiB in complex128), the complex64 path
 is compared with the complex128 path of the same GPU.
 
-Tolerances (the benchmark spec's equivalence rules): complex128 state L2 <= 1e-12;
+Tolerances (the stated equivalence bounds): complex128 state L2 <= 1e-12;
 complex64 state L2 <= 1e-4; |r - r_oracle| <= 1e-6 for both (stated per run
 on stdout); extremes and their indices exact.
 """
