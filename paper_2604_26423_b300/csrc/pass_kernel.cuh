@@ -50,9 +50,9 @@ struct PassArgs {
   int tma_store;          // the final round writes the tile densely into shared memory
                           // and one thread stores it with a tensor store (PassTma)
   int tma_load;           // complex64, one tile per super-tile: the CTA's next tile is
-                          // loaded into shared memory by one tensor load (PassTma.tmap)
-                          // once every thread has read the current tile's last round,
-                          // and the first round reads it from there
+                          // loaded into shared memory by one tensor load (PassTma.tmap),
+                          // issued by the last warp to read the current tile's last
+                          // round, and the first round reads it from there
   unsigned long long* err;  // error word: bit 0 set when a tensor-load wait gave up
   unsigned long long tma_wait_ns;  // limit of one tensor-load wait (ns)
   int dense;              // complex64, one tile per super-tile, no round in menu layout 2:
