@@ -34,6 +34,12 @@ struct AdjArgs {
   int phase_in_smem;
   int prefetch;           // 2: the CTA's next tile of psi (PassTma.tmap) and lambda
                           // (PassTma.smap) into L2 by tensor prefetches; 0: none
+  int tma_load;           // complex64, one tile per super-tile: the CTA's next tiles of
+                          // psi and lambda are loaded into shared memory by tensor loads
+                          // (PassTma.tmap, .smap) issued by the last warp to read the
+                          // current tile's last round; the first round reads them there
+  unsigned long long* err;          // error word: bit 0 set when a tensor-load wait gave up
+  unsigned long long tma_wait_ns;   // limit of one tensor-load wait (ns)
 };
 
 // Sum over the round's register pairs along bit i of Im(conj(l_a) v_b + conj(l_b) v_a).
@@ -163,7 +169,8 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
                                           int gpar, const int* tconst, const typename Cx<Real>::T* phase, int lane,
                                           int warp,
                                           Real& ga, Real& gc, Real& gbv, Real& ge, Real& sc,
-                                          typename Cx<Real>::T* v, typename Cx<Real>::T* l, const AdjPrefetch& pf) {
+                                          typename Cx<Real>::T* v, typename Cx<Real>::T* l, const AdjPrefetch& pf,
+                                          const PassTma* M = nullptr, uint32_t tbar = 0, uint64_t tnext = ~0ull) {
   using C2 = typename Cx<Real>::T;
   constexpr int NA = 1 << R;
   constexpr int AB = sizeof(C2);
@@ -227,6 +234,30 @@ __device__ __forceinline__ void adj_round(const PassDev& P, const AdjArgs& A, co
   } else {
     smem_load<R, WB, AB>(op.layout, tv, sb, v);
     smem_load<R, WB, AB>(op.layout, tl, sb, l);
+  }
+  if constexpr (sizeof(Real) == 4) {
+    if (A.tma_load && op.dstg && op.src == SRC_SMEM_D) {
+      // once every warp has read the tile's last round, the tiles take the
+      // CTA's next ones by tensor loads, issued by the last warp to finish
+      // its reads (lambda is not loaded where the pass creates it)
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();
+        if (tile_read_count_add(tbar) == (1u << WB) - 1) {
+          __threadfence_block();
+          tile_read_count_reset(tbar);
+          if (tnext < P.n_units && !tma_stopped(tbar)) {
+            fence_proxy_async_smem();
+            int32_t c[5];
+            tile_coords(*M, P.outer_runs.scatter(tnext), c);
+            const bool two = !(CC && sp.rd[0].lam);
+            mbar_expect_tx(tbar, (uint32_t(AB) << (R + 5 + WB)) * (two ? 2u : 1u));
+            tma_load_box(&M->tmap, M->tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tv)), tbar);
+            if (two) tma_load_box(&M->smap, M->tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tl)), tbar);
+          }
+        }
+      }
+    }
   }
 
   if constexpr (sizeof(Real) == 4) {
@@ -340,7 +371,8 @@ template <typename Real, int R, int WB, bool FAST, bool CC = true, uint32_t... R
 __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uint64_t unit,
                                          typename Cx<Real>::T* tv, typename Cx<Real>::T* tl, int* tconst,
                                          const typename Cx<Real>::T* phase, double& gA, double& gC, double& gB,
-                                         double& gE, uint32_t* tcount = nullptr, const PassTma* M = nullptr) {
+                                         double& gE, uint32_t* tcount = nullptr, const PassTma* M = nullptr,
+                                         uint32_t tbar = 0, uint32_t* tk = nullptr) {
   using C2 = typename Cx<Real>::T;
   constexpr int T = R + 5 + WB;
   constexpr int NT = 32 << WB;
@@ -375,7 +407,8 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
           if (!(CC && sp.rd[0].lam)) tma_prefetch_l2(&M->smap, M->tdims, c);
         }
       }
-      if (load0 && !pf.on) {
+      const bool tload = sizeof(Real) == 4 && load0 && A.tma_load;
+      if (load0 && !pf.on && !tload) {
         const RoundGeo<R, WB, sizeof(C2)> g0(sp, sp.rd[0], gbase, lane, warp, A.ctabs);
         gray_ptr_walk<R>(reinterpret_cast<const C2*>(A.psi), g0.gb, g0.gstr,
                          [&](int j, const C2* q) { v[j] = __ldcg(q); });
@@ -392,6 +425,42 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
           tc[tid == 15 ? 16 : tid] = __ldg(sp.tct + (((unit << sp.ninner) + ti) * kTileConstInts + tid));
       }
       if (pf.on) cp_async_wait_all();  // this tile's copies (issued by this thread)
+      if constexpr (sizeof(Real) == 4) {
+        if (tload) {
+          // this tile's vectors arrived by tensor loads (the CTA's k-th,
+          // mbarrier phase k & 1): the first round's amplitudes from the
+          // dense boxes; the barrier below ends the reads before the first
+          // round writes the padded tiles
+          const uint32_t k = (*tk)++;
+          if (!tma_stopped(tbar) && !mbar_wait_bounded(tbar, k & 1u, A.tma_wait_ns)) {
+            tma_stop(tbar, k & 1u);
+            if (lane == 0) atomicOr(A.err, 1ull);
+          }
+          constexpr uint32_t S0 = first_sig_or0<RS...>();
+          const RoundDev& rd0 = sp.rd[0];
+          uint32_t tb = 0;
+#pragma unroll
+          for (int i = 0; i < 5; ++i) tb |= uint32_t(lane >> i & 1) << tile_bit<R, WB, S0>(rd0, 1, i);
+#pragma unroll
+          for (int i = 0; i < WB; ++i) tb |= uint32_t(warp >> i & 1) << tile_bit<R, WB, S0>(rd0, 2, i);
+          uint32_t toff[1 << R];
+#pragma unroll
+          for (int j = 0; j < (1 << R); ++j) {
+            toff[j] = 0;
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+              if (j >> i & 1) toff[j] |= 1u << tile_bit<R, WB, S0>(rd0, 0, i);
+          }
+          const C2* dv = dense_tile(tv);
+#pragma unroll
+          for (int j = 0; j < (1 << R); ++j) v[j] = dv[tb + toff[j]];
+          if (!(CC && rd0.lam)) {
+            const C2* dl = dense_tile(tl);
+#pragma unroll
+            for (int j = 0; j < (1 << R); ++j) l[j] = dl[tb + toff[j]];
+          }
+        }
+      }
       __syncthreads();
       if (CC && sp.needs_c && !stream && !tab) {
         if (tid == 0) tconst[16] = 0;
@@ -406,7 +475,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
           const RoundDev& rd = sp.rd[r];
           if (rd.src == SRC_SMEM_D) __syncthreads();
           adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, gpar, tc, phase, lane, warp, gA, gC, gB, gE,
-                                           sc, v, l, pf);
+                                           sc, v, l, pf, M, tbar, unit + gridDim.x);
         }
       } else {
         // fp32: the terms of one tile are summed in fp32, then added in FP64
@@ -419,7 +488,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
             constexpr uint32_t S = decltype(sigc)::value;
             if constexpr ((S >> 2 & 3u) == SRC_SMEM_D) __syncthreads();
             adj_round<Real, R, WB, FAST, CC, S>(P, A, sp, sp.rd[r], tv, tl, gbase, gpar, tc, phase, lane, warp, ga,
-                                                gc, gbv, ge, sc, v, l, pf);
+                                                gc, gbv, ge, sc, v, l, pf, M, tbar, unit + gridDim.x);
             ++r;
           };
           (run(std::integral_constant<uint32_t, RS>{}), ...);
@@ -428,7 +497,7 @@ __device__ __forceinline__ void adj_unit(const PassDev& P, const AdjArgs& A, uin
             const RoundDev& rd = sp.rd[r];
             if (rd.src == SRC_SMEM_D) __syncthreads();
             adj_round<Real, R, WB, FAST, CC>(P, A, sp, rd, tv, tl, gbase, gpar, tc, phase, lane, warp, ga, gc, gbv,
-                                             ge, sc, v, l, pf);
+                                             ge, sc, v, l, pf, M, tbar, unit + gridDim.x);
           }
         }
         gA += double(ga);
@@ -474,8 +543,39 @@ __device__ __forceinline__ void adj_pass_body(const PassDev& P, const AdjArgs& A
       cp_async_commit();
     }
   }
+  // tensor tile loads: the mbarrier (then the stop word and the warps' read
+  // count), and the CTA's first tiles
+  __shared__ __align__(8) unsigned long long tma_bar[2];
+  const uint32_t tbar = (uint32_t)__cvta_generic_to_shared(tma_bar);
+  uint32_t tk = 0;
+  if constexpr (sizeof(Real) == 4) {
+    if (A.tma_load) {
+      if (tid == 0) {
+        tma_bar[1] = 0ull;
+        mbar_init(tbar, 1);
+      }
+      __syncthreads();
+      if (tid == 0 && blockIdx.x < P.n_units) {
+        int32_t c[5];
+        tile_coords(M, P.outer_runs.scatter(blockIdx.x), c);
+        const bool two = !(CC && P.sub[0].rd[0].lam);
+        mbar_expect_tx(tbar, (uint32_t(AB) << T) * (two ? 2u : 1u));
+        tma_load_box(&M.tmap, M.tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tv)), tbar);
+        if (two) tma_load_box(&M.smap, M.tdims, c, (uint32_t)__cvta_generic_to_shared(dense_tile(tl)), tbar);
+      }
+    }
+  }
   for (uint64_t unit = blockIdx.x; unit < P.n_units; unit += gridDim.x)
-    adj_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE, &tcount, &M);
+    adj_unit<Real, R, WB, FAST, CC, RS...>(P, A, unit, tv, tl, tconst, phase, gA, gC, gB, gE, &tcount, &M, tbar, &tk);
+  if constexpr (sizeof(Real) == 4) {
+    if (A.tma_load) {
+      // a CTA whose wait gave up ends only once the loads it gave up on have
+      // landed (bounded)
+      __syncthreads();
+      const uint32_t f = tid == 0 ? tma_stop_word(tbar) : 0u;
+      if (f) mbar_wait_bounded(tbar, f - 1u, kTmaWaitNs);
+    }
+  }
 
   __shared__ double red[4][32];
   for (int o = 16; o > 0; o >>= 1) {

@@ -1107,9 +1107,24 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     PassTma pt;
     memset(&pt, 0, sizeof pt);
     aa.prefetch = 0;
-    if (c->prec == QAOA_C64 && pd.sub[0].cgtab < 0 && adj_l2_prefetch(c) &&
-        prefetch_tensor_map(n, pd, aa.psi, pt, &pt.tmap) && prefetch_tensor_map(n, pd, aa.lam, pt, &pt.smap))
-      aa.prefetch = 2;
+    aa.tma_load = 0;
+    {
+      // tensor loads of each tile pair into shared memory (QAOA_ADJ_TMA_LOAD)
+      const bool c64_single = c->prec == QAOA_C64 && pd.sub[0].cgtab < 0;
+      const bool want_tma = c64_single && on_off(0, "QAOA_ADJ_TMA_LOAD", 1) && tma_load_form(pd);
+      const bool want_pf = c64_single && adj_l2_prefetch(c);
+      if ((want_tma || want_pf) && prefetch_tensor_map(n, pd, aa.psi, pt, &pt.tmap) &&
+          prefetch_tensor_map(n, pd, aa.lam, pt, &pt.smap)) {
+        if (want_pf) aa.prefetch = 2;
+        if (want_tma) aa.tma_load = 1;
+      }
+    }
+    aa.err = (unsigned long long*)((char*)c->d_result.p + kErrWordOffset);
+    {
+      const char* w = getenv("QAOA_TMA_WAIT_NS");
+      const unsigned long long wn = w ? strtoull(w, nullptr, 10) : 0ull;
+      aa.tma_wait_ns = wn > 0 ? wn : kTmaWaitNs;
+    }
     int bps = 0;
     bool cc = false;
     for (const SubPassPlan& sp : pp.subs) cc = cc || sp.needs_c || sp.linit;
@@ -1154,8 +1169,16 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     CUDA_TRY(c, cudaGetLastError());
   }
   std::vector<double> h(4 * npass);
+  uint64_t errw = 0;
   CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->d_gacc.p, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&errw, (char*)c->d_result.p + kErrWordOffset, 8, cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (errw) {
+    CUDA_TRY(c, cudaMemsetAsync((char*)c->d_result.p + kErrWordOffset, 0, 8, c->stream));
+    c->state_ready = false;
+    c->sums_ready = false;
+    return c->set_err(QAOA_ETIMEOUT, "a bounded wait for a tensor tile load gave up in a gradient pass");
+  }
   for (size_t pi = 0; pi < npass; ++pi) {
     const PassPlan& pp = plan->passes[pi];
     if (pp.layer_a >= 0) gbt[pp.layer_a] += -2.0 * h[4 * pi];

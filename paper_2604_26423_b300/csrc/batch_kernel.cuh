@@ -396,6 +396,9 @@ __device__ __forceinline__ void batch_pass(const BatchArgs& B, const BatchInst& 
     A.partial = nullptr;
     A.phase_in_smem = 0;
     A.prefetch = 0;
+    A.tma_load = 0;
+    A.err = nullptr;
+    A.tma_wait_ns = 0;
     constexpr int TILE = padded_size<8>(kBatchRAdj + 5 + kBatchWBAdj);
     float2* tv = reinterpret_cast<float2*>(smem);
     float2* tl = tv + TILE;

@@ -241,6 +241,46 @@ def test_adjoint_tile_prefetch_identical(monkeypatch):
 @pytest.mark.gpu
 @pytest.mark.parametrize("ckpt", [True, False])
 @pytest.mark.parametrize("n,p", [(22, 3), (26, 2)])
+def test_adjoint_tma_tile_loads_identical(n, p, ckpt, monkeypatch):
+    # psi and lambda tiles loaded into shared memory by tensor loads (issued
+    # from the previous tile's last round) carry the same amplitudes as the
+    # global loads: bitwise identical gradients and <C>, with stored forward
+    # states and with psi uncomputed
+    from paper_2604_26423_b300 import inputs
+    from paper_2604_26423_b300.qaoa import Simulator
+    u, v, w = inputs.complete_graph(n, 940 + n)
+    res = []
+    for tl in ("1", "0"):
+        monkeypatch.setenv("QAOA_ADJ_TMA_LOAD", tl)
+        with Simulator(n, u, v, w, 0.1, "c64", with_grad=True, opts=dict(grad_checkpoint=ckpt)) as s:
+            res.append(s.grad(p, 0.6, 0.3))
+    a, b = res
+    assert np.array_equal(a["g_gamma"], b["g_gamma"]) and np.array_equal(a["g_beta"], b["g_beta"])
+    assert a["exp_c"] == b["exp_c"]
+
+
+@pytest.mark.gpu
+def test_adjoint_tma_wait_limit_gives_etimeout_then_recovers(monkeypatch):
+    # a 1 ns limit makes the adjoint's tensor-load waits give up: qaoa_grad
+    # reports ETIMEOUT, and the next gradient on the same device is correct
+    from paper_2604_26423_b300 import inputs
+    from paper_2604_26423_b300.qaoa import QAOA_ETIMEOUT, QaoaError, Simulator
+    n, p = 24, 3
+    u, v, w = inputs.complete_graph(n, 1124)
+    with Simulator(n, u, v, w, 0.1, "c64", with_grad=True) as s:
+        ref = s.grad(p, 0.6, 0.3)
+        monkeypatch.setenv("QAOA_TMA_WAIT_NS", "1")
+        with pytest.raises(QaoaError) as ei:
+            s.grad(p, 0.6, 0.3)
+        assert ei.value.code == QAOA_ETIMEOUT
+        monkeypatch.delenv("QAOA_TMA_WAIT_NS")
+        again = s.grad(p, 0.6, 0.3)
+    assert np.array_equal(ref["g_gamma"], again["g_gamma"]) and np.array_equal(ref["g_beta"], again["g_beta"])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("ckpt", [True, False])
+@pytest.mark.parametrize("n,p", [(22, 3), (26, 2)])
 def test_adjoint_l2_prefetch_identical(n, p, ckpt):
     # tensor prefetches of the next tile of psi and lambda into L2 move no
     # data into the kernel: bitwise identical gradients and <C>, with stored
