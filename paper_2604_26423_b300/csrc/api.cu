@@ -780,9 +780,11 @@ int run_forward(qaoa_ctx* c, int p, const double* gamma, const double* beta, int
         pa.tma_load = 1;
       // dense shared-memory slots (QAOA_DENSE)
       pa.dense = 0;
+      // (only where they drop the tile's first barrier: with the 4x3 tile's
+      // passes, which load through the load-store unit, they measured slower)
       if (c->prec == QAOA_C64 && on_off(0, "QAOA_DENSE", 1) && dense_form(pd)) {
         const RoundDev& r0 = pd.sub[0].rd[0];
-        pa.dense = pa.tma_load && !r0.cost && !r0.reduce && !r0.lam && r0.src == SRC_GLOBAL_D ? 2 : 1;
+        pa.dense = pa.tma_load && !r0.cost && !r0.reduce && !r0.lam && r0.src == SRC_GLOBAL_D ? 2 : 0;
       }
     }
     pa.err = (unsigned long long*)((char*)c->d_result.p + kErrWordOffset);
