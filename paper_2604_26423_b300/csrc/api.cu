@@ -1039,12 +1039,37 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
       return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
     }
   }
+  // two vectors: when the plans mirror each other, the forward's last pass
+  // writes psi_p into the adjoint vector's buffer and leaves its input psi_{P-1}
+  // in the state; the adjoint's first pass, which undoes exactly that pass,
+  // reads psi_p there, creates lambda in place and need not write psi back
+  // (one state write fewer; QAOA_GRAD_HYBRID=0 keeps the in-place forward)
+  void* lam = lambda_ptr(c);
+  if (!lam) return c->set_err(QAOA_ENOMEM, "allocation of the adjoint vector failed");
+  bool hybrid = false;
+  if (outs.empty() && n >= std::max(fwd_shape(c, c->prec).T(), kSmallMaxQubits + 1) &&
+      on_off(0, "QAOA_GRAD_HYBRID", 1)) {
+    try {
+      const Plan* fp = get_plan(c, p, fwd_order);
+      if (!plans_mirror(*fp, *plan) && fwd_order != grad_bwd_order(c)) {
+        fwd_order = grad_bwd_order(c);
+        fp = get_plan(c, p, fwd_order);
+      }
+      if (plans_mirror(*fp, *plan) && fp->passes.size() >= 2 && fp->passes.back().subs.size() == 1) {
+        outs.assign(fp->passes.size(), c->state);
+        outs.back() = lam;
+        hybrid = true;
+      } else {
+        fwd_order = grad_fwd_order(c);
+      }
+    } catch (std::exception& ex) {
+      return c->set_err(QAOA_EINVAL, "planner: %s", ex.what());
+    }
+  }
   // forward: psi_p (and the stored states)
   int rc = run_forward(c, p, gamma, beta, fwd_order, false, outs.empty() ? nullptr : outs.data());
   c->shape_force = -1;
   if (rc) return rc;
-  void* lam = lambda_ptr(c);
-  if (!lam) return c->set_err(QAOA_ENOMEM, "allocation of the adjoint vector failed");
   const bool stream = c->cost_mode == QAOA_COST_STREAM;
   const long long nc = c->c_hi - c->c_lo + 1;
   const size_t tile_amps = ab == 8 ? padded_size<8>(T) : padded_size<16>(T);
@@ -1094,8 +1119,13 @@ int run_gradient(qaoa_ctx* c, int p, const double* gamma, const double* beta, do
     const PassDev& pd = pds[pi];
     const bool fast = fasts[pi];
     AdjArgs aa;
-    aa.psi = outs.empty() ? c->state : outs[npass - 1 - pi];
-    aa.psi_store = outs.empty() ? 1 : 0;
+    if (hybrid) {
+      aa.psi = pi == 0 ? lam : c->state;
+      aa.psi_store = pi == 0 ? 0 : 1;
+    } else {
+      aa.psi = outs.empty() ? c->state : outs[npass - 1 - pi];
+      aa.psi_store = outs.empty() ? 1 : 0;
+    }
     aa.lam = lam;
     aa.diag = stream ? (const int32_t*)((char*)c->aux + (c->aux_bytes - (size_t(4) << n))) : nullptr;
     aa.phase = pp.layer_c >= 0 && c->d_phase.p

@@ -329,6 +329,32 @@ def test_grad_stored_forward_states(n, p, prec, monkeypatch):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("n,p,prec", [(16, 3, "c128"), (22, 4, "c64"), (26, 2, "c64")])
+def test_grad_two_vectors_forward_last_pass_out_of_place(n, p, prec, monkeypatch):
+    # with two vectors, the forward's last pass writes psi_p into the adjoint
+    # vector's buffer and the adjoint's first pass (its mirror) reads it there
+    # and does not write psi back: the gradients of the in-place forward up
+    # to rounding, one state write fewer (the adjoint's counted bytes)
+    u, v, w = inputs.complete_graph(n, 1060 + n)
+    monkeypatch.setenv("QAOA_GRAD_CHECKPOINT", "0")
+    res, adj_bytes = [], []
+    for hy in ("1", "0"):
+        monkeypatch.setenv("QAOA_GRAD_HYBRID", hy)
+        with sim(n, u, v, w, S, prec, with_grad=True) as s:
+            s.profile(True)
+            res.append(s.grad(p, 0.6, 0.3))
+            adj_bytes.append(s.profile_read("adjoint")["bytes"])
+    a, b = res
+    tol = 1e-11 if prec == "c128" else 2e-4
+    scale = max(np.max(np.abs(b["g_gamma"])), np.max(np.abs(b["g_beta"])))
+    assert np.max(np.abs(a["g_gamma"] - b["g_gamma"])) <= tol * scale
+    assert np.max(np.abs(a["g_beta"] - b["g_beta"])) <= tol * scale
+    assert abs(a["exp_c"] - b["exp_c"]) <= tol * abs(b["exp_c"])
+    sb = (8 if prec == "c64" else 16) << n
+    assert adj_bytes[1] - adj_bytes[0] == sb
+
+
+@pytest.mark.gpu
 def test_grad_stored_states_vs_oracle_fd():
     # complex128 with stored forward states against the oracle's central
     # differences (the default path when memory allows)
