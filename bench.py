@@ -251,10 +251,11 @@ def grad_ratio(args, stream, reps: int = 3):
     # amplitudes) of the plan's P passes: the forward moves 2P - 1 (its first
     # pass only writes); the adjoint with stored states 3P - 2 (read psi and
     # lambda, write lambda; the first reads psi only, the last writes
-    # nothing), with two vectors 4P - 3 (psi written back as well)
+    # nothing), with two vectors 4P - 4 (psi written back as well, except by
+    # the first pass, whose input the forward's last pass left in place)
     from paper_2604_26423_b300.qaoa import describe_plan
     npass = int(re.search(r"passes=(\d+)", describe_plan(gn, gp, "c64")).group(1))
-    sw_f, sw_c, sw_2 = 2 * npass - 1, 3 * npass - 2, 4 * npass - 3
+    sw_f, sw_c, sw_2 = 2 * npass - 1, 3 * npass - 2, 4 * npass - 4
     return {"workload": f"K_{gn} complex64, p={gp}, dgamma={GRAD_DGAMMA}, dbeta={GRAD_DBETA}",
             "forward_ms": t_fwd, "grad_ms": t_grad, "ratio": t_grad / t_fwd,
             "grad_ms_two_vectors": t_grad2, "ratio_two_vectors": t_grad2 / t_fwd,
